@@ -1,0 +1,194 @@
+/*
+ * lbsph — lattice Boltzmann for moving rigid spheroids on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the CUDA library.  The method is the one of Thampi, Stratford and
+ * Henrich, "Simulating dynamics of ellipsoidal particles using lattice
+ * Boltzmann method": a D3Q19 lattice Boltzmann fluid (Sec. II.A, Eq. 1-4)
+ * coupled to rigid ellipsoids by link bounce-back on moving boundaries
+ * (Sec. II.B, Eq. fb and Eq. ub), momentum-exchange forces split into
+ * velocity-independent parts and drag matrices (Eq. Fsplit-Eq. drag4), and an
+ * implicit update of translational / angular velocity with a quaternion
+ * orientation (Sec. II.C-D, Eq. Fdiscrete, Eq. Tdiscrete, Eq. posupdate,
+ * Eq. qnplus0-1, Eq. Irot, Eq. Irotdiff), one iteration being the ten steps of
+ * the paper's Appendix.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns lb_status; nothing throws or aborts across the ABI.
+ *    lb_last_error() gives a message for the last failing call on a context.
+ *  - The caller owns every buffer it passes; the library copies inputs and
+ *    never keeps a caller pointer after the call returns.
+ *  - The library owns its device memory.  It allocates through
+ *    lb_options.alloc / lb_options.release when given (e.g. the PyTorch caching
+ *    allocator), else with cudaMalloc / cudaFree.
+ *  - Calls taking a stream enqueue work on it (NULL = the context's own
+ *    stream) and return without waiting, except the getters, which wait for
+ *    the work they need.  Device-side errors (a NaN in a particle state, a
+ *    particle too large for the configured scratch, particles that come too
+ *    close) are recorded in a device status word and returned by the next call
+ *    that synchronises (the getters, lb_synchronize).
+ *  - A context is not thread safe.  Units are lattice units (dx = dt = 1).
+ *  - Quaternions are (q0, q1, q2, q3), unit, Hamilton product, rotating body
+ *    axes into the lab frame (Eq. vectrotn); the body x axis is the axis of
+ *    semi-axis a (the spheroid's long axis e).
+ */
+#ifndef LBSPH_H
+#define LBSPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBSPH_ABI_VERSION 1
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,      /* bad argument; nothing was changed                  */
+    LB_ENOMEM = 2,      /* device allocation failed                           */
+    LB_ECUDA = 3,       /* a CUDA call failed (no device, launch error, ...)  */
+    LB_ETIMEOUT = 4,    /* a bounded device-side wait gave up                 */
+    LB_ENAN = 5,        /* a particle state became NaN or Inf                 */
+    LB_EOVERLAP = 6,    /* particles (or a particle and a wall) came too close */
+    LB_ECAPACITY = 7,   /* a particle outgrew the scratch sized at lb_create  */
+    LB_ESTATE = 8       /* call not allowed in the context's current state    */
+} lb_status;
+
+/* storage of the distributions, always as deviations f_i - w_i rho0 */
+enum { LB_FP32 = 0, LB_FP16 = 1, LB_BF16 = 2 };
+
+/* field selectors for lb_get_fields */
+enum {
+    LB_FIELD_F = 1u,      /* f_i, float32, [19][nz][ny][nx]; 0 on solid nodes     */
+    LB_FIELD_DF = 2u,     /* f_i - w_i rho0, float32, same layout                  */
+    LB_FIELD_RHO = 4u,    /* rho - rho0, float32, [nz][ny][nx]; 0 on solid nodes  */
+    LB_FIELD_U = 8u,      /* u = (sum f c + g/2)/rho, float32, [3][nz][ny][nx]     */
+    LB_FIELD_SOLID = 16u  /* owner, int32, [nz][ny][nx]: 0 fluid, -1 wall, p+1     */
+};
+
+/* option flags */
+enum {
+    LB_FLAG_NO_GRAPH = 1u  /* launch every kernel directly instead of replaying a CUDA graph */
+};
+
+/* One periodic box (x, y, z periodic) or a channel (walls != 0: the planes
+ * y = 0 and y = ny-1 are solid and move with wall_u_lo / wall_u_hi).
+ * nx must be a multiple of 4 (8 for 16-bit storage). */
+typedef struct {
+    int32_t nx, ny, nz;
+    double tau;                 /* BGK relaxation time, nu = (tau - 1/2)/3 (Sec. II.A) */
+    double rho0;                /* mean density; rho_0 of Eq. fb                       */
+    double body_force[3];       /* uniform force density on every fluid node           */
+    int32_t counter_force;      /* 1: fluid also gets -sum(F_ext)/N_fluid (zero net)   */
+    int32_t walls;
+    double wall_u_lo[3], wall_u_hi[3];
+} lb_box_desc;
+
+typedef struct {
+    int32_t precision;          /* LB_FP32 | LB_FP16 | LB_BF16                        */
+    int32_t didt_mode;          /* 0: analytic dI/dt (Eq. Irotdiff); 1: finite difference */
+    int32_t device;             /* CUDA device ordinal                               */
+    uint32_t flags;             /* LB_FLAG_*                                          */
+    int32_t max_semi;           /* largest semi-axis any particle will have (<= 29)  */
+    int32_t max_particles;      /* total particles over all boxes (sizes the state)  */
+    double fp16_scale;          /* LB_FP16: stored value = deviation * scale; 0 = 2^14 */
+    void* (*alloc)(size_t bytes, void* user);   /* optional device allocator          */
+    void (*release)(void* ptr, void* user);
+    void* alloc_user;
+} lb_options;
+
+typedef struct {
+    double semi[3];             /* a (body x, long axis e), b (body y), c (body z)     */
+    double x[3];                /* centre                                             */
+    double q[4];                /* orientation, unit quaternion                        */
+    double U[3], Omega[3];      /* initial velocity and angular velocity              */
+    double density;             /* particle density; M = density * 4/3 pi a b c      */
+    double F_ext[3], T_ext[3];  /* external force and torque                          */
+    double B1, B2;              /* squirmer slip modes (Eq. squirmer); 0 = passive    */
+} lb_particle;
+
+/* Number of doubles per particle written by lb_get_force_torque. */
+#define LB_RECORD_DOUBLES 25
+
+/* Creates a context holding nbox boxes, all fluid at rest (f_i = w_i rho0).
+ * Validates every descriptor (sizes >= 4, nx a multiple of 4 or 8, tau > 1/2,
+ * rho0 > 0) and allocates: two distribution buffers (2*19*N*s bytes, s = 4 or
+ * 2), per particle a ring of two occupancy bitmasks and its state.
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.  *out is NULL on error. */
+lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_options* opt, lb_ctx** out);
+
+/* Frees every allocation of the context (after waiting for its work). */
+lb_status lb_destroy(lb_ctx* ctx);
+
+/* Places n particles in box `box` (replacing any set before) and builds their
+ * solid nodes (Eq. ellipsoidsurface), boundary links and drag matrices
+ * (Eq. drag1-drag4).  Allowed only before the first lb_step.
+ * Errors: LB_EINVAL (bad semi-axes, semi-axis > max_semi, too many particles,
+ * a particle touching a wall), LB_EOVERLAP (bounding boxes of two particles
+ * overlap), LB_ESTATE (after a step). */
+lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particle* p, int32_t n);
+
+/* Sets F_ext and T_ext of the n particles of `box` (box = -1: all particles of
+ * all boxes, in box order) from a host array ft[n][6] = (F_ext, T_ext); one
+ * copy on `stream`, in effect from the next iteration.  Pinned host memory
+ * makes the copy asynchronous; the caller keeps ft valid until it completes. */
+lb_status lb_set_external(lb_ctx* ctx, int32_t box, const double* ft, int32_t n, void* stream);
+
+/* Advances every box by nsteps iterations of the Appendix algorithm (collide,
+ * stream with link bounce-back, F0/T0, inertia, implicit solve, position and
+ * quaternion update, remap with covered/uncovered nodes, drag matrices).
+ * Asynchronous on `stream` (a cudaStream_t, NULL = the context's stream). */
+lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream);
+
+/* Writes the fields `what` (one LB_FIELD_* bit) of box `box` at the current
+ * time t: f(x, t) is the pre-collision distribution at the start of
+ * iteration t.  dst gets dst_bytes bytes (must equal the field's size); it is
+ * device memory when dst_is_device != 0.  Waits for completion. */
+lb_status lb_get_fields(lb_ctx* ctx, int32_t box, uint32_t what, void* dst, size_t dst_bytes,
+                        int32_t dst_is_device, void* stream);
+
+/* Copies, for the n particles of box `box` (box = -1: all particles of all
+ * boxes, in box order), LB_RECORD_DOUBLES doubles each:
+ * F0[3], T0[3] (Eq. F0, Eq. T0 of the last iteration), F[3], T[3] (Eq. Fsplit /
+ * Eq. Tsplit with the new velocities), U[3], Omega[3], x[3], q[4] at the
+ * current time.  out is host memory (one device-to-host copy).  Waits for the
+ * context's work on `stream` (NULL = its own stream). */
+lb_status lb_get_force_torque(lb_ctx* ctx, int32_t box, double* out, int32_t n);
+
+/* Boundary links (x fluid, x + c_b solid) of particle `particle` of box `box`
+ * at the current time, compacted on the device: pairs[2k] = node index
+ * (z*ny + y)*nx + x of the fluid node, pairs[2k+1] = direction index b in the
+ * library's D3Q19 order (lb_lattice).  *count = number of links (all of them
+ * are written only if count <= cap).  Waits for completion. */
+lb_status lb_get_links(lb_ctx* ctx, int32_t box, int32_t particle, int32_t* pairs, int32_t cap,
+                       int32_t* count);
+
+/* The 6x6 drag matrix [[zeta_FU, zeta_FOmega], [zeta_TU, zeta_TOmega]] of
+ * Eq. drag1-drag4 for the current links of a particle, row-major. */
+lb_status lb_get_drag(lb_ctx* ctx, int32_t box, int32_t particle, double* out36);
+
+/* Runs nsteps iterations like lb_step but launches every kernel directly, in
+ * sequence on `stream`, with a CUDA event between consecutive kernels, and
+ * returns the summed device time in milliseconds of the bulk lattice kernels
+ * (ms_out[0]), the boundary kernels (ms_out[1]), the critical particle kernels
+ * (ms_out[2]) and the auxiliary particle kernels (ms_out[3]).  Waits for
+ * completion.  For measurement only. */
+lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, double* ms_out);
+
+/* Waits for all work of the context and returns the device status word's error. */
+lb_status lb_synchronize(lb_ctx* ctx);
+
+/* The library's D3Q19 table: c[19][3] and w[19] (1/3, 1/18, 1/36). */
+void lb_lattice(int32_t* c57, double* w19);
+
+const char* lb_status_string(lb_status s);
+const char* lb_last_error(const lb_ctx* ctx);
+int32_t lb_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,723 @@
+// Host runtime behind the C ABI of include/lbsph.h.
+//
+// One iteration is four kernels: bulk (every node), boundary (the listed nodes
+// near particles), particle-critical (solve, pose, new occupancy, box forces)
+// on the caller's stream, and particle-auxiliary (link moments, drag matrices,
+// next boundary list) on a second stream, overlapping the next bulk kernel and
+// joined before the next boundary kernel.  Chunks of iterations are captured
+// once into a CUDA graph per buffer parity and replayed, so a long run costs
+// one graph launch per chunk and no host synchronisation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbsph.h"
+#include "lbsph_internal.cuh"
+
+namespace lbsph {
+cudaError_t launch_fields(const KParams& p, int precision, int blocks, cudaStream_t s);
+cudaError_t launch_bulk(const BulkParams& p, int precision, int blocks, cudaStream_t s);
+cudaError_t launch_boundary(const BndParams& p, int precision, int list_cap, int np, cudaStream_t s);
+cudaError_t launch_particles(const PParams& p, cudaStream_t s);
+cudaError_t launch_particles_aux(const PParams& p, cudaStream_t s);
+cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
+                         int cap, int* count, cudaStream_t s);
+}  // namespace lbsph
+
+using namespace lbsph;
+
+namespace {
+constexpr int GRAPH_ITERS = 32;     // iterations per captured graph (even)
+}
+
+struct lb_ctx {
+    int device = 0;
+    lb_options opt{};
+    cudaStream_t stream = nullptr;
+    std::vector<lb_box_desc> desc;
+    std::vector<BoxDev> hbox;
+    BoxDev* d_boxes = nullptr;
+    int total_blocks = 0;
+    size_t elem = 4;
+    long long total_elems = 0;
+    void* fbuf[2] = {nullptr, nullptr};
+    int cur = 0;                        // fbuf[cur] holds the latest populations
+    int maxp = 0;
+    int np = 0;
+    std::vector<std::vector<lb_particle>> parts;
+    PartDev* d_pd = nullptr;
+    PartK* d_pk = nullptr;
+    long long* d_acc = nullptr;
+    uint64_t* d_rows = nullptr;
+    unsigned* d_status = nullptr;
+    int* d_links = nullptr;
+    int links_cap = 0;
+    int* d_count = nullptr;
+    float* d_tmp = nullptr;
+    double* d_rec = nullptr;
+    size_t tmp_bytes = 0;
+    bool collided = false;
+    bool stepped = false;
+    unsigned sticky = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaStream_t last_user_stream = nullptr;        // last stream lb_step ran on
+    cudaStream_t aux = nullptr;                     // stream of the auxiliary particle kernel
+    cudaEvent_t ev_crit = nullptr, ev_aux = nullptr;
+    int* d_blk_box = nullptr;
+    BoxDyn* d_box_dyn = nullptr;
+    int* d_box_done = nullptr;
+    unsigned* d_lists = nullptr;
+    int* d_list_count = nullptr;
+    int list_cap = 0;
+    std::string err;
+    std::vector<void*> allocs;
+};
+
+static lb_status fail(lb_ctx* c, lb_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+static lb_status cuda_fail(lb_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, LB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+static void* dev_alloc(lb_ctx* ctx, size_t bytes)
+{
+    void* p = nullptr;
+    if (bytes == 0) bytes = 256;
+    if (ctx->opt.alloc) {
+        p = ctx->opt.alloc(bytes, ctx->opt.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) ctx->allocs.push_back(p);
+    return p;
+}
+
+static void free_all(lb_ctx* ctx)
+{
+    for (void* p : ctx->allocs) {
+        if (ctx->opt.alloc && ctx->opt.release) ctx->opt.release(p, ctx->opt.alloc_user);
+        else if (!ctx->opt.alloc) cudaFree(p);
+    }
+    ctx->allocs.clear();
+}
+
+static cudaStream_t pick(lb_ctx* ctx, void* s) { return s ? static_cast<cudaStream_t>(s) : ctx->stream; }
+
+// errors are returned by the call that caused them; drop a stale one so that a
+// later cudaGetLastError() after a launch reports that launch only
+static void clear_stale_error() { (void)cudaGetLastError(); }
+
+static lb_status read_status(lb_ctx* ctx)
+{
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    ctx->sticky |= st;
+    if (ctx->sticky & ST_NAN) return fail(ctx, LB_ENAN, "a particle state became NaN or Inf");
+    if (ctx->sticky & ST_OVERLAP) return fail(ctx, LB_EOVERLAP, "a particle reached a wall or another particle");
+    if (ctx->sticky & ST_CAPACITY) return fail(ctx, LB_ECAPACITY, "a particle outgrew its bounding cube or a tile met too many particles");
+    return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" int32_t lb_abi_version(void) { return LBSPH_ABI_VERSION; }
+
+extern "C" const char* lb_status_string(lb_status s)
+{
+    switch (s) {
+    case LB_OK: return "ok";
+    case LB_EINVAL: return "invalid argument";
+    case LB_ENOMEM: return "out of device memory";
+    case LB_ECUDA: return "CUDA error";
+    case LB_ETIMEOUT: return "device wait timed out";
+    case LB_ENAN: return "particle state is not finite";
+    case LB_EOVERLAP: return "particles overlap";
+    case LB_ECAPACITY: return "capacity exceeded";
+    case LB_ESTATE: return "call not allowed in this state";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* lb_last_error(const lb_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" void lb_lattice(int32_t* c57, double* w19)
+{
+    for (int i = 0; i < Q; ++i) {
+        if (c57) { c57[3 * i] = cx_of(i); c57[3 * i + 1] = cy_of(i); c57[3 * i + 2] = cz_of(i); }
+        if (w19) w19[i] = wd_of(i);
+    }
+}
+
+extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_options* opt, lb_ctx** out)
+{
+    if (!out) return LB_EINVAL;
+    *out = nullptr;
+    if (!boxes || nbox <= 0) return LB_EINVAL;
+    lb_ctx* ctx = new (std::nothrow) lb_ctx();
+    if (!ctx) return LB_ENOMEM;
+    if (opt) ctx->opt = *opt;
+    else {
+        ctx->opt.max_semi = 16;
+        ctx->opt.max_particles = 64;
+    }
+    lb_options& o = ctx->opt;
+    if (o.max_semi <= 0) o.max_semi = 16;
+    if (o.max_particles <= 0) o.max_particles = 64;
+    auto bad = [&](const std::string& m) { delete ctx; (void)m; return LB_EINVAL; };
+    if (o.precision < 0 || o.precision > 2 || o.didt_mode < 0 || o.didt_mode > 1 || o.max_semi > 29 ||
+        (o.alloc && !o.release) || (!o.alloc && o.release))
+        return bad("options");
+    for (int b = 0; b < nbox; ++b) {
+        const lb_box_desc& d = boxes[b];
+        if (d.nx < 4 || d.ny < 4 || d.nz < 4 || d.nx % 4 != 0) return bad("box size");
+        if (!(d.tau > 0.5) || !(d.rho0 > 0.0) || (d.walls && d.ny < 5)) return bad("box parameters");
+        if ((long long)d.nx * d.ny * d.nz > (1ll << 31) / 19) return bad("box too large");
+    }
+    ctx->device = o.device;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) { delete ctx; return LB_ECUDA; }
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_crit, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_aux, cudaEventDisableTiming) != cudaSuccess) {
+        delete ctx;
+        return LB_ECUDA;
+    }
+    ctx->elem = o.precision == LB_FP32 ? 4 : 2;
+    const float scale = o.precision == LB_FP16 ? (float)(o.fp16_scale > 0 ? o.fp16_scale : 16384.0) : 1.0f;
+    ctx->desc.assign(boxes, boxes + nbox);
+    ctx->parts.assign(nbox, {});
+    long long off = 0;
+    int blk = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const lb_box_desc& d = boxes[b];
+        BoxDev h{};
+        h.nx = d.nx; h.ny = d.ny; h.nz = d.nz; h.nxq = d.nx / 4;
+        h.N = (long long)d.nx * d.ny * d.nz;
+        h.nq = h.N / 4;
+        h.off = off;
+        off += 19 * h.N;
+        h.block_begin = blk;
+        h.nblocks = (int)((h.nq + KBLOCK - 1) / KBLOCK);
+        blk += h.nblocks;
+        h.omega = (float)(1.0 / d.tau);
+        h.rho0 = d.rho0;
+        h.rho0f = (float)d.rho0;
+        for (int k = 0; k < 3; ++k) {
+            h.body[k] = d.body_force[k];
+            h.uw_lo[k] = (float)d.wall_u_lo[k];
+            h.uw_hi[k] = (float)d.wall_u_hi[k];
+        }
+        h.counter = d.counter_force;
+        h.walls = d.walls;
+        h.nwall = d.walls ? 2ll * d.nx * d.nz : 0;
+        h.scale = scale;
+        h.inv_scale = 1.0f / scale;
+        ctx->hbox.push_back(h);
+    }
+    ctx->total_blocks = blk;
+    ctx->total_elems = off;
+    ctx->maxp = o.max_particles;
+    size_t tmp = 0;
+    for (auto& h : ctx->hbox) tmp = std::max(tmp, (size_t)(19 * h.N) * sizeof(float));
+    ctx->tmp_bytes = tmp;
+    bool okm = true;
+    ctx->fbuf[0] = dev_alloc(ctx, (size_t)off * ctx->elem);
+    ctx->fbuf[1] = dev_alloc(ctx, (size_t)off * ctx->elem);
+    ctx->d_boxes = (BoxDev*)dev_alloc(ctx, sizeof(BoxDev) * nbox);
+    ctx->d_pd = (PartDev*)dev_alloc(ctx, sizeof(PartDev) * ctx->maxp);
+    ctx->d_pk = (PartK*)dev_alloc(ctx, sizeof(PartK) * ctx->maxp);
+    ctx->d_acc = (long long*)dev_alloc(ctx, sizeof(long long) * NACC * ctx->maxp);
+    ctx->d_rows = (uint64_t*)dev_alloc(ctx, sizeof(uint64_t) * 2ull * MAXS * MAXS * ctx->maxp);
+    ctx->d_status = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * 4);
+    ctx->d_count = (int*)dev_alloc(ctx, sizeof(int) * 4);
+    ctx->d_blk_box = (int*)dev_alloc(ctx, sizeof(int) * (size_t)blk);
+    ctx->d_box_dyn = (BoxDyn*)dev_alloc(ctx, sizeof(BoxDyn) * nbox);
+    ctx->d_box_done = (int*)dev_alloc(ctx, sizeof(int) * nbox);
+    {
+        const long long Smax = 2ll * (o.max_semi + CUBE_MARGIN) + 2;
+        ctx->list_cap = (int)std::min(Smax * Smax * Smax, 16 * Smax * Smax);
+    }
+    ctx->d_lists = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * (size_t)ctx->list_cap * ctx->maxp);
+    ctx->d_list_count = (int*)dev_alloc(ctx, sizeof(int) * ctx->maxp);
+    for (void* p : {ctx->fbuf[0], ctx->fbuf[1], (void*)ctx->d_boxes, (void*)ctx->d_pd, (void*)ctx->d_pk,
+                    (void*)ctx->d_acc, (void*)ctx->d_rows, (void*)ctx->d_status, (void*)ctx->d_count,
+                    (void*)ctx->d_blk_box, (void*)ctx->d_box_dyn, (void*)ctx->d_box_done, (void*)ctx->d_lists,
+                    (void*)ctx->d_list_count})
+        okm = okm && p;
+    if (!okm) {
+        free_all(ctx);
+        cudaStreamDestroy(ctx->stream);
+        cudaStreamDestroy(ctx->aux);
+        delete ctx;
+        return LB_ENOMEM;
+    }
+    std::vector<int> blk_box(blk);
+    std::vector<BoxDyn> dyn(nbox);
+    for (int b = 0; b < nbox; ++b) {
+        for (int k = 0; k < ctx->hbox[b].nblocks; ++k) blk_box[ctx->hbox[b].block_begin + k] = b;
+        for (int k = 0; k < 3; ++k) dyn[b].g[k] = (float)boxes[b].body_force[k];
+        dyn[b].eps = 0.0f;
+    }
+    cudaError_t err = cudaSuccess;
+    err = err ? err : cudaMemsetAsync(ctx->fbuf[0], 0, (size_t)off * ctx->elem, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->fbuf[1], 0, (size_t)off * ctx->elem, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_acc, 0, sizeof(long long) * NACC * ctx->maxp, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_rows, 0, sizeof(uint64_t) * 2ull * MAXS * MAXS * ctx->maxp, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned) * 4, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_pk, 0, sizeof(PartK) * ctx->maxp, ctx->stream);
+    err = err ? err : cudaMemcpyAsync(ctx->d_boxes, ctx->hbox.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice, ctx->stream);
+    err = err ? err : cudaMemcpyAsync(ctx->d_blk_box, blk_box.data(), sizeof(int) * blk, cudaMemcpyHostToDevice, ctx->stream);
+    err = err ? err : cudaMemcpyAsync(ctx->d_box_dyn, dyn.data(), sizeof(BoxDyn) * nbox, cudaMemcpyHostToDevice, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_box_done, 0, sizeof(int) * nbox, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_list_count, 0, sizeof(int) * ctx->maxp, ctx->stream);
+    err = err ? err : cudaStreamSynchronize(ctx->stream);
+    if (err != cudaSuccess) {
+        free_all(ctx);
+        cudaStreamDestroy(ctx->stream);
+        cudaStreamDestroy(ctx->aux);
+        delete ctx;
+        return LB_ECUDA;
+    }
+    *out = ctx;
+    return LB_OK;
+}
+
+static void drop_graphs(lb_ctx* ctx)
+{
+    for (auto& g : ctx->gexec)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+extern "C" lb_status lb_destroy(lb_ctx* ctx)
+{
+    if (!ctx) return LB_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaDeviceSynchronize();
+    drop_graphs(ctx);
+    free_all(ctx);
+    cudaStreamDestroy(ctx->stream);
+    cudaStreamDestroy(ctx->aux);
+    cudaEventDestroy(ctx->ev_crit);
+    cudaEventDestroy(ctx->ev_aux);
+    delete ctx;
+    return LB_OK;
+}
+
+static PParams particle_params(lb_ctx* ctx)
+{
+    PParams pp{};
+    pp.pd = ctx->d_pd; pp.pk = ctx->d_pk; pp.acc = ctx->d_acc; pp.rows = ctx->d_rows;
+    pp.boxes = ctx->d_boxes; pp.box_dyn = ctx->d_box_dyn; pp.box_done = ctx->d_box_done;
+    pp.status = ctx->d_status; pp.np = ctx->np; pp.init = 0;
+    pp.didt_mode = ctx->opt.didt_mode;
+    pp.smax = 2 * (ctx->opt.max_semi + CUBE_MARGIN) + 2;
+    return pp;
+}
+
+// bounding cube of one particle: h = ceil(max semi) + CUBE_MARGIN, S = 2h + 2
+static void cube_of(const lb_particle& p, int& h, int& S)
+{
+    const double m = std::max(p.semi[0], std::max(p.semi[1], p.semi[2]));
+    h = (int)std::ceil(m) + CUBE_MARGIN;
+    S = 2 * h + 2;
+}
+
+static bool cubes_overlap(const lb_particle& a, const lb_particle& b, const lb_box_desc& d)
+{
+    int ha, Sa, hb, Sb;
+    cube_of(a, ha, Sa);
+    cube_of(b, hb, Sb);
+    const int L[3] = {d.nx, d.ny, d.nz};
+    for (int k = 0; k < 3; ++k) {
+        const int oa = (int)std::floor(a.x[k]) - ha, ob = (int)std::floor(b.x[k]) - hb;
+        int dd = ((ob - oa) % L[k] + L[k]) % L[k];            // offset of b's origin from a's
+        const bool sep = (dd >= Sa) && (L[k] - dd >= Sb);     // disjoint both ways round
+        if (sep) return false;
+    }
+    return true;
+}
+
+extern "C" lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particle* p, int32_t n)
+{
+    if (!ctx) return LB_EINVAL;
+    if (ctx->stepped) return fail(ctx, LB_ESTATE, "particles can only be set before the first step");
+    if (box < 0 || box >= (int)ctx->desc.size() || n < 0 || (n > 0 && !p)) return fail(ctx, LB_EINVAL, "bad box or particle array");
+    const lb_box_desc& d = ctx->desc[box];
+    int total = 0;
+    for (int b = 0; b < (int)ctx->parts.size(); ++b) total += (b == box) ? n : (int)ctx->parts[b].size();
+    if (total > ctx->maxp) return fail(ctx, LB_EINVAL, "more particles than lb_options.max_particles");
+    for (int i = 0; i < n; ++i) {
+        const lb_particle& q = p[i];
+        for (int k = 0; k < 3; ++k)
+            if (!(q.semi[k] > 0.0) || q.semi[k] > ctx->opt.max_semi)
+                return fail(ctx, LB_EINVAL, "semi-axis must be in (0, max_semi]");
+        const double qn = std::sqrt(q.q[0] * q.q[0] + q.q[1] * q.q[1] + q.q[2] * q.q[2] + q.q[3] * q.q[3]);
+        if (std::fabs(qn - 1.0) > 1e-6) return fail(ctx, LB_EINVAL, "quaternion must be unit");
+        if (!(q.density > 0.0)) return fail(ctx, LB_EINVAL, "density must be positive");
+        int h, S;
+        cube_of(q, h, S);
+        if (S > d.nx || S > d.nz || S > d.ny) return fail(ctx, LB_EINVAL, "particle too large for the box");
+        if (d.walls) {
+            const int oy = (int)std::floor(q.x[1]) - h;
+            if (q.x[1] - std::max(q.semi[0], std::max(q.semi[1], q.semi[2])) <= 0.5 ||
+                q.x[1] + std::max(q.semi[0], std::max(q.semi[1], q.semi[2])) >= d.ny - 1.5 || oy + S < 0)
+                return fail(ctx, LB_EINVAL, "particle touches a wall");
+        }
+        for (int j = 0; j < i; ++j)
+            if (cubes_overlap(q, p[j], d)) return fail(ctx, LB_EOVERLAP, "bounding cubes of two particles overlap");
+    }
+    ctx->parts[box].assign(p, p + n);
+    // rebuild the global particle table, boxes in order
+    std::vector<PartDev> pd;
+    int idx = 0;
+    for (int b = 0; b < (int)ctx->parts.size(); ++b) {
+        ctx->hbox[b].pbeg = idx;
+        ctx->hbox[b].pcnt = (int)ctx->parts[b].size();
+        for (const lb_particle& q : ctx->parts[b]) {
+            PartDev s{};
+            for (int k = 0; k < 3; ++k) {
+                s.semi[k] = q.semi[k]; s.x[k] = q.x[k]; s.U[k] = q.U[k]; s.W[k] = q.Omega[k];
+                s.Fext[k] = q.F_ext[k]; s.Text[k] = q.T_ext[k];
+            }
+            const double qn = std::sqrt(q.q[0] * q.q[0] + q.q[1] * q.q[1] + q.q[2] * q.q[2] + q.q[3] * q.q[3]);
+            for (int k = 0; k < 4; ++k) s.q[k] = q.q[k] / qn;
+            s.density = q.density; s.B1 = q.B1; s.B2 = q.B2;
+            const double a = q.semi[0], bb = q.semi[1], c = q.semi[2];
+            s.M = q.density * 4.0 / 3.0 * M_PI * a * bb * c;
+            s.Ib[0] = s.M * (bb * bb + c * c) / 5.0;
+            s.Ib[1] = s.M * (a * a + c * c) / 5.0;
+            s.Ib[2] = s.M * (a * a + bb * bb) / 5.0;
+            cube_of(q, s.h, s.S);
+            s.box = b;
+            pd.push_back(s);
+            ++idx;
+        }
+    }
+    ctx->np = idx;
+    CK(cudaSetDevice(ctx->device));
+    if (idx > 0) CK(cudaMemcpyAsync(ctx->d_pd, pd.data(), sizeof(PartDev) * idx, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_boxes, ctx->hbox.data(), sizeof(BoxDev) * ctx->hbox.size(), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        std::vector<PartK> pk(ctx->maxp);
+        std::memset(pk.data(), 0, sizeof(PartK) * pk.size());
+        for (int i = 0; i < ctx->maxp; ++i) {
+            pk[i].list = ctx->d_lists + (size_t)i * ctx->list_cap;
+            pk[i].list_count = ctx->d_list_count + i;
+            pk[i].list_cap = ctx->list_cap;
+        }
+        CK(cudaMemcpyAsync(ctx->d_pk, pk.data(), sizeof(PartK) * ctx->maxp, cudaMemcpyHostToDevice, ctx->stream));
+        std::vector<BoxDyn> dyn(ctx->desc.size());
+        for (size_t b = 0; b < dyn.size(); ++b) {
+            for (int k = 0; k < 3; ++k) dyn[b].g[k] = (float)ctx->desc[b].body_force[k];
+            dyn[b].eps = 0.0f;
+        }
+        CK(cudaMemcpyAsync(ctx->d_box_dyn, dyn.data(), sizeof(BoxDyn) * dyn.size(), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    clear_stale_error();
+    PParams pp = particle_params(ctx);
+    pp.init = 1;
+    CK(launch_particles(pp, ctx->stream));
+    CK(launch_particles_aux(pp, ctx->stream));
+    CK(cudaEventRecord(ctx->ev_aux, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);
+    return read_status(ctx);
+}
+
+extern "C" lb_status lb_set_external(lb_ctx* ctx, int32_t box, const double* ft, int32_t n, void* stream)
+{
+    if (!ctx) return LB_EINVAL;
+    const bool all = box == -1;
+    if ((!all && (box < 0 || box >= (int)ctx->desc.size())) || !ft ||
+        n != (all ? ctx->np : (int)ctx->parts[box].size()))
+        return fail(ctx, LB_EINVAL, "bad box or count");
+    if (n == 0) return LB_OK;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick(ctx, stream);
+    const int pbeg = all ? 0 : ctx->hbox[box].pbeg;
+    // one strided copy straight into the particle states (F_ext, T_ext are adjacent)
+    CK(cudaMemcpy2DAsync(&ctx->d_pd[pbeg].Fext[0], sizeof(PartDev), ft, 6 * sizeof(double), 6 * sizeof(double), n,
+                         cudaMemcpyHostToDevice, s));
+    return LB_OK;
+}
+
+static KParams base_kparams(lb_ctx* ctx, int mode)
+{
+    KParams k{};
+    k.boxes = ctx->d_boxes;
+    k.nbox = (int)ctx->hbox.size();
+    k.pk = ctx->d_pk;
+    k.status = ctx->d_status;
+    k.mode = mode;
+    return k;
+}
+
+// one iteration: bulk, boundary (after the previous auxiliary kernel), the
+// critical particle kernel on s, then the auxiliary particle kernel on the
+// second stream, recorded so that the next boundary kernel waits for it
+static cudaError_t enqueue_iteration(lb_ctx* ctx, int first, int cur, cudaStream_t s, cudaEvent_t ev_crit,
+                                     cudaEvent_t ev_aux)
+{
+    BulkParams bp{};
+    bp.boxes = ctx->d_boxes; bp.blk_box = ctx->d_blk_box; bp.box_dyn = ctx->d_box_dyn;
+    bp.src = ctx->fbuf[cur]; bp.dst = ctx->fbuf[cur ^ 1]; bp.first = first;
+    cudaError_t e = launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s);
+    if (e != cudaSuccess || ctx->np == 0) return e;
+    if ((e = cudaStreamWaitEvent(s, ev_aux, 0)) != cudaSuccess) return e;
+    BndParams np{};
+    np.boxes = ctx->d_boxes; np.box_dyn = ctx->d_box_dyn; np.pk = ctx->d_pk;
+    np.src = ctx->fbuf[cur]; np.dst = ctx->fbuf[cur ^ 1]; np.first = first;
+    if ((e = launch_boundary(np, ctx->opt.precision, ctx->list_cap, ctx->np, s)) != cudaSuccess) return e;
+    const PParams pp = particle_params(ctx);
+    if ((e = launch_particles(pp, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev_crit, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ctx->aux, ev_crit, 0)) != cudaSuccess) return e;
+    if ((e = launch_particles_aux(pp, ctx->aux)) != cudaSuccess) return e;
+    return cudaEventRecord(ev_aux, ctx->aux);
+}
+
+// The graph gets its own events: an event last recorded inside a capture
+// cannot be waited on outside it.
+static lb_status build_graph(lb_ctx* ctx, int parity)
+{
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaEvent_t fork = nullptr, ec = nullptr, ea = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ec, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ea, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    const bool capturing = e == cudaSuccess;
+    // the auxiliary stream joins the capture through the fork event
+    if (e == cudaSuccess) e = cudaEventRecord(fork, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, fork, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(ea, ctx->aux);
+    int c = parity;
+    for (int i = 0; e == cudaSuccess && i < GRAPH_ITERS; ++i) {
+        e = enqueue_iteration(ctx, 0, c, cs, ec, ea);
+        c ^= 1;
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ea, 0);   // join the auxiliary branch
+    if (capturing) {
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->gexec[parity], g, 0);
+    if (g) cudaGraphDestroy(g);
+    for (cudaEvent_t ev : {fork, ec, ea})
+        if (ev) cudaEventDestroy(ev);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "graph capture");
+    }
+    return LB_OK;
+}
+
+extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
+{
+    if (!ctx) return LB_EINVAL;
+    if (nsteps < 0) return fail(ctx, LB_EINVAL, "negative step count");
+    if (nsteps == 0) return LB_OK;
+    CK(cudaSetDevice(ctx->device));
+    clear_stale_error();
+    cudaStream_t s = pick(ctx, stream);
+    ctx->last_user_stream = s;
+    int left = nsteps;
+    ctx->stepped = true;
+    CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));      // work already enqueued on the auxiliary stream
+    if (!ctx->collided) {
+        CK(enqueue_iteration(ctx, 1, ctx->cur, s, ctx->ev_crit, ctx->ev_aux));
+        ctx->cur ^= 1;
+        ctx->collided = true;
+        --left;
+    }
+    const bool graphs = !(ctx->opt.flags & LB_FLAG_NO_GRAPH);
+    if (graphs && left >= GRAPH_ITERS && !ctx->gexec[ctx->cur]) {
+        // both parities at once, so that no capture happens inside a timed run later
+        lb_status st = build_graph(ctx, 0);
+        if (st == LB_OK) st = build_graph(ctx, 1);
+        if (st != LB_OK) return st;
+    }
+    bool launched = false;
+    if (graphs && left >= GRAPH_ITERS) CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
+    while (graphs && left >= GRAPH_ITERS) {
+        CK(cudaGraphLaunch(ctx->gexec[ctx->cur], s));   // joins its auxiliary branch at the end
+        left -= GRAPH_ITERS;     // even count: parity unchanged
+        launched = true;
+    }
+    if (launched) CK(cudaEventRecord(ctx->ev_aux, s));
+    for (; left > 0; --left) {
+        CK(enqueue_iteration(ctx, 0, ctx->cur, s, ctx->ev_crit, ctx->ev_aux));
+        ctx->cur ^= 1;
+    }
+    CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));      // everything ordered on the caller's stream
+    return LB_OK;
+}
+
+extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, double* ms_out)
+{
+    if (!ctx) return LB_EINVAL;
+    if (nsteps <= 0 || !ms_out) return fail(ctx, LB_EINVAL, "bad step count or output");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick(ctx, stream);
+    ctx->last_user_stream = s;
+    ctx->stepped = true;
+    CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
+    cudaEvent_t ev[5];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    double t[4] = {0, 0, 0, 0};
+    for (int i = 0; i < nsteps; ++i) {
+        const int first = ctx->collided ? 0 : 1;
+        BulkParams bp{};
+        bp.boxes = ctx->d_boxes; bp.blk_box = ctx->d_blk_box; bp.box_dyn = ctx->d_box_dyn;
+        bp.src = ctx->fbuf[ctx->cur]; bp.dst = ctx->fbuf[ctx->cur ^ 1]; bp.first = first;
+        BndParams np{};
+        np.boxes = ctx->d_boxes; np.box_dyn = ctx->d_box_dyn; np.pk = ctx->d_pk;
+        np.src = ctx->fbuf[ctx->cur]; np.dst = ctx->fbuf[ctx->cur ^ 1]; np.first = first;
+        const PParams pp = particle_params(ctx);
+        CK(cudaEventRecord(ev[0], s));
+        CK(launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s));
+        CK(cudaEventRecord(ev[1], s));
+        CK(launch_boundary(np, ctx->opt.precision, ctx->list_cap, ctx->np, s));
+        CK(cudaEventRecord(ev[2], s));
+        CK(launch_particles(pp, s));
+        CK(cudaEventRecord(ev[3], s));
+        CK(launch_particles_aux(pp, s));
+        CK(cudaEventRecord(ev[4], s));
+        CK(cudaEventSynchronize(ev[4]));
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            t[k] += ms;
+        }
+        ctx->cur ^= 1;
+        ctx->collided = true;
+    }
+    CK(cudaEventRecord(ctx->ev_aux, s));
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < 4; ++k) ms_out[k] = t[k];
+    return read_status(ctx);
+}
+
+extern "C" lb_status lb_synchronize(lb_ctx* ctx)
+{
+    if (!ctx) return LB_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    return read_status(ctx);
+}
+
+extern "C" lb_status lb_get_fields(lb_ctx* ctx, int32_t box, uint32_t what, void* dst, size_t dst_bytes,
+                                   int32_t dst_is_device, void* stream)
+{
+    if (!ctx) return LB_EINVAL;
+    if (box < 0 || box >= (int)ctx->desc.size() || !dst) return fail(ctx, LB_EINVAL, "bad box or destination");
+    const BoxDev& B = ctx->hbox[box];
+    size_t need = 0;
+    switch (what) {
+    case LB_FIELD_F: case LB_FIELD_DF: need = 19ull * B.N * 4; break;
+    case LB_FIELD_RHO: case LB_FIELD_SOLID: need = (size_t)B.N * 4; break;
+    case LB_FIELD_U: need = 3ull * B.N * 4; break;
+    default: return fail(ctx, LB_EINVAL, "exactly one LB_FIELD_* bit");
+    }
+    if (dst_bytes != need) return fail(ctx, LB_EINVAL, "dst_bytes does not match the field size");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick(ctx, stream);
+    const bool direct = dst_is_device && ((uintptr_t)dst % 16 == 0);
+    if (!direct && !ctx->d_tmp) {
+        ctx->d_tmp = (float*)dev_alloc(ctx, ctx->tmp_bytes);
+        if (!ctx->d_tmp) return fail(ctx, LB_ENOMEM, "field staging buffer");
+    }
+    float* out = direct ? (float*)dst : ctx->d_tmp;
+    KParams k = base_kparams(ctx, 2);
+    k.src = ctx->fbuf[ctx->cur];
+    k.dst = nullptr;
+    k.only_box = box;
+    k.nopull = ctx->collided ? 0 : 1;
+    k.out_dev = (what == LB_FIELD_DF) ? 1 : 0;
+    if (what == LB_FIELD_F || what == LB_FIELD_DF) k.out_f = out;
+    if (what == LB_FIELD_RHO) k.out_rho = out;
+    if (what == LB_FIELD_U) k.out_u = out;
+    if (what == LB_FIELD_SOLID) k.out_solid = (int*)out;
+    CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
+    CK(launch_fields(k, ctx->opt.precision, B.nblocks, s));
+    if (!direct) CK(cudaMemcpyAsync(dst, out, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return read_status(ctx);
+}
+
+extern "C" lb_status lb_get_force_torque(lb_ctx* ctx, int32_t box, double* out, int32_t n)
+{
+    if (!ctx) return LB_EINVAL;
+    const bool all = box == -1;
+    if ((!all && (box < 0 || box >= (int)ctx->desc.size())) || !out ||
+        n != (all ? ctx->np : (int)ctx->parts[box].size()))
+        return fail(ctx, LB_EINVAL, "bad box, buffer or count");
+    if (n == 0) return LB_OK;
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->last_user_stream) CK(cudaStreamSynchronize(ctx->last_user_stream));
+    const int pbeg = all ? 0 : ctx->hbox[box].pbeg;
+    // gather the records into one staging block, then a single copy
+    if (!ctx->d_rec) {
+        ctx->d_rec = (double*)dev_alloc(ctx, sizeof(double) * LB_RECORD_DOUBLES * ctx->maxp);
+        if (!ctx->d_rec) return fail(ctx, LB_ENOMEM, "record staging buffer");
+    }
+    CK(cudaMemcpy2DAsync(ctx->d_rec, sizeof(double) * LB_RECORD_DOUBLES, &ctx->d_pd[pbeg].rec[0], sizeof(PartDev),
+                         sizeof(double) * LB_RECORD_DOUBLES, n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(out, ctx->d_rec, sizeof(double) * LB_RECORD_DOUBLES * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return read_status(ctx);
+}
+
+extern "C" lb_status lb_get_drag(lb_ctx* ctx, int32_t box, int32_t particle, double* out36)
+{
+    if (!ctx) return LB_EINVAL;
+    if (box < 0 || box >= (int)ctx->desc.size() || particle < 0 || particle >= (int)ctx->parts[box].size() || !out36)
+        return fail(ctx, LB_EINVAL, "bad box or particle");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(out36, &ctx->d_pd[ctx->hbox[box].pbeg + particle].zeta[0], 36 * sizeof(double), cudaMemcpyDeviceToHost));
+    return read_status(ctx);
+}
+
+extern "C" lb_status lb_get_links(lb_ctx* ctx, int32_t box, int32_t particle, int32_t* pairs, int32_t cap,
+                                  int32_t* count)
+{
+    if (!ctx) return LB_EINVAL;
+    if (box < 0 || box >= (int)ctx->desc.size() || particle < 0 || particle >= (int)ctx->parts[box].size() ||
+        !count || cap < 0 || (cap > 0 && !pairs))
+        return fail(ctx, LB_EINVAL, "bad box, particle or buffer");
+    CK(cudaSetDevice(ctx->device));
+    if (!ctx->d_links) {
+        ctx->links_cap = MAXS * MAXS * 18;
+        ctx->d_links = (int*)dev_alloc(ctx, sizeof(int) * 2ull * ctx->links_cap);
+        if (!ctx->d_links) return fail(ctx, LB_ENOMEM, "link buffer");
+    }
+    CK(cudaDeviceSynchronize());
+    const int p = ctx->hbox[box].pbeg + particle;
+    CK(launch_links(ctx->d_pd, ctx->d_rows, ctx->d_boxes, p, ctx->d_links, ctx->links_cap, ctx->d_count, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int n = 0;
+    CK(cudaMemcpy(&n, ctx->d_count, sizeof(int), cudaMemcpyDeviceToHost));
+    *count = n;
+    if (n <= cap && n > 0) CK(cudaMemcpy(pairs, ctx->d_links, sizeof(int) * 2ull * n, cudaMemcpyDeviceToHost));
+    return read_status(ctx);
+}

@@ -1,0 +1,213 @@
+// Internal definitions shared by the CUDA translation units of liblbsph.
+//
+// One iteration t of the paper's Appendix is four kernels:
+//   bulk      every node: pull streaming + BGK/Guo collision, wall links inline
+//             (the only kernel that moves the whole lattice: 2*19*s bytes/node);
+//   boundary  the listed nodes next to a particle's old or new surface: redoes
+//             them with link bounce-back (Eq. fb, Eq. ub), the remap of covered /
+//             uncovered nodes and the momentum-exchange sums of the new links;
+//   particle  (critical) force, implicit solve, pose and quaternion update, the
+//             new occupancy map and the box's uniform forces for the next step;
+//   particle  (auxiliary, concurrent with the next bulk kernel) link moments,
+//             drag matrices (Eq. drag1-drag4) and the next boundary list.
+//
+// Data layout in HBM (one allocation per buffer, every box back to back):
+//   distributions  two buffers (ping-pong), each box b holds 19 planes of
+//                  N_b = nx*ny*nz stored deviations f_i - w_i rho0, plane i at
+//                  box_off + i*N_b, x fastest (SoA), so a warp reads one row of
+//                  a plane with 16-byte loads (4 nodes per thread).
+//   occupancy      per particle a ring of two bitmaps over its bounding cube
+//                  (side S <= 64): one 64-bit word per (y, z) row, bit x set
+//                  when the node is inside the particle (Eq. ellipsoidsurface).
+//                  Boundary links are implicit: (x fluid, x + c_b solid).
+//   particle state PartDev (FP64, owned by the particle kernel) and PartK (the
+//                  FP32 snapshot the lattice kernel reads).
+//   accumulators   per particle NACC int64 fixed-point sums filled by the
+//                  lattice kernel with integer atomics (order independent, so
+//                  every run is bitwise reproducible) and drained by the
+//                  particle kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbsph {
+
+constexpr int Q = 19;
+constexpr int MAXS = 64;            // largest bounding-cube side (one 64-bit word per row)
+constexpr int KBLOCK = 256;         // threads per block of the lattice kernel
+constexpr int PBLOCK = 512;         // threads per block of the particle kernel
+constexpr int MAXC = 4;             // particles a lattice tile may touch (field read-back)
+constexpr int BBLOCK = 128;         // threads per block of the boundary kernel
+constexpr int CBLOCK = 256;         // threads per block of the critical particle kernel
+constexpr int MAXAMB = 512;         // near-surface nodes settled by the exact FP64 test per step
+
+// accumulator layout (int64 per particle)
+constexpr int ACC_LINK = 0;         // [b*4 + {0: sum df*, 1..3: sum df* m}], b = 0..18
+constexpr int ACC_COV = 76;         // n, sum drho, J[3], sum m x j [3]
+constexpr int ACC_UNC = 84;         // n, sum m [3], sum m m^T [6: xx xy xz yy yz zz]
+constexpr int NACC = 96;
+constexpr float FIXF = 70368744177664.0f;    // 2^46: |deviation| * 63 * 2^46 * links stays < 2^63
+constexpr double FIXD = 70368744177664.0;
+
+// status bits of the device status word
+constexpr unsigned ST_NAN = 1u;
+constexpr unsigned ST_CAPACITY = 2u;
+constexpr unsigned ST_OVERLAP = 4u;
+
+// cube margin: h = ceil(max semi-axis) + CUBE_MARGIN, side S = 2h + 2, so the
+// solid nodes of this step and of the last one, grown by one link, stay inside
+// the cube while a particle moves less than one node per step
+constexpr int CUBE_MARGIN = 2;
+
+// ---------------------------------------------------------------------------
+// D3Q19, this library's order: rest, 6 faces in +/- pairs, 12 edges in +/- pairs.
+// opp(i) = i + 1 for odd i, i - 1 for even i > 0.
+__host__ __device__ constexpr int cx_of(int i)
+{
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy_of(int i)
+{
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz_of(int i)
+{
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr float w_of(int i)
+{
+    return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+__host__ __device__ constexpr double wd_of(int i)
+{
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// ---------------------------------------------------------------------------
+struct BoxDev {
+    int nx, ny, nz, nxq;            // nxq = nx / 4 quads per row
+    long long N;                    // nodes
+    long long nq;                   // quads
+    long long off;                  // element offset of plane 0 in a distribution buffer
+    int block_begin, nblocks;       // lattice-kernel blocks of this box
+    float omega;                    // 1 / tau
+    float rho0f;
+    double rho0;
+    double body[3];
+    int counter;                    // counter body force on
+    int walls;
+    float uw_lo[3], uw_hi[3];
+    int pbeg, pcnt;                 // particles of this box
+    long long nwall;                // wall nodes (2 nx nz when walls)
+    float scale, inv_scale;         // 16-bit storage scale (1 for FP32 / BF16)
+};
+
+// FP32 snapshot of one particle for the lattice kernel, written by the
+// particle kernel of iteration t for the lattice kernel of iteration t+1.
+struct PartK {
+    const uint64_t* rows_old;       // occupancy of the pose at t   (map t)
+    const uint64_t* rows_new;       // occupancy of the pose at t+1 (map t+1)
+    long long* acc;                 // NACC accumulators
+    int ow_old[3], ow_new[3];       // cube origins wrapped into the box
+    int S;                          // cube side
+    int box;
+    float ro_old[3];                // origin(t) - x_c(t)     (r = ro + m [+ c/2])
+    float ro_new[3];                // origin(t+1) - x_c(t+1)
+    float U[3], W[3];               // U(t+1), Omega(t+1)
+    float e_old[3];                 // body x axis at t (squirmer slip)
+    float a, b, eps2, B1, B2;       // squirmer parameters
+    int squirmer;
+    int nsolid;                     // solid nodes of map t+1
+    double dm_return;               // mass put back at the next collision
+    double Fext[3];
+    unsigned* list;                 // boundary nodes for the next lattice step (cube-local x|y<<8|z<<16)
+    int* list_count;
+    int list_cap;
+    int pad;
+};
+
+// uniform per-box terms of the next collision: body force g and mass return eps
+struct BoxDyn {
+    float g[3];
+    float eps;
+};
+
+// Full FP64 state of one particle, read and written by the particle kernel only.
+struct PartDev {
+    double semi[3], M, Ib[3], density, B1, B2;
+    double Fext[3], Text[3];
+    double x[3], q[4], U[3], W[3];  // at time t (before the particle kernel of t)
+    double Iprev[9];
+    double zeta[36];                // drag matrix of links(t)
+    int o[3];                       // cube origin (unwrapped) of map t
+    int o_prev[3];                  // cube origin of map t-1
+    int S, h, box, slot;            // slot: ring slot holding map t
+    long long step;
+    int lm[Q][10];                  // link moments of links(t): n, sum m[3], sum m m^T[6]
+    long long slip[Q][4];           // fixed-point sums of (u_s.c_b) and (u_s.c_b) m
+    double rec[25];                 // F0, T0, F, T, U, Omega, x, q of the last iteration
+    int nsolid;
+};
+
+static_assert(sizeof(PartDev) % 8 == 0, "PartDev is copied as 8-byte words");
+static_assert(sizeof(PartK) % 4 == 0, "PartK is copied as 4-byte words");
+
+struct KParams {
+    const BoxDev* boxes;
+    int nbox;
+    const PartK* pk;
+    const void* src;                // distributions of iteration t-1 (post-collision)
+    void* dst;                      // distributions of iteration t
+    unsigned* status;
+    int mode;                       // 0 first collide (no pull), 1 full, 2 pull only (fields)
+    // mode 2 outputs (one box)
+    float* out_f;                   // [19][N] or nullptr
+    int out_dev;                    // 1: out_f holds deviations, 0: full f
+    float* out_rho;                 // [N] rho - rho0 or nullptr
+    float* out_u;                   // [3][N] or nullptr
+    int* out_solid;                 // [N] or nullptr
+    int only_box;                   // mode 2: box index (grid covers that box only)
+    int nopull;                     // mode 2 before the first collision: f = w rho0, no streaming
+};
+
+struct PParams {
+    PartDev* pd;
+    PartK* pk;
+    long long* acc;                 // np * NACC
+    uint64_t* rows;                 // np * 2 * MAXS*MAXS words
+    const BoxDev* boxes;
+    BoxDyn* box_dyn;                // per box
+    int* box_done;                  // per box arrival counters (last block writes box_dyn)
+    unsigned* status;
+    int np;
+    int init;                       // 1: build maps / moments only (no solve, no pose update)
+    int didt_mode;
+    int smax;                       // largest cube side of the context (sizes dynamic shared memory)
+};
+
+struct BulkParams {
+    const BoxDev* boxes;
+    const int* blk_box;             // box of every bulk block
+    const BoxDyn* box_dyn;
+    const void* src;
+    void* dst;
+    int first;                      // 1: first collision of the run (rest state, no streaming)
+};
+
+struct BndParams {
+    const BoxDev* boxes;
+    const BoxDyn* box_dyn;
+    const PartK* pk;
+    const void* src;
+    void* dst;
+    int first;
+};
+
+inline int rows_stride() { return MAXS * MAXS; }
+
+}  // namespace lbsph

@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports every entry point include/lbsph.h declares;
+host-only entry points behave (no GPU compute is issued here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2403_05443_gb300 import build as B
+from paper_2403_05443_gb300 import lbsph as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "lbsph.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_python_binding_has_the_same_names():
+    for n in _declared():
+        assert hasattr(L, n), n
+
+
+def test_abi_version_and_status_strings():
+    assert L.lb_abi_version() == 1
+    assert L.lb_status_string(0) == "ok"
+    assert L.lb_status_string(1) == "invalid argument"
+    assert L.lb_status_string(99) == "unknown status"
+
+
+def test_lattice_table_is_d3q19():
+    """Same velocity set and weights as the oracle's (compared as vectors: the two
+    sides use different direction orders)."""
+    from oracle import oracle as O
+    c, w = L.lb_lattice()
+    co, wo = O.lattice()
+    mine = {tuple(v): wi for v, wi in zip(c.tolist(), w)}
+    theirs = {tuple(v): wi for v, wi in zip(co.tolist(), wo)}
+    assert mine == theirs
+    # opposite directions are adjacent pairs (1,2), (3,4), ...
+    for i in range(1, 19, 2):
+        assert (c[i] == -c[i + 1]).all()
+
+
+def test_create_rejects_bad_boxes_without_touching_the_gpu():
+    opt = L.Options()
+    opt.max_semi, opt.max_particles = 8, 4
+    for bad in ({"nx": 30, "ny": 32, "nz": 32, "tau": 1.0},     # nx not a multiple of 4
+                {"nx": 32, "ny": 32, "nz": 32, "tau": 0.5},     # tau must exceed 1/2
+                {"nx": 32, "ny": 2, "nz": 32, "tau": 1.0},
+                {"nx": 32, "ny": 32, "nz": 32, "tau": 1.0, "rho0": 0.0}):
+        with pytest.raises(L.LBError) as e:
+            L.lb_create([bad], opt)
+        assert e.value.status == 1
+    with pytest.raises(L.LBError):
+        L.lb_create([], opt)
+
+
+def test_header_record_layout():
+    text = open(os.path.join(ROOT, "include", "lbsph.h")).read()
+    assert "#define LB_RECORD_DOUBLES 25" in text
+    assert L.LB_RECORD_DOUBLES == 25

@@ -1,0 +1,194 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 CPU oracle.
+
+Bars:
+  * occupancy maps and boundary-link lists: bit-exact for the same FP64 pose
+    (both sides evaluate Eq. ellipsoidsurface in the same FP64 operation order);
+  * FP32 path: normwise relative error max|x - x_ref| / max|x_ref| <= 1e-5 per
+    field and step for the deviations f_i - w_i rho0, u, F and T; the centre and
+    the quaternion to 1e-5 of the distance travelled / angle turned (+1e-9).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from lb_inputs import (box, particle, rng, random_pose, random_quaternion, single_32, sweep_8x64,
+                       axis_angle_quaternion)
+from parity_util import gpu_links_as_set, normwise, oracle_df_gpu_layout, oracle_links_as_set
+
+pytestmark = pytest.mark.gpu
+
+L = pytest.importorskip("paper_2403_05443_gb300.lbsph")
+
+TOL_FIELD = 1e-5
+TOL_FT = 1e-5
+
+
+def _sim(boxes, parts, **kw):
+    ms = max([max(p["semi"]) for pl in parts for p in pl] + [1.0])
+    return L.Simulation(boxes, parts, max_semi=int(math.ceil(ms)), **kw)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(12))
+def test_solid_map_and_links_bit_exact(seed):
+    g = rng(1000 + seed)
+    n = [int(v) for v in g.choice([16, 20, 24, 32], size=3)]
+    n[0] = 4 * (n[0] // 4)
+    semi = [float(v) for v in g.uniform(1.5, 5.0, 3)]
+    c, q = random_pose(g, min(n), margin=-1)       # anywhere: exercises periodic wrap
+    b = box(*n, 1.0)
+    p = particle(semi, c, q)
+    gpu = _sim([b], [[p]])
+    orc = O.Sim(b, [p], nthreads=4)
+    solid = gpu.field("solid")
+    assert np.array_equal(solid, orc.owner())
+    assert gpu_links_as_set(gpu) == oracle_links_as_set(orc)
+
+
+def test_drag_matrix_matches_oracle():
+    g = rng(5)
+    b = box(32, 28, 36, 1.0)
+    p = particle((5.5, 3.0, 2.5), (10.3, 20.7, 30.1), random_quaternion(g))
+    gpu = _sim([b], [[p]])
+    orc = O.Sim(b, [p], nthreads=4)
+    Z, Zr = gpu.drag(), orc.zeta()
+    assert np.abs(Z - Zr).max() <= 1e-12 * np.abs(Zr).max()
+
+
+# ---------------------------------------------------------------------------
+def _compare_run(boxes, parts, steps, every=1, tol_field=TOL_FIELD, tol_ft=TOL_FT, **kw):
+    gpu = _sim(boxes, parts, **kw)
+    orcs = [O.Sim(b, pl, nthreads=8) for b, pl in zip(boxes, parts)]
+    worst = {"df": 0.0, "u": 0.0, "F": 0.0, "T": 0.0, "x": 0.0, "q": 0.0}
+    x0 = [[np.array(p["x"], float) for p in pl] for pl in parts]
+    q0 = [[np.array(p.get("q", (1, 0, 0, 0)), float) for p in pl] for pl in parts]
+    hist = {bi: {"F": [], "Fr": [], "T": [], "Tr": []} for bi in range(len(boxes))}
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        gpu.step(k)
+        for o in orcs:
+            o.step(k)
+        done += k
+        for bi, (b, o) in enumerate(zip(boxes, orcs)):
+            df = gpu.field("df", bi)
+            ref = oracle_df_gpu_layout(o, b.get("rho0", 1.0))
+            worst["df"] = max(worst["df"], normwise(df, ref))
+            _, ur = o.moments()
+            u = gpu.field("u", bi)
+            worst["u"] = max(worst["u"], normwise(u, np.moveaxis(ur, -1, 0)))
+            for pi in range(len(parts[bi])):
+                r = gpu.particle(bi, pi)
+                s = o.particle(pi)
+                hist[bi]["F"].append(r["F"]); hist[bi]["Fr"].append(s["F"])
+                hist[bi]["T"].append(r["T"]); hist[bi]["Tr"].append(s["T"])
+                moved = float(np.abs(s["x"] - x0[bi][pi]).max())
+                turned = 2.0 * math.acos(min(1.0, abs(float(s["q"] @ q0[bi][pi]))))
+                worst["x"] = max(worst["x"], float(np.abs(r["x"] - s["x"]).max()) / (1e-5 * moved + 1e-9))
+                worst["q"] = max(worst["q"], float(np.abs(r["q"] - s["q"]).max()) / (1e-5 * turned + 1e-9))
+    for bi in hist:
+        if hist[bi]["F"]:
+            worst["F"] = max(worst["F"], normwise(np.array(hist[bi]["F"]), np.array(hist[bi]["Fr"])))
+            worst["T"] = max(worst["T"], normwise(np.array(hist[bi]["T"]), np.array(hist[bi]["Tr"])))
+    print("parity", worst)
+    assert worst["df"] <= tol_field and worst["u"] <= tol_field
+    assert worst["F"] <= tol_ft and worst["T"] <= tol_ft
+    assert worst["x"] <= 1.0 and worst["q"] <= 1.0       # in units of the bar above
+    return gpu, orcs, worst
+
+
+def test_single_spheroid_32_every_step():
+    """32^3, tau = 1, spheroid (4,2,2), random pose, F_ext = 1e-4 with counter force:
+    every field and particle value every step for 200 steps."""
+    boxes, parts = single_32(seed=0)
+    _compare_run(boxes, parts, steps=200, every=1)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_single_spheroid_other_seeds(seed):
+    boxes, parts = single_32(seed=seed)
+    _compare_run(boxes, parts, steps=120, every=10)
+
+
+def test_fast_particle_covers_and_uncovers_nodes():
+    """A particle launched at |U| ~ 0.04 crosses nodes every few steps: the remap
+    (covered / uncovered nodes, mass return) runs on both sides."""
+    g = rng(9)
+    b = box(24, 20, 28, 0.9)
+    p = particle((4.5, 2.5, 2.0), (10.3, 9.1, 11.7), random_quaternion(g), U=(0.03, -0.02, 0.025),
+                 Om=(0.004, 0.006, -0.005), density=5.0)
+    _compare_run([b], [[p]], steps=60, every=3)
+
+
+def test_channel_walls_with_particle():
+    """Moving walls (Couette) plus a free spheroid; nx = 20 is not a multiple of 128
+    (rows shorter than a warp), ny not a power of two."""
+    b = box(20, 22, 24, 1.0, walls=1, wall_u_lo=(-0.01, 0, 0), wall_u_hi=(0.01, 0.0, 0.002))
+    p = particle((5.0, 2.5, 2.5), (10.2, 10.6, 12.3), axis_angle_quaternion((0.3, 0.2, 1.0), 0.7))
+    _compare_run([b], [[p]], steps=80, every=8)
+
+
+def test_squirmer():
+    """A squirmer is force- and torque-free: its F and T are residuals of slip
+    terms (Eq. squirmer) about 100 times larger, evaluated in FP32 on the GPU and
+    in FP64 by the oracle, so the bar on F and T is 5e-5 of their own size."""
+    b = box(28, 28, 28, 1.0)
+    p = particle((6.0, 3.0, 3.0), (14.2, 13.9, 14.1), random_quaternion(rng(11)), B1=1e-3, B2=2e-3)
+    _compare_run([b], [[p]], steps=60, every=6, tol_ft=5e-5)
+
+
+def test_uneven_batch_of_boxes():
+    """Three boxes of different shapes in one launch (ragged rows and tails),
+    one of them empty of particles, one with two particles."""
+    g = rng(12)
+    boxes = [box(48, 20, 24, 0.8, counter_force=1), box(16, 36, 20, 1.2),
+             box(36, 32, 28, 1.0, body_force=(1e-6, 0, -2e-6))]
+    parts = [[particle((4.0, 2.0, 2.0), (20.5, 10.2, 12.1), random_quaternion(g), F_ext=(2e-4, 0, 0))],
+             [],
+             [particle((3.0, 3.0, 3.0), (8.3, 8.1, 7.7), random_quaternion(g), U=(0.01, 0, 0)),
+              particle((4.0, 3.0, 2.0), (26.2, 22.9, 20.4), random_quaternion(g), F_ext=(0, 1e-4, 0))]]
+    _compare_run(boxes, parts, steps=40, every=8)
+
+
+def test_sweep_8x64_bench_workload_sampled():
+    """The benchmark workload (8 boxes of 64^3, tau = 0.8, spheroid (8,4,4)) in the
+    same launch configuration, checked against the oracle for its first steps."""
+    boxes, parts = sweep_8x64(seed=0)
+    _compare_run(boxes, parts, steps=6, every=3)
+
+
+def test_fields_before_first_step_are_rest_state():
+    boxes, parts = single_32(seed=3)
+    gpu = _sim(boxes, parts)
+    f = gpu.field("f")
+    _, w = L.lb_lattice()
+    solid = gpu.field("solid") != 0
+    fl = ~solid
+    assert np.allclose(f[:, fl], w[:, None].astype(np.float32), rtol=0, atol=0)
+    assert (f[:, solid] == 0).all()
+
+
+def test_runs_are_bitwise_reproducible_and_graph_equals_direct():
+    boxes, parts = single_32(seed=4)
+    outs = []
+    for graphs in (True, True, False):
+        g = _sim(boxes, parts, graphs=graphs)
+        g.step(70)
+        outs.append((g.field("df"), g.records()))
+    for df, rec in outs[1:]:
+        assert np.array_equal(df, outs[0][0]) and np.array_equal(rec, outs[0][1])
+
+
+def test_invalid_particles_rejected():
+    b = box(32, 32, 32, 1.0)
+    with pytest.raises(L.LBError):
+        _sim([b], [[particle((40.0, 2.0, 2.0), (16, 16, 16))]])   # larger than max_semi / the box
+    with pytest.raises(L.LBError):
+        _sim([b], [[particle((4.0, 2.0, 2.0), (16, 16, 16), q=(1.0, 1.0, 0.0, 0.0))]])
+    g = L.Simulation([b], [[particle((4.0, 2.0, 2.0), (16, 16, 16))]], max_semi=8)
+    g.step(1)
+    with pytest.raises(L.LBError) as e:
+        g.set_particles(0, [particle((4.0, 2.0, 2.0), (16, 16, 16))])
+    assert e.value.status == 8
