@@ -181,6 +181,34 @@ lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, double* ms_
 /* Waits for all work of the context and returns the device status word's error. */
 lb_status lb_synchronize(lb_ctx* ctx);
 
+/* Boundary links of one spheroid, for callers that cannot allocate device
+ * memory: a plug-in running inside a host program that owns the device's
+ * memory pool and forbids raw allocations, or a real-time loop that cannot take
+ * the implicit synchronisation of cudaMalloc.  The paper has no counterpart of
+ * this entry point; it computes what lb_get_links returns for a particle with
+ * this pose in a box of nx x ny x nz nodes (walls != 0: solid planes y = 0 and
+ * y = ny-1), without a context.
+ *
+ * Inputs: semi[3], q[4] (unit), x[3] in host memory.  Outputs, in caller-owned
+ * device memory: pairs_dev[2k] = node index (z*ny + y)*nx + x of the fluid node,
+ * pairs_dev[2k+1] = direction b (lb_lattice order), for k < min(count, cap), in
+ * no particular order, and *count_dev = the number of links.  Asynchronous on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).
+ *
+ * Allocates nothing: the occupancy bitmap and the counter are kept in one
+ * file-scope device array of 32 KiB + 256 B, held by every GPU that loads the
+ * library until the process exits.  The maximum is a bounding cube of 64 nodes
+ * a side, i.e. semi-axes up to 29 lattice units; larger particles (or a cube
+ * larger than the box) return LB_ECAPACITY.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current,
+ * so make that first call before any stream capture.  Every call shares the
+ * array and clears it first; calls whose work overlaps on the GPU race on it,
+ * so serialise them (one stream, or events).
+ * Errors: LB_EINVAL (bad pose, sizes or pointers), LB_ECAPACITY, LB_ECUDA. */
+lb_status lb_links_noalloc(const double* semi, const double* q, const double* x, int32_t nx, int32_t ny,
+                           int32_t nz, int32_t walls, int32_t* pairs_dev, int32_t cap, int32_t* count_dev,
+                           void* stream);
+
 /* The library's D3Q19 table: c[19][3] and w[19] (1/3, 1/18, 1/36). */
 void lb_lattice(int32_t* c57, double* w19);
 

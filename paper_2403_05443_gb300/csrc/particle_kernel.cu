@@ -23,7 +23,9 @@
 // of the new map, the drag matrices of Eq. drag1-drag4 from them, the
 // squirmer-slip sums, and the list of nodes the boundary kernel must redo.
 #include <cmath>
+#include <mutex>
 
+#include "../../include/lbsph.h"
 #include "lattice_common.cuh"
 
 namespace lbsph {
@@ -798,6 +800,144 @@ __global__ void __launch_bounds__(PBLOCK) links_kernel(const PartDev* pd, const 
         }
     }
 }
+
+// ---------------------------------------------------------------------------
+// Boundary links of one spheroid without any allocation (lb_links_noalloc).
+//
+// The occupancy bitmap and the link counter live in this file-scope scratch,
+// shared by every call on a device and kept from one call to the next; each
+// call clears the part it uses first.  Calls that overlap on the GPU race on it.
+constexpr int NOALLOC_WORDS = MAXS * MAXS;                  // 32 KiB of bitmap rows
+static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_WORDS + 32];
+
+struct NoallocArgs {
+    double semi[3], q[4], x[3];
+    int nx, ny, nz, walls, S, h, cap;
+    int* pairs;
+    int* count;
+};
+
+__global__ void __launch_bounds__(PBLOCK) links_noalloc_kernel(const NoallocArgs a, uint64_t* scratch)
+{
+    uint64_t* rows = scratch;
+    int* cnt = reinterpret_cast<int*>(scratch + NOALLOC_WORDS);
+    const int tid = threadIdx.x, Sd = a.S;
+    __shared__ double s_A[9], s_xc[3];
+    __shared__ float s_e[3][3], s_inv[3], s_ro[3];
+    __shared__ int s_o[3];
+    for (int r = tid; r < Sd * Sd; r += PBLOCK) rows[r] = 0ull;
+    if (tid == 0) {
+        *cnt = 0;
+        double e[3][3];
+        canon_shape(a.semi, a.q, s_A, e);
+        for (int k = 0; k < 3; ++k) {
+            s_o[k] = (int)floor(a.x[k]) - a.h;
+            s_xc[k] = a.x[k];
+            s_ro[k] = (float)((double)s_o[k] - a.x[k]);
+            s_inv[k] = (float)(1.0 / (a.semi[k] * a.semi[k]));
+            for (int j = 0; j < 3; ++j) s_e[k][j] = (float)e[k][j];
+        }
+    }
+    __syncthreads();
+    const bool py = !a.walls;
+    // occupancy: FP32 test away from the surface, exact FP64 test near it
+    for (int n = tid; n < Sd * Sd * Sd; n += PBLOCK) {
+        const int mx = n % Sd, my = (n / Sd) % Sd, mz = n / (Sd * Sd);
+        const float dx = s_ro[0] + mx, dy = s_ro[1] + my, dz = s_ro[2] + mz;
+        float v = 0.0f;
+        for (int m = 0; m < 3; ++m) {
+            const float t = s_e[m][0] * dx + s_e[m][1] * dy + s_e[m][2] * dz;
+            v += t * t * s_inv[m];
+        }
+        bool solid;
+        if (fabsf(v - 1.0f) > 1e-4f) {
+            solid = v < 1.0f;
+        } else {
+            solid = canon_value(s_A, s_xc, wrapi(s_o[0] + mx, a.nx), wrapi(s_o[1] + my, a.ny), wrapi(s_o[2] + mz, a.nz),
+                                a.nx, a.ny, a.nz, py) <= 1.0;
+        }
+        const int Yu = s_o[1] + my;
+        if (solid && !(a.walls && (Yu <= 0 || Yu >= a.ny - 1)))
+            atomicOr(reinterpret_cast<unsigned long long*>(rows + mz * Sd + my), 1ull << mx);
+    }
+    __syncthreads();
+    // links (x fluid, x + c_b solid), written as (node index, direction) pairs
+    const uint64_t maskS = Sd >= 64 ? ~0ull : ((1ull << Sd) - 1ull);
+    for (int it = tid; it < Sd * Sd * 18; it += PBLOCK) {
+        const int r = it / 18, b = 1 + it % 18;
+        const int my = r % Sd, mz = r / Sd;
+        const int Yu = s_o[1] + my;
+        if (a.walls && (Yu <= 0 || Yu >= a.ny - 1)) continue;
+        const int ny2 = my + cy_of(b), nz2 = mz + cz_of(b);
+        if (ny2 < 0 || ny2 >= Sd || nz2 < 0 || nz2 >= Sd) continue;
+        const uint64_t nb = rows[nz2 * Sd + ny2];
+        const uint64_t sh = cx_of(b) == 1 ? (nb >> 1) : (cx_of(b) == -1 ? (nb << 1) : nb);
+        uint64_t L = ~rows[r] & sh & maskS;
+        while (L) {
+            const int mx = __ffsll((long long)L) - 1;
+            L &= L - 1;
+            const int k = atomicAdd(cnt, 1);
+            if (k < a.cap) {
+                const int X = wrapi(s_o[0] + mx, a.nx), Y = wrapi(Yu, a.ny), Z = wrapi(s_o[2] + mz, a.nz);
+                a.pairs[2 * k] = (Z * a.ny + Y) * a.nx + X;
+                a.pairs[2 * k + 1] = b;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) *a.count = *cnt;
+}
+
+}  // namespace lbsph
+
+// Device address of the scratch array, looked up once per device (host code
+// cannot use the array's name as an address).
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_ptr[256];
+
+extern "C" lb_status lb_links_noalloc(const double* semi, const double* q, const double* x, int32_t nx, int32_t ny,
+                                      int32_t nz, int32_t walls, int32_t* pairs_dev, int32_t cap, int32_t* count_dev,
+                                      void* stream)
+{
+    using namespace lbsph;
+    if (!semi || !q || !x || !pairs_dev || !count_dev || cap < 0) return LB_EINVAL;
+    if (nx < 4 || ny < 4 || nz < 4 || (walls && ny < 5)) return LB_EINVAL;
+    const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (std::fabs(qn - 1.0) > 1e-6) return LB_EINVAL;
+    double m = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        if (!(semi[k] > 0.0)) return LB_EINVAL;
+        m = std::fmax(m, semi[k]);
+    }
+    NoallocArgs a{};
+    a.h = (int)std::ceil(m) + CUBE_MARGIN;
+    a.S = 2 * a.h + 2;
+    if (a.S > MAXS || a.S > nx || a.S > nz || (!walls && a.S > ny)) return LB_ECAPACITY;
+    for (int k = 0; k < 3; ++k) { a.semi[k] = semi[k]; a.x[k] = x[k]; }
+    for (int k = 0; k < 4; ++k) a.q[k] = q[k] / qn;
+    a.nx = nx; a.ny = ny; a.nz = nz; a.walls = walls; a.cap = cap;
+    a.pairs = pairs_dev;
+    a.count = count_dev;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return LB_ECUDA;
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return LB_ECUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    links_noalloc_kernel<<<1, PBLOCK, 0, static_cast<cudaStream_t>(stream)>>>(a, static_cast<uint64_t*>(scratch));
+    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;
+}
+
+namespace lbsph {
 
 cudaError_t launch_particles(const PParams& p, cudaStream_t s)
 {

@@ -79,6 +79,8 @@ def library(path: str | None = None):
     L.lb_get_drag.argtypes = [vp, i32, i32, dp]
     L.lb_synchronize.argtypes = [vp]
     L.lb_profile_step.argtypes = [vp, i32, vp, dp]
+    L.lb_links_noalloc.argtypes = [dp, dp, dp, i32, i32, i32, i32, vp, i32, vp, vp]
+    L.lb_links_noalloc.restype = i32
     L.lb_lattice.argtypes = [ip, dp]
     L.lb_lattice.restype = None
     L.lb_status_string.argtypes = [i32]
@@ -212,6 +214,21 @@ def lb_get_drag(ctx, box: int, particle: int) -> np.ndarray:
 
 def lb_synchronize(ctx):
     _check(library().lb_synchronize(ctx), ctx)
+
+
+def lb_links_noalloc(semi, q, x, nx, ny, nz, walls, pairs_dev_ptr: int, cap: int, count_dev_ptr: int, stream=None):
+    """Boundary links of one spheroid into caller-owned device buffers, with no
+    allocation by the library (see include/lbsph.h).  pairs_dev_ptr / count_dev_ptr
+    are device addresses (e.g. tensor.data_ptr())."""
+    def d(v, n):
+        a = np.ascontiguousarray(np.asarray(v, np.float64))
+        assert a.size == n
+        return a
+    s, qq, xx = d(semi, 3), d(q, 4), d(x, 3)
+    dp = C.POINTER(C.c_double)
+    _check(library().lb_links_noalloc(s.ctypes.data_as(dp), qq.ctypes.data_as(dp), xx.ctypes.data_as(dp),
+                                      int(nx), int(ny), int(nz), int(walls), C.c_void_p(pairs_dev_ptr), int(cap),
+                                      C.c_void_p(count_dev_ptr), stream))
 
 
 # ---------------------------------------------------------------------------
