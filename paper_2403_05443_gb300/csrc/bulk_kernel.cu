@@ -11,19 +11,23 @@
 // Wall links (solid planes y = 0 and y = ny-1 moving with u_w) are handled
 // here: they are static and row-uniform.  Nodes next to a particle get a
 // provisional value that the boundary kernel overwrites.
+//
+// The grid is persistent (each CTA walks tiles with a grid stride) and a few
+// CTAs short of two per SM, so that SMs keep room for the particle kernels that
+// run concurrently on the particle stream.
 #include "lattice_common.cuh"
 
 namespace lbsph {
 
 template <class St, bool FIRST>
-__global__ void __launch_bounds__(KBLOCK, 2) bulk_kernel(const BulkParams P)
+__device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile)
 {
     using T = typename St::T;
-    const int bi = __ldg(P.blk_box + blockIdx.x);
+    const int bi = __ldg(P.blk_box + tile);
     const BoxDev& B = P.boxes[bi];
     const int nx = B.nx, ny = B.ny, nz = B.nz, nxq = B.nxq;
     const long long N = B.N;
-    long long q = (long long)(blockIdx.x - B.block_begin) * KBLOCK + threadIdx.x;
+    long long q = (long long)(tile - B.block_begin) * KBLOCK + threadIdx.x;
     const bool valid = q < B.nq;
     if (!valid) q = B.nq - 1;
     const int xq = (int)(q % nxq);
@@ -99,11 +103,31 @@ __global__ void __launch_bounds__(KBLOCK, 2) bulk_kernel(const BulkParams P)
     }
 }
 
-template <class St>
-static cudaError_t launch_bulk_t(const BulkParams& p, int blocks, cudaStream_t s)
+template <class St, bool FIRST>
+__global__ void __launch_bounds__(KBLOCK, 2) bulk_kernel(const BulkParams P, int tiles)
 {
-    if (p.first) bulk_kernel<St, true><<<blocks, KBLOCK, 0, s>>>(p);
-    else bulk_kernel<St, false><<<blocks, KBLOCK, 0, s>>>(p);
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) bulk_tile<St, FIRST>(P, tile);
+}
+
+static int bulk_grid(int tiles)
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 1;
+    }
+    // two CTAs per SM fill the registers; leave half of 16 SMs to the particle stream
+    const int g = nsm > 32 ? 2 * nsm - 16 : 2 * nsm;
+    return tiles < g ? tiles : g;
+}
+
+template <class St>
+static cudaError_t launch_bulk_t(const BulkParams& p, int tiles, cudaStream_t s)
+{
+    const int g = bulk_grid(tiles);
+    if (p.first) bulk_kernel<St, true><<<g, KBLOCK, 0, s>>>(p, tiles);
+    else bulk_kernel<St, false><<<g, KBLOCK, 0, s>>>(p, tiles);
     return cudaGetLastError();
 }
 

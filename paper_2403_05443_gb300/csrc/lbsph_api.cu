@@ -1,10 +1,13 @@
 // Host runtime behind the C ABI of include/lbsph.h.
 //
-// One iteration is four kernels: bulk (every node), boundary (the listed nodes
-// near particles), particle-critical (solve, pose, new occupancy, box forces)
-// on the caller's stream, and particle-auxiliary (link moments, drag matrices,
-// next boundary list) on a second stream, overlapping the next bulk kernel and
-// joined before the next boundary kernel.  Chunks of iterations are captured
+// One iteration is five kernels on two streams.  The caller's stream runs the
+// bulk kernel (every node) and the scatter kernel (boundary nodes into the
+// lattice); a high-priority particle stream runs, while the bulk kernel
+// streams the lattice, the boundary kernel, the critical particle kernel
+// (solve, pose, new occupancy, box forces for the next step) and the auxiliary
+// one (link moments, drag matrices, next boundary list).  Events order them:
+// bulk(t) waits for critical(t-1) (box forces), boundary(t) for scatter(t-1)
+// (complete lattice), scatter(t) for boundary(t).  Chunks of iterations are captured
 // once into a CUDA graph per buffer parity and replayed, so a long run costs
 // one graph launch per chunk and no host synchronisation.
 #include <cmath>
@@ -21,6 +24,7 @@ namespace lbsph {
 cudaError_t launch_fields(const KParams& p, int precision, int blocks, cudaStream_t s);
 cudaError_t launch_bulk(const BulkParams& p, int precision, int blocks, cudaStream_t s);
 cudaError_t launch_boundary(const BndParams& p, int precision, int list_cap, int np, cudaStream_t s);
+cudaError_t launch_scatter(const BndParams& p, int precision, int list_cap, int np, cudaStream_t s);
 cudaError_t launch_particles(const PParams& p, cudaStream_t s);
 cudaError_t launch_particles_aux(const PParams& p, cudaStream_t s);
 cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
@@ -64,8 +68,11 @@ struct lb_ctx {
     unsigned sticky = 0;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaStream_t last_user_stream = nullptr;        // last stream lb_step ran on
-    cudaStream_t aux = nullptr;                     // stream of the auxiliary particle kernel
-    cudaEvent_t ev_crit = nullptr, ev_aux = nullptr;
+    cudaStream_t aux = nullptr;                     // the particle stream
+    cudaEvent_t ev_crit = nullptr, ev_aux = nullptr, ev_fork = nullptr, ev_bnd = nullptr;
+    float* d_side_val = nullptr;
+    int* d_side_idx = nullptr;
+    int* d_side_count = nullptr;
     int* d_blk_box = nullptr;
     BoxDyn* d_box_dyn = nullptr;
     int* d_box_done = nullptr;
@@ -190,10 +197,14 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     ctx->device = o.device;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) { delete ctx; return LB_ECUDA; }
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_crit, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_aux, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_aux, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_bnd, cudaEventDisableTiming) != cudaSuccess) {
         delete ctx;
         return LB_ECUDA;
     }
@@ -246,7 +257,7 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     ctx->d_status = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * 4);
     ctx->d_count = (int*)dev_alloc(ctx, sizeof(int) * 4);
     ctx->d_blk_box = (int*)dev_alloc(ctx, sizeof(int) * (size_t)blk);
-    ctx->d_box_dyn = (BoxDyn*)dev_alloc(ctx, sizeof(BoxDyn) * nbox);
+    ctx->d_box_dyn = (BoxDyn*)dev_alloc(ctx, sizeof(BoxDyn) * 2 * nbox);   // one slot per buffer parity
     ctx->d_box_done = (int*)dev_alloc(ctx, sizeof(int) * nbox);
     {
         const long long Smax = 2ll * (o.max_semi + CUBE_MARGIN) + 2;
@@ -254,10 +265,14 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     }
     ctx->d_lists = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * (size_t)ctx->list_cap * ctx->maxp);
     ctx->d_list_count = (int*)dev_alloc(ctx, sizeof(int) * ctx->maxp);
+    ctx->d_side_val = (float*)dev_alloc(ctx, sizeof(float) * Q * (size_t)ctx->list_cap * ctx->maxp);
+    ctx->d_side_idx = (int*)dev_alloc(ctx, sizeof(int) * (size_t)ctx->list_cap * ctx->maxp);
+    ctx->d_side_count = (int*)dev_alloc(ctx, sizeof(int) * ctx->maxp);
     for (void* p : {ctx->fbuf[0], ctx->fbuf[1], (void*)ctx->d_boxes, (void*)ctx->d_pd, (void*)ctx->d_pk,
                     (void*)ctx->d_acc, (void*)ctx->d_rows, (void*)ctx->d_status, (void*)ctx->d_count,
                     (void*)ctx->d_blk_box, (void*)ctx->d_box_dyn, (void*)ctx->d_box_done, (void*)ctx->d_lists,
-                    (void*)ctx->d_list_count})
+                    (void*)ctx->d_list_count, (void*)ctx->d_side_val, (void*)ctx->d_side_idx,
+                    (void*)ctx->d_side_count})
         okm = okm && p;
     if (!okm) {
         free_all(ctx);
@@ -267,11 +282,11 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
         return LB_ENOMEM;
     }
     std::vector<int> blk_box(blk);
-    std::vector<BoxDyn> dyn(nbox);
+    std::vector<BoxDyn> dyn(2 * nbox);
     for (int b = 0; b < nbox; ++b) {
         for (int k = 0; k < ctx->hbox[b].nblocks; ++k) blk_box[ctx->hbox[b].block_begin + k] = b;
-        for (int k = 0; k < 3; ++k) dyn[b].g[k] = (float)boxes[b].body_force[k];
-        dyn[b].eps = 0.0f;
+        for (int k = 0; k < 3; ++k) dyn[b].g[k] = dyn[nbox + b].g[k] = (float)boxes[b].body_force[k];
+        dyn[b].eps = dyn[nbox + b].eps = 0.0f;
     }
     cudaError_t err = cudaSuccess;
     err = err ? err : cudaMemsetAsync(ctx->fbuf[0], 0, (size_t)off * ctx->elem, ctx->stream);
@@ -282,9 +297,10 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     err = err ? err : cudaMemsetAsync(ctx->d_pk, 0, sizeof(PartK) * ctx->maxp, ctx->stream);
     err = err ? err : cudaMemcpyAsync(ctx->d_boxes, ctx->hbox.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice, ctx->stream);
     err = err ? err : cudaMemcpyAsync(ctx->d_blk_box, blk_box.data(), sizeof(int) * blk, cudaMemcpyHostToDevice, ctx->stream);
-    err = err ? err : cudaMemcpyAsync(ctx->d_box_dyn, dyn.data(), sizeof(BoxDyn) * nbox, cudaMemcpyHostToDevice, ctx->stream);
+    err = err ? err : cudaMemcpyAsync(ctx->d_box_dyn, dyn.data(), sizeof(BoxDyn) * 2 * nbox, cudaMemcpyHostToDevice, ctx->stream);
     err = err ? err : cudaMemsetAsync(ctx->d_box_done, 0, sizeof(int) * nbox, ctx->stream);
     err = err ? err : cudaMemsetAsync(ctx->d_list_count, 0, sizeof(int) * ctx->maxp, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_side_count, 0, sizeof(int) * ctx->maxp, ctx->stream);
     err = err ? err : cudaStreamSynchronize(ctx->stream);
     if (err != cudaSuccess) {
         free_all(ctx);
@@ -315,15 +331,20 @@ extern "C" lb_status lb_destroy(lb_ctx* ctx)
     cudaStreamDestroy(ctx->aux);
     cudaEventDestroy(ctx->ev_crit);
     cudaEventDestroy(ctx->ev_aux);
+    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_bnd);
     delete ctx;
     return LB_OK;
 }
 
-static PParams particle_params(lb_ctx* ctx)
+// the critical particle kernel of iteration t (buffer parity cur) writes the box
+// terms that the bulk and boundary kernels of iteration t+1 (parity cur^1) read
+static PParams particle_params(lb_ctx* ctx, int cur)
 {
     PParams pp{};
     pp.pd = ctx->d_pd; pp.pk = ctx->d_pk; pp.acc = ctx->d_acc; pp.rows = ctx->d_rows;
-    pp.boxes = ctx->d_boxes; pp.box_dyn = ctx->d_box_dyn; pp.box_done = ctx->d_box_done;
+    pp.boxes = ctx->d_boxes; pp.box_dyn = ctx->d_box_dyn + (size_t)(cur ^ 1) * ctx->desc.size();
+    pp.box_done = ctx->d_box_done;
     pp.status = ctx->d_status; pp.np = ctx->np; pp.init = 0;
     pp.didt_mode = ctx->opt.didt_mode;
     pp.smax = 2 * (ctx->opt.max_semi + CUBE_MARGIN) + 2;
@@ -420,21 +441,27 @@ extern "C" lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particl
             pk[i].list = ctx->d_lists + (size_t)i * ctx->list_cap;
             pk[i].list_count = ctx->d_list_count + i;
             pk[i].list_cap = ctx->list_cap;
+            pk[i].side_val = ctx->d_side_val + (size_t)i * ctx->list_cap * Q;
+            pk[i].side_idx = ctx->d_side_idx + (size_t)i * ctx->list_cap;
+            pk[i].side_count = ctx->d_side_count + i;
         }
         CK(cudaMemcpyAsync(ctx->d_pk, pk.data(), sizeof(PartK) * ctx->maxp, cudaMemcpyHostToDevice, ctx->stream));
-        std::vector<BoxDyn> dyn(ctx->desc.size());
-        for (size_t b = 0; b < dyn.size(); ++b) {
-            for (int k = 0; k < 3; ++k) dyn[b].g[k] = (float)ctx->desc[b].body_force[k];
-            dyn[b].eps = 0.0f;
+        const size_t nb = ctx->desc.size();
+        std::vector<BoxDyn> dyn(2 * nb);
+        for (size_t b = 0; b < nb; ++b) {
+            for (int k = 0; k < 3; ++k) dyn[b].g[k] = dyn[nb + b].g[k] = (float)ctx->desc[b].body_force[k];
+            dyn[b].eps = dyn[nb + b].eps = 0.0f;
         }
         CK(cudaMemcpyAsync(ctx->d_box_dyn, dyn.data(), sizeof(BoxDyn) * dyn.size(), cudaMemcpyHostToDevice, ctx->stream));
     }
     clear_stale_error();
-    PParams pp = particle_params(ctx);
+    // the initial state serves the first iteration, which reads parity ctx->cur
+    PParams pp = particle_params(ctx, ctx->cur ^ 1);
     pp.init = 1;
     CK(launch_particles(pp, ctx->stream));
     CK(launch_particles_aux(pp, ctx->stream));
     CK(cudaEventRecord(ctx->ev_aux, ctx->stream));
+    CK(cudaEventRecord(ctx->ev_crit, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     drop_graphs(ctx);
     return read_status(ctx);
@@ -468,29 +495,52 @@ static KParams base_kparams(lb_ctx* ctx, int mode)
     return k;
 }
 
-// one iteration: bulk, boundary (after the previous auxiliary kernel), the
-// critical particle kernel on s, then the auxiliary particle kernel on the
-// second stream, recorded so that the next boundary kernel waits for it
-static cudaError_t enqueue_iteration(lb_ctx* ctx, int first, int cur, cudaStream_t s, cudaEvent_t ev_crit,
-                                     cudaEvent_t ev_aux)
+struct IterEvents {
+    cudaEvent_t fork, bnd, crit, aux;   // fork: lattice of t-1 complete; crit: box forces of t ready
+};
+
+static BulkParams bulk_params(lb_ctx* ctx, int first, int cur)
 {
     BulkParams bp{};
-    bp.boxes = ctx->d_boxes; bp.blk_box = ctx->d_blk_box; bp.box_dyn = ctx->d_box_dyn;
+    bp.boxes = ctx->d_boxes; bp.blk_box = ctx->d_blk_box;
+    bp.box_dyn = ctx->d_box_dyn + (size_t)cur * ctx->desc.size();
     bp.src = ctx->fbuf[cur]; bp.dst = ctx->fbuf[cur ^ 1]; bp.first = first;
-    cudaError_t e = launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s);
-    if (e != cudaSuccess || ctx->np == 0) return e;
-    if ((e = cudaStreamWaitEvent(s, ev_aux, 0)) != cudaSuccess) return e;
-    BndParams np{};
-    np.boxes = ctx->d_boxes; np.box_dyn = ctx->d_box_dyn; np.pk = ctx->d_pk;
-    np.src = ctx->fbuf[cur]; np.dst = ctx->fbuf[cur ^ 1]; np.first = first;
-    if ((e = launch_boundary(np, ctx->opt.precision, ctx->list_cap, ctx->np, s)) != cudaSuccess) return e;
-    const PParams pp = particle_params(ctx);
-    if ((e = launch_particles(pp, s)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(ev_crit, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(ctx->aux, ev_crit, 0)) != cudaSuccess) return e;
-    if ((e = launch_particles_aux(pp, ctx->aux)) != cudaSuccess) return e;
-    return cudaEventRecord(ev_aux, ctx->aux);
+    return bp;
 }
+
+static BndParams bnd_params(lb_ctx* ctx, int first, int cur)
+{
+    BndParams np{};
+    np.boxes = ctx->d_boxes; np.box_dyn = ctx->d_box_dyn + (size_t)cur * ctx->desc.size(); np.pk = ctx->d_pk;
+    np.src = ctx->fbuf[cur]; np.dst = ctx->fbuf[cur ^ 1]; np.first = first;
+    np.smax = 2 * (ctx->opt.max_semi + CUBE_MARGIN) + 2;
+    return np;
+}
+
+// One iteration on the caller's stream s and the particle stream ctx->aux.
+static cudaError_t enqueue_iteration(lb_ctx* ctx, int first, int cur, cudaStream_t s, const IterEvents& ev)
+{
+    cudaError_t e;
+    const BulkParams bp = bulk_params(ctx, first, cur);
+    if (ctx->np == 0) return launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s);
+    if ((e = cudaEventRecord(ev.fork, s)) != cudaSuccess) return e;             // lattice of t-1 complete
+    if ((e = cudaStreamWaitEvent(s, ev.crit, 0)) != cudaSuccess) return e;      // box forces of t
+    if ((e = launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s)) != cudaSuccess) return e;
+    const BndParams np = bnd_params(ctx, first, cur);
+    const PParams pp = particle_params(ctx, cur);
+    cudaStream_t t = ctx->aux;
+    if ((e = cudaStreamWaitEvent(t, ev.fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_boundary(np, ctx->opt.precision, ctx->list_cap, ctx->np, t)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev.bnd, t)) != cudaSuccess) return e;
+    if ((e = launch_particles(pp, t)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev.crit, t)) != cudaSuccess) return e;
+    if ((e = launch_particles_aux(pp, t)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev.aux, t)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, ev.bnd, 0)) != cudaSuccess) return e;
+    return launch_scatter(np, ctx->opt.precision, ctx->list_cap, ctx->np, s);
+}
+
+static IterEvents ctx_events(lb_ctx* ctx) { return IterEvents{ctx->ev_fork, ctx->ev_bnd, ctx->ev_crit, ctx->ev_aux}; }
 
 // The graph gets its own events: an event last recorded inside a capture
 // cannot be waited on outside it.
@@ -499,30 +549,33 @@ static lb_status build_graph(lb_ctx* ctx, int parity)
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
-    cudaEvent_t fork = nullptr, ec = nullptr, ea = nullptr;
-    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ec, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ea, cudaEventDisableTiming);
+    cudaEvent_t evs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (auto& ev : evs)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     const bool capturing = e == cudaSuccess;
-    // the auxiliary stream joins the capture through the fork event
-    if (e == cudaSuccess) e = cudaEventRecord(fork, cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, fork, 0);
-    if (e == cudaSuccess) e = cudaEventRecord(ea, ctx->aux);
+    const IterEvents ev{evs[0], evs[1], evs[2], evs[3]};
+    // the particle stream joins the capture; box forces and list of the first
+    // captured iteration are ready when the graph starts
+    if (e == cudaSuccess) e = cudaEventRecord(evs[4], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, evs[4], 0);
+    if (e == cudaSuccess) e = cudaEventRecord(ev.crit, ctx->aux);
+    if (e == cudaSuccess) e = cudaEventRecord(ev.aux, ctx->aux);
     int c = parity;
     for (int i = 0; e == cudaSuccess && i < GRAPH_ITERS; ++i) {
-        e = enqueue_iteration(ctx, 0, c, cs, ec, ea);
+        e = enqueue_iteration(ctx, 0, c, cs, ev);
         c ^= 1;
     }
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ea, 0);   // join the auxiliary branch
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev.aux, 0);   // join the particle stream
     if (capturing) {
         const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->gexec[parity], g, 0);
     if (g) cudaGraphDestroy(g);
-    for (cudaEvent_t ev : {fork, ec, ea})
-        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t x : evs)
+        if (x) cudaEventDestroy(x);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -542,30 +595,37 @@ extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
     ctx->last_user_stream = s;
     int left = nsteps;
     ctx->stepped = true;
-    CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));      // work already enqueued on the auxiliary stream
+    const IterEvents ev = ctx_events(ctx);
     if (!ctx->collided) {
-        CK(enqueue_iteration(ctx, 1, ctx->cur, s, ctx->ev_crit, ctx->ev_aux));
+        CK(enqueue_iteration(ctx, 1, ctx->cur, s, ev));
         ctx->cur ^= 1;
         ctx->collided = true;
         --left;
     }
-    const bool graphs = !(ctx->opt.flags & LB_FLAG_NO_GRAPH);
+    const bool graphs = !(ctx->opt.flags & LB_FLAG_NO_GRAPH) && ctx->np > 0;
     if (graphs && left >= GRAPH_ITERS && !ctx->gexec[ctx->cur]) {
         // both parities at once, so that no capture happens inside a timed run later
         lb_status st = build_graph(ctx, 0);
         if (st == LB_OK) st = build_graph(ctx, 1);
         if (st != LB_OK) return st;
     }
+    if (graphs && left >= GRAPH_ITERS) {
+        // the graph starts from a finished particle stream
+        CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
+        CK(cudaStreamWaitEvent(s, ctx->ev_crit, 0));
+    }
     bool launched = false;
-    if (graphs && left >= GRAPH_ITERS) CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
     while (graphs && left >= GRAPH_ITERS) {
-        CK(cudaGraphLaunch(ctx->gexec[ctx->cur], s));   // joins its auxiliary branch at the end
+        CK(cudaGraphLaunch(ctx->gexec[ctx->cur], s));   // joins its particle stream at the end
         left -= GRAPH_ITERS;     // even count: parity unchanged
         launched = true;
     }
-    if (launched) CK(cudaEventRecord(ctx->ev_aux, s));
+    if (launched) {
+        CK(cudaEventRecord(ctx->ev_crit, s));
+        CK(cudaEventRecord(ctx->ev_aux, s));
+    }
     for (; left > 0; --left) {
-        CK(enqueue_iteration(ctx, 0, ctx->cur, s, ctx->ev_crit, ctx->ev_aux));
+        CK(enqueue_iteration(ctx, 0, ctx->cur, s, ev));
         ctx->cur ^= 1;
     }
     CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));      // everything ordered on the caller's stream
@@ -577,33 +637,33 @@ extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, 
     if (!ctx) return LB_EINVAL;
     if (nsteps <= 0 || !ms_out) return fail(ctx, LB_EINVAL, "bad step count or output");
     CK(cudaSetDevice(ctx->device));
+    clear_stale_error();
     cudaStream_t s = pick(ctx, stream);
     ctx->last_user_stream = s;
     ctx->stepped = true;
     CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
-    cudaEvent_t ev[5];
+    CK(cudaStreamWaitEvent(s, ctx->ev_crit, 0));
+    cudaEvent_t ev[6];
     for (auto& e : ev) CK(cudaEventCreate(&e));
-    double t[4] = {0, 0, 0, 0};
+    double t[5] = {0, 0, 0, 0, 0};
     for (int i = 0; i < nsteps; ++i) {
         const int first = ctx->collided ? 0 : 1;
-        BulkParams bp{};
-        bp.boxes = ctx->d_boxes; bp.blk_box = ctx->d_blk_box; bp.box_dyn = ctx->d_box_dyn;
-        bp.src = ctx->fbuf[ctx->cur]; bp.dst = ctx->fbuf[ctx->cur ^ 1]; bp.first = first;
-        BndParams np{};
-        np.boxes = ctx->d_boxes; np.box_dyn = ctx->d_box_dyn; np.pk = ctx->d_pk;
-        np.src = ctx->fbuf[ctx->cur]; np.dst = ctx->fbuf[ctx->cur ^ 1]; np.first = first;
-        const PParams pp = particle_params(ctx);
+        const BulkParams bp = bulk_params(ctx, first, ctx->cur);
+        const BndParams np = bnd_params(ctx, first, ctx->cur);
+        const PParams pp = particle_params(ctx, ctx->cur);
         CK(cudaEventRecord(ev[0], s));
         CK(launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s));
         CK(cudaEventRecord(ev[1], s));
         CK(launch_boundary(np, ctx->opt.precision, ctx->list_cap, ctx->np, s));
         CK(cudaEventRecord(ev[2], s));
-        CK(launch_particles(pp, s));
+        CK(launch_scatter(np, ctx->opt.precision, ctx->list_cap, ctx->np, s));
         CK(cudaEventRecord(ev[3], s));
-        CK(launch_particles_aux(pp, s));
+        CK(launch_particles(pp, s));
         CK(cudaEventRecord(ev[4], s));
-        CK(cudaEventSynchronize(ev[4]));
-        for (int k = 0; k < 4; ++k) {
+        CK(launch_particles_aux(pp, s));
+        CK(cudaEventRecord(ev[5], s));
+        CK(cudaEventSynchronize(ev[5]));
+        for (int k = 0; k < 5; ++k) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
             t[k] += ms;
@@ -612,8 +672,12 @@ extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, 
         ctx->collided = true;
     }
     CK(cudaEventRecord(ctx->ev_aux, s));
+    CK(cudaEventRecord(ctx->ev_crit, s));
     for (auto& e : ev) cudaEventDestroy(e);
-    for (int k = 0; k < 4; ++k) ms_out[k] = t[k];
+    ms_out[0] = t[0];            // bulk
+    ms_out[1] = t[1] + t[2];     // boundary + scatter
+    ms_out[2] = t[3];            // particle critical
+    ms_out[3] = t[4];            // particle auxiliary
     return read_status(ctx);
 }
 

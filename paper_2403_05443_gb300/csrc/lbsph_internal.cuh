@@ -1,15 +1,19 @@
 // Internal definitions shared by the CUDA translation units of liblbsph.
 //
-// One iteration t of the paper's Appendix is four kernels:
-//   bulk      every node: pull streaming + BGK/Guo collision, wall links inline
-//             (the only kernel that moves the whole lattice: 2*19*s bytes/node);
-//   boundary  the listed nodes next to a particle's old or new surface: redoes
-//             them with link bounce-back (Eq. fb, Eq. ub), the remap of covered /
-//             uncovered nodes and the momentum-exchange sums of the new links;
-//   particle  (critical) force, implicit solve, pose and quaternion update, the
-//             new occupancy map and the box's uniform forces for the next step;
-//   particle  (auxiliary, concurrent with the next bulk kernel) link moments,
-//             drag matrices (Eq. drag1-drag4) and the next boundary list.
+// One iteration t of the paper's Appendix is five kernels on two streams:
+//   main stream
+//     bulk      every node: pull streaming + BGK/Guo collision, wall links inline
+//               (the only kernel that moves the whole lattice: 2*19*s bytes/node);
+//     scatter   copies the boundary kernel's nodes into the lattice;
+//   particle stream (runs while the bulk kernel streams the lattice)
+//     boundary  the listed nodes next to a particle's old or new surface, redone
+//               with link bounce-back (Eq. fb, Eq. ub), the remap of covered /
+//               uncovered nodes and the momentum-exchange sums of the new links,
+//               into a side buffer;
+//     particle  (critical) force, implicit solve, pose and quaternion update, the
+//               new occupancy map and the box's uniform forces for the next step;
+//     particle  (auxiliary) link moments, drag matrices (Eq. drag1-drag4) and the
+//               next boundary list.
 //
 // Data layout in HBM (one allocation per buffer, every box back to back):
 //   distributions  two buffers (ping-pong), each box b holds 19 planes of
@@ -129,6 +133,10 @@ struct PartK {
     int* list_count;
     int list_cap;
     int pad;
+    float* side_val;                // boundary kernel output: [list_cap][19] post-collision values
+    int* side_idx;                  // node index (>= 0 write, -1 skip, -2-node write zeros)
+    int* side_count;                // entries of side_val / side_idx written by the boundary kernel
+    int pad2;
 };
 
 // uniform per-box terms of the next collision: body force g and mass return eps
@@ -181,7 +189,7 @@ struct PParams {
     long long* acc;                 // np * NACC
     uint64_t* rows;                 // np * 2 * MAXS*MAXS words
     const BoxDev* boxes;
-    BoxDyn* box_dyn;                // per box
+    BoxDyn* box_dyn;                // per box, for the next collision (slot of the next iteration)
     int* box_done;                  // per box arrival counters (last block writes box_dyn)
     unsigned* status;
     int np;
@@ -204,8 +212,9 @@ struct BndParams {
     const BoxDyn* box_dyn;
     const PartK* pk;
     const void* src;
-    void* dst;
+    void* dst;                      // scatter kernel: the lattice buffer of iteration t
     int first;
+    int smax;                       // largest cube side (sizes dynamic shared memory)
 };
 
 inline int rows_stride() { return MAXS * MAXS; }

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(CBLOCK) particle_crit_kernel(const PParams P)
     __shared__ long long s_acc[NACC];
     __shared__ uint64_t s_rows[MAXS * MAXS];
     __shared__ long long s_isum[18];          // integer force sums
+    __shared__ long long s_iterm[Q][18];      // per-direction terms of those sums
     __shared__ double s_F0[3], s_T0[3], s_dP[3], s_dL[3], s_dm;
     __shared__ double s_R[9], s_I[9], s_dI[9], s_x6[6];
     __shared__ float s_e[3][3], s_inv[3], s_ro[3];
@@ -176,11 +177,16 @@ __global__ void __launch_bounds__(CBLOCK) particle_crit_kernel(const PParams P)
     __shared__ int s_amb[MAXAMB];
     __shared__ double s_A[9], s_xc[3];
 
-    // ---- stage the state and this step's accumulators; clear the accumulators
+    // ---- stage the state, the lattice snapshot (so that every field not
+    // updated below, e.g. buffer pointers, carries over) and this step's
+    // accumulators; clear the accumulators
     {
         const unsigned long long* src = reinterpret_cast<const unsigned long long*>(P.pd + p);
         unsigned long long* dst = reinterpret_cast<unsigned long long*>(&S);
         for (int e = tid; e < (int)(sizeof(PartDev) / 8); e += CBLOCK) dst[e] = src[e];
+        const unsigned* ks = reinterpret_cast<const unsigned*>(P.pk + p);
+        unsigned* kd = reinterpret_cast<unsigned*>(&K);
+        for (int e = tid; e < (int)(sizeof(PartK) / 4); e += CBLOCK) kd[e] = ks[e];
         long long* acc = P.acc + (long long)p * NACC;
         for (int e = tid; e < NACC; e += CBLOCK) {
             s_acc[e] = acc[e];
@@ -196,35 +202,26 @@ __global__ void __launch_bounds__(CBLOCK) particle_crit_kernel(const PParams P)
     const double rho0 = B.rho0;
 
     if (!P.init) {
-        // ---- integer sums over directions (lane b of warp 0 holds direction b)
-        if (warp == 0) {
+        // ---- integer sums over directions: lane b of warp 0 writes direction b's terms
+        if (warp == 0 && lane >= 1 && lane < Q) {
             const int b = lane;
-            long long t[18];
-#pragma unroll
-            for (int k = 0; k < 18; ++k) t[k] = 0;
-            if (b >= 1 && b < Q) {
-                const int c[3] = {cx_of(b), cy_of(b), cz_of(b)};
-                const int kw = (b <= 6) ? 2 : 1;                 // 36 w_b
-                const long long D = s_acc[ACC_LINK + 4 * b];
-                const long long E[3] = {s_acc[ACC_LINK + 4 * b + 1], s_acc[ACC_LINK + 4 * b + 2], s_acc[ACC_LINK + 4 * b + 3]};
-                const long long n = S.lm[b][0];
-                const long long M1[3] = {S.lm[b][1], S.lm[b][2], S.lm[b][3]};
-                const long long sl = S.slip[b][0];
-                const long long sm[3] = {S.slip[b][1], S.slip[b][2], S.slip[b][3]};
-                for (int k = 0; k < 3; ++k) {
-                    const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-                    t[k] = D * c[k];                                     // sum D c
-                    t[3 + k] = E[k1] * c[k2] - E[k2] * c[k1];            // sum E x c
-                    t[6 + k] = kw * n * c[k];                            // 36 sum w n c
-                    t[9 + k] = kw * (M1[k1] * c[k2] - M1[k2] * c[k1]);   // 36 sum w M1 x c
-                    t[12 + k] = kw * sl * c[k];                          // 36 sum w s c
-                    t[15 + k] = kw * (sm[k1] * c[k2] - sm[k2] * c[k1]);  // 36 sum w (s m) x c
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 18; ++k) {
-                const long long v = warp_sum_ll(t[k]);
-                if (lane == 0) s_isum[k] = v;
+            const int c[3] = {cx_of(b), cy_of(b), cz_of(b)};
+            const int kw = (b <= 6) ? 2 : 1;                 // 36 w_b
+            const long long D = s_acc[ACC_LINK + 4 * b];
+            const long long E[3] = {s_acc[ACC_LINK + 4 * b + 1], s_acc[ACC_LINK + 4 * b + 2], s_acc[ACC_LINK + 4 * b + 3]};
+            const long long n = S.lm[b][0];
+            const long long M1[3] = {S.lm[b][1], S.lm[b][2], S.lm[b][3]};
+            const long long sl = S.slip[b][0];
+            const long long sm[3] = {S.slip[b][1], S.slip[b][2], S.slip[b][3]};
+            long long* t = s_iterm[b];
+            for (int k = 0; k < 3; ++k) {
+                const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                t[k] = D * c[k];                                     // sum D c
+                t[3 + k] = E[k1] * c[k2] - E[k2] * c[k1];            // sum E x c
+                t[6 + k] = kw * n * c[k];                            // 36 sum w n c
+                t[9 + k] = kw * (M1[k1] * c[k2] - M1[k2] * c[k1]);   // 36 sum w M1 x c
+                t[12 + k] = kw * sl * c[k];                          // 36 sum w s c
+                t[15 + k] = kw * (sm[k1] * c[k2] - sm[k2] * c[k1]);  // 36 sum w (s m) x c
             }
         }
         // ---- rotation matrix at t (warp 1)
@@ -244,27 +241,37 @@ __global__ void __launch_bounds__(CBLOCK) particle_crit_kernel(const PParams P)
             s_R[lane] = r;
         }
         __syncthreads();
+        if (tid < 18) {
+            long long a = 0;
+            for (int b = 1; b < Q; ++b) a += s_iterm[b][tid];
+            s_isum[tid] = a;
+        }
+        __syncthreads();
         const double inv_fix = 1.0 / FIXD;
-        if (warp == 0 && lane < 3) {
-            // F0, T0 (Eq. F0, Eq. T0) with the geometric and slip parts
-            const int k = lane, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-            double phi[3];
-            for (int a = 0; a < 3; ++a) phi[a] = (double)S.o[a] - S.x[a];
-            const double DC[3] = {(double)s_isum[0] * inv_fix, (double)s_isum[1] * inv_fix, (double)s_isum[2] * inv_fix};
-            const double GF[3] = {(double)s_isum[6] / 36.0, (double)s_isum[7] / 36.0, (double)s_isum[8] / 36.0};
-            const double SC[3] = {(double)s_isum[12] * inv_fix / 36.0, (double)s_isum[13] * inv_fix / 36.0,
-                                  (double)s_isum[14] * inv_fix / 36.0};
-            s_F0[k] = 2.0 * DC[k] + 2.0 * rho0 * GF[k] - 6.0 * rho0 * SC[k];
-            const double pxD = phi[k1] * DC[k2] - phi[k2] * DC[k1];
-            const double pxG = phi[k1] * GF[k2] - phi[k2] * GF[k1];
-            const double pxS = phi[k1] * SC[k2] - phi[k2] * SC[k1];
-            s_T0[k] = 2.0 * (pxD + (double)s_isum[3 + k] * inv_fix) + 2.0 * rho0 * (pxG + (double)s_isum[9 + k] / 36.0) -
-                      6.0 * rho0 * (pxS + (double)s_isum[15 + k] * inv_fix / 36.0);
+        if (warp == 0 && lane < 6) {
+            // F0 (lanes 0-2), T0 (lanes 3-5) (Eq. F0, Eq. T0) with the geometric and slip parts
+            const int k = lane % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+            constexpr double i36 = 1.0 / 36.0;
+            const double fix36 = inv_fix * i36;
+            if (lane < 3) {
+                s_F0[k] = 2.0 * ((double)s_isum[k] * inv_fix) + 2.0 * rho0 * ((double)s_isum[6 + k] * i36) -
+                          6.0 * rho0 * ((double)s_isum[12 + k] * fix36);
+            } else {
+                const double phi1 = (double)S.o[k1] - S.x[k1], phi2 = (double)S.o[k2] - S.x[k2];
+                const double pxD = (phi1 * (double)s_isum[k2] - phi2 * (double)s_isum[k1]) * inv_fix;
+                const double pxG = (phi1 * (double)s_isum[6 + k2] - phi2 * (double)s_isum[6 + k1]) * i36;
+                const double pxS = (phi1 * (double)s_isum[12 + k2] - phi2 * (double)s_isum[12 + k1]) * fix36;
+                s_T0[k] = 2.0 * (pxD + (double)s_isum[3 + k] * inv_fix) + 2.0 * rho0 * (pxG + (double)s_isum[9 + k] * i36) -
+                          6.0 * rho0 * (pxS + (double)s_isum[15 + k] * fix36);
+            }
         } else if (warp == 1 && lane < 9) {
             // lab-frame inertia (Eq. Irot): I = R diag(I_body) R^T
             const int i = lane / 3, j = lane % 3;
             s_I[lane] = s_R[i * 3] * S.Ib[0] * s_R[j * 3] + s_R[i * 3 + 1] * S.Ib[1] * s_R[j * 3 + 1] +
                         s_R[i * 3 + 2] * S.Ib[2] * s_R[j * 3 + 2];
+        } else if (warp == 2 && lane == 0 && s_acc[ACC_COV] == 0 && s_acc[ACC_UNC] == 0) {
+            for (int k = 0; k < 3; ++k) { s_dP[k] = 0.0; s_dL[k] = 0.0; }   // no node changed
+            s_dm = 0.0;
         } else if (warp == 2 && lane == 0) {
             // impulse of the nodes covered / uncovered by the last remap
             double phi[3];
@@ -417,10 +424,10 @@ __global__ void __launch_bounds__(CBLOCK) particle_crit_kernel(const PParams P)
             S.Iprev[lane] = s_I[lane];
         }
         __syncthreads();
-        if (tid == 0) {
-            bool bad = false;
-            for (int k = 0; k < 25; ++k) bad |= !isfinite(S.rec[k]);
-            if (bad) atomicOr(P.status, ST_NAN);
+        if (tid < 25) {
+            // exponent all ones: Inf or NaN
+            const unsigned long long b = (unsigned long long)__double_as_longlong(S.rec[tid]);
+            if (((b >> 52) & 0x7ff) == 0x7ff) atomicOr(P.status, ST_NAN);
         }
     } else if (tid == 0) {
         // initial pose: no remap before, nothing to return
@@ -461,32 +468,31 @@ __global__ void __launch_bounds__(CBLOCK) particle_crit_kernel(const PParams P)
     }
     __syncthreads();
 
-    // ---- occupancy of the new pose: FP32 test, near-surface nodes listed
-    const int nwarp = CBLOCK / 32;
-    for (int r = warp; r < Sd * Sd; r += nwarp) {
+    // ---- occupancy of the new pose: one row per thread, FP32 test per node
+    // (the three projections e_m . d grow by e_m.x per node along the row),
+    // near-surface nodes listed for the exact test
+    for (int r = tid; r < Sd * Sd; r += CBLOCK) {
         const int my = r % Sd, mz = r / Sd;
+        const float dy = s_ro[1] + my, dz = s_ro[2] + mz;
+        float t0 = s_e[0][0] * s_ro[0] + s_e[0][1] * dy + s_e[0][2] * dz;
+        float t1 = s_e[1][0] * s_ro[0] + s_e[1][1] * dy + s_e[1][2] * dz;
+        float t2 = s_e[2][0] * s_ro[0] + s_e[2][1] * dy + s_e[2][2] * dz;
         uint64_t word = 0;
-        for (int half = 0; half < 2; ++half) {
-            const int mx = lane + 32 * half;
-            bool solid = false;
-            if (mx < Sd) {
-                const float dx = s_ro[0] + mx, dy = s_ro[1] + my, dz = s_ro[2] + mz;
-                float v = 0.0f;
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const float t = s_e[m][0] * dx + s_e[m][1] * dy + s_e[m][2] * dz;
-                    v += t * t * s_inv[m];
-                }
-                if (fabsf(v - 1.0f) > 1e-4f) {
-                    solid = v < 1.0f;
-                } else {
-                    const int slot = atomicAdd(&s_namb, 1);
-                    if (slot < MAXAMB) s_amb[slot] = (mz << 16) | (my << 8) | mx;
-                }
+        for (int mx = 0; mx < Sd; ++mx) {
+            const float dx = s_ro[0] + mx;
+            // evaluated from dx directly, not accumulated, so rounding does not grow along the row
+            const float u0 = s_e[0][0] * dx + (t0 - s_e[0][0] * s_ro[0]);
+            const float u1 = s_e[1][0] * dx + (t1 - s_e[1][0] * s_ro[0]);
+            const float u2 = s_e[2][0] * dx + (t2 - s_e[2][0] * s_ro[0]);
+            const float v = u0 * u0 * s_inv[0] + u1 * u1 * s_inv[1] + u2 * u2 * s_inv[2];
+            if (fabsf(v - 1.0f) > 1e-4f) {
+                if (v < 1.0f) word |= 1ull << mx;
+            } else {
+                const int slot = atomicAdd(&s_namb, 1);
+                if (slot < MAXAMB) s_amb[slot] = (mz << 16) | (my << 8) | mx;
             }
-            word |= (uint64_t)__ballot_sync(0xffffffffu, solid) << (32 * half);
         }
-        if (lane == 0) s_rows[r] = word;
+        s_rows[r] = word;
     }
     __syncthreads();
     const int namb = s_namb;
@@ -540,10 +546,6 @@ __global__ void __launch_bounds__(CBLOCK) particle_crit_kernel(const PParams P)
         K.B1 = (float)S.B1;
         K.B2 = (float)S.B2;
         K.nsolid = s_nsolid;
-        PartK& G = P.pk[p];
-        K.list = G.list;
-        K.list_count = G.list_count;
-        K.list_cap = G.list_cap;
         if (P.init) {
             K.rows_old = rows_new;
             for (int k = 0; k < 3; ++k) {
@@ -584,12 +586,13 @@ __global__ void __launch_bounds__(CBLOCK) particle_crit_kernel(const PParams P)
                 dm += k.dm_return;
                 ns += k.nsolid;
             }
-            const double nf = (double)(B.N - B.nwall - ns);
-            double g[3] = {B.body[0], B.body[1], B.body[2]};
-            if (B.counter && nf > 0) { g[0] -= fx / nf; g[1] -= fy / nf; g[2] -= fz / nf; }
+            const float nf = (float)(B.N - B.nwall - ns);
+            const float inf = nf > 0.0f ? 1.0f / nf : 0.0f;
             BoxDyn d;
-            d.g[0] = (float)g[0]; d.g[1] = (float)g[1]; d.g[2] = (float)g[2];
-            d.eps = nf > 0 ? (float)(dm / nf) : 0.0f;
+            d.g[0] = (float)B.body[0] - (B.counter ? (float)fx * inf : 0.0f);
+            d.g[1] = (float)B.body[1] - (B.counter ? (float)fy * inf : 0.0f);
+            d.g[2] = (float)B.body[2] - (B.counter ? (float)fz * inf : 0.0f);
+            d.eps = (float)dm * inf;
             P.box_dyn[S.box] = d;
             P.box_done[S.box] = 0;
         }
