@@ -9,12 +9,15 @@
 // block finds its box in a table and starts loading at once.
 //
 // Wall links (solid planes y = 0 and y = ny-1 moving with u_w) are handled
-// here: they are static and row-uniform.  Nodes next to a particle get a
-// provisional value that the boundary kernel overwrites.
+// here: they are static and row-uniform.  Nodes next to a particle's surface
+// (the redo mask of this step) are left to the boundary kernel, which writes
+// them concurrently; a thread tests its row against the cubes of its box's
+// particles, a few integer compares per particle.
 //
-// The grid is persistent (each CTA walks tiles with a grid stride) and a few
-// CTAs short of two per SM, so that SMs keep room for the particle kernels that
-// run concurrently on the particle stream.
+// The grid is persistent: each block (256 threads, half an SM's registers)
+// walks 256-quad tiles with a grid stride.  It has FREE_SLOTS blocks fewer
+// than two per SM, so that about FREE_SLOTS half-SMs stay free for the
+// particle kernels that run concurrently on the particle streams.
 #include "lattice_common.cuh"
 
 namespace lbsph {
@@ -22,18 +25,19 @@ namespace lbsph {
 template <class St, bool FIRST>
 __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile)
 {
+    const int tix = threadIdx.x;
     using T = typename St::T;
     const int bi = __ldg(P.blk_box + tile);
     const BoxDev& B = P.boxes[bi];
     const int nx = B.nx, ny = B.ny, nz = B.nz, nxq = B.nxq;
     const long long N = B.N;
-    long long q = (long long)(tile - B.block_begin) * KBLOCK + threadIdx.x;
+    long long q = (long long)(tile - B.block_begin) * KBLOCK + tix;
     const bool valid = q < B.nq;
     if (!valid) q = B.nq - 1;
     const int xq = (int)(q % nxq);
     const long long row = q / nxq;
     const int y = (int)(row % ny), z = (int)(row / ny);
-    const int lane = threadIdx.x & 31;
+    const int lane = tix & 31;
     const T* A = reinterpret_cast<const T*>(P.src) + B.off;
     T* D = reinterpret_cast<T*>(P.dst) + B.off;
     const float inv = B.inv_scale;
@@ -96,12 +100,46 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile)
 #pragma unroll
         for (int i = 0; i < Q; ++i) set_comp(v[i], k, wallrow ? 0.0f : f[i]);
     }
+    // nodes of this quad that the boundary kernel writes
+    unsigned skip = 0;
+    for (int j = 0; j < B.pcnt; ++j) {
+        const NeedHdr h = P.need_hdr[B.pbeg + j];
+        int dz = z - h.ow[2];
+        if (dz < 0) dz += nz;
+        if (dz >= h.S) continue;
+        int dy = y - h.ow[1];
+        if (dy < 0) dy += ny;
+        if (dy >= h.S) continue;
+        int dx = 4 * xq - h.ow[0];
+        if (dx < 0) dx += nx;
+        if (dx >= h.S && dx + 3 < nx) continue;
+        const uint64_t w = P.need[(size_t)(B.pbeg + j) * (MAXS * MAXS) + dz * h.S + dy];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int mx = dx + k < nx ? dx + k : dx + k - nx;
+            if (mx < h.S && ((w >> mx) & 1ull)) skip |= 1u << k;
+        }
+    }
     if (valid) {
         T* dp = D + own;
+        if (!skip) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) St::st4(dp + (long long)i * N, v[i], B.scale);
+            for (int i = 0; i < Q; ++i) St::st4(dp + (long long)i * N, v[i], B.scale);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if ((skip >> k) & 1u) continue;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) St::st1(dp + (long long)i * N + k, comp(v[i], k), B.scale);
+            }
+        }
     }
 }
+
+#ifndef LBSPH_FREE_SLOTS
+#define LBSPH_FREE_SLOTS 32
+#endif
+constexpr int FREE_SLOTS = LBSPH_FREE_SLOTS;   // half-SMs left to the particle kernels
 
 template <class St, bool FIRST>
 __global__ void __launch_bounds__(KBLOCK, 2) bulk_kernel(const BulkParams P, int tiles)
@@ -117,8 +155,7 @@ static int bulk_grid(int tiles)
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             nsm = 1;
     }
-    // two CTAs per SM fill the registers; leave half of 16 SMs to the particle stream
-    const int g = nsm > 32 ? 2 * nsm - 16 : 2 * nsm;
+    const int g = nsm > FREE_SLOTS ? 2 * nsm - FREE_SLOTS : 2 * nsm;
     return tiles < g ? tiles : g;
 }
 

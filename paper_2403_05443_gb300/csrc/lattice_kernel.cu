@@ -1,27 +1,18 @@
 // Field read-back kernel (lb_get_fields): the pre-collision state of every
-// node, with pull streaming, link bounce-back on moving particle surfaces and
-// walls, and the remap fix-ups of covered / uncovered nodes, all decided per
-// node from the occupancy maps.  It also serves as an independent-layout
-// check of the bulk + boundary kernels that advance the simulation.
-//
-// One launch does, for iteration t of the paper's Appendix, the second half of
-// iteration t-1 (step 2 streaming, step 6 bounce-back with U(t), Omega(t), the
-// remap of step 8) and step 1 of iteration t (collision), so a population is
-// read once and written once per iteration: 2*19*s bytes per node.
+// node of one box at the start of iteration t, i.e. the second half of
+// iteration t-1 of the paper's Appendix (step 2 streaming, step 6 bounce-back
+// with U(t), Omega(t), the remap of step 8) without the collision, with
+// density and velocity moments.  Every decision is taken per node from the
+// occupancy maps, in a layout independent of the bulk + boundary kernels that
+// advance the simulation, so the read-back also cross-checks them.
 //
 // Thread mapping: one thread per 4 consecutive x nodes ("quad"), 256 threads
-// per block, blocks in x-fastest order over each box.  Each direction is read
+// per block, blocks in x-fastest order over the box.  Each direction is read
 // with one 16-byte load of the source row; the +-1 shift in x comes from the
 // neighbouring lane by a warp shuffle (a scalar load at warp and row ends,
-// which also wraps x periodically).
-//
-// Blocks whose tile (grown by one node) does not touch any particle's
-// bounding cube or a wall take the fast path: no per-node tests at all.  The
-// others test each node against the occupancy bitmaps of the particles they
-// touch (old map for the streaming sources, new map for the node itself) and
-// accumulate the momentum-exchange sums of the new links and the remap terms
-// into per-particle int64 fixed-point accumulators (integer atomics: bitwise
-// reproducible).
+// which also wraps x periodically).  Threads whose nodes (grown by one) touch
+// a particle's bounding cube or a wall test them against the occupancy
+// bitmaps (old map for the streaming sources, new map for the node itself).
 #include "lattice_common.cuh"
 
 namespace lbsph {
@@ -87,11 +78,6 @@ __device__ __forceinline__ void slip_f32(const CandK& c, float rx, float ry, flo
     squirmer_slip(c.e_old, c.a, c.eps2, c.B1, c.B2, rx, ry, rz, sx, sy, sz);
 }
 
-__device__ __forceinline__ void sacc_add(long long* a, long long v)
-{
-    if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(v));
-}
-
 // Does the range [lo, hi] of a periodic axis of length L meet [ow, ow+S-1] (mod L)?
 __device__ __forceinline__ bool hits(int lo, int hi, int ow, int S, int L)
 {
@@ -103,38 +89,24 @@ __device__ __forceinline__ bool hits(int lo, int hi, int ow, int S, int L)
 }
 
 // ---------------------------------------------------------------------------
-// PART 0: tiles away from particles and walls only (lean, 2 CTAs per SM);
-// PART 1: the other tiles only; PART 2: every tile (field read-back).
-template <class St, int MODE, int PART>
-__global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(const KParams P)
+template <class St>
+__global__ void __launch_bounds__(KBLOCK) fields_kernel(const KParams P)
 {
     using T = typename St::T;
     __shared__ CandK s_c[MAXC];
-    __shared__ long long s_acc[MAXC][NACC];
-    __shared__ int s_nc, s_slow;
-    __shared__ float s_g[3], s_eps;
+    __shared__ int s_nc;
+    __shared__ float s_g[3];
 
     // ---- box of this block
-    int bi;
-    int blk = blockIdx.x;
-    if (MODE == 2) {
-        bi = P.only_box;
-        blk += P.boxes[bi].block_begin;
-    } else {
-        int lo = 0, hi = P.nbox - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (P.boxes[mid].block_begin <= blk) lo = mid; else hi = mid - 1;
-        }
-        bi = lo;
-    }
+    const int bi = P.only_box;
+    const int blk = blockIdx.x + P.boxes[bi].block_begin;
     const BoxDev& B = P.boxes[bi];
     const int nx = B.nx, ny = B.ny, nz = B.nz, nxq = B.nxq;
     const long long N = B.N;
     const long long q0 = (long long)(blk - B.block_begin) * KBLOCK;
     const long long qlast = min(q0 + KBLOCK, B.nq) - 1;
 
-    // ---- tile classification, box forces (warp 0)
+    // ---- particles near the tile, box forces (warp 0)
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         const long long r0 = q0 / nxq, r1 = qlast / nxq;
@@ -143,7 +115,7 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
         if (z0 == z1) { ylo = y0 - 1; yhi = y1 + 1; } else { ylo = -1; yhi = ny; }
         const int zlo = z0 - 1, zhi = z1 + 1;
         int nc = 0;
-        double fx = 0.0, fy = 0.0, fz = 0.0, dm = 0.0;
+        double fx = 0.0, fy = 0.0, fz = 0.0;
         long long nsol = 0;
         for (int base = 0; base < B.pcnt; base += 32) {
             const int pi = base + lane;
@@ -153,7 +125,6 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
                 hit = (hits(ylo, yhi, k.ow_old[1], k.S, ny) && hits(zlo, zhi, k.ow_old[2], k.S, nz)) ||
                       (hits(ylo, yhi, k.ow_new[1], k.S, ny) && hits(zlo, zhi, k.ow_new[2], k.S, nz));
                 fx += k.Fext[0]; fy += k.Fext[1]; fz += k.Fext[2];
-                dm += k.dm_return;
                 nsol += k.nsolid;
             }
             unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -184,7 +155,6 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
             fx += __shfl_xor_sync(0xffffffffu, fx, o);
             fy += __shfl_xor_sync(0xffffffffu, fy, o);
             fz += __shfl_xor_sync(0xffffffffu, fz, o);
-            dm += __shfl_xor_sync(0xffffffffu, dm, o);
             nsol += __shfl_xor_sync(0xffffffffu, nsol, o);
         }
         if (lane == 0) {
@@ -192,21 +162,12 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
             double g[3] = {B.body[0], B.body[1], B.body[2]};
             if (B.counter && nf > 0) { g[0] -= fx / nf; g[1] -= fy / nf; g[2] -= fz / nf; }
             s_g[0] = (float)g[0]; s_g[1] = (float)g[1]; s_g[2] = (float)g[2];
-            s_eps = (MODE == 2 || nf <= 0) ? 0.0f : (float)(dm / nf);
             s_nc = nc < MAXC ? nc : MAXC;
-            s_slow = (nc > 0) || (B.walls && (ylo <= 0 || yhi >= ny - 1)) || MODE == 2;
         }
     }
     __syncthreads();
-    const bool slow = s_slow != 0;
-    if (PART == 0 && slow) return;
-    if (PART == 1 && !slow) return;
     const int nc = s_nc;
-    const float gx = s_g[0], gy = s_g[1], gz = s_g[2], eps = s_eps;
-    if (slow && MODE != 2) {
-        for (int e = threadIdx.x; e < MAXC * NACC; e += KBLOCK) (&s_acc[0][0])[e] = 0;
-        __syncthreads();
-    }
+    const float gx = s_g[0], gy = s_g[1], gz = s_g[2];
 
     // ---- this thread's quad
     long long q = q0 + threadIdx.x;
@@ -217,8 +178,7 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
     const int y = (int)(row % ny), z = (int)(row / ny);
     const int lane = threadIdx.x & 31;
     const T* A = reinterpret_cast<const T*>(P.src) + B.off;
-    T* D = reinterpret_cast<T*>(P.dst) + B.off;
-    const float inv = B.inv_scale, scl = B.scale;
+    const float inv = B.inv_scale;
 
     long long rofs[3][3];  // element offset of source rows (y + dy, z + dz), wrapped
     {
@@ -233,7 +193,7 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
     const bool right_ld = (lane == 31) || (xq == nxq - 1);
 
     // ---- pull (stream): v[i] = f*_i(x - c_i) for the 4 nodes
-    const bool first = (MODE == 0) || (MODE == 2 && P.nopull);
+    const bool first = P.nopull != 0;
     float4 v[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -255,28 +215,9 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
         v[i] = t;
     }
 
-    if (!slow) {
-        // ---- fast path: plain fluid, periodic neighbours
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float f[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = comp(v[i], k);
-            collide19(f, B.omega, B.rho0f, gx, gy, gz, eps);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) set_comp(v[i], k, f[i]);
-        }
-        if (valid) {
-            T* dp = D + row * nx + 4 * xq;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) St::st4(dp + (long long)i * N, v[i], scl);
-        }
-        return;
-    }
-
-    // ---- slow block: only threads whose nodes (grown by one) touch a particle
-    // cube or a wall do per-node work; they read the neighbourhood occupancy
-    // as 6-bit windows of the 9 rows (y + dy, z + dz).
+    // ---- only threads whose nodes (grown by one) touch a particle cube or a
+    // wall test nodes; they read the neighbourhood occupancy as 6-bit windows
+    // of the 9 rows (y + dy, z + dz)
     bool near = B.walls && (y <= 1 || y >= ny - 2);
     for (int c = 0; c < nc; ++c) {
         const CandK& C = s_c[c];
@@ -290,17 +231,6 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
     const float rho0 = B.rho0f;
     float rho_out[4], u_out[4][3];
     int solid_out[4];
-    if (!near && MODE != 2) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float f[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = comp(v[i], k);
-            collide19(f, B.omega, rho0, gx, gy, gz, eps);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) set_comp(v[i], k, f[i]);
-        }
-    } else {
     unsigned so[3][3], sn[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -352,13 +282,6 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
                 const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
                 f[i] = w_of(i) * rho0 * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
             }
-            if (MODE == 1 && c0 >= 0 && valid) {
-                long long* a = s_acc[c0] + ACC_UNC;
-                sacc_add(a + 0, 1);
-                sacc_add(a + 1, ax); sacc_add(a + 2, ay); sacc_add(a + 3, az);
-                sacc_add(a + 4, ax * ax); sacc_add(a + 5, ax * ay); sacc_add(a + 6, ax * az);
-                sacc_add(a + 7, ay * ay); sacc_add(a + 8, ay * az); sacc_add(a + 9, az * az);
-            }
         } else {
             // fluid at t-1: pulled populations, bounce-back where the source was solid
 #pragma unroll
@@ -399,22 +322,6 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
                 skip = true;
                 const int c = lookup(s_c, nc, false, X, y, z, nx, ny, nz, mx, my, mz);
                 solid_out[k] = c >= 0 ? s_c[c].gidx - B.pbeg + 1 : 0;
-                if (MODE == 1 && c >= 0 && valid) {
-                    float drho = 0.f;
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) drho += f[i];
-                    const float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
-                    const float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
-                    const float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
-                    const long long Jx = fixp(jx), Jy = fixp(jy), Jz = fixp(jz);
-                    long long* a = s_acc[c] + ACC_COV;
-                    sacc_add(a + 0, 1);
-                    sacc_add(a + 1, fixp(drho));
-                    sacc_add(a + 2, Jx); sacc_add(a + 3, Jy); sacc_add(a + 4, Jz);
-                    sacc_add(a + 5, my * Jz - mz * Jy);
-                    sacc_add(a + 6, mz * Jx - mx * Jz);
-                    sacc_add(a + 7, mx * Jy - my * Jx);
-                }
             }
         }
         if (skip) {
@@ -422,76 +329,35 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
             for (int i = 0; i < Q; ++i) set_comp(v[i], k, 0.0f);
             continue;
         }
-        if (MODE == 2) {
-            float drho = 0.f;
+        float drho = 0.f;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) drho += f[i];
-            const float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
-            const float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
-            const float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
-            const float ir = 1.0f / (rho0 + drho);
-            rho_out[k] = drho;
-            u_out[k][0] = (jx + 0.5f * gx) * ir;
-            u_out[k][1] = (jy + 0.5f * gy) * ir;
-            u_out[k][2] = (jz + 0.5f * gz) * ir;
+        for (int i = 0; i < Q; ++i) drho += f[i];
+        const float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
+        const float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
+        const float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
+        const float ir = 1.0f / (rho0 + drho);
+        rho_out[k] = drho;
+        u_out[k][0] = (jx + 0.5f * gx) * ir;
+        u_out[k][1] = (jy + 0.5f * gy) * ir;
+        u_out[k][2] = (jz + 0.5f * gz) * ir;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) set_comp(v[i], k, P.out_dev ? f[i] : f[i] + w_of(i) * rho0);
-            continue;
-        }
-        collide19(f, B.omega, rho0, gx, gy, gz, eps);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) set_comp(v[i], k, f[i]);
-        // momentum-exchange sums of the links (x, b) of map t, with f*(t)
-        if (near) {
-#pragma unroll
-            for (int b = 1; b < Q; ++b) {
-                if (!((sn[1 + cy_of(b)][1 + cz_of(b)] >> (k + 1 + cx_of(b))) & 1u)) continue;
-                int sx, sy, sz;
-                const int c = lookup(s_c, nc, false, wrapd(X + cx_of(b), nx), wrapd(y + cy_of(b), ny),
-                                     wrapd(z + cz_of(b), nz), nx, ny, nz, sx, sy, sz);
-                if (c < 0) continue;
-                const CandK& C = s_c[c];
-                const int mx2 = wrapd(X - C.ow_new[0], nx), my2 = wrapd(y - C.ow_new[1], ny), mz2 = wrapd(z - C.ow_new[2], nz);
-                const long long d = fixp(f[b]);
-                long long* a = s_acc[c] + ACC_LINK + 4 * b;
-                sacc_add(a + 0, d);
-                sacc_add(a + 1, d * mx2);
-                sacc_add(a + 2, d * my2);
-                sacc_add(a + 3, d * mz2);
-            }
-        }
-    }
+        for (int i = 0; i < Q; ++i) set_comp(v[i], k, P.out_dev ? f[i] : f[i] + w_of(i) * rho0);
     }
 
-    if (MODE == 2) {
-        if (valid) {
-            if (P.out_f) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    *reinterpret_cast<float4*>(P.out_f + (long long)i * N + own) = v[i];
-            }
-            if (P.out_rho) *reinterpret_cast<float4*>(P.out_rho + own) = make_float4(rho_out[0], rho_out[1], rho_out[2], rho_out[3]);
-            if (P.out_u) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    *reinterpret_cast<float4*>(P.out_u + (long long)a * N + own) =
-                        make_float4(u_out[0][a], u_out[1][a], u_out[2][a], u_out[3][a]);
-            }
-            if (P.out_solid) *reinterpret_cast<int4*>(P.out_solid + own) = make_int4(solid_out[0], solid_out[1], solid_out[2], solid_out[3]);
-        }
-        return;
-    }
     if (valid) {
-        T* dp = D + own;
+        if (P.out_f) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) St::st4(dp + (long long)i * N, v[i], scl);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nc * NACC; e += KBLOCK) {
-        const int c = e / NACC, j = e % NACC;
-        const long long val = s_acc[c][j];
-        if (val != 0)
-            atomicAdd(reinterpret_cast<unsigned long long*>(P.pk[s_c[c].gidx].acc + j), static_cast<unsigned long long>(val));
+            for (int i = 0; i < Q; ++i)
+                *reinterpret_cast<float4*>(P.out_f + (long long)i * N + own) = v[i];
+        }
+        if (P.out_rho) *reinterpret_cast<float4*>(P.out_rho + own) = make_float4(rho_out[0], rho_out[1], rho_out[2], rho_out[3]);
+        if (P.out_u) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                *reinterpret_cast<float4*>(P.out_u + (long long)a * N + own) =
+                    make_float4(u_out[0][a], u_out[1][a], u_out[2][a], u_out[3][a]);
+        }
+        if (P.out_solid) *reinterpret_cast<int4*>(P.out_solid + own) = make_int4(solid_out[0], solid_out[1], solid_out[2], solid_out[3]);
     }
 }
 
@@ -502,7 +368,7 @@ __global__ void __launch_bounds__(KBLOCK, PART == 0 ? 2 : 1) lattice_kernel(cons
 template <class St>
 static cudaError_t launch_mode(const KParams& p, int blocks, cudaStream_t s)
 {
-    lattice_kernel<St, 2, 2><<<blocks, KBLOCK, 0, s>>>(p);
+    fields_kernel<St><<<blocks, KBLOCK, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -1,13 +1,16 @@
 // Host runtime behind the C ABI of include/lbsph.h.
 //
-// One iteration is five kernels on two streams.  The caller's stream runs the
-// bulk kernel (every node) and the scatter kernel (boundary nodes into the
-// lattice); a high-priority particle stream runs, while the bulk kernel
-// streams the lattice, the boundary kernel, the critical particle kernel
-// (solve, pose, new occupancy, box forces for the next step) and the auxiliary
-// one (link moments, drag matrices, next boundary list).  Events order them:
-// bulk(t) waits for critical(t-1) (box forces), boundary(t) for scatter(t-1)
-// (complete lattice), scatter(t) for boundary(t).  Chunks of iterations are captured
+// One iteration is four kernels on three streams.  The caller's stream runs
+// the bulk kernel (every node but those next to a particle's surface).  While
+// it streams the lattice, a high-priority particle stream runs the boundary
+// kernel (the nodes the bulk kernel skips, written into the same lattice
+// buffer) and the critical particle kernel (solve, pose, new occupancy, redo
+// masks and box forces for the next step), and a third stream the auxiliary
+// particle kernel (drag matrices and the inverse of the next solve), which
+// overlaps the next boundary kernel.  Events order them: bulk(t) waits for
+// critical(t-1) (box forces, redo masks), boundary(t) for bulk(t-1) (complete
+// lattice; boundary(t-1) precedes it on its stream), auxiliary(t) for
+// critical(t), critical(t+1) for auxiliary(t).  Chunks of iterations are captured
 // once into a CUDA graph per buffer parity and replayed, so a long run costs
 // one graph launch per chunk and no host synchronisation.
 #include <cmath>
@@ -23,8 +26,7 @@
 namespace lbsph {
 cudaError_t launch_fields(const KParams& p, int precision, int blocks, cudaStream_t s);
 cudaError_t launch_bulk(const BulkParams& p, int precision, int blocks, cudaStream_t s);
-cudaError_t launch_boundary(const BndParams& p, int precision, int list_cap, int np, cudaStream_t s);
-cudaError_t launch_scatter(const BndParams& p, int precision, int list_cap, int np, cudaStream_t s);
+cudaError_t launch_boundary(const BndParams& p, int precision, int np, cudaStream_t s);
 cudaError_t launch_particles(const PParams& p, cudaStream_t s);
 cudaError_t launch_particles_aux(const PParams& p, cudaStream_t s);
 cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
@@ -69,16 +71,16 @@ struct lb_ctx {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaStream_t last_user_stream = nullptr;        // last stream lb_step ran on
     cudaStream_t aux = nullptr;                     // the particle stream
-    cudaEvent_t ev_crit = nullptr, ev_aux = nullptr, ev_fork = nullptr, ev_bnd = nullptr;
-    float* d_side_val = nullptr;
-    int* d_side_idx = nullptr;
-    int* d_side_count = nullptr;
+    cudaStream_t aux2 = nullptr;                    // the auxiliary kernel's stream
+    cudaEvent_t ev_crit = nullptr, ev_aux = nullptr, ev_fork = nullptr;
+    NeedHdr* d_need_hdr = nullptr;     // [2][maxp]: redo masks, one slot per buffer parity
+    uint64_t* d_need = nullptr;        // [2][maxp][MAXS*MAXS]
     int* d_blk_box = nullptr;
-    BoxDyn* d_box_dyn = nullptr;
+    BoxDyn* d_box_dyn = nullptr;       // [2][nbox]: one slot per buffer parity
+    BoxDyn* d_pdyn = nullptr;          // [2][maxp]: the same per particle
     int* d_box_done = nullptr;
-    unsigned* d_lists = nullptr;
-    int* d_list_count = nullptr;
-    int list_cap = 0;
+    int list_cap = 0;                  // node list entries per boundary block
+    int gx = 1;                        // boundary blocks per particle
     std::string err;
     std::vector<void*> allocs;
 };
@@ -201,10 +203,10 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->aux2, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_crit, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_aux, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_bnd, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
         delete ctx;
         return LB_ECUDA;
     }
@@ -258,26 +260,29 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     ctx->d_count = (int*)dev_alloc(ctx, sizeof(int) * 4);
     ctx->d_blk_box = (int*)dev_alloc(ctx, sizeof(int) * (size_t)blk);
     ctx->d_box_dyn = (BoxDyn*)dev_alloc(ctx, sizeof(BoxDyn) * 2 * nbox);   // one slot per buffer parity
+    ctx->d_pdyn = (BoxDyn*)dev_alloc(ctx, sizeof(BoxDyn) * 2 * ctx->maxp);
     ctx->d_box_done = (int*)dev_alloc(ctx, sizeof(int) * nbox);
     {
+        // block c of a particle takes the cube rows c, c + gx, ... (at most
+        // BBLOCK of them); the boundary nodes of a spheroid filling its cube
+        // number about 2-3 Smax^2, split evenly over the gx blocks
         const long long Smax = 2ll * (o.max_semi + CUBE_MARGIN) + 2;
-        ctx->list_cap = (int)std::min(Smax * Smax * Smax, 16 * Smax * Smax);
+        ctx->gx = (int)std::max(1ll, (3 * Smax * Smax + BBLOCK - 1) / BBLOCK);
+        const long long total = std::min(Smax * Smax * Smax, 16 * Smax * Smax);
+        ctx->list_cap = (int)((total + ctx->gx - 1) / ctx->gx);
     }
-    ctx->d_lists = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * (size_t)ctx->list_cap * ctx->maxp);
-    ctx->d_list_count = (int*)dev_alloc(ctx, sizeof(int) * ctx->maxp);
-    ctx->d_side_val = (float*)dev_alloc(ctx, sizeof(float) * Q * (size_t)ctx->list_cap * ctx->maxp);
-    ctx->d_side_idx = (int*)dev_alloc(ctx, sizeof(int) * (size_t)ctx->list_cap * ctx->maxp);
-    ctx->d_side_count = (int*)dev_alloc(ctx, sizeof(int) * ctx->maxp);
+    ctx->d_need_hdr = (NeedHdr*)dev_alloc(ctx, sizeof(NeedHdr) * 2 * (size_t)ctx->maxp);
+    ctx->d_need = (uint64_t*)dev_alloc(ctx, sizeof(uint64_t) * 2 * (size_t)MAXS * MAXS * ctx->maxp);
     for (void* p : {ctx->fbuf[0], ctx->fbuf[1], (void*)ctx->d_boxes, (void*)ctx->d_pd, (void*)ctx->d_pk,
                     (void*)ctx->d_acc, (void*)ctx->d_rows, (void*)ctx->d_status, (void*)ctx->d_count,
-                    (void*)ctx->d_blk_box, (void*)ctx->d_box_dyn, (void*)ctx->d_box_done, (void*)ctx->d_lists,
-                    (void*)ctx->d_list_count, (void*)ctx->d_side_val, (void*)ctx->d_side_idx,
-                    (void*)ctx->d_side_count})
+                    (void*)ctx->d_blk_box, (void*)ctx->d_box_dyn, (void*)ctx->d_pdyn, (void*)ctx->d_box_done,
+                    (void*)ctx->d_need_hdr, (void*)ctx->d_need})
         okm = okm && p;
     if (!okm) {
         free_all(ctx);
         cudaStreamDestroy(ctx->stream);
         cudaStreamDestroy(ctx->aux);
+        cudaStreamDestroy(ctx->aux2);
         delete ctx;
         return LB_ENOMEM;
     }
@@ -299,13 +304,14 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     err = err ? err : cudaMemcpyAsync(ctx->d_blk_box, blk_box.data(), sizeof(int) * blk, cudaMemcpyHostToDevice, ctx->stream);
     err = err ? err : cudaMemcpyAsync(ctx->d_box_dyn, dyn.data(), sizeof(BoxDyn) * 2 * nbox, cudaMemcpyHostToDevice, ctx->stream);
     err = err ? err : cudaMemsetAsync(ctx->d_box_done, 0, sizeof(int) * nbox, ctx->stream);
-    err = err ? err : cudaMemsetAsync(ctx->d_list_count, 0, sizeof(int) * ctx->maxp, ctx->stream);
-    err = err ? err : cudaMemsetAsync(ctx->d_side_count, 0, sizeof(int) * ctx->maxp, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_need_hdr, 0, sizeof(NeedHdr) * 2 * (size_t)ctx->maxp, ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_need, 0, sizeof(uint64_t) * 2 * (size_t)MAXS * MAXS * ctx->maxp, ctx->stream);
     err = err ? err : cudaStreamSynchronize(ctx->stream);
     if (err != cudaSuccess) {
         free_all(ctx);
         cudaStreamDestroy(ctx->stream);
         cudaStreamDestroy(ctx->aux);
+        cudaStreamDestroy(ctx->aux2);
         delete ctx;
         return LB_ECUDA;
     }
@@ -329,10 +335,10 @@ extern "C" lb_status lb_destroy(lb_ctx* ctx)
     free_all(ctx);
     cudaStreamDestroy(ctx->stream);
     cudaStreamDestroy(ctx->aux);
+    cudaStreamDestroy(ctx->aux2);
     cudaEventDestroy(ctx->ev_crit);
     cudaEventDestroy(ctx->ev_aux);
     cudaEventDestroy(ctx->ev_fork);
-    cudaEventDestroy(ctx->ev_bnd);
     delete ctx;
     return LB_OK;
 }
@@ -344,7 +350,10 @@ static PParams particle_params(lb_ctx* ctx, int cur)
     PParams pp{};
     pp.pd = ctx->d_pd; pp.pk = ctx->d_pk; pp.acc = ctx->d_acc; pp.rows = ctx->d_rows;
     pp.boxes = ctx->d_boxes; pp.box_dyn = ctx->d_box_dyn + (size_t)(cur ^ 1) * ctx->desc.size();
+    pp.pdyn = ctx->d_pdyn + (size_t)(cur ^ 1) * ctx->maxp;
     pp.box_done = ctx->d_box_done;
+    pp.need_hdr = ctx->d_need_hdr + (size_t)(cur ^ 1) * ctx->maxp;
+    pp.need = ctx->d_need + (size_t)(cur ^ 1) * MAXS * MAXS * ctx->maxp;
     pp.status = ctx->d_status; pp.np = ctx->np; pp.init = 0;
     pp.didt_mode = ctx->opt.didt_mode;
     pp.smax = 2 * (ctx->opt.max_semi + CUBE_MARGIN) + 2;
@@ -434,25 +443,44 @@ extern "C" lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particl
     CK(cudaSetDevice(ctx->device));
     if (idx > 0) CK(cudaMemcpyAsync(ctx->d_pd, pd.data(), sizeof(PartDev) * idx, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_boxes, ctx->hbox.data(), sizeof(BoxDev) * ctx->hbox.size(), cudaMemcpyHostToDevice, ctx->stream));
+    // the snapshot's constant fields: squirmer parameters and the particle's box
     {
         std::vector<PartK> pk(ctx->maxp);
         std::memset(pk.data(), 0, sizeof(PartK) * pk.size());
-        for (int i = 0; i < ctx->maxp; ++i) {
-            pk[i].list = ctx->d_lists + (size_t)i * ctx->list_cap;
-            pk[i].list_count = ctx->d_list_count + i;
-            pk[i].list_cap = ctx->list_cap;
-            pk[i].side_val = ctx->d_side_val + (size_t)i * ctx->list_cap * Q;
-            pk[i].side_idx = ctx->d_side_idx + (size_t)i * ctx->list_cap;
-            pk[i].side_count = ctx->d_side_count + i;
+        for (int i = 0; i < idx; ++i) {
+            const PartDev& s = pd[i];
+            const BoxDev& h = ctx->hbox[s.box];
+            PartK& k = pk[i];
+            k.box = s.box;
+            k.a = (float)s.semi[0];
+            k.b = (float)s.semi[1];
+            k.eps2 = (float)std::fmax(0.0, 1.0 - (s.semi[1] * s.semi[1]) / (s.semi[0] * s.semi[0]));
+            k.B1 = (float)s.B1;
+            k.B2 = (float)s.B2;
+            k.squirmer = (s.B1 != 0.0 || s.B2 != 0.0) ? 1 : 0;
+            k.N = h.N; k.off = h.off; k.nwall = h.nwall; k.rho0 = h.rho0;
+            k.nx = h.nx; k.ny = h.ny; k.nz = h.nz; k.walls = h.walls;
+            k.omega = h.omega; k.rho0f = h.rho0f; k.scale = h.scale; k.inv_scale = h.inv_scale;
+            for (int a = 0; a < 3; ++a) {
+                k.uw_lo[a] = h.uw_lo[a]; k.uw_hi[a] = h.uw_hi[a];
+                k.body[a] = (float)h.body[a];
+            }
+            k.counter = h.counter;
+            k.pbeg = h.pbeg; k.pcnt = h.pcnt;
         }
         CK(cudaMemcpyAsync(ctx->d_pk, pk.data(), sizeof(PartK) * ctx->maxp, cudaMemcpyHostToDevice, ctx->stream));
         const size_t nb = ctx->desc.size();
-        std::vector<BoxDyn> dyn(2 * nb);
+        std::vector<BoxDyn> dyn(2 * nb), pdyn(2 * (size_t)ctx->maxp);
         for (size_t b = 0; b < nb; ++b) {
             for (int k = 0; k < 3; ++k) dyn[b].g[k] = dyn[nb + b].g[k] = (float)ctx->desc[b].body_force[k];
             dyn[b].eps = dyn[nb + b].eps = 0.0f;
         }
+        for (int i = 0; i < idx; ++i) pdyn[i] = pdyn[ctx->maxp + i] = dyn[pd[i].box];
         CK(cudaMemcpyAsync(ctx->d_box_dyn, dyn.data(), sizeof(BoxDyn) * dyn.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_pdyn, pdyn.data(), sizeof(BoxDyn) * pdyn.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemsetAsync(ctx->d_box_done, 0, sizeof(int) * nb, ctx->stream));
+        CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(long long) * NACC * ctx->maxp, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));     // the host vectors above go out of scope
     }
     clear_stale_error();
     // the initial state serves the first iteration, which reads parity ctx->cur
@@ -484,19 +512,18 @@ extern "C" lb_status lb_set_external(lb_ctx* ctx, int32_t box, const double* ft,
     return LB_OK;
 }
 
-static KParams base_kparams(lb_ctx* ctx, int mode)
+static KParams base_kparams(lb_ctx* ctx)
 {
     KParams k{};
     k.boxes = ctx->d_boxes;
     k.nbox = (int)ctx->hbox.size();
     k.pk = ctx->d_pk;
     k.status = ctx->d_status;
-    k.mode = mode;
     return k;
 }
 
 struct IterEvents {
-    cudaEvent_t fork, bnd, crit, aux;   // fork: lattice of t-1 complete; crit: box forces of t ready
+    cudaEvent_t fork, crit, aux;        // fork: bulk part of lattice t-1 complete; crit: box forces of t ready
 };
 
 static BulkParams bulk_params(lb_ctx* ctx, int first, int cur)
@@ -504,6 +531,8 @@ static BulkParams bulk_params(lb_ctx* ctx, int first, int cur)
     BulkParams bp{};
     bp.boxes = ctx->d_boxes; bp.blk_box = ctx->d_blk_box;
     bp.box_dyn = ctx->d_box_dyn + (size_t)cur * ctx->desc.size();
+    bp.need_hdr = ctx->d_need_hdr + (size_t)cur * ctx->maxp;
+    bp.need = ctx->d_need + (size_t)cur * MAXS * MAXS * ctx->maxp;
     bp.src = ctx->fbuf[cur]; bp.dst = ctx->fbuf[cur ^ 1]; bp.first = first;
     return bp;
 }
@@ -511,9 +540,14 @@ static BulkParams bulk_params(lb_ctx* ctx, int first, int cur)
 static BndParams bnd_params(lb_ctx* ctx, int first, int cur)
 {
     BndParams np{};
-    np.boxes = ctx->d_boxes; np.box_dyn = ctx->d_box_dyn + (size_t)cur * ctx->desc.size(); np.pk = ctx->d_pk;
-    np.src = ctx->fbuf[cur]; np.dst = ctx->fbuf[cur ^ 1]; np.first = first;
+    np.pdyn = ctx->d_pdyn + (size_t)cur * ctx->maxp;
+    np.pk = ctx->d_pk; np.acc = ctx->d_acc; np.rows = ctx->d_rows;
+    np.need = ctx->d_need + (size_t)cur * MAXS * MAXS * ctx->maxp;
+    np.status = ctx->d_status;
+    np.src = ctx->fbuf[cur]; np.dst = ctx->fbuf[cur ^ 1];
+    np.list_cap = ctx->list_cap; np.first = first;
     np.smax = 2 * (ctx->opt.max_semi + CUBE_MARGIN) + 2;
+    np.gx = ctx->gx;
     return np;
 }
 
@@ -528,19 +562,18 @@ static cudaError_t enqueue_iteration(lb_ctx* ctx, int first, int cur, cudaStream
     if ((e = launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s)) != cudaSuccess) return e;
     const BndParams np = bnd_params(ctx, first, cur);
     const PParams pp = particle_params(ctx, cur);
-    cudaStream_t t = ctx->aux;
+    cudaStream_t t = ctx->aux, a = ctx->aux2;
     if ((e = cudaStreamWaitEvent(t, ev.fork, 0)) != cudaSuccess) return e;
-    if ((e = launch_boundary(np, ctx->opt.precision, ctx->list_cap, ctx->np, t)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(ev.bnd, t)) != cudaSuccess) return e;
+    if ((e = launch_boundary(np, ctx->opt.precision, ctx->np, t)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(t, ev.aux, 0)) != cudaSuccess) return e;       // inverse and drag of t
     if ((e = launch_particles(pp, t)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(ev.crit, t)) != cudaSuccess) return e;
-    if ((e = launch_particles_aux(pp, t)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(ev.aux, t)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(s, ev.bnd, 0)) != cudaSuccess) return e;
-    return launch_scatter(np, ctx->opt.precision, ctx->list_cap, ctx->np, s);
+    if ((e = cudaStreamWaitEvent(a, ev.crit, 0)) != cudaSuccess) return e;
+    if ((e = launch_particles_aux(pp, a)) != cudaSuccess) return e;
+    return cudaEventRecord(ev.aux, a);
 }
 
-static IterEvents ctx_events(lb_ctx* ctx) { return IterEvents{ctx->ev_fork, ctx->ev_bnd, ctx->ev_crit, ctx->ev_aux}; }
+static IterEvents ctx_events(lb_ctx* ctx) { return IterEvents{ctx->ev_fork, ctx->ev_crit, ctx->ev_aux}; }
 
 // The graph gets its own events: an event last recorded inside a capture
 // cannot be waited on outside it.
@@ -549,25 +582,27 @@ static lb_status build_graph(lb_ctx* ctx, int parity)
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
-    cudaEvent_t evs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t evs[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaError_t e = cudaSuccess;
     for (auto& ev : evs)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     const bool capturing = e == cudaSuccess;
-    const IterEvents ev{evs[0], evs[1], evs[2], evs[3]};
-    // the particle stream joins the capture; box forces and list of the first
-    // captured iteration are ready when the graph starts
-    if (e == cudaSuccess) e = cudaEventRecord(evs[4], cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, evs[4], 0);
+    const IterEvents ev{evs[0], evs[1], evs[2]};
+    // the particle streams join the capture; box forces and solve data of the
+    // first captured iteration are ready when the graph starts
+    if (e == cudaSuccess) e = cudaEventRecord(evs[3], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, evs[3], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux2, evs[3], 0);
     if (e == cudaSuccess) e = cudaEventRecord(ev.crit, ctx->aux);
-    if (e == cudaSuccess) e = cudaEventRecord(ev.aux, ctx->aux);
+    if (e == cudaSuccess) e = cudaEventRecord(ev.aux, ctx->aux2);
     int c = parity;
     for (int i = 0; e == cudaSuccess && i < GRAPH_ITERS; ++i) {
         e = enqueue_iteration(ctx, 0, c, cs, ev);
         c ^= 1;
     }
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev.aux, 0);   // join the particle stream
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev.aux, 0);   // join the particle streams
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev.crit, 0);
     if (capturing) {
         const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
@@ -629,6 +664,7 @@ extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
         ctx->cur ^= 1;
     }
     CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));      // everything ordered on the caller's stream
+    CK(cudaStreamWaitEvent(s, ctx->ev_crit, 0));
     return LB_OK;
 }
 
@@ -643,9 +679,9 @@ extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, 
     ctx->stepped = true;
     CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
     CK(cudaStreamWaitEvent(s, ctx->ev_crit, 0));
-    cudaEvent_t ev[6];
+    cudaEvent_t ev[5];
     for (auto& e : ev) CK(cudaEventCreate(&e));
-    double t[5] = {0, 0, 0, 0, 0};
+    double t[4] = {0, 0, 0, 0};
     for (int i = 0; i < nsteps; ++i) {
         const int first = ctx->collided ? 0 : 1;
         const BulkParams bp = bulk_params(ctx, first, ctx->cur);
@@ -654,16 +690,14 @@ extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, 
         CK(cudaEventRecord(ev[0], s));
         CK(launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s));
         CK(cudaEventRecord(ev[1], s));
-        CK(launch_boundary(np, ctx->opt.precision, ctx->list_cap, ctx->np, s));
+        CK(launch_boundary(np, ctx->opt.precision, ctx->np, s));
         CK(cudaEventRecord(ev[2], s));
-        CK(launch_scatter(np, ctx->opt.precision, ctx->list_cap, ctx->np, s));
-        CK(cudaEventRecord(ev[3], s));
         CK(launch_particles(pp, s));
-        CK(cudaEventRecord(ev[4], s));
+        CK(cudaEventRecord(ev[3], s));
         CK(launch_particles_aux(pp, s));
-        CK(cudaEventRecord(ev[5], s));
-        CK(cudaEventSynchronize(ev[5]));
-        for (int k = 0; k < 5; ++k) {
+        CK(cudaEventRecord(ev[4], s));
+        CK(cudaEventSynchronize(ev[4]));
+        for (int k = 0; k < 4; ++k) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
             t[k] += ms;
@@ -675,9 +709,9 @@ extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, 
     CK(cudaEventRecord(ctx->ev_crit, s));
     for (auto& e : ev) cudaEventDestroy(e);
     ms_out[0] = t[0];            // bulk
-    ms_out[1] = t[1] + t[2];     // boundary + scatter
-    ms_out[2] = t[3];            // particle critical
-    ms_out[3] = t[4];            // particle auxiliary
+    ms_out[1] = t[1];            // boundary
+    ms_out[2] = t[2];            // particle critical
+    ms_out[3] = t[3];            // particle auxiliary
     return read_status(ctx);
 }
 
@@ -711,9 +745,8 @@ extern "C" lb_status lb_get_fields(lb_ctx* ctx, int32_t box, uint32_t what, void
         if (!ctx->d_tmp) return fail(ctx, LB_ENOMEM, "field staging buffer");
     }
     float* out = direct ? (float*)dst : ctx->d_tmp;
-    KParams k = base_kparams(ctx, 2);
+    KParams k = base_kparams(ctx);
     k.src = ctx->fbuf[ctx->cur];
-    k.dst = nullptr;
     k.only_box = box;
     k.nopull = ctx->collided ? 0 : 1;
     k.out_dev = (what == LB_FIELD_DF) ? 1 : 0;

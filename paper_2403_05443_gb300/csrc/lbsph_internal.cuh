@@ -1,19 +1,23 @@
 // Internal definitions shared by the CUDA translation units of liblbsph.
 //
-// One iteration t of the paper's Appendix is five kernels on two streams:
+// One iteration t of the paper's Appendix is four kernels on three streams:
 //   main stream
-//     bulk      every node: pull streaming + BGK/Guo collision, wall links inline
-//               (the only kernel that moves the whole lattice: 2*19*s bytes/node);
-//     scatter   copies the boundary kernel's nodes into the lattice;
+//     bulk      every node except those next to a particle's surface: pull
+//               streaming + BGK/Guo collision, wall links inline (the only
+//               kernel that moves the whole lattice: 2*19*s bytes/node);
 //   particle stream (runs while the bulk kernel streams the lattice)
-//     boundary  the listed nodes next to a particle's old or new surface, redone
-//               with link bounce-back (Eq. fb, Eq. ub), the remap of covered /
-//               uncovered nodes and the momentum-exchange sums of the new links,
-//               into a side buffer;
-//     particle  (critical) force, implicit solve, pose and quaternion update, the
-//               new occupancy map and the box's uniform forces for the next step;
-//     particle  (auxiliary) link moments, drag matrices (Eq. drag1-drag4) and the
-//               next boundary list.
+//     boundary  the nodes next to a particle's old or new surface, with link
+//               bounce-back (Eq. fb, Eq. ub), the remap of covered / uncovered
+//               nodes and the momentum-exchange sums of the new links, written
+//               straight into the lattice (the bulk kernel skips them);
+//     particle  (critical) force, implicit solve with the inverse prepared by
+//               the auxiliary kernel, pose and quaternion update, the new
+//               occupancy map, the nodes both lattice kernels split at t+1 and
+//               the box's uniform forces for the next step;
+//   auxiliary stream (overlaps the next boundary kernel)
+//     particle  (auxiliary) integer link sums of the new map, drag matrices (Eq.
+//               drag1-drag4), the inverse of the next implicit solve and the
+//               geometric parts of F0 / T0.
 //
 // Data layout in HBM (one allocation per buffer, every box back to back):
 //   distributions  two buffers (ping-pong), each box b holds 19 planes of
@@ -24,12 +28,15 @@
 //                  (side S <= 64): one 64-bit word per (y, z) row, bit x set
 //                  when the node is inside the particle (Eq. ellipsoidsurface).
 //                  Boundary links are implicit: (x fluid, x + c_b solid).
-//   particle state PartDev (FP64, owned by the particle kernel) and PartK (the
-//                  FP32 snapshot the lattice kernel reads).
+//   redo masks     per particle and buffer parity, the nodes the boundary
+//                  kernel takes over at one step: one 64-bit word per row of
+//                  the particle's current cube, with the cube in a NeedHdr.
+//   particle state PartDev (FP64, owned by the particle kernels) and PartK (the
+//                  FP32 snapshot the lattice kernels read).
 //   accumulators   per particle NACC int64 fixed-point sums filled by the
-//                  lattice kernel with integer atomics (order independent, so
+//                  boundary kernel with integer atomics (order independent, so
 //                  every run is bitwise reproducible) and drained by the
-//                  particle kernel.
+//                  critical particle kernel.
 #pragma once
 
 #include <cstdint>
@@ -40,17 +47,20 @@ namespace lbsph {
 constexpr int Q = 19;
 constexpr int MAXS = 64;            // largest bounding-cube side (one 64-bit word per row)
 constexpr int KBLOCK = 256;         // threads per block of the lattice kernel
-constexpr int PBLOCK = 512;         // threads per block of the particle kernel
+constexpr int PBLOCK = 512;         // threads per block of the links read-back kernels
+constexpr int ABLOCK = 256;         // threads per block of the auxiliary particle kernel
 constexpr int MAXC = 4;             // particles a lattice tile may touch (field read-back)
 constexpr int BBLOCK = 128;         // threads per block of the boundary kernel
-constexpr int CBLOCK = 256;         // threads per block of the critical particle kernel
+constexpr int CBLOCK = 512;         // threads per block of the critical particle kernel
 constexpr int MAXAMB = 512;         // near-surface nodes settled by the exact FP64 test per step
 
-// accumulator layout (int64 per particle)
-constexpr int ACC_LINK = 0;         // [b*4 + {0: sum df*, 1..3: sum df* m}], b = 0..18
-constexpr int ACC_COV = 76;         // n, sum drho, J[3], sum m x j [3]
-constexpr int ACC_UNC = 84;         // n, sum m [3], sum m m^T [6: xx xy xz yy yz zz]
-constexpr int NACC = 96;
+// accumulator layout (int64 per particle); d = fixed-point f* of a link (x, b),
+// m = cube-local position of x
+constexpr int ACC_F = 0;            // sum over links of c_b d                [3]
+constexpr int ACC_T = 3;            // sum over links of m x (c_b d)          [3]
+constexpr int ACC_COV = 6;          // n, sum drho, J[3], sum m x j [3]
+constexpr int ACC_UNC = 14;         // n, sum m [3], sum m m^T [6: xx xy xz yy yz zz]
+constexpr int NACC = 24;
 constexpr float FIXF = 70368744177664.0f;    // 2^46: |deviation| * 63 * 2^46 * links stays < 2^63
 constexpr double FIXD = 70368744177664.0;
 
@@ -111,13 +121,13 @@ struct BoxDev {
     float scale, inv_scale;         // 16-bit storage scale (1 for FP32 / BF16)
 };
 
-// FP32 snapshot of one particle for the lattice kernel, written by the
-// particle kernel of iteration t for the lattice kernel of iteration t+1.
+// FP32 snapshot of one particle for the lattice kernels, written by the
+// critical particle kernel of iteration t for the kernels of iteration t+1.
 struct PartK {
     const uint64_t* rows_old;       // occupancy of the pose at t   (map t)
     const uint64_t* rows_new;       // occupancy of the pose at t+1 (map t+1)
-    long long* acc;                 // NACC accumulators
     int ow_old[3], ow_new[3];       // cube origins wrapped into the box
+    int oy_new;                     // y of the new cube origin, not wrapped (wall rows)
     int S;                          // cube side
     int box;
     float ro_old[3];                // origin(t) - x_c(t)     (r = ro + m [+ c/2])
@@ -129,14 +139,22 @@ struct PartK {
     int nsolid;                     // solid nodes of map t+1
     double dm_return;               // mass put back at the next collision
     double Fext[3];
-    unsigned* list;                 // boundary nodes for the next lattice step (cube-local x|y<<8|z<<16)
-    int* list_count;
-    int list_cap;
-    int pad;
-    float* side_val;                // boundary kernel output: [list_cap][19] post-collision values
-    int* side_idx;                  // node index (>= 0 write, -1 skip, -2-node write zeros)
-    int* side_count;                // entries of side_val / side_idx written by the boundary kernel
-    int pad2;
+    // the particle's box (constant, set with the particles), so that no kernel
+    // of the particle chain needs a second dependent load
+    long long N, off, nwall;
+    double rho0;
+    int nx, ny, nz, walls;
+    float omega, rho0f, scale, inv_scale;
+    float uw_lo[3], uw_hi[3];
+    float body[3];
+    int counter;                    // counter body force on
+    int pbeg, pcnt;                 // particles of the box
+};
+
+// cube of a particle's redo mask: origin wrapped into the box, side
+struct NeedHdr {
+    int ow[3];
+    int S;
 };
 
 // uniform per-box terms of the next collision: body force g and mass return eps
@@ -145,21 +163,24 @@ struct BoxDyn {
     float eps;
 };
 
-// Full FP64 state of one particle, read and written by the particle kernel only.
+// Full FP64 state of one particle, read and written by the particle kernels only.
 struct PartDev {
     double semi[3], M, Ib[3], density, B1, B2;
-    double Fext[3], Text[3];
-    double x[3], q[4], U[3], W[3];  // at time t (before the particle kernel of t)
-    double Iprev[9];
-    double zeta[36];                // drag matrix of links(t)
+    double Fext[3], Text[3];        // adjacent: lb_set_external copies the six together
+    double x[3], q[4], U[3], W[3];  // at time t (before the critical kernel of t)
+    double inv_semi2[3];            // 1 / semi^2, rounded as the exact inside test rounds it
+    // prepared by the auxiliary kernel of t-1 for the critical kernel of t
+    double Icur[9];                 // lab-frame inertia at q(t) (Eq. Irot)
+    double zeta[36];                // drag matrix of links(t) (Eq. drag1-drag4)
+    double Ainv[36];                // inverse of the matrix of Eq. Fdiscrete / Eq. Tdiscrete
+    double F0g[3], T0g[3];          // parts of F0, T0 fixed by links(t) alone (Eq. F0, Eq. T0)
+    double phi[3];                  // cube origin of map t - x_c(t)
     int o[3];                       // cube origin (unwrapped) of map t
     int o_prev[3];                  // cube origin of map t-1
     int S, h, box, slot;            // slot: ring slot holding map t
     long long step;
-    int lm[Q][10];                  // link moments of links(t): n, sum m[3], sum m m^T[6]
-    long long slip[Q][4];           // fixed-point sums of (u_s.c_b) and (u_s.c_b) m
     double rec[25];                 // F0, T0, F, T, U, Omega, x, q of the last iteration
-    int nsolid;
+    int nsolid, pad;
 };
 
 static_assert(sizeof(PartDev) % 8 == 0, "PartDev is copied as 8-byte words");
@@ -170,17 +191,15 @@ struct KParams {
     int nbox;
     const PartK* pk;
     const void* src;                // distributions of iteration t-1 (post-collision)
-    void* dst;                      // distributions of iteration t
     unsigned* status;
-    int mode;                       // 0 first collide (no pull), 1 full, 2 pull only (fields)
-    // mode 2 outputs (one box)
+    // outputs (one box)
     float* out_f;                   // [19][N] or nullptr
     int out_dev;                    // 1: out_f holds deviations, 0: full f
     float* out_rho;                 // [N] rho - rho0 or nullptr
     float* out_u;                   // [3][N] or nullptr
     int* out_solid;                 // [N] or nullptr
-    int only_box;                   // mode 2: box index (grid covers that box only)
-    int nopull;                     // mode 2 before the first collision: f = w rho0, no streaming
+    int only_box;                   // box index (the grid covers that box only)
+    int nopull;                     // before the first collision: f = w rho0, no streaming
 };
 
 struct PParams {
@@ -190,7 +209,10 @@ struct PParams {
     uint64_t* rows;                 // np * 2 * MAXS*MAXS words
     const BoxDev* boxes;
     BoxDyn* box_dyn;                // per box, for the next collision (slot of the next iteration)
-    int* box_done;                  // per box arrival counters (last block writes box_dyn)
+    BoxDyn* pdyn;                   // the same per particle (the boundary kernel's copy)
+    int* box_done;                  // per box arrival counters (boxes with several particles)
+    NeedHdr* need_hdr;              // per particle: redo mask of the next step (written)
+    uint64_t* need;                 // per particle MAXS*MAXS words (written)
     unsigned* status;
     int np;
     int init;                       // 1: build maps / moments only (no solve, no pose update)
@@ -202,19 +224,26 @@ struct BulkParams {
     const BoxDev* boxes;
     const int* blk_box;             // box of every bulk block
     const BoxDyn* box_dyn;
+    const NeedHdr* need_hdr;        // per particle: the nodes left to the boundary kernel
+    const uint64_t* need;           // per particle MAXS*MAXS words
     const void* src;
     void* dst;
     int first;                      // 1: first collision of the run (rest state, no streaming)
 };
 
 struct BndParams {
-    const BoxDev* boxes;
-    const BoxDyn* box_dyn;
+    const BoxDyn* pdyn;             // per particle: the box's uniform terms of this collision
     const PartK* pk;
+    long long* acc;                 // np * NACC
+    const uint64_t* rows;           // np * 2 * MAXS*MAXS words (both ring slots)
+    const uint64_t* need;           // per particle MAXS*MAXS words: the nodes to redo
+    unsigned* status;
     const void* src;
-    void* dst;                      // scatter kernel: the lattice buffer of iteration t
+    void* dst;                      // the lattice buffer of this step (written directly)
+    int list_cap;                   // node list entries per block (shared memory)
     int first;
     int smax;                       // largest cube side (sizes dynamic shared memory)
+    int gx;                         // blocks per particle; block c takes cube rows c, c + gx, ...
 };
 
 inline int rows_stride() { return MAXS * MAXS; }
