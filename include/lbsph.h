@@ -71,7 +71,8 @@ enum {
 
 /* option flags */
 enum {
-    LB_FLAG_NO_GRAPH = 1u  /* launch every kernel directly instead of replaying a CUDA graph */
+    LB_FLAG_SEPARATE_KERNELS = 1u  /* run each step as four kernel launches instead of the
+                                      persistent step kernel (same results, bit for bit) */
 };
 
 /* One periodic box (x, y, z periodic) or a channel (walls != 0: the planes
@@ -140,7 +141,10 @@ lb_status lb_set_external(lb_ctx* ctx, int32_t box, const double* ft, int32_t n,
 /* Advances every box by nsteps iterations of the Appendix algorithm (collide,
  * stream with link bounce-back, F0/T0, inertia, implicit solve, position and
  * quaternion update, remap with covered/uncovered nodes, drag matrices).
- * Asynchronous on `stream` (a cudaStream_t, NULL = the context's stream). */
+ * Asynchronous on `stream` (a cudaStream_t, NULL = the context's stream).
+ * After the first collision the steps run in a persistent cooperative kernel
+ * that occupies every SM, up to 256 iterations per launch; its grid barriers
+ * give up after about two seconds and then report LB_ECUDA. */
 lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream);
 
 /* Writes the fields `what` (one LB_FIELD_* bit) of box `box` at the current

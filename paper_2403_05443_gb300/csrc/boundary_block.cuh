@@ -1,0 +1,274 @@
+// Boundary block (see boundary_kernel.cu for the method), shared by the
+// boundary kernel and the persistent step kernel.
+#pragma once
+
+#include "lattice_common.cuh"
+
+namespace lbsph {
+
+// round(f * 2^46) toward zero, from the IEEE 754 fields with integer
+// instructions (exact for |f| >= 2^-23, off by less than 2^-46 below; 64-bit
+// float-to-integer conversions run at the slow FP64 rate on this part)
+__device__ __forceinline__ long long fixq(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const int ex = (int)((u >> 23) & 0xffu);
+    const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
+    const int sh = ex - 104;                    // f * 2^46 = m * 2^(ex - 127 - 23 + 46)
+    long long v;
+    if (ex == 0 || sh <= -24) v = 0;            // zero, subnormal, or |f| < 2^-46
+    else if (sh >= 0) v = m << (sh > 38 ? 38 : sh);   // saturates for |f| >= 2^16 (no deviation is)
+    else v = m >> (-sh);
+    return (u >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ long long warp_sum(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += (long long)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+    return v;
+}
+
+// block c (of P.gx) of particle p; BBLOCK threads
+template <class St, bool FIRST>
+__device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
+{
+    using T = typename St::T;
+    constexpr int NW = BBLOCK / 32;
+    const int gx = P.gx;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cap = P.list_cap, smax = P.smax;
+
+    extern __shared__ uint64_t s_bits[];            // ring slots 0 and 1 (smax*smax rows each), then the node list
+    unsigned* s_list = reinterpret_cast<unsigned*>(s_bits + 2 * smax * smax);
+    __shared__ PartK K;
+    __shared__ long long s_red[NW][ACC_COV];        // per-warp link sums
+    __shared__ long long s_rare[NACC - ACC_COV];    // covered / uncovered nodes (rare: shared atomics)
+    __shared__ int s_wsum[NW];
+
+    // ---- one round of independent loads
+    const BoxDyn dyn = ldcg_dyn(P.pdyn + p);
+    const int rrow = c + gx * tid;                  // this thread's cube row
+    uint64_t need = rrow < smax * smax ? __ldcg(P.need + (size_t)p * (MAXS * MAXS) + rrow) : 0ull;
+    {
+        ldcg_copy(&K, P.pk + p, tid, BBLOCK);
+        if (tid < NACC - ACC_COV) s_rare[tid] = 0;
+        const uint64_t* r0 = P.rows + (size_t)p * 2 * (MAXS * MAXS);
+        const int n = smax * smax;
+#pragma unroll 4
+        for (int r = tid; r < n; r += BBLOCK) {
+            s_bits[r] = __ldcg(r0 + r);
+            s_bits[n + r] = __ldcg(r0 + MAXS * MAXS + r);
+        }
+    }
+    __syncthreads();
+
+    const int S = K.S;
+    const uint64_t* slot1 = P.rows + ((size_t)p * 2 + 1) * (MAXS * MAXS);
+    const uint64_t* s_new = s_bits + (K.rows_new == slot1 ? smax * smax : 0);
+    const uint64_t* s_old = s_bits + (K.rows_old == slot1 ? smax * smax : 0);
+    const int nx = K.nx, ny = K.ny, nz = K.nz;
+    const bool walls = K.walls != 0;
+    int dsh[3];                                     // o_new - o_old: old-local = new-local + dsh
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int L = k == 0 ? nx : (k == 1 ? ny : nz);
+        int v = K.ow_new[k] - K.ow_old[k];
+        if (v > L / 2) v -= L;
+        if (v < -L / 2) v += L;
+        dsh[k] = FIRST ? 0 : v;
+    }
+    auto bit_new = [&](int ax, int ay, int az) -> bool {
+        if (ax < 0 || ax >= S || ay < 0 || ay >= S || az < 0 || az >= S) return false;
+        return (s_new[az * S + ay] >> ax) & 1ull;
+    };
+    auto bit_old = [&](int ax, int ay, int az) -> bool {
+        ax += dsh[0]; ay += dsh[1]; az += dsh[2];
+        if (ax < 0 || ax >= S || ay < 0 || ay >= S || az < 0 || az >= S) return false;
+        return (s_old[az * S + ay] >> ax) & 1ull;
+    };
+    // ---- this block's rows: the nodes to redo, compacted into shared memory
+    {
+        if (rrow >= S * S) need = 0;
+        // block-wide exclusive scan of the row counts
+        const int cnt = __popcll(need);
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) s_wsum[warp] = inc;
+        __syncthreads();
+        int base = inc - cnt;
+        for (int w = 0; w < warp; ++w) base += s_wsum[w];
+        const int my = rrow % S, mz = rrow / S;
+        for (int k = 0; need; ++k) {
+            const int mx = __ffsll((long long)need) - 1;
+            need &= need - 1;
+            if (base + k < cap) s_list[base + k] = (unsigned)((mz << 16) | (my << 8) | mx);
+        }
+    }
+    __syncthreads();
+    int total = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) total += s_wsum[w];
+    if (tid == 0 && total > cap) atomicOr(P.status, ST_CAPACITY);
+    const int count = min(total, cap);
+
+    const long long N = K.N;
+    const T* A = reinterpret_cast<const T*>(P.src) + K.off;
+    const float inv = K.inv_scale, rho0 = K.rho0f, scale = K.scale;
+    const unsigned long long pol = l2_evict_normal();
+    T* D = reinterpret_cast<T*>(P.dst) + K.off;
+
+    // ---- this block's nodes; per-thread link sums
+    long long aF[3] = {0, 0, 0}, aT[3] = {0, 0, 0};
+    auto rare_add = [&](int j, long long v) {
+        if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&s_rare[j - ACC_COV]), (unsigned long long)v);
+    };
+
+    for (int e = tid; e < count; e += BBLOCK) {
+        const unsigned code = s_list[e];
+        const int mx = code & 0xff, my = (code >> 8) & 0xff, mz = (code >> 16) & 0xff;
+        const int X = wrapd(K.ow_new[0] + mx, nx), Y = wrapd(K.ow_new[1] + my, ny), Z = wrapd(K.ow_new[2] + mz, nz);
+        const long long own = ((long long)Z * ny + Y) * nx + X;
+        const bool wallrow = walls && (Y == 0 || Y == ny - 1);
+        const bool sol_new = bit_new(mx, my, mz);
+        const bool sol_old = !FIRST && bit_old(mx, my, mz);
+        bool write = !wallrow;
+        float f[Q];
+        if (wallrow || (sol_new && (sol_old || FIRST))) {
+            write = false;                          // solid before and after: untouched
+        } else if (sol_old) {
+            // uncovered: f = f_eq(rho0, U + Omega x r) with r = x - x_c(t)
+            const float rx = K.ro_new[0] + mx, ry = K.ro_new[1] + my, rz = K.ro_new[2] + mz;
+            const float ux = K.U[0] + (K.W[1] * rz - K.W[2] * ry);
+            const float uy = K.U[1] + (K.W[2] * rx - K.W[0] * rz);
+            const float uz = K.U[2] + (K.W[0] * ry - K.W[1] * rx);
+            const float uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
+                f[i] = w_of(i) * rho0 * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+            }
+            rare_add(ACC_UNC, 1);
+            rare_add(ACC_UNC + 1, mx); rare_add(ACC_UNC + 2, my); rare_add(ACC_UNC + 3, mz);
+            rare_add(ACC_UNC + 4, mx * mx); rare_add(ACC_UNC + 5, mx * my); rare_add(ACC_UNC + 6, mx * mz);
+            rare_add(ACC_UNC + 7, my * my); rare_add(ACC_UNC + 8, my * mz); rare_add(ACC_UNC + 9, mz * mz);
+        } else if (FIRST) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = 0.0f;
+        } else {
+            // fluid at t-1: decide every source first, then issue the 19 loads together
+            unsigned bb = 0, wl = 0;
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int Ys = Y - cy_of(i);
+                if (walls && (Ys == 0 || Ys == ny - 1)) wl |= 1u << i;
+                else if (bit_old(mx - cx_of(i), my - cy_of(i), mz - cz_of(i))) bb |= 1u << i;
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool back = ((bb | wl) >> i) & 1u;
+                const long long src = back ? (long long)opp_of(i) * N + own
+                                           : (long long)i * N + ((long long)wrapd(Z - cz_of(i), nz) * ny + wrapd(Y - cy_of(i), ny)) * nx +
+                                                 wrapd(X - cx_of(i), nx);
+                f[i] = St::ld1(A + src, inv, pol);
+            }
+            // mid-link bounce-back terms: + 6 w_i rho0 (u_b . c_i) (Eq. fb, Eq. ub, Eq. ubsquirmer)
+            const float ex[3] = {K.e_old[0], K.e_old[1], K.e_old[2]};
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                if (!(((bb | wl) >> i) & 1u)) continue;
+                float ubc;
+                if ((wl >> i) & 1u) {
+                    const float* uw = (Y - cy_of(i) == 0) ? K.uw_lo : K.uw_hi;
+                    ubc = cx_of(i) * uw[0] + cy_of(i) * uw[1] + cz_of(i) * uw[2];
+                } else {
+                    // r_b = x - c_i/2 - x_c(t-1) = ro_old + dsh + m - c_i/2
+                    const float px = K.ro_old[0] + (float)(dsh[0] + mx) - 0.5f * cx_of(i);
+                    const float py = K.ro_old[1] + (float)(dsh[1] + my) - 0.5f * cy_of(i);
+                    const float pz = K.ro_old[2] + (float)(dsh[2] + mz) - 0.5f * cz_of(i);
+                    float ux = K.U[0] + (K.W[1] * pz - K.W[2] * py);
+                    float uy = K.U[1] + (K.W[2] * px - K.W[0] * pz);
+                    float uz = K.U[2] + (K.W[0] * py - K.W[1] * px);
+                    if (K.squirmer) {
+                        float qx, qy, qz;
+                        squirmer_slip(ex, K.a, K.eps2, K.B1, K.B2, px, py, pz, qx, qy, qz);
+                        ux += qx; uy += qy; uz += qz;
+                    }
+                    ubc = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
+                }
+                f[i] += 6.0f * w_of(i) * rho0 * ubc;
+            }
+            if (sol_new) {
+                // covered: mass and momentum go to the particle's next solve
+                write = false;
+                float drho = 0.f;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) drho += f[i];
+                const float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
+                const float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
+                const float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
+                const long long Jx = fixq(jx), Jy = fixq(jy), Jz = fixq(jz);
+                rare_add(ACC_COV, 1);
+                rare_add(ACC_COV + 1, fixq(drho));
+                rare_add(ACC_COV + 2, Jx); rare_add(ACC_COV + 3, Jy); rare_add(ACC_COV + 4, Jz);
+                rare_add(ACC_COV + 5, my * Jz - mz * Jy);
+                rare_add(ACC_COV + 6, mz * Jx - mx * Jz);
+                rare_add(ACC_COV + 7, mx * Jy - my * Jx);
+            }
+        }
+        if (write) {
+            collide19(f, K.omega, rho0, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) St::st1(D + (long long)i * N + own, f[i], scale, pol);
+            // momentum-exchange sums of the new links (x, b), with f*(t)
+            long long fx = 0, fy = 0, fz = 0;
+            bool any = false;
+#pragma unroll
+            for (int b = 1; b < Q; ++b) {
+                if (!bit_new(mx + cx_of(b), my + cy_of(b), mz + cz_of(b))) continue;
+                const long long d = fixq(f[b]);
+                any = true;
+                if (cx_of(b) == 1) fx += d; else if (cx_of(b) == -1) fx -= d;
+                if (cy_of(b) == 1) fy += d; else if (cy_of(b) == -1) fy -= d;
+                if (cz_of(b) == 1) fz += d; else if (cz_of(b) == -1) fz -= d;
+            }
+            if (any) {
+                aF[0] += fx; aF[1] += fy; aF[2] += fz;
+                aT[0] += my * fz - mz * fy;
+                aT[1] += mz * fx - mx * fz;
+                aT[2] += mx * fy - my * fx;
+            }
+        } else if (sol_new && !wallrow) {
+            // solid now: zero it (never read as a source)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) St::st1(D + (long long)i * N + own, 0.0f, scale, pol);
+        }
+    }
+
+    // ---- per-warp link sums into shared memory, then one atomic per nonzero sum
+    if (__any_sync(0xffffffffu, (aF[0] | aF[1] | aF[2] | aT[0] | aT[1] | aT[2]) != 0)) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { aF[k] = warp_sum(aF[k]); aT[k] = warp_sum(aT[k]); }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { s_red[warp][ACC_F + k] = aF[k]; s_red[warp][ACC_T + k] = aT[k]; }
+    }
+    __syncthreads();
+    if (tid < NACC) {
+        long long v = 0;
+        if (tid < ACC_COV) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) v += s_red[w][tid];
+        } else {
+            v = s_rare[tid - ACC_COV];
+        }
+        if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(P.acc + (size_t)p * NACC + tid), static_cast<unsigned long long>(v));
+    }
+}
+
+}  // namespace lbsph

@@ -1,0 +1,130 @@
+// One 256-quad tile of the bulk lattice kernel (see bulk_kernel.cu), shared by
+// the bulk kernel and the persistent step kernel.
+#pragma once
+
+#include "lattice_common.cuh"
+
+namespace lbsph {
+
+template <class St, bool FIRST>
+__device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile)
+{
+    const int tix = threadIdx.x;
+    using T = typename St::T;
+    const int bi = __ldg(P.blk_box + tile);
+    const BoxDev& B = P.boxes[bi];
+    const int nx = B.nx, ny = B.ny, nz = B.nz, nxq = B.nxq;
+    const long long N = B.N;
+    long long q = (long long)(tile - B.block_begin) * KBLOCK + tix;
+    const bool valid = q < B.nq;
+    if (!valid) q = B.nq - 1;
+    const int xq = (int)(q % nxq);
+    const long long row = q / nxq;
+    const int y = (int)(row % ny), z = (int)(row / ny);
+    const int lane = tix & 31;
+    const T* A = reinterpret_cast<const T*>(P.src) + B.off;
+    T* D = reinterpret_cast<T*>(P.dst) + B.off;
+    const float inv = B.inv_scale;
+    const long long own = row * nx + 4 * xq;
+    const unsigned long long pol_first = l2_evict_first();
+
+    long long rofs[3][3];  // element offsets of the source rows (y + dy, z + dz), wrapped
+    {
+        const int yy[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+        const int zz[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) rofs[a][b] = ((long long)zz[b] * ny + yy[a]) * nx;
+    }
+    const bool left_ld = (lane == 0) || (xq == 0);
+    const bool right_ld = (lane == 31) || (xq == nxq - 1);
+
+    float4 v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (FIRST) {
+            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const T* rp = A + (long long)i * N + rofs[1 - cy_of(i)][1 - cz_of(i)];
+        float4 t = St::ld4(rp + 4 * xq, inv, pol_first);
+        if (cx_of(i) == 1) {            // source x - 1
+            float l = __shfl_up_sync(0xffffffffu, t.w, 1);
+            if (left_ld) l = St::ld1(rp + (xq == 0 ? nx - 1 : 4 * xq - 1), inv, pol_first);
+            t = make_float4(l, t.x, t.y, t.z);
+        } else if (cx_of(i) == -1) {    // source x + 1
+            float r = __shfl_down_sync(0xffffffffu, t.x, 1);
+            if (right_ld) r = St::ld1(rp + (xq == nxq - 1 ? 0 : 4 * xq + 4), inv, pol_first);
+            t = make_float4(t.y, t.z, t.w, r);
+        }
+        v[i] = t;
+    }
+
+    const BoxDyn dyn = ldcg_dyn(P.box_dyn + bi);
+    const bool wallrow = B.walls && (y == 0 || y == ny - 1);
+    if (!FIRST && B.walls && (y == 1 || y == ny - 2)) {
+        // link bounce-back on a moving wall (Eq. fb with u_b = u_w)
+        const int cyw = (y == 1) ? 1 : -1;
+        const float* uw = (y == 1) ? B.uw_lo : B.uw_hi;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (cy_of(i) != cyw) continue;
+            const float ubc = cx_of(i) * uw[0] + cy_of(i) * uw[1] + cz_of(i) * uw[2];
+            const float add = 6.0f * w_of(i) * B.rho0f * ubc;
+            const float4 o = St::ld4(A + (long long)opp_of(i) * N + own, inv, pol_first);
+            v[i] = make_float4(o.x + add, o.y + add, o.z + add, o.w + add);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = comp(v[i], k);
+        collide19(f, B.omega, B.rho0f, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) set_comp(v[i], k, wallrow ? 0.0f : f[i]);
+    }
+    // nodes of this quad that the boundary kernel writes; quads within two
+    // nodes of a particle's cube keep their lines in L2 for the next step's
+    // boundary and particle work
+    unsigned skip = 0;
+    bool near = false;
+    for (int j = 0; j < B.pcnt; ++j) {
+        const NeedHdr h = ldcg_hdr(P.need_hdr + B.pbeg + j);
+        int dz = z - h.ow[2];
+        if (dz < 0) dz += nz;
+        int dy = y - h.ow[1];
+        if (dy < 0) dy += ny;
+        int dx = 4 * xq - h.ow[0];
+        if (dx < 0) dx += nx;
+        // within two nodes of the cube, cyclically (a cache hint only)
+        near = near || ((dz < h.S + 2 || dz >= nz - 2) && (dy < h.S + 2 || dy >= ny - 2) &&
+                        (dx < h.S + 2 || dx + 3 >= nx - 2));
+        if (dz >= h.S || dy >= h.S) continue;
+        if (dx >= h.S && dx + 3 < nx) continue;
+        const uint64_t w = __ldcg(P.need + (size_t)(B.pbeg + j) * (MAXS * MAXS) + dz * h.S + dy);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int mx = dx + k < nx ? dx + k : dx + k - nx;
+            if (mx < h.S && ((w >> mx) & 1ull)) skip |= 1u << k;
+        }
+    }
+    if (valid) {
+        T* dp = D + own;
+        const unsigned long long pol = near ? l2_evict_normal() : pol_first;
+        if (!skip) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) St::st4(dp + (long long)i * N, v[i], B.scale, pol);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if ((skip >> k) & 1u) continue;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) St::st1(dp + (long long)i * N + k, comp(v[i], k), B.scale, pol);
+            }
+        }
+    }
+}
+
+}  // namespace lbsph

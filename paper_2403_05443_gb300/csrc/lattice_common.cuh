@@ -10,57 +10,158 @@
 namespace lbsph {
 
 // ---------------------------------------------------------------------------
+// Loads of data that another block may have written earlier in the same
+// (persistent) kernel go through L2 (ld.global.cg): the SM's L1 is not
+// coherent and could still hold a line from an earlier step.
+__device__ __forceinline__ BoxDyn ldcg_dyn(const BoxDyn* p)
+{
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+    BoxDyn d;
+    d.g[0] = v.x; d.g[1] = v.y; d.g[2] = v.z; d.eps = v.w;
+    return d;
+}
+__device__ __forceinline__ NeedHdr ldcg_hdr(const NeedHdr* p)
+{
+    const int4 v = __ldcg(reinterpret_cast<const int4*>(p));
+    NeedHdr h;
+    h.ow[0] = v.x; h.ow[1] = v.y; h.ow[2] = v.z; h.S = v.w;
+    return h;
+}
+// block-wide copy of a struct from global to shared memory, 4-byte words
+template <class T>
+__device__ __forceinline__ void ldcg_copy(T* dst, const T* src, int tid, int nthreads)
+{
+    static_assert(sizeof(T) % 4 == 0, "copied as 4-byte words");
+    const unsigned* s = reinterpret_cast<const unsigned*>(src);
+    unsigned* d = reinterpret_cast<unsigned*>(dst);
+    for (int j = tid; j < (int)(sizeof(T) / 4); j += nthreads) d[j] = __ldcg(s + j);
+}
+
+// ---------------------------------------------------------------------------
+// L2 eviction priority of lattice accesses.  The bulk streams twice the size
+// of L2 per step; with evict-first on its traffic, the particle chain's state
+// and the lattice around the particles stay in L2.  Lattice loads never
+// allocate in L1 (the L1 is not coherent across the steps of a persistent
+// kernel).
+__device__ __forceinline__ unsigned long long l2_evict_first()
+{
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_normal()
+{
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float4 ldh_f4(const void* a, unsigned long long pol)
+{
+    float4 v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ldh_f1(const void* a, unsigned long long pol)
+{
+    float v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint2 ldh_u2(const void* a, unsigned long long pol)
+{
+    uint2 v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ unsigned short ldh_u16(const void* a, unsigned long long pol)
+{
+    unsigned short v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void sth_f4(void* a, float4 v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void sth_f1(void* a, float v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void sth_u2(void* a, uint2 v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1,%2}, %3;" ::"l"(a), "r"(v.x), "r"(v.y), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void sth_u16(void* a, unsigned short v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(a), "h"(v), "l"(pol) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // storage policies: values are deviations f_i - w_i rho0 (x scale for FP16)
 struct StF32 {
     using T = float;
-    static __device__ __forceinline__ float4 ld4(const T* p, float) { return __ldg(reinterpret_cast<const float4*>(p)); }
-    static __device__ __forceinline__ float ld1(const T* p, float) { return __ldg(p); }
-    static __device__ __forceinline__ void st4(T* p, float4 v, float) { *reinterpret_cast<float4*>(p) = v; }
-    static __device__ __forceinline__ void st1(T* p, float v, float) { *p = v; }
+    static __device__ __forceinline__ float4 ld4(const T* p, float, unsigned long long pol) { return ldh_f4(p, pol); }
+    static __device__ __forceinline__ float ld1(const T* p, float, unsigned long long pol) { return ldh_f1(p, pol); }
+    static __device__ __forceinline__ void st4(T* p, float4 v, float, unsigned long long pol) { sth_f4(p, v, pol); }
+    static __device__ __forceinline__ void st1(T* p, float v, float, unsigned long long pol) { sth_f1(p, v, pol); }
 };
 
 struct StF16 {
     using T = __half;
-    static __device__ __forceinline__ float4 ld4(const T* p, float inv)
+    static __device__ __forceinline__ float4 ld4(const T* p, float inv, unsigned long long pol)
     {
-        uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-        float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
-        float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        const uint2 u = ldh_u2(p, pol);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
         return make_float4(a.x * inv, a.y * inv, b.x * inv, b.y * inv);
     }
-    static __device__ __forceinline__ float ld1(const T* p, float inv) { return __half2float(p[0]) * inv; }
-    static __device__ __forceinline__ void st4(T* p, float4 v, float scale)
+    static __device__ __forceinline__ float ld1(const T* p, float inv, unsigned long long pol)
+    {
+        return __half2float(__ushort_as_half(ldh_u16(p, pol))) * inv;
+    }
+    static __device__ __forceinline__ void st4(T* p, float4 v, float scale, unsigned long long pol)
     {
         __half2 a = __floats2half2_rn(v.x * scale, v.y * scale);
         __half2 b = __floats2half2_rn(v.z * scale, v.w * scale);
         uint2 u;
         u.x = *reinterpret_cast<unsigned*>(&a);
         u.y = *reinterpret_cast<unsigned*>(&b);
-        *reinterpret_cast<uint2*>(p) = u;
+        sth_u2(p, u, pol);
     }
-    static __device__ __forceinline__ void st1(T* p, float v, float scale) { *p = __float2half_rn(v * scale); }
+    static __device__ __forceinline__ void st1(T* p, float v, float scale, unsigned long long pol)
+    {
+        sth_u16(p, __half_as_ushort(__float2half_rn(v * scale)), pol);
+    }
 };
 
 struct StBF16 {
     using T = __nv_bfloat16;
-    static __device__ __forceinline__ float4 ld4(const T* p, float)
+    static __device__ __forceinline__ float4 ld4(const T* p, float, unsigned long long pol)
     {
-        uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-        float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-        float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+        const uint2 u = ldh_u2(p, pol);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
         return make_float4(a.x, a.y, b.x, b.y);
     }
-    static __device__ __forceinline__ float ld1(const T* p, float) { return __bfloat162float(p[0]); }
-    static __device__ __forceinline__ void st4(T* p, float4 v, float)
+    static __device__ __forceinline__ float ld1(const T* p, float, unsigned long long pol)
+    {
+        return __bfloat162float(__ushort_as_bfloat16(ldh_u16(p, pol)));
+    }
+    static __device__ __forceinline__ void st4(T* p, float4 v, float, unsigned long long pol)
     {
         __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
         __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
         uint2 u;
         u.x = *reinterpret_cast<unsigned*>(&a);
         u.y = *reinterpret_cast<unsigned*>(&b);
-        *reinterpret_cast<uint2*>(p) = u;
+        sth_u2(p, u, pol);
     }
-    static __device__ __forceinline__ void st1(T* p, float v, float) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void st1(T* p, float v, float, unsigned long long pol)
+    {
+        sth_u16(p, __bfloat16_as_ushort(__float2bfloat16_rn(v)), pol);
+    }
 };
 
 // ---------------------------------------------------------------------------

@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(KBLOCK) fields_kernel(const KParams P)
     const int lane = threadIdx.x & 31;
     const T* A = reinterpret_cast<const T*>(P.src) + B.off;
     const float inv = B.inv_scale;
+    const unsigned long long pol = l2_evict_normal();
 
     long long rofs[3][3];  // element offset of source rows (y + dy, z + dz), wrapped
     {
@@ -202,14 +203,14 @@ __global__ void __launch_bounds__(KBLOCK) fields_kernel(const KParams P)
             continue;
         }
         const T* rp = A + (long long)i * N + rofs[1 - cy_of(i)][1 - cz_of(i)];
-        float4 t = St::ld4(rp + 4 * xq, inv);
+        float4 t = St::ld4(rp + 4 * xq, inv, pol);
         if (cx_of(i) == 1) {           // source x - 1
             float l = __shfl_up_sync(0xffffffffu, t.w, 1);
-            if (left_ld) l = St::ld1(rp + (xq == 0 ? nx - 1 : 4 * xq - 1), inv);
+            if (left_ld) l = St::ld1(rp + (xq == 0 ? nx - 1 : 4 * xq - 1), inv, pol);
             t = make_float4(l, t.x, t.y, t.z);
         } else if (cx_of(i) == -1) {   // source x + 1
             float r = __shfl_down_sync(0xffffffffu, t.x, 1);
-            if (right_ld) r = St::ld1(rp + (xq == nxq - 1 ? 0 : 4 * xq + 4), inv);
+            if (right_ld) r = St::ld1(rp + (xq == nxq - 1 ? 0 : 4 * xq + 4), inv, pol);
             t = make_float4(t.y, t.z, t.w, r);
         }
         v[i] = t;
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(KBLOCK) fields_kernel(const KParams P)
                     if (B.walls && (Ys == 0 || Ys == ny - 1)) {
                         const float* uw = (Ys == 0) ? B.uw_lo : B.uw_hi;
                         const float ubc = cx_of(i) * uw[0] + cy_of(i) * uw[1] + cz_of(i) * uw[2];
-                        f[i] = St::ld1(A + (long long)opp_of(i) * N + own + k, inv) + 6.0f * w_of(i) * rho0 * ubc;
+                        f[i] = St::ld1(A + (long long)opp_of(i) * N + own + k, inv, pol) + 6.0f * w_of(i) * rho0 * ubc;
                         continue;
                     }
                     if (!((so[1 - cy_of(i)][1 - cz_of(i)] >> (k + 1 - cx_of(i))) & 1u)) continue;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(KBLOCK) fields_kernel(const KParams P)
                         ux += qx; uy += qy; uz += qz;
                     }
                     const float ubc = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
-                    f[i] = St::ld1(A + (long long)opp_of(i) * N + own + k, inv) + 6.0f * w_of(i) * rho0 * ubc;
+                    f[i] = St::ld1(A + (long long)opp_of(i) * N + own + k, inv, pol) + 6.0f * w_of(i) * rho0 * ubc;
                 }
             }
             if (sol_new) {

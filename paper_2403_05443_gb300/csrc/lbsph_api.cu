@@ -1,16 +1,14 @@
 // Host runtime behind the C ABI of include/lbsph.h.
 //
-// One iteration is four kernels on three streams.  The caller's stream runs
-// the bulk kernel (every node but those next to a particle's surface).  While
-// it streams the lattice, a high-priority particle stream runs the boundary
-// kernel (the nodes the bulk kernel skips, written into the same lattice
-// buffer) and the critical particle kernel (solve, pose, new occupancy, redo
-// masks and box forces for the next step), and a third stream the auxiliary
-// particle kernel (drag matrices and the inverse of the next solve), which
-// overlaps the next boundary kernel.  Events order them: bulk(t) waits for
-// critical(t-1) (box forces, redo masks), boundary(t) for bulk(t-1) (complete
-// lattice; boundary(t-1) precedes it on its stream), auxiliary(t) for
-// critical(t), critical(t+1) for auxiliary(t).  Chunks of iterations are captured
+// One iteration has four parts: the bulk lattice part (every node but those
+// next to a particle's surface), the boundary part (the nodes the bulk part
+// skips, written into the same lattice buffer), the critical particle part
+// (solve, pose, new occupancy, redo masks and box forces for the next step)
+// and the auxiliary particle part (drag matrices and the inverse of the next
+// solve).  Time steps run in the persistent step kernel (step_kernel.cu), many
+// iterations per cooperative launch; the first collision, the per-kernel
+// profile and LB_FLAG_SEPARATE_KERNELS run the four parts as separate kernels
+// in stream order.  Everything runs on the caller's stream.  Chunks of iterations are captured
 // once into a CUDA graph per buffer parity and replayed, so a long run costs
 // one graph launch per chunk and no host synchronisation.
 #include <cmath>
@@ -29,6 +27,8 @@ cudaError_t launch_bulk(const BulkParams& p, int precision, int blocks, cudaStre
 cudaError_t launch_boundary(const BndParams& p, int precision, int np, cudaStream_t s);
 cudaError_t launch_particles(const PParams& p, cudaStream_t s);
 cudaError_t launch_particles_aux(const PParams& p, cudaStream_t s);
+cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const PParams part[2], unsigned* sync,
+                        unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, cudaStream_t s);
 cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
                          int cap, int* count, cudaStream_t s);
 }  // namespace lbsph
@@ -36,7 +36,7 @@ cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* 
 using namespace lbsph;
 
 namespace {
-constexpr int GRAPH_ITERS = 32;     // iterations per captured graph (even)
+constexpr int STEP_ITERS = 256;     // iterations per launch of the step kernel
 }
 
 struct lb_ctx {
@@ -68,11 +68,9 @@ struct lb_ctx {
     bool collided = false;
     bool stepped = false;
     unsigned sticky = 0;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaStream_t last_user_stream = nullptr;        // last stream lb_step ran on
-    cudaStream_t aux = nullptr;                     // the particle stream
-    cudaStream_t aux2 = nullptr;                    // the auxiliary kernel's stream
-    cudaEvent_t ev_crit = nullptr, ev_aux = nullptr, ev_fork = nullptr;
+    cudaEvent_t ev_done = nullptr;                  // end of the last lb_step
+    unsigned* d_sync = nullptr;                     // step kernel: barrier, work and item counters, block SM ids
     NeedHdr* d_need_hdr = nullptr;     // [2][maxp]: redo masks, one slot per buffer parity
     uint64_t* d_need = nullptr;        // [2][maxp][MAXS*MAXS]
     int* d_blk_box = nullptr;
@@ -139,6 +137,7 @@ static lb_status read_status(lb_ctx* ctx)
     if (ctx->sticky & ST_NAN) return fail(ctx, LB_ENAN, "a particle state became NaN or Inf");
     if (ctx->sticky & ST_OVERLAP) return fail(ctx, LB_EOVERLAP, "a particle reached a wall or another particle");
     if (ctx->sticky & ST_CAPACITY) return fail(ctx, LB_ECAPACITY, "a particle outgrew its bounding cube or a tile met too many particles");
+    if (ctx->sticky & ST_TIMEOUT) return fail(ctx, LB_ECUDA, "a grid barrier of the step kernel timed out");
     return LB_OK;
 }
 
@@ -199,14 +198,8 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     ctx->device = o.device;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) { delete ctx; return LB_ECUDA; }
-    int prio_least = 0, prio_greatest = 0;
-    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&ctx->aux2, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_crit, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_aux, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming) != cudaSuccess) {
         delete ctx;
         return LB_ECUDA;
     }
@@ -273,16 +266,16 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     }
     ctx->d_need_hdr = (NeedHdr*)dev_alloc(ctx, sizeof(NeedHdr) * 2 * (size_t)ctx->maxp);
     ctx->d_need = (uint64_t*)dev_alloc(ctx, sizeof(uint64_t) * 2 * (size_t)MAXS * MAXS * ctx->maxp);
+    ctx->d_sync = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * (4 + (size_t)ctx->maxp + 4096));
     for (void* p : {ctx->fbuf[0], ctx->fbuf[1], (void*)ctx->d_boxes, (void*)ctx->d_pd, (void*)ctx->d_pk,
                     (void*)ctx->d_acc, (void*)ctx->d_rows, (void*)ctx->d_status, (void*)ctx->d_count,
                     (void*)ctx->d_blk_box, (void*)ctx->d_box_dyn, (void*)ctx->d_pdyn, (void*)ctx->d_box_done,
-                    (void*)ctx->d_need_hdr, (void*)ctx->d_need})
+                    (void*)ctx->d_need_hdr, (void*)ctx->d_need, (void*)ctx->d_sync})
         okm = okm && p;
     if (!okm) {
         free_all(ctx);
         cudaStreamDestroy(ctx->stream);
-        cudaStreamDestroy(ctx->aux);
-        cudaStreamDestroy(ctx->aux2);
+        cudaEventDestroy(ctx->ev_done);
         delete ctx;
         return LB_ENOMEM;
     }
@@ -310,19 +303,12 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     if (err != cudaSuccess) {
         free_all(ctx);
         cudaStreamDestroy(ctx->stream);
-        cudaStreamDestroy(ctx->aux);
-        cudaStreamDestroy(ctx->aux2);
+        cudaEventDestroy(ctx->ev_done);
         delete ctx;
         return LB_ECUDA;
     }
     *out = ctx;
     return LB_OK;
-}
-
-static void drop_graphs(lb_ctx* ctx)
-{
-    for (auto& g : ctx->gexec)
-        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
 extern "C" lb_status lb_destroy(lb_ctx* ctx)
@@ -331,14 +317,9 @@ extern "C" lb_status lb_destroy(lb_ctx* ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     cudaDeviceSynchronize();
-    drop_graphs(ctx);
     free_all(ctx);
     cudaStreamDestroy(ctx->stream);
-    cudaStreamDestroy(ctx->aux);
-    cudaStreamDestroy(ctx->aux2);
-    cudaEventDestroy(ctx->ev_crit);
-    cudaEventDestroy(ctx->ev_aux);
-    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_done);
     delete ctx;
     return LB_OK;
 }
@@ -488,10 +469,8 @@ extern "C" lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particl
     pp.init = 1;
     CK(launch_particles(pp, ctx->stream));
     CK(launch_particles_aux(pp, ctx->stream));
-    CK(cudaEventRecord(ctx->ev_aux, ctx->stream));
-    CK(cudaEventRecord(ctx->ev_crit, ctx->stream));
+    CK(cudaEventRecord(ctx->ev_done, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    drop_graphs(ctx);
     return read_status(ctx);
 }
 
@@ -522,10 +501,6 @@ static KParams base_kparams(lb_ctx* ctx)
     return k;
 }
 
-struct IterEvents {
-    cudaEvent_t fork, crit, aux;        // fork: bulk part of lattice t-1 complete; crit: box forces of t ready
-};
-
 static BulkParams bulk_params(lb_ctx* ctx, int first, int cur)
 {
     BulkParams bp{};
@@ -551,72 +526,33 @@ static BndParams bnd_params(lb_ctx* ctx, int first, int cur)
     return np;
 }
 
-// One iteration on the caller's stream s and the particle stream ctx->aux.
-static cudaError_t enqueue_iteration(lb_ctx* ctx, int first, int cur, cudaStream_t s, const IterEvents& ev)
+// One iteration as separate kernels, in stream order on s.
+static cudaError_t enqueue_iteration(lb_ctx* ctx, int first, int cur, cudaStream_t s)
 {
     cudaError_t e;
-    const BulkParams bp = bulk_params(ctx, first, cur);
-    if (ctx->np == 0) return launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s);
-    if ((e = cudaEventRecord(ev.fork, s)) != cudaSuccess) return e;             // lattice of t-1 complete
-    if ((e = cudaStreamWaitEvent(s, ev.crit, 0)) != cudaSuccess) return e;      // box forces of t
-    if ((e = launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s)) != cudaSuccess) return e;
-    const BndParams np = bnd_params(ctx, first, cur);
+    if ((e = launch_bulk(bulk_params(ctx, first, cur), ctx->opt.precision, ctx->total_blocks, s)) != cudaSuccess) return e;
+    if (ctx->np == 0) return cudaSuccess;
+    if ((e = launch_boundary(bnd_params(ctx, first, cur), ctx->opt.precision, ctx->np, s)) != cudaSuccess) return e;
     const PParams pp = particle_params(ctx, cur);
-    cudaStream_t t = ctx->aux, a = ctx->aux2;
-    if ((e = cudaStreamWaitEvent(t, ev.fork, 0)) != cudaSuccess) return e;
-    if ((e = launch_boundary(np, ctx->opt.precision, ctx->np, t)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(t, ev.aux, 0)) != cudaSuccess) return e;       // inverse and drag of t
-    if ((e = launch_particles(pp, t)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(ev.crit, t)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(a, ev.crit, 0)) != cudaSuccess) return e;
-    if ((e = launch_particles_aux(pp, a)) != cudaSuccess) return e;
-    return cudaEventRecord(ev.aux, a);
+    if ((e = launch_particles(pp, s)) != cudaSuccess) return e;
+    return launch_particles_aux(pp, s);
 }
 
-static IterEvents ctx_events(lb_ctx* ctx) { return IterEvents{ctx->ev_fork, ctx->ev_crit, ctx->ev_aux}; }
-
-// The graph gets its own events: an event last recorded inside a capture
-// cannot be waited on outside it.
-static lb_status build_graph(lb_ctx* ctx, int parity)
+// k iterations in one launch of the step kernel, starting at buffer parity cur
+static cudaError_t enqueue_steps(lb_ctx* ctx, int k, int cur, cudaStream_t s)
 {
-    cudaStream_t cs;
-    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    cudaEvent_t evs[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaError_t e = cudaSuccess;
-    for (auto& ev : evs)
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    const bool capturing = e == cudaSuccess;
-    const IterEvents ev{evs[0], evs[1], evs[2]};
-    // the particle streams join the capture; box forces and solve data of the
-    // first captured iteration are ready when the graph starts
-    if (e == cudaSuccess) e = cudaEventRecord(evs[3], cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, evs[3], 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux2, evs[3], 0);
-    if (e == cudaSuccess) e = cudaEventRecord(ev.crit, ctx->aux);
-    if (e == cudaSuccess) e = cudaEventRecord(ev.aux, ctx->aux2);
-    int c = parity;
-    for (int i = 0; e == cudaSuccess && i < GRAPH_ITERS; ++i) {
-        e = enqueue_iteration(ctx, 0, c, cs, ev);
-        c ^= 1;
+    BulkParams bulk[2];
+    BndParams bnd[2];
+    PParams part[2];
+    for (int c = 0; c < 2; ++c) {
+        bulk[c] = bulk_params(ctx, 0, c);
+        bnd[c] = bnd_params(ctx, 0, c);
+        part[c] = particle_params(ctx, c);
     }
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev.aux, 0);   // join the particle streams
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev.crit, 0);
-    if (capturing) {
-        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-        if (e == cudaSuccess) e = e2;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->gexec[parity], g, 0);
-    if (g) cudaGraphDestroy(g);
-    for (cudaEvent_t x : evs)
-        if (x) cudaEventDestroy(x);
-    cudaStreamDestroy(cs);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return cuda_fail(ctx, e, "graph capture");
-    }
-    return LB_OK;
+    cudaError_t e = cudaMemsetAsync(ctx->d_sync, 0, sizeof(unsigned) * (4 + (size_t)ctx->np), s);
+    if (e != cudaSuccess) return e;
+    return launch_step(bulk, bnd, part, ctx->d_sync, ctx->d_status, ctx->np, ctx->gx, ctx->total_blocks, k, cur,
+                       ctx->opt.precision, s);
 }
 
 extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
@@ -627,44 +563,30 @@ extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
     CK(cudaSetDevice(ctx->device));
     clear_stale_error();
     cudaStream_t s = pick(ctx, stream);
+    if (ctx->last_user_stream && ctx->last_user_stream != s) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     ctx->last_user_stream = s;
-    int left = nsteps;
     ctx->stepped = true;
-    const IterEvents ev = ctx_events(ctx);
+    int left = nsteps;
     if (!ctx->collided) {
-        CK(enqueue_iteration(ctx, 1, ctx->cur, s, ev));
+        CK(enqueue_iteration(ctx, 1, ctx->cur, s));
         ctx->cur ^= 1;
         ctx->collided = true;
         --left;
     }
-    const bool graphs = !(ctx->opt.flags & LB_FLAG_NO_GRAPH) && ctx->np > 0;
-    if (graphs && left >= GRAPH_ITERS && !ctx->gexec[ctx->cur]) {
-        // both parities at once, so that no capture happens inside a timed run later
-        lb_status st = build_graph(ctx, 0);
-        if (st == LB_OK) st = build_graph(ctx, 1);
-        if (st != LB_OK) return st;
+    const bool separate = (ctx->opt.flags & LB_FLAG_SEPARATE_KERNELS) != 0;
+    while (left > 0) {
+        if (separate) {
+            CK(enqueue_iteration(ctx, 0, ctx->cur, s));
+            ctx->cur ^= 1;
+            --left;
+        } else {
+            const int k = left < STEP_ITERS ? left : STEP_ITERS;
+            CK(enqueue_steps(ctx, k, ctx->cur, s));
+            ctx->cur ^= (k & 1);
+            left -= k;
+        }
     }
-    if (graphs && left >= GRAPH_ITERS) {
-        // the graph starts from a finished particle stream
-        CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
-        CK(cudaStreamWaitEvent(s, ctx->ev_crit, 0));
-    }
-    bool launched = false;
-    while (graphs && left >= GRAPH_ITERS) {
-        CK(cudaGraphLaunch(ctx->gexec[ctx->cur], s));   // joins its particle stream at the end
-        left -= GRAPH_ITERS;     // even count: parity unchanged
-        launched = true;
-    }
-    if (launched) {
-        CK(cudaEventRecord(ctx->ev_crit, s));
-        CK(cudaEventRecord(ctx->ev_aux, s));
-    }
-    for (; left > 0; --left) {
-        CK(enqueue_iteration(ctx, 0, ctx->cur, s, ev));
-        ctx->cur ^= 1;
-    }
-    CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));      // everything ordered on the caller's stream
-    CK(cudaStreamWaitEvent(s, ctx->ev_crit, 0));
+    CK(cudaEventRecord(ctx->ev_done, s));
     return LB_OK;
 }
 
@@ -675,10 +597,9 @@ extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, 
     CK(cudaSetDevice(ctx->device));
     clear_stale_error();
     cudaStream_t s = pick(ctx, stream);
+    if (ctx->last_user_stream && ctx->last_user_stream != s) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     ctx->last_user_stream = s;
     ctx->stepped = true;
-    CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
-    CK(cudaStreamWaitEvent(s, ctx->ev_crit, 0));
     cudaEvent_t ev[5];
     for (auto& e : ev) CK(cudaEventCreate(&e));
     double t[4] = {0, 0, 0, 0};
@@ -705,8 +626,7 @@ extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, 
         ctx->cur ^= 1;
         ctx->collided = true;
     }
-    CK(cudaEventRecord(ctx->ev_aux, s));
-    CK(cudaEventRecord(ctx->ev_crit, s));
+    CK(cudaEventRecord(ctx->ev_done, s));
     for (auto& e : ev) cudaEventDestroy(e);
     ms_out[0] = t[0];            // bulk
     ms_out[1] = t[1];            // boundary
@@ -754,7 +674,7 @@ extern "C" lb_status lb_get_fields(lb_ctx* ctx, int32_t box, uint32_t what, void
     if (what == LB_FIELD_RHO) k.out_rho = out;
     if (what == LB_FIELD_U) k.out_u = out;
     if (what == LB_FIELD_SOLID) k.out_solid = (int*)out;
-    CK(cudaStreamWaitEvent(s, ctx->ev_aux, 0));
+    CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     CK(launch_fields(k, ctx->opt.precision, B.nblocks, s));
     if (!direct) CK(cudaMemcpyAsync(dst, out, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -50,8 +50,8 @@ constexpr int KBLOCK = 256;         // threads per block of the lattice kernel
 constexpr int PBLOCK = 512;         // threads per block of the links read-back kernels
 constexpr int ABLOCK = 256;         // threads per block of the auxiliary particle kernel
 constexpr int MAXC = 4;             // particles a lattice tile may touch (field read-back)
-constexpr int BBLOCK = 128;         // threads per block of the boundary kernel
-constexpr int CBLOCK = 512;         // threads per block of the critical particle kernel
+constexpr int BBLOCK = 256;         // threads per block of the boundary kernel
+constexpr int CBLOCK = 256;         // threads per block of the critical particle kernel
 constexpr int MAXAMB = 512;         // near-surface nodes settled by the exact FP64 test per step
 
 // accumulator layout (int64 per particle); d = fixed-point f* of a link (x, b),
@@ -68,6 +68,7 @@ constexpr double FIXD = 70368744177664.0;
 constexpr unsigned ST_NAN = 1u;
 constexpr unsigned ST_CAPACITY = 2u;
 constexpr unsigned ST_OVERLAP = 4u;
+constexpr unsigned ST_TIMEOUT = 8u;  // a grid barrier of the step kernel gave up waiting
 
 // cube margin: h = ceil(max semi-axis) + CUBE_MARGIN, side S = 2h + 2, so the
 // solid nodes of this step and of the last one, grown by one link, stay inside

@@ -1,0 +1,782 @@
+// Critical and auxiliary particle blocks (see particle_kernel.cu for the
+// method), shared by the particle kernels and the persistent step kernel.
+#pragma once
+
+#include "lattice_common.cuh"
+
+namespace lbsph {
+
+// ---- exact FP64 inside test (no contraction: explicit round-to-nearest ops)
+__device__ inline void canon_rotate(const double q[4], const double s[3], double o[3])
+{
+    const double a = __dsub_rn(__dmul_rn(2.0, __dmul_rn(q[0], q[0])), 1.0);
+    const double qs = __dadd_rn(__dadd_rn(__dmul_rn(q[1], s[0]), __dmul_rn(q[2], s[1])), __dmul_rn(q[3], s[2]));
+    const double cx = __dsub_rn(__dmul_rn(q[2], s[2]), __dmul_rn(q[3], s[1]));
+    const double cy = __dsub_rn(__dmul_rn(q[3], s[0]), __dmul_rn(q[1], s[2]));
+    const double cz = __dsub_rn(__dmul_rn(q[1], s[1]), __dmul_rn(q[2], s[0]));
+    const double tqs = __dmul_rn(2.0, qs), tq0 = __dmul_rn(2.0, q[0]);
+    o[0] = __dadd_rn(__dadd_rn(__dmul_rn(a, s[0]), __dmul_rn(tqs, q[1])), __dmul_rn(tq0, cx));
+    o[1] = __dadd_rn(__dadd_rn(__dmul_rn(a, s[1]), __dmul_rn(tqs, q[2])), __dmul_rn(tq0, cy));
+    o[2] = __dadd_rn(__dadd_rn(__dmul_rn(a, s[2]), __dmul_rn(tqs, q[3])), __dmul_rn(tq0, cz));
+}
+
+__device__ inline void canon_shape(const double semi[3], const double q[4], double A[9], double e[3][3])
+{
+    double inv[3];
+    for (int m = 0; m < 3; ++m) {
+        double u[3] = {0.0, 0.0, 0.0};
+        u[m] = 1.0;
+        canon_rotate(q, u, e[m]);
+        inv[m] = __ddiv_rn(1.0, __dmul_rn(semi[m], semi[m]));
+    }
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k)
+            A[j * 3 + k] = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(e[0][j], e[0][k]), inv[0]),
+                                               __dmul_rn(__dmul_rn(e[1][j], e[1][k]), inv[1])),
+                                     __dmul_rn(__dmul_rn(e[2][j], e[2][k]), inv[2]));
+}
+
+__device__ __forceinline__ double canon_minimage(double d, int L, bool periodic)
+{
+    if (!periodic) return d;
+    const double Ld = (double)L;
+    // |d| <= L/2 - 1 puts d/L + 0.5 inside (0, 1) whatever the rounding, so the
+    // shift below is exactly zero and d comes back unchanged
+    if (fabs(d) <= 0.5 * Ld - 1.0) return d;
+    return __dsub_rn(d, __dmul_rn(Ld, floor(__dadd_rn(__ddiv_rn(d, Ld), 0.5))));
+}
+
+__device__ inline double canon_value(const double A[9], const double xc[3], int X, int Y, int Z, int nx, int ny,
+                              int nz, bool py)
+{
+    double d[3];
+    d[0] = canon_minimage(__dsub_rn((double)X, xc[0]), nx, true);
+    d[1] = canon_minimage(__dsub_rn((double)Y, xc[1]), ny, py);
+    d[2] = canon_minimage(__dsub_rn((double)Z, xc[2]), nz, true);
+    double Ad[3];
+    for (int j = 0; j < 3; ++j)
+        Ad[j] = __dadd_rn(__dadd_rn(__dmul_rn(A[j * 3 + 0], d[0]), __dmul_rn(A[j * 3 + 1], d[1])),
+                          __dmul_rn(A[j * 3 + 2], d[2]));
+    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], Ad[0]), __dmul_rn(d[1], Ad[1])), __dmul_rn(d[2], Ad[2]));
+}
+
+__device__ __forceinline__ int wrapi(int a, int L) { a %= L; return a < 0 ? a + L : a; }
+
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += (long long)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// The exact inside-test matrix A = sum_m e_m e_m^T / semi_m^2 of canon_shape,
+// spread over lanes 0..8 of one warp (same operations, same order per entry).
+__device__ inline void canon_shape_warp(const double inv[3], const double q[4], double* s_E, double* s_A, int lane)
+{
+    if (lane < 3) {
+        const double u[3] = {lane == 0 ? 1.0 : 0.0, lane == 1 ? 1.0 : 0.0, lane == 2 ? 1.0 : 0.0};
+        double o[3];
+        canon_rotate(q, u, o);
+        s_E[lane * 3 + 0] = o[0]; s_E[lane * 3 + 1] = o[1]; s_E[lane * 3 + 2] = o[2];
+    }
+    __syncwarp();
+    if (lane < 9) {
+        const int j = lane / 3, k = lane % 3;
+        s_A[lane] = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(s_E[j], s_E[k]), inv[0]),
+                                        __dmul_rn(__dmul_rn(s_E[3 + j], s_E[3 + k]), inv[1])),
+                              __dmul_rn(__dmul_rn(s_E[6 + j], s_E[6 + k]), inv[2]));
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// particle p; CBLOCK threads
+__device__ __forceinline__ void crit_block(const PParams& P, int p)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ PartDev S;
+    __shared__ PartK K;
+    __shared__ long long s_acc[NACC];
+    extern __shared__ uint64_t s_maps[];            // both ring slots of the occupancy map, smax*smax rows each
+    __shared__ double s_E[9], s_A[9], s_xc[3], s_dm;
+    __shared__ float s_e[3][3], s_inv[3], s_ro[3];
+    __shared__ int s_o[3], s_nsolid, s_namb;
+    __shared__ int s_amb[MAXAMB];
+
+    // ---- stage the state, the snapshot (so that every field not updated
+    // below carries over) and this step's accumulators; clear the accumulators
+    {
+        ldcg_copy(&S, P.pd + p, tid, CBLOCK);
+        ldcg_copy(&K, P.pk + p, tid, CBLOCK);
+        long long* acc = P.acc + (long long)p * NACC;
+        for (int e = tid; e < NACC; e += CBLOCK) {
+            s_acc[e] = __ldcg(acc + e);
+            acc[e] = 0;
+        }
+        const uint64_t* r0 = P.rows + (size_t)p * 2 * (MAXS * MAXS);
+        const int n = P.smax * P.smax;
+        for (int r = tid; r < n; r += CBLOCK) {
+            s_maps[r] = __ldcg(r0 + r);
+            s_maps[n + r] = __ldcg(r0 + MAXS * MAXS + r);
+        }
+        if (tid == 0) { s_nsolid = 0; s_namb = 0; s_dm = 0.0; }
+    }
+    __syncthreads();
+    const int slot_new = P.init ? 0 : (S.slot ^ 1);
+    uint64_t* s_rows = s_maps + slot_new * P.smax * P.smax;          // map t+1, built below
+    const uint64_t* s_old = s_maps + (P.init ? slot_new : S.slot) * P.smax * P.smax;   // map t
+    const int nx = K.nx, ny = K.ny, nz = K.nz;
+    const bool py = !K.walls;
+    const int Sd = S.S;
+
+    // ---- warp 0: force, solve, pose (lane k < 3: x/F component k, 3 <= lane < 6: torque component lane-3)
+    if (warp == 0 && !P.init) {
+        const double rho0 = K.rho0;
+        const double inv_fix = 1.0 / FIXD;
+        const int k = lane % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        const bool isT = lane >= 3;
+        // F0, T0 (Eq. F0, Eq. T0): this step's link sums about the cube origin,
+        // moved to the centre (phi x F for the torque), plus the parts the links
+        // alone fix; one branch-free expression for force and torque lanes
+        const double phi1 = isT ? S.phi[k1] : 0.0, phi2 = isT ? S.phi[k2] : 0.0;
+        const double a0 = (double)s_acc[isT ? ACC_T + k : ACC_F + k];
+        const double pxD = phi1 * (double)s_acc[ACC_F + k2] - phi2 * (double)s_acc[ACC_F + k1];
+        const double ft0 = 2.0 * ((pxD + a0) * inv_fix) + (isT ? S.T0g[k] : S.F0g[k]);
+        // impulse of the nodes covered / uncovered by the last remap (Appendix, step 8)
+        double dpl = 0.0;
+        const long long ncv = s_acc[ACC_COV], nun = s_acc[ACC_UNC];
+        if (ncv != 0 || nun != 0) {
+            const double* phi = S.phi;
+            const double Jk1 = (double)s_acc[ACC_COV + 2 + k1] * inv_fix, Jk2 = (double)s_acc[ACC_COV + 2 + k2] * inv_fix;
+            dpl = isT ? (phi[k1] * Jk2 - phi[k2] * Jk1) + (double)s_acc[ACC_COV + 5 + k] * inv_fix
+                      : (double)s_acc[ACC_COV + 2 + k] * inv_fix;
+            double dm = (double)ncv * rho0 + (double)s_acc[ACC_COV + 1] * inv_fix;
+            if (nun > 0) {
+                const double nu = (double)nun;
+                const double SM[3] = {(double)s_acc[ACC_UNC + 1], (double)s_acc[ACC_UNC + 2], (double)s_acc[ACC_UNC + 3]};
+                double Sr[3];
+                for (int a = 0; a < 3; ++a) Sr[a] = nu * phi[a] + SM[a];
+                if (!isT) {
+                    dpl -= rho0 * (nu * S.U[k] + (S.W[k1] * Sr[k2] - S.W[k2] * Sr[k1]));
+                } else {
+                    const int ui[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};
+                    auto RR = [&](int i, int j) {
+                        return nu * phi[i] * phi[j] + phi[i] * SM[j] + SM[i] * phi[j] + (double)s_acc[ACC_UNC + ui[i][j]];
+                    };
+                    const double tr = RR(0, 0) + RR(1, 1) + RR(2, 2);
+                    const double RRW = RR(k, 0) * S.W[0] + RR(k, 1) * S.W[1] + RR(k, 2) * S.W[2];
+                    const double SxU = Sr[k1] * S.U[k2] - Sr[k2] * S.U[k1];
+                    dpl -= rho0 * (SxU + S.W[k] * tr - RRW);
+                }
+                dm -= nu * rho0;
+            }
+            if (lane == 0) s_dm = dm;
+        }
+        // right-hand side of Eq. Fdiscrete / Eq. Tdiscrete (dt = 1), times the
+        // inverse the auxiliary kernel prepared from zeta, M, I and dI/dt
+        double rhs;
+        {
+            // force lanes: M U_k; torque lanes: (I Omega)_k
+            const double m0 = isT ? S.Icur[k * 3] : S.M, v0 = isT ? S.W[0] : S.U[k];
+            const double m1 = isT ? S.Icur[k * 3 + 1] : 0.0, m2 = isT ? S.Icur[k * 3 + 2] : 0.0;
+            rhs = m0 * v0 + m1 * S.W[1] + m2 * S.W[2] + ft0 + (isT ? S.Text[k] : S.Fext[k]) + dpl;
+        }
+        const int row = lane < 6 ? lane : 5;
+        double x6 = 0.0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) x6 += S.Ainv[row * 6 + j] * __shfl_sync(0xffffffffu, rhs, j);
+        // F = F0 - zeta_FU U' - zeta_FOmega Omega' (Eq. Fsplit), T likewise (Eq. Tsplit)
+        double xs[6], ft = ft0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            xs[j] = __shfl_sync(0xffffffffu, x6, j);
+            ft -= S.zeta[row * 6 + j] * xs[j];
+        }
+        // Eq. posupdate, Eq. qnplus0-1: rotation by Omega_mid = (Omega + Omega') / 2
+        double Wm[3];
+        for (int a = 0; a < 3; ++a) Wm[a] = 0.5 * (S.W[a] + xs[3 + a]);
+        const double th2 = Wm[0] * Wm[0] + Wm[1] * Wm[1] + Wm[2] * Wm[2];
+        double qt[4];
+        if (th2 < 1e-4) {
+            // cos(th/2) and sin(th/2)/th by their Taylor series (th < 0.01: error < 1e-20)
+            const double x2 = 0.25 * th2;
+            const double c = 1.0 - x2 * (0.5 - x2 * (1.0 / 24.0 - x2 * (1.0 / 720.0)));
+            const double sc = 0.5 * (1.0 - x2 * (1.0 / 6.0 - x2 * (1.0 / 120.0 - x2 * (1.0 / 5040.0))));
+            qt[0] = c; qt[1] = sc * Wm[0]; qt[2] = sc * Wm[1]; qt[3] = sc * Wm[2];
+        } else {
+            const double th = sqrt(th2);
+            double sn, cs;
+            sincos(0.5 * th, &sn, &cs);
+            sn /= th;
+            qt[0] = cs; qt[1] = sn * Wm[0]; qt[2] = sn * Wm[1]; qt[3] = sn * Wm[2];
+        }
+        // q' = qt q, component j on lane j: sum_m +-qt_m q_(m xor j), the sign
+        // applied by flipping the sign bit
+        constexpr unsigned NEG = (1u << 1) | (1u << 2) | (1u << 3) | (1u << 7) | (1u << 9) | (1u << 14);
+        const int jq = lane & 3;
+        double qn = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const unsigned long long sgn = (unsigned long long)((NEG >> (jq * 4 + m)) & 1u) << 63;
+            const double qs = __longlong_as_double(__double_as_longlong(qt[m]) ^ (long long)sgn);
+            qn = fma(qs, S.q[m ^ jq], qn);
+        }
+        // body x axis at t (the squirmer's axis for the next bounce-back):
+        // R_k0 = base + 2 (qa qb + s qc qd)
+        const double* q = S.q;
+        const double qa = q[k == 0 ? 2 : 1], qb = q[k == 0 ? 2 : (k == 1 ? 2 : 3)];
+        const double qc = q[k == 0 ? 3 : 0], qd = q[k == 0 ? 3 : (k == 1 ? 3 : 2)];
+        const double t2 = fma(k == 2 ? -qc : qc, qd, qa * qb);
+        const double ex = fma(k == 0 ? -2.0 : 2.0, t2, k == 0 ? 1.0 : 0.0);
+        const double xk = S.x[k], Uk = S.U[k], phik = S.phi[k];
+        const int ok = S.o[k];
+        const double ft0_t = __shfl_sync(0xffffffffu, ft0, 3 + k);
+        const double ft_t = __shfl_sync(0xffffffffu, ft, 3 + k);
+        __syncwarp();
+        if (lane < 3) {
+            const int L = k == 0 ? nx : (k == 1 ? ny : nz);
+            K.ow_old[k] = wrapi(ok, L);
+            K.ro_old[k] = (float)phik;
+            K.e_old[k] = (float)ex;
+            const double xn = xk + 0.5 * (Uk + xs[k]);
+            S.x[k] = xn;
+            S.U[k] = xs[k];
+            S.W[k] = xs[3 + k];
+            S.o_prev[k] = ok;
+            S.rec[k] = ft0; S.rec[3 + k] = ft0_t;
+            S.rec[6 + k] = ft; S.rec[9 + k] = ft_t;
+            S.rec[12 + k] = xs[k]; S.rec[15 + k] = xs[3 + k]; S.rec[18 + k] = xn;
+        }
+        if (lane < 4) { S.q[lane] = qn; S.rec[21 + lane] = qn; }
+        if (lane == 0) {
+            K.rows_old = P.rows + ((long long)p * 2 + S.slot) * (MAXS * MAXS);
+            K.dm_return = s_dm;
+        }
+        __syncwarp();
+        if (lane < 25) {
+            // exponent all ones: Inf or NaN
+            const unsigned long long b = (unsigned long long)__double_as_longlong(S.rec[lane]);
+            if (((b >> 52) & 0x7ff) == 0x7ff) atomicOr(P.status, ST_NAN);
+        }
+    } else if (warp == 0 && lane == 0) {
+        // initial pose: no remap before, nothing to return
+        for (int k = 0; k < 3; ++k) {
+            S.rec[12 + k] = S.U[k]; S.rec[15 + k] = S.W[k]; S.rec[18 + k] = S.x[k];
+            S.rec[k] = S.rec[3 + k] = S.rec[6 + k] = S.rec[9 + k] = 0.0;
+            S.inv_semi2[k] = __ddiv_rn(1.0, __dmul_rn(S.semi[k], S.semi[k]));
+        }
+        for (int k = 0; k < 4; ++k) S.rec[21 + k] = S.q[k];
+        K.dm_return = 0.0;
+    }
+    __syncwarp();
+
+    // ---- the new pose: cube origin and FP32 data of the inside test (warp 0)
+    if (warp == 0) {
+        if (lane < 3) {
+            const int o = (int)floor(S.x[lane]) - S.h;
+            s_o[lane] = o;
+            s_xc[lane] = S.x[lane];
+            s_ro[lane] = (float)((double)o - S.x[lane]);
+            s_inv[lane] = (float)S.inv_semi2[lane];
+        } else if (lane == 3) {
+            const double* q = S.q;
+            const float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+            // body axes e_m = R(q) u_m in FP32 (the FP32 test only needs ~1e-6)
+            const float Rf[9] = {1.f - 2.f * (qf[2] * qf[2] + qf[3] * qf[3]), 2.f * (qf[1] * qf[2] - qf[0] * qf[3]),
+                                 2.f * (qf[1] * qf[3] + qf[0] * qf[2]), 2.f * (qf[1] * qf[2] + qf[0] * qf[3]),
+                                 1.f - 2.f * (qf[1] * qf[1] + qf[3] * qf[3]), 2.f * (qf[2] * qf[3] - qf[0] * qf[1]),
+                                 2.f * (qf[1] * qf[3] - qf[0] * qf[2]), 2.f * (qf[2] * qf[3] + qf[0] * qf[1]),
+                                 1.f - 2.f * (qf[1] * qf[1] + qf[2] * qf[2])};
+            for (int m = 0; m < 3; ++m)
+                for (int j = 0; j < 3; ++j) s_e[m][j] = Rf[j * 3 + m];
+        }
+    }
+    __syncthreads();
+
+    // ---- occupancy of the new pose: one row per thread, FP32 test per node,
+    // near-surface nodes listed for the exact test
+    for (int r = tid; r < Sd * Sd; r += CBLOCK) {
+        const int my = r % Sd, mz = r / Sd;
+        const float dy = s_ro[1] + my, dz = s_ro[2] + mz;
+        const float t0 = s_e[0][1] * dy + s_e[0][2] * dz;
+        const float t1 = s_e[1][1] * dy + s_e[1][2] * dz;
+        const float t2 = s_e[2][1] * dy + s_e[2][2] * dz;
+        uint64_t word = 0;
+        for (int mx = 0; mx < Sd; ++mx) {
+            // evaluated from dx directly, not accumulated, so rounding does not grow along the row
+            const float dx = s_ro[0] + mx;
+            const float u0 = s_e[0][0] * dx + t0;
+            const float u1 = s_e[1][0] * dx + t1;
+            const float u2 = s_e[2][0] * dx + t2;
+            const float v = u0 * u0 * s_inv[0] + u1 * u1 * s_inv[1] + u2 * u2 * s_inv[2];
+            if (fabsf(v - 1.0f) > 1e-4f) {
+                if (v < 1.0f) word |= 1ull << mx;
+            } else {
+                const int slot = atomicAdd(&s_namb, 1);
+                if (slot < MAXAMB) s_amb[slot] = (mz << 16) | (my << 8) | mx;
+            }
+        }
+        s_rows[r] = word;
+    }
+    __syncthreads();
+    const int namb = s_namb;
+    if (namb > 0) {
+        // exact FP64 test in the oracle's operation order, only for listed nodes
+        if (warp == 0) canon_shape_warp(S.inv_semi2, S.q, s_E, s_A, lane);
+        if (tid == 0 && namb > MAXAMB) atomicOr(P.status, ST_CAPACITY);
+        __syncthreads();
+        for (int a = tid; a < min(namb, MAXAMB); a += CBLOCK) {
+            const int code = s_amb[a];
+            const int mx = code & 0xff, my = (code >> 8) & 0xff, mz = (code >> 16) & 0xff;
+            const int Xw = wrapi(s_o[0] + mx, nx), Yw = wrapi(s_o[1] + my, ny), Zw = wrapi(s_o[2] + mz, nz);
+            if (canon_value(s_A, s_xc, Xw, Yw, Zw, nx, ny, nz, py) <= 1.0)
+                atomicOr(reinterpret_cast<unsigned long long*>(&s_rows[mz * Sd + my]), 1ull << mx);
+        }
+        __syncthreads();
+    }
+    // ---- publish the map, count solid nodes, reject walls inside the particle
+    uint64_t* rows_new = P.rows + ((long long)p * 2 + slot_new) * (MAXS * MAXS);
+    {
+        int ns = 0;
+        for (int r = tid; r < Sd * Sd; r += CBLOCK) {
+            uint64_t word = s_rows[r];
+            const int Yu = s_o[1] + r % Sd;
+            if (!py && (Yu <= 0 || Yu >= ny - 1) && word) {
+                atomicOr(P.status, ST_OVERLAP);
+                word = 0;
+                s_rows[r] = 0;
+            }
+            rows_new[r] = word;
+            ns += __popcll(word);
+        }
+        ns = __reduce_add_sync(0xffffffffu, ns);
+        if (lane == 0 && ns) atomicAdd(&s_nsolid, ns);
+    }
+    __syncthreads();
+    // ---- redo mask of step t+1 in the new cube: nodes fluid now with a solid
+    // neighbour now or before, or solid before (uncovered), and nodes covered now;
+    // the bulk kernel of t+1 skips them and the boundary kernel writes them
+    {
+        int dsh[3];                                 // new origin - old origin: old-local = new-local + dsh
+        for (int k = 0; k < 3; ++k) dsh[k] = P.init ? 0 : s_o[k] - S.o[k];
+        if (tid == 0 && (abs(dsh[0]) > 1 || abs(dsh[1]) > 1 || abs(dsh[2]) > 1)) atomicOr(P.status, ST_CAPACITY);
+        const uint64_t maskS = Sd >= 64 ? ~0ull : ((1ull << Sd) - 1ull);
+        auto row_old = [&](int ay, int az) -> uint64_t {
+            ay += dsh[1]; az += dsh[2];
+            if (ay < 0 || ay >= Sd || az < 0 || az >= Sd) return 0ull;
+            const uint64_t w = s_old[az * Sd + ay];
+            return (dsh[0] == 1 ? (w >> 1) : (dsh[0] == -1 ? (w << 1) : w)) & maskS;
+        };
+        uint64_t* need = P.need + (size_t)p * (MAXS * MAXS);
+        for (int r = tid; r < Sd * Sd; r += CBLOCK) {
+            const int my = r % Sd, mz = r / Sd;
+            const int Yu = s_o[1] + my;
+            uint64_t nd = 0;
+            if (py || (Yu > 0 && Yu < ny - 1)) {
+                uint64_t dil = 0;
+#pragma unroll
+                for (int b = 1; b < Q; ++b) {
+                    const int ay = my + cy_of(b), az = mz + cz_of(b);
+                    if (ay < 0 || ay >= Sd || az < 0 || az >= Sd) continue;
+                    const uint64_t nb = s_rows[az * Sd + ay] | row_old(ay, az);
+                    dil |= cx_of(b) == 1 ? (nb >> 1) : (cx_of(b) == -1 ? (nb << 1) : nb);
+                }
+                const uint64_t nw = s_rows[r], od = row_old(my, mz);
+                nd = (((dil | od) & ~nw) | (nw & ~od)) & maskS;
+            }
+            need[r] = nd;
+        }
+        if (tid == 0) {
+            NeedHdr h;
+            for (int k = 0; k < 3; ++k) h.ow[k] = wrapi(s_o[k], k == 0 ? nx : (k == 1 ? ny : nz));
+            h.S = Sd;
+            P.need_hdr[p] = h;
+        }
+    }
+    if (tid == 0) {
+        K.rows_new = rows_new;
+        K.oy_new = s_o[1];
+        for (int k = 0; k < 3; ++k) {
+            K.ow_new[k] = wrapi(s_o[k], k == 0 ? nx : (k == 1 ? ny : nz));
+            K.ro_new[k] = s_ro[k];
+            K.U[k] = (float)S.U[k];
+            K.W[k] = (float)S.W[k];
+            K.Fext[k] = S.Fext[k];
+        }
+        K.S = Sd;
+        K.nsolid = s_nsolid;
+        if (P.init) {
+            K.rows_old = rows_new;
+            for (int k = 0; k < 3; ++k) {
+                K.ow_old[k] = K.ow_new[k];
+                K.ro_old[k] = K.ro_new[k];
+                K.e_old[k] = s_e[0][k];
+                S.o_prev[k] = s_o[k];
+            }
+        }
+        S.slot = slot_new;
+        for (int k = 0; k < 3; ++k) S.o[k] = s_o[k];
+        S.nsolid = s_nsolid;
+        if (!P.init) S.step += 1;
+        if (Sd > nx || Sd > nz || (py && Sd > ny)) atomicOr(P.status, ST_CAPACITY);
+    }
+    __syncthreads();
+    // ---- write back
+    {
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&S);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(P.pd + p);
+        for (int e = tid; e < (int)(sizeof(PartDev) / 8); e += CBLOCK) dst[e] = src[e];
+        const unsigned* ks = reinterpret_cast<const unsigned*>(&K);
+        unsigned* kd = reinterpret_cast<unsigned*>(P.pk + p);
+        for (int e = tid; e < (int)(sizeof(PartK) / 4); e += CBLOCK) kd[e] = ks[e];
+    }
+    // ---- the box's uniform terms of the next collision: body force with the
+    // counter force over the fluid nodes, and the mass put back
+    auto box_terms = [&](double fx, double fy, double fz, double dm, long long ns) {
+        const float nf = (float)(K.N - K.nwall - ns);
+        const float inf = nf > 0.0f ? 1.0f / nf : 0.0f;
+        BoxDyn d;
+        d.g[0] = K.body[0] - (K.counter ? (float)fx * inf : 0.0f);
+        d.g[1] = K.body[1] - (K.counter ? (float)fy * inf : 0.0f);
+        d.g[2] = K.body[2] - (K.counter ? (float)fz * inf : 0.0f);
+        d.eps = (float)dm * inf;
+        return d;
+    };
+    if (K.pcnt == 1) {
+        // the only particle of its box: no other block to wait for
+        if (tid == 0) {
+            const BoxDyn d = box_terms(K.Fext[0], K.Fext[1], K.Fext[2], K.dm_return, K.nsolid);
+            P.box_dyn[K.box] = d;
+            P.pdyn[p] = d;
+        }
+        return;
+    }
+    // several particles: the last block of the box sums them
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const int prev = atomicAdd(P.box_done + K.box, 1);
+        if (prev == K.pcnt - 1) {
+            __threadfence();
+            double fx = 0, fy = 0, fz = 0, dm = 0;
+            long long ns = 0;
+            for (int i = 0; i < K.pcnt; ++i) {
+                const volatile PartK& k = P.pk[K.pbeg + i];
+                fx += k.Fext[0]; fy += k.Fext[1]; fz += k.Fext[2];
+                dm += k.dm_return;
+                ns += k.nsolid;
+            }
+            const BoxDyn d = box_terms(fx, fy, fz, dm, ns);
+            P.box_dyn[K.box] = d;
+            for (int i = 0; i < K.pcnt; ++i) P.pdyn[K.pbeg + i] = d;
+            P.box_done[K.box] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// D3Q19 velocity components packed two bits per direction (value + 1), so that
+// a rolled loop over directions stays small in the instruction cache
+__host__ __device__ constexpr unsigned long long pack_c(int comp)
+{
+    unsigned long long v = 0;
+    for (int b = 0; b < Q; ++b) v |= (unsigned long long)((comp == 0 ? cx_of(b) : (comp == 1 ? cy_of(b) : cz_of(b))) + 1) << (2 * b);
+    return v;
+}
+__device__ __forceinline__ int c_of(unsigned long long packed, int b) { return (int)((packed >> (2 * b)) & 3ull) - 1; }
+
+// Auxiliary particle kernel, after the critical one of iteration t and before
+// the critical one of t+1: everything the next solve needs that depends only
+// on the new pose and map.
+//   - the drag matrix (Eq. drag1-drag4).  Per link g = (c_b, r_b x c_b) and
+//     zeta = sum_b (2 rho0 w_b / c_s^2) g g^T.  With r_b = phi + m (phi = cube
+//     origin - x_c; the -c_b/2 drops out of r_b x c_b) g = T g0, g0 = (c_b,
+//     m x c_b), T = [[1, 0], [phi x, 1]], so zeta = T zeta0 T^T where zeta0 =
+//     (rho0 / 6) sum_links 36 w_b g0 g0^T is an exact integer sum.  Along a
+//     cube row y, z are fixed and m x c_b = alpha + beta x, so a row adds its
+//     link count n, sum x and sum x^2 per direction;
+//   - the same integer sums give the geometric parts of F0 and T0 (Eq. F0,
+//     Eq. T0); squirmer links add their slip (Eq. ubsquirmer) one by one;
+//   - the lab-frame inertia and its rate at t+1 (Eq. Irot, Eq. Irotdiff, or
+//     the finite difference), and the inverse of the implicit-solve matrix
+//     [[M + zeta_FU, zeta_FOmega], [zeta_TU, I + dI/dt + zeta_TOmega]] by
+//     Gauss-Jordan elimination with partial pivoting, one column per lane.
+constexpr int NSUM = 27;            // zeta0: FU 6, FOmega 9, TOmega 6; sum w n c 3; sum w m x c 3
+// particle p; ABLOCK threads
+__device__ __forceinline__ void aux_block(const PParams& P, int p)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    PartDev& G = P.pd[p];
+    extern __shared__ uint64_t s_new[];
+    __shared__ PartDev S;
+    __shared__ long long s_sum[NSUM], s_slip[6];
+    __shared__ double s_R[9], s_I[9], s_dI[9], s_P[36], s_Z[36];
+    __shared__ float s_ro[3], s_ex[3];
+    {
+        ldcg_copy(&S, P.pd + p, tid, ABLOCK);
+        if (tid < NSUM) s_sum[tid] = 0;
+        if (tid >= 32 && tid < 38) s_slip[tid - 32] = 0;
+    }
+    __syncthreads();
+    const BoxDev& B = P.boxes[S.box];
+    const int ny = B.ny;
+    const bool walls = B.walls != 0;
+    const double rho0 = B.rho0;
+    const int Sd = S.S;
+    const uint64_t maskS = Sd >= 64 ? ~0ull : ((1ull << Sd) - 1ull);
+    if (tid < 3) {
+        const double ph = (double)S.o[tid] - S.x[tid];
+        G.phi[tid] = ph;
+        s_ro[tid] = (float)ph;
+    }
+    if (warp == 1 && lane < 9) {
+        // rotation matrix at t+1 (body -> lab)
+        const double* q = S.q;
+        const int i = lane / 3, j = lane % 3;
+        double r;
+        if (i == j) {
+            const double a = q[1 + (i + 1) % 3], bq = q[1 + (i + 2) % 3];
+            r = 1.0 - 2.0 * (a * a + bq * bq);
+        } else {
+            const int kk = 3 - i - j;
+            const double sgn = ((j - i + 3) % 3 == 1) ? -1.0 : 1.0;
+            r = 2.0 * (q[1 + i] * q[1 + j] + sgn * q[0] * q[1 + kk]);
+        }
+        s_R[lane] = r;
+        if (j == 0) s_ex[i] = (float)r;
+    }
+    {
+        const uint64_t* rn = P.rows + ((long long)p * 2 + S.slot) * (MAXS * MAXS);
+        for (int r = tid; r < Sd * Sd; r += ABLOCK) s_new[r] = __ldcg(rn + r);
+    }
+    __syncthreads();
+
+    // ---- integer link sums of the new map, one cube row per thread; the
+    // direction loop is unrolled so that every c_b is a constant and the 27
+    // sums stay in registers
+    const bool squirmer = (S.B1 != 0.0 || S.B2 != 0.0);
+    {
+        int fu0 = 0, fu1 = 0, fu2 = 0, fu3 = 0, fu4 = 0, fu5 = 0;                 // FU: xx xy xz yy yz zz
+        int fo[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};                                   // FOmega[i][j]
+        int to0 = 0, to1 = 0, to2 = 0, to3 = 0, to4 = 0, to5 = 0;                 // TOmega: xx xy xz yy yz zz
+        int g0 = 0, g1 = 0, g2 = 0, gm0 = 0, gm1 = 0, gm2 = 0;                    // sum w n c, sum w m x c
+        for (int r = tid; r < Sd * Sd; r += ABLOCK) {
+            const int my = r % Sd, mz = r / Sd;
+            const int Yu = S.o[1] + my;
+            if (walls && (Yu <= 0 || Yu >= ny - 1)) continue;
+            const uint64_t fluid = ~s_new[r] & maskS;
+#pragma unroll
+            for (int b = 1; b < Q; ++b) {
+                const int cx = cx_of(b), cy = cy_of(b), cz = cz_of(b);
+                const int ay = my + cy, az = mz + cz;
+                if (ay < 0 || ay >= Sd || az < 0 || az >= Sd) continue;
+                const uint64_t nb = s_new[az * Sd + ay];
+                uint64_t L = fluid & (cx == 1 ? (nb >> 1) : (cx == -1 ? (nb << 1) : nb));
+                if (!L) continue;
+                const int kw = b <= 6 ? 2 : 1;               // 36 w_b
+                const int n = __popcll(L);
+                int sx = 0, sxx = 0;
+                while (L) {
+                    const int mx = __ffsll((long long)L) - 1;
+                    L &= L - 1;
+                    sx += mx;
+                    sxx += mx * mx;
+                }
+                // m x c = alpha + beta x along the row
+                const int a0 = my * cz - mz * cy, a1 = mz * cx, a2 = -my * cx;
+                const int b1 = -cz, b2 = cy;
+                const int v0 = a0 * n, v1 = a1 * n + b1 * sx, v2 = a2 * n + b2 * sx;
+                fu0 += kw * n * cx * cx; fu1 += kw * n * cx * cy; fu2 += kw * n * cx * cz;
+                fu3 += kw * n * cy * cy; fu4 += kw * n * cy * cz; fu5 += kw * n * cz * cz;
+                fo[0] += kw * cx * v0; fo[1] += kw * cx * v1; fo[2] += kw * cx * v2;
+                fo[3] += kw * cy * v0; fo[4] += kw * cy * v1; fo[5] += kw * cy * v2;
+                fo[6] += kw * cz * v0; fo[7] += kw * cz * v1; fo[8] += kw * cz * v2;
+                to0 += kw * a0 * a0 * n;
+                to1 += kw * (a0 * a1 * n + a0 * b1 * sx);
+                to2 += kw * (a0 * a2 * n + a0 * b2 * sx);
+                to3 += kw * (a1 * a1 * n + 2 * a1 * b1 * sx + b1 * b1 * sxx);
+                to4 += kw * (a1 * a2 * n + (a1 * b2 + a2 * b1) * sx + b1 * b2 * sxx);
+                to5 += kw * (a2 * a2 * n + 2 * a2 * b2 * sx + b2 * b2 * sxx);
+                g0 += kw * n * cx; g1 += kw * n * cy; g2 += kw * n * cz;
+                gm0 += kw * v0; gm1 += kw * v1; gm2 += kw * v2;
+            }
+        }
+        const int acc[NSUM] = {fu0, fu1, fu2, fu3, fu4, fu5, fo[0], fo[1], fo[2], fo[3], fo[4], fo[5], fo[6], fo[7], fo[8],
+                               to0, to1, to2, to3, to4, to5, g0, g1, g2, gm0, gm1, gm2};
+#pragma unroll
+        for (int k = 0; k < NSUM; ++k) {
+            const long long v = (k >= 15 && k < 21) ? warp_sum_ll(acc[k]) : (long long)__reduce_add_sync(0xffffffffu, acc[k]);
+            if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long*>(&s_sum[k]), (unsigned long long)v);
+        }
+    }
+    if (squirmer) {
+        // squirmer slip (Eq. ubsquirmer) at every link: sum w s c and sum w s (m x c)
+        constexpr unsigned long long PX = pack_c(0), PY = pack_c(1), PZ = pack_c(2);
+        long long sl[6] = {0, 0, 0, 0, 0, 0};
+        const float sa = (float)S.semi[0];
+        const float seps2 = (float)fmax(0.0, 1.0 - (S.semi[1] * S.semi[1]) / (S.semi[0] * S.semi[0]));
+        const float sB1 = (float)S.B1, sB2 = (float)S.B2;
+        for (int r = tid; r < Sd * Sd; r += ABLOCK) {
+            const int my = r % Sd, mz = r / Sd;
+            const int Yu = S.o[1] + my;
+            if (walls && (Yu <= 0 || Yu >= ny - 1)) continue;
+            const uint64_t fluid = ~s_new[r] & maskS;
+#pragma unroll 1
+            for (int b = 1; b < Q; ++b) {
+                const int cx = c_of(PX, b), cy = c_of(PY, b), cz = c_of(PZ, b);
+                const int ay = my + cy, az = mz + cz;
+                if (ay < 0 || ay >= Sd || az < 0 || az >= Sd) continue;
+                const uint64_t nb = s_new[az * Sd + ay];
+                uint64_t L = fluid & (cx == 1 ? (nb >> 1) : (cx == -1 ? (nb << 1) : nb));
+                const int kw = b <= 6 ? 2 : 1;
+                while (L) {
+                    const int mx = __ffsll((long long)L) - 1;
+                    L &= L - 1;
+                    const float rx = s_ro[0] + mx + 0.5f * cx, ry = s_ro[1] + my + 0.5f * cy, rz = s_ro[2] + mz + 0.5f * cz;
+                    float ux, uy, uz;
+                    squirmer_slip(s_ex, sa, seps2, sB1, sB2, rx, ry, rz, ux, uy, uz);
+                    const long long sv = kw * __float2ll_rn((ux * cx + uy * cy + uz * cz) * FIXF);
+                    sl[0] += sv * cx; sl[1] += sv * cy; sl[2] += sv * cz;
+                    sl[3] += sv * (my * cz - mz * cy); sl[4] += sv * (mz * cx - mx * cz); sl[5] += sv * (mx * cy - my * cx);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const long long v = warp_sum_ll(sl[k]);
+            if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long*>(&s_slip[k]), (unsigned long long)v);
+        }
+    }
+    if (warp == 2 && lane < 9) {
+        // lab-frame inertia at t+1 (Eq. Irot): I = R diag(I_body) R^T
+        const int i = lane / 3, j = lane % 3;
+        s_I[lane] = s_R[i * 3] * S.Ib[0] * s_R[j * 3] + s_R[i * 3 + 1] * S.Ib[1] * s_R[j * 3 + 1] +
+                    s_R[i * 3 + 2] * S.Ib[2] * s_R[j * 3 + 2];
+    }
+    __syncthreads();
+
+    // ---- P = T zeta0, the inertia rate, the fixed parts of F0 and T0
+    double phi[3];
+    for (int a = 0; a < 3; ++a) phi[a] = (double)S.o[a] - S.x[a];
+    auto z0 = [&](int i, int j) -> double {        // zeta0 / (rho0 / 6) from the packed sums
+        constexpr int sym[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+        if (i < 3 && j < 3) return (double)s_sum[sym[i][j]];
+        if (i < 3) return (double)s_sum[6 + i * 3 + (j - 3)];
+        if (j < 3) return (double)s_sum[6 + j * 3 + (i - 3)];
+        return (double)s_sum[15 + sym[i - 3][j - 3]];
+    };
+    if (tid < 36) {
+        // rows 3..5 of P gain [phi x] times rows 0..2
+        const int i = tid / 6, j = tid % 6;
+        double v = z0(i, j);
+        if (i >= 3) {
+            const int a = i - 3, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+            v += -phi[a2] * z0(a1, j) + phi[a1] * z0(a2, j);
+        }
+        s_P[tid] = v;
+    } else if (warp == 2 && lane < 9) {
+        // its rate (Eq. Irotdiff): [Omega]x I - I [Omega]x, or the finite difference
+        const int i = lane / 3, j = lane % 3;
+        if (P.didt_mode == 0) {
+            const double* W = S.W;
+            const double Wk[9] = {0, -W[2], W[1], W[2], 0, -W[0], -W[1], W[0], 0};
+            s_dI[lane] = Wk[i * 3] * s_I[j] + Wk[i * 3 + 1] * s_I[3 + j] + Wk[i * 3 + 2] * s_I[6 + j] -
+                         (s_I[i * 3] * Wk[j] + s_I[i * 3 + 1] * Wk[3 + j] + s_I[i * 3 + 2] * Wk[6 + j]);
+        } else {
+            s_dI[lane] = P.init ? 0.0 : s_I[lane] - S.Icur[lane];
+        }
+    } else if (warp == 3 && lane < 6) {
+        // F0, T0 parts fixed by the links: 2 rho0 sum w_b c_b (geometric) and the
+        // squirmer slip, about the centre (Eq. F0, Eq. T0)
+        const double inv_fix = 1.0 / FIXD;
+        constexpr double i36 = 1.0 / 36.0;
+        const double fix36 = inv_fix * i36;
+        const int k = lane % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        const long long* Gs = s_sum + 21;     // [0..2] sum w n c, [3..5] sum w m x c
+        if (lane < 3) {
+            G.F0g[k] = 2.0 * rho0 * ((double)Gs[k] * i36) - 6.0 * rho0 * ((double)s_slip[k] * fix36);
+        } else {
+            const double pxG = (phi[k1] * (double)Gs[k2] - phi[k2] * (double)Gs[k1]) * i36;
+            const double pxS = (phi[k1] * (double)s_slip[k2] - phi[k2] * (double)s_slip[k1]) * fix36;
+            G.T0g[k] = 2.0 * rho0 * (pxG + (double)Gs[3 + k] * i36) - 6.0 * rho0 * (pxS + (double)s_slip[3 + k] * fix36);
+        }
+    }
+    __syncthreads();
+    // ---- zeta = (rho0 / 6) P T^T
+    if (tid < 36) {
+        // columns 3..5 gain P times [phi x]^T
+        const int i = tid / 6, j = tid % 6;
+        double v = s_P[tid];
+        if (j >= 3) {
+            const int b = j - 3, b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+            v += -phi[b2] * s_P[i * 6 + b1] + phi[b1] * s_P[i * 6 + b2];
+        }
+        v *= rho0 * (1.0 / 6.0);
+        s_Z[tid] = v;
+        G.zeta[tid] = v;
+    }
+    __syncthreads();
+    // ---- inverse of the solve matrix A = [[M + zeta_FU, zeta_FOmega], [zeta_TU, I + dI/dt + zeta_TOmega]]
+    if (warp == 0) {
+        // Gauss-Jordan on [A | 1], column j on lane j (lanes 12..31 idle copies)
+        double col[6];
+        const int j = lane < 12 ? lane : 11;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double v;
+            if (j < 6) {
+                v = s_Z[i * 6 + j];
+                if (i == j && i < 3) v += S.M;
+                if (i >= 3 && j >= 3) v += s_I[(i - 3) * 3 + (j - 3)] + s_dI[(i - 3) * 3 + (j - 3)];
+            } else {
+                v = (i == j - 6) ? 1.0 : 0.0;
+            }
+            col[i] = v;
+        }
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            int piv = k;
+            if (lane == k) {
+                unsigned long long best = abs_bits(col[k]);
+#pragma unroll
+                for (int i = k + 1; i < 6; ++i) {
+                    const unsigned long long bi = abs_bits(col[i]);
+                    if (bi > best) { best = bi; piv = i; }
+                }
+            }
+            piv = __shfl_sync(0xffffffffu, piv, k);
+            double rowk = col[k], rowp = col[k];
+#pragma unroll
+            for (int i = k + 1; i < 6; ++i)
+                if (i == piv) rowp = col[i];
+#pragma unroll
+            for (int i = k + 1; i < 6; ++i)
+                if (i == piv) col[i] = rowk;
+            col[k] = rowp;
+            const double pv = __shfl_sync(0xffffffffu, col[k], k);
+            ok = ok && (pv != 0.0);
+            col[k] *= 1.0 / pv;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                if (i == k) continue;
+                const double fi = __shfl_sync(0xffffffffu, col[i], k);
+                col[i] -= fi * col[k];
+            }
+        }
+        if (lane >= 6 && lane < 12) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) G.Ainv[i * 6 + (lane - 6)] = col[i];
+        }
+        if (lane == 0 && !ok) atomicOr(P.status, ST_NAN);
+    } else if (warp == 1 && lane < 9) {
+        G.Icur[lane] = s_I[lane];
+    }
+}
+
+}  // namespace lbsph

@@ -1,0 +1,188 @@
+// Persistent step kernel: many iterations of the method in one cooperative
+// launch, so that no step pays kernel launches, stream hand-offs or a cold
+// instruction cache on the SMs that take the particle work.
+//
+// Each iteration (two 256-thread blocks per SM, all resident by the
+// cooperative launch):
+//   - particle items, gx + 1 per particle, on fixed blocks ranked by SM, so
+//     that they fill whole SMs (no bulk traffic next to them while they run)
+//     and the same SMs keep their code cached from step to step: gx boundary
+//     chunks of step t (the
+//     nodes next to the particle's surface, boundary_block.cuh) and the
+//     auxiliary block of step t-1 (drag matrix and inverse of the solve of
+//     step t); the last of the particle's items to finish goes on with its
+//     critical block (force, implicit solve, pose, new occupancy, redo masks
+//     and box terms of step t+1);
+//   - bulk tiles (bulk_tile.cuh), every other node of every box, taken by all
+//     blocks from a counter; the next tile is fetched while one runs.
+// A grid barrier ends the iteration: after it the lattice of step t, the box
+// terms and the redo masks of step t+1 are complete.  The auxiliary block of
+// the last iteration runs after the loop.
+//
+// Cross-block data are read through L2 (ld.global.cg, see lattice_common.cuh).
+// Every wait is bounded: a barrier that waits longer than SPIN_LIMIT polls
+// sets ST_TIMEOUT in the status word, and every block leaves the kernel at the
+// next barrier it reaches.
+#include "boundary_block.cuh"
+#include "bulk_tile.cuh"
+#include "particle_blocks.cuh"
+
+namespace lbsph {
+
+constexpr int SYNC_BAR = 0;          // barrier arrivals
+constexpr int SYNC_GEN = 1;          // barrier generation
+constexpr int SYNC_WORK = 2;         // work counter of the current iteration
+constexpr int SYNC_PART = 4;         // + p: items of particle p done in this iteration
+constexpr int SYNC_WORDS_FIXED = 4;  // then np particle words, then MAX_GRID block SM ids
+constexpr int MAX_GRID = 4096;
+constexpr long long SPIN_LIMIT = 1ll << 24;   // polls of about 100 ns: under 2 s
+
+struct StepParams {
+    BulkParams bulk[2];              // by buffer parity of the iteration
+    BndParams bnd[2];
+    PParams part[2];
+    unsigned* sync;                  // SYNC_PART + np words, zero at launch, then the blocks' SM ids
+    unsigned* status;
+    int np, gx, tiles, iters, cur0;
+};
+
+__device__ __forceinline__ bool grid_barrier(const StepParams& SP)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = SP.sync + SYNC_GEN;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(SP.sync + SYNC_BAR, 1u) == gridDim.x - 1) {
+            // last to arrive: reset the counters of the next iteration, then release
+            SP.sync[SYNC_BAR] = 0;
+            SP.sync[SYNC_WORK] = 0;
+            __threadfence();
+            atomicExch(SP.sync + SYNC_GEN, g + 1);
+        } else {
+            long long n = 0;
+            while (*gen == g) {
+                if (++n > SPIN_LIMIT) {
+                    atomicOr(SP.status, ST_TIMEOUT);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = (*reinterpret_cast<volatile unsigned*>(SP.status) & ST_TIMEOUT) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class St>
+__global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__ StepParams SP)
+{
+    __shared__ int s_item[2];
+    __shared__ int s_last, s_rank;
+    const int tid = threadIdx.x;
+    const int gx = SP.gx;
+    const int npart = SP.np * (gx + 1);
+    // ---- rank of this block by (SM, block index): particle items go to whole SMs
+    unsigned* blk_sm = SP.sync + SYNC_PART + SP.np;
+    if (tid == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        blk_sm[blockIdx.x] = smid;
+        s_rank = 0;
+    }
+    if (!grid_barrier(SP)) return;
+    {
+        const unsigned mine = __ldcg(blk_sm + blockIdx.x);
+        int before = 0;
+        for (int b = tid; b < (int)gridDim.x; b += KBLOCK) {
+            const unsigned o = __ldcg(blk_sm + b);
+            before += (o < mine) || (o == mine && b < (int)blockIdx.x);
+        }
+        if (before) atomicAdd(&s_rank, before);
+    }
+    __syncthreads();
+    const int prank = s_rank;
+    for (int it = 0; it < SP.iters; ++it) {
+        const int cur = (SP.cur0 + it) & 1;
+        const BulkParams& BP = SP.bulk[cur];
+        const BndParams& NP = SP.bnd[cur];
+        const PParams& PP = SP.part[cur];
+        // ---- particle items
+        for (int item = prank; item < npart; item += gridDim.x) {
+            const int p = item / (gx + 1), c = item % (gx + 1);
+            if (c < gx) boundary_block<St, false>(NP, p, c);
+            else if (it > 0) aux_block(PP, p);     // at it == 0 it ran before this launch
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(SP.sync + SYNC_PART + p, 1u) == (unsigned)gx;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                if (tid == 0) SP.sync[SYNC_PART + p] = 0;
+                crit_block(PP, p);
+            }
+            __syncthreads();
+        }
+        // ---- bulk tiles
+        if (tid == 0) s_item[0] = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
+        __syncthreads();
+        int buf = 0, item = s_item[0];
+        while (item < SP.tiles) {
+            if (tid == 0) s_item[buf ^ 1] = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
+            bulk_tile<St, false>(BP, item);
+            __syncthreads();
+            buf ^= 1;
+            item = s_item[buf];
+        }
+        if (!grid_barrier(SP)) return;
+    }
+    // ---- auxiliary blocks of the last iteration, for the next launch's first solve
+    for (int p = blockIdx.x; p < SP.np; p += gridDim.x) {
+        aux_block(SP.part[0], p);
+        __syncthreads();
+    }
+}
+
+template <class St>
+static cudaError_t launch_step_t(const StepParams& sp, size_t smem, cudaStream_t s)
+{
+    static int grid[2] = {0, 0};                 // per dynamic shared memory size seen first
+    static size_t grid_smem = 0;
+    cudaError_t e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(step_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (grid[0] == 0 || grid_smem != smem) {
+        int dev = 0, nsm = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<St>, KBLOCK, smem)) != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+        grid[0] = occ * nsm < MAX_GRID ? occ * nsm : MAX_GRID;
+        grid_smem = smem;
+    }
+    void* args[] = {const_cast<StepParams*>(&sp)};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(step_kernel<St>), dim3(grid[0]), dim3(KBLOCK), args,
+                                       smem, s);
+}
+
+cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const PParams part[2], unsigned* sync,
+                        unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, cudaStream_t s)
+{
+    StepParams sp;
+    for (int c = 0; c < 2; ++c) { sp.bulk[c] = bulk[c]; sp.bnd[c] = bnd[c]; sp.part[c] = part[c]; }
+    sp.sync = sync; sp.status = status;
+    sp.np = np; sp.gx = gx; sp.tiles = tiles; sp.iters = iters; sp.cur0 = cur0;
+    const int smax = bnd[0].smax;
+    const size_t maps = 2ull * smax * smax * sizeof(uint64_t);
+    const size_t smem = np > 0 ? maps + (size_t)bnd[0].list_cap * sizeof(unsigned) : 0;
+    if (precision == 1) return launch_step_t<StF16>(sp, smem, s);
+    if (precision == 2) return launch_step_t<StBF16>(sp, smem, s);
+    return launch_step_t<StF32>(sp, smem, s);
+}
+
+}  // namespace lbsph

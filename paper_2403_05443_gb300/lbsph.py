@@ -15,7 +15,7 @@ from . import build as _build
 
 LB_FP32, LB_FP16, LB_BF16 = 0, 1, 2
 LB_FIELD_F, LB_FIELD_DF, LB_FIELD_RHO, LB_FIELD_U, LB_FIELD_SOLID = 1, 2, 4, 8, 16
-LB_FLAG_NO_GRAPH = 1
+LB_FLAG_SEPARATE_KERNELS = 1
 LB_RECORD_DOUBLES = 25
 STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ETIMEOUT",
           5: "LB_ENAN", 6: "LB_EOVERLAP", 7: "LB_ECAPACITY", 8: "LB_ESTATE"}
@@ -276,12 +276,12 @@ class Simulation:
     """A context plus the particles of its boxes; marshals to the C entry points."""
 
     def __init__(self, boxes, particles=None, precision=LB_FP32, didt_mode=0, device=0, max_semi=16,
-                 max_particles=None, fp16_scale=0.0, graphs=True, torch_alloc=False):
+                 max_particles=None, fp16_scale=0.0, separate_kernels=False, torch_alloc=False):
         self.boxes = [dict(b) for b in boxes]
         parts = particles or [[] for _ in boxes]
         opt = Options()
         opt.precision, opt.didt_mode, opt.device = precision, didt_mode, device
-        opt.flags = 0 if graphs else LB_FLAG_NO_GRAPH
+        opt.flags = LB_FLAG_SEPARATE_KERNELS if separate_kernels else 0
         opt.max_semi = int(max_semi)
         opt.max_particles = int(max_particles or max(1, sum(len(p) for p in parts)))
         opt.fp16_scale = float(fp16_scale)
