@@ -25,7 +25,7 @@ namespace lbsph {
 template <class St, bool FIRST>
 __global__ void __launch_bounds__(KBLOCK, 2) bulk_kernel(const BulkParams P, int tiles)
 {
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) bulk_tile<St, FIRST>(P, tile);
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) bulk_tile<St, FIRST>(P, tile, threadIdx.x);
 }
 
 static int bulk_grid(int tiles)

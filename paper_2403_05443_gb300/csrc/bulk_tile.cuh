@@ -6,10 +6,10 @@
 
 namespace lbsph {
 
+// quad tix (0..255) of tile `tile`; the 32 quads of a warp are consecutive
 template <class St, bool FIRST>
-__device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile)
+__device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix)
 {
-    const int tix = threadIdx.x;
     using T = typename St::T;
     const int bi = __ldg(P.blk_box + tile);
     const BoxDev& B = P.boxes[bi];

@@ -191,7 +191,8 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
         return bad("options");
     for (int b = 0; b < nbox; ++b) {
         const lb_box_desc& d = boxes[b];
-        if (d.nx < 4 || d.ny < 4 || d.nz < 4 || d.nx % 4 != 0) return bad("box size");
+        // rows are moved in 16-byte units: nx a multiple of 4 (8 for 16-bit storage)
+        if (d.nx < 4 || d.ny < 4 || d.nz < 4 || d.nx % (o.precision == LB_FP32 ? 4 : 8) != 0) return bad("box size");
         if (!(d.tau > 0.5) || !(d.rho0 > 0.0) || (d.walls && d.ny < 5)) return bad("box parameters");
         if ((long long)d.nx * d.ny * d.nz > (1ll << 31) / 19) return bad("box too large");
     }

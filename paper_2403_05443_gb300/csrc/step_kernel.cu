@@ -33,7 +33,6 @@ constexpr int SYNC_BAR = 0;          // barrier arrivals
 constexpr int SYNC_GEN = 1;          // barrier generation
 constexpr int SYNC_WORK = 2;         // work counter of the current iteration
 constexpr int SYNC_PART = 4;         // + p: items of particle p done in this iteration
-constexpr int SYNC_WORDS_FIXED = 4;  // then np particle words, then MAX_GRID block SM ids
 constexpr int MAX_GRID = 4096;
 constexpr long long SPIN_LIMIT = 1ll << 24;   // polls of about 100 ns: under 2 s
 
@@ -126,13 +125,13 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
             }
             __syncthreads();
         }
-        // ---- bulk tiles
+        // ---- bulk tiles from the counter
         if (tid == 0) s_item[0] = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
         __syncthreads();
         int buf = 0, item = s_item[0];
         while (item < SP.tiles) {
             if (tid == 0) s_item[buf ^ 1] = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
-            bulk_tile<St, false>(BP, item);
+            bulk_tile<St, false>(BP, item, tid);
             __syncthreads();
             buf ^= 1;
             item = s_item[buf];
