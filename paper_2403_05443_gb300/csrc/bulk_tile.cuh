@@ -14,28 +14,30 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
     const int bi = __ldg(P.blk_box + tile);
     const BoxDev& B = P.boxes[bi];
     const int nx = B.nx, ny = B.ny, nz = B.nz, nxq = B.nxq;
-    const long long N = B.N;
-    long long q = (long long)(tile - B.block_begin) * KBLOCK + tix;
-    const bool valid = q < B.nq;
-    if (!valid) q = B.nq - 1;
-    const int xq = (int)(q % nxq);
-    const long long row = q / nxq;
-    const int y = (int)(row % ny), z = (int)(row / ny);
+    // every offset within a box fits in 32 bits: 19 N < 2^31 (checked at lb_create)
+    const int N = (int)B.N;
+    int q = (tile - B.block_begin) * KBLOCK + tix;
+    const bool valid = q < (int)B.nq;
+    if (!valid) q = (int)B.nq - 1;
+    const int row = q / nxq;
+    const int xq = q - row * nxq;
+    const int z = row / ny;
+    const int y = row - z * ny;
     const int lane = tix & 31;
     const T* A = reinterpret_cast<const T*>(P.src) + B.off;
     T* D = reinterpret_cast<T*>(P.dst) + B.off;
     const float inv = B.inv_scale;
-    const long long own = row * nx + 4 * xq;
+    const int own = row * nx + 4 * xq;
     const unsigned long long pol_first = l2_evict_first();
 
-    long long rofs[3][3];  // element offsets of the source rows (y + dy, z + dz), wrapped
+    int rofs[3][3];  // element offsets of the source rows (y + dy, z + dz), wrapped
     {
         const int yy[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
         const int zz[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) rofs[a][b] = ((long long)zz[b] * ny + yy[a]) * nx;
+            for (int b = 0; b < 3; ++b) rofs[a][b] = (zz[b] * ny + yy[a]) * nx;
     }
     const bool left_ld = (lane == 0) || (xq == 0);
     const bool right_ld = (lane == 31) || (xq == nxq - 1);
@@ -47,7 +49,7 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
             v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
         }
-        const T* rp = A + (long long)i * N + rofs[1 - cy_of(i)][1 - cz_of(i)];
+        const T* rp = A + (i * N + rofs[1 - cy_of(i)][1 - cz_of(i)]);
         float4 t = St::ld4(rp + 4 * xq, inv, pol_first);
         if (cx_of(i) == 1) {            // source x - 1
             float l = __shfl_up_sync(0xffffffffu, t.w, 1);
@@ -72,16 +74,18 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
             if (cy_of(i) != cyw) continue;
             const float ubc = cx_of(i) * uw[0] + cy_of(i) * uw[1] + cz_of(i) * uw[2];
             const float add = 6.0f * w_of(i) * B.rho0f * ubc;
-            const float4 o = St::ld4(A + (long long)opp_of(i) * N + own, inv, pol_first);
+            const float4 o = St::ld4(A + (opp_of(i) * N + own), inv, pol_first);
             v[i] = make_float4(o.x + add, o.y + add, o.z + add, o.w + add);
         }
     }
+    Collider C;
+    C.init(B.omega, B.rho0f, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         float f[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i] = comp(v[i], k);
-        collide19(f, B.omega, B.rho0f, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps);
+        C.apply(f);
 #pragma unroll
         for (int i = 0; i < Q; ++i) set_comp(v[i], k, wallrow ? 0.0f : f[i]);
     }
@@ -115,13 +119,13 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
         const unsigned long long pol = near ? l2_evict_normal() : pol_first;
         if (!skip) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) St::st4(dp + (long long)i * N, v[i], B.scale, pol);
+            for (int i = 0; i < Q; ++i) St::st4(dp + i * N, v[i], B.scale, pol);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if ((skip >> k) & 1u) continue;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) St::st1(dp + (long long)i * N + k, comp(v[i], k), B.scale, pol);
+                for (int i = 0; i < Q; ++i) St::st1(dp + (i * N + k), comp(v[i], k), B.scale, pol);
             }
         }
     }

@@ -174,45 +174,91 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float a)
     if (k == 0) v.x = a; else if (k == 1) v.y = a; else if (k == 2) v.z = a; else v.w = a;
 }
 
-// BGK collision (Eq. 3-4) on deviations with Guo forcing; eps is the mass put
-// back by an earlier remap (w_i eps added to every population first).
+// BGK collision (Eq. 3-4) on deviations d_i = f_i - w_i rho0 with Guo
+// forcing, arranged per pair of opposite directions (i, i+1 for odd i).  With
+// rho = rho0 + sum d, j = sum c d, u = (j + g/2)/rho and cf = 1 - omega/2, the
+// post-collision deviations are
+//   d_i' = (1 - omega) d_i + sym_i + asym_i,  d_{i+1}' = (1 - omega) d_{i+1} + sym_i - asym_i,
+//   sym_i  = w_i P + cu (4.5 omega rho w_i cu + 9 cf w_i (c_i.g)),
+//   asym_i = 3 omega rho w_i cu + 3 cf w_i (c_i.g),
+//   P = omega drho - 1.5 omega rho u.u - 3 cf u.g  (+ (1 - omega) eps),
+// cu = c_i.u; the rest population gets d_0' = (1 - omega) d_0 + w_0 P.  This is
+// the BGK relaxation to the second-order equilibrium plus (1 - omega/2) times
+// the Guo source w_i [3 (c_i - u).g + 9 (c_i.u)(c_i.g)], with every term that
+// depends only on the box's uniform force g computed once per box.  eps is the
+// mass put back by an earlier remap: w_i eps is added to every population
+// first, which only moves drho and P.
+struct Collider {
+    float omega, om1, rho0, eps;
+    float gx, gy, gz;
+    float cfug;                     // 3 cf, the factor of u.g in P
+    float k[9], l[9];               // per pair: 9 cf w (c.g) and 3 cf w (c.g)
+
+    __device__ __forceinline__ void init(float omega_, float rho0_, float gx_, float gy_, float gz_, float eps_)
+    {
+        omega = omega_;
+        om1 = 1.0f - omega_;
+        rho0 = rho0_;
+        eps = eps_;
+        gx = gx_; gy = gy_; gz = gz_;
+        const float cf = 1.0f - 0.5f * omega_;
+        cfug = 3.0f * cf;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const int i = 2 * m + 1;
+            const float cg = cx_of(i) * gx_ + cy_of(i) * gy_ + cz_of(i) * gz_;
+            k[m] = (9.0f * w_of(i)) * cf * cg;
+            l[m] = (3.0f * w_of(i)) * cf * cg;
+        }
+    }
+
+    __device__ __forceinline__ void apply(float (&f)[Q]) const
+    {
+        float sm[9], df[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            sm[m] = f[2 * m + 1] + f[2 * m + 2];
+            df[m] = f[2 * m + 1] - f[2 * m + 2];
+        }
+        float drho = f[0] + eps;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) drho += sm[m];
+        float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const int i = 2 * m + 1;
+            if (cx_of(i) == 1) jx += df[m]; else if (cx_of(i) == -1) jx -= df[m];
+            if (cy_of(i) == 1) jy += df[m]; else if (cy_of(i) == -1) jy -= df[m];
+            if (cz_of(i) == 1) jz += df[m]; else if (cz_of(i) == -1) jz -= df[m];
+        }
+        const float rho = rho0 + drho;
+        const float ir = __fdividef(1.0f, rho);
+        const float ux = (jx + 0.5f * gx) * ir, uy = (jy + 0.5f * gy) * ir, uz = (jz + 0.5f * gz) * ir;
+        const float uu = ux * ux + uy * uy + uz * uz;
+        const float ug = ux * gx + uy * gy + uz * gz;
+        const float orho = omega * rho;
+        const float P = omega * drho - 1.5f * orho * uu - cfug * ug + om1 * eps;
+        f[0] = om1 * f[0] + w_of(0) * P;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const int i = 2 * m + 1;
+            const float w = w_of(i);
+            const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
+            const float sym = w * P + cu * ((4.5f * w) * orho * cu + k[m]);
+            const float asym = (3.0f * w) * orho * cu + l[m];
+            f[i] = om1 * f[i] + (sym + asym);
+            f[i + 1] = om1 * f[i + 1] + (sym - asym);
+        }
+    }
+};
+
+// one node's collision with freshly set-up box terms
 __device__ __forceinline__ void collide19(float (&f)[Q], float omega, float rho0, float gx, float gy,
                                           float gz, float eps)
 {
-    if (eps != 0.0f) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] += w_of(i) * eps;
-    }
-    float drho = 0.0f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) drho += f[i];
-    const float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
-    const float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
-    const float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
-    const float rho = rho0 + drho;
-    const float ir = 1.0f / rho;
-    const float ux = (jx + 0.5f * gx) * ir, uy = (jy + 0.5f * gy) * ir, uz = (jz + 0.5f * gz) * ir;
-    const float uu = ux * ux + uy * uy + uz * uz;
-    const float ug = ux * gx + uy * gy + uz * gz;
-    const float om1 = 1.0f - omega;
-    const float cf = 1.0f - 0.5f * omega;
-    {
-        const float w = w_of(0);
-        f[0] = om1 * f[0] + omega * w * (drho - 1.5f * rho * uu) - 3.0f * cf * w * ug;
-    }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
-        const float cg = cx_of(i) * gx + cy_of(i) * gy + cz_of(i) * gz;
-        const float w = w_of(i);
-        const float sym = w * (drho + rho * (4.5f * cu * cu - 1.5f * uu));
-        const float asym = 3.0f * w * rho * cu;
-        const float ss = cf * w * (9.0f * cu * cg - 3.0f * ug);
-        const float sa = 3.0f * cf * w * cg;
-        const float a = f[i], b = f[i + 1];
-        f[i] = om1 * a + omega * (sym + asym) + ss + sa;
-        f[i + 1] = om1 * b + omega * (sym - asym) + ss - sa;
-    }
+    Collider C;
+    C.init(omega, rho0, gx, gy, gz, eps);
+    C.apply(f);
 }
 
 
