@@ -12,13 +12,15 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbsph.so")
-UNITS = ["bulk_kernel.cu", "boundary_kernel.cu", "lattice_kernel.cu", "particle_kernel.cu", "step_kernel.cu", "lbsph_api.cu"]
+UNITS = ["bulk_kernel.cu", "boundary_kernel.cu", "lattice_kernel.cu", "particle_kernel.cu", "step_kernel.cu", "lbsph_api.cu",
+         "mlp_kernel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
 
 def _deps():
-    files = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(ROOT, "include", "lbsph.h")]
+    inc = os.path.join(ROOT, "include")
+    files = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(inc, f) for f in os.listdir(inc)]
     return max(os.path.getmtime(f) for f in files)
 
 
