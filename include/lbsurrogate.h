@@ -105,6 +105,28 @@ lb_status lb_spd_solve6(const float* R_dev, const double* f_dev, double* u_dev, 
  * place and symmetrises the result: measured mobilities -> resistance targets. */
 lb_status lb_spd_invert6(double* M_dev, int32_t n, void* stream);
 
+/* Network inputs from geometry, per sample geom_dev[n][8] (FP64, device) =
+ * (a, b, nu, L, e_x, e_y, e_z, rho0): long and short semi-axes, kinematic
+ * viscosity, box edge (for several particles in one box: the edge of the volume
+ * per particle), unit long axis e (e and -e give the same features: the sign is
+ * taken so that e_z >= 0), fluid density.  x_dev[n][8] (FP32, device) =
+ * (a/b - 2, b - 3, 10 (nu - 1/6), 10 b/L - 1, e, 1). */
+lb_status lb_mlp_features(const double* geom_dev, int32_t n, float* x_dev, void* stream);
+
+/* Training targets from measured mobilities: M_dev[n][36] (FP64, device; column
+ * j = (U, Omega) at steady state per unit (F, T) along j) -> Rhat_dev[n][36]
+ * (FP32) = (D M D)^-1, symmetrised, with D = diag(s_t I3, s_r I3), s_t^2 =
+ * 6 pi mu b, s_r^2 = 8 pi mu b^3, mu = rho0 nu: the dimensionless resistance
+ * tensor R^ = D^-1 R D^-1, the identity for a radius-b sphere in free space. */
+lb_status lb_resistance_targets(const double* M_dev, const double* geom_dev, int32_t n, float* Rhat_dev,
+                                void* stream);
+
+/* Warm-start velocities: UW_dev[n][6] = (U, Omega) = R^-1 (F, T) with R =
+ * D R^ D from a predicted Rhat_dev[n][36] (FP32) and FT_dev[n][6] = (F_ext,
+ * T_ext) (FP64).  Cholesky in FP64 on the device. */
+lb_status lb_warm_velocities(const float* Rhat_dev, const double* geom_dev, const double* FT_dev, int32_t n,
+                             double* UW_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

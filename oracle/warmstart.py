@@ -1,0 +1,106 @@
+"""FP64 reference of the warm-start pieces: the periodic Stokes flow of the
+particles' forces, the equilibrium initial fluid, the network's input
+features and the scaling of resistance tensors.
+
+Test infrastructure only (tests, smoke, bench baselines); shares no code with
+the CUDA library.
+
+Stokes flow on the periodic lattice: mu Lap u - grad p + g = 0, div u = 0,
+solved mode by mode with numpy's FFT as the transform.  With kt_d =
+2 sin(pi k_d / n_d), |kt|^2 is the symbol of the 7-point Laplacian and the
+flow is u^ = (g^ - kt (kt . g^) / |kt|^2) / (mu |kt|^2), u^(0) = 0.  g puts
+each particle's F_ext uniformly on its solid nodes, and the body force plus
+(with counter_force) -sum F_ext / N_fluid on the fluid nodes.  Pinned by the
+single-mode closed form, the projection (divergence-free in the lattice
+symbol) and the symmetry of the periodic Green's function
+(tests/test_oracle_warmstart.py).
+
+Scaling: D = diag(s_t I3, s_r I3), s_t^2 = 6 pi mu b, s_r^2 = 8 pi mu b^3
+(mu = rho0 nu); the network predicts R^ = D^-1 R D^-1, so a radius-b sphere in
+free space has R^ = I (Stokes drag 6 pi mu b and torque 8 pi mu b^3).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def stokes_field(nx, ny, nz, owner, F_ext, mu, counter=False, body=(0.0, 0.0, 0.0)):
+    """u[3, nz, ny, nx]; owner[nz, ny, nx] (0 fluid, p+1 particle p, -1 wall);
+    F_ext[np, 3]."""
+    owner = np.asarray(owner)
+    F = np.asarray(F_ext, np.float64).reshape(-1, 3)
+    g = np.zeros((3, nz, ny, nx))
+    fluid = owner == 0
+    nfl = int(fluid.sum())
+    for k in range(3):
+        gk = np.zeros((nz, ny, nx))
+        gk[fluid] = body[k] - (F[:, k].sum() / nfl if (counter and nfl) else 0.0)
+        for p in range(F.shape[0]):
+            m = owner == p + 1
+            if m.any():
+                gk[m] = F[p, k] / m.sum()
+        g[k] = gk
+    return stokes_solve(g, mu)
+
+
+def stokes_solve(g, mu):
+    """Periodic lattice Stokes flow of a force density g[3, nz, ny, nx]."""
+    _, nz, ny, nx = g.shape
+    kz = 2 * np.sin(np.pi * np.arange(nz) / nz)[:, None, None]
+    ky = 2 * np.sin(np.pi * np.arange(ny) / ny)[None, :, None]
+    kx = 2 * np.sin(np.pi * np.arange(nx) / nx)[None, None, :]
+    k = [np.broadcast_to(kx, (nz, ny, nx)), np.broadcast_to(ky, (nz, ny, nx)), np.broadcast_to(kz, (nz, ny, nx))]
+    k2 = k[0] ** 2 + k[1] ** 2 + k[2] ** 2
+    gh = [np.fft.fftn(g[c]) for c in range(3)]
+    safe = np.where(k2 > 0, k2, 1.0)
+    proj = (k[0] * gh[0] + k[1] * gh[1] + k[2] * gh[2]) / safe
+    u = np.zeros_like(g)
+    for c in range(3):
+        uh = (gh[c] - k[c] * proj) / (mu * safe)
+        uh[k2 == 0] = 0.0
+        u[c] = np.real(np.fft.ifftn(uh))
+    return u
+
+
+def equilibrium_f(u, rho0, c, w):
+    """f_i = w_i [rho0 + rho0 (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)] for u[3, ...]
+    (the second-order equilibrium at density rho0); returns [..., 19] in the
+    order of the table (c, w) given."""
+    u = np.moveaxis(np.asarray(u, np.float64), 0, -1)
+    cu = u @ np.asarray(c, np.float64).T
+    uu = (u * u).sum(-1, keepdims=True)
+    return np.asarray(w) * rho0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)
+
+
+def features(geom):
+    """Network inputs from geom[n, 8] = (a, b, nu, L, e, rho0)."""
+    g = np.asarray(geom, np.float64).reshape(-1, 8)
+    sg = np.where(g[:, 6] < 0, -1.0, 1.0)
+    x = np.stack([g[:, 0] / g[:, 1] - 2.0, g[:, 1] - 3.0, (g[:, 2] - 1.0 / 6.0) * 10.0, g[:, 1] / g[:, 3] * 10.0 - 1.0,
+                  sg * g[:, 4], sg * g[:, 5], sg * g[:, 6], np.ones(len(g))], axis=1)
+    return x
+
+
+def scales(geom):
+    g = np.asarray(geom, np.float64).reshape(-1, 8)
+    mu = g[:, 7] * g[:, 2]
+    b = g[:, 1]
+    st, sr = np.sqrt(6 * np.pi * mu * b), np.sqrt(8 * np.pi * mu * b ** 3)
+    return np.stack([st, st, st, sr, sr, sr], axis=1)
+
+
+def targets(M, geom):
+    """R^ = (D M D)^-1, symmetrised, from measured mobilities M[n, 6, 6]."""
+    d = scales(geom)
+    A = d[:, :, None] * np.asarray(M, np.float64).reshape(-1, 6, 6) * d[:, None, :]
+    R = np.linalg.inv(A)
+    return 0.5 * (R + np.transpose(R, (0, 2, 1)))
+
+
+def warm_velocities(Rhat, geom, FT):
+    """(U, Omega) = D^-1 R^^-1 D^-1 (F, T)."""
+    d = scales(geom)
+    R = np.asarray(Rhat, np.float64).reshape(-1, 6, 6)
+    R = 0.5 * (R + np.transpose(R, (0, 2, 1)))
+    f = np.asarray(FT, np.float64).reshape(-1, 6) / d
+    return np.stack([np.linalg.solve(a, b) for a, b in zip(R, f)]) / d

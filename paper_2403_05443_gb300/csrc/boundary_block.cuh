@@ -157,8 +157,9 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
             rare_add(ACC_UNC + 4, mx * mx); rare_add(ACC_UNC + 5, mx * my); rare_add(ACC_UNC + 6, mx * mz);
             rare_add(ACC_UNC + 7, my * my); rare_add(ACC_UNC + 8, my * mz); rare_add(ACC_UNC + 9, mz * mz);
         } else if (FIRST) {
+            // first collision: the node's initial distributions, no streaming
 #pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = 0.0f;
+            for (int i = 0; i < Q; ++i) f[i] = St::ld1(A + ((long long)i * N + own), inv, pol);
         } else {
             // fluid at t-1: decide every source first, then issue the 19 loads together
             unsigned bb = 0, wl = 0;

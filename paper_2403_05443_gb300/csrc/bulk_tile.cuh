@@ -46,7 +46,9 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (FIRST) {
-            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            // first collision: the initial distributions of the node itself
+            // (rest, or a field set by lb_init_fluid), no streaming
+            v[i] = St::ld4(A + (i * N + own), inv, pol_first);
             continue;
         }
         const T* rp = A + (i * N + rofs[1 - cy_of(i)][1 - cz_of(i)]);

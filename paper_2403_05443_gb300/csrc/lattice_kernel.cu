@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(KBLOCK) fields_kernel(const KParams P)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (first) {
-            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            // before the first collision: the initial distributions in place
+            v[i] = St::ld4(A + (long long)i * N + rofs[1][1] + 4 * xq, inv, pol);
             continue;
         }
         const T* rp = A + (long long)i * N + rofs[1 - cy_of(i)][1 - cz_of(i)];

@@ -31,6 +31,10 @@ cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const 
                         unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, cudaStream_t s);
 cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
                          int cap, int* count, cudaStream_t s);
+cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const int* owner,
+                              cudaStream_t s);
+cudaError_t launch_stokes(const BoxDev& B, const int* owner, const PartDev* pd, int np, int counter_on,
+                          const double body[3], float mu, float2* work, int* counts, float* u, cudaStream_t s);
 }  // namespace lbsph
 
 using namespace lbsph;
@@ -63,6 +67,8 @@ struct lb_ctx {
     int links_cap = 0;
     int* d_count = nullptr;
     float* d_tmp = nullptr;
+    float2* d_stokes = nullptr;         // lb_stokes_field: two complex [3][N] buffers of the largest box
+    int* d_counts = nullptr;
     double* d_rec = nullptr;
     size_t tmp_bytes = 0;
     bool collided = false;
@@ -737,5 +743,74 @@ extern "C" lb_status lb_get_links(lb_ctx* ctx, int32_t box, int32_t particle, in
     CK(cudaMemcpy(&n, ctx->d_count, sizeof(int), cudaMemcpyDeviceToHost));
     *count = n;
     if (n <= cap && n > 0) CK(cudaMemcpy(pairs, ctx->d_links, sizeof(int) * 2ull * n, cudaMemcpyDeviceToHost));
+    return read_status(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// Warm start: an initial fluid field and the periodic Stokes flow of the
+// particles' forces (warm_kernel.cu).
+
+// owner field of box `box` into d_tmp[0, N) (before the first collision)
+static cudaError_t owner_field(lb_ctx* ctx, int box, cudaStream_t s)
+{
+    KParams k = base_kparams(ctx);
+    k.src = ctx->fbuf[ctx->cur];
+    k.only_box = box;
+    k.nopull = 1;
+    k.out_solid = reinterpret_cast<int*>(ctx->d_tmp);
+    return launch_fields(k, ctx->opt.precision, ctx->hbox[box].nblocks, s);
+}
+
+extern "C" lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, size_t u_bytes, int32_t u_is_device,
+                                   void* stream)
+{
+    if (!ctx) return LB_EINVAL;
+    if (box < 0 || box >= (int)ctx->desc.size() || !u) return fail(ctx, LB_EINVAL, "bad box or field");
+    if (ctx->stepped) return fail(ctx, LB_ESTATE, "lb_init_fluid after the first step");
+    const BoxDev& B = ctx->hbox[box];
+    if (u_bytes != 3ull * B.N * sizeof(float)) return fail(ctx, LB_EINVAL, "u_bytes must be 3*N*4");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick(ctx, stream);
+    if (!ctx->d_tmp) {
+        ctx->d_tmp = (float*)dev_alloc(ctx, ctx->tmp_bytes);
+        if (!ctx->d_tmp) return fail(ctx, LB_ENOMEM, "field staging buffer");
+    }
+    float* ud = ctx->d_tmp + B.N;                      // [3][N] after the owner field
+    CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
+    CK(cudaMemcpyAsync(ud, u, u_bytes, u_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CK(owner_field(ctx, box, s));
+    CK(launch_init_fluid(B, ctx->opt.precision, ctx->fbuf[ctx->cur], ud, reinterpret_cast<int*>(ctx->d_tmp), s));
+    CK(cudaStreamSynchronize(s));
+    return read_status(ctx);
+}
+
+extern "C" lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, void* stream)
+{
+    if (!ctx) return LB_EINVAL;
+    if (box < 0 || box >= (int)ctx->desc.size() || !u_dev) return fail(ctx, LB_EINVAL, "bad box or output");
+    const lb_box_desc& d = ctx->desc[box];
+    if (d.walls) return fail(ctx, LB_EINVAL, "lb_stokes_field needs a fully periodic box");
+    if (d.nx > 4096 || d.ny > 4096 || d.nz > 4096) return fail(ctx, LB_EINVAL, "box edge above 4096");
+    if (ctx->stepped) return fail(ctx, LB_ESTATE, "lb_stokes_field after the first step");
+    const BoxDev& B = ctx->hbox[box];
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick(ctx, stream);
+    if (!ctx->d_tmp) {
+        ctx->d_tmp = (float*)dev_alloc(ctx, ctx->tmp_bytes);
+        if (!ctx->d_tmp) return fail(ctx, LB_ENOMEM, "field staging buffer");
+    }
+    if (!ctx->d_stokes) {
+        long long nmax = 0;
+        for (auto& h : ctx->hbox) nmax = std::max(nmax, h.N);
+        ctx->d_stokes = (float2*)dev_alloc(ctx, sizeof(float2) * 6 * (size_t)nmax);
+        ctx->d_counts = (int*)dev_alloc(ctx, sizeof(int) * (size_t)(ctx->maxp + 1));
+        if (!ctx->d_stokes || !ctx->d_counts) return fail(ctx, LB_ENOMEM, "Stokes work buffers");
+    }
+    CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
+    CK(owner_field(ctx, box, s));
+    const double mu = d.rho0 * (d.tau - 0.5) / 3.0;
+    CK(launch_stokes(B, reinterpret_cast<int*>(ctx->d_tmp), ctx->d_pd + B.pbeg, B.pcnt, d.counter_force,
+                     d.body_force, (float)mu, ctx->d_stokes, ctx->d_counts, u_dev, s));
+    CK(cudaStreamSynchronize(s));
     return read_status(ctx);
 }

@@ -365,14 +365,11 @@ __global__ void adam_kernel(float* p, const float* g, float* m1, float* m2, int 
     p[i] -= lr * (a * c1) / (sqrtf(b * c2) + 1e-8f);
 }
 
-// Cholesky solve of R u = f per sample, FP64 (R read as FP32)
-__global__ void spd_solve_kernel(const float* R, const double* f, double* u, int n)
+// Cholesky solve of A u = f for one symmetric positive definite 6x6 A (FP64,
+// A overwritten)
+__device__ void chol_solve6(double (&A)[6][6], const double* f, double* u)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    double A[6][6], y[6];
-    for (int i = 0; i < 6; ++i)
-        for (int j = 0; j < 6; ++j) A[i][j] = 0.5 * ((double)R[s * 36 + i * 6 + j] + (double)R[s * 36 + j * 6 + i]);
+    double y[6];
     for (int j = 0; j < 6; ++j) {                      // A = C C^T, C lower, in place
         double d = A[j][j];
         for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
@@ -385,26 +382,35 @@ __global__ void spd_solve_kernel(const float* R, const double* f, double* u, int
         }
     }
     for (int i = 0; i < 6; ++i) {
-        double a = f[s * 6 + i];
+        double a = f[i];
         for (int k = 0; k < i; ++k) a -= A[i][k] * y[k];
         y[i] = A[i][i] > 0.0 ? a / A[i][i] : 0.0;
     }
     for (int i = 5; i >= 0; --i) {
         double a = y[i];
-        for (int k = i + 1; k < 6; ++k) a -= A[k][i] * u[s * 6 + k];
-        u[s * 6 + i] = A[i][i] > 0.0 ? a / A[i][i] : 0.0;
+        for (int k = i + 1; k < 6; ++k) a -= A[k][i] * u[k];
+        u[i] = A[i][i] > 0.0 ? a / A[i][i] : 0.0;
     }
 }
 
-// in-place inverse of symmetric positive definite 6x6 matrices (Gauss-Jordan
-// with partial pivoting, FP64), symmetrised
-__global__ void spd_invert_kernel(double* M, int n)
+// Cholesky solve of R u = f per sample, FP64 (R read as FP32, symmetrised)
+__global__ void spd_solve_kernel(const float* R, const double* f, double* u, int n)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    double A[6][6];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) A[i][j] = 0.5 * ((double)R[s * 36 + i * 6 + j] + (double)R[s * 36 + j * 6 + i]);
+    chol_solve6(A, f + s * 6, u + s * 6);
+}
+
+// inverse of a 6x6 matrix M (Gauss-Jordan with partial pivoting, FP64),
+// symmetrised, into out
+__device__ void invert6_sym(const double* M, double* out)
+{
     double A[6][12];
     for (int i = 0; i < 6; ++i)
-        for (int j = 0; j < 12; ++j) A[i][j] = j < 6 ? M[s * 36 + i * 6 + j] : (j - 6 == i ? 1.0 : 0.0);
+        for (int j = 0; j < 12; ++j) A[i][j] = j < 6 ? M[i * 6 + j] : (j - 6 == i ? 1.0 : 0.0);
     for (int c = 0; c < 6; ++c) {
         int piv = c;
         for (int r = c + 1; r < 6; ++r)
@@ -421,7 +427,76 @@ __global__ void spd_invert_kernel(double* M, int n)
         }
     }
     for (int i = 0; i < 6; ++i)
-        for (int j = 0; j < 6; ++j) M[s * 36 + i * 6 + j] = 0.5 * (A[i][j + 6] + A[j][i + 6]);
+        for (int j = 0; j < 6; ++j) out[i * 6 + j] = 0.5 * (A[i][j + 6] + A[j][i + 6]);
+}
+
+__global__ void spd_invert_kernel(double* M, int n)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double t[36];
+    invert6_sym(M + s * 36, t);
+    for (int k = 0; k < 36; ++k) M[s * 36 + k] = t[k];
+}
+
+// ---- features and scaling of the resistance tensor.  geom per sample:
+// (a, b, nu, L, e_x, e_y, e_z, rho0): semi-axes a (along the unit long axis e)
+// and b, kinematic viscosity, box edge (or the edge of the volume per
+// particle), fluid density.  D = diag(s_t I3, s_r I3) with s_t^2 = 6 pi mu b and
+// s_r^2 = 8 pi mu b^3 (mu = rho0 nu): the radius-b sphere's Stokes resistances,
+// so that R^ = D^-1 R D^-1 is the identity for that sphere in free space.
+__device__ __forceinline__ void scales(const double* g, double& st, double& sr)
+{
+    const double mu = g[7] * g[2], b = g[1];
+    st = sqrt(6.0 * M_PI * mu * b);
+    sr = sqrt(8.0 * M_PI * mu * b * b * b);
+}
+
+__global__ void features_geom_kernel(const double* geom, int n, float* x)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double* g = geom + s * 8;
+    const double sg = g[6] < 0.0 ? -1.0 : 1.0;       // head-tail symmetry: e and -e are the same spheroid
+    x[s * 8 + 0] = (float)(g[0] / g[1] - 2.0);
+    x[s * 8 + 1] = (float)(g[1] - 3.0);
+    x[s * 8 + 2] = (float)((g[2] - 1.0 / 6.0) * 10.0);
+    x[s * 8 + 3] = (float)(g[1] / g[3] * 10.0 - 1.0);
+    x[s * 8 + 4] = (float)(sg * g[4]);
+    x[s * 8 + 5] = (float)(sg * g[5]);
+    x[s * 8 + 6] = (float)(sg * g[6]);
+    x[s * 8 + 7] = 1.0f;
+}
+
+// measured mobility M (6x6, FP64) -> R^ = (D M D)^-1 (FP32)
+__global__ void targets_kernel(const double* M, const double* geom, int n, float* Rhat)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double st, sr;
+    scales(geom + s * 8, st, sr);
+    double A[36], t[36];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) A[i * 6 + j] = (i < 3 ? st : sr) * M[s * 36 + i * 6 + j] * (j < 3 ? st : sr);
+    invert6_sym(A, t);
+    for (int k = 0; k < 36; ++k) Rhat[s * 36 + k] = (float)t[k];
+}
+
+// (U, Omega) = R^-1 (F, T) = D^-1 R^^-1 D^-1 (F, T)
+__global__ void warm_velocities_kernel(const float* Rhat, const double* geom, const double* FT, int n, double* UW)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double st, sr;
+    scales(geom + s * 8, st, sr);
+    double A[6][6], f[6], u[6];
+    for (int i = 0; i < 6; ++i) {
+        f[i] = FT[s * 6 + i] / (i < 3 ? st : sr);
+        for (int j = 0; j < 6; ++j)
+            A[i][j] = 0.5 * ((double)Rhat[s * 36 + i * 6 + j] + (double)Rhat[s * 36 + j * 6 + i]);
+    }
+    chol_solve6(A, f, u);
+    for (int i = 0; i < 6; ++i) UW[s * 6 + i] = u[i] / (i < 3 ? st : sr);
 }
 
 }  // namespace lbsur
@@ -660,5 +735,29 @@ extern "C" lb_status lb_spd_invert6(double* M_dev, int32_t n, void* stream)
 {
     if (!M_dev || n < 1) return LB_EINVAL;
     spd_invert_kernel<<<blocks(n, 64), 64, 0, static_cast<cudaStream_t>(stream)>>>(M_dev, n);
+    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;
+}
+
+extern "C" lb_status lb_mlp_features(const double* geom_dev, int32_t n, float* x_dev, void* stream)
+{
+    if (!geom_dev || !x_dev || n < 1) return LB_EINVAL;
+    features_geom_kernel<<<blocks(n, 64), 64, 0, static_cast<cudaStream_t>(stream)>>>(geom_dev, n, x_dev);
+    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;
+}
+
+extern "C" lb_status lb_resistance_targets(const double* M_dev, const double* geom_dev, int32_t n, float* Rhat_dev,
+                                           void* stream)
+{
+    if (!M_dev || !geom_dev || !Rhat_dev || n < 1) return LB_EINVAL;
+    targets_kernel<<<blocks(n, 64), 64, 0, static_cast<cudaStream_t>(stream)>>>(M_dev, geom_dev, n, Rhat_dev);
+    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;
+}
+
+extern "C" lb_status lb_warm_velocities(const float* Rhat_dev, const double* geom_dev, const double* FT_dev, int32_t n,
+                                        double* UW_dev, void* stream)
+{
+    if (!Rhat_dev || !geom_dev || !FT_dev || !UW_dev || n < 1) return LB_EINVAL;
+    warm_velocities_kernel<<<blocks(n, 64), 64, 0, static_cast<cudaStream_t>(stream)>>>(Rhat_dev, geom_dev, FT_dev, n,
+                                                                                         UW_dev);
     return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;
 }

@@ -81,6 +81,8 @@ def library(path: str | None = None):
     L.lb_profile_step.argtypes = [vp, i32, vp, dp]
     L.lb_links_noalloc.argtypes = [dp, dp, dp, i32, i32, i32, i32, vp, i32, vp, vp]
     L.lb_links_noalloc.restype = i32
+    L.lb_init_fluid.argtypes = [vp, i32, vp, C.c_size_t, i32, vp]
+    L.lb_stokes_field.argtypes = [vp, i32, vp, vp]
     L.lb_lattice.argtypes = [ip, dp]
     L.lb_lattice.restype = None
     L.lb_status_string.argtypes = [i32]
@@ -90,7 +92,7 @@ def library(path: str | None = None):
     L.lb_abi_version.restype = i32
     for name in ("lb_create", "lb_destroy", "lb_set_particles", "lb_set_external", "lb_step",
                  "lb_get_fields", "lb_get_force_torque", "lb_get_links", "lb_get_drag", "lb_synchronize",
-                 "lb_profile_step"):
+                 "lb_profile_step", "lb_init_fluid", "lb_stokes_field"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -210,6 +212,17 @@ def lb_get_drag(ctx, box: int, particle: int) -> np.ndarray:
     out = np.zeros(36)
     _check(library().lb_get_drag(ctx, box, particle, out.ctypes.data_as(C.POINTER(C.c_double))), ctx)
     return out.reshape(6, 6)
+
+
+def lb_init_fluid(ctx, box: int, u_ptr: int, nbytes: int, u_is_device: bool, stream=None):
+    """Initial fluid f = f_eq(rho0, u) of a box before the first step; u_ptr is
+    a host or device address of FP32 [3][nz][ny][nx]."""
+    _check(library().lb_init_fluid(ctx, box, C.c_void_p(u_ptr), nbytes, int(u_is_device), stream), ctx)
+
+
+def lb_stokes_field(ctx, box: int, u_dev_ptr: int, stream=None):
+    """Periodic Stokes flow of the box's particle forces into device FP32 [3][N]."""
+    _check(library().lb_stokes_field(ctx, box, C.c_void_p(u_dev_ptr), stream), ctx)
 
 
 def lb_synchronize(ctx):
@@ -339,6 +352,11 @@ class Simulation:
 
     def drag(self, box: int = 0, p: int = 0):
         return lb_get_drag(self.ctx, box, p)
+
+    def init_fluid(self, box: int, u: np.ndarray):
+        """Initial velocity field u (host, [3][nz][ny][nx]) of a box."""
+        a = np.ascontiguousarray(np.asarray(u, np.float32))
+        lb_init_fluid(self.ctx, box, a.ctypes.data, a.nbytes, False)
 
     def set_external(self, box, ft, stream=None):
         lb_set_external(self.ctx, box, ft, stream)

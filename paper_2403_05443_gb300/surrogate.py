@@ -42,9 +42,12 @@ def _lib():
     L.lb_mlp_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp]
     L.lb_spd_solve6.argtypes = [vp, vp, vp, i32, vp]
     L.lb_spd_invert6.argtypes = [vp, i32, vp]
+    L.lb_mlp_features.argtypes = [vp, i32, vp, vp]
+    L.lb_resistance_targets.argtypes = [vp, vp, i32, vp, vp]
+    L.lb_warm_velocities.argtypes = [vp, vp, vp, i32, vp, vp]
     for n in ("lb_gemm_bf16", "lb_gemm_status", "lb_mlp_create", "lb_mlp_destroy", "lb_mlp_set_params",
               "lb_mlp_get_params", "lb_mlp_forward", "lb_mlp_loss_grad", "lb_mlp_train_step", "lb_spd_solve6",
-              "lb_spd_invert6"):
+              "lb_spd_invert6", "lb_mlp_features", "lb_resistance_targets", "lb_warm_velocities"):
         getattr(L, n).restype = i32
     _bound = True
     return L
@@ -111,6 +114,19 @@ def lb_spd_solve6(R_dev, f_dev, u_dev, n, stream=None):
 
 def lb_spd_invert6(M_dev, n, stream=None):
     _check(_lib().lb_spd_invert6(_p(M_dev), n, stream), "lb_spd_invert6")
+
+
+def lb_mlp_features(geom_dev, n, x_dev, stream=None):
+    _check(_lib().lb_mlp_features(_p(geom_dev), n, _p(x_dev), stream), "lb_mlp_features")
+
+
+def lb_resistance_targets(M_dev, geom_dev, n, Rhat_dev, stream=None):
+    _check(_lib().lb_resistance_targets(_p(M_dev), _p(geom_dev), n, _p(Rhat_dev), stream), "lb_resistance_targets")
+
+
+def lb_warm_velocities(Rhat_dev, geom_dev, FT_dev, n, UW_dev, stream=None):
+    _check(_lib().lb_warm_velocities(_p(Rhat_dev), _p(geom_dev), _p(FT_dev), n, _p(UW_dev), stream),
+           "lb_warm_velocities")
 
 
 def unpack(params: np.ndarray) -> dict:

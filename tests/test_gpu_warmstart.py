@@ -1,0 +1,112 @@
+"""Parity of the warm-start entry points (lb_stokes_field, lb_init_fluid,
+lb_mlp_features, lb_resistance_targets, lb_warm_velocities), called through
+the C ABI, with the FP64 reference oracle/warmstart.py and the FP64 LB oracle.
+
+Bars: the Stokes flow within 1e-4 normwise (FP32 DFTs of length <= 40 against
+numpy's FP64 FFT: each pass adds a few FP32 roundings per term); a run started
+from lb_init_fluid within the bars of the plain runs (1e-5 normwise on the
+deviations, u, F and T every few steps); features, targets and velocities
+within FP32 rounding (2e-6 normwise)."""
+import math
+
+import numpy as np
+import pytest
+
+from lb_inputs import box, particle, random_quaternion, rng
+from oracle import oracle as O
+from oracle import warmstart as W
+from parity_util import direction_map, normwise, oracle_df_gpu_layout
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+L = pytest.importorskip("paper_2403_05443_gb300.lbsph")
+SU = pytest.importorskip("paper_2403_05443_gb300.surrogate")
+
+
+def _case():
+    g = rng(31)
+    b = box(40, 24, 36, 0.9, counter_force=1)
+    parts = [particle((4.5, 2.5, 2.0), (9.3, 9.1, 10.7), random_quaternion(g), F_ext=(2e-4, -1e-4, 5e-5)),
+             particle((3.0, 2.0, 2.0), (29.2, 15.6, 27.9), random_quaternion(g), F_ext=(-5e-5, 1e-4, 1e-4))]
+    return b, parts
+
+
+def _sim(b, parts):
+    return L.Simulation([b], [parts], max_semi=int(math.ceil(max(max(p["semi"]) for p in parts))))
+
+
+def _gpu_stokes(sim, b):
+    N = b["nx"] * b["ny"] * b["nz"]
+    u = torch.zeros(3 * N, dtype=torch.float32, device="cuda")
+    L.lb_stokes_field(sim.ctx, 0, u.data_ptr())
+    return u
+
+
+def test_stokes_field_matches_reference():
+    b, parts = _case()
+    sim = _sim(b, parts)
+    u = _gpu_stokes(sim, b).cpu().numpy().reshape(3, b["nz"], b["ny"], b["nx"])
+    owner = sim.field("solid")
+    mu = b["rho0"] * (b["tau"] - 0.5) / 3.0
+    ref = W.stokes_field(b["nx"], b["ny"], b["nz"], owner, [p["F_ext"] for p in parts], mu, counter=True)
+    err = normwise(u, ref)
+    print("stokes error", err)
+    assert err <= 1e-4
+
+
+def test_run_from_initial_fluid_matches_oracle():
+    """Start both sides from f = f_eq(rho0, u_Stokes) and compare every field
+    and particle value over 40 steps."""
+    b, parts = _case()
+    sim = _sim(b, parts)
+    ud = _gpu_stokes(sim, b)
+    L.lb_init_fluid(sim.ctx, 0, ud.data_ptr(), ud.numel() * 4, True)
+    u = ud.cpu().numpy().astype(np.float64).reshape(3, b["nz"], b["ny"], b["nx"])
+    o = O.Sim(b, parts, nthreads=8)
+    co, wo = O.lattice()
+    f = o.f()
+    fluid = o.owner() == 0
+    feq = W.equilibrium_f(u, b["rho0"], co, wo)
+    f[fluid] = feq[fluid]
+    o.set_f(f)
+    # before the first collision the read-back is the initial field itself
+    assert normwise(sim.field("df"), oracle_df_gpu_layout(o, b["rho0"])) <= 1e-6
+    worst = {"df": 0.0, "u": 0.0, "F": 0.0}
+    for _ in range(8):
+        sim.step(5)
+        o.step(5)
+        worst["df"] = max(worst["df"], normwise(sim.field("df"), oracle_df_gpu_layout(o, b["rho0"])))
+        _, ur = o.moments()
+        worst["u"] = max(worst["u"], normwise(sim.field("u"), np.moveaxis(ur, -1, 0)))
+        for p in range(2):
+            worst["F"] = max(worst["F"], normwise(sim.particle(0, p)["F"], o.particle(p)["F"]))
+    print("warm-start parity", worst)
+    assert worst["df"] <= 1e-5 and worst["u"] <= 1e-5 and worst["F"] <= 1e-5
+
+
+def test_features_targets_and_velocities_match_reference():
+    g = np.random.default_rng(5)
+    n = 50
+    e = g.normal(0, 1, (n, 3))
+    e /= np.linalg.norm(e, axis=1, keepdims=True)
+    geom = np.column_stack([g.uniform(2, 9, n), g.uniform(2, 4, n), g.uniform(0.1, 0.25, n), g.uniform(24, 64, n),
+                            e, np.ones(n)])
+    A = g.normal(0, 1, (n, 6, 6))
+    M = np.einsum("nik,njk->nij", A, A) * 1e-3 + 1e-2 * np.eye(6)
+    FT = g.normal(0, 1e-4, (n, 6))
+    gd = torch.from_numpy(geom).cuda()
+    x = torch.zeros((n, 8), dtype=torch.float32, device="cuda")
+    SU.lb_mlp_features(gd.data_ptr(), n, x.data_ptr())
+    Md = torch.from_numpy(M.reshape(n, 36)).cuda()
+    Rh = torch.zeros((n, 36), dtype=torch.float32, device="cuda")
+    SU.lb_resistance_targets(Md.data_ptr(), gd.data_ptr(), n, Rh.data_ptr())
+    FTd = torch.from_numpy(FT).cuda()
+    UW = torch.zeros((n, 6), dtype=torch.float64, device="cuda")
+    SU.lb_warm_velocities(Rh.data_ptr(), gd.data_ptr(), FTd.data_ptr(), n, UW.data_ptr())
+    torch.cuda.synchronize()
+    assert normwise(x.cpu().numpy(), W.features(geom)) <= 2e-7
+    Rref = W.targets(M, geom)
+    assert normwise(Rh.cpu().numpy().reshape(n, 6, 6), Rref) <= 2e-6
+    Rf = Rh.cpu().numpy().astype(np.float64)
+    assert normwise(UW.cpu().numpy(), W.warm_velocities(Rf, geom, FT)) <= 1e-10

@@ -1,0 +1,79 @@
+"""Pins of the warm-start reference (oracle/warmstart.py): closed forms of the
+lattice Stokes solve, its projection, the symmetry of the periodic Green's
+function, Stokes' law through the scaling, and the head-tail symmetry of the
+features."""
+import numpy as np
+import pytest
+
+from oracle import warmstart as W
+
+
+def test_single_mode_force_gives_the_closed_form_shear_wave():
+    """g = F0 sin(2 pi y / ny) x: divergence-free, so no pressure, and
+    mu Lap_h u = -g with the 7-point Laplacian, whose eigenvalue on that mode is
+    -4 sin^2(pi / ny): u_x = F0 sin(2 pi y / ny) / (4 mu sin^2(pi / ny))."""
+    nx, ny, nz, mu, F0 = 6, 20, 5, 0.1, 1e-3
+    y = np.arange(ny)
+    g = np.zeros((3, nz, ny, nx))
+    g[0] = (F0 * np.sin(2 * np.pi * y / ny))[None, :, None]
+    u = W.stokes_solve(g, mu)
+    exact = F0 * np.sin(2 * np.pi * y / ny) / (4 * mu * np.sin(np.pi / ny) ** 2)
+    assert np.allclose(u[0], exact[None, :, None], rtol=0, atol=1e-15)
+    assert np.abs(u[1:]).max() < 1e-18
+    # the same through a real-space 7-point Laplacian: mu Lap_h u + g = 0
+    lap = sum(np.roll(u[0], s, axis=a) for a in range(3) for s in (1, -1)) - 6 * u[0]
+    assert np.allclose(mu * lap + g[0], 0.0, atol=1e-15)
+
+
+def test_flow_is_projected_and_has_zero_mean():
+    g = np.random.default_rng(0).normal(0, 1, (3, 7, 9, 8))
+    u = W.stokes_solve(g, 0.2)
+    nz, ny, nx = u.shape[1:]
+    kt = [2 * np.sin(np.pi * np.arange(n) / n) for n in (nx, ny, nz)]
+    uh = [np.fft.fftn(u[c]) for c in range(3)]
+    div = kt[0][None, None, :] * uh[0] + kt[1][None, :, None] * uh[1] + kt[2][:, None, None] * uh[2]
+    assert np.abs(div).max() < 1e-12 * np.abs(uh[0]).max()
+    assert np.abs(u.mean(axis=(1, 2, 3))).max() < 1e-15
+
+
+def test_periodic_greens_function_is_symmetric():
+    """Response at node a along i to a unit force at node b along j equals the
+    response at b along j to a unit force at a along i."""
+    shape = (6, 7, 8)
+    a, b = (1, 2, 3), (4, 0, 6)
+    for i in range(3):
+        for j in range(3):
+            ga = np.zeros((3,) + shape)
+            ga[i][a] = 1.0
+            gb = np.zeros((3,) + shape)
+            gb[j][b] = 1.0
+            ua, ub = W.stokes_solve(ga, 0.3), W.stokes_solve(gb, 0.3)
+            assert ub[i][a] == pytest.approx(ua[j][b], rel=1e-12, abs=1e-15)
+
+
+def test_particle_force_spread_and_counter_force():
+    owner = np.zeros((4, 5, 6), np.int32)
+    owner[1:3, 2, 2:4] = 1
+    u = W.stokes_field(6, 5, 4, owner, [[1e-3, 0, 0]], 0.1, counter=True)
+    # with the counter force the total force is zero; the flow follows the force
+    assert u[0][owner == 1].mean() > 0 and abs(u.mean()) < 1e-15
+
+
+def test_scaling_gives_stokes_law_for_the_reference_sphere():
+    """R = D^2 (a radius-b sphere in free space) is R^ = I, and the warm-start
+    velocity is then U = F / (6 pi mu b), Omega = T / (8 pi mu b^3)."""
+    geom = np.array([[3.0, 3.0, 0.1, 64.0, 0.0, 0.0, 1.0, 1.0]])
+    mu, b = 0.1, 3.0
+    D2 = np.diag([6 * np.pi * mu * b] * 3 + [8 * np.pi * mu * b ** 3] * 3)
+    assert np.allclose(W.targets(np.linalg.inv(D2)[None], geom)[0], np.eye(6), atol=1e-12)
+    FT = np.array([[1e-3, 2e-3, -1e-3, 1e-2, 0, 5e-3]])
+    UW = W.warm_velocities(np.eye(6)[None], geom, FT)[0]
+    assert np.allclose(UW[:3], FT[0, :3] / (6 * np.pi * mu * b), rtol=1e-13)
+    assert np.allclose(UW[3:], FT[0, 3:] / (8 * np.pi * mu * b ** 3), rtol=1e-13)
+
+
+def test_features_are_head_tail_symmetric():
+    g = np.array([[6.0, 3.0, 0.1, 32.0, 0.6, 0.0, -0.8, 1.0], [6.0, 3.0, 0.1, 32.0, -0.6, 0.0, 0.8, 1.0]])
+    x = W.features(g)
+    assert np.array_equal(x[0], x[1])
+    assert np.allclose(x[0], [0.0, 0.0, (0.1 - 1 / 6) * 10, 3 / 32 * 10 - 1, -0.6, 0.0, 0.8, 1.0])
