@@ -214,30 +214,39 @@ lb_status lb_links_noalloc(const double* semi, const double* q, const double* x,
                            void* stream);
 
 /* Sets the initial fluid of box `box` (before the first lb_step, after
- * lb_set_particles) to the local equilibrium f_i = f_eq_i(rho0, u(x)) of the
- * velocity field u (FP32 [3][nz][ny][nx], host memory or, if u_is_device,
- * device memory; u_bytes = 3*N*4) on every fluid node; solid and wall nodes keep
- * no distributions.  The first iteration then collides these distributions in
- * place (the Appendix's step 1 at t = 0) instead of the rest state.  Not part
- * of the paper: this is the fluid half of the learned warm start
- * (lbsurrogate.h).  Waits for completion.
+ * lb_set_particles) to the local equilibrium f_i = f_eq_i(rho0 + drho(x), u(x))
+ * of the velocity field u (FP32 [3][nz][ny][nx], u_bytes = 3*N*4) and the
+ * density deviation drho (FP32 [nz][ny][nx], NULL = uniform rho0) on every fluid
+ * node; solid and wall nodes keep no distributions.  u and drho are host memory,
+ * or device memory if is_device.  The first iteration then collides these
+ * distributions in place (the Appendix's step 1 at t = 0) instead of the rest
+ * state.  Not part of the paper: this is the fluid half of the learned warm
+ * start (lbsurrogate.h).  Waits for completion.
  * Errors: LB_EINVAL (bad box or size), LB_ESTATE (after a step), LB_ECUDA. */
-lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, size_t u_bytes, int32_t u_is_device,
-                        void* stream);
+lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, size_t u_bytes, const float* drho,
+                        int32_t is_device, void* stream);
 
 /* The periodic Stokes flow (mu Lap u - grad p + g = 0, div u = 0, mu = rho0 nu)
  * driven by the particles of box `box`: g puts each particle's F_ext uniformly on
- * its solid nodes and the box's body force plus, with counter_force, the
- * balancing -sum F_ext / N_fluid on the fluid nodes; a net mean force is
- * dropped.  Solved in Fourier space with the symbols of the lattice's
- * nearest-neighbour operators (DFTs on the device).  u_dev: device FP32
- * [3][nz][ny][nx].  Fully periodic boxes only, before the first step (it reads
- * the particles' initial solid nodes).  This is the long-range part of a warm
- * start (feed it to lb_init_fluid): the diffusive development of this flow
- * over the whole box is what makes a cold start slow.  Not part of the paper.
- * Waits for completion.  Errors: LB_EINVAL (walls, edge > 4096), LB_ESTATE,
- * LB_ENOMEM, LB_ECUDA. */
-lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, void* stream);
+ * the fluid nodes next to it (a face neighbour is its solid node: a uniform
+ * traction just outside the surface, under which a sphere's interior moves
+ * rigidly at its Stokes velocity) and the box's body force plus, with
+ * counter_force, the balancing -sum F_ext / N_fluid on the fluid nodes; a net
+ * mean force is dropped.  Solved in Fourier space with the symbols of the
+ * lattice's nearest-neighbour operators (DFTs on the device); then a uniform
+ * velocity is added on the fluid nodes so that rho0 sum_fluid u + sum_p M_p U_p
+ * = 0 with the particles' current (initial) velocities, the total momentum of a
+ * run that starts from rest under balanced forces.  u_dev: device FP32
+ * [3][nz][ny][nx]; drho_dev (device FP32 [nz][ny][nx], may be NULL): the density
+ * deviation p / c_s^2 of the flow's pressure (zero mean over the fluid nodes),
+ * which the lattice fluid needs to balance the forces at steady state.  Fully
+ * periodic boxes only, before the first step (it reads the particles' initial
+ * solid nodes).  This is the long-range part of a warm start (feed both to
+ * lb_init_fluid): the diffusive development of this flow and the acoustic
+ * settling of its pressure over the whole box are what make a cold start slow.
+ * Not part of the paper.  Waits for completion.
+ * Errors: LB_EINVAL (walls, edge > 4096), LB_ESTATE, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, float* drho_dev, void* stream);
 
 /* The library's D3Q19 table: c[19][3] and w[19] (1/3, 1/18, 1/36). */
 void lb_lattice(int32_t* c57, double* w19);

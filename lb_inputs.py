@@ -132,3 +132,68 @@ def random_pose(g: np.random.Generator, n: int, margin: float):
     else:
         c = g.uniform(0.0, n, size=3)
     return [float(v) for v in c], random_quaternion(g)
+
+
+def unit_vector(g: np.random.Generator) -> list:
+    """Uniform random direction (normalised Gaussian triple)."""
+    v = g.normal(0.0, 1.0, 3)
+    return [float(x) for x in v / np.linalg.norm(v)]
+
+
+def long_axis_quaternion(e) -> list:
+    """A unit quaternion turning the body x axis onto the unit vector e (the
+    roll about e is irrelevant for a spheroid with b = c)."""
+    e = np.asarray(e, np.float64)
+    ax = np.cross([1.0, 0.0, 0.0], e)
+    s = np.linalg.norm(ax)
+    if s < 1e-12:
+        return [1.0, 0.0, 0.0, 0.0] if e[0] > 0 else [0.0, 0.0, 0.0, 1.0]
+    return axis_angle_quaternion(ax, math.atan2(s, e[0]))
+
+
+def resistance_samples(seed: int, n: int, L: int, taus=(0.8, 1.0, 1.2), aspect=(1.0, 3.0), b_range=(2.0, 3.5)):
+    """n spheroids for resistance runs in periodic L^3 boxes: aspect ratio
+    r = a/b and b uniform in the ranges, tau drawn from taus, long axis e
+    uniform on the sphere, centre = box centre + U(-0.5,0.5)^3."""
+    g = rng(seed)
+    out = []
+    for _ in range(n):
+        r = float(g.uniform(*aspect))
+        b = float(g.uniform(*b_range))
+        tau = float(g.choice(taus))
+        e = unit_vector(g)
+        centre = [0.5 * L + v for v in g.uniform(-0.5, 0.5, size=3)]
+        out.append(dict(a=r * b, b=b, tau=tau, L=int(L), e=e, q=long_axis_quaternion(e), x=centre))
+    return out
+
+
+def many_spheroids(seed: int = 0, n: int = 128, count: int = 16, aspect=(1.5, 2.5), b_range=(2.5, 3.0),
+                   force=2e-5, tau=1.0, gap: int = 2, max_semi: int = 8):
+    """`count` spheroids in one periodic n^3 box with random orientations and
+    external forces of magnitude `force` in random directions (counter body
+    force on the fluid).  Centres by rejection sampling so that the bounding
+    cubes of side 2 (max_semi + 2) + 2 keep `gap` nodes between them
+    (periodically)."""
+    g = rng(seed)
+    S = 2 * (max_semi + 2) + 2 + gap
+    centres = []
+    while len(centres) < count:
+        c = g.uniform(0.0, n, size=3)
+        ok = True
+        for d in centres:
+            dd = np.abs(c - d)
+            dd = np.minimum(dd, n - dd)
+            if np.all(dd < S):
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+    parts = []
+    for c in centres:
+        r = float(g.uniform(*aspect))
+        b = float(g.uniform(*b_range))
+        e = unit_vector(g)
+        f = unit_vector(g)
+        parts.append(particle((r * b, b, b), [float(v) for v in c], long_axis_quaternion(e),
+                              F_ext=[force * v for v in f]))
+    return [box(n, n, n, tau, counter_force=1)], [parts]

@@ -9,10 +9,14 @@ Stokes flow on the periodic lattice: mu Lap u - grad p + g = 0, div u = 0,
 solved mode by mode with numpy's FFT as the transform.  With kt_d =
 2 sin(pi k_d / n_d), |kt|^2 is the symbol of the 7-point Laplacian and the
 flow is u^ = (g^ - kt (kt . g^) / |kt|^2) / (mu |kt|^2), u^(0) = 0.  g puts
-each particle's F_ext uniformly on its solid nodes, and the body force plus
-(with counter_force) -sum F_ext / N_fluid on the fluid nodes.  Pinned by the
+each particle's F_ext uniformly on the fluid nodes next to it (a face
+neighbour is its solid node), and the body force plus
+(with counter_force) -sum F_ext / N_fluid on the fluid nodes; the mean flow
+on the fluid nodes is then shifted so that fluid and particle momenta add up to
+zero (the total momentum of a run started from rest).  Pinned by the
 single-mode closed form, the projection (divergence-free in the lattice
-symbol) and the symmetry of the periodic Green's function
+symbol), the closed form of a curl-free force's pressure and the symmetry of
+the periodic Green's function
 (tests/test_oracle_warmstart.py).
 
 Scaling: D = diag(s_t I3, s_r I3), s_t^2 = 6 pi mu b, s_r^2 = 8 pi mu b^3
@@ -24,9 +28,13 @@ from __future__ import annotations
 import numpy as np
 
 
-def stokes_field(nx, ny, nz, owner, F_ext, mu, counter=False, body=(0.0, 0.0, 0.0)):
+def stokes_field(nx, ny, nz, owner, F_ext, mu, counter=False, body=(0.0, 0.0, 0.0), MU=None, rho0=1.0,
+                 density=False):
     """u[3, nz, ny, nx]; owner[nz, ny, nx] (0 fluid, p+1 particle p, -1 wall);
-    F_ext[np, 3]."""
+    F_ext[np, 3].  The fluid's mean is then shifted so that rho0 sum_fluid u +
+    sum_p M_p U_p = 0 (MU[np, 3] = M_p U_p; zero if None).  With density=True
+    returns (u, drho), drho the pressure's density deviation with zero sum over
+    the fluid nodes."""
     owner = np.asarray(owner)
     F = np.asarray(F_ext, np.float64).reshape(-1, 3)
     g = np.zeros((3, nz, ny, nx))
@@ -35,12 +43,49 @@ def stokes_field(nx, ny, nz, owner, F_ext, mu, counter=False, body=(0.0, 0.0, 0.
     for k in range(3):
         gk = np.zeros((nz, ny, nx))
         gk[fluid] = body[k] - (F[:, k].sum() / nfl if (counter and nfl) else 0.0)
+        shell = shell_owner(owner)
         for p in range(F.shape[0]):
-            m = owner == p + 1
+            m = shell == p + 1
             if m.any():
-                gk[m] = F[p, k] / m.sum()
+                gk[m] += F[p, k] / m.sum()
         g[k] = gk
-    return stokes_solve(g, mu)
+    u = stokes_solve(g, mu)
+    P = np.zeros(3) if MU is None else np.asarray(MU, np.float64).reshape(-1, 3).sum(0)
+    for k in range(3):
+        u[k][fluid] += (-P[k] / rho0 - u[k][fluid].sum()) / nfl
+    if not density:
+        return u
+    d = pressure_density(g)
+    d[fluid] -= d[fluid].sum() / nfl
+    return u, d
+
+
+def pressure_density(g):
+    """drho = p / c_s^2 = 3 p of the Stokes pressure, grad_c p = P_long g with
+    the central difference: p^ = -i (s . g^) / |s|^2, s_d = sin(2 pi k_d / n_d),
+    p^ = 0 where |s| = 0."""
+    _, nz, ny, nx = g.shape
+    s = [np.broadcast_to(np.sin(2 * np.pi * np.arange(nx) / nx)[None, None, :], (nz, ny, nx)),
+         np.broadcast_to(np.sin(2 * np.pi * np.arange(ny) / ny)[None, :, None], (nz, ny, nx)),
+         np.broadcast_to(np.sin(2 * np.pi * np.arange(nz) / nz)[:, None, None], (nz, ny, nx))]
+    s2 = s[0] ** 2 + s[1] ** 2 + s[2] ** 2
+    gh = [np.fft.fftn(g[c]) for c in range(3)]
+    ph = -1j * (s[0] * gh[0] + s[1] * gh[1] + s[2] * gh[2]) / np.where(s2 > 1e-12, s2, 1.0)
+    ph[s2 <= 1e-12] = 0.0
+    return 3.0 * np.real(np.fft.ifftn(ph))
+
+
+def shell_owner(owner):
+    """For each fluid node, the particle (p + 1) owning one of its 6 face
+    neighbours (periodic), 0 if none; with several, the first in the order
+    -x, -y, -z, +x, +y, +z."""
+    owner = np.asarray(owner)
+    out = np.zeros_like(owner)
+    for sh in (1, -1):
+        for a in (2, 1, 0):             # x, y, z of an [nz, ny, nx] array
+            nb = np.roll(owner, sh, axis=a)
+            out = np.where((out == 0) & (nb > 0), nb, out)
+    return np.where(owner == 0, out, 0)
 
 
 def stokes_solve(g, mu):
@@ -62,14 +107,15 @@ def stokes_solve(g, mu):
     return u
 
 
-def equilibrium_f(u, rho0, c, w):
-    """f_i = w_i [rho0 + rho0 (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)] for u[3, ...]
-    (the second-order equilibrium at density rho0); returns [..., 19] in the
-    order of the table (c, w) given."""
+def equilibrium_f(u, rho, c, w):
+    """f_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u) for u[3, ...] and a
+    density rho (scalar or [...]): the second-order equilibrium; returns
+    [..., 19] in the order of the table (c, w) given."""
     u = np.moveaxis(np.asarray(u, np.float64), 0, -1)
     cu = u @ np.asarray(c, np.float64).T
     uu = (u * u).sum(-1, keepdims=True)
-    return np.asarray(w) * rho0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)
+    rho = np.asarray(rho, np.float64)[..., None] if np.ndim(rho) else rho
+    return np.asarray(w) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)
 
 
 def features(geom):

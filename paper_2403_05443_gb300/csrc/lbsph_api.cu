@@ -31,10 +31,11 @@ cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const 
                         unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, cudaStream_t s);
 cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
                          int cap, int* count, cudaStream_t s);
-cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const int* owner,
-                              cudaStream_t s);
+cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const float* drho,
+                              const int* owner, cudaStream_t s);
 cudaError_t launch_stokes(const BoxDev& B, const int* owner, const PartDev* pd, int np, int counter_on,
-                          const double body[3], float mu, float2* work, int* counts, float* u, cudaStream_t s);
+                          const double body[3], float mu, float2* work, int* counts, double* sum, float* u,
+                          cudaStream_t s);
 }  // namespace lbsph
 
 using namespace lbsph;
@@ -761,8 +762,8 @@ static cudaError_t owner_field(lb_ctx* ctx, int box, cudaStream_t s)
     return launch_fields(k, ctx->opt.precision, ctx->hbox[box].nblocks, s);
 }
 
-extern "C" lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, size_t u_bytes, int32_t u_is_device,
-                                   void* stream)
+extern "C" lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, size_t u_bytes, const float* drho,
+                                   int32_t is_device, void* stream)
 {
     if (!ctx) return LB_EINVAL;
     if (box < 0 || box >= (int)ctx->desc.size() || !u) return fail(ctx, LB_EINVAL, "bad box or field");
@@ -775,16 +776,19 @@ extern "C" lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, siz
         ctx->d_tmp = (float*)dev_alloc(ctx, ctx->tmp_bytes);
         if (!ctx->d_tmp) return fail(ctx, LB_ENOMEM, "field staging buffer");
     }
-    float* ud = ctx->d_tmp + B.N;                      // [3][N] after the owner field
+    float* ud = ctx->d_tmp + B.N;                      // [3][N] after the owner field, then drho [N]
+    float* dd = drho ? ctx->d_tmp + 4 * B.N : nullptr;
+    const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
-    CK(cudaMemcpyAsync(ud, u, u_bytes, u_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ud, u, u_bytes, kind, s));
+    if (dd) CK(cudaMemcpyAsync(dd, drho, (size_t)B.N * sizeof(float), kind, s));
     CK(owner_field(ctx, box, s));
-    CK(launch_init_fluid(B, ctx->opt.precision, ctx->fbuf[ctx->cur], ud, reinterpret_cast<int*>(ctx->d_tmp), s));
+    CK(launch_init_fluid(B, ctx->opt.precision, ctx->fbuf[ctx->cur], ud, dd, reinterpret_cast<int*>(ctx->d_tmp), s));
     CK(cudaStreamSynchronize(s));
     return read_status(ctx);
 }
 
-extern "C" lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, void* stream)
+extern "C" lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, float* drho_dev, void* stream)
 {
     if (!ctx) return LB_EINVAL;
     if (box < 0 || box >= (int)ctx->desc.size() || !u_dev) return fail(ctx, LB_EINVAL, "bad box or output");
@@ -802,15 +806,20 @@ extern "C" lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, voi
     if (!ctx->d_stokes) {
         long long nmax = 0;
         for (auto& h : ctx->hbox) nmax = std::max(nmax, h.N);
-        ctx->d_stokes = (float2*)dev_alloc(ctx, sizeof(float2) * 6 * (size_t)nmax);
-        ctx->d_counts = (int*)dev_alloc(ctx, sizeof(int) * (size_t)(ctx->maxp + 1));
+        ctx->d_stokes = (float2*)dev_alloc(ctx, sizeof(float2) * 8 * (size_t)nmax);
+        // np + 1 counts, then (8-byte aligned) 4 double sums
+        ctx->d_counts = (int*)dev_alloc(ctx, sizeof(double) * ((size_t)(ctx->maxp + 2) / 2 + 4));
         if (!ctx->d_stokes || !ctx->d_counts) return fail(ctx, LB_ENOMEM, "Stokes work buffers");
     }
     CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     CK(owner_field(ctx, box, s));
     const double mu = d.rho0 * (d.tau - 0.5) / 3.0;
+    float* out = ctx->d_tmp + B.N;                     // [4][N]: u, then drho
     CK(launch_stokes(B, reinterpret_cast<int*>(ctx->d_tmp), ctx->d_pd + B.pbeg, B.pcnt, d.counter_force,
-                     d.body_force, (float)mu, ctx->d_stokes, ctx->d_counts, u_dev, s));
+                     d.body_force, (float)mu, ctx->d_stokes, ctx->d_counts,
+                     reinterpret_cast<double*>(ctx->d_counts) + (ctx->maxp + 2) / 2, out, s));
+    CK(cudaMemcpyAsync(u_dev, out, 3ull * B.N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (drho_dev) CK(cudaMemcpyAsync(drho_dev, out + 3 * B.N, (size_t)B.N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
     return read_status(ctx);
 }

@@ -1,14 +1,19 @@
 // Warm start of a run (lb_init_fluid, lb_stokes_field): an initial fluid at
-// the local equilibrium of a given velocity field, and the periodic Stokes flow
-// driven by the particles' external forces, as that field.
+// the local equilibrium of given velocity and density fields, and the periodic
+// Stokes flow (with its pressure) driven by the particles' external forces, as
+// those fields.
 //
 // Stokes flow (mu Lap u - grad p + g = 0, div u = 0 on the periodic lattice):
-// the force density g puts F_ext of each particle uniformly on its solid nodes
+// the force density g puts F_ext of each particle uniformly on the fluid
+// nodes next to it
 // and the box's uniform counter force and body force on the fluid nodes; the
 // mean of g (if the forces do not balance) is dropped.  In Fourier space, with
 // kt_d = 2 sin(pi k_d / n_d) (the symbol of the nearest-neighbour difference,
 // so that |kt|^2 is the symbol of the 7-point Laplacian),
 //   u^(k) = (g^ - kt (kt . g^) / |kt|^2) / (mu |kt|^2),  u^(0) = 0.
+// The mean flow is then set so that the fluid and particle momenta add up to
+// zero (rho0 sum_fluid u = -sum_p M_p U_p, with the particles' initial
+// velocities), as they do in a run from rest with a balancing counter force.
 // The transforms are separable DFTs along x, y and z computed by definition,
 // one output element per thread with the line's twiddle table in shared
 // memory (box edges are not powers of two in general); FP32 complex.
@@ -16,9 +21,10 @@
 
 namespace lbsph {
 
-// f = f_eq(rho0, u) - w rho0 on fluid nodes (deviation storage), 0 elsewhere
+// f = f_eq(rho0 + drho, u) - w rho0 on fluid nodes (deviation storage), 0
+// elsewhere; drho may be null (uniform density)
 template <class St>
-__global__ void init_fluid_kernel(const BoxDev B, void* fbuf, const float* u, const int* owner)
+__global__ void init_fluid_kernel(const BoxDev B, void* fbuf, const float* u, const float* drho, const int* owner)
 {
     using T = typename St::T;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -27,50 +33,80 @@ __global__ void init_fluid_kernel(const BoxDev B, void* fbuf, const float* u, co
     const bool fluid = owner[n] == 0;
     const float ux = fluid ? u[n] : 0.0f, uy = fluid ? u[B.N + n] : 0.0f, uz = fluid ? u[2 * B.N + n] : 0.0f;
     const float uu = ux * ux + uy * uy + uz * uz;
+    const float dr = (fluid && drho) ? drho[n] : 0.0f;
+    const float rho = B.rho0f + dr;
     const unsigned long long pol = l2_evict_normal();
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
-        const float d = fluid ? w_of(i) * B.rho0f * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu) : 0.0f;
+        const float d = fluid ? w_of(i) * (dr + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu)) : 0.0f;
         St::st1(f + (long long)i * B.N + n, d, B.scale, pol);
     }
 }
 
-// solid-node count of each particle of the box (owner = p + 1) and fluid count
-__global__ void count_owner_kernel(const int* owner, long long N, int* counts, int np)
+// shell owner of a fluid node: the particle (p + 1) owning one of its six face
+// neighbours, 0 if none (periodic; the first one found if several)
+__device__ __forceinline__ int shell_owner(const int* owner, int nx, int ny, int nz, long long n)
 {
-    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const int o = owner[n];
-    if (o > 0 && o <= np) atomicAdd(counts + o, 1);
-    else if (o == 0) atomicAdd(counts, 1);
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    const int xs[2] = {x == 0 ? nx - 1 : x - 1, x == nx - 1 ? 0 : x + 1};
+    const int ys[2] = {y == 0 ? ny - 1 : y - 1, y == ny - 1 ? 0 : y + 1};
+    const int zs[2] = {z == 0 ? nz - 1 : z - 1, z == nz - 1 ? 0 : z + 1};
+    const long long row = (long long)nx * ny;
+    int o = 0;
+    for (int k = 0; k < 2; ++k) {
+        const int a = owner[z * row + (long long)y * nx + xs[k]];
+        const int b = owner[z * row + (long long)ys[k] * nx + x];
+        const int c = owner[zs[k] * row + (long long)y * nx + x];
+        if (o == 0 && a > 0) o = a;
+        if (o == 0 && b > 0) o = b;
+        if (o == 0 && c > 0) o = c;
+    }
+    return o;
 }
 
-// force density as complex [3][N]: F_ext / nsolid on a particle's solid nodes,
-// the body force plus (counter_on) -sum F_ext / N_fluid on fluid nodes
-__global__ void force_density_kernel(const int* owner, long long N, const int* counts, const PartDev* pd, int np,
-                                     int counter_on, double bx, double by, double bz, float2* g)
+// shell-node count of each particle of the box (fluid nodes next to it) and
+// fluid count
+__global__ void count_owner_kernel(const int* owner, int nx, int ny, int nz, int* counts, int np)
 {
+    const long long N = (long long)nx * ny * nz;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= N || owner[n] != 0) return;
+    atomicAdd(counts, 1);
+    const int o = shell_owner(owner, nx, ny, nz, n);
+    if (o > 0 && o <= np) atomicAdd(counts + o, 1);
+}
+
+// force density as complex [3][N]: F_ext / nshell on the fluid nodes next to
+// a particle (a uniform traction just outside its surface, under which a
+// sphere's interior moves rigidly at its Stokes velocity), plus the body force
+// and (counter_on) -sum F_ext / N_fluid on every fluid node
+__global__ void force_density_kernel(const int* owner, int nx, int ny, int nz, const int* counts, const PartDev* pd,
+                                     int np, int counter_on, double bx, double by, double bz, float2* g)
+{
+    const long long N = (long long)nx * ny * nz;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int o = owner[n];
     double f[3] = {0.0, 0.0, 0.0};
-    if (o > 0 && o <= np) {
-        const double c = 1.0 / (double)counts[o];
-        for (int k = 0; k < 3; ++k) f[k] = pd[o - 1].Fext[k] * c;
-    } else if (o == 0) {
+    if (owner[n] == 0) {
         f[0] = bx; f[1] = by; f[2] = bz;
         if (counter_on && counts[0] > 0) {
             for (int p = 0; p < np; ++p)
                 for (int k = 0; k < 3; ++k) f[k] -= pd[p].Fext[k] / (double)counts[0];
+        }
+        const int o = shell_owner(owner, nx, ny, nz, n);
+        if (o > 0 && o <= np) {
+            const double c = 1.0 / (double)counts[o];
+            for (int k = 0; k < 3; ++k) f[k] += pd[o - 1].Fext[k] * c;
         }
     }
     for (int k = 0; k < 3; ++k) g[k * N + n] = make_float2((float)f[k], 0.0f);
 }
 
 // one DFT pass along one axis: out(.., k, ..) = sum_j in(.., j, ..) w^(j k),
-// w = exp(sign 2 pi i / n); three components of [nz][ny][nx] each
-__global__ void dft_axis_kernel(const float2* in, float2* out, int nx, int ny, int nz, int axis, float sign)
+// w = exp(sign 2 pi i / n); ncomp components of [nz][ny][nx] each
+__global__ void dft_axis_kernel(const float2* in, float2* out, int nx, int ny, int nz, int axis, float sign,
+                                int ncomp)
 {
     extern __shared__ float2 tw[];
     const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
@@ -82,7 +118,7 @@ __global__ void dft_axis_kernel(const float2* in, float2* out, int nx, int ny, i
     __syncthreads();
     const long long N = (long long)nx * ny * nz;
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= 3 * N) return;
+    if (e >= ncomp * N) return;
     const int comp = (int)(e / N);
     const long long r = e - comp * N;
     const int x = (int)(r % nx), y = (int)((r / nx) % ny), z = (int)(r / ((long long)nx * ny));
@@ -102,7 +138,10 @@ __global__ void dft_axis_kernel(const float2* in, float2* out, int nx, int ny, i
     out[e] = make_float2(ar, ai);
 }
 
-// u^ = P g^ / (mu |kt|^2) in place; also folds in the 1/N of the inverse DFT
+// u^ = P g^ / (mu |kt|^2) in place, and the density deviation of the
+// pressure, drho^ = p^ / c_s^2 = -3 i (s . g^) / |s|^2 with s_d = sin(2 pi k_d /
+// n_d) (the central difference, as the lattice's momentum balance sees the
+// pressure gradient), into component 3; folds in the 1/N of the inverse DFT
 __global__ void stokes_solve_kernel(float2* g, int nx, int ny, int nz, float mu)
 {
     const long long N = (long long)nx * ny * nz;
@@ -111,11 +150,19 @@ __global__ void stokes_solve_kernel(float2* g, int nx, int ny, int nz, float mu)
     const int x = (int)(r % nx), y = (int)((r / nx) % ny), z = (int)(r / ((long long)nx * ny));
     const float kx = 2.0f * sinpif((float)x / (float)nx), ky = 2.0f * sinpif((float)y / (float)ny),
                 kz = 2.0f * sinpif((float)z / (float)nz);
-    const float k2 = kx * kx + ky * ky + kz * kz;
-    float2 a = g[r], b = g[N + r], c = g[2 * N + r];
+    const float sx = sinpif(2.0f * (float)x / (float)nx), sy = sinpif(2.0f * (float)y / (float)ny),
+                sz = sinpif(2.0f * (float)z / (float)nz);
+    const float k2 = kx * kx + ky * ky + kz * kz, s2 = sx * sx + sy * sy + sz * sz;
+    float2 a = g[r], b = g[N + r], c = g[2 * N + r], d = make_float2(0.0f, 0.0f);
     if (r == 0 || k2 == 0.0f) {
         a = b = c = make_float2(0.0f, 0.0f);
     } else {
+        if (s2 > 1e-12f) {
+            // -3 i (s . g^) / |s|^2 / N
+            const float re = sx * a.x + sy * b.x + sz * c.x, im = sx * a.y + sy * b.y + sz * c.y;
+            const float q = 3.0f / (s2 * (float)N);
+            d = make_float2(im * q, -re * q);
+        }
         const float pr = (kx * a.x + ky * b.x + kz * c.x) / k2, pi = (kx * a.y + ky * b.y + kz * c.y) / k2;
         const float sc = 1.0f / (mu * k2 * (float)N);
         a = make_float2((a.x - kx * pr) * sc, (a.y - kx * pi) * sc);
@@ -125,6 +172,7 @@ __global__ void stokes_solve_kernel(float2* g, int nx, int ny, int nz, float mu)
     g[r] = a;
     g[N + r] = b;
     g[2 * N + r] = c;
+    g[3 * N + r] = d;
 }
 
 __global__ void real_part_kernel(const float2* g, long long n3, float* u)
@@ -133,45 +181,79 @@ __global__ void real_part_kernel(const float2* g, long long n3, float* u)
     if (e < n3) u[e] = g[e].x;
 }
 
+// sum over fluid nodes of u and drho (4 doubles), one atomic per warp
+__global__ void fluid_sum_kernel(const float* u, const int* owner, long long N, double* sum)
+{
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (n < N && owner[n] == 0)
+        for (int k = 0; k < 4; ++k) v[k] = u[k * N + n];
+    for (int k = 0; k < 4; ++k) {
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if ((threadIdx.x & 31) == 0 && v[k] != 0.0) atomicAdd(sum + k, v[k]);
+    }
+}
+
+// uniform shift of the fluid so that fluid + particle momentum is zero:
+// rho0 sum_fluid u + sum_p M_p U_p = 0
+__global__ void momentum_shift_kernel(float* u, const int* owner, long long N, const double* sum, const int* counts,
+                                      const PartDev* pd, int np, double rho0)
+{
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= N || owner[n] != 0 || counts[0] == 0) return;
+    for (int k = 0; k < 3; ++k) {
+        double P = 0.0;
+        for (int p = 0; p < np; ++p) P += pd[p].M * pd[p].U[k];
+        const double shift = (-P / rho0 - sum[k]) / (double)counts[0];
+        u[k * N + n] += (float)shift;
+    }
+    u[3 * N + n] -= (float)(sum[3] / (double)counts[0]);     // no net mass change
+}
+
 static unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const int* owner,
-                              cudaStream_t s)
+cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const float* drho,
+                              const int* owner, cudaStream_t s)
 {
     const unsigned g = nblk(B.N, 256);
-    if (precision == 1) init_fluid_kernel<StF16><<<g, 256, 0, s>>>(B, fbuf, u, owner);
-    else if (precision == 2) init_fluid_kernel<StBF16><<<g, 256, 0, s>>>(B, fbuf, u, owner);
-    else init_fluid_kernel<StF32><<<g, 256, 0, s>>>(B, fbuf, u, owner);
+    if (precision == 1) init_fluid_kernel<StF16><<<g, 256, 0, s>>>(B, fbuf, u, drho, owner);
+    else if (precision == 2) init_fluid_kernel<StBF16><<<g, 256, 0, s>>>(B, fbuf, u, drho, owner);
+    else init_fluid_kernel<StF32><<<g, 256, 0, s>>>(B, fbuf, u, drho, owner);
     return cudaGetLastError();
 }
 
-// work: 6 N float2 (two complex [3][N] buffers); counts: np + 1 ints
+// work: 8 N float2 (two complex [4][N] buffers); counts: np + 1 ints; sum: 4
+// doubles; u: [4][N] (velocity, then the density deviation)
 cudaError_t launch_stokes(const BoxDev& B, const int* owner, const PartDev* pd, int np, int counter_on,
-                          const double body[3], float mu, float2* work, int* counts, float* u, cudaStream_t s)
+                          const double body[3], float mu, float2* work, int* counts, double* sum, float* u,
+                          cudaStream_t s)
 {
     cudaError_t e;
     const long long N = B.N;
     if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * (np + 1), s)) != cudaSuccess) return e;
-    count_owner_kernel<<<nblk(N, 256), 256, 0, s>>>(owner, N, counts, np);
+    count_owner_kernel<<<nblk(N, 256), 256, 0, s>>>(owner, B.nx, B.ny, B.nz, counts, np);
     float2* a = work;
-    float2* b = work + 3 * N;
-    force_density_kernel<<<nblk(N, 256), 256, 0, s>>>(owner, N, counts, pd, np, counter_on, body[0], body[1], body[2],
-                                                       a);
+    float2* b = work + 4 * N;
+    force_density_kernel<<<nblk(N, 256), 256, 0, s>>>(owner, B.nx, B.ny, B.nz, counts, pd, np, counter_on, body[0],
+                                                       body[1], body[2], a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int nmax = B.nx > B.ny ? (B.nx > B.nz ? B.nx : B.nz) : (B.ny > B.nz ? B.ny : B.nz);
     const size_t sh = sizeof(float2) * nmax;
     for (int ax = 0; ax < 3; ++ax) {
         dft_axis_kernel<<<nblk(3 * N, 256), 256, sh, s>>>(ax % 2 == 0 ? a : b, ax % 2 == 0 ? b : a, B.nx, B.ny, B.nz, ax,
-                                                          -1.0f);
+                                                          -1.0f, 3);
     }
     // forward result in b (three passes: a->b, b->a, a->b)
     stokes_solve_kernel<<<nblk(N, 256), 256, 0, s>>>(b, B.nx, B.ny, B.nz, mu);
     for (int ax = 0; ax < 3; ++ax) {
-        dft_axis_kernel<<<nblk(3 * N, 256), 256, sh, s>>>(ax % 2 == 0 ? b : a, ax % 2 == 0 ? a : b, B.nx, B.ny, B.nz, ax,
-                                                          1.0f);
+        dft_axis_kernel<<<nblk(4 * N, 256), 256, sh, s>>>(ax % 2 == 0 ? b : a, ax % 2 == 0 ? a : b, B.nx, B.ny, B.nz, ax,
+                                                          1.0f, 4);
     }
     // inverse result in a
-    real_part_kernel<<<nblk(3 * N, 256), 256, 0, s>>>(a, 3 * N, u);
+    real_part_kernel<<<nblk(4 * N, 256), 256, 0, s>>>(a, 4 * N, u);
+    if ((e = cudaMemsetAsync(sum, 0, 4 * sizeof(double), s)) != cudaSuccess) return e;
+    fluid_sum_kernel<<<nblk(N, 256), 256, 0, s>>>(u, owner, N, sum);
+    momentum_shift_kernel<<<nblk(N, 256), 256, 0, s>>>(u, owner, N, sum, counts, pd, np, B.rho0);
     return cudaGetLastError();
 }
 

@@ -81,8 +81,8 @@ def library(path: str | None = None):
     L.lb_profile_step.argtypes = [vp, i32, vp, dp]
     L.lb_links_noalloc.argtypes = [dp, dp, dp, i32, i32, i32, i32, vp, i32, vp, vp]
     L.lb_links_noalloc.restype = i32
-    L.lb_init_fluid.argtypes = [vp, i32, vp, C.c_size_t, i32, vp]
-    L.lb_stokes_field.argtypes = [vp, i32, vp, vp]
+    L.lb_init_fluid.argtypes = [vp, i32, vp, C.c_size_t, vp, i32, vp]
+    L.lb_stokes_field.argtypes = [vp, i32, vp, vp, vp]
     L.lb_lattice.argtypes = [ip, dp]
     L.lb_lattice.restype = None
     L.lb_status_string.argtypes = [i32]
@@ -214,15 +214,19 @@ def lb_get_drag(ctx, box: int, particle: int) -> np.ndarray:
     return out.reshape(6, 6)
 
 
-def lb_init_fluid(ctx, box: int, u_ptr: int, nbytes: int, u_is_device: bool, stream=None):
-    """Initial fluid f = f_eq(rho0, u) of a box before the first step; u_ptr is
-    a host or device address of FP32 [3][nz][ny][nx]."""
-    _check(library().lb_init_fluid(ctx, box, C.c_void_p(u_ptr), nbytes, int(u_is_device), stream), ctx)
+def lb_init_fluid(ctx, box: int, u_ptr: int, nbytes: int, drho_ptr, is_device: bool, stream=None):
+    """Initial fluid f = f_eq(rho0 + drho, u) of a box before the first step;
+    u_ptr / drho_ptr (drho may be None) are host or device addresses of FP32
+    [3][nz][ny][nx] / [nz][ny][nx]."""
+    _check(library().lb_init_fluid(ctx, box, C.c_void_p(u_ptr), nbytes,
+                                   None if drho_ptr is None else C.c_void_p(drho_ptr), int(is_device), stream), ctx)
 
 
-def lb_stokes_field(ctx, box: int, u_dev_ptr: int, stream=None):
-    """Periodic Stokes flow of the box's particle forces into device FP32 [3][N]."""
-    _check(library().lb_stokes_field(ctx, box, C.c_void_p(u_dev_ptr), stream), ctx)
+def lb_stokes_field(ctx, box: int, u_dev_ptr: int, drho_dev_ptr=None, stream=None):
+    """Periodic Stokes flow of the box's particle forces into device FP32 [3][N]
+    (and its pressure as a density deviation [N] if drho_dev_ptr is given)."""
+    _check(library().lb_stokes_field(ctx, box, C.c_void_p(u_dev_ptr),
+                                     None if drho_dev_ptr is None else C.c_void_p(drho_dev_ptr), stream), ctx)
 
 
 def lb_synchronize(ctx):
@@ -304,6 +308,7 @@ class Simulation:
             opt.alloc, opt.release = self._alloc
         self.ctx = lb_create(self.boxes, opt)
         self.nparts = [0] * len(boxes)
+        self._parts = [[] for _ in boxes]
         for b, plist in enumerate(parts):
             if plist:
                 self.set_particles(b, plist)
@@ -322,6 +327,11 @@ class Simulation:
     def set_particles(self, box, plist):
         lb_set_particles(self.ctx, box, plist)
         self.nparts[box] = len(plist)
+        self._parts[box] = [dict(p) for p in plist]
+
+    def parts_of(self, box: int):
+        """The particle dictionaries last given for a box (initial state)."""
+        return [dict(p) for p in self._parts[box]]
 
     def step(self, n=1, stream=None):
         lb_step(self.ctx, n, stream)
@@ -353,10 +363,12 @@ class Simulation:
     def drag(self, box: int = 0, p: int = 0):
         return lb_get_drag(self.ctx, box, p)
 
-    def init_fluid(self, box: int, u: np.ndarray):
-        """Initial velocity field u (host, [3][nz][ny][nx]) of a box."""
+    def init_fluid(self, box: int, u: np.ndarray, drho: np.ndarray | None = None):
+        """Initial velocity field u (host, [3][nz][ny][nx]) and density
+        deviation drho (host, [nz][ny][nx], or None) of a box."""
         a = np.ascontiguousarray(np.asarray(u, np.float32))
-        lb_init_fluid(self.ctx, box, a.ctypes.data, a.nbytes, False)
+        d = None if drho is None else np.ascontiguousarray(np.asarray(drho, np.float32))
+        lb_init_fluid(self.ctx, box, a.ctypes.data, a.nbytes, None if d is None else d.ctypes.data, False)
 
     def set_external(self, box, ft, stream=None):
         lb_set_external(self.ctx, box, ft, stream)

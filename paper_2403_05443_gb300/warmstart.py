@@ -1,0 +1,314 @@
+"""Learned warm start of spheroid runs: resistance tensors measured by the LB
+method, the surrogate trained on them, and its use to start a run near steady
+state.  Orchestration only: the LB runs, the Stokes flow, the network's
+training and inference and the 6x6 solves are calls into liblbsph.so
+(include/lbsph.h, include/lbsurrogate.h); the host assembles the calls'
+inputs and outputs.
+
+Resistance data (the paper measures drag at steady state, Sec. III): for each
+sample, six periodic boxes hold the same spheroid, box k with a unit force
+(k < 3) or torque (k >= 3) along axis k and the opposite force spread over the
+fluid; after the flow has developed, (U, Omega) of box k is column k of the
+mobility M, and the target is R^ = (D M D)^-1 (lb_resistance_targets).  The 24
+rotations of the cube map the periodic D3Q19 lattice onto itself, so each
+sample also gives the mobility of the 23 rotated spheroids, P M P^T with
+P = diag(Q, Q): exact copies of what the method would measure for them (up to
+the centre's sub-node offset, which is random anyway).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+from . import lbsph as L
+from . import surrogate as SU
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def cube_rotations():
+    """The 24 proper rotations of the cube as 3x3 signed permutation matrices."""
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            P = np.zeros((3, 3))
+            for i, j in enumerate(perm):
+                P[i, j] = signs[i]
+            if round(np.linalg.det(P)) == 1:
+                out.append(P)
+    return out
+
+
+def geom_of(a, b, tau, Ledge, e, rho0=1.0):
+    return [float(a), float(b), (float(tau) - 0.5) / 3.0, float(Ledge), float(e[0]), float(e[1]), float(e[2]),
+            float(rho0)]
+
+
+def measure_mobility(samples, steps: int, force: float = 1e-4, device: int = 0, batch: int = 64):
+    """Mobility matrices M[n, 6, 6] of the samples (dicts of
+    lb_inputs.resistance_samples, all with the same box edge), from `steps`
+    iterations of the LB method in batched contexts of 6 boxes per sample."""
+    out = np.zeros((len(samples), 6, 6))
+    for s0 in range(0, len(samples), batch):
+        chunk = samples[s0:s0 + batch]
+        boxes, parts = [], []
+        for smp in chunk:
+            for k in range(6):
+                unit = np.eye(3)[k % 3]
+                fe = force * unit if k < 3 else np.zeros(3)
+                te = force * smp["b"] * unit if k >= 3 else np.zeros(3)
+                boxes.append(dict(nx=smp["L"], ny=smp["L"], nz=smp["L"], tau=smp["tau"], rho0=1.0,
+                                  counter_force=1))
+                parts.append([dict(semi=(smp["a"], smp["b"], smp["b"]), x=smp["x"], q=smp["q"],
+                                   F_ext=list(fe), T_ext=list(te))])
+        ms = int(math.ceil(max(s["a"] for s in chunk)))
+        sim = L.Simulation(boxes, parts, max_semi=ms, device=device)
+        sim.step(steps)
+        rec = L.lb_get_force_torque(sim.ctx, -1, len(boxes))
+        sim.close()
+        for i, smp in enumerate(chunk):
+            for k in range(6):
+                mag = force if k < 3 else force * smp["b"]
+                r = rec[6 * i + k]
+                out[s0 + i, :3, k] = r[12:15] / mag
+                out[s0 + i, 3:, k] = r[15:18] / mag
+    return out
+
+
+def augment(geoms, M):
+    """Cube-rotated copies: e -> Q e, M -> P M P^T with P = diag(Q, Q)."""
+    G, Ms = [], []
+    for Q in cube_rotations():
+        P = np.zeros((6, 6))
+        P[:3, :3] = Q
+        P[3:, 3:] = Q
+        for g, m in zip(geoms, M):
+            e = Q @ np.asarray(g[4:7])
+            G.append(list(g[:4]) + list(e) + [g[7]])
+            Ms.append(P @ m @ P.T)
+    return np.asarray(G), np.asarray(Ms)
+
+
+def targets(geoms, M):
+    """R^ targets (device FP32 [n, 36]) and features (device FP32 [n, 8])."""
+    torch = _torch()
+    n = len(geoms)
+    gd = torch.as_tensor(np.asarray(geoms, np.float64), device="cuda")
+    Md = torch.as_tensor(np.asarray(M, np.float64).reshape(n, 36), device="cuda")
+    R = torch.zeros((n, 36), dtype=torch.float32, device="cuda")
+    x = torch.zeros((n, 8), dtype=torch.float32, device="cuda")
+    SU.lb_resistance_targets(Md.data_ptr(), gd.data_ptr(), n, R.data_ptr())
+    SU.lb_mlp_features(gd.data_ptr(), n, x.data_ptr())
+    return x, R
+
+
+def init_params(seed: int = 0):
+    """He-style initial weights (seeded), zero biases except the diagonal of L
+    (softplus(0.55) = 1: the output starts at R^ = I)."""
+    g = np.random.default_rng(seed)
+    p = np.zeros(SU.LB_MLP_NPARAM, np.float32)
+    P = SU.unpack(p)
+    P["W1"][:, :8] = g.normal(0, math.sqrt(2.0 / 8), (256, 8))
+    P["W2"][:] = g.normal(0, math.sqrt(2.0 / 256), (256, 256))
+    P["W3"][:21] = g.normal(0, 0.1 * math.sqrt(1.0 / 256), (21, 256))
+    for i in range(6):
+        P["b3"][i * (i + 1) // 2 + i] = 0.5413
+    return p
+
+
+def train(x, R, steps: int = 3000, batch: int = 512, lr: float = 2e-3, seed: int = 0, net=None):
+    """Adam on minibatches drawn (seeded) from the device arrays x, R; the
+    learning rate decays linearly to lr/20.  Returns the network and the loss
+    of the last minibatches."""
+    torch = _torch()
+    n = x.shape[0]
+    batch = min(batch, n)
+    net = net or SU.Surrogate(max_batch=max(batch, 1024), params=init_params(seed))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    loss = torch.zeros(1, device="cuda")
+    hist = []
+    for t in range(steps):
+        idx = torch.randint(0, n, (batch,), device="cuda", generator=g)
+        xb, Rb = x[idx].contiguous(), R[idx].contiguous()
+        rate = lr * (1.0 - 0.95 * t / max(1, steps - 1))
+        SU.lb_mlp_train_step(net.h, xb.data_ptr(), Rb.data_ptr(), batch, rate, loss.data_ptr())
+        if t >= steps - 20:
+            hist.append(float(loss.item()))
+    return net, float(np.mean(hist)) if hist else float("nan")
+
+
+def predict(net, x):
+    """R^ (device FP32 [n, 36]) for features x (device FP32 [n, 8])."""
+    torch = _torch()
+    n = x.shape[0]
+    R = torch.zeros((n, 36), dtype=torch.float32, device="cuda")
+    for s0 in range(0, n, 1024):
+        m = min(1024, n - s0)
+        SU.lb_mlp_forward(net.h, x[s0:s0 + m].data_ptr(), m, None, R[s0:s0 + m].data_ptr())
+    return R
+
+
+def long_axis(q):
+    """The lab direction of the body x axis for a unit quaternion (q0, q1, q2, q3)."""
+    q0, q1, q2, q3 = q
+    return [q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3, 2 * (q1 * q2 + q0 * q3), 2 * (q1 * q3 - q0 * q2)]
+
+
+def warm_start(sim, box: int, net, use_net: bool = True, use_fluid: bool = True):
+    """Before the first step: set each particle's (U, Omega) to the surrogate's
+    steady estimate R^-1 (F_ext, T_ext) (use_net) and the fluid to the lattice
+    Stokes flow of the particle forces and its pressure (use_fluid).  For several particles in a
+    box the confinement feature uses the edge of the volume per particle."""
+    torch = _torch()
+    b = sim.boxes[box]
+    parts = [dict(p) for p in sim.parts_of(box)]
+    n = len(parts)
+    if use_net and n:
+        Ledge = (b["nx"] * b["ny"] * b["nz"] / n) ** (1.0 / 3.0)
+        geoms = [geom_of(p["semi"][0], p["semi"][1], b["tau"], Ledge, long_axis(p["q"]), b.get("rho0", 1.0))
+                 for p in parts]
+        gd = torch.as_tensor(np.asarray(geoms), device="cuda")
+        x = torch.zeros((n, 8), dtype=torch.float32, device="cuda")
+        SU.lb_mlp_features(gd.data_ptr(), n, x.data_ptr())
+        R = predict(net, x)
+        FT = torch.as_tensor(np.asarray([list(p.get("F_ext", (0, 0, 0))) + list(p.get("T_ext", (0, 0, 0)))
+                                         for p in parts], np.float64), device="cuda")
+        UW = torch.zeros((n, 6), dtype=torch.float64, device="cuda")
+        SU.lb_warm_velocities(R.data_ptr(), gd.data_ptr(), FT.data_ptr(), n, UW.data_ptr())
+        uw = UW.cpu().numpy()
+        for p, v in zip(parts, uw):
+            p["U"], p["Om"] = [float(t) for t in v[:3]], [float(t) for t in v[3:]]
+        sim.set_particles(box, parts)
+    if use_fluid:
+        N = b["nx"] * b["ny"] * b["nz"]
+        u = torch.zeros(3 * N, dtype=torch.float32, device="cuda")
+        d = torch.zeros(N, dtype=torch.float32, device="cuda")
+        L.lb_stokes_field(sim.ctx, box, u.data_ptr(), d.data_ptr())
+        L.lb_init_fluid(sim.ctx, box, u.data_ptr(), u.numel() * 4, d.data_ptr(), True)
+
+
+def velocity_history(sim, box: int, steps: int, every: int):
+    """U and Omega of the box's particles every `every` steps: [k, n, 6]."""
+    out = []
+    for _ in range(steps // every):
+        sim.step(every)
+        r = sim.records(box)
+        out.append(r[:, 12:18].copy())
+    return np.asarray(out)
+
+
+def velocity_error(hist, ref):
+    """max over particles of |U - U_ref| / rms |U_ref| at each record."""
+    scale = float(np.sqrt((np.linalg.norm(ref, axis=1) ** 2).mean()))
+    return np.abs(hist[:, :, :3] - ref[None]).max(axis=2).max(axis=1) / scale
+
+
+def steps_to_steady(hist, ref, every: int, tol: float = 1e-3):
+    """First step after which every particle's velocity stays within tol (in
+    units of the particles' rms steady speed) of the steady velocities ref[n, 3];
+    None if it never does within the record."""
+    worst = velocity_error(hist, ref)
+    bad = np.nonzero(worst > tol)[0]
+    if len(bad) == 0:
+        return every
+    if bad[-1] == len(worst) - 1:
+        return None
+    return int((bad[-1] + 2) * every)
+
+
+def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int = 4000, eval_n: int = 128,
+               eval_count: int = 16, force: float = 2e-5, every: int = 50, ref_steps: int = 40000, device: int = 0):
+    """The whole learned warm start, end to end on the GPU:
+      1. resistance data from the LB method: n32 samples in 32^3 boxes and n48
+         in 48^3 boxes (tau in {0.8, 1, 1.2}, a/b in [1, 3], b in [2, 3.5]),
+         each flow developed for 8 diffusion times L^2 / (4 pi^2 nu) of its box;
+      2. 24-fold cube-rotation augmentation, 10 % of the LB samples held out;
+      3. training of the network;
+      4. an eval_n^3 box with eval_count spheroids and random forces, run cold
+         (fluid at rest, particles at rest), with the Stokes fluid only, and with
+         the Stokes fluid plus the network's velocities, each compared with the
+         steady velocities of a long cold run: steps until every particle's
+         velocity stays within 1e-3 of it.
+    Returns a dict of the measurements."""
+    import time
+
+    import lb_inputs as I
+    torch = _torch()
+    t0 = time.time()
+    samples = I.resistance_samples(seed, n32, 32) + I.resistance_samples(seed + 1, n48, 48)
+    M = np.zeros((len(samples), 6, 6))
+    for Ledge in (32, 48):
+        idx = [i for i, s in enumerate(samples) if s["L"] == Ledge]
+        for tau in (0.8, 1.0, 1.2):
+            sub = [i for i in idx if samples[i]["tau"] == tau]
+            if not sub:
+                continue
+            nu = (tau - 0.5) / 3.0
+            steps = int(8 * Ledge * Ledge / (4 * math.pi ** 2 * nu))
+            M[sub] = measure_mobility([samples[i] for i in sub], steps, device=device)
+    t_data = time.time() - t0
+    geoms = np.asarray([geom_of(s["a"], s["b"], s["tau"], s["L"], s["e"]) for s in samples])
+    g = np.random.default_rng(seed)
+    perm = g.permutation(len(samples))
+    nval = max(1, len(samples) // 10)
+    val, tr = perm[:nval], perm[nval:]
+    Gt, Mt = augment(geoms[tr], M[tr])
+    x, R = targets(Gt, Mt)
+    t1 = time.time()
+    net, train_loss = train(x, R, steps=train_steps, seed=seed)
+    t_train = time.time() - t1
+    xv, Rv = targets(geoms[val], M[val])
+    Pv = predict(net, xv)
+    rel = (torch.linalg.matrix_norm((Pv - Rv).reshape(-1, 6, 6)) /
+           torch.linalg.matrix_norm(Rv.reshape(-1, 6, 6))).cpu().numpy()
+    # evaluation runs
+    boxes, parts = I.many_spheroids(seed, n=eval_n, count=eval_count, force=force)
+    ms = int(math.ceil(max(p["semi"][0] for p in parts[0])))
+
+    def run(mode, steps):
+        sim = L.Simulation(boxes, parts, max_semi=ms, device=device)
+        if mode != "cold":
+            warm_start(sim, 0, net, use_net=(mode == "warm"), use_fluid=True)
+        h = velocity_history(sim, 0, steps, every)
+        sim.close()
+        return h
+
+    t2 = time.time()
+    ref = run("cold", ref_steps)
+    U_ss = ref[-1, :, :3]
+    drift = float(velocity_error(ref[-11:-10], U_ss)[0])
+    tols = (1e-2, 3e-3, 1e-3)
+    res = {f"cold@{t:g}": steps_to_steady(ref, U_ss, every, t) for t in tols}
+    curves = {"cold": velocity_error(ref, U_ss)}
+    for mode in ("stokes_fluid_only", "warm"):
+        h = run(mode, ref_steps // 2)
+        for t in tols:
+            res[f"{mode}@{t:g}"] = steps_to_steady(h, U_ss, every, t)
+        curves[mode] = velocity_error(h, U_ss)
+    pick = lambda c: {int((i + 1) * every): float(c[i]) for i in range(0, len(c), max(1, len(c) // 40))}
+    t_eval = time.time() - t2
+    return {"samples": len(samples), "augmented": int(len(Gt)), "train_loss": train_loss,
+            "val_rel_err_median": float(np.median(rel)), "val_rel_err_max": float(rel.max()),
+            "steps_to_steady": res,
+            "gain_warm_vs_cold": {f"{t:g}": (res[f"cold@{t:g}"] / res[f"warm@{t:g}"])
+                                  if res[f"cold@{t:g}"] and res[f"warm@{t:g}"] else None for t in tols},
+            "reference_drift_last_500_steps": drift, "eval": f"{eval_n}^3, {eval_count} spheroids, |F|={force}",
+            "error_curves": {k: pick(v) for k, v in curves.items()},
+            "seconds": {"data": t_data, "train": t_train, "eval": t_eval}}
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+
+    kw = {}
+    for a in sys.argv[1:]:
+        k, v = a.split("=")
+        kw[k] = int(v) if v.isdigit() else float(v)
+    print(json.dumps(experiment(**kw)))

@@ -39,35 +39,41 @@ def _sim(b, parts):
 def _gpu_stokes(sim, b):
     N = b["nx"] * b["ny"] * b["nz"]
     u = torch.zeros(3 * N, dtype=torch.float32, device="cuda")
-    L.lb_stokes_field(sim.ctx, 0, u.data_ptr())
-    return u
+    d = torch.zeros(N, dtype=torch.float32, device="cuda")
+    L.lb_stokes_field(sim.ctx, 0, u.data_ptr(), d.data_ptr())
+    return u, d
 
 
 def test_stokes_field_matches_reference():
     b, parts = _case()
     sim = _sim(b, parts)
-    u = _gpu_stokes(sim, b).cpu().numpy().reshape(3, b["nz"], b["ny"], b["nx"])
+    ud, dd = _gpu_stokes(sim, b)
+    u = ud.cpu().numpy().reshape(3, b["nz"], b["ny"], b["nx"])
+    d = dd.cpu().numpy().reshape(b["nz"], b["ny"], b["nx"])
     owner = sim.field("solid")
     mu = b["rho0"] * (b["tau"] - 0.5) / 3.0
-    ref = W.stokes_field(b["nx"], b["ny"], b["nz"], owner, [p["F_ext"] for p in parts], mu, counter=True)
-    err = normwise(u, ref)
-    print("stokes error", err)
-    assert err <= 1e-4
+    ref, dref = W.stokes_field(b["nx"], b["ny"], b["nz"], owner, [p["F_ext"] for p in parts], mu, counter=True,
+                               density=True)
+    err, derr = normwise(u, ref), normwise(d, dref)
+    print("stokes error", err, derr)
+    assert err <= 1e-4 and derr <= 1e-4
 
 
 def test_run_from_initial_fluid_matches_oracle():
-    """Start both sides from f = f_eq(rho0, u_Stokes) and compare every field
+    """Start both sides from f = f_eq(rho0 + drho, u) of the Stokes flow and its
+    pressure and compare every field
     and particle value over 40 steps."""
     b, parts = _case()
     sim = _sim(b, parts)
-    ud = _gpu_stokes(sim, b)
-    L.lb_init_fluid(sim.ctx, 0, ud.data_ptr(), ud.numel() * 4, True)
+    ud, dd = _gpu_stokes(sim, b)
+    L.lb_init_fluid(sim.ctx, 0, ud.data_ptr(), ud.numel() * 4, dd.data_ptr(), True)
     u = ud.cpu().numpy().astype(np.float64).reshape(3, b["nz"], b["ny"], b["nx"])
+    d = dd.cpu().numpy().astype(np.float64).reshape(b["nz"], b["ny"], b["nx"])
     o = O.Sim(b, parts, nthreads=8)
     co, wo = O.lattice()
     f = o.f()
     fluid = o.owner() == 0
-    feq = W.equilibrium_f(u, b["rho0"], co, wo)
+    feq = W.equilibrium_f(u, b["rho0"] + d, co, wo)
     f[fluid] = feq[fluid]
     o.set_f(f)
     # before the first collision the read-back is the initial field itself

@@ -25,6 +25,22 @@ def test_single_mode_force_gives_the_closed_form_shear_wave():
     assert np.allclose(mu * lap + g[0], 0.0, atol=1e-15)
 
 
+def test_curl_free_force_is_balanced_by_pressure_alone():
+    """g = G cos(2 pi y / n) y is a gradient: no flow, and the pressure has the
+    central difference g, p = G sin(2 pi y / n) / sin(2 pi / n); drho = 3 p."""
+    n, G = 16, 1e-4
+    y = np.arange(n)
+    g = np.zeros((3, 4, n, 5))
+    g[1] = (G * np.cos(2 * np.pi * y / n))[None, :, None]
+    u = W.stokes_solve(g, 0.1)
+    assert np.abs(u).max() < 1e-17
+    d = W.pressure_density(g)
+    exact = 3 * G * np.sin(2 * np.pi * y / n) / np.sin(2 * np.pi / n)
+    assert np.allclose(d, exact[None, :, None], rtol=0, atol=1e-15)
+    p = d / 3
+    assert np.allclose((np.roll(p, -1, axis=1) - np.roll(p, 1, axis=1)) / 2, g[1], atol=1e-18)
+
+
 def test_flow_is_projected_and_has_zero_mean():
     g = np.random.default_rng(0).normal(0, 1, (3, 7, 9, 8))
     u = W.stokes_solve(g, 0.2)
@@ -51,12 +67,18 @@ def test_periodic_greens_function_is_symmetric():
             assert ub[i][a] == pytest.approx(ua[j][b], rel=1e-12, abs=1e-15)
 
 
-def test_particle_force_spread_and_counter_force():
+def test_particle_force_spread_and_momentum_balance():
     owner = np.zeros((4, 5, 6), np.int32)
     owner[1:3, 2, 2:4] = 1
     u = W.stokes_field(6, 5, 4, owner, [[1e-3, 0, 0]], 0.1, counter=True)
-    # with the counter force the total force is zero; the flow follows the force
-    assert u[0][owner == 1].mean() > 0 and abs(u.mean()) < 1e-15
+    # the flow follows the force; the fluid carries no net momentum
+    fluid = owner == 0
+    assert u[0][owner == 1].mean() > 0
+    assert np.abs([u[k][fluid].sum() for k in range(3)]).max() < 1e-15
+    # with a moving particle the fluid takes the opposite momentum
+    MU = [[2.0, -1.0, 0.5]]
+    u = W.stokes_field(6, 5, 4, owner, [[1e-3, 0, 0]], 0.1, counter=True, MU=MU, rho0=1.0)
+    assert np.allclose([u[k][fluid].sum() for k in range(3)], [-2.0, 1.0, -0.5], atol=1e-13)
 
 
 def test_scaling_gives_stokes_law_for_the_reference_sphere():
