@@ -51,15 +51,18 @@ def measured_peak():
 STEP_ITERS = 256   # iterations per launch of the step kernel (the library's chunk)
 
 
+STEP_SOURCES = ("step_kernel.cu", "boundary_block.cuh", "bulk_tile.cuh", "particle_blocks.cuh", "lattice_common.cuh",
+                "lbsph_internal.cuh")
+
+
 def kernel_hash():
-    """Hash of every device source file: the step kernel includes them all."""
+    """Hash of the device sources the persistent step kernel is compiled from."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2403_05443_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode())
-                h.update(fh.read())
+    for f in STEP_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
