@@ -25,7 +25,12 @@ namespace lbsph {
 template <class St, bool FIRST>
 __global__ void __launch_bounds__(KBLOCK, 2) bulk_kernel(const BulkParams P, int tiles)
 {
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) bulk_tile<St, FIRST>(P, tile, threadIdx.x);
+    // warp-sized units of 32 quads, strided over all warps of the grid
+    constexpr int WPB = KBLOCK / 32;
+    const int lane = threadIdx.x & 31;
+    const int units = tiles * WPB;
+    for (int u = blockIdx.x * WPB + (threadIdx.x >> 5); u < units; u += gridDim.x * WPB)
+        bulk_tile<St, FIRST>(P, u / WPB, (u % WPB) * 32 + lane);
 }
 
 static int bulk_grid(int tiles)

@@ -13,8 +13,10 @@
 //     step t); the last of the particle's items to finish goes on with its
 //     critical block (force, implicit solve, pose, new occupancy, redo masks
 //     and box terms of step t+1);
-//   - bulk tiles (bulk_tile.cuh), every other node of every box, taken by all
-//     blocks from a counter; the next tile is fetched while one runs.
+//   - bulk work (bulk_tile.cuh), every other node of every box, taken by
+//     every warp from a counter in units of 32 quads (128 nodes), so that the
+//     warps of a block load and compute out of step with each other; the next
+//     unit is fetched while one runs.
 // A grid barrier ends the iteration: after it the lattice of step t, the box
 // terms and the redo masks of step t+1 are complete.  The auxiliary block of
 // the last iteration runs after the loop.
@@ -79,7 +81,6 @@ __device__ __forceinline__ bool grid_barrier(const StepParams& SP)
 template <class St>
 __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__ StepParams SP)
 {
-    __shared__ int s_item[2];
     __shared__ int s_last, s_rank;
     const int tid = threadIdx.x;
     const int gx = SP.gx;
@@ -125,16 +126,21 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
             }
             __syncthreads();
         }
-        // ---- bulk tiles from the counter
-        if (tid == 0) s_item[0] = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
-        __syncthreads();
-        int buf = 0, item = s_item[0];
-        while (item < SP.tiles) {
-            if (tid == 0) s_item[buf ^ 1] = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
-            bulk_tile<St, false>(BP, item, tid);
-            __syncthreads();
-            buf ^= 1;
-            item = s_item[buf];
+        // ---- bulk work, one warp-sized unit (32 quads of a tile) at a time from
+        // the counter: no block barrier, each warp moves on as soon as its
+        // stores are issued; the next unit's index is fetched while one runs
+        {
+            const int lane = tid & 31;
+            const int units = SP.tiles * (KBLOCK / 32);
+            int u = 0;
+            if (lane == 0) u = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            while (u < units) {
+                int nu = 0;
+                if (lane == 0) nu = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
+                bulk_tile<St, false>(BP, u >> 3, ((u & 7) << 5) + lane);
+                u = __shfl_sync(0xffffffffu, nu, 0);
+            }
         }
         if (!grid_barrier(SP)) return;
     }
