@@ -28,8 +28,13 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_LUP = {"fp32": 152, "fp16": 76, "bf16": 76}   # 2 * 19 * s, read + write
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
-WORKLOAD = ("sweep_8x64: 8 periodic 64^3 D3Q19 boxes, BGK tau=0.8, one prolate spheroid (8,4,4) per box "
-            "at 0,15,...,90 deg and a random orientation to the force, |F_ext|=5e-4 with counter body force")
+WORKLOADS = {
+    "sweep_8x64": ("sweep_8x64: 8 periodic 64^3 D3Q19 boxes, BGK tau=0.8, one prolate spheroid (8,4,4) per box "
+                   "at 0,15,...,90 deg and a random orientation to the force, |F_ext|=5e-4 with counter body force"),
+    "squirmer_batch": ("squirmer_batch: 32 periodic cubic D3Q19 boxes of edges drawn from {48,64,96,128} in one "
+                       "launch, BGK tau=1, one squirmer spheroid (6,3,3) per box, B1=1e-3, B2/B1 in {-2,0,2}"),
+}
+WORKLOAD = WORKLOADS["sweep_8x64"]
 
 
 def env_int(k, d):
@@ -193,7 +198,7 @@ def run_ours(args):
     import torch
 
     import paper_2403_05443_gb300 as pkg
-    from lb_inputs import sweep_8x64
+    import lb_inputs
 
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(local)
@@ -201,7 +206,7 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    boxes, parts = sweep_8x64(seed=args.seed + rank)
+    boxes, parts = getattr(lb_inputs, args.workload)(seed=args.seed + rank)
     nodes = sum(b["nx"] * b["ny"] * b["nz"] for b in boxes)
     sim = pkg.Simulation(boxes, parts, precision=PREC[args.precision], max_semi=8, device=local,
                          torch_alloc=True)
@@ -209,6 +214,9 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     sp = pkg.lbsph.stream_handle(stream)
     sim.step(args.warmup, stream=sp)
+    # launch shape of the step kernel for this workload (untimed; the
+    # candidates compute identical values, so this is more warm-up)
+    fetch, fetch_ms = pkg.lbsph.lb_autotune(sim.ctx, 64, sp)
     torch.cuda.synchronize()
 
     def barrier():
@@ -241,7 +249,7 @@ def run_ours(args):
     peak, peak_src = measured_peak()
     algo = BYTES_PER_LUP[args.precision] * nodes
     achieved = algo / (ms / args.steps / 1e3) / 1e9
-    traffic = committed_traffic(args.precision, nodes)
+    traffic = committed_traffic(args.precision, nodes) if args.workload == "sweep_8x64" else None
     # the four parts as separate kernels, serialised with CUDA events between them
     nprof = max(50, min(500, args.steps // 10))
     k_ms, b_ms, c_ms, a_ms = pkg.lb_profile_step(sim.ctx, nprof, sp)
@@ -271,7 +279,7 @@ def run_ours(args):
         e2e_v = nodes * ke * world / float(t.item()) / 1e6
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "sweep_8x64":
         cpu = cpu_baseline(boxes_parts=(boxes, parts))
 
     if rank == 0:
@@ -281,7 +289,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else f"f32 arithmetic, {args.precision} storage",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "boxes": len(boxes), "nodes_per_gpu": nodes,
+            "config": {"workload": WORKLOADS[args.workload], "boxes": len(boxes), "nodes_per_gpu": nodes,
+                       "autotune": {"units_per_fetch": fetch, "ms_per_step_1_2_4_8": [round(v, 5) for v in fetch_ms]},
                        "precision": args.precision,
                        "l2": f"state {2 * nodes * BYTES_PER_LUP[args.precision] // 2 / 1e6:.0f} MB > 129 MB L2; not flushed",
                        "parallelism": f"{world} rank(s), 8 independent boxes each, no collective"},
@@ -319,6 +328,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(PREC))
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--workload", default="sweep_8x64", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

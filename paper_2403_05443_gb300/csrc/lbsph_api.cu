@@ -28,7 +28,8 @@ cudaError_t launch_boundary(const BndParams& p, int precision, int np, cudaStrea
 cudaError_t launch_particles(const PParams& p, cudaStream_t s);
 cudaError_t launch_particles_aux(const PParams& p, cudaStream_t s);
 cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const PParams part[2], unsigned* sync,
-                        unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, cudaStream_t s);
+                        unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, int fetch,
+                        cudaStream_t s);
 cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
                          int cap, int* count, cudaStream_t s);
 cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const float* drho,
@@ -86,6 +87,7 @@ struct lb_ctx {
     int* d_box_done = nullptr;
     int list_cap = 0;                  // node list entries per boundary block
     int gx = 1;                        // boundary blocks per particle
+    int fetch = 1;                     // bulk units a warp takes per counter fetch (lb_autotune)
     std::string err;
     std::vector<void*> allocs;
 };
@@ -560,7 +562,7 @@ static cudaError_t enqueue_steps(lb_ctx* ctx, int k, int cur, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(ctx->d_sync, 0, sizeof(unsigned) * (4 + (size_t)ctx->np), s);
     if (e != cudaSuccess) return e;
     return launch_step(bulk, bnd, part, ctx->d_sync, ctx->d_status, ctx->np, ctx->gx, ctx->total_blocks, k, cur,
-                       ctx->opt.precision, s);
+                       ctx->opt.precision, ctx->fetch, s);
 }
 
 extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
@@ -821,5 +823,53 @@ extern "C" lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, flo
     CK(cudaMemcpyAsync(u_dev, out, 3ull * B.N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (drho_dev) CK(cudaMemcpyAsync(drho_dev, out + 3 * B.N, (size_t)B.N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
+    return read_status(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the step kernel's launch shape: how many consecutive 32-quad
+// bulk units a warp takes per fetch from the work counter (1, 2, 4 or 8).
+// More units per fetch cost fewer atomics and keep a warp on neighbouring
+// rows; fewer balance the end of each iteration better.  Every candidate
+// computes the same values bit for bit (the assignment of units to warps does
+// not enter any node's arithmetic), so tuning advances the simulation exactly
+// as lb_step would.
+extern "C" lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void* stream, int32_t* chosen,
+                                 double* ms_per_step)
+{
+    if (!ctx) return LB_EINVAL;
+    if (steps_per_candidate < 1) return fail(ctx, LB_EINVAL, "steps_per_candidate must be positive");
+    if (ctx->opt.flags & LB_FLAG_SEPARATE_KERNELS) return fail(ctx, LB_ESTATE, "no step kernel to tune");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick(ctx, stream);
+    if (!ctx->collided) {
+        const lb_status r = lb_step(ctx, 1, stream);
+        if (r != LB_OK) return r;
+    }
+    static const int cand[4] = {1, 2, 4, 8};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_f = ctx->fetch;
+    for (int c = 0; c < 4; ++c) {
+        ctx->fetch = cand[c];
+        lb_status r = lb_step(ctx, 2, stream);               // warm the new shape
+        if (r != LB_OK) return r;
+        CK(cudaEventRecord(e0, s));
+        r = lb_step(ctx, steps_per_candidate, stream);
+        if (r != LB_OK) return r;
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per = ms / steps_per_candidate;
+        if (ms_per_step) ms_per_step[c] = per;
+        if (per < best) { best = per; best_f = cand[c]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->fetch = best_f;
+    if (chosen) *chosen = best_f;
     return read_status(ctx);
 }

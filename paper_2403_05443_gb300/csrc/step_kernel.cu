@@ -45,6 +45,7 @@ struct StepParams {
     unsigned* sync;                  // SYNC_PART + np words, zero at launch, then the blocks' SM ids
     unsigned* status;
     int np, gx, tiles, iters, cur0;
+    int fetch;                       // bulk units per counter fetch (1, 2, 4, 8)
 };
 
 __device__ __forceinline__ bool grid_barrier(const StepParams& SP)
@@ -126,19 +127,22 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
             }
             __syncthreads();
         }
-        // ---- bulk work, one warp-sized unit (32 quads of a tile) at a time from
-        // the counter: no block barrier, each warp moves on as soon as its
-        // stores are issued; the next unit's index is fetched while one runs
+        // ---- bulk work in warp-sized units (32 quads of a tile), SP.fetch
+        // consecutive units per fetch from the counter: no block barrier, each
+        // warp moves on as soon as its stores are issued; the next fetch is
+        // issued before the current units run
         {
             const int lane = tid & 31;
             const int units = SP.tiles * (KBLOCK / 32);
+            const int fetch = SP.fetch;
             int u = 0;
-            if (lane == 0) u = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
+            if (lane == 0) u = (int)atomicAdd(SP.sync + SYNC_WORK, 1u) * fetch;
             u = __shfl_sync(0xffffffffu, u, 0);
             while (u < units) {
                 int nu = 0;
-                if (lane == 0) nu = (int)atomicAdd(SP.sync + SYNC_WORK, 1u);
-                bulk_tile<St, false>(BP, u >> 3, ((u & 7) << 5) + lane);
+                if (lane == 0) nu = (int)atomicAdd(SP.sync + SYNC_WORK, 1u) * fetch;
+                const int end = min(u + fetch, units);
+                for (int v = u; v < end; ++v) bulk_tile<St, false>(BP, v >> 3, ((v & 7) << 5) + lane);
                 u = __shfl_sync(0xffffffffu, nu, 0);
             }
         }
@@ -176,12 +180,13 @@ static cudaError_t launch_step_t(const StepParams& sp, size_t smem, cudaStream_t
 }
 
 cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const PParams part[2], unsigned* sync,
-                        unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, cudaStream_t s)
+                        unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, int fetch,
+                        cudaStream_t s)
 {
     StepParams sp;
     for (int c = 0; c < 2; ++c) { sp.bulk[c] = bulk[c]; sp.bnd[c] = bnd[c]; sp.part[c] = part[c]; }
     sp.sync = sync; sp.status = status;
-    sp.np = np; sp.gx = gx; sp.tiles = tiles; sp.iters = iters; sp.cur0 = cur0;
+    sp.np = np; sp.gx = gx; sp.fetch = fetch < 1 ? 1 : fetch; sp.tiles = tiles; sp.iters = iters; sp.cur0 = cur0;
     const int smax = bnd[0].smax;
     const size_t maps = 2ull * smax * smax * sizeof(uint64_t);
     const size_t smem = np > 0 ? maps + (size_t)bnd[0].list_cap * sizeof(unsigned) : 0;

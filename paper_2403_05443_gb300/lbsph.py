@@ -81,6 +81,7 @@ def library(path: str | None = None):
     L.lb_profile_step.argtypes = [vp, i32, vp, dp]
     L.lb_links_noalloc.argtypes = [dp, dp, dp, i32, i32, i32, i32, vp, i32, vp, vp]
     L.lb_links_noalloc.restype = i32
+    L.lb_autotune.argtypes = [vp, i32, vp, ip, dp]
     L.lb_init_fluid.argtypes = [vp, i32, vp, C.c_size_t, vp, i32, vp]
     L.lb_stokes_field.argtypes = [vp, i32, vp, vp, vp]
     L.lb_lattice.argtypes = [ip, dp]
@@ -92,7 +93,7 @@ def library(path: str | None = None):
     L.lb_abi_version.restype = i32
     for name in ("lb_create", "lb_destroy", "lb_set_particles", "lb_set_external", "lb_step",
                  "lb_get_fields", "lb_get_force_torque", "lb_get_links", "lb_get_drag", "lb_synchronize",
-                 "lb_profile_step", "lb_init_fluid", "lb_stokes_field"):
+                 "lb_profile_step", "lb_init_fluid", "lb_stokes_field", "lb_autotune"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -227,6 +228,15 @@ def lb_stokes_field(ctx, box: int, u_dev_ptr: int, drho_dev_ptr=None, stream=Non
     (and its pressure as a density deviation [N] if drho_dev_ptr is given)."""
     _check(library().lb_stokes_field(ctx, box, C.c_void_p(u_dev_ptr),
                                      None if drho_dev_ptr is None else C.c_void_p(drho_dev_ptr), stream), ctx)
+
+
+def lb_autotune(ctx, steps_per_candidate: int, stream=None):
+    """(units per fetch kept, ms per step of each candidate 1, 2, 4, 8)."""
+    ch = C.c_int32(0)
+    ms = np.zeros(4)
+    _check(library().lb_autotune(ctx, int(steps_per_candidate), stream, C.byref(ch),
+                                 ms.ctypes.data_as(C.POINTER(C.c_double))), ctx)
+    return ch.value, ms
 
 
 def lb_synchronize(ctx):
