@@ -86,6 +86,22 @@ def committed_traffic(precision, nodes):
         return None
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The maximum of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Weak scaling: every rank advances its own nodes_per_rank nodes by steps
+    iterations; the job's rate divides all of them by the slowest rank's time."""
+    return nodes_per_rank * steps * world / seconds / 1e6
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -236,11 +252,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     sim.sync()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nodes * args.steps * world / (ms / 1e3) / 1e6
+    ms = max_over_ranks(ms, dist)
+    value = whole_job_mlups(nodes, args.steps, world, ms / 1e3)
 
     # dominant kernel: the persistent step kernel is the whole timed region
     # (ceil(K / 256) launches, one small memset before each); its algorithmic
@@ -271,12 +284,8 @@ def run_ours(args):
         pkg.lb_set_external(sim.ctx, -1, ft_np, sp)
         sim.step(1, stream=sp)
         pkg.lb_get_force_torque(sim.ctx, -1, np_tot, rec_np)
-    t_e2e = time.perf_counter() - t0
-    e2e_v = nodes * ke * world / t_e2e / 1e6
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_v = nodes * ke * world / float(t.item()) / 1e6
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e_v = whole_job_mlups(nodes, ke, world, t_e2e)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "sweep_8x64":
