@@ -1,0 +1,77 @@
+"""The CUDA path at the scale of the paper's workloads, against the closed
+forms the paper compares with (oracle/analytic.py):
+
+  * Jeffery orbit (Sec. III.C, Eq. jeffery): a spheroid (8,4,4), r = 2, in the
+    flow-gradient plane of a Couette flow between walls at y = 0 and y = 63
+    moving at -/+0.01 (128 x 64 x 128 nodes, tau = 1).  With link bounce-back
+    the walls sit half a link inside, so the shear rate is 0.02 / 62 and the
+    period T = 2 pi (r + 1/r) / shear = 48,695 steps; the axis turns by pi in
+    T/2.  Bar: 5 % on the period (the discretised spheroid's effective aspect
+    ratio is not exactly 2).
+  * Squirmer (Sec. III.D-E, Eq. squirmervel): a spheroidal squirmer (6,3,3)
+    in a 96^3 periodic box swims along its axis at U_s = 0.826 B1, independent
+    of B2.  Bar: 10 % on U_s (slip applied half a link off the surface at this
+    radius), 3 % between B2 = 0 and B2 = 2 B1.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from lb_inputs import axis_angle_quaternion, box, particle
+from oracle import analytic as A
+
+pytestmark = pytest.mark.gpu
+
+L = pytest.importorskip("paper_2403_05443_gb300.lbsph")
+
+
+def _axis(q):
+    q0, q1, q2, q3 = q
+    return np.array([q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3, 2 * (q1 * q2 + q0 * q3), 2 * (q1 * q3 - q0 * q2)])
+
+
+def test_jeffery_period_in_couette_flow():
+    nx, ny, nz, uw = 128, 64, 128, 0.01
+    b = box(nx, ny, nz, 1.0, walls=1, wall_u_lo=(-uw, 0, 0), wall_u_hi=(uw, 0, 0))
+    phi0 = 0.3
+    p = particle((8.0, 4.0, 4.0), (0.5 * nx, 0.5 * (ny - 1), 0.5 * nz), axis_angle_quaternion((0, 0, 1), phi0))
+    sim = L.Simulation([b], [[p]], max_semi=8)
+    every, steps = 200, 40000
+    phis = [phi0]
+    for _ in range(steps // every):
+        sim.step(every)
+        e = _axis(sim.particle(0, 0)["q"])
+        phis.append(math.atan2(e[1], e[0]))
+        assert abs(e[2]) < 1e-6                     # stays in the flow-gradient plane
+    phi = np.unwrap(np.array(phis))
+    t = np.arange(len(phi)) * every
+    turned = phi0 - phi                             # u_x = shear * y turns the axis clockwise
+    k = int(np.argmax(turned >= math.pi))
+    assert turned[k] >= math.pi
+    t_half = t[k - 1] + (math.pi - turned[k - 1]) / (turned[k] - turned[k - 1]) * every
+    T = 2 * t_half
+    want = A.jeffery_period(2.0, 2 * uw / (ny - 2))
+    print("Jeffery period", T, "closed form", want)
+    assert abs(T / want - 1.0) < 0.05
+
+
+def test_squirmer_swimming_speed():
+    n, B1 = 96, 1e-3
+    speeds = []
+    for beta in (0.0, 2.0):
+        b = box(n, n, n, 1.0)
+        q = axis_angle_quaternion((0.3, 1.0, -0.2), 0.7)
+        p = particle((6.0, 3.0, 3.0), (0.5 * n, 0.5 * n, 0.5 * n), q, B1=B1, B2=beta * B1)
+        sim = L.Simulation([b], [[p]], max_semi=6)
+        sim.step(2000)
+        U = []
+        for _ in range(20):
+            sim.step(50)
+            r = sim.particle(0, 0)
+            U.append(r["U"] @ _axis(r["q"]))
+        speeds.append(float(np.mean(U)))
+    want = A.squirmer_speed(B1, 6.0, 3.0)
+    print("squirmer speeds", speeds, "closed form", want)
+    assert abs(speeds[0] / want - 1.0) < 0.10
+    assert abs(speeds[1] / speeds[0] - 1.0) < 0.03
