@@ -75,3 +75,43 @@ def test_squirmer_swimming_speed():
     print("squirmer speeds", speeds, "closed form", want)
     assert abs(speeds[0] / want - 1.0) < 0.10
     assert abs(speeds[1] / speeds[0] - 1.0) < 0.03
+
+
+def test_orientation_sweep_oberbeck_and_drift():
+    """The 8 x 64^3 benchmark workload run to steady state (6000 steps, about six
+    diffusion times): the end-on spheroid settles faster than the broadside one
+    by the Oberbeck difference F/(6 pi mu a) (1/C_par - 1/C_perp) (Sec. III.A;
+    the leading periodic correction is the same for both and cancels), and an
+    inclined one drifts sideways by the angle of Eq. drift (Sec. III.B).  Bars:
+    25 % on the difference (a small difference of two discretised shapes);
+    the drift angle within 10 % of Eq. drift built, as the paper builds it,
+    from the measured end-on and broadside velocities (tan(alpha - delta) =
+    (U_broad / U_end) tan alpha, Stokes linearity) and within 35 % of Eq. drift
+    with the free-space Oberbeck coefficients (the periodic images act
+    differently on the two principal directions at the next order in a/L); 2 %
+    on the force-direction velocity at 45 degrees against the mean of the
+    aligned ones."""
+    from lb_inputs import SWEEP_ANGLES, sweep_8x64
+
+    boxes, parts = sweep_8x64(seed=0)
+    sim = L.Simulation(boxes, parts, max_semi=8)
+    sim.step(6000)
+    U = {ang: sim.particle(k, 0)["U"] for k, ang in enumerate(SWEEP_ANGLES) if ang is not None}
+    a, bb, F, mu = 8.0, 4.0, 5e-4, 0.1
+    cpar, cperp = A.oberbeck_coefficients(A.eccentricity(a, bb))
+    want = F / (6 * math.pi * mu * a) * (1 / cpar - 1 / cperp)
+    got = U[0.0][0] - U[90.0][0]
+    print("end-on minus broadside", got, "closed form", want)
+    assert got > 0 and abs(got / want - 1.0) < 0.25
+    assert abs(U[45.0][0] / (0.5 * (U[0.0][0] + U[90.0][0])) - 1.0) < 0.02
+    ratio = U[90.0][0] / U[0.0][0]
+    for ang in (15.0, 30.0, 45.0, 60.0, 75.0):
+        alpha = math.radians(ang)
+        # the velocity turns from the force towards the long axis by delta
+        delta = math.atan2(U[ang][1], U[ang][0])
+        linear = alpha - math.atan(ratio * math.tan(alpha))
+        free = A.drift_angle(alpha, a, bb)
+        print("drift", ang, math.degrees(delta), math.degrees(linear), math.degrees(free))
+        assert delta > 0
+        assert abs(delta / linear - 1.0) < 0.10
+        assert abs(delta / free - 1.0) < 0.35
