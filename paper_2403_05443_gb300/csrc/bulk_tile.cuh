@@ -91,11 +91,8 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
 #pragma unroll
         for (int i = 0; i < Q; ++i) set_comp(v[i], k, wallrow ? 0.0f : f[i]);
     }
-    // nodes of this quad that the boundary kernel writes; quads within two
-    // nodes of a particle's cube keep their lines in L2 for the next step's
-    // boundary and particle work
+    // nodes of this quad that the boundary kernel writes
     unsigned skip = 0;
-    bool near = false;
     for (int j = 0; j < B.pcnt; ++j) {
         const NeedHdr h = ldcg_hdr(P.need_hdr + B.pbeg + j);
         int dz = z - h.ow[2];
@@ -105,8 +102,6 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
         int dx = 4 * xq - h.ow[0];
         if (dx < 0) dx += nx;
         // within two nodes of the cube, cyclically (a cache hint only)
-        near = near || ((dz < h.S + 2 || dz >= nz - 2) && (dy < h.S + 2 || dy >= ny - 2) &&
-                        (dx < h.S + 2 || dx + 3 >= nx - 2));
         if (dz >= h.S || dy >= h.S) continue;
         if (dx >= h.S && dx + 3 < nx) continue;
         const uint64_t w = __ldcg(P.need + (size_t)(B.pbeg + j) * (MAXS * MAXS) + dz * h.S + dy);
@@ -118,7 +113,7 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
     }
     if (valid) {
         T* dp = D + own;
-        const unsigned long long pol = near ? l2_evict_normal() : pol_first;
+        const unsigned long long pol = pol_first;
         if (!skip) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) St::st4(dp + i * N, v[i], B.scale, pol);
