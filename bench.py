@@ -232,7 +232,7 @@ def run_ours(args):
     sim.step(args.warmup, stream=sp)
     # launch shape of the step kernel for this workload (untimed; the
     # candidates compute identical values, so this is more warm-up)
-    fetch, fetch_ms = pkg.lbsph.lb_autotune(sim.ctx, 64, sp)
+    (fetch, gx, _), tune_ms = pkg.lbsph.lb_autotune(sim.ctx, 64, sp)
     torch.cuda.synchronize()
 
     def barrier():
@@ -299,7 +299,9 @@ def run_ours(args):
             "dtype": "f32" if args.precision == "fp32" else f"f32 arithmetic, {args.precision} storage",
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "boxes": len(boxes), "nodes_per_gpu": nodes,
-                       "autotune": {"units_per_fetch": fetch, "ms_per_step_1_2_4_8": [round(v, 5) for v in fetch_ms]},
+                       "autotune": {"units_per_fetch": fetch, "blocks_per_particle": gx,
+                                    "ms_per_step_gx_1_2_3_default": [round(v, 5) for v in tune_ms[:4]],
+                                    "ms_per_step_fetch_1_2_4_8": [round(v, 5) for v in tune_ms[4:]]},
                        "precision": args.precision,
                        "l2": f"state {2 * nodes * BYTES_PER_LUP[args.precision] // 2 / 1e6:.0f} MB > 129 MB L2; not flushed",
                        "parallelism": f"{world} rank(s), 8 independent boxes each, no collective"},

@@ -183,17 +183,19 @@ lb_status lb_get_drag(lb_ctx* ctx, int32_t box, int32_t particle, double* out36)
 lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, double* ms_out);
 
 /* Autotuner of the time-step kernel's launch shape for this context's boxes:
- * runs the candidates for the number of consecutive 128-node bulk units a
- * warp takes per fetch from the work counter (1, 2, 4, 8), each for 2 + 
- * steps_per_candidate iterations, times them with CUDA events and keeps the
- * fastest for later lb_step calls.  The candidates compute the same values bit
- * for bit, so this advances the simulation by 4 (2 + steps_per_candidate)
- * iterations (plus the first collision if none ran yet) exactly as lb_step
- * would.  chosen (may be NULL) receives the units per fetch kept; ms_per_step
- * (may be NULL, 4 doubles) the measured time per iteration of each candidate.
- * Not part of the paper.  Waits for completion.
- * Errors: LB_EINVAL, LB_ESTATE (separate-kernels mode), LB_ECUDA. */
-lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void* stream, int32_t* chosen, double* ms_per_step);
+ * runs, each for 2 + steps_per_candidate iterations timed with CUDA events,
+ * (1) the number of blocks that share one particle's boundary nodes (1, 2, 3
+ * and the size-based default, those below the default whose node lists fit
+ * 100 KB of shared memory), then (2) the number of consecutive 128-node bulk
+ * units a warp takes per fetch from the work counter (1, 2, 4, 8), and keeps the
+ * fastest of each for later lb_step calls.  The candidates compute the same
+ * values bit for bit, so tuning advances the simulation exactly as lb_step
+ * would.  out3 (may be NULL): units per fetch kept, blocks per particle kept,
+ * iterations advanced (including the first collision if none ran yet).
+ * ms_per_step (may be NULL, 8 doubles): time per iteration of each candidate
+ * (0 where a candidate was skipped).  Not part of the paper.  Waits for
+ * completion.  Errors: LB_EINVAL, LB_ESTATE (separate-kernels mode), LB_ECUDA. */
+lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void* stream, int32_t* out3, double* ms_per_step);
 
 /* Waits for all work of the context and returns the device status word's error. */
 lb_status lb_synchronize(lb_ctx* ctx);

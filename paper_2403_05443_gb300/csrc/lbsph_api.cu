@@ -827,14 +827,22 @@ extern "C" lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, flo
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner of the step kernel's launch shape: how many consecutive 32-quad
-// bulk units a warp takes per fetch from the work counter (1, 2, 4 or 8).
-// More units per fetch cost fewer atomics and keep a warp on neighbouring
-// rows; fewer balance the end of each iteration better.  Every candidate
-// computes the same values bit for bit (the assignment of units to warps does
-// not enter any node's arithmetic), so tuning advances the simulation exactly
-// as lb_step would.
-extern "C" lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void* stream, int32_t* chosen,
+// Autotuner of the step kernel's launch shape on the context's own boxes:
+// first the number of blocks that share a particle's boundary nodes (gx: 1,
+// 2, 3 or the size-based default; fewer blocks spend less SM time on fixed
+// per-block costs, more blocks shorten the particle chain), then how many
+// consecutive 32-quad bulk units a warp takes per fetch from the work counter
+// (1, 2, 4, 8).  Every candidate computes the same values bit for bit: the
+// boundary sums are integer atomics, whose order does not matter, and the
+// assignment of bulk units to warps does not enter any node's arithmetic.
+static int list_cap_for(lb_ctx* ctx, int gx)
+{
+    const long long Smax = 2ll * (ctx->opt.max_semi + CUBE_MARGIN) + 2;
+    const long long total = std::min(Smax * Smax * Smax, 16 * Smax * Smax);
+    return (int)((total + gx - 1) / gx);
+}
+
+extern "C" lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void* stream, int32_t* out3,
                                  double* ms_per_step)
 {
     if (!ctx) return LB_EINVAL;
@@ -842,19 +850,17 @@ extern "C" lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void*
     if (ctx->opt.flags & LB_FLAG_SEPARATE_KERNELS) return fail(ctx, LB_ESTATE, "no step kernel to tune");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = pick(ctx, stream);
+    int advanced = 0;
     if (!ctx->collided) {
         const lb_status r = lb_step(ctx, 1, stream);
         if (r != LB_OK) return r;
+        advanced = 1;
     }
-    static const int cand[4] = {1, 2, 4, 8};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    double best = 1e300;
-    int best_f = ctx->fetch;
-    for (int c = 0; c < 4; ++c) {
-        ctx->fetch = cand[c];
-        lb_status r = lb_step(ctx, 2, stream);               // warm the new shape
+    auto timed = [&](double& per) -> lb_status {
+        lb_status r = lb_step(ctx, 2, stream);              // warm the new shape
         if (r != LB_OK) return r;
         CK(cudaEventRecord(e0, s));
         r = lb_step(ctx, steps_per_candidate, stream);
@@ -863,13 +869,49 @@ extern "C" lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void*
         CK(cudaEventSynchronize(e1));
         float ms = 0.0f;
         CK(cudaEventElapsedTime(&ms, e0, e1));
-        const double per = ms / steps_per_candidate;
+        per = ms / steps_per_candidate;
+        advanced += 2 + steps_per_candidate;
+        return LB_OK;
+    };
+    const long long Smax = 2ll * (ctx->opt.max_semi + CUBE_MARGIN) + 2;
+    const int gx0 = (int)std::max(1ll, (3 * Smax * Smax + BBLOCK - 1) / BBLOCK);
+    const int gcand[4] = {1, 2, 3, gx0};
+    double best = 1e300;
+    int best_gx = ctx->gx;
+    for (int c = 0; c < 4; ++c) {
+        if (ms_per_step) ms_per_step[c] = 0.0;
+        if (ctx->np == 0 || (c < 3 && gcand[c] >= gx0)) continue;    // only fewer blocks than the default
+        // the node list of one block lives in shared memory next to two maps
+        const size_t smem = 2ull * Smax * Smax * sizeof(uint64_t) + (size_t)list_cap_for(ctx, gcand[c]) * 4;
+        if (smem > 100 * 1024) continue;
+        ctx->gx = gcand[c];
+        ctx->list_cap = list_cap_for(ctx, gcand[c]);
+        double per = 0.0;
+        const lb_status r = timed(per);
+        if (r != LB_OK) return r;
         if (ms_per_step) ms_per_step[c] = per;
-        if (per < best) { best = per; best_f = cand[c]; }
+        if (per < best) { best = per; best_gx = gcand[c]; }
+    }
+    ctx->gx = best_gx;
+    ctx->list_cap = list_cap_for(ctx, best_gx);
+    static const int fcand[4] = {1, 2, 4, 8};
+    best = 1e300;
+    int best_f = ctx->fetch;
+    for (int c = 0; c < 4; ++c) {
+        ctx->fetch = fcand[c];
+        double per = 0.0;
+        const lb_status r = timed(per);
+        if (r != LB_OK) return r;
+        if (ms_per_step) ms_per_step[4 + c] = per;
+        if (per < best) { best = per; best_f = fcand[c]; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->fetch = best_f;
-    if (chosen) *chosen = best_f;
+    if (out3) {
+        out3[0] = best_f;
+        out3[1] = best_gx;
+        out3[2] = advanced;
+    }
     return read_status(ctx);
 }

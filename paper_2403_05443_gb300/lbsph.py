@@ -231,12 +231,13 @@ def lb_stokes_field(ctx, box: int, u_dev_ptr: int, drho_dev_ptr=None, stream=Non
 
 
 def lb_autotune(ctx, steps_per_candidate: int, stream=None):
-    """(units per fetch kept, ms per step of each candidate 1, 2, 4, 8)."""
-    ch = C.c_int32(0)
-    ms = np.zeros(4)
-    _check(library().lb_autotune(ctx, int(steps_per_candidate), stream, C.byref(ch),
+    """((units per fetch, blocks per particle, iterations advanced), ms per
+    step of the 4 blocks-per-particle and the 4 units-per-fetch candidates)."""
+    out = np.zeros(3, np.int32)
+    ms = np.zeros(8)
+    _check(library().lb_autotune(ctx, int(steps_per_candidate), stream, out.ctypes.data_as(C.POINTER(C.c_int32)),
                                  ms.ctypes.data_as(C.POINTER(C.c_double))), ctx)
-    return ch.value, ms
+    return tuple(int(v) for v in out), ms
 
 
 def lb_synchronize(ctx):

@@ -201,18 +201,19 @@ def test_invalid_particles_rejected():
 
 
 def test_autotune_keeps_results_bitwise_and_picks_a_candidate():
-    """The launch-shape candidates compute the same values bit for bit, so a
-    tuned run equals an untuned run of the same number of steps."""
+    """The launch-shape candidates (blocks per particle, units per fetch)
+    compute the same values bit for bit, so a tuned run equals an untuned run
+    of the same number of steps."""
     boxes = [box(48, 20, 24, 0.8, counter_force=1), box(32, 36, 20, 1.2)]
     g = rng(21)
     parts = [[particle((4.0, 2.0, 2.0), (20.5, 10.2, 12.1), random_quaternion(g), F_ext=(2e-4, 0, 0))],
              [particle((3.0, 2.5, 2.0), (15.3, 18.1, 9.7), random_quaternion(g), F_ext=(0, 1e-4, 0))]]
     a = _sim(boxes, parts)
-    chosen, ms = L.lb_autotune(a.ctx, 5)
-    assert chosen in (1, 2, 4, 8) and np.all(ms > 0)
+    (fetch, gx, advanced), ms = L.lb_autotune(a.ctx, 5)
+    assert fetch in (1, 2, 4, 8) and gx >= 1 and np.all(ms[4:] > 0)
     a.step(9)
     b = _sim(boxes, parts)
-    b.step(1 + 4 * (2 + 5) + 9)
+    b.step(advanced + 9)
     for bi in range(2):
         assert np.array_equal(a.field("df", bi), b.field("df", bi))
         assert np.array_equal(a.records(bi), b.records(bi))
