@@ -72,7 +72,9 @@ enum {
 /* option flags */
 enum {
     LB_FLAG_SEPARATE_KERNELS = 1u  /* run each step as four kernel launches instead of the
-                                      persistent step kernel (same results, bit for bit) */
+                                      persistent step kernel (the same arithmetic; the two
+                                      compilations may contract a*b+c differently, so the
+                                      results agree to FP32 round-off) */
 };
 
 /* One periodic box (x, y, z periodic) or a channel (walls != 0: the planes

@@ -19,14 +19,13 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
     int q = (tile - B.block_begin) * KBLOCK + tix;
     const bool valid = q < (int)B.nq;
     if (!valid) q = (int)B.nq - 1;
-    const int row = q / nxq;
+    const int row = div_magic(q, B.dq_m, B.dq_s);
     const int xq = q - row * nxq;
-    const int z = row / ny;
+    const int z = div_magic(row, B.dy_m, B.dy_s);
     const int y = row - z * ny;
     const int lane = tix & 31;
     const T* A = reinterpret_cast<const T*>(P.src) + B.off;
     T* D = reinterpret_cast<T*>(P.dst) + B.off;
-    const float inv = B.inv_scale;
     const int own = row * nx + 4 * xq;
     const unsigned long long pol_first = l2_evict_first();
 
@@ -39,30 +38,42 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
 #pragma unroll
             for (int b = 0; b < 3; ++b) rofs[a][b] = (zz[b] * ny + yy[a]) * nx;
     }
-    const bool left_ld = (lane == 0) || (xq == 0);
-    const bool right_ld = (lane == 31) || (xq == nxq - 1);
-
     float4 v[Q];
+    if (FIRST) {
+        // first collision: the initial distributions of the node itself
+        // (rest, or a field set by lb_init_fluid), no streaming
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        if (FIRST) {
-            // first collision: the initial distributions of the node itself
-            // (rest, or a field set by lb_init_fluid), no streaming
-            v[i] = St::ld4(A + (i * N + own), inv, pol_first);
-            continue;
+        for (int i = 0; i < Q; ++i) v[i] = St::ld4r(A + (i * N + own), pol_first);
+    } else if (B.rowwarp) {
+        // every row lies within this warp's 32 quads (nxq divides 32 and
+        // the unit starts a row): the periodic wrap in x is a shuffle too
+        const int srcl = xq == 0 ? lane + nxq - 1 : lane - 1;
+        const int srcr = xq == nxq - 1 ? lane - nxq + 1 : lane + 1;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float4 t = St::ld4r(A + (i * N + rofs[1 - cy_of(i)][1 - cz_of(i)] + 4 * xq), pol_first);
+            if (cx_of(i) == 1) t = make_float4(__shfl_sync(0xffffffffu, t.w, srcl), t.x, t.y, t.z);
+            else if (cx_of(i) == -1) t = make_float4(t.y, t.z, t.w, __shfl_sync(0xffffffffu, t.x, srcr));
+            v[i] = t;
         }
-        const T* rp = A + (i * N + rofs[1 - cy_of(i)][1 - cz_of(i)]);
-        float4 t = St::ld4(rp + 4 * xq, inv, pol_first);
-        if (cx_of(i) == 1) {            // source x - 1
-            float l = __shfl_up_sync(0xffffffffu, t.w, 1);
-            if (left_ld) l = St::ld1(rp + (xq == 0 ? nx - 1 : 4 * xq - 1), inv, pol_first);
-            t = make_float4(l, t.x, t.y, t.z);
-        } else if (cx_of(i) == -1) {    // source x + 1
-            float r = __shfl_down_sync(0xffffffffu, t.x, 1);
-            if (right_ld) r = St::ld1(rp + (xq == nxq - 1 ? 0 : 4 * xq + 4), inv, pol_first);
-            t = make_float4(t.y, t.z, t.w, r);
+    } else {
+        const bool left_ld = (lane == 0) || (xq == 0);
+        const bool right_ld = (lane == 31) || (xq == nxq - 1);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const T* rp = A + (i * N + rofs[1 - cy_of(i)][1 - cz_of(i)]);
+            float4 t = St::ld4r(rp + 4 * xq, pol_first);
+            if (cx_of(i) == 1) {            // source x - 1
+                float l = __shfl_up_sync(0xffffffffu, t.w, 1);
+                if (left_ld) l = St::ld1r(rp + (xq == 0 ? nx - 1 : 4 * xq - 1), pol_first);
+                t = make_float4(l, t.x, t.y, t.z);
+            } else if (cx_of(i) == -1) {    // source x + 1
+                float r = __shfl_down_sync(0xffffffffu, t.x, 1);
+                if (right_ld) r = St::ld1r(rp + (xq == nxq - 1 ? 0 : 4 * xq + 4), pol_first);
+                t = make_float4(t.y, t.z, t.w, r);
+            }
+            v[i] = t;
         }
-        v[i] = t;
     }
 
     const BoxDyn dyn = ldcg_dyn(P.box_dyn + bi);
@@ -75,13 +86,14 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
         for (int i = 1; i < Q; ++i) {
             if (cy_of(i) != cyw) continue;
             const float ubc = cx_of(i) * uw[0] + cy_of(i) * uw[1] + cz_of(i) * uw[2];
-            const float add = 6.0f * w_of(i) * B.rho0f * ubc;
-            const float4 o = St::ld4(A + (opp_of(i) * N + own), inv, pol_first);
+            float add = 6.0f * w_of(i) * B.rho0f * ubc;
+            if (St::SCALED) add *= B.scale;
+            const float4 o = St::ld4r(A + (opp_of(i) * N + own), pol_first);
             v[i] = make_float4(o.x + add, o.y + add, o.z + add, o.w + add);
         }
     }
-    Collider C;
-    C.init(B.omega, B.rho0f, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps);
+    ColliderT<St::SCALED> C;
+    C.init(B.omega, B.rho0f, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps, B.scale, B.inv_scale);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         float f[Q];
@@ -89,7 +101,7 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
         for (int i = 0; i < Q; ++i) f[i] = comp(v[i], k);
         C.apply(f);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) set_comp(v[i], k, wallrow ? 0.0f : f[i]);
+        for (int i = 0; i < Q; ++i) set_comp(v[i], k, f[i]);
     }
     // nodes of this quad that the boundary kernel writes
     unsigned skip = 0;
@@ -111,18 +123,19 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
             if (mx < h.S && ((w >> mx) & 1ull)) skip |= 1u << k;
         }
     }
-    if (valid) {
+    // the solid wall planes keep the zeros they were created with
+    if (valid && !wallrow) {
         T* dp = D + own;
         const unsigned long long pol = pol_first;
         if (!skip) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) St::st4(dp + i * N, v[i], B.scale, pol);
+            for (int i = 0; i < Q; ++i) St::st4r(dp + i * N, v[i], pol);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if ((skip >> k) & 1u) continue;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) St::st1(dp + (i * N + k), comp(v[i], k), B.scale, pol);
+                for (int i = 0; i < Q; ++i) St::st1r(dp + (i * N + k), comp(v[i], k), pol);
             }
         }
     }

@@ -99,17 +99,26 @@ __device__ __forceinline__ void sth_u16(void* a, unsigned short v, unsigned long
 }
 
 // ---------------------------------------------------------------------------
-// storage policies: values are deviations f_i - w_i rho0 (x scale for FP16)
+// storage policies: values are deviations f_i - w_i rho0 (x scale for FP16).
+// ld4/ld1/st4/st1 convert to and from physical units; the raw forms keep the
+// stored scale (SCALED: FP16), for the bulk tile, whose collision works in
+// stored units (ColliderT<true>).
 struct StF32 {
     using T = float;
+    static constexpr bool SCALED = false;
     static __device__ __forceinline__ float4 ld4(const T* p, float, unsigned long long pol) { return ldh_f4(p, pol); }
     static __device__ __forceinline__ float ld1(const T* p, float, unsigned long long pol) { return ldh_f1(p, pol); }
     static __device__ __forceinline__ void st4(T* p, float4 v, float, unsigned long long pol) { sth_f4(p, v, pol); }
     static __device__ __forceinline__ void st1(T* p, float v, float, unsigned long long pol) { sth_f1(p, v, pol); }
+    static __device__ __forceinline__ float4 ld4r(const T* p, unsigned long long pol) { return ldh_f4(p, pol); }
+    static __device__ __forceinline__ float ld1r(const T* p, unsigned long long pol) { return ldh_f1(p, pol); }
+    static __device__ __forceinline__ void st4r(T* p, float4 v, unsigned long long pol) { sth_f4(p, v, pol); }
+    static __device__ __forceinline__ void st1r(T* p, float v, unsigned long long pol) { sth_f1(p, v, pol); }
 };
 
 struct StF16 {
     using T = __half;
+    static constexpr bool SCALED = true;
     static __device__ __forceinline__ float4 ld4(const T* p, float inv, unsigned long long pol)
     {
         const uint2 u = ldh_u2(p, pol);
@@ -134,10 +143,35 @@ struct StF16 {
     {
         sth_u16(p, __half_as_ushort(__float2half_rn(v * scale)), pol);
     }
+    static __device__ __forceinline__ float4 ld4r(const T* p, unsigned long long pol)
+    {
+        const uint2 u = ldh_u2(p, pol);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ float ld1r(const T* p, unsigned long long pol)
+    {
+        return __half2float(__ushort_as_half(ldh_u16(p, pol)));
+    }
+    static __device__ __forceinline__ void st4r(T* p, float4 v, unsigned long long pol)
+    {
+        __half2 a = __floats2half2_rn(v.x, v.y);
+        __half2 b = __floats2half2_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<unsigned*>(&a);
+        u.y = *reinterpret_cast<unsigned*>(&b);
+        sth_u2(p, u, pol);
+    }
+    static __device__ __forceinline__ void st1r(T* p, float v, unsigned long long pol)
+    {
+        sth_u16(p, __half_as_ushort(__float2half_rn(v)), pol);
+    }
 };
 
 struct StBF16 {
     using T = __nv_bfloat16;
+    static constexpr bool SCALED = false;
     static __device__ __forceinline__ float4 ld4(const T* p, float, unsigned long long pol)
     {
         const uint2 u = ldh_u2(p, pol);
@@ -162,6 +196,10 @@ struct StBF16 {
     {
         sth_u16(p, __bfloat16_as_ushort(__float2bfloat16_rn(v)), pol);
     }
+    static __device__ __forceinline__ float4 ld4r(const T* p, unsigned long long pol) { return ld4(p, 1.0f, pol); }
+    static __device__ __forceinline__ float ld1r(const T* p, unsigned long long pol) { return ld1(p, 1.0f, pol); }
+    static __device__ __forceinline__ void st4r(T* p, float4 v, unsigned long long pol) { st4(p, v, 1.0f, pol); }
+    static __device__ __forceinline__ void st1r(T* p, float v, unsigned long long pol) { st1(p, v, 1.0f, pol); }
 };
 
 // ---------------------------------------------------------------------------
@@ -188,27 +226,40 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float a)
 // depends only on the box's uniform force g computed once per box.  eps is the
 // mass put back by an earlier remap: w_i eps is added to every population
 // first, which only moves drho and P.
-struct Collider {
-    float omega, om1, rho0, eps;
+//
+// SCALED: the populations come and go in stored units (times the FP16 storage
+// scale sc, a power of two): drho and j are brought to physical units by one
+// multiplication each, and omega (where it multiplies an equilibrium term),
+// 3 cf, eps and the force terms are held times sc, so that P and the pair terms
+// come out times sc; no population is scaled on load or on store.  With a
+// power-of-two sc each of these products is exact, so the results are the
+// same bits as scaling every population.
+template <bool SCALED>
+struct ColliderT {
+    float omega, om1, rho0, eps;    // SCALED: omega and eps times sc
     float gx, gy, gz;
-    float cfug;                     // 3 cf, the factor of u.g in P
-    float k[9], l[9];               // per pair: 9 cf w (c.g) and 3 cf w (c.g)
+    float cfug;                     // 3 cf, the factor of u.g in P (times sc)
+    float k[9], l[9];               // per pair: 9 cf w (c.g) and 3 cf w (c.g) (times sc)
+    float isc;                      // SCALED: 1 / sc
 
-    __device__ __forceinline__ void init(float omega_, float rho0_, float gx_, float gy_, float gz_, float eps_)
+    __device__ __forceinline__ void init(float omega_, float rho0_, float gx_, float gy_, float gz_, float eps_,
+                                         float scale = 1.0f, float inv_scale = 1.0f)
     {
-        omega = omega_;
+        const float s = SCALED ? scale : 1.0f;
+        omega = omega_ * s;
         om1 = 1.0f - omega_;
         rho0 = rho0_;
-        eps = eps_;
+        eps = eps_ * s;
         gx = gx_; gy = gy_; gz = gz_;
+        isc = inv_scale;
         const float cf = 1.0f - 0.5f * omega_;
-        cfug = 3.0f * cf;
+        cfug = (3.0f * cf) * s;
 #pragma unroll
         for (int m = 0; m < 9; ++m) {
             const int i = 2 * m + 1;
             const float cg = cx_of(i) * gx_ + cy_of(i) * gy_ + cz_of(i) * gz_;
-            k[m] = (9.0f * w_of(i)) * cf * cg;
-            l[m] = (3.0f * w_of(i)) * cf * cg;
+            k[m] = ((9.0f * w_of(i)) * cf * cg) * s;
+            l[m] = ((3.0f * w_of(i)) * cf * cg) * s;
         }
     }
 
@@ -231,6 +282,12 @@ struct Collider {
             if (cy_of(i) == 1) jy += df[m]; else if (cy_of(i) == -1) jy -= df[m];
             if (cz_of(i) == 1) jz += df[m]; else if (cz_of(i) == -1) jz -= df[m];
         }
+        if (SCALED) {
+            drho *= isc;
+            jx *= isc;
+            jy *= isc;
+            jz *= isc;
+        }
         const float rho = rho0 + drho;
         const float ir = __fdividef(1.0f, rho);
         const float ux = (jx + 0.5f * gx) * ir, uy = (jy + 0.5f * gy) * ir, uz = (jz + 0.5f * gz) * ir;
@@ -251,6 +308,8 @@ struct Collider {
         }
     }
 };
+
+using Collider = ColliderT<false>;
 
 // one node's collision with freshly set-up box terms
 __device__ __forceinline__ void collide19(float (&f)[Q], float omega, float rho0, float gx, float gy,

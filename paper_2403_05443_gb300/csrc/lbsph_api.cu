@@ -243,6 +243,9 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
         h.nwall = d.walls ? 2ll * d.nx * d.nz : 0;
         h.scale = scale;
         h.inv_scale = 1.0f / scale;
+        magic_div((unsigned)h.nxq, h.dq_m, h.dq_s);
+        magic_div((unsigned)h.ny, h.dy_m, h.dy_s);
+        h.rowwarp = (32 % h.nxq) == 0;
         ctx->hbox.push_back(h);
     }
     ctx->total_blocks = blk;

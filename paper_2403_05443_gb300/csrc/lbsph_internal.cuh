@@ -120,7 +120,39 @@ struct BoxDev {
     int pbeg, pcnt;                 // particles of this box
     long long nwall;                // wall nodes (2 nx nz when walls)
     float scale, inv_scale;         // 16-bit storage scale (1 for FP32 / BF16)
+    unsigned dq_m, dy_m;            // q / nxq and row / ny as __umulhi(n, m) >> s (div_magic)
+    int dq_s, dy_s;
+    int rowwarp;                    // 1: nxq divides 32, every row lies within one warp's 32 quads
 };
+
+// Division by a box constant d without a divide: n / d == (n m / 2^32) >> s
+// for 0 <= n < 2^31, with l = ceil(log2 d), m = ceil(2^(31+l) / d) and
+// s = l - 1 (m < 2^32).  m exceeds 2^(31+l) / d by less than 1, so n m / 2^(31+l)
+// exceeds n / d by less than n / 2^(31+l) < 1 / d, which cannot reach the next
+// integer (the fraction of n / d is at most 1 - 1/d).  d = 1 gives s = -1.
+inline void magic_div(unsigned d, unsigned& m, int& s)
+{
+    if (d <= 1) {
+        m = 0;
+        s = -1;
+        return;
+    }
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned long long num = 1ull << (31 + l);
+    m = (unsigned)((num + d - 1) / d);
+    s = l - 1;
+}
+
+// n / d for 0 <= n < 2^31 with the multiplier and shift of magic_div (s < 0: d = 1)
+__host__ __device__ __forceinline__ int div_magic(int n, unsigned m, int s)
+{
+#ifdef __CUDA_ARCH__
+    return s < 0 ? n : (int)(__umulhi((unsigned)n, m) >> s);
+#else
+    return s < 0 ? n : (int)((((unsigned long long)(unsigned)n * m) >> 32) >> s);
+#endif
+}
 
 // FP32 snapshot of one particle for the lattice kernels, written by the
 // critical particle kernel of iteration t for the kernels of iteration t+1.
