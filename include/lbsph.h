@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define LBSPH_ABI_VERSION 1
+#define LBSPH_ABI_VERSION 2
 
 typedef struct lb_ctx lb_ctx;
 
@@ -235,13 +235,20 @@ lb_status lb_links_noalloc(const double* semi, const double* q, const double* x,
  * of the velocity field u (FP32 [3][nz][ny][nx], u_bytes = 3*N*4) and the
  * density deviation drho (FP32 [nz][ny][nx], NULL = uniform rho0) on every fluid
  * node; solid and wall nodes keep no distributions.  u and drho are host memory,
- * or device memory if is_device.  The first iteration then collides these
- * distributions in place (the Appendix's step 1 at t = 0) instead of the rest
- * state.  Not part of the paper: this is the fluid half of the learned warm
- * start (lbsurrogate.h).  Waits for completion.
+ * or device memory if is_device.  with_stress != 0 adds the first-order
+ * (Chapman-Enskog) non-equilibrium part of a viscous flow,
+ *   f_i += -3 tau rho w_i (c_ia c_ib - delta_ab / 3) d_a u_b,
+ * rho = rho0 + drho, d_a the periodic central difference of u, so that the
+ * populations start with the flow's viscous stress (second moment
+ * -tau rho c_s^2 (grad u + grad u^T)) instead of none, which otherwise relaxes
+ * in the first steps and launches shear and sound waves through the box.  The
+ * first iteration then collides these distributions in place (the Appendix's
+ * step 1 at t = 0) instead of the rest state.  Not part of the paper: this is
+ * the fluid half of the learned warm start (lbsurrogate.h).  Waits for
+ * completion.
  * Errors: LB_EINVAL (bad box or size), LB_ESTATE (after a step), LB_ECUDA. */
 lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, size_t u_bytes, const float* drho,
-                        int32_t is_device, void* stream);
+                        int32_t is_device, int32_t with_stress, void* stream);
 
 /* The periodic Stokes flow (mu Lap u - grad p + g = 0, div u = 0, mu = rho0 nu)
  * driven by the particles of box `box`: g puts each particle's F_ext uniformly on

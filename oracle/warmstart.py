@@ -19,6 +19,12 @@ symbol), the closed form of a curl-free force's pressure and the symmetry of
 the periodic Green's function
 (tests/test_oracle_warmstart.py).
 
+Non-equilibrium start (stress_f): the first-order Chapman-Enskog part of the
+populations of a viscous flow, pinned by its moments (none in mass and
+momentum, the viscous stress in the second moment, a closed form for a shear
+wave) and by the LB's own decay of a shear wave, which it starts on the decaying
+mode (tests/test_oracle_warmstart.py).
+
 Scaling: D = diag(s_t I3, s_r I3), s_t^2 = 6 pi mu b, s_r^2 = 8 pi mu b^3
 (mu = rho0 nu); the network predicts R^ = D^-1 R D^-1, so a radius-b sphere in
 free space has R^ = I (Stokes drag 6 pi mu b and torque 8 pi mu b^3).
@@ -116,6 +122,32 @@ def equilibrium_f(u, rho, c, w):
     uu = (u * u).sum(-1, keepdims=True)
     rho = np.asarray(rho, np.float64)[..., None] if np.ndim(rho) else rho
     return np.asarray(w) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)
+
+
+def stress_f(u, rho, tau, c, w):
+    """First-order (Chapman-Enskog) non-equilibrium populations of a viscous
+    flow u[3, nz, ny, nx]: f_i = -3 tau rho w_i (c_ia c_ib - delta_ab / 3)
+    d_a u_b, with d_a the periodic central difference; returns [..., 19] in the
+    order of the table (c, w).  Its second moment is -tau rho c_s^2 (grad u +
+    grad u^T) and its zeroth and first moments vanish."""
+    u = np.asarray(u, np.float64)
+    # grad[a][b] = d_a u_b; axis of x in an [nz, ny, nx] array is 2
+    axis = {0: 2, 1: 1, 2: 0}
+    grad = np.zeros((3, 3) + u.shape[1:])
+    for a in range(3):
+        for b in range(3):
+            grad[a, b] = 0.5 * (np.roll(u[b], -1, axis=axis[a]) - np.roll(u[b], 1, axis=axis[a]))
+    c = np.asarray(c, np.float64)
+    div = grad[0, 0] + grad[1, 1] + grad[2, 2]
+    out = np.zeros(u.shape[1:] + (len(w),))
+    rho = np.asarray(rho, np.float64)
+    for i in range(len(w)):
+        q = -div / 3.0
+        for a in range(3):
+            for b in range(3):
+                q = q + c[i, a] * c[i, b] * grad[a, b]
+        out[..., i] = -3.0 * tau * rho * w[i] * q
+    return out
 
 
 def features(geom):

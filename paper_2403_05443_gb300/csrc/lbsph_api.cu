@@ -33,7 +33,7 @@ cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const 
 cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
                          int cap, int* count, cudaStream_t s);
 cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const float* drho,
-                              const int* owner, cudaStream_t s);
+                              const int* owner, float tau, int stress, cudaStream_t s);
 cudaError_t launch_stokes(const BoxDev& B, const int* owner, const PartDev* pd, int np, int counter_on,
                           const double body[3], float mu, float2* work, int* counts, double* sum, float* u,
                           cudaStream_t s);
@@ -768,7 +768,7 @@ static cudaError_t owner_field(lb_ctx* ctx, int box, cudaStream_t s)
 }
 
 extern "C" lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, size_t u_bytes, const float* drho,
-                                   int32_t is_device, void* stream)
+                                   int32_t is_device, int32_t with_stress, void* stream)
 {
     if (!ctx) return LB_EINVAL;
     if (box < 0 || box >= (int)ctx->desc.size() || !u) return fail(ctx, LB_EINVAL, "bad box or field");
@@ -788,7 +788,8 @@ extern "C" lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, siz
     CK(cudaMemcpyAsync(ud, u, u_bytes, kind, s));
     if (dd) CK(cudaMemcpyAsync(dd, drho, (size_t)B.N * sizeof(float), kind, s));
     CK(owner_field(ctx, box, s));
-    CK(launch_init_fluid(B, ctx->opt.precision, ctx->fbuf[ctx->cur], ud, dd, reinterpret_cast<int*>(ctx->d_tmp), s));
+    CK(launch_init_fluid(B, ctx->opt.precision, ctx->fbuf[ctx->cur], ud, dd, reinterpret_cast<int*>(ctx->d_tmp),
+                         (float)ctx->desc[box].tau, with_stress != 0, s));
     CK(cudaStreamSynchronize(s));
     return read_status(ctx);
 }

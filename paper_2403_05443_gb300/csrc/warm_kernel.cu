@@ -1,5 +1,6 @@
 // Warm start of a run (lb_init_fluid, lb_stokes_field): an initial fluid at
-// the local equilibrium of given velocity and density fields, and the periodic
+// the local equilibrium of given velocity and density fields (optionally with
+// the viscous stress of the velocity field in its non-equilibrium part), and the periodic
 // Stokes flow (with its pressure) driven by the particles' external forces, as
 // those fields.
 //
@@ -22,9 +23,12 @@
 namespace lbsph {
 
 // f = f_eq(rho0 + drho, u) - w rho0 on fluid nodes (deviation storage), 0
-// elsewhere; drho may be null (uniform density)
+// elsewhere; drho may be null (uniform density).  stress: plus the first-order
+// non-equilibrium part -3 tau rho w_i (c_ia c_ib - delta_ab / 3) d_a u_b with
+// d_a the periodic central difference (u is read on every node, solid or not)
 template <class St>
-__global__ void init_fluid_kernel(const BoxDev B, void* fbuf, const float* u, const float* drho, const int* owner)
+__global__ void init_fluid_kernel(const BoxDev B, void* fbuf, const float* u, const float* drho, const int* owner,
+                                  float tau, int stress)
 {
     using T = typename St::T;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -35,12 +39,40 @@ __global__ void init_fluid_kernel(const BoxDev B, void* fbuf, const float* u, co
     const float uu = ux * ux + uy * uy + uz * uz;
     const float dr = (fluid && drho) ? drho[n] : 0.0f;
     const float rho = B.rho0f + dr;
+    float du[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};   // du[a][b] = d_a u_b
+    if (stress && fluid) {
+        const int nx = B.nx, ny = B.ny, nz = B.nz;
+        const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+        const long long row = (long long)nx * ny;
+        const long long yz = (long long)z * row + (long long)y * nx;
+        const long long nb[3][2] = {
+            {yz + (x == nx - 1 ? 0 : x + 1), yz + (x == 0 ? nx - 1 : x - 1)},
+            {(long long)z * row + (long long)(y == ny - 1 ? 0 : y + 1) * nx + x,
+             (long long)z * row + (long long)(y == 0 ? ny - 1 : y - 1) * nx + x},
+            {(long long)(z == nz - 1 ? 0 : z + 1) * row + (long long)y * nx + x,
+             (long long)(z == 0 ? nz - 1 : z - 1) * row + (long long)y * nx + x}};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) du[a][b] = 0.5f * (u[b * B.N + nb[a][0]] - u[b * B.N + nb[a][1]]);
+    }
+    const float dv = (du[0][0] + du[1][1] + du[2][2]) * (1.0f / 3.0f);
     const unsigned long long pol = l2_evict_normal();
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
-        const float d = fluid ? w_of(i) * (dr + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu)) : 0.0f;
-        St::st1(f + (long long)i * B.N + n, d, B.scale, pol);
+        float d = w_of(i) * (dr + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+        if (stress) {
+            const int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+            float q = -dv;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    if (c[a] * c[b] != 0) q += (float)(c[a] * c[b]) * du[a][b];
+            d += -3.0f * tau * rho * w_of(i) * q;
+        }
+        St::st1(f + (long long)i * B.N + n, fluid ? d : 0.0f, B.scale, pol);
     }
 }
 
@@ -213,12 +245,12 @@ __global__ void momentum_shift_kernel(float* u, const int* owner, long long N, c
 static unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const float* drho,
-                              const int* owner, cudaStream_t s)
+                              const int* owner, float tau, int stress, cudaStream_t s)
 {
     const unsigned g = nblk(B.N, 256);
-    if (precision == 1) init_fluid_kernel<StF16><<<g, 256, 0, s>>>(B, fbuf, u, drho, owner);
-    else if (precision == 2) init_fluid_kernel<StBF16><<<g, 256, 0, s>>>(B, fbuf, u, drho, owner);
-    else init_fluid_kernel<StF32><<<g, 256, 0, s>>>(B, fbuf, u, drho, owner);
+    if (precision == 1) init_fluid_kernel<StF16><<<g, 256, 0, s>>>(B, fbuf, u, drho, owner, tau, stress);
+    else if (precision == 2) init_fluid_kernel<StBF16><<<g, 256, 0, s>>>(B, fbuf, u, drho, owner, tau, stress);
+    else init_fluid_kernel<StF32><<<g, 256, 0, s>>>(B, fbuf, u, drho, owner, tau, stress);
     return cudaGetLastError();
 }
 

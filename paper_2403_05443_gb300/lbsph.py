@@ -82,7 +82,7 @@ def library(path: str | None = None):
     L.lb_links_noalloc.argtypes = [dp, dp, dp, i32, i32, i32, i32, vp, i32, vp, vp]
     L.lb_links_noalloc.restype = i32
     L.lb_autotune.argtypes = [vp, i32, vp, ip, dp]
-    L.lb_init_fluid.argtypes = [vp, i32, vp, C.c_size_t, vp, i32, vp]
+    L.lb_init_fluid.argtypes = [vp, i32, vp, C.c_size_t, vp, i32, i32, vp]
     L.lb_stokes_field.argtypes = [vp, i32, vp, vp, vp]
     L.lb_lattice.argtypes = [ip, dp]
     L.lb_lattice.restype = None
@@ -215,12 +215,15 @@ def lb_get_drag(ctx, box: int, particle: int) -> np.ndarray:
     return out.reshape(6, 6)
 
 
-def lb_init_fluid(ctx, box: int, u_ptr: int, nbytes: int, drho_ptr, is_device: bool, stream=None):
-    """Initial fluid f = f_eq(rho0 + drho, u) of a box before the first step;
-    u_ptr / drho_ptr (drho may be None) are host or device addresses of FP32
-    [3][nz][ny][nx] / [nz][ny][nx]."""
+def lb_init_fluid(ctx, box: int, u_ptr: int, nbytes: int, drho_ptr, is_device: bool, with_stress: bool = False,
+                  stream=None):
+    """Initial fluid f = f_eq(rho0 + drho, u) of a box before the first step
+    (with_stress: plus the first-order non-equilibrium part of the flow's
+    viscous stress); u_ptr / drho_ptr (drho may be None) are host or device
+    addresses of FP32 [3][nz][ny][nx] / [nz][ny][nx]."""
     _check(library().lb_init_fluid(ctx, box, C.c_void_p(u_ptr), nbytes,
-                                   None if drho_ptr is None else C.c_void_p(drho_ptr), int(is_device), stream), ctx)
+                                   None if drho_ptr is None else C.c_void_p(drho_ptr), int(is_device),
+                                   int(bool(with_stress)), stream), ctx)
 
 
 def lb_stokes_field(ctx, box: int, u_dev_ptr: int, drho_dev_ptr=None, stream=None):
@@ -374,12 +377,13 @@ class Simulation:
     def drag(self, box: int = 0, p: int = 0):
         return lb_get_drag(self.ctx, box, p)
 
-    def init_fluid(self, box: int, u: np.ndarray, drho: np.ndarray | None = None):
+    def init_fluid(self, box: int, u: np.ndarray, drho: np.ndarray | None = None, with_stress: bool = False):
         """Initial velocity field u (host, [3][nz][ny][nx]) and density
         deviation drho (host, [nz][ny][nx], or None) of a box."""
         a = np.ascontiguousarray(np.asarray(u, np.float32))
         d = None if drho is None else np.ascontiguousarray(np.asarray(drho, np.float32))
-        lb_init_fluid(self.ctx, box, a.ctypes.data, a.nbytes, None if d is None else d.ctypes.data, False)
+        lb_init_fluid(self.ctx, box, a.ctypes.data, a.nbytes, None if d is None else d.ctypes.data, False,
+                      with_stress)
 
     def set_external(self, box, ft, stream=None):
         lb_set_external(self.ctx, box, ft, stream)

@@ -160,11 +160,14 @@ def long_axis(q):
     return [q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3, 2 * (q1 * q2 + q0 * q3), 2 * (q1 * q3 - q0 * q2)]
 
 
-def warm_start(sim, box: int, net, use_net: bool = True, use_fluid: bool = True):
+def warm_start(sim, box: int, net, use_net: bool = True, use_fluid: bool = True, use_stress: bool = True):
     """Before the first step: set each particle's (U, Omega) to the surrogate's
     steady estimate R^-1 (F_ext, T_ext) (use_net) and the fluid to the lattice
-    Stokes flow of the particle forces and its pressure (use_fluid).  For several particles in a
-    box the confinement feature uses the edge of the volume per particle."""
+    Stokes flow of the particle forces and its pressure (use_fluid), with the
+    flow's viscous stress in the populations' non-equilibrium part
+    (use_stress; no effect at tau = 1, where the first collision discards it).
+    For several particles in a box the confinement feature uses the edge of the
+    volume per particle."""
     torch = _torch()
     b = sim.boxes[box]
     parts = [dict(p) for p in sim.parts_of(box)]
@@ -190,7 +193,7 @@ def warm_start(sim, box: int, net, use_net: bool = True, use_fluid: bool = True)
         u = torch.zeros(3 * N, dtype=torch.float32, device="cuda")
         d = torch.zeros(N, dtype=torch.float32, device="cuda")
         L.lb_stokes_field(sim.ctx, box, u.data_ptr(), d.data_ptr())
-        L.lb_init_fluid(sim.ctx, box, u.data_ptr(), u.numel() * 4, d.data_ptr(), True)
+        L.lb_init_fluid(sim.ctx, box, u.data_ptr(), u.numel() * 4, d.data_ptr(), True, use_stress)
 
 
 def velocity_history(sim, box: int, steps: int, every: int):
@@ -223,16 +226,18 @@ def steps_to_steady(hist, ref, every: int, tol: float = 1e-3):
 
 
 def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int = 4000, eval_n: int = 128,
-               eval_count: int = 16, force: float = 2e-5, every: int = 50, ref_steps: int = 40000, device: int = 0):
+               eval_count: int = 16, force: float = 2e-5, every: int = 50, ref_steps: int = 40000, device: int = 0,
+               eval_tau: float = 1.0):
     """The whole learned warm start, end to end on the GPU:
       1. resistance data from the LB method: n32 samples in 32^3 boxes and n48
          in 48^3 boxes (tau in {0.8, 1, 1.2}, a/b in [1, 3], b in [2, 3.5]),
          each flow developed for 8 diffusion times L^2 / (4 pi^2 nu) of its box;
       2. 24-fold cube-rotation augmentation, 10 % of the LB samples held out;
       3. training of the network;
-      4. an eval_n^3 box with eval_count spheroids and random forces, run cold
-         (fluid at rest, particles at rest), with the Stokes fluid only, and with
-         the Stokes fluid plus the network's velocities, each compared with the
+      4. an eval_n^3 box (eval_tau) with eval_count spheroids and random forces,
+         run cold (fluid at rest, particles at rest), with the Stokes fluid only,
+         and with the Stokes fluid plus the network's velocities (for
+         eval_tau != 1 also without the stress part), each compared with the
          steady velocities of a long cold run: steps until every particle's
          velocity stays within 1e-3 of it.
     Returns a dict of the measurements."""
@@ -268,13 +273,14 @@ def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int =
     rel = (torch.linalg.matrix_norm((Pv - Rv).reshape(-1, 6, 6)) /
            torch.linalg.matrix_norm(Rv.reshape(-1, 6, 6))).cpu().numpy()
     # evaluation runs
-    boxes, parts = I.many_spheroids(seed, n=eval_n, count=eval_count, force=force)
+    boxes, parts = I.many_spheroids(seed, n=eval_n, count=eval_count, force=force, tau=eval_tau)
     ms = int(math.ceil(max(p["semi"][0] for p in parts[0])))
 
     def run(mode, steps):
         sim = L.Simulation(boxes, parts, max_semi=ms, device=device)
         if mode != "cold":
-            warm_start(sim, 0, net, use_net=(mode == "warm"), use_fluid=True)
+            warm_start(sim, 0, net, use_net=mode.startswith("warm"), use_fluid=True,
+                       use_stress=(mode != "warm_no_stress"))
         h = velocity_history(sim, 0, steps, every)
         sim.close()
         return h
@@ -286,11 +292,14 @@ def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int =
     tols = (1e-2, 3e-3, 1e-3)
     res = {f"cold@{t:g}": steps_to_steady(ref, U_ss, every, t) for t in tols}
     curves = {"cold": velocity_error(ref, U_ss)}
-    for mode in ("stokes_fluid_only", "warm"):
+    modes = ("stokes_fluid_only", "warm") + (("warm_no_stress",) if eval_tau != 1.0 else ())
+    end_vs_ref = {}
+    for mode in modes:
         h = run(mode, ref_steps // 2)
         for t in tols:
             res[f"{mode}@{t:g}"] = steps_to_steady(h, U_ss, every, t)
         curves[mode] = velocity_error(h, U_ss)
+        end_vs_ref[mode] = float(curves[mode][-1])
     pick = lambda c: {int((i + 1) * every): float(c[i]) for i in range(0, len(c), max(1, len(c) // 40))}
     t_eval = time.time() - t2
     return {"samples": len(samples), "augmented": int(len(Gt)), "train_loss": train_loss,
@@ -298,7 +307,8 @@ def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int =
             "steps_to_steady": res,
             "gain_warm_vs_cold": {f"{t:g}": (res[f"cold@{t:g}"] / res[f"warm@{t:g}"])
                                   if res[f"cold@{t:g}"] and res[f"warm@{t:g}"] else None for t in tols},
-            "reference_drift_last_500_steps": drift, "eval": f"{eval_n}^3, {eval_count} spheroids, |F|={force}",
+            "reference_drift_last_500_steps": drift, "end_of_warm_runs_vs_reference": end_vs_ref,
+            "eval": f"{eval_n}^3, {eval_count} spheroids, |F|={force}, tau={eval_tau}",
             "error_curves": {k: pick(v) for k, v in curves.items()},
             "seconds": {"data": t_data, "train": t_train, "eval": t_eval}}
 

@@ -1,6 +1,7 @@
-"""Parity of the warm-start entry points (lb_stokes_field, lb_init_fluid,
-lb_mlp_features, lb_resistance_targets, lb_warm_velocities), called through
-the C ABI, with the FP64 reference oracle/warmstart.py and the FP64 LB oracle.
+"""Parity of the warm-start entry points (lb_stokes_field, lb_init_fluid with
+and without the stress part, lb_mlp_features, lb_resistance_targets,
+lb_warm_velocities), called through the C ABI, with the FP64 reference
+oracle/warmstart.py and the FP64 LB oracle.
 
 Bars: the Stokes flow within 1e-4 normwise (FP32 DFTs of length <= 40 against
 numpy's FP64 FFT: each pass adds a few FP32 roundings per term); a run started
@@ -66,7 +67,7 @@ def test_run_from_initial_fluid_matches_oracle():
     b, parts = _case()
     sim = _sim(b, parts)
     ud, dd = _gpu_stokes(sim, b)
-    L.lb_init_fluid(sim.ctx, 0, ud.data_ptr(), ud.numel() * 4, dd.data_ptr(), True)
+    L.lb_init_fluid(sim.ctx, 0, ud.data_ptr(), ud.numel() * 4, dd.data_ptr(), True, False)
     u = ud.cpu().numpy().astype(np.float64).reshape(3, b["nz"], b["ny"], b["nx"])
     d = dd.cpu().numpy().astype(np.float64).reshape(b["nz"], b["ny"], b["nx"])
     o = O.Sim(b, parts, nthreads=8)
@@ -116,3 +117,37 @@ def test_features_targets_and_velocities_match_reference():
     assert normwise(Rh.cpu().numpy().reshape(n, 6, 6), Rref) <= 2e-6
     Rf = Rh.cpu().numpy().astype(np.float64)
     assert normwise(UW.cpu().numpy(), W.warm_velocities(Rf, geom, FT)) <= 1e-10
+
+
+def test_run_from_initial_fluid_with_stress_matches_oracle():
+    """lb_init_fluid with the non-equilibrium stress part (tau = 0.9, where the
+    collision keeps part of it): the stored start equals the oracle's f_eq +
+    stress_f, and a run from it follows the oracle's run from the same start."""
+    b, parts = _case()
+    sim = _sim(b, parts)
+    ud, dd = _gpu_stokes(sim, b)
+    L.lb_init_fluid(sim.ctx, 0, ud.data_ptr(), ud.numel() * 4, dd.data_ptr(), True, True)
+    u = ud.cpu().numpy().astype(np.float64).reshape(3, b["nz"], b["ny"], b["nx"])
+    d = dd.cpu().numpy().astype(np.float64).reshape(b["nz"], b["ny"], b["nx"])
+    o = O.Sim(b, parts, nthreads=8)
+    co, wo = O.lattice()
+    f = o.f()
+    fluid = o.owner() == 0
+    rho = b["rho0"] + d
+    start = W.equilibrium_f(u, rho, co, wo) + W.stress_f(u, rho, b["tau"], co, wo)
+    f[fluid] = start[fluid]
+    o.set_f(f)
+    assert normwise(sim.field("df"), oracle_df_gpu_layout(o, b["rho0"])) <= 1e-6
+    # the stress part is a visible share of the start
+    plain = W.equilibrium_f(u, rho, co, wo)
+    share = np.abs(start - plain)[fluid].max() / np.abs(plain - wo * b["rho0"])[fluid].max()
+    assert share > 1e-2
+    worst = {"df": 0.0, "F": 0.0}
+    for _ in range(8):
+        sim.step(5)
+        o.step(5)
+        worst["df"] = max(worst["df"], normwise(sim.field("df"), oracle_df_gpu_layout(o, b["rho0"])))
+        for p in range(2):
+            worst["F"] = max(worst["F"], normwise(sim.particle(0, p)["F"], o.particle(p)["F"]))
+    print("stress warm-start parity", worst, "stress share", share)
+    assert worst["df"] <= 1e-5 and worst["F"] <= 1e-5
