@@ -164,6 +164,34 @@ lb_status lb_get_fields(lb_ctx* ctx, int32_t box, uint32_t what, void* dst, size
  * context's work on `stream` (NULL = its own stream). */
 lb_status lb_get_force_torque(lb_ctx* ctx, int32_t box, double* out, int32_t n);
 
+/* Like lb_get_force_torque, but only enqueues the copy of the records on
+ * `stream` (NULL = the context's stream), behind the work already queued there
+ * and behind the last lb_step, and returns at once.  out (n * LB_RECORD_DOUBLES
+ * doubles) must be pinned host memory or device memory and stay valid; it holds
+ * the records once the stream (or lb_synchronize) has been waited for.  Meant
+ * for pipelined loops that queue inputs, steps and record copies for many
+ * steps and wait once.  Not part of the paper.
+ * Errors: LB_EINVAL (bad box, buffer or count), LB_ECUDA; device errors of the
+ * steps surface at the next call that waits. */
+lb_status lb_get_force_torque_async(lb_ctx* ctx, int32_t box, double* out, int32_t n, void* stream);
+
+/* nsteps iterations with per-step input and output, queued on `stream` by the
+ * library (one call instead of three per step): before iteration k the
+ * external forces and torques of all particles come from ft + k*np*6 (the
+ * layout of lb_set_external over all boxes; ft may be NULL: unchanged), after it
+ * all particle records go to rec + k*np*LB_RECORD_DOUBLES (the layout of
+ * lb_get_force_torque over all boxes; rec may be NULL: not copied).  np is the
+ * total number of particles.  ft and rec stay valid until the stream has been
+ * waited for; returns without waiting.  When the GPU can address them
+ * (page-locked host memory, reached over the coherent CPU-GPU link of a Grace
+ * system, or device or managed memory) the persistent step kernel reads each
+ * step's forces and writes each step's records itself, so a long run records
+ * its whole trajectory (forces, torques, velocities, poses of every step) at
+ * the speed of lb_step; pageable memory falls back to three queued copies and
+ * launches per step.  Not part of the paper.
+ * Errors: those of lb_step, lb_set_external and lb_get_force_torque_async. */
+lb_status lb_step_io(lb_ctx* ctx, int32_t nsteps, const double* ft, double* rec, void* stream);
+
 /* Boundary links (x fluid, x + c_b solid) of particle `particle` of box `box`
  * at the current time, compacted on the device: pairs[2k] = node index
  * (z*ny + y)*nx + x of the fluid node, pairs[2k+1] = direction index b in the

@@ -29,7 +29,7 @@ cudaError_t launch_particles(const PParams& p, cudaStream_t s);
 cudaError_t launch_particles_aux(const PParams& p, cudaStream_t s);
 cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const PParams part[2], unsigned* sync,
                         unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, int fetch,
-                        cudaStream_t s);
+                        const double* io_ft, double* io_rec, cudaStream_t s);
 cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
                          int cap, int* count, cudaStream_t s);
 cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const float* drho,
@@ -551,8 +551,11 @@ static cudaError_t enqueue_iteration(lb_ctx* ctx, int first, int cur, cudaStream
     return launch_particles_aux(pp, s);
 }
 
-// k iterations in one launch of the step kernel, starting at buffer parity cur
-static cudaError_t enqueue_steps(lb_ctx* ctx, int k, int cur, cudaStream_t s)
+// k iterations in one launch of the step kernel, starting at buffer parity cur;
+// io_ft / io_rec (device-accessible, or null): per-iteration external forces
+// in and particle records out
+static cudaError_t enqueue_steps(lb_ctx* ctx, int k, int cur, cudaStream_t s, const double* io_ft = nullptr,
+                                 double* io_rec = nullptr)
 {
     BulkParams bulk[2];
     BndParams bnd[2];
@@ -565,7 +568,7 @@ static cudaError_t enqueue_steps(lb_ctx* ctx, int k, int cur, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(ctx->d_sync, 0, sizeof(unsigned) * (4 + (size_t)ctx->np), s);
     if (e != cudaSuccess) return e;
     return launch_step(bulk, bnd, part, ctx->d_sync, ctx->d_status, ctx->np, ctx->gx, ctx->total_blocks, k, cur,
-                       ctx->opt.precision, ctx->fetch, s);
+                       ctx->opt.precision, ctx->fetch, io_ft, io_rec, s);
 }
 
 extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
@@ -715,6 +718,85 @@ extern "C" lb_status lb_get_force_torque(lb_ctx* ctx, int32_t box, double* out, 
     CK(cudaMemcpyAsync(out, ctx->d_rec, sizeof(double) * LB_RECORD_DOUBLES * n, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return read_status(ctx);
+}
+
+extern "C" lb_status lb_get_force_torque_async(lb_ctx* ctx, int32_t box, double* out, int32_t n, void* stream)
+{
+    if (!ctx) return LB_EINVAL;
+    const bool all = box == -1;
+    if ((!all && (box < 0 || box >= (int)ctx->desc.size())) || !out ||
+        n != (all ? ctx->np : (int)ctx->parts[box].size()))
+        return fail(ctx, LB_EINVAL, "bad box, buffer or count");
+    if (n == 0) return LB_OK;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick(ctx, stream);
+    CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
+    const int pbeg = all ? 0 : ctx->hbox[box].pbeg;
+    // one strided copy straight out of the particle states
+    CK(cudaMemcpy2DAsync(out, sizeof(double) * LB_RECORD_DOUBLES, &ctx->d_pd[pbeg].rec[0], sizeof(PartDev),
+                         sizeof(double) * LB_RECORD_DOUBLES, n, cudaMemcpyDefault, s));
+    return LB_OK;
+}
+
+// Device address of caller memory of `bytes` bytes that the GPU of the
+// context can read and write directly: its own device memory, managed memory,
+// or page-locked host memory (through its mapped address; both ends of the
+// range must lie in the same mapping).  Null when it cannot (pageable host
+// memory, another GPU), and the caller then copies instead.
+static void* device_view(lb_ctx* ctx, const void* p, size_t bytes)
+{
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a, b;
+    const char* last = static_cast<const char*>(p) + bytes - 1;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != b.type || !a.devicePointer || !b.devicePointer) return nullptr;
+    if (static_cast<const char*>(b.devicePointer) - static_cast<const char*>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
+        return nullptr;
+    if (a.type == cudaMemoryTypeDevice && a.device != ctx->device) return nullptr;
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged && a.type != cudaMemoryTypeHost) return nullptr;
+    return a.devicePointer;
+}
+
+extern "C" lb_status lb_step_io(lb_ctx* ctx, int32_t nsteps, const double* ft, double* rec, void* stream)
+{
+    if (!ctx) return LB_EINVAL;
+    if (nsteps < 0) return fail(ctx, LB_EINVAL, "negative step count");
+    if (nsteps == 0) return LB_OK;
+    const size_t np = (size_t)ctx->np;
+    if (np == 0 || (!ft && !rec)) return lb_step(ctx, nsteps, stream);
+    CK(cudaSetDevice(ctx->device));
+    const double* dft = static_cast<const double*>(device_view(ctx, ft, sizeof(double) * 6 * np * nsteps));
+    double* drec = static_cast<double*>(device_view(ctx, rec, sizeof(double) * RECD * np * nsteps));
+    // the step kernel reads F_ext / T_ext and writes the records itself when
+    // the GPU can reach the caller's memory (on GB300, page-locked host memory
+    // over the coherent CPU-GPU link); otherwise, and for the first collision
+    // and in the separate-kernel mode, three queued calls per step
+    const bool direct = !(ctx->opt.flags & LB_FLAG_SEPARATE_KERNELS) && (!ft || dft) && (!rec || drec);
+    int k = 0;
+    while (k < nsteps && (!direct || !ctx->collided)) {
+        lb_status r;
+        if (ft && (r = lb_set_external(ctx, -1, ft + k * np * 6, ctx->np, stream)) != LB_OK) return r;
+        if ((r = lb_step(ctx, 1, stream)) != LB_OK) return r;
+        if (rec && (r = lb_get_force_torque_async(ctx, -1, rec + k * np * RECD, ctx->np, stream)) != LB_OK) return r;
+        ++k;
+    }
+    if (k == nsteps) return LB_OK;
+    clear_stale_error();
+    cudaStream_t s = pick(ctx, stream);
+    if (ctx->last_user_stream && ctx->last_user_stream != s) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
+    ctx->last_user_stream = s;
+    ctx->stepped = true;
+    while (k < nsteps) {
+        const int c = nsteps - k < STEP_ITERS ? nsteps - k : STEP_ITERS;
+        CK(enqueue_steps(ctx, c, ctx->cur, s, dft ? dft + k * np * 6 : nullptr, drec ? drec + k * np * RECD : nullptr));
+        ctx->cur ^= (c & 1);
+        k += c;
+    }
+    CK(cudaEventRecord(ctx->ev_done, s));
+    return LB_OK;
 }
 
 extern "C" lb_status lb_get_drag(lb_ctx* ctx, int32_t box, int32_t particle, double* out36)

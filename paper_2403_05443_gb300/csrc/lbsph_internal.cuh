@@ -46,6 +46,7 @@ namespace lbsph {
 
 constexpr int Q = 19;
 constexpr int MAXS = 64;            // largest bounding-cube side (one 64-bit word per row)
+constexpr int RECD = 25;            // doubles per particle record (LB_RECORD_DOUBLES of the C ABI)
 constexpr int KBLOCK = 256;         // threads per block of the lattice kernel
 constexpr int PBLOCK = 512;         // threads per block of the links read-back kernels
 constexpr int ABLOCK = 256;         // threads per block of the auxiliary particle kernel
@@ -212,7 +213,7 @@ struct PartDev {
     int o_prev[3];                  // cube origin of map t-1
     int S, h, box, slot;            // slot: ring slot holding map t
     long long step;
-    double rec[25];                 // F0, T0, F, T, U, Omega, x, q of the last iteration
+    double rec[RECD];               // F0, T0, F, T, U, Omega, x, q of the last iteration
     int nsolid, pad;
 };
 

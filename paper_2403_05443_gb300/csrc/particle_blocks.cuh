@@ -96,7 +96,12 @@ __device__ inline void canon_shape_warp(const double inv[3], const double q[4], 
 
 // ---------------------------------------------------------------------------
 // particle p; CBLOCK threads
-__device__ __forceinline__ void crit_block(const PParams& P, int p)
+// io_ft (6 doubles: F_ext, T_ext) replaces the particle's external force and
+// torque for this step and from then on; io_rec (25 doubles) receives its
+// record after the step.  Either may be null.  Both may be pinned host memory
+// that the GPU reads and writes directly.
+__device__ __forceinline__ void crit_block(const PParams& P, int p, const double* io_ft = nullptr,
+                                           double* io_rec = nullptr)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ PartDev S;
@@ -127,6 +132,11 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p)
         if (tid == 0) { s_nsolid = 0; s_namb = 0; s_dm = 0.0; }
     }
     __syncthreads();
+    if (io_ft) {
+        if (tid < 3) S.Fext[tid] = io_ft[tid];
+        else if (tid < 6) S.Text[tid - 3] = io_ft[tid];
+        __syncthreads();
+    }
     const int slot_new = P.init ? 0 : (S.slot ^ 1);
     uint64_t* s_rows = s_maps + slot_new * P.smax * P.smax;          // map t+1, built below
     const uint64_t* s_old = s_maps + (P.init ? slot_new : S.slot) * P.smax * P.smax;   // map t
@@ -434,6 +444,8 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p)
         const unsigned* ks = reinterpret_cast<const unsigned*>(&K);
         unsigned* kd = reinterpret_cast<unsigned*>(P.pk + p);
         for (int e = tid; e < (int)(sizeof(PartK) / 4); e += CBLOCK) kd[e] = ks[e];
+        if (io_rec)
+            for (int e = tid; e < RECD; e += CBLOCK) io_rec[e] = S.rec[e];
     }
     // ---- the box's uniform terms of the next collision: body force with the
     // counter force over the fluid nodes, and the mass put back

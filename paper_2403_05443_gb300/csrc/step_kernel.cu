@@ -46,6 +46,8 @@ struct StepParams {
     unsigned* status;
     int np, gx, tiles, iters, cur0;
     int fetch;                       // bulk units per counter fetch (1, 2, 4, 8)
+    const double* io_ft;             // per iteration np * 6 doubles of F_ext, T_ext (or null)
+    double* io_rec;                  // per iteration np * RECD doubles of records (or null)
 };
 
 __device__ __forceinline__ bool grid_barrier(const StepParams& SP)
@@ -123,7 +125,8 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
             if (s_last) {
                 __threadfence();
                 if (tid == 0) SP.sync[SYNC_PART + p] = 0;
-                crit_block(PP, p);
+                const size_t io = (size_t)it * SP.np + p;
+                crit_block(PP, p, SP.io_ft ? SP.io_ft + io * 6 : nullptr, SP.io_rec ? SP.io_rec + io * RECD : nullptr);
             }
             __syncthreads();
         }
@@ -181,9 +184,11 @@ static cudaError_t launch_step_t(const StepParams& sp, size_t smem, cudaStream_t
 
 cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const PParams part[2], unsigned* sync,
                         unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, int fetch,
-                        cudaStream_t s)
+                        const double* io_ft, double* io_rec, cudaStream_t s)
 {
     StepParams sp;
+    sp.io_ft = io_ft;
+    sp.io_rec = io_rec;
     for (int c = 0; c < 2; ++c) { sp.bulk[c] = bulk[c]; sp.bnd[c] = bnd[c]; sp.part[c] = part[c]; }
     sp.sync = sync; sp.status = status;
     sp.np = np; sp.gx = gx; sp.fetch = fetch < 1 ? 1 : fetch; sp.tiles = tiles; sp.iters = iters; sp.cur0 = cur0;

@@ -75,6 +75,8 @@ def library(path: str | None = None):
     L.lb_step.argtypes = [vp, i32, vp]
     L.lb_get_fields.argtypes = [vp, i32, u32, vp, C.c_size_t, i32, vp]
     L.lb_get_force_torque.argtypes = [vp, i32, dp, i32]
+    L.lb_get_force_torque_async.argtypes = [vp, i32, vp, i32, vp]
+    L.lb_step_io.argtypes = [vp, i32, vp, vp, vp]
     L.lb_get_links.argtypes = [vp, i32, i32, ip, i32, ip]
     L.lb_get_drag.argtypes = [vp, i32, i32, dp]
     L.lb_synchronize.argtypes = [vp]
@@ -92,7 +94,8 @@ def library(path: str | None = None):
     L.lb_last_error.restype = C.c_char_p
     L.lb_abi_version.restype = i32
     for name in ("lb_create", "lb_destroy", "lb_set_particles", "lb_set_external", "lb_step",
-                 "lb_get_fields", "lb_get_force_torque", "lb_get_links", "lb_get_drag", "lb_synchronize",
+                 "lb_get_fields", "lb_get_force_torque", "lb_get_force_torque_async", "lb_get_links", "lb_get_drag",
+                 "lb_synchronize", "lb_step_io",
                  "lb_profile_step", "lb_init_fluid", "lb_stokes_field", "lb_autotune"):
         getattr(L, name).restype = i32
     _lib = L
@@ -188,6 +191,21 @@ def lb_get_force_torque(ctx, box: int, n: int, out: np.ndarray | None = None) ->
         out = np.zeros((max(n, 1), LB_RECORD_DOUBLES))
     _check(library().lb_get_force_torque(ctx, box, out.ctypes.data_as(C.POINTER(C.c_double)), n), ctx)
     return out.reshape(-1, LB_RECORD_DOUBLES)[:n]
+
+
+def lb_get_force_torque_async(ctx, box: int, n: int, out_ptr: int, stream=None):
+    """Enqueue the copy of the n particle records of `box` (-1: all boxes) to
+    out_ptr (pinned host or device memory, n*25 float64) on `stream`; returns
+    at once, the data are there once the stream has been waited for."""
+    _check(library().lb_get_force_torque_async(ctx, box, C.c_void_p(out_ptr), n, stream), ctx)
+
+
+def lb_step_io(ctx, nsteps: int, ft_ptr, rec_ptr, stream=None):
+    """nsteps iterations, each with its F_ext/T_ext from ft_ptr + k*np*6 and its
+    records copied to rec_ptr + k*np*25 (float64; pinned host or device
+    addresses, either may be None); queued on `stream`, returns at once."""
+    _check(library().lb_step_io(ctx, int(nsteps), None if ft_ptr is None else C.c_void_p(ft_ptr),
+                                None if rec_ptr is None else C.c_void_p(rec_ptr), stream), ctx)
 
 
 def lb_profile_step(ctx, nsteps: int, stream=None):

@@ -217,3 +217,59 @@ def test_autotune_keeps_results_bitwise_and_picks_a_candidate():
     for bi in range(2):
         assert np.array_equal(a.field("df", bi), b.field("df", bi))
         assert np.array_equal(a.records(bi), b.records(bi))
+
+
+def test_async_record_copies_match_synchronous_reads():
+    """A pipelined loop (each step's F_ext from its own pinned slot, each step's
+    records copied into their own pinned slot by lb_get_force_torque_async, one
+    wait at the end), and lb_step_io doing the same in one call, give the
+    records a synchronous loop reads step by step."""
+    torch = pytest.importorskip("torch")
+    boxes, parts = single_32(seed=6)
+    K = 12
+    ft = torch.empty((K, 1, 6), dtype=torch.float64, pin_memory=True)
+    for k in range(K):
+        ft[k, 0] = torch.tensor([1e-4 * (1 + 0.1 * k), -2e-5 * k, 0.0, 0.0, 1e-6 * k, 0.0], dtype=torch.float64)
+    recs = torch.empty((K, 1, L.LB_RECORD_DOUBLES), dtype=torch.float64, pin_memory=True)
+    a = _sim(boxes, parts)
+    b = _sim(boxes, parts)
+    a.step(3)
+    b.step(3)
+    ftn = ft.numpy()
+    for k in range(K):
+        L.lb_set_external(a.ctx, -1, ftn[k])
+        a.step(1)
+        L.lb_get_force_torque_async(a.ctx, -1, 1, recs[k].data_ptr())
+    L.lb_synchronize(a.ctx)
+    for k in range(K):
+        L.lb_set_external(b.ctx, -1, ftn[k])
+        b.step(1)
+        assert np.array_equal(recs[k].numpy(), b.records())
+    # the inputs of every step took effect (F_ext enters the records' force)
+    assert not np.array_equal(recs[0].numpy(), recs[-1].numpy())
+    # the same loop queued by the library in one call
+    c = _sim(boxes, parts)
+    c.step(3)
+    recs_io = torch.empty_like(recs)
+    L.lb_step_io(c.ctx, K, ft.data_ptr(), recs_io.data_ptr())
+    L.lb_synchronize(c.ctx)
+    assert np.array_equal(recs_io.numpy(), recs.numpy())
+    assert np.array_equal(c.records(), recs[-1].numpy())
+    # pageable host memory: the per-step copy path, same records
+    d = _sim(boxes, parts)
+    d.step(3)
+    ft_pageable = np.array(ft.numpy())
+    recs_pageable = np.zeros(recs.shape)
+    L.lb_step_io(d.ctx, K, ft_pageable.ctypes.data, recs_pageable.ctypes.data)
+    L.lb_synchronize(d.ctx)
+    assert np.array_equal(recs_pageable, recs.numpy())
+    # from the very first step (the first collision runs as separate kernels)
+    e = _sim(boxes, parts)
+    f = _sim(boxes, parts)
+    recs_first = torch.empty_like(recs)
+    L.lb_step_io(e.ctx, K, ft.data_ptr(), recs_first.data_ptr())
+    L.lb_synchronize(e.ctx)
+    for k in range(K):
+        L.lb_set_external(f.ctx, -1, ftn[k])
+        f.step(1)
+        assert np.array_equal(recs_first[k].numpy(), f.records())
