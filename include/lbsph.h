@@ -146,7 +146,12 @@ lb_status lb_set_external(lb_ctx* ctx, int32_t box, const double* ft, int32_t n,
  * Asynchronous on `stream` (a cudaStream_t, NULL = the context's stream).
  * After the first collision the steps run in a persistent cooperative kernel
  * that occupies every SM, up to 256 iterations per launch; its grid barriers
- * give up after about two seconds and then report LB_ECUDA. */
+ * give up after about two seconds and then report LB_ECUDA.  On a stream that
+ * is being captured into a CUDA graph the launches are recorded instead of run:
+ * after the first step, a graph of an even number of steps (the two
+ * distribution buffers return to the same parity) can be replayed any number of
+ * times to continue the run; wait for the replays (e.g. lb_synchronize) before
+ * the getters. */
 lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream);
 
 /* Writes the fields `what` (one LB_FIELD_* bit) of box `box` at the current

@@ -571,6 +571,20 @@ static cudaError_t enqueue_steps(lb_ctx* ctx, int k, int cur, cudaStream_t s, co
                        ctx->opt.precision, ctx->fetch, io_ft, io_rec, s);
 }
 
+// A stream that is being captured into a CUDA graph: its work is recorded,
+// not run, so the context's completion event is neither waited on nor
+// recorded there (an event recorded inside a capture cannot be waited on
+// outside it).
+static bool capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
 {
     if (!ctx) return LB_EINVAL;
@@ -579,7 +593,8 @@ extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
     CK(cudaSetDevice(ctx->device));
     clear_stale_error();
     cudaStream_t s = pick(ctx, stream);
-    if (ctx->last_user_stream && ctx->last_user_stream != s) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
+    const bool cap = capturing(s);
+    if (!cap && ctx->last_user_stream && ctx->last_user_stream != s) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     ctx->last_user_stream = s;
     ctx->stepped = true;
     int left = nsteps;
@@ -602,7 +617,7 @@ extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
             left -= k;
         }
     }
-    CK(cudaEventRecord(ctx->ev_done, s));
+    if (!cap) CK(cudaEventRecord(ctx->ev_done, s));
     return LB_OK;
 }
 
@@ -730,7 +745,7 @@ extern "C" lb_status lb_get_force_torque_async(lb_ctx* ctx, int32_t box, double*
     if (n == 0) return LB_OK;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = pick(ctx, stream);
-    CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
+    if (!capturing(s)) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     const int pbeg = all ? 0 : ctx->hbox[box].pbeg;
     // one strided copy straight out of the particle states
     CK(cudaMemcpy2DAsync(out, sizeof(double) * LB_RECORD_DOUBLES, &ctx->d_pd[pbeg].rec[0], sizeof(PartDev),
@@ -786,7 +801,8 @@ extern "C" lb_status lb_step_io(lb_ctx* ctx, int32_t nsteps, const double* ft, d
     if (k == nsteps) return LB_OK;
     clear_stale_error();
     cudaStream_t s = pick(ctx, stream);
-    if (ctx->last_user_stream && ctx->last_user_stream != s) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
+    const bool cap = capturing(s);
+    if (!cap && ctx->last_user_stream && ctx->last_user_stream != s) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     ctx->last_user_stream = s;
     ctx->stepped = true;
     while (k < nsteps) {
@@ -795,7 +811,7 @@ extern "C" lb_status lb_step_io(lb_ctx* ctx, int32_t nsteps, const double* ft, d
         ctx->cur ^= (c & 1);
         k += c;
     }
-    CK(cudaEventRecord(ctx->ev_done, s));
+    if (!cap) CK(cudaEventRecord(ctx->ev_done, s));
     return LB_OK;
 }
 

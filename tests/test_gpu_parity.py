@@ -306,6 +306,21 @@ def test_async_record_copies_match_synchronous_reads():
     L.lb_step_io(d.ctx, K, ft_pageable.ctypes.data, recs_pageable.ctypes.data)
     L.lb_synchronize(d.ctx)
     assert np.array_equal(recs_pageable, recs.numpy())
+    # device memory: the step kernel reads and writes it directly as well
+    g = _sim(boxes, parts)
+    g.step(3)
+    ft_dev, recs_dev = ft.cuda(), torch.zeros(recs.shape, dtype=torch.float64, device="cuda")
+    L.lb_step_io(g.ctx, K, ft_dev.data_ptr(), recs_dev.data_ptr())
+    L.lb_synchronize(g.ctx)
+    assert np.array_equal(recs_dev.cpu().numpy(), recs.numpy())
+    # forces only, records only
+    h = _sim(boxes, parts)
+    h.step(3)
+    L.lb_step_io(h.ctx, K, ft.data_ptr(), None)
+    L.lb_synchronize(h.ctx)
+    assert np.array_equal(h.records(), recs[-1].numpy())
+    with pytest.raises(L.LBError):
+        L.lb_step_io(h.ctx, -1, None, None)
     # from the very first step (the first collision runs as separate kernels)
     e = _sim(boxes, parts)
     f = _sim(boxes, parts)
@@ -316,3 +331,29 @@ def test_async_record_copies_match_synchronous_reads():
         L.lb_set_external(f.ctx, -1, ftn[k])
         f.step(1)
         assert np.array_equal(recs_first[k].numpy(), f.records())
+
+
+def test_steps_capture_into_a_cuda_graph_and_replay():
+    """lb_step on a capturing stream records the persistent step kernel (and its
+    counter reset) into a CUDA graph; replaying a graph of an even number of
+    steps (the two distribution buffers come back to the same parity) continues
+    the run exactly as direct calls do."""
+    torch = pytest.importorskip("torch")
+    boxes, parts = single_32(seed=7)
+    s = torch.cuda.Stream()
+    sp = L.stream_handle(s)
+    a = _sim(boxes, parts)
+    b = _sim(boxes, parts)
+    a.step(2, stream=sp)
+    b.step(2, stream=sp)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        L.lb_step(a.ctx, 8, sp)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    b.step(24, stream=sp)
+    L.lb_synchronize(b.ctx)
+    assert np.array_equal(a.records(), b.records())
+    assert np.array_equal(a.field("df"), b.field("df"))
