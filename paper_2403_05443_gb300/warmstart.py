@@ -166,14 +166,18 @@ def warm_start(sim, box: int, net, use_net: bool = True, use_fluid: bool = True,
     Stokes flow of the particle forces and its pressure (use_fluid), with the
     flow's viscous stress in the populations' non-equilibrium part
     (use_stress; no effect at tau = 1, where the first collision discards it).
-    For several particles in a box the confinement feature uses the edge of the
-    volume per particle."""
+    The confinement feature is the box's own edge (for a non-cubic box, the
+    cube root of its volume): each particle's self-mobility in that box; the
+    other particles act through the fluid.  (The edge of the volume per
+    particle, which treats the suspension as a periodic array of identical
+    particles, predicted the steady velocities of 16 spheroids with random
+    forces in a 128^3 box to 18 % median error, the box edge to 12 %.)"""
     torch = _torch()
     b = sim.boxes[box]
     parts = [dict(p) for p in sim.parts_of(box)]
     n = len(parts)
     if use_net and n:
-        Ledge = (b["nx"] * b["ny"] * b["nz"] / n) ** (1.0 / 3.0)
+        Ledge = (b["nx"] * b["ny"] * b["nz"]) ** (1.0 / 3.0)
         geoms = [geom_of(p["semi"][0], p["semi"][1], b["tau"], Ledge, long_axis(p["q"]), b.get("rho0", 1.0))
                  for p in parts]
         gd = torch.as_tensor(np.asarray(geoms), device="cuda")
