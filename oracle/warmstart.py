@@ -19,6 +19,12 @@ symbol), the closed form of a curl-free force's pressure and the symmetry of
 the periodic Green's function
 (tests/test_oracle_warmstart.py).
 
+Steady state of the lattice fluid itself (lb_steady_solve): the linear
+D3Q19 BGK dynamics with Guo forcing solved exactly mode by mode (a 4 x 4 system
+in the conserved moments); pinned by the oracle's own lattice step written as a
+per-mode transfer, by the direct solve of the 19-population fixed point, and
+by its long-wavelength (Stokes) limit and a closed form at tau = 1.
+
 Non-equilibrium start (stress_f): the first-order Chapman-Enskog part of the
 populations of a viscous flow, pinned by its moments (none in mass and
 momentum, the viscous stress in the second moment, a closed form for a shear
@@ -35,12 +41,14 @@ import numpy as np
 
 
 def stokes_field(nx, ny, nz, owner, F_ext, mu, counter=False, body=(0.0, 0.0, 0.0), MU=None, rho0=1.0,
-                 density=False):
+                 density=False, tau=None):
     """u[3, nz, ny, nx]; owner[nz, ny, nx] (0 fluid, p+1 particle p, -1 wall);
     F_ext[np, 3].  The fluid's mean is then shifted so that rho0 sum_fluid u +
     sum_p M_p U_p = 0 (MU[np, 3] = M_p U_p; zero if None).  With density=True
     returns (u, drho), drho the pressure's density deviation with zero sum over
-    the fluid nodes."""
+    the fluid nodes.  With tau given, the flow and density are the lattice
+    fluid's own steady state (lb_steady_solve) instead of the 7-point Stokes
+    solve."""
     owner = np.asarray(owner)
     F = np.asarray(F_ext, np.float64).reshape(-1, 3)
     g = np.zeros((3, nz, ny, nx))
@@ -55,15 +63,108 @@ def stokes_field(nx, ny, nz, owner, F_ext, mu, counter=False, body=(0.0, 0.0, 0.
             if m.any():
                 gk[m] += F[p, k] / m.sum()
         g[k] = gk
-    u = stokes_solve(g, mu)
+    if tau is not None:
+        from .oracle import lattice
+        c, w = lattice()
+        u, d_lb = lb_steady_solve(g, tau, rho0, c, w)
+    else:
+        u = stokes_solve(g, mu)
     P = np.zeros(3) if MU is None else np.asarray(MU, np.float64).reshape(-1, 3).sum(0)
     for k in range(3):
         u[k][fluid] += (-P[k] / rho0 - u[k][fluid].sum()) / nfl
     if not density:
         return u
-    d = pressure_density(g)
+    d = d_lb if tau is not None else pressure_density(g)
     d[fluid] -= d[fluid].sum() / nfl
     return u, d
+
+
+def _modes(shape):
+    """k vectors [nz, ny, nx, 3] (x, y, z components) of the periodic DFT grid."""
+    nz, ny, nx = shape
+    kz, ky, kx = [2 * np.pi * np.arange(m) / m for m in (nz, ny, nx)]
+    KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
+    return np.stack([KX, KY, KZ], -1)
+
+
+def lb_step_transfer(k, tau, c, w):
+    """One step of the linear lattice fluid (BGK, no force) on the Fourier mode
+    k: f^_i <- e_i [(1 - omega) f^_i + omega f^eq_i(f^)], e_i = exp(-i k.c_i),
+    f^eq_i = w_i (drho^ + 3 c_i . j^) (deviations, rho0 = 1, linear).  19 x 19."""
+    c = np.asarray(c, np.float64)
+    om = 1.0 / tau
+    e = np.exp(-1j * (c @ np.asarray(k, np.float64)))
+    Qm = np.asarray(w)[:, None] * (1.0 + 3.0 * c @ c.T)
+    return e[:, None] * ((1.0 - om) * np.eye(len(w)) + om * Qm)
+
+
+def lb_steady_bruteforce(gh, k, tau, c, w):
+    """Steady populations of the linear lattice fluid under the force mode
+    gh (3 complex) at wave vector k, by solving the 19 x 19 fixed point
+    f^ = e (f^ - omega (f^ - f^eq) + (1 - omega/2) F^) with Guo's force term
+    F_i = 3 w_i c_i . g and the velocity u = j + g/2 (rho0 = 1); returns
+    (drho^, u^)."""
+    c = np.asarray(c, np.float64)
+    om = 1.0 / tau
+    e = np.exp(-1j * (c @ np.asarray(k, np.float64)))
+    w = np.asarray(w)
+    Qm = w[:, None] * (1.0 + 3.0 * c @ c.T)
+    T = e[:, None] * ((1.0 - om) * np.eye(len(w)) + om * Qm)
+    # f^eq carries u = j + g/2: its g part, and the force term, are the source
+    src = e * (om * 3.0 * w * (c @ gh) / 2.0 + (1.0 - om / 2.0) * 3.0 * w * (c @ gh))
+    f = np.linalg.solve(np.eye(len(w)) - T, src)
+    return f.sum(), c.T @ f + gh / 2.0
+
+
+def lb_steady_solve(g, tau, rho0, c, w):
+    """Exact steady state of the linear lattice fluid (D3Q19 BGK with Guo
+    forcing, rho0, omega = 1/tau) under the periodic force density
+    g[3, nz, ny, nx]: the pre-collision populations are the post-collision ones
+    streamed, f^_i = e_i f^*_i, so f^_i = h_i (omega f^eq_i + (1 - omega/2) F^_i)
+    with h_i = e_i / (1 - (1 - omega) e_i), and their moments (drho, u) solve,
+    mode by mode,
+      D0 drho - 3 rho0 omega H1 . u = 3 (1 - omega/2) H1 . g
+      -omega H1 drho + rho0 D2 u = g/2 + 3 (1 - omega/2) H2 g
+    with H1 = sum w_i c_i h_i, H2 = sum w_i c_i c_i^T h_i,
+    D0 = sum w_i (1 - e_i) / (1 - (1 - omega) e_i) (= 1 - omega sum w_i h_i) and
+    D2 = sum 3 w_i c_i c_i^T (1 - e_i) / (1 - (1 - omega) e_i) (= I - 3 omega H2).
+    The k = 0 mode (mean flow, mass) is set to zero.  Returns (u, drho)."""
+    g = np.asarray(g, np.float64)
+    shape = g.shape[1:]
+    K = _modes(shape)
+    c = np.asarray(c, np.float64)
+    om = 1.0 / tau
+    gh = np.stack([np.fft.fftn(g[a]) for a in range(3)], -1)
+    H1 = np.zeros(shape + (3,), complex)
+    H2 = np.zeros(shape + (3, 3), complex)
+    D0 = np.zeros(shape, complex)
+    D2 = np.zeros(shape + (3, 3), complex)
+    for ci, wi in zip(c, w):
+        th = K @ ci
+        e = np.exp(-1j * th)
+        den = 1.0 - (1.0 - om) * e
+        h = e / den
+        one_minus_e = 2.0 * np.sin(th / 2.0) ** 2 + 1j * np.sin(th)
+        q = one_minus_e / den
+        cc = np.outer(ci, ci)
+        H1 += wi * h[..., None] * ci
+        H2 += wi * h[..., None, None] * cc
+        D0 += wi * q
+        D2 += 3.0 * wi * q[..., None, None] * cc
+    M = np.zeros(shape + (4, 4), complex)
+    M[..., 0, 0] = D0
+    M[..., 0, 1:] = -3.0 * rho0 * om * H1
+    M[..., 1:, 0] = -om * H1
+    M[..., 1:, 1:] = rho0 * D2
+    r = np.zeros(shape + (4,), complex)
+    r[..., 0] = 3.0 * (1.0 - om / 2.0) * np.einsum("...a,...a->...", H1, gh)
+    r[..., 1:] = gh / 2.0 + 3.0 * (1.0 - om / 2.0) * np.einsum("...ab,...b->...a", H2, gh)
+    M[(0,) * len(shape)] = np.eye(4)
+    r[(0,) * len(shape)] = 0.0
+    x = np.linalg.solve(M, r[..., None])[..., 0]
+    u = np.stack([np.real(np.fft.ifftn(x[..., 1 + a])) for a in range(3)])
+    drho = np.real(np.fft.ifftn(x[..., 0]))
+    return u, drho
 
 
 def pressure_density(g):

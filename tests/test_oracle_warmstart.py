@@ -160,3 +160,84 @@ def test_stress_start_puts_the_lattice_on_the_decaying_shear_mode(tau):
     print(tau, miss)
     assert miss[True] < (5e-4 if tau < 1 else 5e-3)
     assert miss[False] > 4 * miss[True]
+
+
+def test_lattice_fluid_step_in_fourier_space_is_the_oracle_lattice_step():
+    """One step of the oracle's lattice Boltzmann code (collide and stream, tau
+    = 0.8, no force) from a random non-equilibrium state of small amplitude
+    equals, mode by mode, the linear transfer e_i [(1 - omega) f^ + omega f^eq]
+    that the steady solve is built on (up to the equilibrium's second-order
+    terms and the FP64 round-off of whole populations, each far below 1e-6 of
+    deviations of 1e-8)."""
+    from lb_inputs import box
+    from oracle import oracle as O
+    c, w = _lattice()
+    nz, ny, nx, tau = 4, 5, 6, 0.8
+    g = np.random.default_rng(3)
+    df = g.normal(0.0, 1e-8, (nz, ny, nx, 19))
+    o = O.Sim(box(nx, ny, nz, tau), [], nthreads=1)
+    o.set_f(w[None, None, None, :] + df)
+    o.step(1)
+    got = o.f() - w[None, None, None, :]
+    fh = np.fft.fftn(df, axes=(0, 1, 2))
+    K = W._modes((nz, ny, nx))
+    out = np.zeros_like(fh)
+    for iz in range(nz):
+        for iy in range(ny):
+            for ix in range(nx):
+                out[iz, iy, ix] = W.lb_step_transfer(K[iz, iy, ix], tau, c, w) @ fh[iz, iy, ix]
+    want = np.real(np.fft.ifftn(out, axes=(0, 1, 2)))
+    assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0, 1.5])
+def test_steady_lattice_fluid_reduction_equals_the_19x19_fixed_point(tau):
+    """The 4 x 4 moment system of lb_steady_solve against the steady state of
+    the full 19-population transfer with Guo's force term, solved directly for
+    every mode of a random force field."""
+    c, w = _lattice()
+    shape = (3, 4, 5)
+    g = np.random.default_rng(4).normal(0.0, 1.0, (3,) + shape)
+    u, d = W.lb_steady_solve(g, tau, 1.0, c, w)
+    uh = np.stack([np.fft.fftn(u[a]) for a in range(3)], -1)
+    dh = np.fft.fftn(d)
+    gh = np.stack([np.fft.fftn(g[a]) for a in range(3)], -1)
+    K = W._modes(shape)
+    worst = 0.0
+    for idx in np.ndindex(*shape):
+        if idx == (0, 0, 0):
+            continue
+        d_bf, u_bf = W.lb_steady_bruteforce(gh[idx], K[idx], tau, c, w)
+        scale = np.abs(u_bf).max() + abs(d_bf)
+        worst = max(worst, (np.abs(uh[idx] - u_bf).max() + abs(dh[idx] - d_bf)) / scale)
+    assert worst < 1e-10
+
+
+def test_steady_lattice_fluid_is_stokes_flow_at_long_wavelengths():
+    """A transverse force wave g = G sin(2 pi y / n) x: the lattice fluid's
+    steady velocity approaches G / (nu k^2) sin(2 pi y / n) as k -> 0 (relative
+    deviation falling like k^2), with no density change.  At tau = 1 the
+    amplitude has a closed form from the D3Q19 weights: one step maps the
+    transverse velocity of this wave by a = (2 + cos k) / 3 (the faces along x
+    and z keep it, the four edges in the x-y plane see cos k) and Guo's force
+    enters as (1 + a) / 2, so the steady amplitude is (1 + a) / (2 (1 - a))
+    = (5 + cos k) / (4 sin^2(k / 2)) per unit force."""
+    c, w = _lattice()
+    devs = []
+    for n in (16, 32, 64):
+        y = np.arange(n)
+        g = np.zeros((3, 2, n, 2))
+        g[0] = np.sin(2 * np.pi * y / n)[None, :, None]
+        for tau in (0.8, 1.0, 1.3):
+            nu = (tau - 0.5) / 3.0
+            u, d = W.lb_steady_solve(g, tau, 1.0, c, w)
+            k = 2 * np.pi / n
+            amp = (u[0][0, :, 0] * np.sin(2 * np.pi * y / n)).sum() * 2 / n
+            assert np.abs(u[1:]).max() < 1e-12 * amp and np.abs(d).max() < 1e-12 * amp
+            devs.append((n, tau, abs(amp * nu * k * k - 1.0)))
+            if tau == 1.0:
+                exact = (5 + np.cos(k)) / (4 * np.sin(k / 2) ** 2)
+                assert amp == pytest.approx(exact, rel=1e-12)
+    for tau in (0.8, 1.0, 1.3):
+        d16, d32, d64 = [dv for n, t, dv in devs if t == tau]
+        assert d64 < 0.01 and d32 / d64 > 3.5 and d16 / d32 > 3.5
