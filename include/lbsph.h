@@ -283,25 +283,26 @@ lb_status lb_links_noalloc(const double* semi, const double* q, const double* x,
 lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, size_t u_bytes, const float* drho,
                         int32_t is_device, int32_t with_stress, void* stream);
 
-/* The periodic Stokes flow (mu Lap u - grad p + g = 0, div u = 0, mu = rho0 nu)
- * driven by the particles of box `box`: g puts each particle's F_ext uniformly on
- * the fluid nodes next to it (a face neighbour is its solid node: a uniform
- * traction just outside the surface, under which a sphere's interior moves
- * rigidly at its Stokes velocity) and the box's body force plus, with
- * counter_force, the balancing -sum F_ext / N_fluid on the fluid nodes; a net
- * mean force is dropped.  Solved in Fourier space with the symbols of the
- * lattice's nearest-neighbour operators (DFTs on the device); then a uniform
- * velocity is added on the fluid nodes so that rho0 sum_fluid u + sum_p M_p U_p
- * = 0 with the particles' current (initial) velocities, the total momentum of a
- * run that starts from rest under balanced forces.  u_dev: device FP32
- * [3][nz][ny][nx]; drho_dev (device FP32 [nz][ny][nx], may be NULL): the density
- * deviation p / c_s^2 of the flow's pressure (zero mean over the fluid nodes),
- * which the lattice fluid needs to balance the forces at steady state.  Fully
- * periodic boxes only, before the first step (it reads the particles' initial
- * solid nodes).  This is the long-range part of a warm start (feed both to
- * lb_init_fluid): the diffusive development of this flow and the acoustic
- * settling of its pressure over the whole box are what make a cold start slow.
- * Not part of the paper.  Waits for completion.
+/* The periodic steady flow that the particles of box `box` drive in the lattice
+ * fluid, with its density: g puts each particle's F_ext uniformly on the fluid
+ * nodes next to it (a face neighbour is its solid node: a uniform traction
+ * just outside the surface) and the box's body force plus, with counter_force,
+ * the balancing -sum F_ext / N_fluid on the fluid nodes; a net mean force is
+ * dropped.  The flow is the exact steady state of the linear lattice dynamics
+ * itself (D3Q19 BGK with Guo forcing at the box's tau and rho0), solved mode by
+ * mode in Fourier space (DFTs on the device, a 4 x 4 system in the conserved
+ * moments per mode in FP64): at the scales of a few nodes the lattice's own
+ * viscous and pressure operators differ from a Stokes stencil by several per
+ * cent, and only a start on the lattice's own steady state avoids the slow
+ * relaxation of that difference.  Then a uniform velocity is added on the
+ * fluid nodes so that rho0 sum_fluid u + sum_p M_p U_p = 0 with the particles'
+ * current (initial) velocities, the total momentum of a run that starts from
+ * rest under balanced forces.  u_dev: device FP32 [3][nz][ny][nx]; drho_dev
+ * (device FP32 [nz][ny][nx], may be NULL): the density deviation of the steady
+ * state (zero mean over the fluid nodes).  Fully periodic boxes only, before
+ * the first step (it reads the particles' initial solid nodes).  This is the
+ * fluid half of a warm start (feed both to lb_init_fluid).  Not part of the
+ * paper.  Waits for completion.
  * Errors: LB_EINVAL (walls, edge > 4096), LB_ESTATE, LB_ENOMEM, LB_ECUDA. */
 lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, float* drho_dev, void* stream);
 

@@ -10,8 +10,9 @@
  * viscosity, confinement and orientation.  It is trained on resistance
  * tensors that the LB method itself produces, and its prediction warm-starts a
  * run: particle velocities (U, Omega) = R^-1 (F_ext, T_ext) plus the periodic
- * Stokes flow of the particles' forces as the initial fluid (lbsph.h,
- * lb_stokes_field / lb_init_fluid), so that fewer steps reach steady state.
+ * steady flow of the particles' forces in the lattice fluid as the initial
+ * fluid (lbsph.h, lb_stokes_field / lb_init_fluid), so that fewer steps reach
+ * steady state.
  *
  * Network (fixed shape): x[8] -> 256 -> 256 -> 21, ReLU between layers, inputs
  * padded to 16 and outputs to 32 for the tensor-core tiles.  The 21 outputs

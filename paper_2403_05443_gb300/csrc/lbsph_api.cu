@@ -35,7 +35,7 @@ cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* 
 cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const float* drho,
                               const int* owner, float tau, int stress, cudaStream_t s);
 cudaError_t launch_stokes(const BoxDev& B, const int* owner, const PartDev* pd, int np, int counter_on,
-                          const double body[3], float mu, float2* work, int* counts, double* sum, float* u,
+                          const double body[3], float2* work, int* counts, double* sum, float* u,
                           cudaStream_t s);
 }  // namespace lbsph
 
@@ -917,10 +917,9 @@ extern "C" lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, flo
     }
     CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     CK(owner_field(ctx, box, s));
-    const double mu = d.rho0 * (d.tau - 0.5) / 3.0;
     float* out = ctx->d_tmp + B.N;                     // [4][N]: u, then drho
     CK(launch_stokes(B, reinterpret_cast<int*>(ctx->d_tmp), ctx->d_pd + B.pbeg, B.pcnt, d.counter_force,
-                     d.body_force, (float)mu, ctx->d_stokes, ctx->d_counts,
+                     d.body_force, ctx->d_stokes, ctx->d_counts,
                      reinterpret_cast<double*>(ctx->d_counts) + (ctx->maxp + 2) / 2, out, s));
     CK(cudaMemcpyAsync(u_dev, out, 3ull * B.N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (drho_dev) CK(cudaMemcpyAsync(drho_dev, out + 3 * B.N, (size_t)B.N * sizeof(float), cudaMemcpyDeviceToDevice, s));

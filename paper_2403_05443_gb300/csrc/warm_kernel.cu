@@ -1,23 +1,24 @@
 // Warm start of a run (lb_init_fluid, lb_stokes_field): an initial fluid at
 // the local equilibrium of given velocity and density fields (optionally with
-// the viscous stress of the velocity field in its non-equilibrium part), and the periodic
-// Stokes flow (with its pressure) driven by the particles' external forces, as
-// those fields.
+// the viscous stress of the velocity field in its non-equilibrium part), and
+// the periodic steady flow (with its density) that the particles' external
+// forces drive in the lattice fluid, as those fields.
 //
-// Stokes flow (mu Lap u - grad p + g = 0, div u = 0 on the periodic lattice):
-// the force density g puts F_ext of each particle uniformly on the fluid
-// nodes next to it
-// and the box's uniform counter force and body force on the fluid nodes; the
-// mean of g (if the forces do not balance) is dropped.  In Fourier space, with
-// kt_d = 2 sin(pi k_d / n_d) (the symbol of the nearest-neighbour difference,
-// so that |kt|^2 is the symbol of the 7-point Laplacian),
-//   u^(k) = (g^ - kt (kt . g^) / |kt|^2) / (mu |kt|^2),  u^(0) = 0.
-// The mean flow is then set so that the fluid and particle momenta add up to
-// zero (rho0 sum_fluid u = -sum_p M_p U_p, with the particles' initial
-// velocities), as they do in a run from rest with a balancing counter force.
-// The transforms are separable DFTs along x, y and z computed by definition,
-// one output element per thread with the line's twiddle table in shared
-// memory (box edges are not powers of two in general); FP32 complex.
+// The force density g puts F_ext of each particle uniformly on the fluid nodes
+// next to it, and the box's uniform counter force and body force on the fluid
+// nodes; the mean of g (if the forces do not balance) is dropped.  The flow is
+// the exact steady state of the linear lattice dynamics itself (D3Q19 BGK with
+// Guo forcing, lattice_steady_kernel), not of a discretised Stokes operator:
+// at the scales of a few nodes the lattice's viscous and pressure operators
+// differ from any fixed stencil by several per cent, and a start that differs
+// from the lattice's own steady state by that much relaxes on the flow's slow
+// time scales.  The mean flow is then set so that the fluid and particle
+// momenta add up to zero (rho0 sum_fluid u = -sum_p M_p U_p, with the
+// particles' initial velocities), as they do in a run from rest with a
+// balancing counter force.  The transforms are separable DFTs along x, y and z
+// computed by definition, one output element per thread with the line's
+// twiddle table in shared memory (box edges are not powers of two in general);
+// FP32 complex, the per-mode solve in FP64.
 #include "lattice_common.cuh"
 
 namespace lbsph {
@@ -170,41 +171,118 @@ __global__ void dft_axis_kernel(const float2* in, float2* out, int nx, int ny, i
     out[e] = make_float2(ar, ai);
 }
 
-// u^ = P g^ / (mu |kt|^2) in place, and the density deviation of the
-// pressure, drho^ = p^ / c_s^2 = -3 i (s . g^) / |s|^2 with s_d = sin(2 pi k_d /
-// n_d) (the central difference, as the lattice's momentum balance sees the
-// pressure gradient), into component 3; folds in the 1/N of the inverse DFT
-__global__ void stokes_solve_kernel(float2* g, int nx, int ny, int nz, float mu)
+// Steady state of the linear lattice fluid itself (D3Q19 BGK, omega = 1/tau,
+// Guo forcing, about rho0) under the force density g, mode by mode (k = 2 pi
+// (x/nx, y/ny, z/nz) for the DFT index (x, y, z)).  The steady pre-collision
+// populations are the post-collision ones streamed, f^_i = e_i f^*_i with
+// e_i = exp(-i k.c_i), hence f^_i = h_i (omega f^eq_i + (1 - omega/2) F^_i),
+// h_i = e_i / (1 - (1 - omega) e_i), F_i = 3 w_i c_i.g, and their moments
+// (drho, u = j + g/2) solve
+//   D0 drho - 3 rho0 omega H1 . u = 3 (1 - omega/2) H1 . g
+//   -omega H1 drho + rho0 D2 u     = g/2 + 3 (1 - omega/2) H2 g
+// with H1 = sum w_i c_i h_i, H2 = sum w_i c_i c_i^T h_i,
+// D0 = sum w_i (1 - e_i) q_i and D2 = sum 3 w_i c_i c_i^T (1 - e_i) q_i,
+// q_i = 1 / (1 - (1 - omega) e_i), with 1 - e_i = 2 sin^2(th/2) + i sin th
+// written without cancellation (D0 and D2 vanish like k^2).  In FP64, by
+// Gaussian elimination with partial pivoting; the k = 0 mode (mean flow and
+// mass, set afterwards) and numerically singular modes are zero.  On entry g
+// holds the transformed force density (components 0-2); on exit u^ (0-2) and
+// drho^ (3), with the 1/N of the inverse DFT folded in.
+struct cplx {
+    double re, im;
+};
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b)
+{
+    const double d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+__device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cplx cscale(cplx a, double s) { return {a.re * s, a.im * s}; }
+
+__global__ void lattice_steady_kernel(float2* g, int nx, int ny, int nz, double omega, double rho0)
 {
     const long long N = (long long)nx * ny * nz;
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (r >= N) return;
     const int x = (int)(r % nx), y = (int)((r / nx) % ny), z = (int)(r / ((long long)nx * ny));
-    const float kx = 2.0f * sinpif((float)x / (float)nx), ky = 2.0f * sinpif((float)y / (float)ny),
-                kz = 2.0f * sinpif((float)z / (float)nz);
-    const float sx = sinpif(2.0f * (float)x / (float)nx), sy = sinpif(2.0f * (float)y / (float)ny),
-                sz = sinpif(2.0f * (float)z / (float)nz);
-    const float k2 = kx * kx + ky * ky + kz * kz, s2 = sx * sx + sy * sy + sz * sz;
-    float2 a = g[r], b = g[N + r], c = g[2 * N + r], d = make_float2(0.0f, 0.0f);
-    if (r == 0 || k2 == 0.0f) {
-        a = b = c = make_float2(0.0f, 0.0f);
-    } else {
-        if (s2 > 1e-12f) {
-            // -3 i (s . g^) / |s|^2 / N
-            const float re = sx * a.x + sy * b.x + sz * c.x, im = sx * a.y + sy * b.y + sz * c.y;
-            const float q = 3.0f / (s2 * (float)N);
-            d = make_float2(im * q, -re * q);
+    const double kx = 2.0 * 3.14159265358979323846 * x / nx, ky = 2.0 * 3.14159265358979323846 * y / ny,
+                 kz = 2.0 * 3.14159265358979323846 * z / nz;
+    cplx H1[3] = {}, H2[3][3] = {}, D0 = {}, D2[3][3] = {};
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {        // the rest population has c = 0: no share in H1, H2, D0, D2
+        const int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+        const double th = kx * c[0] + ky * c[1] + kz * c[2];
+        double sn, cs, sh;
+        sincos(th, &sn, &cs);
+        sh = sin(0.5 * th);
+        const cplx e = {cs, -sn};
+        const cplx den = {1.0 - (1.0 - omega) * cs, (1.0 - omega) * sn};
+        const cplx h = cdiv(e, den);
+        const cplx q = cdiv({2.0 * sh * sh, sn}, den);
+        const double w = wd_of(i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (c[a] == 0) continue;
+            H1[a] = cadd(H1[a], cscale(h, w * c[a]));
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (c[b] == 0) continue;
+                H2[a][b] = cadd(H2[a][b], cscale(h, w * c[a] * c[b]));
+                D2[a][b] = cadd(D2[a][b], cscale(q, 3.0 * w * c[a] * c[b]));
+            }
         }
-        const float pr = (kx * a.x + ky * b.x + kz * c.x) / k2, pi = (kx * a.y + ky * b.y + kz * c.y) / k2;
-        const float sc = 1.0f / (mu * k2 * (float)N);
-        a = make_float2((a.x - kx * pr) * sc, (a.y - kx * pi) * sc);
-        b = make_float2((b.x - ky * pr) * sc, (b.y - ky * pi) * sc);
-        c = make_float2((c.x - kz * pr) * sc, (c.y - kz * pi) * sc);
+        D0 = cadd(D0, cscale(q, w));
     }
-    g[r] = a;
-    g[N + r] = b;
-    g[2 * N + r] = c;
-    g[3 * N + r] = d;
+    const float2 g0 = g[r], g1 = g[N + r], g2 = g[2 * N + r];
+    const cplx gh[3] = {{g0.x, g0.y}, {g1.x, g1.y}, {g2.x, g2.y}};
+    const double fo = 3.0 * (1.0 - 0.5 * omega);
+    // augmented 4 x 5 system: unknowns (drho, ux, uy, uz)
+    cplx M[4][5];
+    M[0][0] = D0;
+    cplx r0 = {0.0, 0.0};
+    for (int a = 0; a < 3; ++a) {
+        M[0][1 + a] = cscale(H1[a], -3.0 * rho0 * omega);
+        r0 = cadd(r0, cmul(H1[a], gh[a]));
+    }
+    M[0][4] = cscale(r0, fo);
+    for (int a = 0; a < 3; ++a) {
+        M[1 + a][0] = cscale(H1[a], -omega);
+        cplx ra = cscale(gh[a], 0.5);
+        for (int b = 0; b < 3; ++b) {
+            M[1 + a][1 + b] = cscale(D2[a][b], rho0);
+            ra = cadd(ra, cscale(cmul(H2[a][b], gh[b]), fo));
+        }
+        M[1 + a][4] = ra;
+    }
+    double scale = 0.0;
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) scale = fmax(scale, fabs(M[a][b].re) + fabs(M[a][b].im));
+    bool ok = r != 0 && scale > 0.0;
+    for (int col = 0; col < 4 && ok; ++col) {
+        int piv = col;
+        double best = 0.0;
+        for (int row = col; row < 4; ++row) {
+            const double m = M[row][col].re * M[row][col].re + M[row][col].im * M[row][col].im;
+            if (m > best) { best = m; piv = row; }
+        }
+        if (!(sqrt(best) > 1e-14 * scale)) { ok = false; break; }
+        if (piv != col)
+            for (int j = 0; j < 5; ++j) { const cplx t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
+        for (int row = 0; row < 4; ++row) {
+            if (row == col) continue;
+            const cplx f = cdiv(M[row][col], M[col][col]);
+            for (int j = col; j < 5; ++j) M[row][j] = csub(M[row][j], cmul(f, M[col][j]));
+        }
+    }
+    cplx sol[4] = {};
+    if (ok)
+        for (int a = 0; a < 4; ++a) sol[a] = cscale(cdiv(M[a][4], M[a][a]), 1.0 / (double)N);
+    g[r] = make_float2((float)sol[1].re, (float)sol[1].im);
+    g[N + r] = make_float2((float)sol[2].re, (float)sol[2].im);
+    g[2 * N + r] = make_float2((float)sol[3].re, (float)sol[3].im);
+    g[3 * N + r] = make_float2((float)sol[0].re, (float)sol[0].im);
 }
 
 __global__ void real_part_kernel(const float2* g, long long n3, float* u)
@@ -257,7 +335,7 @@ cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const 
 // work: 8 N float2 (two complex [4][N] buffers); counts: np + 1 ints; sum: 4
 // doubles; u: [4][N] (velocity, then the density deviation)
 cudaError_t launch_stokes(const BoxDev& B, const int* owner, const PartDev* pd, int np, int counter_on,
-                          const double body[3], float mu, float2* work, int* counts, double* sum, float* u,
+                          const double body[3], float2* work, int* counts, double* sum, float* u,
                           cudaStream_t s)
 {
     cudaError_t e;
@@ -276,7 +354,7 @@ cudaError_t launch_stokes(const BoxDev& B, const int* owner, const PartDev* pd, 
                                                           -1.0f, 3);
     }
     // forward result in b (three passes: a->b, b->a, a->b)
-    stokes_solve_kernel<<<nblk(N, 256), 256, 0, s>>>(b, B.nx, B.ny, B.nz, mu);
+    lattice_steady_kernel<<<nblk(N, 128), 128, 0, s>>>(b, B.nx, B.ny, B.nz, (double)B.omega, B.rho0);
     for (int ax = 0; ax < 3; ++ax) {
         dft_axis_kernel<<<nblk(4 * N, 256), 256, sh, s>>>(ax % 2 == 0 ? b : a, ax % 2 == 0 ? a : b, B.nx, B.ny, B.nz, ax,
                                                           1.0f, 4);

@@ -1,6 +1,6 @@
 """Learned warm start of spheroid runs: resistance tensors measured by the LB
 method, the surrogate trained on them, and its use to start a run near steady
-state.  Orchestration only: the LB runs, the Stokes flow, the network's
+state.  Orchestration only: the LB runs, the lattice fluid's steady flow, the network's
 training and inference and the 6x6 solves are calls into liblbsph.so
 (include/lbsph.h, include/lbsurrogate.h); the host assembles the calls'
 inputs and outputs.
@@ -163,7 +163,7 @@ def long_axis(q):
 def warm_start(sim, box: int, net, use_net: bool = True, use_fluid: bool = True, use_stress: bool = True):
     """Before the first step: set each particle's (U, Omega) to the surrogate's
     steady estimate R^-1 (F_ext, T_ext) (use_net) and the fluid to the lattice
-    Stokes flow of the particle forces and its pressure (use_fluid), with the
+    fluid's own steady flow and density under the particle forces (use_fluid), with the
     flow's viscous stress in the populations' non-equilibrium part
     (use_stress; no effect at tau = 1, where the first collision discards it).
     The confinement feature is the box's own edge (for a non-cubic box, the
@@ -239,8 +239,8 @@ def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int =
       2. 24-fold cube-rotation augmentation, 10 % of the LB samples held out;
       3. training of the network;
       4. an eval_n^3 box (eval_tau) with eval_count spheroids and random forces,
-         run cold (fluid at rest, particles at rest), with the Stokes fluid only,
-         and with the Stokes fluid plus the network's velocities (for
+         run cold (fluid at rest, particles at rest), with the steady lattice
+         fluid only, and with that fluid plus the network's velocities (for
          eval_tau != 1 also without the stress part), each compared with the
          steady velocities of a long cold run: steps until every particle's
          velocity stays within 1e-3 of it.
@@ -280,12 +280,20 @@ def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int =
     boxes, parts = I.many_spheroids(seed, n=eval_n, count=eval_count, force=force, tau=eval_tau)
     ms = int(math.ceil(max(p["semi"][0] for p in parts[0])))
 
+    cost = {}
+
     def run(mode, steps):
         sim = L.Simulation(boxes, parts, max_semi=ms, device=device)
         if mode != "cold":
+            torch.cuda.synchronize()
+            t = time.perf_counter()
             warm_start(sim, 0, net, use_net=mode.startswith("warm"), use_fluid=True,
                        use_stress=(mode != "warm_no_stress"))
+            torch.cuda.synchronize()
+            cost[mode + "_warm_start_s"] = time.perf_counter() - t
+        t = time.perf_counter()
         h = velocity_history(sim, 0, steps, every)
+        cost[mode + "_seconds_per_step"] = (time.perf_counter() - t) / steps
         sim.close()
         return h
 
@@ -314,7 +322,7 @@ def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int =
             "reference_drift_last_500_steps": drift, "end_of_warm_runs_vs_reference": end_vs_ref,
             "eval": f"{eval_n}^3, {eval_count} spheroids, |F|={force}, tau={eval_tau}",
             "error_curves": {k: pick(v) for k, v in curves.items()},
-            "seconds": {"data": t_data, "train": t_train, "eval": t_eval}}
+            "seconds": {"data": t_data, "train": t_train, "eval": t_eval, **cost}}
 
 
 if __name__ == "__main__":

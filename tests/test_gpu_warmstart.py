@@ -3,8 +3,9 @@ and without the stress part, lb_mlp_features, lb_resistance_targets,
 lb_warm_velocities), called through the C ABI, with the FP64 reference
 oracle/warmstart.py and the FP64 LB oracle.
 
-Bars: the Stokes flow within 1e-4 normwise (FP32 DFTs of length <= 40 against
-numpy's FP64 FFT: each pass adds a few FP32 roundings per term); a run started
+Bars: the steady flow of the lattice fluid and its density within 1e-4
+normwise (FP32 DFTs of length <= 40 against numpy's FP64 FFT: each pass adds
+a few FP32 roundings per term; the per-mode solve is FP64 on both sides); a run started
 from lb_init_fluid within the bars of the plain runs (1e-5 normwise on the
 deviations, u, F and T every few steps); features, targets and velocities
 within FP32 rounding (2e-6 normwise)."""
@@ -54,7 +55,7 @@ def test_stokes_field_matches_reference():
     owner = sim.field("solid")
     mu = b["rho0"] * (b["tau"] - 0.5) / 3.0
     ref, dref = W.stokes_field(b["nx"], b["ny"], b["nz"], owner, [p["F_ext"] for p in parts], mu, counter=True,
-                               density=True)
+                               density=True, tau=b["tau"], rho0=b["rho0"])
     err, derr = normwise(u, ref), normwise(d, dref)
     print("stokes error", err, derr)
     assert err <= 1e-4 and derr <= 1e-4
