@@ -239,7 +239,7 @@ struct ColliderT {
     float omega, om1, rho0, eps;    // SCALED: omega and eps times sc
     float gx, gy, gz;
     float cfug;                     // 3 cf, the factor of u.g in P (times sc)
-    float k[9], l[9];               // per pair: 9 cf w (c.g) and 3 cf w (c.g) (times sc)
+    float l[9];                     // per pair: 3 cf w (c.g) (times sc); 9 cf w (c.g) is 3 l
     float isc;                      // SCALED: 1 / sc
 
     __device__ __forceinline__ void init(float omega_, float rho0_, float gx_, float gy_, float gz_, float eps_,
@@ -258,7 +258,6 @@ struct ColliderT {
         for (int m = 0; m < 9; ++m) {
             const int i = 2 * m + 1;
             const float cg = cx_of(i) * gx_ + cy_of(i) * gy_ + cz_of(i) * gz_;
-            k[m] = ((9.0f * w_of(i)) * cf * cg) * s;
             l[m] = ((3.0f * w_of(i)) * cf * cg) * s;
         }
     }
@@ -301,7 +300,7 @@ struct ColliderT {
             const int i = 2 * m + 1;
             const float w = w_of(i);
             const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
-            const float sym = w * P + cu * ((4.5f * w) * orho * cu + k[m]);
+            const float sym = w * P + cu * ((4.5f * w) * orho * cu + 3.0f * l[m]);
             const float asym = (3.0f * w) * orho * cu + l[m];
             f[i] = om1 * f[i] + (sym + asym);
             f[i + 1] = om1 * f[i + 1] + (sym - asym);

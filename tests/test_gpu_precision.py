@@ -9,9 +9,9 @@ covered or uncovered in the run, so both sides follow the same geometry),
 drag |U - U_ref| / |U_ref| (the drag coefficient F / U has the same relative
 error) and torque |T - T_ref| / (|F_ext| a), a = 4 the long semi-axis.
 Bars: FP32 1e-5 (the plain path's bar); FP16 (scale 2^14, 11-bit significand)
-1e-3, the mixed-storage target, measured 6.2e-4; BF16 (8-bit significand, each
+1e-3, the mixed-storage target, measured 6.1e-4; BF16 (8-bit significand, each
 stored value rounded by up to 2^-9 of itself every step) misses that target,
-measured 1.6e-3, and is held to 2.5e-3 so that a regression still shows.
+measured 1.5e-3, and is held to 2.5e-3 so that a regression still shows.
 
 The second test is the squirmer batch of the benchmark's second workload
 (2000 steps, the swimming velocity and flow field per storage format against
