@@ -315,8 +315,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "boxes": len(boxes), "nodes_per_gpu": nodes,
                        "autotune": {"units_per_fetch": fetch, "blocks_per_particle": gx,
-                                    "ms_per_step_gx_1_2_3_default": [round(v, 5) for v in tune_ms[:4]],
-                                    "ms_per_step_fetch_1_2_4_8": [round(v, 5) for v in tune_ms[4:]]},
+                                    "ms_per_step_gx_1_2_3_d_2d_3d": [round(v, 5) for v in tune_ms[:6]],
+                                    "ms_per_step_fetch_1_2_4_8": [round(v, 5) for v in tune_ms[6:]]},
                        "precision": args.precision,
                        "l2": f"state {2 * nodes * BYTES_PER_LUP[args.precision] // 2 / 1e6:.0f} MB > 129 MB L2; not flushed",
                        "parallelism": f"{world} rank(s), 8 independent boxes each, no collective"},

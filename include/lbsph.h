@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define LBSPH_ABI_VERSION 2
+#define LBSPH_ABI_VERSION 3
 
 typedef struct lb_ctx lb_ctx;
 
@@ -219,16 +219,19 @@ lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, double* ms_
 
 /* Autotuner of the time-step kernel's launch shape for this context's boxes:
  * runs, each for 2 + steps_per_candidate iterations timed with CUDA events,
- * (1) the number of blocks that share one particle's boundary nodes (1, 2, 3
- * and the size-based default, those below the default whose node lists fit
- * 100 KB of shared memory), then (2) the number of consecutive 128-node bulk
+ * (1) the number of blocks that share one particle's boundary nodes (1, 2, 3,
+ * the size-based default d, 2d and 3d: those below d whose node lists fit
+ * 100 KB of shared memory and whose threads still cover every row of the
+ * largest bounding cube, those above d while every particle item still gets a
+ * block of its own), then (2) the number of consecutive 128-node bulk
  * units a warp takes per fetch from the work counter (1, 2, 4, 8), and keeps the
  * fastest of each for later lb_step calls.  The candidates compute the same
  * values bit for bit, so tuning advances the simulation exactly as lb_step
  * would.  out3 (may be NULL): units per fetch kept, blocks per particle kept,
  * iterations advanced (including the first collision if none ran yet).
- * ms_per_step (may be NULL, 8 doubles): time per iteration of each candidate
- * (0 where a candidate was skipped).  Not part of the paper.  Waits for
+ * ms_per_step (may be NULL, 10 doubles): time per iteration of each candidate,
+ * blocks per particle 1, 2, 3, d, 2d, 3d then units per fetch 1, 2, 4, 8 (0
+ * where a candidate was skipped).  Not part of the paper.  Waits for
  * completion.  Errors: LB_EINVAL, LB_ESTATE (separate-kernels mode), LB_ECUDA. */
 lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void* stream, int32_t* out3, double* ms_per_step);
 

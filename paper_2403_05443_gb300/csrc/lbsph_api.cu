@@ -976,12 +976,21 @@ extern "C" lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void*
     };
     const long long Smax = 2ll * (ctx->opt.max_semi + CUBE_MARGIN) + 2;
     const int gx0 = (int)std::max(1ll, (3 * Smax * Smax + BBLOCK - 1) / BBLOCK);
-    const int gcand[4] = {1, 2, 3, gx0};
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    // fewer blocks than the size-based default leave more SMs to the bulk work;
+    // more shorten the chain boundary -> critical block, which an iteration of
+    // 16-bit storage can wait for
+    const int gcand[6] = {1, 2, 3, gx0, 2 * gx0, 3 * gx0};
     double best = 1e300;
     int best_gx = ctx->gx;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 6; ++c) {
         if (ms_per_step) ms_per_step[c] = 0.0;
-        if (ctx->np == 0 || (c < 3 && gcand[c] >= gx0)) continue;    // only fewer blocks than the default
+        if (ctx->np == 0 || (c < 3 && gcand[c] >= gx0)) continue;    // below the default only
+        // a boundary block gives one thread to each of its cube rows: the blocks
+        // of a particle must have a thread for every one of its S^2 rows
+        if ((long long)gcand[c] * BBLOCK < Smax * Smax) continue;
+        if (c > 3 && (long long)ctx->np * (gcand[c] + 1) > 2ll * nsm) continue;   // one block per particle item
         // the node list of one block lives in shared memory next to two maps
         const size_t smem = 2ull * Smax * Smax * sizeof(uint64_t) + (size_t)list_cap_for(ctx, gcand[c]) * 4;
         if (smem > 100 * 1024) continue;
@@ -1003,7 +1012,7 @@ extern "C" lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void*
         double per = 0.0;
         const lb_status r = timed(per);
         if (r != LB_OK) return r;
-        if (ms_per_step) ms_per_step[4 + c] = per;
+        if (ms_per_step) ms_per_step[6 + c] = per;
         if (per < best) { best = per; best_f = fcand[c]; }
     }
     cudaEventDestroy(e0);

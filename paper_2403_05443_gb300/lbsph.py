@@ -253,9 +253,10 @@ def lb_stokes_field(ctx, box: int, u_dev_ptr: int, drho_dev_ptr=None, stream=Non
 
 def lb_autotune(ctx, steps_per_candidate: int, stream=None):
     """((units per fetch, blocks per particle, iterations advanced), ms per
-    step of the 4 blocks-per-particle and the 4 units-per-fetch candidates)."""
+    step of the 6 blocks-per-particle (1, 2, 3, d, 2d, 3d) and the 4
+    units-per-fetch candidates)."""
     out = np.zeros(3, np.int32)
-    ms = np.zeros(8)
+    ms = np.zeros(10)
     _check(library().lb_autotune(ctx, int(steps_per_candidate), stream, out.ctypes.data_as(C.POINTER(C.c_int32)),
                                  ms.ctypes.data_as(C.POINTER(C.c_double))), ctx)
     return tuple(int(v) for v in out), ms

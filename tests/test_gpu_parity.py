@@ -253,13 +253,32 @@ def test_autotune_keeps_results_bitwise_and_picks_a_candidate():
              [particle((3.0, 2.5, 2.0), (15.3, 18.1, 9.7), random_quaternion(g), F_ext=(0, 1e-4, 0))]]
     a = _sim(boxes, parts)
     (fetch, gx, advanced), ms = L.lb_autotune(a.ctx, 5)
-    assert fetch in (1, 2, 4, 8) and gx >= 1 and np.all(ms[4:] > 0)
+    assert fetch in (1, 2, 4, 8) and gx >= 1 and np.all(ms[6:] > 0) and ms[3] > 0
     a.step(9)
     b = _sim(boxes, parts)
     b.step(advanced + 9)
     for bi in range(2):
         assert np.array_equal(a.field("df", bi), b.field("df", bi))
         assert np.array_equal(a.records(bi), b.records(bi))
+
+
+def test_autotune_with_large_particles_keeps_results_bitwise():
+    """Semi-axis 7 (cube side 20, 400 rows): the tuner may not try fewer blocks
+    per particle than cover every cube row with a thread (one block of 256
+    threads would leave rows 256-399 of each cube undone), and every candidate
+    it tries must leave the run bit for bit where an untuned run is."""
+    g = rng(23)
+    boxes = [box(64, 48, 48, 0.9, counter_force=1)]
+    parts = [[particle((7.0, 3.0, 2.5), (20.5, 21.2, 19.1), random_quaternion(g), F_ext=(2e-4, -1e-4, 0)),
+              particle((6.0, 3.0, 3.0), (48.3, 30.1, 38.7), random_quaternion(g), F_ext=(0, 1e-4, 1e-4))]]
+    a = _sim(boxes, parts)
+    (fetch, gx, advanced), ms = L.lb_autotune(a.ctx, 5)
+    assert ms[0] == 0.0 and gx >= 2
+    a.step(7)
+    b = _sim(boxes, parts)
+    b.step(advanced + 7)
+    assert np.array_equal(a.field("df"), b.field("df"))
+    assert np.array_equal(a.records(), b.records())
 
 
 def test_async_record_copies_match_synchronous_reads():
