@@ -9,7 +9,7 @@
  * test (Eq. ellipsoidsurface) is evaluated with exactly the stated operation
  * order.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - lattice: D3Q19 textbook set, weights 1/3, 1/18, 1/36, c_s^2 = 1/3 (Sec. II.A);
  *   - collision: BGK with the quadratic equilibrium of Eq. 4 (Sec. II.A);
  *   - body force: Guo forcing, u = (sum f c + g/2)/rho, applied on fluid nodes;
