@@ -241,3 +241,19 @@ def test_steady_lattice_fluid_is_stokes_flow_at_long_wavelengths():
     for tau in (0.8, 1.0, 1.3):
         d16, d32, d64 = [dv for n, t, dv in devs if t == tau]
         assert d64 < 0.01 and d32 / d64 > 3.5 and d16 / d32 > 3.5
+
+
+def test_lattice_steady_field_momentum_balance_and_zero_mass():
+    """The warm-start field from the lattice fluid's steady state keeps the
+    bookkeeping of the 7-point one: the fluid carries minus the particles'
+    momentum, its density deviation sums to zero over the fluid, and a
+    uniform counter force makes no net flow."""
+    owner = np.zeros((6, 7, 8), np.int32)
+    owner[2:4, 3, 3:5] = 1
+    MU = [[2.0, -1.0, 0.5]]
+    u, d = W.stokes_field(8, 7, 6, owner, [[1e-3, -2e-4, 5e-4]], 0.1, counter=True, MU=MU, rho0=1.0,
+                          density=True, tau=0.8)
+    fluid = owner == 0
+    assert np.allclose([u[k][fluid].sum() for k in range(3)], [-2.0, 1.0, -0.5], atol=1e-12)
+    assert abs(d[fluid].sum()) < 1e-15
+    assert u[0][owner == 1].mean() > u[0][fluid].mean()   # the flow follows the force
