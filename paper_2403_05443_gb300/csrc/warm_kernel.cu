@@ -15,10 +15,10 @@
 // time scales.  The mean flow is then set so that the fluid and particle
 // momenta add up to zero (rho0 sum_fluid u = -sum_p M_p U_p, with the
 // particles' initial velocities), as they do in a run from rest with a
-// balancing counter force.  The transforms are separable DFTs along x, y and z
-// computed by definition, one output element per thread with the line's
-// twiddle table in shared memory (box edges are not powers of two in general);
-// FP32 complex, the per-mode solve in FP64.
+// balancing counter force.  The transforms are separable DFTs along x, y and z:
+// a radix-2 FFT per line in shared memory for power-of-two edges, otherwise
+// computed by definition (one output element per thread, the line's twiddle
+// table in shared memory); FP32 complex, the per-mode solve in FP64.
 #include "lattice_common.cuh"
 
 namespace lbsph {
@@ -169,6 +169,65 @@ __global__ void dft_axis_kernel(const float2* in, float2* out, int nx, int ny, i
         if (idx >= n) idx -= n;
     }
     out[e] = make_float2(ar, ai);
+}
+
+// the same pass for a power-of-two length n = 2^logn: one block per line, the
+// line staged in shared memory in bit-reversed order and transformed by logn
+// radix-2 butterfly stages (decimation in time) with the twiddles of the line
+// in shared memory; O(n log n) instead of O(n^2) per line
+__global__ void fft_axis_kernel(const float2* in, float2* out, int nx, int ny, int nz, int axis, float sign, int logn)
+{
+    extern __shared__ float2 fsm[];
+    const int n = 1 << logn;
+    float2* buf = fsm;
+    float2* tw = fsm + n;
+    const long long N = (long long)nx * ny * nz;
+    const long long lines = N / n;                  // lines of one component
+    const int comp = (int)(blockIdx.x / lines);
+    const long long l = blockIdx.x - comp * lines;
+    long long base, stride;
+    if (axis == 0) {
+        stride = 1;
+        base = comp * N + l * nx;
+    } else if (axis == 1) {
+        stride = nx;
+        base = comp * N + (l / nx) * ((long long)nx * ny) + (l % nx);
+    } else {
+        stride = (long long)nx * ny;
+        base = comp * N + l;                        // l = y * nx + x
+    }
+    for (int j = threadIdx.x; j < n / 2; j += blockDim.x) {
+        float sn, cs;
+        sincospif(2.0f * (float)j / (float)n, &sn, &cs);
+        tw[j] = make_float2(cs, sign * sn);
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int rj = (int)(__brev((unsigned)j) >> (32 - logn));
+        buf[rj] = in[base + j * stride];
+    }
+    __syncthreads();
+    for (int st = 1; st <= logn; ++st) {
+        const int half = 1 << (st - 1);
+        for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
+            const int grp = t >> (st - 1), pos = t & (half - 1);
+            const int i0 = (grp << st) + pos, i1 = i0 + half;
+            const float2 w = tw[pos << (logn - st)];
+            const float2 a = buf[i0], b = buf[i1];
+            const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
+            buf[i0] = make_float2(a.x + bw.x, a.y + bw.y);
+            buf[i1] = make_float2(a.x - bw.x, a.y - bw.y);
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) out[base + j * stride] = buf[j];
+}
+
+static int log2_if_pow2(int n)
+{
+    if (n < 2 || (n & (n - 1)) != 0) return -1;
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
 }
 
 // Steady state of the linear lattice fluid itself (D3Q19 BGK, omega = 1/tau,
@@ -349,16 +408,23 @@ cudaError_t launch_stokes(const BoxDev& B, const int* owner, const PartDev* pd, 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int nmax = B.nx > B.ny ? (B.nx > B.nz ? B.nx : B.nz) : (B.ny > B.nz ? B.ny : B.nz);
     const size_t sh = sizeof(float2) * nmax;
-    for (int ax = 0; ax < 3; ++ax) {
-        dft_axis_kernel<<<nblk(3 * N, 256), 256, sh, s>>>(ax % 2 == 0 ? a : b, ax % 2 == 0 ? b : a, B.nx, B.ny, B.nz, ax,
-                                                          -1.0f, 3);
-    }
+    // one pass along an axis: the radix-2 FFT for power-of-two edges, else the
+    // transform by definition
+    auto pass = [&](const float2* src, float2* dst, int ax, float sign, int ncomp) {
+        const int n = ax == 0 ? B.nx : (ax == 1 ? B.ny : B.nz);
+        const int lg = log2_if_pow2(n);
+        if (lg > 0) {
+            const int threads = n / 2 < 32 ? 32 : (n / 2 > 256 ? 256 : n / 2);
+            fft_axis_kernel<<<(unsigned)(ncomp * (N / n)), threads, sizeof(float2) * (n + n / 2), s>>>(
+                src, dst, B.nx, B.ny, B.nz, ax, sign, lg);
+        } else {
+            dft_axis_kernel<<<nblk(ncomp * N, 256), 256, sh, s>>>(src, dst, B.nx, B.ny, B.nz, ax, sign, ncomp);
+        }
+    };
+    for (int ax = 0; ax < 3; ++ax) pass(ax % 2 == 0 ? a : b, ax % 2 == 0 ? b : a, ax, -1.0f, 3);
     // forward result in b (three passes: a->b, b->a, a->b)
     lattice_steady_kernel<<<nblk(N, 128), 128, 0, s>>>(b, B.nx, B.ny, B.nz, (double)B.omega, B.rho0);
-    for (int ax = 0; ax < 3; ++ax) {
-        dft_axis_kernel<<<nblk(4 * N, 256), 256, sh, s>>>(ax % 2 == 0 ? b : a, ax % 2 == 0 ? a : b, B.nx, B.ny, B.nz, ax,
-                                                          1.0f, 4);
-    }
+    for (int ax = 0; ax < 3; ++ax) pass(ax % 2 == 0 ? b : a, ax % 2 == 0 ? a : b, ax, 1.0f, 4);
     // inverse result in a
     real_part_kernel<<<nblk(4 * N, 256), 256, 0, s>>>(a, 4 * N, u);
     if ((e = cudaMemsetAsync(sum, 0, 4 * sizeof(double), s)) != cudaSuccess) return e;

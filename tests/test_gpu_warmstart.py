@@ -61,6 +61,27 @@ def test_stokes_field_matches_reference():
     assert err <= 1e-4 and derr <= 1e-4
 
 
+@pytest.mark.parametrize("shape", [(32, 16, 64), (64, 24, 32)])
+def test_stokes_field_with_power_of_two_edges_matches_reference(shape):
+    """Power-of-two edges take the radix-2 FFT pass (one edge of the second box
+    does not, and keeps the transform by definition)."""
+    nx, ny, nz = shape
+    g = rng(37)
+    b = box(nx, ny, nz, 0.8, counter_force=1)
+    parts = [particle((4.5, 2.5, 2.0), (nx * 0.3, ny * 0.45, nz * 0.4), random_quaternion(g), F_ext=(2e-4, -1e-4, 5e-5)),
+             particle((3.0, 2.0, 2.0), (nx * 0.75, ny * 0.55, nz * 0.8), random_quaternion(g), F_ext=(-5e-5, 1e-4, 1e-4))]
+    sim = _sim(b, parts)
+    ud, dd = _gpu_stokes(sim, b)
+    u = ud.cpu().numpy().reshape(3, nz, ny, nx)
+    d = dd.cpu().numpy().reshape(nz, ny, nx)
+    mu = b["rho0"] * (b["tau"] - 0.5) / 3.0
+    ref, dref = W.stokes_field(nx, ny, nz, sim.field("solid"), [p["F_ext"] for p in parts], mu, counter=True,
+                               density=True, tau=b["tau"], rho0=b["rho0"])
+    err, derr = normwise(u, ref), normwise(d, dref)
+    print("stokes error", shape, err, derr)
+    assert err <= 1e-4 and derr <= 1e-4
+
+
 def test_run_from_initial_fluid_matches_oracle():
     """Start both sides from f = f_eq(rho0 + drho, u) of the Stokes flow and its
     pressure and compare every field
