@@ -242,8 +242,9 @@ static int log2_if_pow2(int n)
 // with H1 = sum w_i c_i h_i, H2 = sum w_i c_i c_i^T h_i,
 // D0 = sum w_i (1 - e_i) q_i and D2 = sum 3 w_i c_i c_i^T (1 - e_i) q_i,
 // q_i = 1 / (1 - (1 - omega) e_i), with 1 - e_i = 2 sin^2(th/2) + i sin th
-// written without cancellation (D0 and D2 vanish like k^2).  In FP64, by
-// Gaussian elimination with partial pivoting; the k = 0 mode (mean flow and
+// written without cancellation (D0 and D2 vanish like k^2).  The terms of one
+// direction in FP32, their sums and the solve in FP64 (Gaussian elimination
+// with partial pivoting); the k = 0 mode (mean flow and
 // mass, set afterwards) and numerically singular modes are zero.  On entry g
 // holds the transformed force density (components 0-2); on exit u^ (0-2) and
 // drho^ (3), with the 1/N of the inverse DFT folded in.
@@ -266,20 +267,26 @@ __global__ void lattice_steady_kernel(float2* g, int nx, int ny, int nz, double 
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (r >= N) return;
     const int x = (int)(r % nx), y = (int)((r / nx) % ny), z = (int)(r / ((long long)nx * ny));
-    const double kx = 2.0 * 3.14159265358979323846 * x / nx, ky = 2.0 * 3.14159265358979323846 * y / ny,
-                 kz = 2.0 * 3.14159265358979323846 * z / nz;
     cplx H1[3] = {}, H2[3][3] = {}, D0 = {}, D2[3][3] = {};
+    // each direction's terms in FP32 (the terms of c and -c are exact complex
+    // conjugates, so the imaginary parts still cancel pairwise), summed in FP64
+    const float fx = (float)x / nx, fy = (float)y / ny, fz = (float)z / nz, om1 = (float)(1.0 - omega);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {        // the rest population has c = 0: no share in H1, H2, D0, D2
         const int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
-        const double th = kx * c[0] + ky * c[1] + kz * c[2];
-        double sn, cs, sh;
-        sincos(th, &sn, &cs);
-        sh = sin(0.5 * th);
-        const cplx e = {cs, -sn};
-        const cplx den = {1.0 - (1.0 - omega) * cs, (1.0 - omega) * sn};
-        const cplx h = cdiv(e, den);
-        const cplx q = cdiv({2.0 * sh * sh, sn}, den);
+        // theta / pi, reduced to [-1, 1) so that sinpi / cospi stay exact at multiples of pi
+        float tp = 2.0f * (fx * c[0] + fy * c[1] + fz * c[2]);
+        tp -= 2.0f * floorf(0.5f * tp + 0.5f);
+        float snf, csf;
+        sincospif(tp, &snf, &csf);
+        const float shf = sinpif(0.5f * tp);
+        const float dre = 1.0f - om1 * csf, dim = om1 * snf, dd = dre * dre + dim * dim;
+        // h = e / den, q = (1 - e) / den with e = cs - i sn, 1 - e = 2 sh^2 + i sn
+        const float hre = (csf * dre - snf * dim) / dd, him = (-snf * dre - csf * dim) / dd;
+        const float are = 2.0f * shf * shf, aim = snf;
+        const float qre = (are * dre + aim * dim) / dd, qim = (aim * dre - are * dim) / dd;
+        const cplx h = {(double)hre, (double)him};
+        const cplx q = {(double)qre, (double)qim};
         const double w = wd_of(i);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
