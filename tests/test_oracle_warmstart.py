@@ -257,3 +257,30 @@ def test_lattice_steady_field_momentum_balance_and_zero_mass():
     assert np.allclose([u[k][fluid].sum() for k in range(3)], [-2.0, 1.0, -0.5], atol=1e-12)
     assert abs(d[fluid].sum()) < 1e-15
     assert u[0][owner == 1].mean() > u[0][fluid].mean()   # the flow follows the force
+
+
+def test_lattice_steady_state_scales_with_rho0_and_respects_cube_symmetry():
+    """Linear in the force, with u = j / rho0: doubling rho0 halves the flow and
+    keeps the density change; and the D3Q19 lattice is symmetric under the
+    cube's rotations, so a force field turned by 90 degrees about z gives the
+    turned flow (a plain Laplacian would too; moving 0.01 of weight from the
+    +x face to the +y face breaks it by 8 % of the flow)."""
+    c, w = _lattice()
+    g = np.random.default_rng(8).normal(0.0, 1.0, (3, 6, 6, 6))
+    u1, d1 = W.lb_steady_solve(g, 0.9, 1.0, c, w)
+    u2, d2 = W.lb_steady_solve(g, 0.9, 2.0, c, w)
+    assert np.allclose(u2, u1 / 2.0, rtol=0, atol=1e-12 * np.abs(u1).max())
+    assert np.allclose(d2, d1, rtol=0, atol=1e-12 * np.abs(d1).max())
+    # rotation about z by 90 degrees: (x, y) -> (-y, x) for positions and vectors
+    def turn(v):
+        # arrays are [z][y][x]: a quarter turn of the (y, x) index plane
+        return np.rot90(v, k=1, axes=(2, 1))
+    gt = np.stack([-turn(g[1]), turn(g[0]), turn(g[2])])
+    ut, dt = W.lb_steady_solve(gt, 0.9, 1.0, c, w)
+    want = np.stack([-turn(u1[1]), turn(u1[0]), turn(u1[2])])
+    scale = np.abs(u1).max()
+    # the same rotation of the lattice positions up to a periodic shift of the origin
+    best = min(np.abs(np.roll(ut, (sy, sx), axis=(2, 3)) - want).max() for sy in range(6) for sx in range(6))
+    assert best < 1e-12 * scale
+    bestd = min(np.abs(np.roll(dt, (sy, sx), axis=(1, 2)) - turn(d1)).max() for sy in range(6) for sx in range(6))
+    assert bestd < 1e-12 * np.abs(d1).max()
