@@ -10,6 +10,12 @@ A step is one iteration of the paper's Appendix over all 8 boxes.  The state
 (two distribution buffers of 160 MB each in FP32) is larger than the 129 MB L2,
 so no flush is done between steps.  Under torchrun each rank runs its own 8
 boxes (weak scaling, no collective on the data path).
+
+The line's value is the FP32 leg (or --precision's).  After it, the same
+workload runs with FP16 and BF16 deviation storage for the same K steps
+("mixed": MLUPS, roofline fraction and ratio to FP32), and one box of the sweep
+is run in all three formats against the FP64 oracle for --drag-steps
+iterations ("mixed.drag_error_vs_oracle").
 """
 from __future__ import annotations
 
@@ -179,34 +185,121 @@ def cpu_baseline(target_s: float = 12.0, boxes_parts=None):
                       f"FP64, OpenMP over {threads} threads, {dt:.1f} s"}
 
 
+def static_config(args, boxes, world):
+    """The workload description both arms print (identical dicts)."""
+    nodes = sum(b["nx"] * b["ny"] * b["nz"] for b in boxes)
+    return {"workload": WORKLOADS[args.workload], "boxes": len(boxes), "nodes_per_gpu": nodes,
+            "precision": args.precision,
+            "l2": f"state {2 * nodes * BYTES_PER_LUP[args.precision] // 2 / 1e6:.0f} MB > 129 MB L2; not flushed",
+            "parallelism": f"{world} rank(s), {len(boxes)} independent boxes each, no collective"}
+
+
 def run_reference(args):
-    rank = env_int("RANK", 0)
+    rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
     if rank != 0:
         return 0
-    from lb_inputs import sweep_8x64
+    import lb_inputs
     from oracle import oracle as O
 
-    boxes, parts = sweep_8x64(seed=args.seed)
+    boxes, parts = getattr(lb_inputs, args.workload)(seed=args.seed)
     threads = os.cpu_count() or 1
-    sims = [O.Sim(b, p, nthreads=threads) for b, p in zip(boxes, parts)]
-    per = boxes[0]["nx"] * boxes[0]["ny"] * boxes[0]["nz"]
-    # each step is a bounded sample: one iteration of one of the 8 boxes, in turn
-    for i in range(args.warmup):
-        sims[i % 8].step(1)
+    nb = len(boxes)
+    sims = [None] * nb
+    # each step is a bounded sample: one iteration of one of the boxes, in turn
+    # (a box's oracle state is created on its first use, outside the timed steps)
+    for i in range(max(args.warmup, nb)):
+        k = i % nb
+        if sims[k] is None:
+            sims[k] = O.Sim(boxes[k], parts[k], nthreads=threads)
+        sims[k].step(1)
+    nodes = 0
     t0 = time.perf_counter()
     for i in range(args.steps):
-        sims[i % 8].step(1)
+        k = i % nb
+        sims[k].step(1)
+        nodes += boxes[k]["nx"] * boxes[k]["ny"] * boxes[k]["nz"]
     dt = time.perf_counter() - t0
-    v = per * args.steps / dt / 1e6
+    v = nodes / dt / 1e6
     line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": "one iteration of one 64^3 box"},
+            "data": "synthetic", "config": static_config(args, boxes, world),
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-                             "sample": f"{args.steps} single-box iterations (262,144 nodes each), FP64"},
+                             "sample": f"{args.steps} single-box iterations of the FP64 oracle, the boxes in "
+                                       f"turn ({nodes:,} node updates), OpenMP over {threads} threads"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def drag_error_vs_oracle(steps: int, seed: int = 0):
+    """Drag and torque error of each storage format against the FP64 oracle on
+    one box of the sweep (the 45-degree spheroid: drag along and across its
+    axis, and a torque-free drift), after `steps` iterations: |U - U_ref| /
+    |U_ref| and |Omega - Omega_ref| a / |U_ref| (the rotation's surface speed)."""
+    import numpy as np
+
+    import paper_2403_05443_gb300 as pkg
+    from lb_inputs import sweep_8x64
+    from oracle import oracle as O
+
+    boxes, parts = sweep_8x64(seed=seed)
+    b, pl = boxes[3], parts[3]
+    t0 = time.perf_counter()
+    ref = O.Sim(b, pl, nthreads=os.cpu_count() or 1)
+    ref.step(steps)
+    r = ref.particle(0)
+    t_orc = time.perf_counter() - t0
+    ref.close()
+    a = max(pl[0]["semi"])
+    out = {}
+    for name, prec in PREC.items():
+        sim = pkg.Simulation([b], [pl], precision=prec, max_semi=8)
+        sim.step(steps)
+        g = sim.particle(0)
+        sim.close()
+        nU = float(np.linalg.norm(r["U"]))
+        out[name] = {"drag": float(np.linalg.norm(g["U"] - r["U"]) / nU),
+                     "rotation": float(np.linalg.norm(g["Om"] - r["Om"]) * a / nU)}
+    out["sample"] = (f"box 4 of the sweep (64^3, tau 0.8, (8,4,4) at 45 deg, |F| 5e-4), {steps} iterations, "
+                     f"GPU storage formats against the FP64 oracle ({t_orc:.1f} s on the host)")
+    out["U_ref"] = [float(v) for v in r["U"]]
+    return out
+
+
+def run_leg(args, pkg, precision, boxes, parts, local, dist, stream, sp, primary):
+    """Warm-up, autotune and the timed K steps of one storage format on the
+    workload; returns its measurements (and the simulation, still open)."""
+    import torch
+
+    nodes = sum(b["nx"] * b["ny"] * b["nz"] for b in boxes)
+    sim = pkg.Simulation(boxes, parts, precision=PREC[precision], max_semi=8, device=local, torch_alloc=True)
+    sim.step(args.warmup, stream=sp)
+    # launch shape of the step kernel for this workload (untimed; the
+    # candidates compute identical values, so this is more warm-up)
+    (fetch, gx, _), tune_ms = pkg.lbsph.lb_autotune(sim.ctx, 64, sp)
+    sim.step(args.warmup, stream=sp)           # the kept shape, right before the timed steps
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps, stream=sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    per = ms / args.steps / 1e3
+    peak, peak_src = measured_peak()
+    achieved = BYTES_PER_LUP[precision] * nodes / per / 1e9
+    return sim, {"value": whole_job_mlups(nodes, args.steps, env_int("WORLD_SIZE", 1), ms / 1e3),
+                 "ms_per_step": ms / args.steps, "achieved_gbs": achieved, "frac": achieved / peak,
+                 "peak": peak, "peak_source": peak_src,
+                 "tuning": {"units_per_fetch": fetch, "blocks_per_particle": gx,
+                            "ms_per_step_gx_1_2_3_d_2d_3d": [round(v, 5) for v in tune_ms[:6]],
+                            "ms_per_step_fetch_1_2_4_8": [round(v, 5) for v in tune_ms[6:]]}}
 
 
 def run_ours(args):
@@ -224,45 +317,17 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     boxes, parts = getattr(lb_inputs, args.workload)(seed=args.seed + rank)
     nodes = sum(b["nx"] * b["ny"] * b["nz"] for b in boxes)
-    sim = pkg.Simulation(boxes, parts, precision=PREC[args.precision], max_semi=8, device=local,
-                         torch_alloc=True)
     stream = torch.cuda.Stream()                  # every launch and event on this one stream
     torch.cuda.set_stream(stream)
     sp = pkg.lbsph.stream_handle(stream)
-    sim.step(args.warmup, stream=sp)
-    # launch shape of the step kernel for this workload (untimed; the
-    # candidates compute identical values, so this is more warm-up)
-    (fetch, gx, _), tune_ms = pkg.lbsph.lb_autotune(sim.ctx, 64, sp)
-    torch.cuda.synchronize()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
+    # clocks are sampled from before the first warm-up step to after the last
+    # timed leg, so that no idle gap precedes a timed region
     clocks = ClockSampler(local)
     clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(args.steps, stream=sp)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
-    sim.sync()
-    ms = max_over_ranks(ms, dist)
-    value = whole_job_mlups(nodes, args.steps, world, ms / 1e3)
-
-    # dominant kernel: the persistent step kernel is the whole timed region
-    # (ceil(K / 256) launches, one small memset before each); its algorithmic
-    # traffic is every population of every node read and written once per step
+    sim, lead = run_leg(args, pkg, args.precision, boxes, parts, local, dist, stream, sp, True)
     launches = -(-args.steps // STEP_ITERS)
-    peak, peak_src = measured_peak()
-    algo = BYTES_PER_LUP[args.precision] * nodes
-    achieved = algo / (ms / args.steps / 1e3) / 1e9
     traffic = committed_traffic(args.precision, nodes) if args.workload == "sweep_8x64" else None
+
     # the four parts as separate kernels, serialised with CUDA events between them
     nprof = max(50, min(500, args.steps // 10))
     k_ms, b_ms, c_ms, a_ms = pkg.lb_profile_step(sim.ctx, nprof, sp)
@@ -278,7 +343,8 @@ def run_ours(args):
         ft_np[i, 3:] = pl[0]["T_ext"]
     ke = max(20, min(400, args.steps // 20))
     torch.cuda.synchronize()
-    barrier()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(ke):
         pkg.lb_set_external(sim.ctx, -1, ft_np, sp)
@@ -292,7 +358,8 @@ def run_ours(args):
     ft_ring[:] = ft_in
     rec_ring = torch.empty((ke, np_tot, pkg.lbsph.LB_RECORD_DOUBLES), dtype=torch.float64, pin_memory=True)
     torch.cuda.synchronize()
-    barrier()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     pkg.lb_step_io(sim.ctx, ke, ft_ring.data_ptr(), rec_ring.data_ptr(), sp)
     stream.synchronize()
@@ -301,37 +368,50 @@ def run_ours(args):
     e2e_v = whole_job_mlups(nodes, ke, world, t_e2e)
     if not np.array_equal(rec_ring[-1].numpy(), pkg.lb_get_force_torque(sim.ctx, -1, np_tot)):
         raise RuntimeError("pipelined records differ from the synchronous read-back")
+    sim.close()
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "sweep_8x64":
-        cpu = cpu_baseline(boxes_parts=(boxes, parts))
+    # mixed precision: the same workload and step count with 16-bit storage
+    mixed = None
+    if args.precision == "fp32" and not args.no_mixed:
+        mixed = {}
+        for prec in ("fp16", "bf16"):
+            s16, leg = run_leg(args, pkg, prec, boxes, parts, local, dist, stream, sp, False)
+            s16.close()
+            mixed[prec] = {"value": leg["value"], "unit": "MLUPS", "ms_per_step": leg["ms_per_step"],
+                           "roofline": {"achieved": leg["achieved_gbs"], "peak": leg["peak"], "unit": "GB/s",
+                                        "frac": leg["frac"], "bytes_per_lup": BYTES_PER_LUP[prec]},
+                           "tuning": leg["tuning"]}
+            mixed[prec]["ratio_vs_fp32"] = leg["value"] / lead["value"]
+    clk = clocks.stop()
+
+    extra = {}
+    if rank == 0 and world == 1 and args.workload == "sweep_8x64" and not args.no_cpu_baseline:
+        extra["cpu_baseline"] = cpu_baseline(boxes_parts=(boxes, parts))
+        if mixed is not None and args.drag_steps > 0:
+            mixed["drag_error_vs_oracle"] = drag_error_vs_oracle(args.drag_steps, seed=args.seed)
 
     if rank == 0:
         line = {
-            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "metric": "MLUPS", "value": lead["value"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": lead["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else f"f32 arithmetic, {args.precision} storage",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "boxes": len(boxes), "nodes_per_gpu": nodes,
-                       "autotune": {"units_per_fetch": fetch, "blocks_per_particle": gx,
-                                    "ms_per_step_gx_1_2_3_d_2d_3d": [round(v, 5) for v in tune_ms[:6]],
-                                    "ms_per_step_fetch_1_2_4_8": [round(v, 5) for v in tune_ms[6:]]},
-                       "precision": args.precision,
-                       "l2": f"state {2 * nodes * BYTES_PER_LUP[args.precision] // 2 / 1e6:.0f} MB > 129 MB L2; not flushed",
-                       "parallelism": f"{world} rank(s), 8 independent boxes each, no collective"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+            "config": static_config(args, boxes, world),
+            "tuning": lead["tuning"],
+            "roofline": {"bound": "hbm", "achieved": lead["achieved_gbs"], "peak": lead["peak"], "unit": "GB/s",
+                         "frac": lead["frac"], "traffic": traffic, "peak_source": lead["peak_source"],
                          "kernel": "step_kernel (persistent: bulk pull streaming + BGK/Guo collision, "
                                    "boundary links, particle solve), per iteration",
                          "bytes_per_lup": BYTES_PER_LUP[args.precision],
                          "method": f"CUDA events on the launching stream around the timed region "
-                                   f"({launches} launches of up to {STEP_ITERS} iterations)",
+                                   f"({launches} launch(es) of up to {STEP_ITERS} iterations)",
                          "parts_ms_separate_kernels": {
                              "bulk": k_ms / nprof, "boundary": b_ms / nprof,
                              "particle_critical": c_ms / nprof, "particle_aux": a_ms / nprof,
                              "method": f"lb_profile_step: the four parts as separate kernels, {nprof} "
                                        "iterations after the timed region, CUDA events between them"}},
+            "mixed": mixed,
             "e2e": {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": int(ft_in.numel() * 8),
                     "d2h_bytes_per_step": int(rec_out.numel() * 8), "steps": ke,
                     "path": "lb_step_io over all steps: per step F_ext/T_ext in from that step's pinned slot, "
@@ -342,10 +422,9 @@ def run_ours(args):
                                               "(waits) per step"}},
             "gpu_launches": launches,   # step-kernel launches in the timed region
             "clocks": clk,
-            "cpu_baseline": cpu,
+            "cpu_baseline": extra.get("cpu_baseline"),
         }
         print(json.dumps(line))
-    sim.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -361,6 +440,9 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workload", default="sweep_8x64", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP16 / BF16 legs")
+    ap.add_argument("--drag-steps", type=int, default=3000,
+                    help="iterations of the drag-error check against the oracle (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -106,7 +106,7 @@ typedef struct {
 typedef struct {
     double semi[3];             /* a (body x, long axis e), b (body y), c (body z)     */
     double x[3];                /* centre                                             */
-    double q[4];                /* orientation, unit quaternion                        */
+    double q[4];                /* orientation, unit; divided by its norm on input     */
     double U[3], Omega[3];      /* initial velocity and angular velocity              */
     double density;             /* particle density; M = density * 4/3 pi a b c      */
     double F_ext[3], T_ext[3];  /* external force and torque                          */
@@ -256,11 +256,13 @@ lb_status lb_synchronize(lb_ctx* ctx);
  * file-scope device array of 32 KiB + 256 B, held by every GPU that loads the
  * library until the process exits.  The maximum is a bounding cube of 64 nodes
  * a side, i.e. semi-axes up to 29 lattice units; larger particles (or a cube
- * larger than the box) return LB_ECAPACITY.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current,
- * so make that first call before any stream capture.  Every call shares the
- * array and clears it first; calls whose work overlaps on the GPU race on it,
- * so serialise them (one stream, or events).
+ * larger than the box) return LB_ECAPACITY.  Every call looks up the array's
+ * address in the current device's context (cudaGetSymbolAddress, no allocation
+ * and no synchronisation), so a context that was reset and created again is
+ * served at its new address; the first call on a device may load the module,
+ * so make it before any stream capture.  Every call shares the array and
+ * clears it first; calls whose work overlaps on the GPU race on it, so
+ * serialise them (one stream, or events).
  * Errors: LB_EINVAL (bad pose, sizes or pointers), LB_ECAPACITY, LB_ECUDA. */
 lb_status lb_links_noalloc(const double* semi, const double* q, const double* x, int32_t nx, int32_t ny,
                            int32_t nz, int32_t walls, int32_t* pairs_dev, int32_t cap, int32_t* count_dev,

@@ -67,6 +67,17 @@ def hasimoto_velocity(F: float, mu: float, a: float, L: float) -> float:
     return F / (6.0 * math.pi * mu * a) * (1.0 - HASIMOTO_SC * a / L)
 
 
+def hasimoto_series(a: float, L: float) -> float:
+    """U_L / U_Stokes of a simple cubic array of spheres of radius a, cell side L,
+    moving through the fluid at zero mean volume flux (Hasimoto 1959, cited in
+    Sec. III.A, with the next terms of Sangani and Acrivos 1982):
+    1 - 1.7601 phi^(1/3) + phi - 1.5593 phi^2, phi = (4 pi / 3)(a / L)^3.
+    The first term is the shape-independent Stokeslet image sum,
+    1.7601 phi^(1/3) = HASIMOTO_SC a / L."""
+    phi = 4.0 * math.pi / 3.0 * (a / L) ** 3
+    return 1.0 - 1.7601 * phi ** (1.0 / 3.0) + phi - 1.5593 * phi * phi
+
+
 def jeffery_rhs(e: np.ndarray, G: np.ndarray, beta: float) -> np.ndarray:
     """Eq. jeffery: de/dt = Lambda e + beta (E e - e (e.E e)), G = grad u (G_ij = du_i/dx_j)."""
     E = 0.5 * (G + G.T)

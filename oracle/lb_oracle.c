@@ -22,6 +22,8 @@
  *   - external force and torque enter the right-hand sides of Eq. Fdiscrete /
  *     Eq. Tdiscrete;
  *   - dI/dt at time t uses qdot = Omega(t) q(t)/2 (Eq. qevolution);
+ *   - the initial quaternion is divided by its norm, sqrt of the sum of the
+ *     squares of q0..q3 taken in that order (Eq. vectrotn assumes |q| = 1);
  *   - covered / uncovered nodes at the remap (Appendix step 8): a covered node's
  *     momentum and angular momentum go to the particle's next solve; an
  *     uncovered node gets f_eq(rho0, U + Omega x r) and that momentum is taken
@@ -686,7 +688,10 @@ orc_sim* orc_create(const orc_box* box, const orc_particle* parts, int np, int n
         const orc_particle* I = parts + p;
         memcpy(P->semi, I->semi, sizeof(P->semi));
         memcpy(P->x, I->x, sizeof(P->x));
-        memcpy(P->q, I->q, sizeof(P->q));
+        {   /* Eq. vectrotn needs a unit quaternion: q is normalised on input */
+            const double qn = sqrt(I->q[0] * I->q[0] + I->q[1] * I->q[1] + I->q[2] * I->q[2] + I->q[3] * I->q[3]);
+            for (int k = 0; k < 4; ++k) P->q[k] = I->q[k] / qn;
+        }
         memcpy(P->U, I->U, sizeof(P->U));
         memcpy(P->Om, I->Om, sizeof(P->Om));
         memcpy(P->F_ext, I->F_ext, sizeof(P->F_ext));

@@ -9,9 +9,10 @@ Network (fixed shape, as the library defines it): x (8 features, padded with
 zeros to 16) -> h1 = relu(W1 x + b1) (256) -> h2 = relu(W2 h1 + b2) (256) ->
 y = W3 h2 + b3 (21 used of 32).  The 21 outputs fill a lower-triangular L row
 by row (diagonal through softplus) and the prediction is R^ = L L^T, an SPD
-6x6 resistance tensor in units of the radius-b sphere (translation block
-6 pi mu b, rotation block 8 pi mu b^3, coupling block 6 pi mu b^2 ... see
-features.py for the scaling).  Loss: mean over samples of mean over the 36
+6x6 resistance tensor in units of the radius-b sphere: R^ = D^-1 R D^-1 with
+D = diag(sqrt(6 pi mu b) I3, sqrt(8 pi mu b^3) I3), so that the translation
+block is in units of 6 pi mu b, the rotation block of 8 pi mu b^3 and the
+coupling blocks of sqrt(48) pi mu b^2 (oracle/warmstart.py: scales, targets).  Loss: mean over samples of mean over the 36
 entries of (R^ - R_target)^2.
 
 With emulate=True the reference rounds to BF16 at exactly the points where

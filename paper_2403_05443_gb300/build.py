@@ -15,7 +15,10 @@ LIB = os.path.join(OUT, "liblbsph.so")
 UNITS = ["bulk_kernel.cu", "boundary_kernel.cu", "lattice_kernel.cu", "particle_kernel.cu", "step_kernel.cu", "lbsph_api.cu",
          "mlp_kernel.cu", "warm_kernel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+# host code without contraction of a*b+c (aarch64 gcc contracts by default): the
+# quaternion normalised on input must round the same on every host
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I",
+         os.path.join(ROOT, "include")]
 
 
 def _deps():

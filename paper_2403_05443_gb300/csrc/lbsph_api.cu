@@ -88,6 +88,8 @@ struct lb_ctx {
     int list_cap = 0;                  // node list entries per boundary block
     int gx = 1;                        // boundary blocks per particle
     int fetch = 1;                     // bulk units a warp takes per counter fetch (lb_autotune)
+    bool aux_pending = false;          // the auxiliary particle blocks of the last step kernel's
+                                       // last iteration have not run yet (the next launch runs them)
     std::string err;
     std::vector<void*> allocs;
 };
@@ -312,6 +314,8 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     err = err ? err : cudaMemsetAsync(ctx->d_box_done, 0, sizeof(int) * nbox, ctx->stream);
     err = err ? err : cudaMemsetAsync(ctx->d_need_hdr, 0, sizeof(NeedHdr) * 2 * (size_t)ctx->maxp, ctx->stream);
     err = err ? err : cudaMemsetAsync(ctx->d_need, 0, sizeof(uint64_t) * 2 * (size_t)MAXS * MAXS * ctx->maxp, ctx->stream);
+    // the step kernel's counters start at zero and every launch leaves them so
+    err = err ? err : cudaMemsetAsync(ctx->d_sync, 0, sizeof(unsigned) * (4 + (size_t)ctx->maxp + 4096), ctx->stream);
     err = err ? err : cudaStreamSynchronize(ctx->stream);
     if (err != cudaSuccess) {
         free_all(ctx);
@@ -429,6 +433,7 @@ extern "C" lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particl
             s.Ib[2] = s.M * (a * a + bb * bb) / 5.0;
             cube_of(q, s.h, s.S);
             s.box = b;
+            s.aux_step = -1;
             pd.push_back(s);
             ++idx;
         }
@@ -539,10 +544,21 @@ static BndParams bnd_params(lb_ctx* ctx, int first, int cur)
     return np;
 }
 
+// The auxiliary particle blocks left over by the last step-kernel launch (its
+// last iteration's), before anything that reads their results.
+static cudaError_t flush_aux(lb_ctx* ctx, cudaStream_t s)
+{
+    if (!ctx->aux_pending || ctx->np == 0) return cudaSuccess;
+    const cudaError_t e = launch_particles_aux(particle_params(ctx, ctx->cur), s);
+    if (e == cudaSuccess) ctx->aux_pending = false;
+    return e;
+}
+
 // One iteration as separate kernels, in stream order on s.
 static cudaError_t enqueue_iteration(lb_ctx* ctx, int first, int cur, cudaStream_t s)
 {
     cudaError_t e;
+    if ((e = flush_aux(ctx, s)) != cudaSuccess) return e;
     if ((e = launch_bulk(bulk_params(ctx, first, cur), ctx->opt.precision, ctx->total_blocks, s)) != cudaSuccess) return e;
     if (ctx->np == 0) return cudaSuccess;
     if ((e = launch_boundary(bnd_params(ctx, first, cur), ctx->opt.precision, ctx->np, s)) != cudaSuccess) return e;
@@ -565,10 +581,11 @@ static cudaError_t enqueue_steps(lb_ctx* ctx, int k, int cur, cudaStream_t s, co
         bnd[c] = bnd_params(ctx, 0, c);
         part[c] = particle_params(ctx, c);
     }
-    cudaError_t e = cudaMemsetAsync(ctx->d_sync, 0, sizeof(unsigned) * (4 + (size_t)ctx->np), s);
-    if (e != cudaSuccess) return e;
-    return launch_step(bulk, bnd, part, ctx->d_sync, ctx->d_status, ctx->np, ctx->gx, ctx->total_blocks, k, cur,
-                       ctx->opt.precision, ctx->fetch, io_ft, io_rec, s);
+    // no reset of the counters: each launch leaves them at zero
+    const cudaError_t e = launch_step(bulk, bnd, part, ctx->d_sync, ctx->d_status, ctx->np, ctx->gx, ctx->total_blocks,
+                                      k, cur, ctx->opt.precision, ctx->fetch, io_ft, io_rec, s);
+    if (e == cudaSuccess && ctx->np > 0) ctx->aux_pending = true;
+    return e;
 }
 
 // A stream that is being captured into a CUDA graph: its work is recorded,
@@ -631,6 +648,7 @@ extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, 
     if (ctx->last_user_stream && ctx->last_user_stream != s) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     ctx->last_user_stream = s;
     ctx->stepped = true;
+    CK(flush_aux(ctx, s));
     cudaEvent_t ev[5];
     for (auto& e : ev) CK(cudaEventCreate(&e));
     double t[4] = {0, 0, 0, 0};
@@ -822,6 +840,8 @@ extern "C" lb_status lb_get_drag(lb_ctx* ctx, int32_t box, int32_t particle, dou
         return fail(ctx, LB_EINVAL, "bad box or particle");
     CK(cudaSetDevice(ctx->device));
     CK(cudaDeviceSynchronize());
+    CK(flush_aux(ctx, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(out36, &ctx->d_pd[ctx->hbox[box].pbeg + particle].zeta[0], 36 * sizeof(double), cudaMemcpyDeviceToHost));
     return read_status(ctx);
 }

@@ -214,6 +214,7 @@ struct PartDev {
     int S, h, box, slot;            // slot: ring slot holding map t
     long long step;
     double rec[RECD];               // F0, T0, F, T, U, Omega, x, q of the last iteration
+    long long aux_step;             // value of `step` the auxiliary block last ran for (-1: none)
     int nsolid, pad;
 };
 

@@ -535,6 +535,10 @@ __device__ __forceinline__ void aux_block(const PParams& P, int p)
         if (tid >= 32 && tid < 38) s_slip[tid - 32] = 0;
     }
     __syncthreads();
+    // once per pose: a second call for the same step leaves everything as it is
+    // (the finite-difference dI/dt would otherwise see I(t+1) twice)
+    if (S.aux_step == S.step) return;
+    if (tid == 0) G.aux_step = S.step;
     const BoxDev& B = P.boxes[S.box];
     const int ny = B.ny;
     const bool walls = B.walls != 0;

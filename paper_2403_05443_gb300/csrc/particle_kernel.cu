@@ -24,7 +24,6 @@
 // the fixed parts of F0 and T0, and the list of nodes the boundary kernel must
 // redo.
 #include <cmath>
-#include <mutex>
 
 #include "../../include/lbsph.h"
 #include "particle_blocks.cuh"
@@ -189,11 +188,6 @@ __global__ void __launch_bounds__(PBLOCK) links_noalloc_kernel(const NoallocArgs
 
 }  // namespace lbsph
 
-// Device address of the scratch array, looked up once per device (host code
-// cannot use the array's name as an address).
-static std::mutex g_noalloc_mutex;
-static void* g_noalloc_ptr[256];
-
 extern "C" lb_status lb_links_noalloc(const double* semi, const double* q, const double* x, int32_t nx, int32_t ny,
                                       int32_t nz, int32_t walls, int32_t* pairs_dev, int32_t cap, int32_t* count_dev,
                                       void* stream)
@@ -217,20 +211,16 @@ extern "C" lb_status lb_links_noalloc(const double* semi, const double* q, const
     a.nx = nx; a.ny = ny; a.nz = nz; a.walls = walls; a.cap = cap;
     a.pairs = pairs_dev;
     a.count = count_dev;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return LB_ECUDA;
+    // Device address of the scratch array in the current device's context.
+    // Host code cannot use the array's name as an address, and the address
+    // belongs to the context: it is looked up on every call (a table lookup in
+    // the runtime, no allocation and no synchronisation) rather than kept, so
+    // that a context destroyed and created again (cudaDeviceReset) never
+    // leaves a stale address behind.
     void* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-                cudaGetLastError();
-                return LB_ECUDA;
-            }
-            g_noalloc_ptr[dev] = p;
-        }
-        scratch = g_noalloc_ptr[dev];
+    if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess || !scratch) {
+        cudaGetLastError();
+        return LB_ECUDA;
     }
     links_noalloc_kernel<<<1, PBLOCK, 0, static_cast<cudaStream_t>(stream)>>>(a, static_cast<uint64_t*>(scratch));
     return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;

@@ -19,7 +19,9 @@
 //     unit is fetched while one runs.
 // A grid barrier ends the iteration: after it the lattice of step t, the box
 // terms and the redo masks of step t+1 are complete.  The auxiliary block of
-// the last iteration runs after the loop.
+// the last iteration runs first in the next launch: a launch ends at its last
+// barrier, and the barrier, work and item counters are zero again then, so
+// launches follow each other with no reset in between.
 //
 // Cross-block data are read through L2 (ld.global.cg, see lattice_common.cuh).
 // Every wait is bounded: a barrier that waits longer than SPIN_LIMIT polls
@@ -42,7 +44,7 @@ struct StepParams {
     BulkParams bulk[2];              // by buffer parity of the iteration
     BndParams bnd[2];
     PParams part[2];
-    unsigned* sync;                  // SYNC_PART + np words, zero at launch, then the blocks' SM ids
+    unsigned* sync;                  // SYNC_PART + np words, zero at launch (and again at exit), then the blocks' SM ids
     unsigned* status;
     int np, gx, tiles, iters, cur0;
     int fetch;                       // bulk units per counter fetch (1, 2, 4, 8)
@@ -88,6 +90,9 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
     const int tid = threadIdx.x;
     const int gx = SP.gx;
     const int npart = SP.np * (gx + 1);
+    // a context whose barrier timed out before keeps its counters as they were
+    // left: do no work (the status word already reports the timeout)
+    if (__ldcg(SP.status) & ST_TIMEOUT) return;
     // ---- rank of this block by (SM, block index): particle items go to whole SMs
     unsigned* blk_sm = SP.sync + SYNC_PART + SP.np;
     if (tid == 0) {
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
         for (int item = prank; item < npart; item += gridDim.x) {
             const int p = item / (gx + 1), c = item % (gx + 1);
             if (c < gx) boundary_block<St, false>(NP, p, c);
-            else if (it > 0) aux_block(PP, p);     // at it == 0 it ran before this launch
+            else aux_block(PP, p);                 // a no-op if it already ran for this pose
             __threadfence();
             __syncthreads();
             if (tid == 0) s_last = atomicAdd(SP.sync + SYNC_PART + p, 1u) == (unsigned)gx;
@@ -151,34 +156,28 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
         }
         if (!grid_barrier(SP)) return;
     }
-    // ---- auxiliary blocks of the last iteration, for the next launch's first solve
-    for (int p = blockIdx.x; p < SP.np; p += gridDim.x) {
-        aux_block(SP.part[0], p);
-        __syncthreads();
-    }
+    // the auxiliary blocks of the last iteration run as the first items of the
+    // next launch (or before the next separate-kernel iteration or getter)
 }
 
 template <class St>
 static cudaError_t launch_step_t(const StepParams& sp, size_t smem, cudaStream_t s)
 {
-    static int grid[2] = {0, 0};                 // per dynamic shared memory size seen first
-    static size_t grid_smem = 0;
+    // co-resident blocks for this device and dynamic shared memory size (one
+    // cheap occupancy query per launch: a process may drive several devices)
     cudaError_t e;
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(step_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    if (grid[0] == 0 || grid_smem != smem) {
-        int dev = 0, nsm = 0, occ = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<St>, KBLOCK, smem)) != cudaSuccess) return e;
-        if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
-        grid[0] = occ * nsm < MAX_GRID ? occ * nsm : MAX_GRID;
-        grid_smem = smem;
-    }
+    int dev = 0, nsm = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<St>, KBLOCK, smem)) != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const int grid = occ * nsm < MAX_GRID ? occ * nsm : MAX_GRID;
     void* args[] = {const_cast<StepParams*>(&sp)};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(step_kernel<St>), dim3(grid[0]), dim3(KBLOCK), args,
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(step_kernel<St>), dim3(grid), dim3(KBLOCK), args,
                                        smem, s);
 }
 

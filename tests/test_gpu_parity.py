@@ -47,6 +47,24 @@ def test_solid_map_and_links_bit_exact(seed):
     assert gpu_links_as_set(gpu) == oracle_links_as_set(orc)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_links_bit_exact_for_a_quaternion_off_unit_norm(seed):
+    """Both sides divide the input quaternion by its norm (Eq. vectrotn assumes
+    |q| = 1), with the same FP64 operations: a pose given with |q| = 1 + 9e-7
+    (inside the 1e-6 the library accepts) still gives identical solid nodes
+    and links."""
+    g = rng(1100 + seed)
+    semi = [float(v) for v in g.uniform(2.0, 5.0, 3)]
+    c, q = random_pose(g, 24, margin=-1)
+    q = [v * (1.0 + 9e-7) for v in q]
+    b = box(24, 24, 24, 1.0)
+    p = particle(semi, c, q)
+    gpu = _sim([b], [[p]])
+    orc = O.Sim(b, [p], nthreads=4)
+    assert np.array_equal(gpu.field("solid"), orc.owner())
+    assert gpu_links_as_set(gpu) == oracle_links_as_set(orc)
+
+
 def test_drag_matrix_matches_oracle():
     g = rng(5)
     b = box(32, 28, 36, 1.0)

@@ -143,3 +143,42 @@ def test_closed_form_limits():
     assert np.abs(e[-1] - e[0]).max() < 1e-6
     half = np.argmin(np.abs(t - T / 2))
     assert np.abs(e[half] + e[0]).max() < 1e-3               # half a period flips the axis
+
+
+def _settle_sphere(a, L, F, mu_tau=1.0, tol=2e-5, max_steps=20000):
+    """Steady settling velocity of a sphere under F_ext in a periodic L^3 box
+    with the counter body force (zero total momentum, as in sedimentation)."""
+    b = box(L, L, L, mu_tau, counter_force=1)
+    s = O.Sim(b, [particle((a, a, a), (L / 2 + 0.25, L / 2 - 0.125, L / 2 + 0.375), F_ext=(F, 0.0, 0.0))])
+    prev = None
+    for _ in range(max_steps // 100):
+        s.step(100)
+        U = s.particle(0)["U"][0]
+        if prev is not None and abs(U - prev) < tol * abs(U):
+            return U
+        prev = U
+    raise AssertionError("no steady state")
+
+
+def test_sphere_settling_absolute_scale_against_hasimoto():
+    """Absolute drag, not a difference of orientations: the change of a
+    sphere's settling velocity between two periodic boxes is fixed by the
+    Stokeslet image sum (Hasimoto's constant, Sec. III.A) and the fluid's
+    viscosity mu = rho0 (tau - 1/2)/3 alone; the sphere's own, discretisation-
+    dependent hydrodynamic radius only enters the O((a/L)^3) terms (a +-10 %
+    radius moves the expected value by under 2 %).  A wrong viscosity, force
+    scale or momentum-exchange factor shows up in full."""
+    a, F, mu = 3.0, 1e-4, 1.0 / 6.0
+    L1, L2 = 20, 28
+    U1, U2 = _settle_sphere(a, L1, F), _settle_sphere(a, L2, F)
+    U0 = A.stokes_velocity(F, mu, a)
+    want = U0 * (A.hasimoto_series(a, L2) - A.hasimoto_series(a, L1))
+    # leading term alone, shape independent: 2.8373 F / (6 pi mu) (1/L1 - 1/L2)
+    lead = A.hasimoto_velocity(F, mu, a, L2) - A.hasimoto_velocity(F, mu, a, L1)
+    assert abs(want / lead - 1.0) < 0.1
+    assert U2 > U1 > 0
+    assert abs((U2 - U1) / want - 1.0) < 0.05
+    # each box on its own, with the input radius (the hydrodynamic radius of a
+    # link-bounce-back sphere of radius 3 differs by a few per cent)
+    for U, Lb in ((U1, L1), (U2, L2)):
+        assert abs(U / (U0 * A.hasimoto_series(a, Lb)) - 1.0) < 0.12

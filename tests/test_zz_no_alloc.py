@@ -6,16 +6,19 @@ take the implicit synchronisation of cudaMalloc.  lb_links_noalloc serves them
 from a fixed scratch array inside the library, with outputs in buffers the
 caller owns.  This test calls it through the C ABI twice in a row (the second
 call finds the first call's bitmap in the shared scratch) and checks each
-result against lb_get_links of a context holding the same particle.
+result against the FP64 CPU oracle's links for the same pose (bit-exact: both
+sides evaluate the inside test in the same FP64 operation order) and against
+lb_get_links of a context holding the same particle.
 """
 import pytest
 
 from lb_inputs import axis_angle_quaternion, box, particle, random_quaternion, rng
+from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_links_match_context_links_on_two_calls():
+def test_noalloc_links_match_oracle_and_context_links_on_two_calls():
     torch = pytest.importorskip("torch")
     from paper_2403_05443_gb300 import lbsph as L
 
@@ -44,6 +47,10 @@ def test_noalloc_links_match_context_links_on_two_calls():
         sim.close()
         assert n == len(want) > 0
         assert got == want
+        # the oracle's links, as (node, velocity vector)
+        onode, ocv = O.Sim(b, [p], nthreads=4).links()
+        want_o = {(int(a), tuple(int(v) for v in cv)) for a, cv in zip(onode, ocv)}
+        assert {(a, tuple(int(v) for v in c[d])) for a, d in got} == want_o
 
 
 def test_noalloc_rejects_particles_beyond_the_scratch():
