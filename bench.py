@@ -15,7 +15,10 @@ The line's value is the FP32 leg (or --precision's).  After it, the same
 workload runs with FP16 and BF16 deviation storage for the same K steps
 ("mixed": MLUPS, roofline fraction and ratio to FP32), and one box of the sweep
 is run in all three formats against the FP64 oracle for --drag-steps
-iterations ("mixed.drag_error_vs_oracle").
+iterations ("mixed.drag_error_vs_oracle").  "steps_to_steady" is the learned
+warm start on the surrogate workload's evaluation box (128^3, 16 spheroids):
+steps until every particle's velocity stays within 1e-2 / 3e-3 / 1e-3 of its
+steady value, cold, with the lattice fluid's steady flow only, and warm.
 """
 from __future__ import annotations
 
@@ -233,10 +236,11 @@ def run_reference(args):
 
 
 def drag_error_vs_oracle(steps: int, seed: int = 0):
-    """Drag and torque error of each storage format against the FP64 oracle on
+    """Drag and rotation error of each storage format against the FP64 oracle on
     one box of the sweep (the 45-degree spheroid: drag along and across its
-    axis, and a torque-free drift), after `steps` iterations: |U - U_ref| /
-    |U_ref| and |Omega - Omega_ref| a / |U_ref| (the rotation's surface speed)."""
+    axis, and a torque-free drift), the velocities averaged over the last 500 of
+    `steps` iterations: |U - U_ref| / |U_ref| and |Omega - Omega_ref| a / |U_ref|
+    (the rotation's surface speed)."""
     import numpy as np
 
     import paper_2403_05443_gb300 as pkg
@@ -245,26 +249,79 @@ def drag_error_vs_oracle(steps: int, seed: int = 0):
 
     boxes, parts = sweep_8x64(seed=seed)
     b, pl = boxes[3], parts[3]
+    avg = min(500, steps // 2)
+
+    def steady(step, read):
+        # mean over the last `avg` steps (a node covered a few steps apart on
+        # the two sides moves the instantaneous drag by ~1e-3 of itself)
+        step(steps - avg)
+        acc = []
+        for _ in range(avg // 25):
+            step(25)
+            acc.append(read())
+        return {k: np.mean([x[k] for x in acc], axis=0) for k in ("U", "Om")}
+
     t0 = time.perf_counter()
     ref = O.Sim(b, pl, nthreads=os.cpu_count() or 1)
-    ref.step(steps)
-    r = ref.particle(0)
+    r = steady(ref.step, lambda: ref.particle(0))
     t_orc = time.perf_counter() - t0
     ref.close()
     a = max(pl[0]["semi"])
     out = {}
     for name, prec in PREC.items():
         sim = pkg.Simulation([b], [pl], precision=prec, max_semi=8)
-        sim.step(steps)
-        g = sim.particle(0)
+        g = steady(sim.step, lambda: sim.particle(0))
         sim.close()
         nU = float(np.linalg.norm(r["U"]))
         out[name] = {"drag": float(np.linalg.norm(g["U"] - r["U"]) / nU),
                      "rotation": float(np.linalg.norm(g["Om"] - r["Om"]) * a / nU)}
     out["sample"] = (f"box 4 of the sweep (64^3, tau 0.8, (8,4,4) at 45 deg, |F| 5e-4), {steps} iterations, "
-                     f"GPU storage formats against the FP64 oracle ({t_orc:.1f} s on the host)")
+                     f"means over the last {avg}; GPU storage formats against the FP64 oracle "
+                     f"({t_orc:.1f} s on the host)")
     out["U_ref"] = [float(v) for v in r["U"]]
     return out
+
+
+SURROGATE_WEIGHTS = os.path.join(ROOT, "paper_2403_05443_gb300", "surrogate_config5.npy")
+
+
+def steps_to_steady_block(args):
+    """Steps to steady state of the surrogate workload's evaluation box (128^3,
+    16 spheroids with a/b in [1, 4] and b in [3, 5], random orientations,
+    forces in random directions with the counter force, tau = 1): cold, the
+    lattice fluid's steady flow alone, and warm (that flow plus the network's
+    velocities), against the velocities at the end of the cold run.  The
+    network is the one trained on the workload's 64^3 resistance runs
+    (surrogate_config5.npy, written by `python -m
+    paper_2403_05443_gb300.warmstart config5`); without that file a small
+    network is trained here first on 96 samples in 32^3 boxes."""
+    from paper_2403_05443_gb300 import warmstart as W
+
+    t0 = time.perf_counter()
+    if os.path.exists(SURROGATE_WEIGHTS):
+        net = W.load_params(SURROGATE_WEIGHTS)
+        origin = "surrogate_config5.npy (trained on the workload's 64^3 resistance runs)"
+    else:
+        import lb_inputs as I
+        import numpy as np
+
+        smp = I.resistance_samples(args.seed, 96, 32)
+        M = np.zeros((len(smp), 6, 6))
+        for tau in (0.8, 1.0, 1.2):
+            sub = [i for i, s in enumerate(smp) if s["tau"] == tau]
+            if sub:
+                steps = int(8 * 32 * 32 / (4 * 3.141592653589793 ** 2 * (tau - 0.5) / 3.0))
+                M[sub] = W.measure_mobility([smp[i] for i in sub], steps)[0]
+        geoms = np.asarray([W.geom_of(s["a"], s["b"], s["tau"], s["L"], s["e"]) for s in smp])
+        x, R = W.targets(*W.augment(geoms, M))
+        net, _ = W.train(x, R, steps=1500, seed=args.seed)
+        origin = "trained here: 96 samples in 32^3 boxes, 1500 steps (no surrogate_config5.npy)"
+    ev = W.evaluate(net, seed=args.seed, eval_n=128, eval_count=16, force=1e-7, every=50, ref_steps=args.steady_steps,
+                    eval_tau=1.0, aspect=(1.0, 4.0), b_range=(3.0, 5.0))
+    ev.pop("error_curves", None)
+    ev["network"] = origin
+    ev["seconds_total"] = time.perf_counter() - t0
+    return ev
 
 
 def run_leg(args, pkg, precision, boxes, parts, local, dist, stream, sp, primary):
@@ -389,6 +446,8 @@ def run_ours(args):
         extra["cpu_baseline"] = cpu_baseline(boxes_parts=(boxes, parts))
         if mixed is not None and args.drag_steps > 0:
             mixed["drag_error_vs_oracle"] = drag_error_vs_oracle(args.drag_steps, seed=args.seed)
+    if rank == 0 and world == 1 and args.steady_steps > 0:
+        extra["steps_to_steady"] = steps_to_steady_block(args)
 
     if rank == 0:
         line = {
@@ -420,6 +479,7 @@ def run_ours(args):
                     "sync_per_step": {"value": e2e_sync, "unit": "MLUPS",
                                       "path": "lb_set_external(-1) + lb_step(1) + lb_get_force_torque(-1) "
                                               "(waits) per step"}},
+            "steps_to_steady": extra.get("steps_to_steady"),
             "gpu_launches": launches,   # step-kernel launches in the timed region
             "clocks": clk,
             "cpu_baseline": extra.get("cpu_baseline"),
@@ -443,6 +503,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP16 / BF16 legs")
     ap.add_argument("--drag-steps", type=int, default=3000,
                     help="iterations of the drag-error check against the oracle (0: skip)")
+    ap.add_argument("--steady-steps", type=int, default=40000,
+                    help="length of the cold reference run of the steps-to-steady check (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

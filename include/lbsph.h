@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define LBSPH_ABI_VERSION 3
+#define LBSPH_ABI_VERSION 4
 
 typedef struct lb_ctx lb_ctx;
 
@@ -88,11 +88,27 @@ typedef struct {
     int32_t counter_force;      /* 1: fluid also gets -sum(F_ext)/N_fluid (zero net)   */
     int32_t walls;
     double wall_u_lo[3], wall_u_hi[3];
+    /* Lubrication correction between particles of the box (0: none).  Below
+     * this gap h_c (lattice units, at most 4; 2/3 is the usual choice) the
+     * squeeze force of two spheres that the lattice does not resolve is added
+     * along the line of centres (the Nguyen-Ladd correction of the
+     * moving-boundary method of Sec. II.B; the paper itself does not use it):
+     * F_a = -6 pi mu R^2 (1/h - 1/h_c) (n . (U_a - U_b)) n = -F_b, n the unit
+     * vector from a to b, h = |x_b - x_a| - R_a - R_b with R = (n^T A n)^(-1/2)
+     * each body's centre-to-surface distance along n (A of
+     * Eq. ellipsoidsurface), R = R_a R_b / (R_a + R_b), mu = rho0 (tau - 1/2)/3,
+     * h >= 0.1, velocities of time t, the coefficient at most the reduced mass
+     * M_a M_b / (M_a + M_b).  It is part of the reported F and enters the
+     * right-hand side of Eq. Fdiscrete. */
+    double lub_cut;
 } lb_box_desc;
 
 typedef struct {
     int32_t precision;          /* LB_FP32 | LB_FP16 | LB_BF16                        */
-    int32_t didt_mode;          /* 0: analytic dI/dt (Eq. Irotdiff); 1: finite difference */
+    int32_t didt_mode;          /* I(t+1) in Eq. Tdiscrete: 0 I + dI/dt (Eq. Irotdiff);
+                                   1 I + (I(t) - I(t-1)); 2 predictor-corrector: the mode-0
+                                   solution predicts q(t+1) and the system is solved again
+                                   with I(q(t+1)) (Eq. Irot; Sec. II.D names it)      */
     int32_t device;             /* CUDA device ordinal                               */
     uint32_t flags;             /* LB_FLAG_*                                          */
     int32_t max_semi;           /* largest semi-axis any particle will have (<= 29)  */
@@ -128,10 +144,16 @@ lb_status lb_destroy(lb_ctx* ctx);
 
 /* Places n particles in box `box` (replacing any set before) and builds their
  * solid nodes (Eq. ellipsoidsurface), boundary links and drag matrices
- * (Eq. drag1-drag4).  Allowed only before the first lb_step.
+ * (Eq. drag1-drag4).  Allowed only before the first lb_step.  Particles may
+ * come as close as the lattice allows: where the bounding cubes of two
+ * particles reach each other (partners, at most 8 per particle), the nodes
+ * between them are updated once with the links of both surfaces, and the
+ * critical parts of such a cluster run after all of its boundary work.
  * Errors: LB_EINVAL (bad semi-axes, semi-axis > max_semi, too many particles,
- * a particle touching a wall), LB_EOVERLAP (bounding boxes of two particles
- * overlap), LB_ESTATE (after a step). */
+ * more than 64 particles in the box, a box too small for two nearby cubes,
+ * a particle touching a wall), LB_ECAPACITY (more than 8 partners), LB_EOVERLAP
+ * (two bodies share a node), LB_ESTATE (after a step).  During a run, two
+ * bodies that come to share a node stop it with LB_EOVERLAP. */
 lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particle* p, int32_t n);
 
 /* Sets F_ext and T_ext of the n particles of `box` (box = -1: all particles of

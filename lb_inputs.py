@@ -50,11 +50,12 @@ def axis_angle_quaternion(axis, angle: float) -> list:
 
 
 def box(nx, ny, nz, tau, rho0=1.0, body_force=(0.0, 0.0, 0.0), counter_force=0, walls=0,
-        wall_u_lo=(0.0, 0.0, 0.0), wall_u_hi=(0.0, 0.0, 0.0), didt_mode=0) -> dict:
+        wall_u_lo=(0.0, 0.0, 0.0), wall_u_hi=(0.0, 0.0, 0.0), didt_mode=0, lub_cut=0.0, collision=0) -> dict:
     return dict(nx=int(nx), ny=int(ny), nz=int(nz), tau=float(tau), rho0=float(rho0),
                 body_force=list(map(float, body_force)), counter_force=int(counter_force),
                 walls=int(walls), wall_u_lo=list(map(float, wall_u_lo)),
-                wall_u_hi=list(map(float, wall_u_hi)), didt_mode=int(didt_mode))
+                wall_u_hi=list(map(float, wall_u_hi)), didt_mode=int(didt_mode), lub_cut=float(lub_cut),
+                collision=int(collision))
 
 
 def particle(semi, x, q=(1.0, 0.0, 0.0, 0.0), U=(0.0, 0.0, 0.0), Om=(0.0, 0.0, 0.0), density=1.0,
@@ -151,16 +152,20 @@ def long_axis_quaternion(e) -> list:
     return axis_angle_quaternion(ax, math.atan2(s, e[0]))
 
 
-def resistance_samples(seed: int, n: int, L: int, taus=(0.8, 1.0, 1.2), aspect=(1.0, 3.0), b_range=(2.0, 3.5)):
+def resistance_samples(seed: int, n: int, L: int, taus=(0.8, 1.0, 1.2), aspect=(1.0, 3.0), b_range=(2.0, 3.5),
+                       tau_range=None):
     """n spheroids for resistance runs in periodic L^3 boxes: aspect ratio
-    r = a/b and b uniform in the ranges, tau drawn from taus, long axis e
-    uniform on the sphere, centre = box centre + U(-0.5,0.5)^3."""
+    r = a/b and b uniform in the ranges, tau drawn from taus (or uniform in
+    tau_range when given), long axis e uniform on the sphere, centre = box
+    centre + U(-0.5,0.5)^3.  The surrogate workload's training set is
+    resistance_samples(seed, 2000, 64, tau_range=(0.6, 1.5), aspect=(1, 4),
+    b_range=(3, 5))."""
     g = rng(seed)
     out = []
     for _ in range(n):
         r = float(g.uniform(*aspect))
         b = float(g.uniform(*b_range))
-        tau = float(g.choice(taus))
+        tau = float(g.uniform(*tau_range)) if tau_range is not None else float(g.choice(taus))
         e = unit_vector(g)
         centre = [0.5 * L + v for v in g.uniform(-0.5, 0.5, size=3)]
         out.append(dict(a=r * b, b=b, tau=tau, L=int(L), e=e, q=long_axis_quaternion(e), x=centre))
@@ -168,32 +173,40 @@ def resistance_samples(seed: int, n: int, L: int, taus=(0.8, 1.0, 1.2), aspect=(
 
 
 def many_spheroids(seed: int = 0, n: int = 128, count: int = 16, aspect=(1.5, 2.5), b_range=(2.5, 3.0),
-                   force=2e-5, tau=1.0, gap: int = 2, max_semi: int = 8):
+                   force=2e-5, tau=1.0, gap: int = 2, max_semi=None, margin: int = 2):
     """`count` spheroids in one periodic n^3 box with random orientations and
     external forces of magnitude `force` in random directions (counter body
-    force on the fluid).  Centres by rejection sampling so that the bounding
-    cubes of side 2 (max_semi + 2) + 2 keep `gap` nodes between them
-    (periodically)."""
+    force on the fluid).  Sizes first (aspect ratio and b uniform in the
+    ranges), then centres by rejection sampling so that the bounding cubes,
+    of side 2 (ceil(semi) + margin) + 2 (or of the common max_semi when
+    given), keep `gap` nodes between them (periodically)."""
     g = rng(seed)
-    S = 2 * (max_semi + 2) + 2 + gap
-    centres = []
-    while len(centres) < count:
-        c = g.uniform(0.0, n, size=3)
-        ok = True
-        for d in centres:
-            dd = np.abs(c - d)
-            dd = np.minimum(dd, n - dd)
-            if np.all(dd < S):
-                ok = False
-                break
-        if ok:
-            centres.append(c)
-    parts = []
-    for c in centres:
+    sizes = []
+    for _ in range(count):
         r = float(g.uniform(*aspect))
         b = float(g.uniform(*b_range))
+        sizes.append((r * b, b))
+    side = [2 * (int(math.ceil(a if max_semi is None else max_semi)) + margin) + 2 for a, _ in sizes]
+    centres = []
+    for k in range(count):
+        for _ in range(100000):
+            c = g.uniform(0.0, n, size=3)
+            ok = True
+            for j, d in enumerate(centres):
+                dd = np.abs(c - d)
+                dd = np.minimum(dd, n - dd)
+                if np.all(dd < 0.5 * (side[k] + side[j]) + gap):
+                    ok = False
+                    break
+            if ok:
+                centres.append(c)
+                break
+        else:
+            raise RuntimeError("no room for the spheroids")
+    parts = []
+    for (a, b), c in zip(sizes, centres):
         e = unit_vector(g)
         f = unit_vector(g)
-        parts.append(particle((r * b, b, b), [float(v) for v in c], long_axis_quaternion(e),
+        parts.append(particle((a, b, b), [float(v) for v in c], long_axis_quaternion(e),
                               F_ext=[force * v for v in f]))
     return [box(n, n, n, tau, counter_force=1)], [parts]

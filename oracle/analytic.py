@@ -102,6 +102,22 @@ def jeffery_orbit(e0, G, beta, t_end: float, dt: float):
     return np.arange(n + 1) * dt, np.array(out)
 
 
+def jeffery_orbit_constant(p, r: float):
+    """Orbit constant of Eq. jeffery in simple shear u_x = gamma y (flow x,
+    gradient y, vorticity z): C = tan(theta) (r^2 cos^2 phi + sin^2 phi)^(1/2) / r
+    with theta the angle of the axis p from the vorticity axis and phi its
+    azimuth from the gradient axis, i.e. C = (r^2 p_y^2 + p_x^2)^(1/2) / (r |p_z|)
+    (Jeffery 1922, cited in Sec. III.C)."""
+    p = np.asarray(p, dtype=np.float64)
+    return np.sqrt(r * r * p[..., 1] ** 2 + p[..., 0] ** 2) / (r * np.abs(p[..., 2]))
+
+
+def jeffery_aspect_from_period(T: float, gamma_dot: float) -> float:
+    """The aspect ratio r >= 1 with T = 2 pi (r + 1/r) / gamma_dot."""
+    s = T * gamma_dot / (2.0 * math.pi)           # r + 1/r
+    return 0.5 * (s + math.sqrt(max(0.0, s * s - 4.0)))
+
+
 def jeffery_period(r: float, gamma_dot: float) -> float:
     """T = 2 pi (r + 1/r) / gamma_dot (Jeffery 1922, cited in Sec. III.C)."""
     return 2.0 * math.pi * (r + 1.0 / r) / gamma_dot

@@ -21,7 +21,9 @@
  *   - r_b = x_b - x_c with x_b = x + c_b/2, minimum image (Eq. ub);
  *   - external force and torque enter the right-hand sides of Eq. Fdiscrete /
  *     Eq. Tdiscrete;
- *   - dI/dt at time t uses qdot = Omega(t) q(t)/2 (Eq. qevolution);
+ *   - dI/dt at time t uses qdot = Omega(t) q(t)/2 (Eq. qevolution); the
+ *     optional predictor-corrector (didt_mode 2) re-solves with I(t+1) of the
+ *     orientation the first solve predicts;
  *   - the initial quaternion is divided by its norm, sqrt of the sum of the
  *     squares of q0..q3 taken in that order (Eq. vectrotn assumes |q| = 1);
  *   - covered / uncovered nodes at the remap (Appendix step 8): a covered node's
@@ -91,12 +93,14 @@ typedef struct {
     double dm_return;            /* mass of the remap before, returned at the next collision */
     double Iprev[9];
     double F0[3], T0[3], F[3], T[3];
+    double FL[3];                /* lubrication force of this iteration (part of F) */
 } part_t;
 
 struct orc_sim {
     int nx, ny, nz, N;
     double tau, rho0, gbody[3];
-    int counter, walls, didt_mode;
+    int counter, walls, didt_mode, collision;
+    double lub_cut;
     double uw_lo[3], uw_hi[3];
     double *f, *fpost, *fnext;
     int *owner, *owner_new;
@@ -386,7 +390,20 @@ static void body_force(const orc_sim* s, double g[3])
 
 /* Appendix step 1: BGK collision (Eq. 3-4) with Guo forcing on every fluid node.
  * Before it, the mass removed by an earlier remap is put back uniformly:
- * f_i += w_i eps, eps = sum_p dm_return / N_fluid. */
+ * f_i += w_i eps, eps = sum_p dm_return / N_fluid.
+ *
+ * collision == 1, the scheme the paper's simulations use (Sec. II.A: one
+ * relaxation time for the non-conserved hydrodynamic modes, instantaneous
+ * relaxation of the non-hydrodynamic ones): of the non-equilibrium part
+ * f_i - feq_i only its projection on the hydrodynamic Hermite modes survives
+ * the collision, relaxed by (1 - 1/tau); every other (ghost) mode is set to its
+ * equilibrium value:
+ *   f*_i = feq_i + (1 - 1/tau) w_i [c_i . j_neq / c_s^2
+ *                                   + (c_i c_i - c_s^2 I) : Pi_neq / (2 c_s^4)] + S_i,
+ * j_neq = sum_i c_i (f_i - feq_i) (= -g/2 with the half-force velocity),
+ * Pi_neq = sum_i c_i c_i (f_i - feq_i), S_i the same Guo source (its moments
+ * are of first and second order only).  Mass, momentum (+ g) and the relaxed
+ * stress are those of BGK; at tau = 1 the two are the same. */
 static void collide(orc_sim* s, const double g[3])
 {
     const double tau = s->tau;
@@ -407,12 +424,29 @@ static void collide(orc_sim* s, const double g[3])
         }
         double u[3];
         for (int k = 0; k < 3; ++k) u[k] = (m[k] + 0.5 * g[k]) / rho;
+        double Pn[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, jn[3] = {0.0, 0.0, 0.0};
+        if (s->collision == 1)
+            for (int i = 0; i < Q; ++i) {
+                const double d = f[i] - feq_i(i, rho, u);
+                for (int a = 0; a < 3; ++a) {
+                    jn[a] += C[i][a] * d;
+                    for (int b = 0; b < 3; ++b) Pn[a][b] += C[i][a] * C[i][b] * d;
+                }
+            }
         for (int i = 0; i < Q; ++i) {
             double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
             double cg = C[i][0] * g[0] + C[i][1] * g[1] + C[i][2] * g[2];
             double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
             double S = (1.0 - 0.5 / tau) * Wt[i] * (3.0 * (cg - ug) + 9.0 * cu * cg);
-            fo[i] = f[i] - (f[i] - feq_i(i, rho, u)) / tau + S;
+            if (s->collision == 1) {
+                double QP = 0.0;        /* (c c - c_s^2 I) : Pi_neq */
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) QP += (C[i][a] * C[i][b] - (a == b ? 1.0 / 3.0 : 0.0)) * Pn[a][b];
+                const double cj = C[i][0] * jn[0] + C[i][1] * jn[1] + C[i][2] * jn[2];
+                fo[i] = feq_i(i, rho, u) + (1.0 - 1.0 / tau) * Wt[i] * (3.0 * cj + 4.5 * QP) + S;
+            } else {
+                fo[i] = f[i] - (f[i] - feq_i(i, rho, u)) / tau + S;
+            }
         }
     }
 }
@@ -461,29 +495,133 @@ static void force0(orc_sim* s, part_t* P)
     }
 }
 
-/* Appendix steps 4-5: inertia (Eq. Irot, Eq. Irotdiff or finite difference)
- * and the implicit solve of Eq. Fdiscrete / Eq. Tdiscrete (dt = 1). */
-static int solve_velocities(orc_sim* s, part_t* P, double Unew[3], double Wnew[3], double Inow[9])
+/* Lubrication correction (the Nguyen-Ladd correction the paper's method builds
+ * on, Sec. II.B; the paper itself does not use it).  Readings:
+ *   - gap and radii along the line of centres: n = d/|d|, d = minimum image of
+ *     x_q - x_p; R(n) = (n^T A n)^(-1/2) is the body's centre-to-surface
+ *     distance along n (A of Eq. ellipsoidsurface); h = |d| - R_p(n) - R_q(-n);
+ *   - below the cut-off gap h_c the lattice no longer resolves the gap, and the
+ *     missing normal squeeze force of two spheres of radii R_p, R_q is added:
+ *     F_p = -6 pi mu R^2 (1/h - 1/h_c) (n . (U_p - U_q)) n, R = R_p R_q/(R_p + R_q),
+ *     F_q = -F_p (no torque: the force acts along the line of centres);
+ *   - h is clamped at H_MIN = 0.1 and the velocities are those of time t, so
+ *     the force is explicit and exactly antisymmetric (combined momentum is
+ *     conserved); its coefficient is capped at the reduced mass M_p M_q /
+ *     (M_p + M_q), which stops the normal relative motion within one step
+ *     (the largest coefficient an explicit update keeps stable). */
+#define LUB_H_MIN 0.1
+
+void orc_lubrication_pair(const double semi_p[3], const double q_p[4], const double x_p[3], const double U_p[3],
+                          double M_p, const double semi_q[3], const double q_q[4], const double x_q[3],
+                          const double U_q[3], double M_q, const int L[3], const int periodic[3], double mu,
+                          double h_cut, double force_p[3], double* gap)
+{
+    double d[3], n[3], Ap[3][3], Aq[3][3];
+    for (int k = 0; k < 3; ++k) d[k] = min_image(x_q[k] - x_p[k], L[k], periodic[k]);
+    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    force_p[0] = force_p[1] = force_p[2] = 0.0;
+    for (int k = 0; k < 3; ++k) n[k] = d[k] / r;
+    shape_matrix(semi_p, q_p, Ap);
+    shape_matrix(semi_q, q_q, Aq);
+    const double Rp = 1.0 / sqrt(quad_form(Ap, n)), Rq = 1.0 / sqrt(quad_form(Aq, n));
+    const double h = r - Rp - Rq;
+    *gap = h;
+    if (!(h < h_cut)) return;
+    const double hh = h > LUB_H_MIN ? h : LUB_H_MIN;
+    const double R = Rp * Rq / (Rp + Rq);
+    double k = 6.0 * M_PI * mu * R * R * (1.0 / hh - 1.0 / h_cut);
+    const double kmax = M_p * M_q / (M_p + M_q);
+    if (k > kmax) k = kmax;
+    const double vn = n[0] * (U_p[0] - U_q[0]) + n[1] * (U_p[1] - U_q[1]) + n[2] * (U_p[2] - U_q[2]);
+    for (int c = 0; c < 3; ++c) force_p[c] = -k * vn * n[c];
+}
+
+/* Lubrication forces of every pair of particles at time t (zero when off). */
+static void lubrication(orc_sim* s)
+{
+    int L[3] = {s->nx, s->ny, s->nz}, per[3];
+    for (int k = 0; k < 3; ++k) per[k] = periodic_axis(s, k);
+    for (int p = 0; p < s->np; ++p) s->P[p].FL[0] = s->P[p].FL[1] = s->P[p].FL[2] = 0.0;
+    if (!(s->lub_cut > 0.0)) return;
+    const double mu = s->rho0 * (s->tau - 0.5) / 3.0;
+    for (int p = 0; p < s->np; ++p)
+        for (int q = p + 1; q < s->np; ++q) {
+            part_t *A = s->P + p, *B = s->P + q;
+            double f[3], h;
+            orc_lubrication_pair(A->semi, A->q, A->x, A->U, A->M, B->semi, B->q, B->x, B->U, B->M, L, per, mu,
+                                 s->lub_cut, f, &h);
+            for (int k = 0; k < 3; ++k) { A->FL[k] += f[k]; B->FL[k] -= f[k]; }
+        }
+}
+
+/* Appendix steps 4-5 for one body: inertia (Eq. Irot) and the implicit solve of
+ * Eq. Fdiscrete / Eq. Tdiscrete (dt = 1) for U(t+1), Omega(t+1), given the drag
+ * matrix zeta and the velocity-independent forces rF = F0 + F_ext + dP,
+ * rT = T0 + T_ext + dL.  The rotational equation needs I(t+1):
+ *   mode 0: I(t) + dI/dt, dI/dt of Eq. Irotdiff at time t;
+ *   mode 1: I(t) + (I(t) - I(t-1)) (finite difference, Iprev = I(t-1));
+ *   mode 2: predictor-corrector (Sec. II.D names it as the refinement of the
+ *           Eq. Irotdiff step): the mode-0 solution predicts Omega(t+1), hence
+ *           the orientation q_p = qnplus(q, (Omega(t) + Omega_p)/2) of
+ *           Eq. qnplus0-1, and the system is solved again with
+ *           I(t+1) = I(q_p) of Eq. Irot.
+ * The right-hand side is the same in every mode: M U(t) + rF and
+ * I(t) Omega(t) + rT.  Returns 0, or 1 if a pivot vanishes. */
+static int solve_body(double M, const double Ib[3], const double q[4], const double U[3], const double Om[3],
+                      const double zeta[6][6], const double rF[3], const double rT[3], const double Iprev[9],
+                      int mode, double Unew[3], double Wnew[3], double Inow[9])
 {
     double dI[9], A[36], rhs[6], x6[6];
-    orc_inertia_lab(P->q, P->Ibody, Inow);
-    if (s->didt_mode == 0) {
-        orc_inertia_rate(P->q, P->Om, P->Ibody, dI);
+    orc_inertia_lab(q, Ib, Inow);
+    if (mode == 1) {
+        for (int k = 0; k < 9; ++k) dI[k] = Inow[k] - Iprev[k];
     } else {
-        for (int k = 0; k < 9; ++k) dI[k] = Inow[k] - P->Iprev[k];
+        orc_inertia_rate(q, Om, Ib, dI);
     }
     for (int i = 0; i < 6; ++i)
-        for (int j = 0; j < 6; ++j) A[i * 6 + j] = P->zeta[i][j];
-    for (int k = 0; k < 3; ++k) A[k * 6 + k] += P->M;
+        for (int j = 0; j < 6; ++j) A[i * 6 + j] = zeta[i][j];
+    for (int k = 0; k < 3; ++k) A[k * 6 + k] += M;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) A[(i + 3) * 6 + (j + 3)] += Inow[i * 3 + j] + dI[i * 3 + j];
     for (int k = 0; k < 3; ++k) {
-        rhs[k] = P->M * P->U[k] + P->F0[k] + P->F_ext[k] + P->dP[k];
-        double IW = Inow[k * 3 + 0] * P->Om[0] + Inow[k * 3 + 1] * P->Om[1] + Inow[k * 3 + 2] * P->Om[2];
-        rhs[k + 3] = IW + P->T0[k] + P->T_ext[k] + P->dL[k];
+        rhs[k] = M * U[k] + rF[k];
+        double IW = Inow[k * 3 + 0] * Om[0] + Inow[k * 3 + 1] * Om[1] + Inow[k * 3 + 2] * Om[2];
+        rhs[k + 3] = IW + rT[k];
     }
     if (orc_gauss_solve(6, A, rhs, x6) != 0) return 1;
+    if (mode == 2) {
+        /* corrector: I(t+1) from the predicted orientation */
+        double Wm[3], qp[4], Ip[9];
+        for (int k = 0; k < 3; ++k) Wm[k] = 0.5 * (Om[k] + x6[k + 3]);
+        orc_quat_step(q, Wm, qp);
+        orc_inertia_lab(qp, Ib, Ip);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) A[(i + 3) * 6 + (j + 3)] = zeta[i + 3][j + 3] + Ip[i * 3 + j];
+        if (orc_gauss_solve(6, A, rhs, x6) != 0) return 1;
+    }
     for (int k = 0; k < 3; ++k) { Unew[k] = x6[k]; Wnew[k] = x6[k + 3]; }
+    return 0;
+}
+
+int orc_rigid_solve(double M, const double Ib[3], const double q[4], const double U[3], const double Om[3],
+                    const double zeta36[36], const double rF[3], const double rT[3], const double Iprev[9], int mode,
+                    double Unew[3], double Wnew[3])
+{
+    double Z[6][6], Inow[9];
+    memcpy(Z, zeta36, sizeof(Z));
+    return solve_body(M, Ib, q, U, Om, Z, rF, rT, Iprev, mode, Unew, Wnew, Inow);
+}
+
+/* Appendix steps 4-5 for particle P, then F and T of Eq. Fsplit / Eq. Tsplit. */
+static int solve_velocities(orc_sim* s, part_t* P, double Unew[3], double Wnew[3], double Inow[9])
+{
+    double rF[3], rT[3];
+    for (int k = 0; k < 3; ++k) {
+        rF[k] = P->F0[k] + P->FL[k] + P->F_ext[k] + P->dP[k];
+        rT[k] = P->T0[k] + P->T_ext[k] + P->dL[k];
+    }
+    if (solve_body(P->M, P->Ibody, P->q, P->U, P->Om, P->zeta, rF, rT, P->Iprev, s->didt_mode, Unew, Wnew, Inow))
+        return 1;
     for (int k = 0; k < 3; ++k) {
         double zu = 0.0, zw = 0.0, tu = 0.0, tw = 0.0;
         for (int j = 0; j < 3; ++j) {
@@ -492,7 +630,7 @@ static int solve_velocities(orc_sim* s, part_t* P, double Unew[3], double Wnew[3
             tu += P->zeta[k + 3][j] * Unew[j];
             tw += P->zeta[k + 3][j + 3] * Wnew[j];
         }
-        P->F[k] = P->F0[k] - zu - zw;
+        P->F[k] = P->F0[k] - zu - zw + P->FL[k];
         P->T[k] = P->T0[k] - tu - tw;
     }
     return 0;
@@ -670,6 +808,8 @@ orc_sim* orc_create(const orc_box* box, const orc_particle* parts, int np, int n
         s->uw_hi[k] = box->wall_u_hi[k];
     }
     s->counter = box->counter_force; s->walls = box->walls; s->didt_mode = box->didt_mode;
+    s->lub_cut = box->lub_cut;
+    s->collision = box->collision;
     s->nthreads = nthreads > 0 ? nthreads : 1;
     size_t nf = (size_t)s->N * Q;
     s->f = (double*)calloc(nf, sizeof(double));
@@ -732,6 +872,7 @@ static int step_once(orc_sim* s)
     collide(s, g);                                               /* step 1 */
     stream(s);                                                   /* step 2 */
     for (int p = 0; p < s->np; ++p) force0(s, s->P + p);         /* step 3 */
+    lubrication(s);                                              /* (f1) pair forces at t */
     for (int p = 0; p < s->np; ++p)                              /* steps 4-5 */
         if (solve_velocities(s, s->P + p, Un[p], Wn[p], In[p])) return 1;
     for (int p = 0; p < s->np; ++p) {

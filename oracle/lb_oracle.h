@@ -30,7 +30,10 @@ typedef struct {
     int counter_force;      /* 1: fluid also gets -sum(F_ext)/N_fluid      */
     int walls;
     double wall_u_lo[3], wall_u_hi[3];
-    int didt_mode;          /* 0: analytic Eq. Irotdiff, 1: finite difference */
+    int didt_mode;          /* 0: analytic Eq. Irotdiff, 1: finite difference, 2: predictor-corrector */
+    double lub_cut;         /* lubrication correction below this gap (0: none)  */
+    int collision;          /* 0: BGK; 1: the paper's ghost-mode scheme (stress modes relax with tau,
+                               non-hydrodynamic modes to equilibrium at once) */
 } orc_box;
 
 typedef struct {
@@ -80,6 +83,18 @@ void orc_inertia_lab(const double q[4], const double Ibody[3], double out[9]);
 void orc_inertia_rate(const double q[4], const double Om[3], const double Ibody[3], double out[9]);
 void orc_quat_step(const double q[4], const double Om_mean[3], double out[4]);
 int  orc_gauss_solve(int n, const double* A, const double* b, double* x);
+/* Lubrication correction between two bodies (positions, velocities and
+ * orientations at time t): force on body p (the opposite acts on q) and the
+ * gap h along the line of centres.  L/periodic: box edges for the minimum image. */
+void orc_lubrication_pair(const double semi_p[3], const double q_p[4], const double x_p[3], const double U_p[3],
+                          double M_p, const double semi_q[3], const double q_q[4], const double x_q[3],
+                          const double U_q[3], double M_q, const int L[3], const int periodic[3], double mu,
+                          double h_cut, double force_p[3], double* gap);
+/* Steps 4-5 for one body with a given drag matrix (row-major 6x6) and
+ * velocity-independent forces rF, rT; Iprev = I(t-1) (mode 1 only). */
+int  orc_rigid_solve(double M, const double Ib[3], const double q[4], const double U[3], const double Om[3],
+                     const double zeta36[36], const double rF[3], const double rT[3], const double Iprev[9],
+                     int mode, double Unew[3], double Wnew[3]);
 double orc_inside_value(const double semi[3], const double q[4], const double xc[3],
                         const int X[3], const int L[3], const int periodic[3]);
 void orc_squirmer_slip(const double semi[3], const double q[4], double B1, double B2,

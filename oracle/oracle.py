@@ -39,7 +39,8 @@ class OrcBox(C.Structure):
                 ("tau", C.c_double), ("rho0", C.c_double),
                 ("body_force", C.c_double * 3), ("counter_force", C.c_int),
                 ("walls", C.c_int), ("wall_u_lo", C.c_double * 3),
-                ("wall_u_hi", C.c_double * 3), ("didt_mode", C.c_int)]
+                ("wall_u_hi", C.c_double * 3), ("didt_mode", C.c_int), ("lub_cut", C.c_double),
+                ("collision", C.c_int)]
 
 
 class OrcParticle(C.Structure):
@@ -91,6 +92,10 @@ def lib():
         L.orc_inside_value.argtypes = [_D, _D, _D, _I, _I, _I]
         L.orc_inside_value.restype = C.c_double
         L.orc_squirmer_slip.argtypes = [_D, _D, C.c_double, C.c_double, _D, _D]
+        L.orc_rigid_solve.argtypes = [C.c_double, _D, _D, _D, _D, _D, _D, _D, _D, C.c_int, _D, _D]
+        L.orc_rigid_solve.restype = C.c_int
+        L.orc_lubrication_pair.argtypes = [_D, _D, _D, _D, C.c_double, _D, _D, _D, _D, C.c_double, _I, _I,
+                                           C.c_double, C.c_double, _D, _D]
     return _lib
 
 
@@ -179,6 +184,33 @@ def squirmer_slip(semi, q, B1, B2, r):
     return out
 
 
+def rigid_solve(M, Ibody, q, U, Om, zeta, rF, rT, Iprev=None, mode=0):
+    """Appendix steps 4-5 for one body (Eq. Fdiscrete / Eq. Tdiscrete, dt = 1):
+    (U(t+1), Omega(t+1)) for drag matrix zeta (6x6) and velocity-independent
+    forces rF, rT; mode 0 analytic dI/dt, 1 finite difference (Iprev = I(t-1)),
+    2 predictor-corrector."""
+    Un, Wn = np.zeros(3), np.zeros(3)
+    Ip = _f64(Iprev if Iprev is not None else np.zeros(9), 9)
+    rc = lib().orc_rigid_solve(float(M), _dp(_f64(Ibody, 3)), _dp(_f64(q, 4)), _dp(_f64(U, 3)), _dp(_f64(Om, 3)),
+                               _dp(_f64(zeta, 36)), _dp(_f64(rF, 3)), _dp(_f64(rT, 3)), _dp(Ip), int(mode),
+                               _dp(Un), _dp(Wn))
+    if rc:
+        raise ArithmeticError("singular system")
+    return Un, Wn
+
+
+def lubrication_pair(a: dict, b: dict, L, mu, h_cut, periodic=(1, 1, 1)):
+    """(force on a, gap) of the lubrication correction between particle
+    dicts a and b (semi, q, x, U, M)."""
+    f, h = np.zeros(3), np.zeros(1)
+    lib().orc_lubrication_pair(_dp(_f64(a["semi"], 3)), _dp(_f64(a["q"], 4)), _dp(_f64(a["x"], 3)),
+                               _dp(_f64(a["U"], 3)), float(a["M"]), _dp(_f64(b["semi"], 3)), _dp(_f64(b["q"], 4)),
+                               _dp(_f64(b["x"], 3)), _dp(_f64(b["U"], 3)), float(b["M"]),
+                               _ip(np.asarray(L, np.int32)), _ip(np.asarray(periodic, np.int32)), float(mu),
+                               float(h_cut), _dp(f), _dp(h))
+    return f, float(h[0])
+
+
 # ----------------------------------------------------------------------------
 class Sim:
     """One box of fluid with its particles, stepped by the oracle.
@@ -200,6 +232,8 @@ class Sim:
         b.wall_u_lo[:] = list(box.get("wall_u_lo", (0.0, 0.0, 0.0)))
         b.wall_u_hi[:] = list(box.get("wall_u_hi", (0.0, 0.0, 0.0)))
         b.didt_mode = int(box.get("didt_mode", 0))
+        b.lub_cut = float(box.get("lub_cut", 0.0))
+        b.collision = int(box.get("collision", 0))
         ps = (OrcParticle * max(1, len(particles)))()
         for k, p in enumerate(particles):
             ps[k].semi[:] = list(p["semi"])

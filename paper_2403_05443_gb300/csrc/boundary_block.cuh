@@ -45,6 +45,8 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
     __shared__ long long s_red[NW][ACC_COV];        // per-warp link sums
     __shared__ long long s_rare[NACC - ACC_COV];    // covered / uncovered nodes (rare: shared atomics)
     __shared__ int s_wsum[NW];
+    __shared__ PartK s_pk[MAXNB];                   // partners' snapshots (particles whose cubes reach this one's)
+    __shared__ NeedHdr s_ph[MAXNB];
 
     // ---- one round of independent loads
     const BoxDyn dyn = ldcg_dyn(P.pdyn + p);
@@ -63,6 +65,14 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
     }
     __syncthreads();
 
+    // partners: their snapshots and redo-mask cubes (the critical blocks of a
+    // partner run only after this block: the cluster's items come first)
+    const int nnb = min(K.nnb, MAXNB);
+    if (nnb > 0) {
+        for (int j = 0; j < nnb; ++j) ldcg_copy(&s_pk[j], P.pk + K.nb[j], tid, BBLOCK);
+        if (tid < nnb) s_ph[tid] = ldcg_hdr(P.need_hdr + K.nb[tid]);
+        __syncthreads();
+    }
     const int S = K.S;
     const uint64_t* slot1 = P.rows + ((size_t)p * 2 + 1) * (MAXS * MAXS);
     const uint64_t* s_new = s_bits + (K.rows_new == slot1 ? smax * smax : 0);
@@ -86,6 +96,26 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
         ax += dsh[0]; ay += dsh[1]; az += dsh[2];
         if (ax < 0 || ax >= S || ay < 0 || ay >= S || az < 0 || az >= S) return false;
         return (s_old[az * S + ay] >> ax) & 1ull;
+    };
+    // a node (X, Y, Z in the box) in partner j's new or old cube: its local coordinates
+    auto ploc = [&](int j, bool nw, int X_, int Y_, int Z_, int& lx, int& ly, int& lz) -> bool {
+        const int* ow = nw ? s_pk[j].ow_new : s_pk[j].ow_old;
+        lx = X_ - ow[0]; if (lx < 0) lx += nx;
+        ly = Y_ - ow[1]; if (ly < 0) ly += ny;
+        lz = Z_ - ow[2]; if (lz < 0) lz += nz;
+        const int Sq = s_pk[j].S;
+        return lx < Sq && ly < Sq && lz < Sq;
+    };
+    auto pbit = [&](int j, bool nw, int X_, int Y_, int Z_) -> bool {
+        int lx, ly, lz;
+        if (!ploc(j, nw, X_, Y_, Z_, lx, ly, lz)) return false;
+        const uint64_t* rw = nw ? s_pk[j].rows_new : s_pk[j].rows_old;
+        return (__ldcg(rw + lz * s_pk[j].S + ly) >> lx) & 1ull;
+    };
+    // integer sums that belong to partner j (global atomics: rare)
+    auto padd = [&](int j, int e, long long v) {
+        if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(P.acc + (size_t)K.nb[j] * NACC + e),
+                              static_cast<unsigned long long>(v));
     };
     // ---- this block's rows: the nodes to redo, compacted into shared memory
     {
@@ -136,38 +166,74 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
         const bool wallrow = walls && (Y == 0 || Y == ny - 1);
         const bool sol_new = bit_new(mx, my, mz);
         const bool sol_old = !FIRST && bit_old(mx, my, mz);
+        // partners: a node in the redo masks of two particles is done once, by
+        // the one of lower index; a partner may hold it now (pn) or before (po)
+        int pn = -1, po = -1;
+        if (nnb > 0) {
+            bool dup = false;
+            for (int j = 0; j < nnb; ++j) {
+                if (K.nb[j] < p) {
+                    const NeedHdr& h = s_ph[j];
+                    int lx = X - h.ow[0], ly = Y - h.ow[1], lz = Z - h.ow[2];
+                    if (lx < 0) lx += nx;
+                    if (ly < 0) ly += ny;
+                    if (lz < 0) lz += nz;
+                    if (lx < h.S && ly < h.S && lz < h.S &&
+                        ((__ldcg(P.need + (size_t)K.nb[j] * (MAXS * MAXS) + lz * h.S + ly) >> lx) & 1ull))
+                        dup = true;
+                }
+                if (pbit(j, true, X, Y, Z)) pn = j;
+                if (!FIRST && pbit(j, false, X, Y, Z)) po = j;
+            }
+            if (dup) continue;
+        }
+        const bool solN = sol_new || pn >= 0, solO = sol_old || po >= 0;
         bool write = !wallrow;
         float f[Q];
-        if (wallrow || (sol_new && (sol_old || FIRST))) {
+        if (wallrow || (solN && (solO || FIRST))) {
             write = false;                          // solid before and after: untouched
-        } else if (sol_old) {
-            // uncovered: f = f_eq(rho0, U + Omega x r) with r = x - x_c(t)
-            const float rx = K.ro_new[0] + mx, ry = K.ro_new[1] + my, rz = K.ro_new[2] + mz;
-            const float ux = K.U[0] + (K.W[1] * rz - K.W[2] * ry);
-            const float uy = K.U[1] + (K.W[2] * rx - K.W[0] * rz);
-            const float uz = K.U[2] + (K.W[0] * ry - K.W[1] * rx);
+        } else if (solO) {
+            // uncovered: f = f_eq(rho0, U + Omega x r) with r = x - x_c(t+1) of the
+            // body that held it, whose sums get its cube coordinates m
+            int m0 = mx, m1 = my, m2 = mz;
+            const PartK& Ko = sol_old ? K : s_pk[po];
+            if (!sol_old) ploc(po, true, X, Y, Z, m0, m1, m2);
+            const float rx = Ko.ro_new[0] + m0, ry = Ko.ro_new[1] + m1, rz = Ko.ro_new[2] + m2;
+            const float ux = Ko.U[0] + (Ko.W[1] * rz - Ko.W[2] * ry);
+            const float uy = Ko.U[1] + (Ko.W[2] * rx - Ko.W[0] * rz);
+            const float uz = Ko.U[2] + (Ko.W[0] * ry - Ko.W[1] * rx);
             const float uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
                 f[i] = w_of(i) * rho0 * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
             }
-            rare_add(ACC_UNC, 1);
-            rare_add(ACC_UNC + 1, mx); rare_add(ACC_UNC + 2, my); rare_add(ACC_UNC + 3, mz);
-            rare_add(ACC_UNC + 4, mx * mx); rare_add(ACC_UNC + 5, mx * my); rare_add(ACC_UNC + 6, mx * mz);
-            rare_add(ACC_UNC + 7, my * my); rare_add(ACC_UNC + 8, my * mz); rare_add(ACC_UNC + 9, mz * mz);
+            const long long uv[10] = {1, m0, m1, m2, m0 * m0, m0 * m1, m0 * m2, m1 * m1, m1 * m2, m2 * m2};
+            for (int e2 = 0; e2 < 10; ++e2) {
+                if (sol_old) rare_add(ACC_UNC + e2, uv[e2]);
+                else padd(po, ACC_UNC + e2, uv[e2]);
+            }
         } else if (FIRST) {
             // first collision: the node's initial distributions, no streaming
 #pragma unroll
             for (int i = 0; i < Q; ++i) f[i] = St::ld1(A + ((long long)i * N + own), inv, pol);
         } else {
             // fluid at t-1: decide every source first, then issue the 19 loads together
-            unsigned bb = 0, wl = 0;
+            unsigned bb = 0, wl = 0, pb = 0;        // own, wall and partner bounce-back
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int Ys = Y - cy_of(i);
                 if (walls && (Ys == 0 || Ys == ny - 1)) wl |= 1u << i;
                 else if (bit_old(mx - cx_of(i), my - cy_of(i), mz - cz_of(i))) bb |= 1u << i;
+            }
+            if (nnb > 0) {
+                for (int i = 1; i < Q; ++i) {
+                    if (((bb | wl) >> i) & 1u) continue;
+                    const int Xs = wrapd(X - cx_of(i), nx), Ys = wrapd(Y - cy_of(i), ny), Zs = wrapd(Z - cz_of(i), nz);
+                    for (int j = 0; j < nnb; ++j)
+                        if (pbit(j, false, Xs, Ys, Zs)) pb |= 1u << i;
+                }
+                bb |= pb;
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -186,6 +252,26 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
                 if ((wl >> i) & 1u) {
                     const float* uw = (Y - cy_of(i) == 0) ? K.uw_lo : K.uw_hi;
                     ubc = cx_of(i) * uw[0] + cy_of(i) * uw[1] + cz_of(i) * uw[2];
+                } else if ((pb >> i) & 1u) {
+                    // a partner's surface: its velocity at r_b = x - c_i/2 - x_c(t) of that body
+                    const int Xs = wrapd(X - cx_of(i), nx), Ys = wrapd(Y - cy_of(i), ny), Zs = wrapd(Z - cz_of(i), nz);
+                    int j = 0;
+                    while (j < nnb - 1 && !pbit(j, false, Xs, Ys, Zs)) ++j;
+                    const PartK& Kq = s_pk[j];
+                    int l0, l1, l2;
+                    ploc(j, false, X, Y, Z, l0, l1, l2);
+                    const float px = Kq.ro_old[0] + (float)l0 - 0.5f * cx_of(i);
+                    const float py = Kq.ro_old[1] + (float)l1 - 0.5f * cy_of(i);
+                    const float pz = Kq.ro_old[2] + (float)l2 - 0.5f * cz_of(i);
+                    float ux = Kq.U[0] + (Kq.W[1] * pz - Kq.W[2] * py);
+                    float uy = Kq.U[1] + (Kq.W[2] * px - Kq.W[0] * pz);
+                    float uz = Kq.U[2] + (Kq.W[0] * py - Kq.W[1] * px);
+                    if (Kq.squirmer) {
+                        float qx, qy, qz;
+                        squirmer_slip(Kq.e_old, Kq.a, Kq.eps2, Kq.B1, Kq.B2, px, py, pz, qx, qy, qz);
+                        ux += qx; uy += qy; uz += qz;
+                    }
+                    ubc = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
                 } else {
                     // r_b = x - c_i/2 - x_c(t-1) = ro_old + dsh + m - c_i/2
                     const float px = K.ro_old[0] + (float)(dsh[0] + mx) - 0.5f * cx_of(i);
@@ -203,8 +289,9 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
                 }
                 f[i] += 6.0f * w_of(i) * rho0 * ubc;
             }
-            if (sol_new) {
-                // covered: mass and momentum go to the particle's next solve
+            if (solN) {
+                // covered: mass and momentum go to the next solve of the body that
+                // holds the node now
                 write = false;
                 float drho = 0.f;
 #pragma unroll
@@ -213,12 +300,14 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
                 const float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
                 const float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
                 const long long Jx = fixq(jx), Jy = fixq(jy), Jz = fixq(jz);
-                rare_add(ACC_COV, 1);
-                rare_add(ACC_COV + 1, fixq(drho));
-                rare_add(ACC_COV + 2, Jx); rare_add(ACC_COV + 3, Jy); rare_add(ACC_COV + 4, Jz);
-                rare_add(ACC_COV + 5, my * Jz - mz * Jy);
-                rare_add(ACC_COV + 6, mz * Jx - mx * Jz);
-                rare_add(ACC_COV + 7, mx * Jy - my * Jx);
+                int m0 = mx, m1 = my, m2 = mz;
+                if (!sol_new) ploc(pn, true, X, Y, Z, m0, m1, m2);
+                const long long cv[8] = {1, fixq(drho), Jx, Jy, Jz, m1 * Jz - m2 * Jy, m2 * Jx - m0 * Jz,
+                                         m0 * Jy - m1 * Jx};
+                for (int e2 = 0; e2 < 8; ++e2) {
+                    if (sol_new) rare_add(ACC_COV + e2, cv[e2]);
+                    else padd(pn, ACC_COV + e2, cv[e2]);
+                }
             }
         }
         if (write) {
@@ -243,7 +332,24 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
                 aT[1] += mz * fx - mx * fz;
                 aT[2] += mx * fy - my * fx;
             }
-        } else if (sol_new && !wallrow) {
+            // links to partners' surfaces: their sums, about their cube origins
+            if (nnb > 0) {
+                for (int b = 1; b < Q; ++b) {
+                    const int Xb = wrapd(X + cx_of(b), nx), Yb = wrapd(Y + cy_of(b), ny), Zb = wrapd(Z + cz_of(b), nz);
+                    for (int j = 0; j < nnb; ++j) {
+                        if (!pbit(j, true, Xb, Yb, Zb)) continue;
+                        int l0, l1, l2;
+                        ploc(j, true, X, Y, Z, l0, l1, l2);
+                        const long long d = fixq(f[b]);
+                        const long long gx_ = cx_of(b) * d, gy_ = cy_of(b) * d, gz_ = cz_of(b) * d;
+                        padd(j, ACC_F, gx_); padd(j, ACC_F + 1, gy_); padd(j, ACC_F + 2, gz_);
+                        padd(j, ACC_T, l1 * gz_ - l2 * gy_);
+                        padd(j, ACC_T + 1, l2 * gx_ - l0 * gz_);
+                        padd(j, ACC_T + 2, l0 * gy_ - l1 * gx_);
+                    }
+                }
+            }
+        } else if (solN && !wallrow) {
             // solid now: zero it (never read as a source)
 #pragma unroll
             for (int i = 0; i < Q; ++i) St::st1(D + (long long)i * N + own, 0.0f, scale, pol);

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(BBLOCK, 2) boundary_kernel(const __grid_consta
 template <class St>
 static cudaError_t launch_bnd_t(const BndParams& p, dim3 grid, size_t smem, cudaStream_t s)
 {
-    if (smem > 48 * 1024) {
+    if (smem > 0) {        // static + dynamic may pass the 48 KB default: always opt in
         cudaError_t e = cudaFuncSetAttribute(boundary_kernel<St, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(boundary_kernel<St, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

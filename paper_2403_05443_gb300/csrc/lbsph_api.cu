@@ -30,7 +30,7 @@ cudaError_t launch_particles_aux(const PParams& p, cudaStream_t s);
 cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const PParams part[2], unsigned* sync,
                         unsigned* status, int np, int gx, int tiles, int iters, int cur0, int precision, int fetch,
                         const double* io_ft, double* io_rec, cudaStream_t s);
-cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
+cudaError_t launch_links(const PartDev* pd, const PartK* pk, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
                          int cap, int* count, cudaStream_t s);
 cudaError_t launch_init_fluid(const BoxDev& B, int precision, void* fbuf, const float* u, const float* drho,
                               const int* owner, float tau, int stress, cudaStream_t s);
@@ -79,6 +79,7 @@ struct lb_ctx {
     cudaStream_t last_user_stream = nullptr;        // last stream lb_step ran on
     cudaEvent_t ev_done = nullptr;                  // end of the last lb_step
     unsigned* d_sync = nullptr;                     // step kernel: barrier, work and item counters, block SM ids
+    double* d_ring = nullptr;                       // [maxp][2][RINGD] poses of the last two times (partners)
     NeedHdr* d_need_hdr = nullptr;     // [2][maxp]: redo masks, one slot per buffer parity
     uint64_t* d_need = nullptr;        // [2][maxp][MAXS*MAXS]
     int* d_blk_box = nullptr;
@@ -197,14 +198,15 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     if (o.max_semi <= 0) o.max_semi = 16;
     if (o.max_particles <= 0) o.max_particles = 64;
     auto bad = [&](const std::string& m) { delete ctx; (void)m; return LB_EINVAL; };
-    if (o.precision < 0 || o.precision > 2 || o.didt_mode < 0 || o.didt_mode > 1 || o.max_semi > 29 ||
+    if (o.precision < 0 || o.precision > 2 || o.didt_mode < 0 || o.didt_mode > 2 || o.max_semi > 29 ||
         (o.alloc && !o.release) || (!o.alloc && o.release))
         return bad("options");
     for (int b = 0; b < nbox; ++b) {
         const lb_box_desc& d = boxes[b];
         // rows are moved in 16-byte units: nx a multiple of 4 (8 for 16-bit storage)
         if (d.nx < 4 || d.ny < 4 || d.nz < 4 || d.nx % (o.precision == LB_FP32 ? 4 : 8) != 0) return bad("box size");
-        if (!(d.tau > 0.5) || !(d.rho0 > 0.0) || (d.walls && d.ny < 5)) return bad("box parameters");
+        if (!(d.tau > 0.5) || !(d.rho0 > 0.0) || (d.walls && d.ny < 5) || !(d.lub_cut >= 0.0) || d.lub_cut > 4.0)
+            return bad("box parameters");
         if ((long long)d.nx * d.ny * d.nz > (1ll << 31) / 19) return bad("box too large");
     }
     ctx->device = o.device;
@@ -242,6 +244,8 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
         }
         h.counter = d.counter_force;
         h.walls = d.walls;
+        h.lub_cut = d.lub_cut;
+        h.mu = d.rho0 * (d.tau - 0.5) / 3.0;
         h.nwall = d.walls ? 2ll * d.nx * d.nz : 0;
         h.scale = scale;
         h.inv_scale = 1.0f / scale;
@@ -282,10 +286,11 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     ctx->d_need_hdr = (NeedHdr*)dev_alloc(ctx, sizeof(NeedHdr) * 2 * (size_t)ctx->maxp);
     ctx->d_need = (uint64_t*)dev_alloc(ctx, sizeof(uint64_t) * 2 * (size_t)MAXS * MAXS * ctx->maxp);
     ctx->d_sync = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * (4 + (size_t)ctx->maxp + 4096));
+    ctx->d_ring = (double*)dev_alloc(ctx, sizeof(double) * 2 * RINGD * (size_t)ctx->maxp);
     for (void* p : {ctx->fbuf[0], ctx->fbuf[1], (void*)ctx->d_boxes, (void*)ctx->d_pd, (void*)ctx->d_pk,
                     (void*)ctx->d_acc, (void*)ctx->d_rows, (void*)ctx->d_status, (void*)ctx->d_count,
                     (void*)ctx->d_blk_box, (void*)ctx->d_box_dyn, (void*)ctx->d_pdyn, (void*)ctx->d_box_done,
-                    (void*)ctx->d_need_hdr, (void*)ctx->d_need, (void*)ctx->d_sync})
+                    (void*)ctx->d_need_hdr, (void*)ctx->d_need, (void*)ctx->d_sync, (void*)ctx->d_ring})
         okm = okm && p;
     if (!okm) {
         free_all(ctx);
@@ -352,7 +357,7 @@ static PParams particle_params(lb_ctx* ctx, int cur)
     pp.box_done = ctx->d_box_done;
     pp.need_hdr = ctx->d_need_hdr + (size_t)(cur ^ 1) * ctx->maxp;
     pp.need = ctx->d_need + (size_t)(cur ^ 1) * MAXS * MAXS * ctx->maxp;
-    pp.status = ctx->d_status; pp.np = ctx->np; pp.init = 0;
+    pp.status = ctx->d_status; pp.ring = ctx->d_ring; pp.np = ctx->np; pp.init = 0;
     pp.didt_mode = ctx->opt.didt_mode;
     pp.smax = 2 * (ctx->opt.max_semi + CUBE_MARGIN) + 2;
     return pp;
@@ -366,17 +371,20 @@ static void cube_of(const lb_particle& p, int& h, int& S)
     S = 2 * h + 2;
 }
 
-static bool cubes_overlap(const lb_particle& a, const lb_particle& b, const lb_box_desc& d)
+// Partners: particles of a box whose bounding cubes come within reach of each
+// other this step or the next (|x_b - x_a| < (S_a + S_b)/2 + 3 along every axis,
+// minimum image, positions of the same time); the relation the critical
+// blocks evaluate each step, from the same doubles in the same order for both
+// particles of a pair, so it is symmetric.
+static bool partners(const double xlo[3], int Slo, const double xhi[3], int Shi, const lb_box_desc& d)
 {
-    int ha, Sa, hb, Sb;
-    cube_of(a, ha, Sa);
-    cube_of(b, hb, Sb);
     const int L[3] = {d.nx, d.ny, d.nz};
+    const bool per[3] = {true, d.walls == 0, true};
+    const double reach = 0.5 * (double)(Slo + Shi) + 3.0;
     for (int k = 0; k < 3; ++k) {
-        const int oa = (int)std::floor(a.x[k]) - ha, ob = (int)std::floor(b.x[k]) - hb;
-        int dd = ((ob - oa) % L[k] + L[k]) % L[k];            // offset of b's origin from a's
-        const bool sep = (dd >= Sa) && (L[k] - dd >= Sb);     // disjoint both ways round
-        if (sep) return false;
+        double v = xhi[k] - xlo[k];
+        if (per[k]) v = v - (double)L[k] * std::floor(v / (double)L[k] + 0.5);
+        if (!(std::fabs(v) < reach)) return false;
     }
     return true;
 }
@@ -407,8 +415,26 @@ extern "C" lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particl
                 q.x[1] + std::max(q.semi[0], std::max(q.semi[1], q.semi[2])) >= d.ny - 1.5 || oy + S < 0)
                 return fail(ctx, LB_EINVAL, "particle touches a wall");
         }
-        for (int j = 0; j < i; ++j)
-            if (cubes_overlap(q, p[j], d)) return fail(ctx, LB_EOVERLAP, "bounding cubes of two particles overlap");
+    }
+    // particles whose cubes reach each other (partners): the box must leave room
+    // for both cubes side by side, and clusters are tracked over at most MAXPB
+    // particles of a box
+    {
+        std::vector<int> cnt(n, 0);
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                int hi_, Si, hj_, Sj;
+                cube_of(p[i], hi_, Si);
+                cube_of(p[j], hj_, Sj);
+                if (!partners(p[i].x, Si, p[j].x, Sj, d)) continue;
+                if (Si + Sj + 2 > d.nx || Si + Sj + 2 > d.nz || (!d.walls && Si + Sj + 2 > d.ny))
+                    return fail(ctx, LB_EINVAL, "box too small for two nearby particles' cubes");
+                ++cnt[i];
+                ++cnt[j];
+            }
+        for (int i = 0; i < n; ++i)
+            if (cnt[i] > MAXNB) return fail(ctx, LB_ECAPACITY, "a particle has more than MAXNB neighbours in reach");
+        if (n > MAXPB) return fail(ctx, LB_EINVAL, "at most 64 particles in a box");
     }
     ctx->parts[box].assign(p, p + n);
     // rebuild the global particle table, boxes in order
@@ -466,7 +492,24 @@ extern "C" lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particl
             }
             k.counter = h.counter;
             k.pbeg = h.pbeg; k.pcnt = h.pcnt;
+            k.lub_cut = h.lub_cut;
+            k.mu = h.mu;
+            k.nnb = 0;
+            const lb_box_desc& bd = ctx->desc[s.box];
+            for (int j = h.pbeg; j < h.pbeg + h.pcnt; ++j) {
+                if (j == i) continue;
+                const int lo = std::min(i, j), hi = std::max(i, j);
+                if (partners(pd[lo].x, pd[lo].S, pd[hi].x, pd[hi].S, bd) && k.nnb < MAXNB) k.nb[k.nnb++] = j;
+            }
         }
+        std::vector<double> ring(2 * RINGD * (size_t)ctx->maxp, 0.0);
+        for (int i = 0; i < idx; ++i)
+            for (int t = 0; t < 2; ++t) {
+                double* r = &ring[((size_t)i * 2 + t) * RINGD];
+                for (int a = 0; a < 3; ++a) { r[a] = pd[i].x[a]; r[3 + a] = pd[i].U[a]; }
+                for (int a = 0; a < 4; ++a) r[6 + a] = pd[i].q[a];
+            }
+        CK(cudaMemcpyAsync(ctx->d_ring, ring.data(), sizeof(double) * ring.size(), cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ctx->d_pk, pk.data(), sizeof(PartK) * ctx->maxp, cudaMemcpyHostToDevice, ctx->stream));
         const size_t nb = ctx->desc.size();
         std::vector<BoxDyn> dyn(2 * nb), pdyn(2 * (size_t)ctx->maxp);
@@ -536,6 +579,7 @@ static BndParams bnd_params(lb_ctx* ctx, int first, int cur)
     np.pdyn = ctx->d_pdyn + (size_t)cur * ctx->maxp;
     np.pk = ctx->d_pk; np.acc = ctx->d_acc; np.rows = ctx->d_rows;
     np.need = ctx->d_need + (size_t)cur * MAXS * MAXS * ctx->maxp;
+    np.need_hdr = ctx->d_need_hdr + (size_t)cur * ctx->maxp;
     np.status = ctx->d_status;
     np.src = ctx->fbuf[cur]; np.dst = ctx->fbuf[cur ^ 1];
     np.list_cap = ctx->list_cap; np.first = first;
@@ -861,7 +905,8 @@ extern "C" lb_status lb_get_links(lb_ctx* ctx, int32_t box, int32_t particle, in
     }
     CK(cudaDeviceSynchronize());
     const int p = ctx->hbox[box].pbeg + particle;
-    CK(launch_links(ctx->d_pd, ctx->d_rows, ctx->d_boxes, p, ctx->d_links, ctx->links_cap, ctx->d_count, ctx->stream));
+    CK(launch_links(ctx->d_pd, ctx->d_pk, ctx->d_rows, ctx->d_boxes, p, ctx->d_links, ctx->links_cap, ctx->d_count,
+                    ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     int n = 0;
     CK(cudaMemcpy(&n, ctx->d_count, sizeof(int), cudaMemcpyDeviceToHost));

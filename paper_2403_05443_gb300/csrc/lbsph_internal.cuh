@@ -54,6 +54,9 @@ constexpr int MAXC = 4;             // particles a lattice tile may touch (field
 constexpr int BBLOCK = 256;         // threads per block of the boundary kernel
 constexpr int CBLOCK = 256;         // threads per block of the critical particle kernel
 constexpr int MAXAMB = 512;         // near-surface nodes settled by the exact FP64 test per step
+constexpr int MAXNB = 8;            // partners of a particle: others whose bounding cubes come within reach
+constexpr int MAXPB = 64;           // particles of one box when any of them has partners (cluster masks)
+constexpr int RINGD = 10;           // doubles per particle and step parity in the pose ring: x, U, q
 
 // accumulator layout (int64 per particle); d = fixed-point f* of a link (x, b),
 // m = cube-local position of x
@@ -121,6 +124,7 @@ struct BoxDev {
     int pbeg, pcnt;                 // particles of this box
     long long nwall;                // wall nodes (2 nx nz when walls)
     float scale, inv_scale;         // 16-bit storage scale (1 for FP32 / BF16)
+    double lub_cut, mu;             // lubrication cut-off gap (0: none), dynamic viscosity rho0 (tau - 1/2) / 3
     unsigned dq_m, dy_m;            // q / nxq and row / ny as __umulhi(n, m) >> s (div_magic)
     int dq_s, dy_s;
     int rowwarp;                    // 1: nxq divides 32, every row lies within one warp's 32 quads
@@ -183,6 +187,12 @@ struct PartK {
     float body[3];
     int counter;                    // counter body force on
     int pbeg, pcnt;                 // particles of the box
+    double lub_cut, mu;             // the box's lubrication cut-off and viscosity
+    // partners: the other particles of the box whose bounding cubes come within
+    // reach of this one's (symmetric); their boundary nodes, links, covered and
+    // uncovered nodes interleave with this particle's
+    int nnb;
+    int nb[MAXNB];
 };
 
 // cube of a particle's redo mask: origin wrapped into the box, side
@@ -249,6 +259,7 @@ struct PParams {
     NeedHdr* need_hdr;              // per particle: redo mask of the next step (written)
     uint64_t* need;                 // per particle MAXS*MAXS words (written)
     unsigned* status;
+    double* ring;                   // [np][2][RINGD]: x, U, q at time t in slot t & 1 (partners read it)
     int np;
     int init;                       // 1: build maps / moments only (no solve, no pose update)
     int didt_mode;
@@ -272,6 +283,7 @@ struct BndParams {
     long long* acc;                 // np * NACC
     const uint64_t* rows;           // np * 2 * MAXS*MAXS words (both ring slots)
     const uint64_t* need;           // per particle MAXS*MAXS words: the nodes to redo
+    const NeedHdr* need_hdr;        // per particle: the cube of its redo mask (partners' nodes)
     unsigned* status;
     const void* src;
     void* dst;                      // the lattice buffer of this step (written directly)

@@ -67,6 +67,134 @@ __device__ __forceinline__ unsigned long long abs_bits(double x)
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
+// Minimum image of a displacement along a periodic axis of length L.
+__device__ __forceinline__ double min_image_d(double d, int L, bool periodic)
+{
+    return periodic ? d - (double)L * floor(d / (double)L + 0.5) : d;
+}
+
+// Centre-to-surface distance of an ellipsoid along the unit vector n:
+// (n^T A n)^(-1/2), A = R diag(1/s^2) R^T (Eq. ellipsoidsurface), i.e. the body
+// components of n, (R^T n)_m, weighted by 1/s_m^2.
+__device__ __forceinline__ double radius_along(const double* q, const double* semi, const double n[3])
+{
+    const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+    const double R[3][3] = {{1.0 - 2.0 * (q2 * q2 + q3 * q3), 2.0 * (q1 * q2 - q0 * q3), 2.0 * (q1 * q3 + q0 * q2)},
+                            {2.0 * (q1 * q2 + q0 * q3), 1.0 - 2.0 * (q1 * q1 + q3 * q3), 2.0 * (q2 * q3 - q0 * q1)},
+                            {2.0 * (q1 * q3 - q0 * q2), 2.0 * (q2 * q3 + q0 * q1), 1.0 - 2.0 * (q1 * q1 + q2 * q2)}};
+    double v = 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const double b = R[0][m] * n[0] + R[1][m] * n[1] + R[2][m] * n[2];
+        v += b * b / (semi[m] * semi[m]);
+    }
+    return 1.0 / sqrt(v);
+}
+
+// Lubrication correction on body `lo` from body `hi` (the opposite acts on hi):
+// with d the minimum image of x_hi - x_lo, n = d/|d|, radii R = (n^T A n)^(-1/2)
+// of both bodies along n and the gap h = |d| - R_lo - R_hi along the line of
+// centres, below the cut-off h_c the squeeze force of two spheres of those radii
+// that the lattice does not resolve, -6 pi mu R_e^2 (1/h - 1/h_c) (n.(U_lo -
+// U_hi)) n, R_e = R_lo R_hi / (R_lo + R_hi), h >= 0.1, the coefficient at most
+// the reduced mass (an explicit update stays stable).  Velocities and
+// orientations of time t; ring entries x[3], U[3], q[4].
+constexpr double LUB_H_MIN = 0.1;
+__device__ __forceinline__ void lubrication_pair(const double* rlo, const double* semi_lo, double M_lo,
+                                                 const double* rhi, const double* semi_hi, double M_hi,
+                                                 const int L[3], const bool per[3], double mu, double h_cut,
+                                                 double f[3])
+{
+    double d[3], n[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = min_image_d(rhi[k] - rlo[k], L[k], per[k]);
+    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n[k] = d[k] / r;
+    const double Rl = radius_along(rlo + 6, semi_lo, n), Rh = radius_along(rhi + 6, semi_hi, n);
+    const double h = r - Rl - Rh;
+    f[0] = f[1] = f[2] = 0.0;
+    if (!(h < h_cut)) return;
+    const double hh = h > LUB_H_MIN ? h : LUB_H_MIN;
+    const double Re = Rl * Rh / (Rl + Rh);
+    double k = 6.0 * M_PI * mu * Re * Re * (1.0 / hh - 1.0 / h_cut);
+    const double kmax = M_lo * M_hi / (M_lo + M_hi);
+    if (k > kmax) k = kmax;
+    const double vn = n[0] * (rlo[3] - rhi[3]) + n[1] * (rlo[4] - rhi[4]) + n[2] * (rlo[5] - rhi[5]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[c] = -k * vn * n[c];
+}
+
+// Component jq of q' = qt(Wm) q (Eq. qnplus0-1, rotation by the mean angular
+// velocity Wm over one step), for a warp whose lanes all hold Wm and q.
+__device__ __forceinline__ double quat_step_component(const double Wm[3], const double* q, int jq)
+{
+    const double th2 = Wm[0] * Wm[0] + Wm[1] * Wm[1] + Wm[2] * Wm[2];
+    double qt[4];
+    if (th2 < 1e-4) {
+        // cos(th/2) and sin(th/2)/th by their Taylor series (th < 0.01: error < 1e-20)
+        const double x2 = 0.25 * th2;
+        const double c = 1.0 - x2 * (0.5 - x2 * (1.0 / 24.0 - x2 * (1.0 / 720.0)));
+        const double sc = 0.5 * (1.0 - x2 * (1.0 / 6.0 - x2 * (1.0 / 120.0 - x2 * (1.0 / 5040.0))));
+        qt[0] = c; qt[1] = sc * Wm[0]; qt[2] = sc * Wm[1]; qt[3] = sc * Wm[2];
+    } else {
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(0.5 * th, &sn, &cs);
+        sn /= th;
+        qt[0] = cs; qt[1] = sn * Wm[0]; qt[2] = sn * Wm[1]; qt[3] = sn * Wm[2];
+    }
+    // sum_m +-qt_m q_(m xor jq), the sign applied by flipping the sign bit
+    constexpr unsigned NEG = (1u << 1) | (1u << 2) | (1u << 3) | (1u << 7) | (1u << 9) | (1u << 14);
+    double qn = 0.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const unsigned long long sgn = (unsigned long long)((NEG >> (jq * 4 + m)) & 1u) << 63;
+        const double qs = __longlong_as_double(__double_as_longlong(qt[m]) ^ (long long)sgn);
+        qn = fma(qs, q[m ^ jq], qn);
+    }
+    return qn;
+}
+
+// Solution of the 6x6 system A x = b by Gauss-Jordan elimination with partial
+// pivoting, one warp: lane j < 6 holds column j of A, lane 6 holds b (col[i] =
+// row i); on return lane 6 holds x.  Returns false if a pivot vanishes.
+__device__ __forceinline__ bool gj_solve6_warp(double col[6], int lane)
+{
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        int piv = k;
+        if (lane == k) {
+            unsigned long long best = abs_bits(col[k]);
+#pragma unroll
+            for (int i = k + 1; i < 6; ++i) {
+                const unsigned long long bi = abs_bits(col[i]);
+                if (bi > best) { best = bi; piv = i; }
+            }
+        }
+        piv = __shfl_sync(0xffffffffu, piv, k);
+        double rowk = col[k], rowp = col[k];
+#pragma unroll
+        for (int i = k + 1; i < 6; ++i)
+            if (i == piv) rowp = col[i];
+#pragma unroll
+        for (int i = k + 1; i < 6; ++i)
+            if (i == piv) col[i] = rowk;
+        col[k] = rowp;
+        const double pv = __shfl_sync(0xffffffffu, col[k], k);
+        ok = ok && (pv != 0.0);
+        col[k] *= 1.0 / pv;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            if (i == k) continue;
+            const double fi = __shfl_sync(0xffffffffu, col[i], k);
+            col[i] -= fi * col[k];
+        }
+    }
+    return ok;
+}
+
 __device__ __forceinline__ long long warp_sum_ll(long long v)
 {
     for (int o = 16; o > 0; o >>= 1) v += (long long)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
@@ -112,6 +240,8 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
     __shared__ float s_e[3][3], s_inv[3], s_ro[3];
     __shared__ int s_o[3], s_nsolid, s_namb;
     __shared__ int s_amb[MAXAMB];
+    __shared__ double s_FL[3], s_fpair[MAXPB][3];   // lubrication: total and per other particle of the box
+    __shared__ int s_nnb, s_nbl[MAXNB];
 
     // ---- stage the state, the snapshot (so that every field not updated
     // below carries over) and this step's accumulators; clear the accumulators
@@ -137,6 +267,60 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
         else if (tid < 6) S.Text[tid - 3] = io_ft[tid];
         __syncthreads();
     }
+    // ---- partners for the next iteration and the lubrication forces of this
+    // one, from the poses of time t in the ring (slot t & 1, which no crit
+    // block writes during this iteration): the same inputs on both sides of
+    // every pair, so the partner relation is symmetric and the pair forces are
+    // exactly opposite; warp 1, while warp 0 prepares the solve
+    if (tid == 0) { s_FL[0] = s_FL[1] = s_FL[2] = 0.0; s_nnb = 0; }
+    __syncthreads();
+    if (!P.init && K.pcnt > 1 && warp == 1) {
+        const int t = (int)(S.step & 1);
+        const int Lb[3] = {K.nx, K.ny, K.nz};
+        const bool per[3] = {true, !K.walls, true};
+        const bool lub = K.lub_cut > 0.0;
+        for (int j0 = 0; j0 < K.pcnt; j0 += 32) {
+            const int j = j0 + lane;
+            const int q = K.pbeg + j;
+            bool near = false;
+            double fp[3] = {0.0, 0.0, 0.0};
+            if (j < K.pcnt && q != p) {
+                const int lo = min(p, q), hi = max(p, q);
+                double rl[RINGD], rh[RINGD];
+                for (int e = 0; e < RINGD; ++e) {
+                    rl[e] = __ldcg(P.ring + ((size_t)lo * 2 + t) * RINGD + e);
+                    rh[e] = __ldcg(P.ring + ((size_t)hi * 2 + t) * RINGD + e);
+                }
+                const double reach = 0.5 * (double)(P.pd[lo].S + P.pd[hi].S) + 3.0;
+                near = true;
+                for (int k = 0; k < 3; ++k)
+                    near = near && fabs(min_image_d(rh[k] - rl[k], Lb[k], per[k])) < reach;
+                if (near && lub) {
+                    double f[3];
+                    lubrication_pair(rl, P.pd[lo].semi, P.pd[lo].M, rh, P.pd[hi].semi, P.pd[hi].M, Lb, per, K.mu,
+                                     K.lub_cut, f);
+                    const double sg = (p == lo) ? 1.0 : -1.0;
+                    for (int c = 0; c < 3; ++c) fp[c] = sg * f[c];
+                }
+            }
+            if (j < MAXPB)
+                for (int c = 0; c < 3; ++c) s_fpair[j][c] = fp[c];
+            const unsigned bal = __ballot_sync(0xffffffffu, near);
+            if (near) {
+                const int slot = s_nnb + __popc(bal & ((1u << lane) - 1u));
+                if (slot < MAXNB) s_nbl[slot] = q;
+            }
+            __syncwarp();
+            if (lane == 0) s_nnb += __popc(bal);
+            __syncwarp();
+        }
+        if (lane < 3 && lub) {
+            double a = 0.0;
+            for (int j = 0; j < K.pcnt && j < MAXPB; ++j) a += s_fpair[j][lane];    // in index order
+            s_FL[lane] = a;
+        }
+    }
+    __syncthreads();
     const int slot_new = P.init ? 0 : (S.slot ^ 1);
     uint64_t* s_rows = s_maps + slot_new * P.smax * P.smax;          // map t+1, built below
     const uint64_t* s_old = s_maps + (P.init ? slot_new : S.slot) * P.smax * P.smax;   // map t
@@ -194,14 +378,64 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
             // force lanes: M U_k; torque lanes: (I Omega)_k
             const double m0 = isT ? S.Icur[k * 3] : S.M, v0 = isT ? S.W[0] : S.U[k];
             const double m1 = isT ? S.Icur[k * 3 + 1] : 0.0, m2 = isT ? S.Icur[k * 3 + 2] : 0.0;
-            rhs = m0 * v0 + m1 * S.W[1] + m2 * S.W[2] + ft0 + (isT ? S.Text[k] : S.Fext[k]) + dpl;
+            rhs = m0 * v0 + m1 * S.W[1] + m2 * S.W[2] + ft0 + (isT ? S.Text[k] : S.Fext[k] + s_FL[k]) + dpl;
         }
         const int row = lane < 6 ? lane : 5;
         double x6 = 0.0;
 #pragma unroll
         for (int j = 0; j < 6; ++j) x6 += S.Ainv[row * 6 + j] * __shfl_sync(0xffffffffu, rhs, j);
-        // F = F0 - zeta_FU U' - zeta_FOmega Omega' (Eq. Fsplit), T likewise (Eq. Tsplit)
-        double xs[6], ft = ft0;
+        if (P.didt_mode == 2) {
+            // predictor-corrector for I(t+1): the solution above (I(t+1) ~ I(t) +
+            // dI/dt) predicts Omega(t+1), hence the orientation q_p by Eq.
+            // qnplus0-1 with the mean angular velocity; the system is solved
+            // again with I(t+1) = R(q_p) I_body R(q_p)^T (Eq. Irot)
+            double Wp[3], qp[4];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Wp[a] = 0.5 * (S.W[a] + __shfl_sync(0xffffffffu, x6, 3 + a));
+            const double qpl = quat_step_component(Wp, S.q, lane & 3);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) qp[m] = __shfl_sync(0xffffffffu, qpl, m);
+            double R[3][3];
+            R[0][0] = 1.0 - 2.0 * (qp[2] * qp[2] + qp[3] * qp[3]);
+            R[1][1] = 1.0 - 2.0 * (qp[1] * qp[1] + qp[3] * qp[3]);
+            R[2][2] = 1.0 - 2.0 * (qp[1] * qp[1] + qp[2] * qp[2]);
+            R[0][1] = 2.0 * (qp[1] * qp[2] - qp[0] * qp[3]);
+            R[1][0] = 2.0 * (qp[1] * qp[2] + qp[0] * qp[3]);
+            R[0][2] = 2.0 * (qp[1] * qp[3] + qp[0] * qp[2]);
+            R[2][0] = 2.0 * (qp[1] * qp[3] - qp[0] * qp[2]);
+            R[1][2] = 2.0 * (qp[2] * qp[3] - qp[0] * qp[1]);
+            R[2][1] = 2.0 * (qp[2] * qp[3] + qp[0] * qp[1]);
+            // lane j < 6: column j of the corrected matrix; lane 6: the right-hand side
+            double col[6];
+            const int jc = lane < 7 ? lane : 6;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const double b = __shfl_sync(0xffffffffu, rhs, i);
+                double v = 0.0;
+                if (jc < 6) {
+                    v = S.zeta[i * 6 + jc];
+                    if (i == jc && i < 3) v += S.M;
+                    if (i >= 3 && jc >= 3) {
+                        const int a = i - 3, c = jc - 3;
+                        v += R[a][0] * S.Ib[0] * R[c][0] + R[a][1] * S.Ib[1] * R[c][1] + R[a][2] * S.Ib[2] * R[c][2];
+                    }
+                } else {
+                    v = b;
+                }
+                col[i] = v;
+            }
+            if (!gj_solve6_warp(col, lane) && lane == 0) atomicOr(P.status, ST_NAN);
+            double xr = 0.0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const double v = __shfl_sync(0xffffffffu, col[i], 6);
+                if (row == i) xr = v;
+            }
+            x6 = xr;
+        }
+        // F = F0 - zeta_FU U' - zeta_FOmega Omega' (Eq. Fsplit) + the lubrication
+        // force, T likewise (Eq. Tsplit)
+        double xs[6], ft = isT ? ft0 : ft0 + s_FL[k];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
             xs[j] = __shfl_sync(0xffffffffu, x6, j);
@@ -210,32 +444,7 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
         // Eq. posupdate, Eq. qnplus0-1: rotation by Omega_mid = (Omega + Omega') / 2
         double Wm[3];
         for (int a = 0; a < 3; ++a) Wm[a] = 0.5 * (S.W[a] + xs[3 + a]);
-        const double th2 = Wm[0] * Wm[0] + Wm[1] * Wm[1] + Wm[2] * Wm[2];
-        double qt[4];
-        if (th2 < 1e-4) {
-            // cos(th/2) and sin(th/2)/th by their Taylor series (th < 0.01: error < 1e-20)
-            const double x2 = 0.25 * th2;
-            const double c = 1.0 - x2 * (0.5 - x2 * (1.0 / 24.0 - x2 * (1.0 / 720.0)));
-            const double sc = 0.5 * (1.0 - x2 * (1.0 / 6.0 - x2 * (1.0 / 120.0 - x2 * (1.0 / 5040.0))));
-            qt[0] = c; qt[1] = sc * Wm[0]; qt[2] = sc * Wm[1]; qt[3] = sc * Wm[2];
-        } else {
-            const double th = sqrt(th2);
-            double sn, cs;
-            sincos(0.5 * th, &sn, &cs);
-            sn /= th;
-            qt[0] = cs; qt[1] = sn * Wm[0]; qt[2] = sn * Wm[1]; qt[3] = sn * Wm[2];
-        }
-        // q' = qt q, component j on lane j: sum_m +-qt_m q_(m xor j), the sign
-        // applied by flipping the sign bit
-        constexpr unsigned NEG = (1u << 1) | (1u << 2) | (1u << 3) | (1u << 7) | (1u << 9) | (1u << 14);
-        const int jq = lane & 3;
-        double qn = 0.0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const unsigned long long sgn = (unsigned long long)((NEG >> (jq * 4 + m)) & 1u) << 63;
-            const double qs = __longlong_as_double(__double_as_longlong(qt[m]) ^ (long long)sgn);
-            qn = fma(qs, S.q[m ^ jq], qn);
-        }
+        const double qn = quat_step_component(Wm, S.q, lane & 3);
         // body x axis at t (the squirmer's axis for the next bounce-back):
         // R_k0 = base + 2 (qa qb + s qc qd)
         const double* q = S.q;
@@ -433,6 +642,11 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
         for (int k = 0; k < 3; ++k) S.o[k] = s_o[k];
         S.nsolid = s_nsolid;
         if (!P.init) S.step += 1;
+        if (!P.init && K.pcnt > 1) {
+            K.nnb = min(s_nnb, MAXNB);
+            for (int j = 0; j < K.nnb; ++j) K.nb[j] = s_nbl[j];
+            if (s_nnb > MAXNB) atomicOr(P.status, ST_CAPACITY);
+        }
         if (Sd > nx || Sd > nz || (py && Sd > ny)) atomicOr(P.status, ST_CAPACITY);
     }
     __syncthreads();
@@ -446,6 +660,10 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
         for (int e = tid; e < (int)(sizeof(PartK) / 4); e += CBLOCK) kd[e] = ks[e];
         if (io_rec)
             for (int e = tid; e < RECD; e += CBLOCK) io_rec[e] = S.rec[e];
+        // the pose of time t+1 for the partners of the next iteration
+        if (!P.init && tid < RINGD)
+            P.ring[((size_t)p * 2 + (S.step & 1)) * RINGD + tid] =
+                tid < 3 ? S.x[tid] : (tid < 6 ? S.U[tid - 3] : S.q[tid - 6]);
     }
     // ---- the box's uniform terms of the next collision: body force with the
     // counter force over the fluid nodes, and the mass put back
@@ -520,6 +738,33 @@ __device__ __forceinline__ int c_of(unsigned long long packed, int b) { return (
 //     Gauss-Jordan elimination with partial pivoting, one column per lane.
 constexpr int NSUM = 27;            // zeta0: FU 6, FOmega 9, TOmega 6; sum w n c 3; sum w m x c 3
 // particle p; ABLOCK threads
+// Nodes of row (my, mz) of particle p's current cube that are solid in a
+// partner's current map (after the critical blocks of the last iteration),
+// as bits of that row.
+__device__ __forceinline__ uint64_t partner_row_mask(const PartDev* pd, const PartK* pk, const uint64_t* rows, int p,
+                                                     const int o[3], int nnb, const int L[3], int my, int mz,
+                                                     uint64_t maskS)
+{
+    uint64_t pm = 0;
+    for (int j = 0; j < nnb; ++j) {
+        const int q = __ldcg(&pk[p].nb[j]);
+        const PartDev& Gq = pd[q];
+        const int Sq = Gq.S;
+        int dd[3];
+        for (int k = 0; k < 3; ++k) {
+            int v = (Gq.o[k] - o[k]) % L[k];
+            if (v < -L[k] / 2) v += L[k];
+            if (v >= (L[k] + 1) / 2) v -= L[k];
+            dd[k] = v;                              // partner origin - this origin
+        }
+        const int qy = my - dd[1], qz = mz - dd[2];
+        if (qy < 0 || qy >= Sq || qz < 0 || qz >= Sq || dd[0] <= -64 || dd[0] >= 64) continue;
+        const uint64_t w = __ldcg(rows + ((long long)q * 2 + Gq.slot) * (MAXS * MAXS) + qz * Sq + qy);
+        pm |= dd[0] >= 0 ? (w << dd[0]) : (w >> -dd[0]);
+    }
+    return pm & maskS;
+}
+
 __device__ __forceinline__ void aux_block(const PParams& P, int p)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -570,7 +815,20 @@ __device__ __forceinline__ void aux_block(const PParams& P, int p)
         const uint64_t* rn = P.rows + ((long long)p * 2 + S.slot) * (MAXS * MAXS);
         for (int r = tid; r < Sd * Sd; r += ABLOCK) s_new[r] = __ldcg(rn + r);
     }
+    // nodes solid in a partner's new map, in this cube's rows (its links and
+    // the drag matrices count fluid nodes only); a node solid in both maps
+    // means the bodies overlap
+    uint64_t* s_pm = s_new + P.smax * P.smax;
+    const int nnb = __ldcg(&P.pk[p].nnb);
+    if (nnb > 0) {
+        const int Lb[3] = {B.nx, B.ny, B.nz};
+        for (int r = tid; r < Sd * Sd; r += ABLOCK)
+            s_pm[r] = partner_row_mask(P.pd, P.pk, P.rows, p, S.o, nnb, Lb, r % Sd, r / Sd, maskS);
+    }
     __syncthreads();
+    if (nnb > 0)
+        for (int r = tid; r < Sd * Sd; r += ABLOCK)
+            if (s_new[r] & s_pm[r]) atomicOr(P.status, ST_OVERLAP);
 
     // ---- integer link sums of the new map, one cube row per thread; the
     // direction loop is unrolled so that every c_b is a constant and the 27
@@ -585,7 +843,7 @@ __device__ __forceinline__ void aux_block(const PParams& P, int p)
             const int my = r % Sd, mz = r / Sd;
             const int Yu = S.o[1] + my;
             if (walls && (Yu <= 0 || Yu >= ny - 1)) continue;
-            const uint64_t fluid = ~s_new[r] & maskS;
+            const uint64_t fluid = ~s_new[r] & (nnb > 0 ? ~s_pm[r] : ~0ull) & maskS;
 #pragma unroll
             for (int b = 1; b < Q; ++b) {
                 const int cx = cx_of(b), cy = cy_of(b), cz = cz_of(b);
@@ -641,7 +899,7 @@ __device__ __forceinline__ void aux_block(const PParams& P, int p)
             const int my = r % Sd, mz = r / Sd;
             const int Yu = S.o[1] + my;
             if (walls && (Yu <= 0 || Yu >= ny - 1)) continue;
-            const uint64_t fluid = ~s_new[r] & maskS;
+            const uint64_t fluid = ~s_new[r] & (nnb > 0 ? ~s_pm[r] : ~0ull) & maskS;
 #pragma unroll 1
             for (int b = 1; b < Q; ++b) {
                 const int cx = c_of(PX, b), cy = c_of(PY, b), cz = c_of(PZ, b);
@@ -698,7 +956,7 @@ __device__ __forceinline__ void aux_block(const PParams& P, int p)
     } else if (warp == 2 && lane < 9) {
         // its rate (Eq. Irotdiff): [Omega]x I - I [Omega]x, or the finite difference
         const int i = lane / 3, j = lane % 3;
-        if (P.didt_mode == 0) {
+        if (P.didt_mode != 1) {
             const double* W = S.W;
             const double Wk[9] = {0, -W[2], W[1], W[2], 0, -W[0], -W[1], W[0], 0};
             s_dI[lane] = Wk[i * 3] * s_I[j] + Wk[i * 3 + 1] * s_I[3 + j] + Wk[i * 3 + 2] * s_I[6 + j] -

@@ -42,12 +42,14 @@ __global__ void __launch_bounds__(ABLOCK) particle_aux_kernel(const __grid_const
 
 // Boundary links of one particle's current map, compacted in (row, direction,
 // x) order: a block-wide count, an exclusive scan, then the writes.
-__global__ void __launch_bounds__(PBLOCK) links_kernel(const PartDev* pd, const uint64_t* rows_all,
+__global__ void __launch_bounds__(PBLOCK) links_kernel(const PartDev* pd, const PartK* pk, const uint64_t* rows_all,
                                                       const BoxDev* boxes, int p, int* out, int cap,
                                                       int* count)
 {
     const PartDev& S = pd[p];
     const BoxDev& B = boxes[S.box];
+    const int nnb = pk[p].nnb;
+    const int Lb[3] = {B.nx, B.ny, B.nz};
     const uint64_t* rows = rows_all + ((long long)p * 2 + S.slot) * (MAXS * MAXS);
     const int Sd = S.S;
     const uint64_t maskS = Sd >= 64 ? ~0ull : ((1ull << Sd) - 1ull);
@@ -72,6 +74,8 @@ __global__ void __launch_bounds__(PBLOCK) links_kernel(const PartDev* pd, const 
             const int cbx = cx_of(b);
             const uint64_t sh = cbx == 1 ? (nb >> 1) : (cbx == -1 ? (nb << 1) : nb);
             uint64_t L = ~rows[r] & sh & maskS;
+            // a node solid in a partner is no fluid end of a link
+            if (L && nnb > 0) L &= ~partner_row_mask(pd, pk, rows_all, p, S.o, nnb, Lb, my, mz, maskS);
             while (L) {
                 const int mx = __ffsll((long long)L) - 1;
                 L &= L - 1;
@@ -232,7 +236,7 @@ cudaError_t launch_particles(const PParams& p, cudaStream_t s)
 {
     if (p.np <= 0) return cudaSuccess;
     const size_t smem = 2ull * p.smax * p.smax * sizeof(uint64_t);
-    if (smem > 48 * 1024) {
+    if (smem > 0) {        // static + dynamic may pass the 48 KB default: always opt in
         const cudaError_t e = cudaFuncSetAttribute(particle_crit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -243,8 +247,8 @@ cudaError_t launch_particles(const PParams& p, cudaStream_t s)
 cudaError_t launch_particles_aux(const PParams& p, cudaStream_t s)
 {
     if (p.np <= 0) return cudaSuccess;
-    const size_t smem = (size_t)p.smax * p.smax * sizeof(uint64_t);
-    if (smem > 48 * 1024) {
+    const size_t smem = 2ull * p.smax * p.smax * sizeof(uint64_t);     // the new map, the partners' solids
+    if (smem > 0) {        // static + dynamic may pass the 48 KB default: always opt in
         const cudaError_t e = cudaFuncSetAttribute(particle_aux_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -252,10 +256,10 @@ cudaError_t launch_particles_aux(const PParams& p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_links(const PartDev* pd, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
+cudaError_t launch_links(const PartDev* pd, const PartK* pk, const uint64_t* rows, const BoxDev* boxes, int p, int* out,
                          int cap, int* count, cudaStream_t s)
 {
-    links_kernel<<<1, PBLOCK, 0, s>>>(pd, rows, boxes, p, out, cap, count);
+    links_kernel<<<1, PBLOCK, 0, s>>>(pd, pk, rows, boxes, p, out, cap, count);
     return cudaGetLastError();
 }
 

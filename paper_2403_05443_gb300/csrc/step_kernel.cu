@@ -83,10 +83,45 @@ __device__ __forceinline__ bool grid_barrier(const StepParams& SP)
     return s_ok != 0;
 }
 
+// The cluster of particle p for this iteration: the particles reachable from p
+// through the partner lists (symmetric) that the critical blocks of the last
+// iteration wrote.  A particle's boundary blocks read its partners' maps and
+// add to their accumulators, so no critical block of a cluster may start before
+// every item of the cluster is done.  Returns the lowest index (the cluster's
+// counter) and the members as a mask over the box's particles (at most MAXPB
+// when any particle has partners).  One thread.
+__device__ __forceinline__ int cluster_of(const PartK* pk, int p, unsigned long long& members, int& size)
+{
+    const int nnb0 = __ldcg(&pk[p].nnb);
+    if (nnb0 == 0) {
+        members = 0;
+        size = 1;
+        return p;
+    }
+    const int pbeg = __ldcg(&pk[p].pbeg);
+    unsigned long long seen = 1ull << (p - pbeg), todo = seen;
+    while (todo) {
+        const int j = __ffsll((long long)todo) - 1;
+        todo &= todo - 1;
+        const int q = pbeg + j;
+        const int n = min(__ldcg(&pk[q].nnb), MAXNB);
+        for (int k = 0; k < n; ++k) {
+            const int r = __ldcg(&pk[q].nb[k]) - pbeg;
+            if (r < 0 || r >= MAXPB) continue;
+            const unsigned long long bit = 1ull << r;
+            if (!(seen & bit)) { seen |= bit; todo |= bit; }
+        }
+    }
+    members = seen;
+    size = __popcll(seen);
+    return pbeg + __ffsll((long long)seen) - 1;
+}
+
 template <class St>
 __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__ StepParams SP)
 {
-    __shared__ int s_last, s_rank;
+    __shared__ int s_last, s_rank, s_root;
+    __shared__ unsigned long long s_members;
     const int tid = threadIdx.x;
     const int gx = SP.gx;
     const int npart = SP.np * (gx + 1);
@@ -125,13 +160,34 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
             else aux_block(PP, p);                 // a no-op if it already ran for this pose
             __threadfence();
             __syncthreads();
-            if (tid == 0) s_last = atomicAdd(SP.sync + SYNC_PART + p, 1u) == (unsigned)gx;
+            if (tid == 0) {
+                // the last item of the particle's cluster runs the cluster's
+                // critical blocks (a single particle: its own), in index order
+                unsigned long long mem;
+                int size;
+                const int root = cluster_of(PP.pk, p, mem, size);
+                s_root = root;
+                s_members = mem;
+                s_last = atomicAdd(SP.sync + SYNC_PART + root, 1u) == (unsigned)(size * (gx + 1) - 1);
+            }
             __syncthreads();
             if (s_last) {
                 __threadfence();
-                if (tid == 0) SP.sync[SYNC_PART + p] = 0;
-                const size_t io = (size_t)it * SP.np + p;
-                crit_block(PP, p, SP.io_ft ? SP.io_ft + io * 6 : nullptr, SP.io_rec ? SP.io_rec + io * RECD : nullptr);
+                const int root = s_root;
+                if (tid == 0) SP.sync[SYNC_PART + root] = 0;
+                unsigned long long mem = s_members;
+                const int pbeg = root - (mem ? __ffsll((long long)mem) - 1 : 0);
+                int q = root;
+                do {
+                    if (mem) {
+                        q = pbeg + __ffsll((long long)mem) - 1;
+                        mem &= mem - 1;
+                    }
+                    const size_t io = (size_t)it * SP.np + q;
+                    crit_block(PP, q, SP.io_ft ? SP.io_ft + io * 6 : nullptr,
+                               SP.io_rec ? SP.io_rec + io * RECD : nullptr);
+                    __syncthreads();
+                } while (mem);
             }
             __syncthreads();
         }
@@ -166,7 +222,7 @@ static cudaError_t launch_step_t(const StepParams& sp, size_t smem, cudaStream_t
     // co-resident blocks for this device and dynamic shared memory size (one
     // cheap occupancy query per launch: a process may drive several devices)
     cudaError_t e;
-    if (smem > 48 * 1024) {
+    if (smem > 0) {        // static + dynamic may pass the 48 KB default: always opt in
         e = cudaFuncSetAttribute(step_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -32,7 +32,7 @@ class BoxDesc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("tau", C.c_double), ("rho0", C.c_double), ("body_force", C.c_double * 3),
                 ("counter_force", C.c_int32), ("walls", C.c_int32),
-                ("wall_u_lo", C.c_double * 3), ("wall_u_hi", C.c_double * 3)]
+                ("wall_u_lo", C.c_double * 3), ("wall_u_hi", C.c_double * 3), ("lub_cut", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -116,6 +116,7 @@ def _box_struct(d: dict) -> BoxDesc:
     b.counter_force, b.walls = int(d.get("counter_force", 0)), int(d.get("walls", 0))
     b.wall_u_lo[:] = list(d.get("wall_u_lo", (0.0, 0.0, 0.0)))
     b.wall_u_hi[:] = list(d.get("wall_u_hi", (0.0, 0.0, 0.0)))
+    b.lub_cut = float(d.get("lub_cut", 0.0))
     return b
 
 

@@ -49,35 +49,121 @@ def geom_of(a, b, tau, Ledge, e, rho0=1.0):
             float(rho0)]
 
 
-def measure_mobility(samples, steps: int, force: float = 1e-4, device: int = 0, batch: int = 64):
+def _ft_of(smp, k, force, torque):
+    unit = np.eye(3)[k % 3]
+    fe = force * unit if k < 3 else np.zeros(3)
+    te = torque * unit if k >= 3 else np.zeros(3)
+    return fe, te
+
+
+def measure_mobility(samples, max_steps: int, force=1e-4, torque=None, device: int = 0, batch: int = 64,
+                     check_every: int = 0, tol: float = 1e-5, checks: int = 3, warm_fluid: bool = False,
+                     history=None):
     """Mobility matrices M[n, 6, 6] of the samples (dicts of
-    lb_inputs.resistance_samples, all with the same box edge), from `steps`
-    iterations of the LB method in batched contexts of 6 boxes per sample."""
+    lb_inputs.resistance_samples, all with the same box edge) from the LB
+    method, in batched contexts of 6 boxes per sample (box k: unit force or
+    torque along axis k).  force / torque: a number, or a function of the
+    sample (default torque: force * b).
+
+    check_every = 0: `max_steps` iterations.  Otherwise each run goes to steady
+    state: every check_every iterations the (U, b Omega) of every box is
+    compared with the last check's, and a batch stops once every box has
+    changed by less than tol (relative) at `checks` consecutive checks, or at
+    max_steps (history, a list, collects (step, largest change, median change)
+    of every check).  warm_fluid: each box starts from the lattice fluid's own steady
+    flow under its particle's force (lb_stokes_field, lb_init_fluid), the
+    particles at rest, which leaves only the particle's and the near field's
+    adjustment to relax.  Returns (M, steps used per sample, converged per
+    sample)."""
+    torch = _torch()
     out = np.zeros((len(samples), 6, 6))
+    used = np.zeros(len(samples), np.int64)
+    conv = np.zeros(len(samples), bool)
+    fofs = force if callable(force) else (lambda smp: force)
+    tofs = torque if callable(torque) else ((lambda smp: torque) if torque is not None
+                                             else (lambda smp: fofs(smp) * smp["b"]))
     for s0 in range(0, len(samples), batch):
         chunk = samples[s0:s0 + batch]
         boxes, parts = [], []
         for smp in chunk:
             for k in range(6):
-                unit = np.eye(3)[k % 3]
-                fe = force * unit if k < 3 else np.zeros(3)
-                te = force * smp["b"] * unit if k >= 3 else np.zeros(3)
+                fe, te = _ft_of(smp, k, fofs(smp), tofs(smp))
                 boxes.append(dict(nx=smp["L"], ny=smp["L"], nz=smp["L"], tau=smp["tau"], rho0=1.0,
                                   counter_force=1))
                 parts.append([dict(semi=(smp["a"], smp["b"], smp["b"]), x=smp["x"], q=smp["q"],
                                    F_ext=list(fe), T_ext=list(te))])
         ms = int(math.ceil(max(s["a"] for s in chunk)))
         sim = L.Simulation(boxes, parts, max_semi=ms, device=device)
-        sim.step(steps)
+        if warm_fluid:
+            for bi, b in enumerate(boxes):
+                N = b["nx"] * b["ny"] * b["nz"]
+                u = torch.zeros(3 * N, dtype=torch.float32, device="cuda")
+                d = torch.zeros(N, dtype=torch.float32, device="cuda")
+                L.lb_stokes_field(sim.ctx, bi, u.data_ptr(), d.data_ptr())
+                L.lb_init_fluid(sim.ctx, bi, u.data_ptr(), u.numel() * 4, d.data_ptr(), True, True)
+        bscale = np.repeat(np.array([s["b"] for s in chunk]), 6)[:, None]
+        if check_every <= 0:
+            sim.step(max_steps)
+            done_steps, ok = max_steps, False
+        else:
+            prev, streak, done_steps, ok = None, 0, 0, False
+            while done_steps < max_steps:
+                sim.step(check_every)
+                done_steps += check_every
+                rec = L.lb_get_force_torque(sim.ctx, -1, len(boxes))
+                X = np.concatenate([rec[:, 12:15], rec[:, 15:18] * bscale], axis=1)
+                if prev is not None:
+                    ch = np.linalg.norm(X - prev, axis=1) / np.maximum(np.linalg.norm(X, axis=1), 1e-300)
+                    if history is not None:
+                        history.append((done_steps, float(ch.max()), float(np.median(ch))))
+                    streak = streak + 1 if ch.max() < tol else 0
+                    if streak >= checks:
+                        ok = True
+                        break
+                prev = X
         rec = L.lb_get_force_torque(sim.ctx, -1, len(boxes))
         sim.close()
         for i, smp in enumerate(chunk):
+            used[s0 + i], conv[s0 + i] = done_steps, ok
             for k in range(6):
-                mag = force if k < 3 else force * smp["b"]
+                mag = fofs(smp) if k < 3 else tofs(smp)
                 r = rec[6 * i + k]
                 out[s0 + i, :3, k] = r[12:15] / mag
                 out[s0 + i, 3:, k] = r[15:18] / mag
-    return out
+    return out, used, conv
+
+
+def config5_dataset(seed: int = 0, n: int = 2000, L_edge: int = 64, max_steps: int = 40000, batch: int = 96,
+                    device: int = 0, drift: float = 0.02, tol: float = 1e-4, history=None):
+    """The surrogate workload's training set: n samples in periodic L^3
+    boxes, tau uniform in [0.6, 1.5], a/b in [1, 4], b in [3, 5], uniform
+    orientation; each run to steady state (checked every 500 steps, relative
+    change of every box's (U, b Omega) below tol at three consecutive checks,
+    from the lattice fluid's steady flow).  The force and torque of each sample are scaled so that the
+    particle moves at most `drift` lattice units (and its surface turns by at
+    most that) in max_steps: no node is covered or uncovered, which would
+    jitter the velocity by a few 1e-3 and defeat the steady-state test.
+    Samples run in batches of similar tau (similar relaxation times)."""
+    import lb_inputs as I
+    samples = I.resistance_samples(seed, n, L_edge, tau_range=(0.6, 1.5), aspect=(1.0, 4.0), b_range=(3.0, 5.0))
+    order = np.argsort([s["tau"] for s in samples], kind="stable")
+
+    def fmag(smp):
+        mu = (smp["tau"] - 0.5) / 3.0
+        return drift * 6.0 * math.pi * mu * smp["b"] / max_steps
+
+    def tmag(smp):
+        mu = (smp["tau"] - 0.5) / 3.0
+        return drift * 8.0 * math.pi * mu * smp["b"] ** 3 / (smp["a"] * max_steps)
+
+    M = np.zeros((n, 6, 6))
+    used = np.zeros(n, np.int64)
+    conv = np.zeros(n, bool)
+    sub = [samples[i] for i in order]
+    Ms, us, cs = measure_mobility(sub, max_steps, force=fmag, torque=tmag, device=device, batch=batch,
+                                  check_every=500, tol=tol, checks=3, warm_fluid=True, history=history)
+    M[order], used[order], conv[order] = Ms, us, cs
+    return samples, M, used, conv
 
 
 def augment(geoms, M):
@@ -229,57 +315,36 @@ def steps_to_steady(hist, ref, every: int, tol: float = 1e-3):
     return int((bad[-1] + 2) * every)
 
 
-def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int = 4000, eval_n: int = 128,
-               eval_count: int = 16, force: float = 2e-5, every: int = 50, ref_steps: int = 40000, device: int = 0,
-               eval_tau: float = 1.0):
-    """The whole learned warm start, end to end on the GPU:
-      1. resistance data from the LB method: n32 samples in 32^3 boxes and n48
-         in 48^3 boxes (tau in {0.8, 1, 1.2}, a/b in [1, 3], b in [2, 3.5]),
-         each flow developed for 8 diffusion times L^2 / (4 pi^2 nu) of its box;
-      2. 24-fold cube-rotation augmentation, 10 % of the LB samples held out;
-      3. training of the network;
-      4. an eval_n^3 box (eval_tau) with eval_count spheroids and random forces,
-         run cold (fluid at rest, particles at rest), with the steady lattice
-         fluid only, and with that fluid plus the network's velocities (for
-         eval_tau != 1 also without the stress part), each compared with the
-         steady velocities of a long cold run: steps until every particle's
-         velocity stays within 1e-3 of it.
-    Returns a dict of the measurements."""
+def save_params(net, path: str):
+    """The network's FP32 parameters to a .npy file."""
+    np.save(path, net.params())
+
+
+def load_params(path: str, device: int = 0, max_batch: int = 1024):
+    """A network with the parameters of a .npy file written by save_params."""
+    p = np.load(path).astype(np.float32)
+    return SU.Surrogate(device=device, max_batch=max_batch, params=p)
+
+
+def evaluate(net, seed: int = 0, eval_n: int = 128, eval_count: int = 16, force: float = 1e-7, every: int = 50,
+             ref_steps: int = 40000, eval_tau: float = 1.0, aspect=(1.5, 2.5), b_range=(2.5, 3.0), device: int = 0,
+             modes=("stokes_fluid_only", "warm")):
+    """Steps to steady state of an eval_n^3 box with eval_count spheroids (sizes
+    drawn from the ranges, random orientations, forces of magnitude `force`
+    in random directions with the counter force) started cold (fluid and
+    particles at rest), with the lattice fluid's steady flow only, and with that
+    flow plus the network's velocities ("warm"), each against the velocities
+    at the end of a ref_steps cold run: the first step after which every
+    particle's velocity stays within 1e-2, 3e-3 and 1e-3 (in units of the rms
+    steady speed) of it.  The forces are small enough that no particle covers a
+    node during the runs."""
     import time
 
     import lb_inputs as I
     torch = _torch()
-    t0 = time.time()
-    samples = I.resistance_samples(seed, n32, 32) + I.resistance_samples(seed + 1, n48, 48)
-    M = np.zeros((len(samples), 6, 6))
-    for Ledge in (32, 48):
-        idx = [i for i, s in enumerate(samples) if s["L"] == Ledge]
-        for tau in (0.8, 1.0, 1.2):
-            sub = [i for i in idx if samples[i]["tau"] == tau]
-            if not sub:
-                continue
-            nu = (tau - 0.5) / 3.0
-            steps = int(8 * Ledge * Ledge / (4 * math.pi ** 2 * nu))
-            M[sub] = measure_mobility([samples[i] for i in sub], steps, device=device)
-    t_data = time.time() - t0
-    geoms = np.asarray([geom_of(s["a"], s["b"], s["tau"], s["L"], s["e"]) for s in samples])
-    g = np.random.default_rng(seed)
-    perm = g.permutation(len(samples))
-    nval = max(1, len(samples) // 10)
-    val, tr = perm[:nval], perm[nval:]
-    Gt, Mt = augment(geoms[tr], M[tr])
-    x, R = targets(Gt, Mt)
-    t1 = time.time()
-    net, train_loss = train(x, R, steps=train_steps, seed=seed)
-    t_train = time.time() - t1
-    xv, Rv = targets(geoms[val], M[val])
-    Pv = predict(net, xv)
-    rel = (torch.linalg.matrix_norm((Pv - Rv).reshape(-1, 6, 6)) /
-           torch.linalg.matrix_norm(Rv.reshape(-1, 6, 6))).cpu().numpy()
-    # evaluation runs
-    boxes, parts = I.many_spheroids(seed, n=eval_n, count=eval_count, force=force, tau=eval_tau)
+    boxes, parts = I.many_spheroids(seed, n=eval_n, count=eval_count, force=force, tau=eval_tau, aspect=aspect,
+                                    b_range=b_range)
     ms = int(math.ceil(max(p["semi"][0] for p in parts[0])))
-
     cost = {}
 
     def run(mode, steps):
@@ -297,14 +362,12 @@ def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int =
         sim.close()
         return h
 
-    t2 = time.time()
     ref = run("cold", ref_steps)
     U_ss = ref[-1, :, :3]
     drift = float(velocity_error(ref[-11:-10], U_ss)[0])
     tols = (1e-2, 3e-3, 1e-3)
     res = {f"cold@{t:g}": steps_to_steady(ref, U_ss, every, t) for t in tols}
     curves = {"cold": velocity_error(ref, U_ss)}
-    modes = ("stokes_fluid_only", "warm") + (("warm_no_stress",) if eval_tau != 1.0 else ())
     end_vs_ref = {}
     for mode in modes:
         h = run(mode, ref_steps // 2)
@@ -313,24 +376,131 @@ def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int =
         curves[mode] = velocity_error(h, U_ss)
         end_vs_ref[mode] = float(curves[mode][-1])
     pick = lambda c: {int((i + 1) * every): float(c[i]) for i in range(0, len(c), max(1, len(c) // 40))}
-    t_eval = time.time() - t2
+    gain = lambda a, b: (res[a] / res[b]) if res[a] and res[b] else None
+    return {"steps_to_steady": res,
+            "gain_warm_vs_cold": {f"{t:g}": gain(f"cold@{t:g}", f"warm@{t:g}") for t in tols},
+            "gain_warm_vs_fluid_only": ({f"{t:g}": gain(f"stokes_fluid_only@{t:g}", f"warm@{t:g}") for t in tols}
+                                        if "stokes_fluid_only" in modes else None),
+            "reference_drift_last_500_steps": drift, "end_of_runs_vs_reference": end_vs_ref,
+            "eval": (f"{eval_n}^3, {eval_count} spheroids (a/b in {list(aspect)}, b in {list(b_range)}), "
+                     f"|F|={force}, tau={eval_tau}"),
+            "error_curves": {k: pick(v) for k, v in curves.items()}, "seconds": cost}
+
+
+def held_out_error(net, geoms, M):
+    """Relative (Frobenius) error of the network's R^ on samples it was not trained on."""
+    torch = _torch()
+    xv, Rv = targets(geoms, M)
+    Pv = predict(net, xv)
+    return (torch.linalg.matrix_norm((Pv - Rv).reshape(-1, 6, 6)) /
+            torch.linalg.matrix_norm(Rv.reshape(-1, 6, 6))).cpu().numpy()
+
+
+def experiment(seed: int = 0, n32: int = 384, n48: int = 128, train_steps: int = 4000, eval_n: int = 128,
+               eval_count: int = 16, force: float = 2e-5, every: int = 50, ref_steps: int = 40000, device: int = 0,
+               eval_tau: float = 1.0):
+    """A reduced learned warm start, end to end on the GPU:
+      1. resistance data from the LB method: n32 samples in 32^3 boxes and n48
+         in 48^3 boxes (tau in {0.8, 1, 1.2}, a/b in [1, 3], b in [2, 3.5]),
+         each flow developed for 8 diffusion times L^2 / (4 pi^2 nu) of its box;
+      2. 24-fold cube-rotation augmentation, 10 % of the LB samples held out;
+      3. training of the network;
+      4. evaluate(): an eval_n^3 box with eval_count spheroids, cold, steady
+         lattice fluid only, and warm.
+    Returns a dict of the measurements.  config5() is the full-size form."""
+    import time
+
+    import lb_inputs as I
+    t0 = time.time()
+    samples = I.resistance_samples(seed, n32, 32) + I.resistance_samples(seed + 1, n48, 48)
+    M = np.zeros((len(samples), 6, 6))
+    for Ledge in (32, 48):
+        idx = [i for i, s in enumerate(samples) if s["L"] == Ledge]
+        for tau in (0.8, 1.0, 1.2):
+            sub = [i for i in idx if samples[i]["tau"] == tau]
+            if not sub:
+                continue
+            nu = (tau - 0.5) / 3.0
+            steps = int(8 * Ledge * Ledge / (4 * math.pi ** 2 * nu))
+            M[sub] = measure_mobility([samples[i] for i in sub], steps, device=device)[0]
+    t_data = time.time() - t0
+    geoms = np.asarray([geom_of(s["a"], s["b"], s["tau"], s["L"], s["e"]) for s in samples])
+    g = np.random.default_rng(seed)
+    perm = g.permutation(len(samples))
+    nval = max(1, len(samples) // 10)
+    val, tr = perm[:nval], perm[nval:]
+    Gt, Mt = augment(geoms[tr], M[tr])
+    x, R = targets(Gt, Mt)
+    t1 = time.time()
+    net, train_loss = train(x, R, steps=train_steps, seed=seed)
+    t_train = time.time() - t1
+    rel = held_out_error(net, geoms[val], M[val])
+    t2 = time.time()
+    ev = evaluate(net, seed=seed, eval_n=eval_n, eval_count=eval_count, force=force, every=every,
+                  ref_steps=ref_steps, eval_tau=eval_tau, device=device,
+                  modes=("stokes_fluid_only", "warm") + (("warm_no_stress",) if eval_tau != 1.0 else ()))
+    ev["seconds"].update({"data": t_data, "train": t_train, "eval": time.time() - t2})
     return {"samples": len(samples), "augmented": int(len(Gt)), "train_loss": train_loss,
-            "val_rel_err_median": float(np.median(rel)), "val_rel_err_max": float(rel.max()),
-            "steps_to_steady": res,
-            "gain_warm_vs_cold": {f"{t:g}": (res[f"cold@{t:g}"] / res[f"warm@{t:g}"])
-                                  if res[f"cold@{t:g}"] and res[f"warm@{t:g}"] else None for t in tols},
-            "reference_drift_last_500_steps": drift, "end_of_warm_runs_vs_reference": end_vs_ref,
-            "eval": f"{eval_n}^3, {eval_count} spheroids, |F|={force}, tau={eval_tau}",
-            "error_curves": {k: pick(v) for k, v in curves.items()},
-            "seconds": {"data": t_data, "train": t_train, "eval": t_eval, **cost}}
+            "val_rel_err_median": float(np.median(rel)), "val_rel_err_max": float(rel.max()), **ev}
+
+
+def config5(seed: int = 0, n: int = 2000, train_steps: int = 8000, out: str = "", device: int = 0):
+    """The surrogate workload at its stated size: config5_dataset (n runs on
+    64^3 boxes to steady state), 24-fold augmentation with 10 % of the LB
+    samples held out, training, and the held-out error; the parameters go to
+    `out` (.npy) when given.  Returns (net, summary)."""
+    import time
+
+    t0 = time.time()
+    samples, M, used, conv = config5_dataset(seed=seed, n=n, device=device)
+    t_data = time.time() - t0
+    geoms = np.asarray([geom_of(s["a"], s["b"], s["tau"], s["L"], s["e"]) for s in samples])
+    g = np.random.default_rng(seed)
+    perm = g.permutation(len(samples))
+    nval = max(1, len(samples) // 10)
+    val, tr = perm[:nval], perm[nval:]
+    Gt, Mt = augment(geoms[tr], M[tr])
+    x, R = targets(Gt, Mt)
+    t1 = time.time()
+    net, train_loss = train(x, R, steps=train_steps, seed=seed, batch=1024)
+    t_train = time.time() - t1
+    rel = held_out_error(net, geoms[val], M[val])
+    if out:
+        save_params(net, out)
+    taus = np.array([s["tau"] for s in samples])
+    summary = {"samples": len(samples), "augmented": int(len(Gt)), "train_loss": train_loss,
+               "converged": int(conv.sum()), "steps_used_median": int(np.median(used)),
+               "steps_used_max": int(used.max()),
+               "steps_used_by_tau": {f"{lo:.1f}-{lo + 0.3:.1f}": int(np.median(used[(taus >= lo) & (taus < lo + 0.3)]))
+                                     for lo in (0.6, 0.9, 1.2) if ((taus >= lo) & (taus < lo + 0.3)).any()},
+               "val_rel_err_median": float(np.median(rel)), "val_rel_err_max": float(rel.max()),
+               "seconds": {"data": t_data, "train": t_train}}
+    return net, summary
 
 
 if __name__ == "__main__":
     import json
     import sys
 
+    args = sys.argv[1:]
+    cmd = args.pop(0) if args and "=" not in args[0] else "experiment"
     kw = {}
-    for a in sys.argv[1:]:
-        k, v = a.split("=")
-        kw[k] = int(v) if v.isdigit() else float(v)
-    print(json.dumps(experiment(**kw)))
+    for a in args:
+        k, v = a.split("=", 1)
+        try:
+            kw[k] = int(v)
+        except ValueError:
+            try:
+                kw[k] = float(v)
+            except ValueError:
+                kw[k] = v
+    if cmd == "config5":
+        ev_kw = {k[3:]: kw.pop(k) for k in list(kw) if k.startswith("ev.")}   # evaluate()'s arguments
+        net, summ = config5(**kw)
+        summ["evaluation"] = evaluate(net, aspect=(1.0, 4.0), b_range=(3.0, 5.0), **ev_kw)
+        print(json.dumps(summ))
+    elif cmd == "evaluate":
+        net = load_params(kw.pop("weights"))
+        print(json.dumps(evaluate(net, **kw)))
+    else:
+        print(json.dumps(experiment(**kw)))

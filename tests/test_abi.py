@@ -40,7 +40,7 @@ def test_python_binding_has_the_same_names():
 
 
 def test_abi_version_and_status_strings():
-    assert L.lb_abi_version() == 3
+    assert L.lb_abi_version() == 4
     assert L.lb_status_string(0) == "ok"
     assert L.lb_status_string(1) == "invalid argument"
     assert L.lb_status_string(99) == "unknown status"

@@ -156,6 +156,79 @@ def test_fast_particle_covers_and_uncovers_nodes():
     _compare_run([b], [[p]], steps=60, every=3)
 
 
+@pytest.mark.parametrize("didt_mode", [1, 2])
+def test_inertia_rate_modes_spinning_triaxial_body(didt_mode):
+    """The two other forms of I(t+1) in Eq. Tdiscrete: the finite difference
+    (mode 1) and the predictor-corrector (mode 2: the solve is repeated with
+    I of the predicted orientation), on a fast-spinning triaxial body under an
+    external torque, which turns it by several degrees."""
+    g = rng(13)
+    b = box(24, 24, 28, 0.9, didt_mode=didt_mode)
+    p = particle((5.5, 3.5, 2.5), (11.7, 12.2, 13.9), random_quaternion(g), Om=(0.004, -0.006, 0.008),
+                 T_ext=(2e-3, 1e-3, -1.5e-3), density=3.0)
+    _compare_run([b], [[p]], steps=60, every=6, didt_mode=didt_mode)
+
+
+@pytest.mark.parametrize("semi", [(2.5, 5.0, 5.0), (5.5, 3.5, 2.0)])
+def test_oblate_and_triaxial_bodies(semi):
+    """An oblate spheroid (body x the short symmetry axis) and a triaxial
+    ellipsoid (Sec. IV), settling and turning under a force and a torque."""
+    g = rng(14)
+    b = box(28, 28, 28, 1.0, counter_force=1)
+    p = particle(semi, (13.6, 14.3, 13.2), random_quaternion(g), F_ext=(1e-3, -5e-4, 2e-4),
+                 T_ext=(2e-3, 0.0, -1e-3))
+    _compare_run([b], [[p]], steps=60, every=6)
+
+
+def _close_pair(lub_cut):
+    """A sphere and a spheroid pushed together from a gap of 0.89 lattice units
+    (to 0.68 without, 0.72 with the lubrication correction): their bounding
+    cubes overlap, nodes between them have links to both surfaces, and nodes
+    are covered and uncovered next to both."""
+    b = box(40, 32, 32, 0.9, counter_force=1, lub_cut=lub_cut)
+    qB = axis_angle_quaternion((0.2, 0.3, 1.0), 0.15)
+    pA = particle((3.5, 3.5, 3.5), (14.3, 15.8, 16.1), U=(0.01, 0, 0), F_ext=(3e-3, 0, 0), density=2.0)
+    pB = particle((4.5, 2.5, 2.0), (23.15, 16.2, 15.9), qB, U=(-0.01, 0.001, 0), F_ext=(-3e-3, 5e-4, 0), density=2.0)
+    return b, [pA, pB]
+
+
+@pytest.mark.parametrize("lub_cut", [0.0, 1.0])
+def test_close_particles_with_overlapping_cubes(lub_cut):
+    """Multiple particles within reach of each other: the nodes
+    between two bodies are updated once, with bounce-back on both surfaces, the
+    remap and the momentum-exchange sums going to the body each link or node
+    belongs to; with lub_cut > 0 the lubrication correction (Nguyen-Ladd, the
+    squeeze force the lattice does not resolve below the cut-off gap) enters
+    both solves.  Every field and particle value every 4 steps for 80 steps."""
+    b, parts = _close_pair(lub_cut)
+    _compare_run([b], [parts], steps=80, every=4)
+
+
+def test_close_particles_links_and_owner_bit_exact():
+    b, parts = _close_pair(1.0)
+    gpu = _sim([b], [parts])
+    orc = O.Sim(b, parts, nthreads=4)
+    for k in range(3):
+        assert np.array_equal(gpu.field("solid"), orc.owner())
+        for p in range(2):
+            assert gpu_links_as_set(gpu, 0, p) == oracle_links_as_set(orc, p)
+        gpu.step(20)
+        orc.step(20)
+
+
+def test_cluster_of_three_particles():
+    """A chain of three bodies within reach of each other: one cluster whose
+    critical parts run one after the other once all its boundary work is done;
+    a fourth particle far away stays on its own."""
+    g = rng(15)
+    b = box(56, 32, 36, 1.0, counter_force=1, lub_cut=2.0 / 3.0)
+    parts = [particle((3.0, 3.0, 3.0), (10.2, 15.7, 17.9), F_ext=(2e-3, 0, 0), U=(0.008, 0, 0)),
+             particle((4.0, 2.5, 2.5), (18.9, 16.3, 18.2), random_quaternion(g), U=(0.0, 0.004, 0)),
+             particle((3.0, 3.0, 3.0), (27.6, 15.9, 18.3), F_ext=(-2e-3, 0, 0), U=(-0.008, 0, 0)),
+             particle((2.5, 2.5, 2.5), (47.4, 16.1, 6.2), random_quaternion(g), F_ext=(0, 1e-3, 0))]
+    _compare_run([b], [parts], steps=60, every=6)
+
+
 def test_channel_walls_with_particle():
     """Moving walls (Couette) plus a free spheroid; nx = 20 is not a multiple of 128
     (rows shorter than a warp), ny not a power of two."""

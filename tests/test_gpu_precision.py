@@ -13,6 +13,19 @@ Bars: FP32 1e-5 (the plain path's bar); FP16 (scale 2^14, 11-bit significand)
 stored value rounded by up to 2^-9 of itself every step) misses that target,
 measured 1.5e-3, and is held to 2.5e-3 so that a regression still shows.
 
+The same measurement on the first two benchmark workloads at their own
+forces: config 1 (the 32^3 box above at |F_ext| = 1e-4, 1200 steps) and one box
+of the orientation sweep (64^3, tau = 0.8, spheroid (8,4,4) at 45 degrees to
+|F_ext| = 5e-4, 3000 steps, about three diffusion times L^2 / (4 pi^2 nu)),
+where the spheroid moves and covers nodes.  Measured (means over the last 500
+steps): FP32 2.3e-6 / 1.7e-5, FP16 2.5e-4 / 9.0e-4, BF16 9.8e-4 / 8.6e-3.  FP16
+meets the mixed-storage target of 1e-3 on both (bar 1e-3); BF16 meets it on
+config 1 only and is held to 1.5e-3 / 1.2e-2 so that a regression shows.  The
+FP32 path is held to 3e-5 on the 3000-step run: the counter force spreads
+|F_ext| / N = 2e-9 per node, whose per-population increments (~1e-11) lie a
+few FP32 units in the last place below the stored deviations of the far field,
+so their rounding is correlated between nodes of nearly equal deviations.
+
 The second test is the squirmer batch of the benchmark's second workload
 (2000 steps, the swimming velocity and flow field per storage format against
 the oracle): there BF16 stays within 1e-3 on the velocity (5.8e-4)."""
@@ -51,6 +64,64 @@ def test_drag_and_torque_error_of_the_storage_format(precision, bar):
     torque = float(np.linalg.norm(g["T"] - r["T"]) / (1e-5 * 4.0))
     print("storage", precision, "drag error", drag, "torque error", torque)
     assert drag <= bar and torque <= bar
+
+
+_wref = {}
+
+
+def _workload(name):
+    from lb_inputs import sweep_8x64
+    if name == "config1":
+        boxes, parts = single_32(seed=0)
+        return [boxes[0]], [parts[0]], 1200, 4
+    boxes, parts = sweep_8x64(seed=0)
+    return [boxes[3]], [parts[3]], 3000, 8
+
+
+AVG = 500          # steady values: means over the last AVG steps, read every 25
+
+
+def _mean_tail(step, read, steps):
+    step(steps - AVG)
+    acc = []
+    for _ in range(AVG // 25):
+        step(25)
+        acc.append(read())
+    return {k: np.mean([a[k] for a in acc], axis=0) for k in ("U", "Om", "T")}
+
+
+def _workload_reference(name):
+    if name not in _wref:
+        boxes, parts, steps, _ = _workload(name)
+        o = O.Sim(boxes[0], parts[0], nthreads=16)
+        _wref[name] = _mean_tail(o.step, lambda: o.particle(0), steps)
+    return _wref[name]
+
+
+BARS = {("config1", L.LB_FP32): 1e-5, ("config2", L.LB_FP32): 3e-5,
+        ("config1", L.LB_FP16): 1e-3, ("config2", L.LB_FP16): 1e-3,
+        ("config1", L.LB_BF16): 1.5e-3, ("config2", L.LB_BF16): 1.2e-2}
+
+
+@pytest.mark.parametrize("name", ["config1", "config2"])
+@pytest.mark.parametrize("precision", [L.LB_FP32, L.LB_FP16, L.LB_BF16])
+def test_drag_error_on_the_benchmark_workloads(name, precision):
+    """Steady velocity and torque, averaged over the last 500 steps on both sides
+    (a moving spheroid's drag jumps by 1e-3 of itself when it covers a node,
+    and the two sides may cover one at steps a few apart)."""
+    boxes, parts, steps, ms = _workload(name)
+    sim = L.Simulation(boxes, parts, precision=precision, max_semi=ms)
+    g = _mean_tail(sim.step, lambda: sim.particle(0, 0), steps)
+    r = _workload_reference(name)
+    sim.close()
+    F = float(np.linalg.norm(parts[0][0]["F_ext"]))
+    a = max(parts[0][0]["semi"])
+    drag = float(np.linalg.norm(g["U"] - r["U"]) / np.linalg.norm(r["U"]))
+    torque = float(np.linalg.norm(g["T"] - r["T"]) / (F * a))
+    rot = float(np.linalg.norm(g["Om"] - r["Om"]) * a / np.linalg.norm(r["U"]))
+    bar = BARS[(name, precision)]
+    print(name, "storage", precision, "drag error", drag, "torque error", torque, "rotation error", rot)
+    assert drag <= bar and torque <= bar and rot <= bar
 
 
 def test_squirmer_batch_swimming_speed_and_flow_per_storage_format():

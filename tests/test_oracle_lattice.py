@@ -140,3 +140,80 @@ def test_couette_profile_exact(tau):
     expect = -uw + 2 * uw * (y - 0.5) / (ny - 2)
     assert np.abs(u[0, 1:ny - 1, 0, 0] - expect).max() < 1e-10
     assert np.abs(u[0, 1:ny - 1, 0, 1:]).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# The paper's collision (Sec. II.A: one relaxation time for the non-conserved
+# hydrodynamic modes, instantaneous relaxation of the non-hydrodynamic ones),
+# box option collision = 1.
+
+def _uniform_collision(tau, collision, g=(2e-5, -1e-5, 3e-5), seed=3):
+    """One step of a spatially uniform random non-equilibrium state in a
+    periodic box: streaming maps the uniform post-collision state onto itself,
+    so f(t+1) is the post-collision distribution of every node."""
+    c, w = O.lattice()
+    rng = np.random.default_rng(seed)
+    f0 = O.feq(1.02, (0.01, -0.02, 0.015)) + 1e-3 * w * rng.standard_normal(19)
+    b = box(3, 3, 3, tau, body_force=g, collision=collision)
+    s = O.Sim(b, [], nthreads=1)
+    s.set_f(np.tile(f0, 27))
+    s.step(1)
+    return f0, s.f()[0, 0, 0]
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.4])
+def test_ghost_mode_collision_keeps_only_the_relaxed_stress(tau):
+    c, w = O.lattice()
+    c = c.astype(float)
+    g = np.array([2e-5, -1e-5, 3e-5])
+    f0, fs = _uniform_collision(tau, 1, g)
+    rho = f0.sum()
+    u = (f0 @ c + 0.5 * g) / rho
+    feq = O.feq(rho, u)
+    S = (1 - 0.5 / tau) * w * (3 * (c @ g - u @ g) + 9 * (c @ u) * (c @ g))
+    d = fs - feq - S
+    # the hydrodynamic Hermite modes of D3Q19 beyond mass: w_i c_ia and
+    # w_i (c_ia c_ib - delta_ab / 3)
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    H = np.stack([w * c[:, a] for a in range(3)] +
+                 [w * (c[:, a] * c[:, b] - (a == b) / 3.0) for a, b in pairs], axis=1)
+    coef, *_ = np.linalg.lstsq(H, d, rcond=None)
+    assert np.abs(d - H @ coef).max() < 1e-15                     # no ghost content left
+    Pn = np.einsum("i,ia,ib->ab", f0 - feq, c, c)
+    Ps = np.einsum("i,ia,ib->ab", d, c, c)
+    assert np.abs(Ps - (1 - 1 / tau) * Pn).max() < 1e-15          # the stress relaxed by 1 - 1/tau
+    assert np.abs(d @ c - (1 - 1 / tau) * ((f0 - feq) @ c)).max() < 1e-16
+    assert abs(fs.sum() - rho) < 1e-15
+    assert np.abs(fs @ c - (f0 @ c + g)).max() < 1e-15            # momentum + the force
+    # BGK keeps (1 - 1/tau) of the ghost content of f - feq, so the two differ
+    _, fb = _uniform_collision(tau, 0, g)
+    db = fb - feq - S
+    cb, *_ = np.linalg.lstsq(H, db, rcond=None)
+    assert np.abs(db - H @ cb).max() > 1e-6 * abs(1 - 1 / tau)
+
+
+def test_ghost_mode_collision_equals_bgk_at_tau_one():
+    _, f1 = _uniform_collision(1.0, 1)
+    _, f0 = _uniform_collision(1.0, 0)
+    assert np.abs(f1 - f0).max() < 1e-16
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.4])
+def test_ghost_mode_collision_viscosity(tau):
+    """The shear viscosity is still (tau - 1/2)/3: the shear-wave decay."""
+    c, w = O.lattice()
+    ny, U0 = 64, 1e-4
+    b = box(2, ny, 2, tau, collision=1)
+    s = O.Sim(b, [], nthreads=1)
+    f = np.zeros((2, ny, 2, 19))
+    for j in range(ny):
+        f[:, j, :, :] = O.feq(1.0, (U0 * math.sin(2 * math.pi * j / ny), 0.0, 0.0))
+    s.set_f(f.ravel())
+    basis = np.sin(2 * math.pi * np.arange(ny) / ny)
+    amps = []
+    for _ in range(400):
+        s.step(1)
+        amps.append(2.0 / ny * (s.moments()[1][0, :, 0, 0] @ basis))
+    t = np.arange(1, 401)
+    rate = -np.polyfit(t[50:], np.log(np.array(amps)[50:]), 1)[0] / (2 * math.pi / ny) ** 2
+    assert abs(rate / ((tau - 0.5) / 3.0) - 1.0) < 0.005

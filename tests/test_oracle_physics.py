@@ -143,6 +143,18 @@ def test_closed_form_limits():
     assert np.abs(e[-1] - e[0]).max() < 1e-6
     half = np.argmin(np.abs(t - T / 2))
     assert np.abs(e[half] + e[0]).max() < 1e-3               # half a period flips the axis
+    # a 3-D orbit (axis off the vorticity axis): the orbit constant is constant
+    # along the integrated Eq. jeffery, and an orbit of another aspect ratio
+    # does not keep it
+    for r in (2.0, 3.0):
+        beta = (r * r - 1) / (r * r + 1)
+        T = A.jeffery_period(r, gam)
+        e0 = np.array([0.5, 0.3, 0.8]) / np.linalg.norm([0.5, 0.3, 0.8])
+        t, e = A.jeffery_orbit(e0, G, beta, 1.5 * T, T / 20000)
+        C = A.jeffery_orbit_constant(e, r)
+        assert np.ptp(C) < 1e-6 * C.mean()
+        assert np.ptp(A.jeffery_orbit_constant(e, 1.1 * r)) > 0.05 * C.mean()
+        assert abs(A.jeffery_aspect_from_period(T, gam) - r) < 1e-12
 
 
 def _settle_sphere(a, L, F, mu_tau=1.0, tol=2e-5, max_steps=20000):

@@ -122,3 +122,61 @@ def test_body_inertia_of_spheroid():
     s = O.Sim(box(24, 24, 24, 1.0), [particle((5.0, 3.0, 2.0), (12, 12, 12), density=1.3)], nthreads=1)
     M = s.mass(0)
     assert abs(M - 1.3 * 4 / 3 * math.pi * 30) < 1e-12
+
+
+def _free_step_L_error(mode, q, Ib, Om):
+    """Relative change of the angular momentum I(q) Omega over one step of a
+    free body (no drag, no torque), which the exact dynamics conserves."""
+    M = 4.0
+    L0 = O.inertia_lab(q, Ib) @ Om
+    _, Wn = O.rigid_solve(M, Ib, q, (0, 0, 0), Om, np.zeros(36), (0, 0, 0), (0, 0, 0), mode=mode)
+    qn = O.quat_step(q, 0.5 * (np.asarray(Om) + Wn))
+    return float(np.linalg.norm(O.inertia_lab(qn, Ib) @ Wn - L0) / np.linalg.norm(L0))
+
+
+def test_predictor_corrector_conserves_angular_momentum_to_higher_order():
+    """Sec. II.D: replacing I(t+1) by I(t) + dI/dt (Eq. Irotdiff) leaves a
+    one-step angular-momentum error of second order in |Omega| dt; the
+    predictor-corrector (I(t+1) from the predicted orientation, Eq. Irot) is of
+    third order.  Halving Omega divides the errors by 4 and by 8."""
+    g = rng(21)
+    q = random_quaternion(g)
+    Ib = np.array([1.0, 2.0, 3.5])                      # triaxial
+    ax = np.array([0.3, 1.0, -0.6]) / np.linalg.norm([0.3, 1.0, -0.6])
+    e0 = [_free_step_L_error(0, q, Ib, w * ax) for w in (0.02, 0.01, 0.005)]
+    e2 = [_free_step_L_error(2, q, Ib, w * ax) for w in (0.02, 0.01, 0.005)]
+    for k in range(2):
+        assert 3.6 < e0[k] / e0[k + 1] < 4.4
+        assert 7.2 < e2[k] / e2[k + 1] < 8.8
+    assert e2[0] < 0.05 * e0[0]
+
+
+def test_predictor_corrector_limits():
+    """An isotropic body has I(q) = I for every q: dI/dt = 0 and I(q_p) = I, so
+    all three modes give the same solution to round-off.  For an anisotropic
+    body with drag, mode 2 differs from mode 0 by O(|Omega|^2) (the second-order
+    term of I(t+1) that Eq. Irotdiff drops)."""
+    g = rng(22)
+    q = random_quaternion(g)
+    A = g.standard_normal((6, 6))
+    Z = A @ A.T * 0.05 + np.eye(6) * 0.1                # a drag matrix: SPD
+    rF, rT = g.standard_normal(3) * 1e-4, g.standard_normal(3) * 1e-4
+    U0 = g.standard_normal(3) * 1e-3
+    ax = g.standard_normal(3)
+    ax /= np.linalg.norm(ax)
+    Iso = np.array([2.0, 2.0, 2.0])
+    Om = 0.03 * ax
+    I0 = O.inertia_lab(q, Iso)
+    sols = [O.rigid_solve(5.0, Iso, q, U0, Om, Z, rF, rT, Iprev=I0, mode=m) for m in (0, 1, 2)]
+    for m in (1, 2):
+        assert np.allclose(np.concatenate(sols[m]), np.concatenate(sols[0]), rtol=0, atol=1e-14)
+    # no velocity-independent forces: every velocity scales with Omega(t)
+    Ib = np.array([1.0, 2.0, 3.5])
+    d, x = [], []
+    for w in (0.02, 0.01, 0.005):
+        x0 = np.concatenate(O.rigid_solve(5.0, Ib, q, w * U0, w * ax, Z, (0, 0, 0), (0, 0, 0), mode=0))
+        x2 = np.concatenate(O.rigid_solve(5.0, Ib, q, w * U0, w * ax, Z, (0, 0, 0), (0, 0, 0), mode=2))
+        d.append(float(np.abs(x2 - x0).max()))
+        x.append(float(np.abs(x0).max()))
+    for k in range(2):
+        assert 3.6 < (d[k] / x[k]) / (d[k + 1] / x[k + 1]) * 2 < 4.4
