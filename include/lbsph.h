@@ -117,6 +117,13 @@ typedef struct {
     void* (*alloc)(size_t bytes, void* user);   /* optional device allocator          */
     void (*release)(void* ptr, void* user);
     void* alloc_user;
+    /* Collision: 0 BGK (Eq. 3-4); 1 the paper's scheme (Sec. II.A): one
+     * relaxation time for the non-conserved hydrodynamic modes, the
+     * non-hydrodynamic (ghost) modes set to equilibrium in every collision,
+     * i.e. f_i' = feq_i + (1 - 1/tau) w_i [c_i.j_neq / c_s^2 + (c_i c_i -
+     * c_s^2 I) : Pi_neq / (2 c_s^4)] + the Guo source; the same as BGK at
+     * tau = 1.  1 needs LB_FP32 storage. */
+    int32_t collision;
 } lb_options;
 
 typedef struct {

@@ -311,7 +311,7 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
             }
         }
         if (write) {
-            collide19(f, K.omega, rho0, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps);
+            collide19<St::GHOST>(f, K.omega, rho0, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps);
 #pragma unroll
             for (int i = 0; i < Q; ++i) St::st1(D + (long long)i * N + own, f[i], scale, pol);
             // momentum-exchange sums of the new links (x, b), with f*(t)

@@ -53,6 +53,7 @@ cudaError_t launch_boundary(const BndParams& p, int precision, int np, cudaStrea
     const size_t smem = 2ull * p.smax * p.smax * sizeof(uint64_t) + (size_t)p.list_cap * sizeof(unsigned);
     if (precision == 1) return launch_bnd_t<StF16>(p, grid, smem, s);
     if (precision == 2) return launch_bnd_t<StBF16>(p, grid, smem, s);
+    if (precision == 3) return launch_bnd_t<StF32G>(p, grid, smem, s);   // FP32, the paper's collision
     return launch_bnd_t<StF32>(p, grid, smem, s);
 }
 

@@ -58,6 +58,7 @@ cudaError_t launch_bulk(const BulkParams& p, int precision, int blocks, cudaStre
 {
     if (precision == 1) return launch_bulk_t<StF16>(p, blocks, s);
     if (precision == 2) return launch_bulk_t<StBF16>(p, blocks, s);
+    if (precision == 3) return launch_bulk_t<StF32G>(p, blocks, s);   // FP32, the paper's collision
     return launch_bulk_t<StF32>(p, blocks, s);
 }
 

@@ -92,7 +92,7 @@ __device__ __forceinline__ void bulk_tile(const BulkParams& P, int tile, int tix
             v[i] = make_float4(o.x + add, o.y + add, o.z + add, o.w + add);
         }
     }
-    ColliderT<St::SCALED> C;
+    ColliderT<St::SCALED, St::GHOST> C;
     C.init(B.omega, B.rho0f, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps, B.scale, B.inv_scale);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

@@ -106,6 +106,7 @@ __device__ __forceinline__ void sth_u16(void* a, unsigned short v, unsigned long
 struct StF32 {
     using T = float;
     static constexpr bool SCALED = false;
+    static constexpr bool GHOST = false;       // collision: BGK
     static __device__ __forceinline__ float4 ld4(const T* p, float, unsigned long long pol) { return ldh_f4(p, pol); }
     static __device__ __forceinline__ float ld1(const T* p, float, unsigned long long pol) { return ldh_f1(p, pol); }
     static __device__ __forceinline__ void st4(T* p, float4 v, float, unsigned long long pol) { sth_f4(p, v, pol); }
@@ -119,6 +120,7 @@ struct StF32 {
 struct StF16 {
     using T = __half;
     static constexpr bool SCALED = true;
+    static constexpr bool GHOST = false;
     static __device__ __forceinline__ float4 ld4(const T* p, float inv, unsigned long long pol)
     {
         const uint2 u = ldh_u2(p, pol);
@@ -172,6 +174,7 @@ struct StF16 {
 struct StBF16 {
     using T = __nv_bfloat16;
     static constexpr bool SCALED = false;
+    static constexpr bool GHOST = false;
     static __device__ __forceinline__ float4 ld4(const T* p, float, unsigned long long pol)
     {
         const uint2 u = ldh_u2(p, pol);
@@ -200,6 +203,12 @@ struct StBF16 {
     static __device__ __forceinline__ float ld1r(const T* p, unsigned long long pol) { return ld1(p, 1.0f, pol); }
     static __device__ __forceinline__ void st4r(T* p, float4 v, unsigned long long pol) { st4(p, v, 1.0f, pol); }
     static __device__ __forceinline__ void st1r(T* p, float v, unsigned long long pol) { st1(p, v, 1.0f, pol); }
+};
+
+// FP32 storage with the paper's collision (ghost modes relaxed at once, see
+// ColliderT): the same layout as StF32.
+struct StF32G : StF32 {
+    static constexpr bool GHOST = true;
 };
 
 // ---------------------------------------------------------------------------
@@ -234,8 +243,23 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float a)
 // come out times sc; no population is scaled on load or on store.  With a
 // power-of-two sc each of these products is exact, so the results are the
 // same bits as scaling every population.
-template <bool SCALED>
+//
+// GHOST (FP32 only): the collision the paper's simulations use (Sec. II.A: one
+// relaxation time for the non-conserved hydrodynamic modes, the
+// non-hydrodynamic ("ghost") modes relaxed at once to equilibrium).  Of the
+// non-equilibrium part only its projection on the hydrodynamic Hermite modes
+// is kept and relaxed:
+//   d_i' = deq_i + (1 - omega) w_i [3 c_i.j_neq + 4.5 (c_i c_i - I/3) : Pi_neq] + S_i,
+// deq_i = w_i (drho + rho (3 cu + 4.5 cu^2 - 1.5 u.u)), S_i the Guo source,
+// j_neq = j - rho u = -g/2, Pi_neq = sum_i c_i c_i d_i + (eps - drho)/3 I - rho u u
+// (the mass return eps added to every population first, as above).  Per pair
+// the odd part is 3 w rho cu + 1.5 w (c_i.g) whatever omega (the momentum
+// gains g), the even part w (drho + rho (4.5 cu^2 - 1.5 u.u)) + (1 - omega)
+// 4.5 w Q_i + cf w (9 cu (c_i.g) - 3 u.g), Q_i = c_i.Pi_neq.c_i - tr Pi_neq / 3.
+// At omega = 1 it is BGK.
+template <bool SCALED, bool GHOST = false>
 struct ColliderT {
+    static_assert(!(SCALED && GHOST), "the ghost-mode collision works on unscaled populations");
     float omega, om1, rho0, eps;    // SCALED: omega and eps times sc
     float gx, gy, gz;
     float cfug;                     // 3 cf, the factor of u.g in P (times sc)
@@ -264,6 +288,10 @@ struct ColliderT {
 
     __device__ __forceinline__ void apply(float (&f)[Q]) const
     {
+        if (GHOST) {
+            apply_ghost(f);
+            return;
+        }
         float sm[9], df[9];
 #pragma unroll
         for (int m = 0; m < 9; ++m) {
@@ -306,15 +334,78 @@ struct ColliderT {
             f[i + 1] = om1 * f[i + 1] + (sym - asym);
         }
     }
+
+    __device__ __forceinline__ void apply_ghost(float (&f)[Q]) const
+    {
+        float sm[9], df[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            sm[m] = f[2 * m + 1] + f[2 * m + 2];
+            df[m] = f[2 * m + 1] - f[2 * m + 2];
+        }
+        float drho = f[0] + eps;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) drho += sm[m];
+        float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+        float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const int i = 2 * m + 1;
+            const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+            if (cx == 1) jx += df[m]; else if (cx == -1) jx -= df[m];
+            if (cy == 1) jy += df[m]; else if (cy == -1) jy -= df[m];
+            if (cz == 1) jz += df[m]; else if (cz == -1) jz -= df[m];
+            if (cx) pxx += sm[m];
+            if (cy) pyy += sm[m];
+            if (cz) pzz += sm[m];
+            if (cx * cy == 1) pxy += sm[m]; else if (cx * cy == -1) pxy -= sm[m];
+            if (cx * cz == 1) pxz += sm[m]; else if (cx * cz == -1) pxz -= sm[m];
+            if (cy * cz == 1) pyz += sm[m]; else if (cy * cz == -1) pyz -= sm[m];
+        }
+        const float rho = rho0 + drho;
+        const float ir = __fdividef(1.0f, rho);
+        const float ux = (jx + 0.5f * gx) * ir, uy = (jy + 0.5f * gy) * ir, uz = (jz + 0.5f * gz) * ir;
+        const float uu = ux * ux + uy * uy + uz * uz;
+        const float ug = ux * gx + uy * gy + uz * gz;
+        // Pi_neq (the populations' second moment beyond the rest state w rho0
+        // is sum c c d + eps/3 I; that of the equilibrium rho/3 I + rho u u)
+        const float iso = (eps - drho) * (1.0f / 3.0f);
+        const float nxx = pxx + iso - rho * ux * ux, nyy = pyy + iso - rho * uy * uy, nzz = pzz + iso - rho * uz * uz;
+        const float nxy = pxy - rho * ux * uy, nxz = pxz - rho * ux * uz, nyz = pyz - rho * uy * uz;
+        const float tr3 = (nxx + nyy + nzz) * (1.0f / 3.0f);
+        const float cf = 1.0f - 0.5f * omega;
+        const float even0 = drho - 1.5f * rho * uu - 3.0f * cf * ug;   // times w: the even part's common terms
+        f[0] = w_of(0) * (even0 - om1 * 4.5f * tr3);
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const int i = 2 * m + 1;
+            const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+            const float w = w_of(i);
+            const float cu = cx * ux + cy * uy + cz * uz;
+            const float cg = cx * gx + cy * gy + cz * gz;
+            float qn = -tr3;
+            if (cx) qn += nxx;
+            if (cy) qn += nyy;
+            if (cz) qn += nzz;
+            if (cx * cy) qn += 2.0f * (cx * cy) * nxy;
+            if (cx * cz) qn += 2.0f * (cx * cz) * nxz;
+            if (cy * cz) qn += 2.0f * (cy * cz) * nyz;
+            const float sym = w * (even0 + 4.5f * rho * cu * cu + om1 * 4.5f * qn + 9.0f * cf * cu * cg);
+            const float asym = w * (3.0f * rho * cu + 1.5f * cg);
+            f[i] = sym + asym;
+            f[i + 1] = sym - asym;
+        }
+    }
 };
 
 using Collider = ColliderT<false>;
 
 // one node's collision with freshly set-up box terms
+template <bool GHOST = false>
 __device__ __forceinline__ void collide19(float (&f)[Q], float omega, float rho0, float gx, float gy,
                                           float gz, float eps)
 {
-    Collider C;
+    ColliderT<false, GHOST> C;
     C.init(omega, rho0, gx, gy, gz, eps);
     C.apply(f);
 }

@@ -89,6 +89,7 @@ struct lb_ctx {
     int list_cap = 0;                  // node list entries per boundary block
     int gx = 1;                        // boundary blocks per particle
     int fetch = 1;                     // bulk units a warp takes per counter fetch (lb_autotune)
+    int kprec = 0;                     // kernel variant: precision, or 3 for FP32 with the ghost-mode collision
     bool aux_pending = false;          // the auxiliary particle blocks of the last step kernel's
                                        // last iteration have not run yet (the next launch runs them)
     std::string err;
@@ -199,6 +200,7 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     if (o.max_particles <= 0) o.max_particles = 64;
     auto bad = [&](const std::string& m) { delete ctx; (void)m; return LB_EINVAL; };
     if (o.precision < 0 || o.precision > 2 || o.didt_mode < 0 || o.didt_mode > 2 || o.max_semi > 29 ||
+        o.collision < 0 || o.collision > 1 || (o.collision == 1 && o.precision != LB_FP32) ||
         (o.alloc && !o.release) || (!o.alloc && o.release))
         return bad("options");
     for (int b = 0; b < nbox; ++b) {
@@ -218,6 +220,7 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
         return LB_ECUDA;
     }
     ctx->elem = o.precision == LB_FP32 ? 4 : 2;
+    ctx->kprec = o.collision == 1 ? 3 : o.precision;
     const float scale = o.precision == LB_FP16 ? (float)(o.fp16_scale > 0 ? o.fp16_scale : 16384.0) : 1.0f;
     ctx->desc.assign(boxes, boxes + nbox);
     ctx->parts.assign(nbox, {});
@@ -460,6 +463,7 @@ extern "C" lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particl
             cube_of(q, s.h, s.S);
             s.box = b;
             s.aux_step = -1;
+            s.lsum_step = -1;
             pd.push_back(s);
             ++idx;
         }
@@ -603,9 +607,9 @@ static cudaError_t enqueue_iteration(lb_ctx* ctx, int first, int cur, cudaStream
 {
     cudaError_t e;
     if ((e = flush_aux(ctx, s)) != cudaSuccess) return e;
-    if ((e = launch_bulk(bulk_params(ctx, first, cur), ctx->opt.precision, ctx->total_blocks, s)) != cudaSuccess) return e;
+    if ((e = launch_bulk(bulk_params(ctx, first, cur), ctx->kprec, ctx->total_blocks, s)) != cudaSuccess) return e;
     if (ctx->np == 0) return cudaSuccess;
-    if ((e = launch_boundary(bnd_params(ctx, first, cur), ctx->opt.precision, ctx->np, s)) != cudaSuccess) return e;
+    if ((e = launch_boundary(bnd_params(ctx, first, cur), ctx->kprec, ctx->np, s)) != cudaSuccess) return e;
     const PParams pp = particle_params(ctx, cur);
     if ((e = launch_particles(pp, s)) != cudaSuccess) return e;
     return launch_particles_aux(pp, s);
@@ -627,7 +631,7 @@ static cudaError_t enqueue_steps(lb_ctx* ctx, int k, int cur, cudaStream_t s, co
     }
     // no reset of the counters: each launch leaves them at zero
     const cudaError_t e = launch_step(bulk, bnd, part, ctx->d_sync, ctx->d_status, ctx->np, ctx->gx, ctx->total_blocks,
-                                      k, cur, ctx->opt.precision, ctx->fetch, io_ft, io_rec, s);
+                                      k, cur, ctx->kprec, ctx->fetch, io_ft, io_rec, s);
     if (e == cudaSuccess && ctx->np > 0) ctx->aux_pending = true;
     return e;
 }
@@ -702,9 +706,9 @@ extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, 
         const BndParams np = bnd_params(ctx, first, ctx->cur);
         const PParams pp = particle_params(ctx, ctx->cur);
         CK(cudaEventRecord(ev[0], s));
-        CK(launch_bulk(bp, ctx->opt.precision, ctx->total_blocks, s));
+        CK(launch_bulk(bp, ctx->kprec, ctx->total_blocks, s));
         CK(cudaEventRecord(ev[1], s));
-        CK(launch_boundary(np, ctx->opt.precision, ctx->np, s));
+        CK(launch_boundary(np, ctx->kprec, ctx->np, s));
         CK(cudaEventRecord(ev[2], s));
         CK(launch_particles(pp, s));
         CK(cudaEventRecord(ev[3], s));

@@ -225,6 +225,8 @@ struct PartDev {
     long long step;
     double rec[RECD];               // F0, T0, F, T, U, Omega, x, q of the last iteration
     long long aux_step;             // value of `step` the auxiliary block last ran for (-1: none)
+    long long lsum[27];             // the auxiliary block's integer link sums of its map
+    long long lsum_step;            // value of `step` they belong to (-1: none)
     int nsolid, pad;
 };
 

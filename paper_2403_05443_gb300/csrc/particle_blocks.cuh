@@ -765,7 +765,7 @@ __device__ __forceinline__ uint64_t partner_row_mask(const PartDev* pd, const Pa
     return pm & maskS;
 }
 
-__device__ __forceinline__ void aux_block(const PParams& P, int p)
+static __device__ __noinline__ void aux_block(const PParams& P, int p)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     PartDev& G = P.pd[p];
@@ -829,12 +829,30 @@ __device__ __forceinline__ void aux_block(const PParams& P, int p)
     if (nnb > 0)
         for (int r = tid; r < Sd * Sd; r += ABLOCK)
             if (s_new[r] & s_pm[r]) atomicOr(P.status, ST_OVERLAP);
+    // the integer link sums depend on the map alone: when the new map is the
+    // last one, on the same cube (no partner, sums of the last pose kept),
+    // they are taken over instead of summed again; a particle covers or
+    // uncovers a node only every few tens of steps at these speeds
+    __shared__ int s_same;
+    if (tid == 0)
+        s_same = nnb == 0 && S.lsum_step == S.step - 1 && S.o[0] == S.o_prev[0] && S.o[1] == S.o_prev[1] &&
+                 S.o[2] == S.o_prev[2];
+    __syncthreads();
+    if (s_same) {
+        const uint64_t* ro = P.rows + ((long long)p * 2 + (S.slot ^ 1)) * (MAXS * MAXS);
+        bool diff = false;
+        for (int r = tid; r < Sd * Sd; r += ABLOCK) diff = diff || (__ldcg(ro + r) != s_new[r]);
+        if (__syncthreads_or(diff) && tid == 0) s_same = 0;
+        __syncthreads();
+    }
 
     // ---- integer link sums of the new map, one cube row per thread; the
     // direction loop is unrolled so that every c_b is a constant and the 27
     // sums stay in registers
     const bool squirmer = (S.B1 != 0.0 || S.B2 != 0.0);
-    {
+    if (s_same) {
+        if (tid < NSUM) s_sum[tid] = S.lsum[tid];
+    } else {
         int fu0 = 0, fu1 = 0, fu2 = 0, fu3 = 0, fu4 = 0, fu5 = 0;                 // FU: xx xy xz yy yz zz
         int fo[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};                                   // FOmega[i][j]
         int to0 = 0, to1 = 0, to2 = 0, to3 = 0, to4 = 0, to5 = 0;                 // TOmega: xx xy xz yy yz zz
@@ -887,7 +905,10 @@ __device__ __forceinline__ void aux_block(const PParams& P, int p)
             const long long v = (k >= 15 && k < 21) ? warp_sum_ll(acc[k]) : (long long)__reduce_add_sync(0xffffffffu, acc[k]);
             if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long*>(&s_sum[k]), (unsigned long long)v);
         }
+        __syncthreads();
+        if (tid < NSUM) G.lsum[tid] = s_sum[tid];
     }
+    if (tid == 0) G.lsum_step = S.step;
     if (squirmer) {
         // squirmer slip (Eq. ubsquirmer) at every link: sum w s c and sum w s (m x c)
         constexpr unsigned long long PX = pack_c(0), PY = pack_c(1), PZ = pack_c(2);
@@ -996,56 +1017,73 @@ __device__ __forceinline__ void aux_block(const PParams& P, int p)
     }
     __syncthreads();
     // ---- inverse of the solve matrix A = [[M + zeta_FU, zeta_FOmega], [zeta_TU, I + dI/dt + zeta_TOmega]]
+    // by blocks, A = [[P, B], [C, D]] (each 3 x 3): with X = P^-1 B, Y = C P^-1
+    // and the Schur complement S = D - C X,
+    //   A^-1 = [[P^-1 + X S^-1 Y, -X S^-1], [-S^-1 Y, S^-1]];
+    // P (M I + the drag's translation block) and S are symmetric positive
+    // definite up to the small dI/dt, so their 3 x 3 inverses by cofactors need
+    // no pivoting.  Lane e < 9 of warp 0 holds entry (e / 3, e % 3) of each
+    // 3 x 3 block: five short dependent rounds and two divisions instead of the
+    // six pivot steps of an elimination on the 6 x 6 system (the FP64 rate of
+    // this part makes every dependent step count).
     if (warp == 0) {
-        // Gauss-Jordan on [A | 1], column j on lane j (lanes 12..31 idle copies)
-        double col[6];
-        const int j = lane < 12 ? lane : 11;
+        double* sP = s_P;                           // free again: P^-1 in [0, 9), X [9, 18), Y [18, 27), S^-1 [27, 36)
+        const int e = lane < 9 ? lane : 8, r = e / 3, c = e % 3;
+        const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        auto Pm = [&](int a, int b) { return s_Z[a * 6 + b] + (a == b ? S.M : 0.0); };
+        auto Dm = [&](int a, int b) { return s_Z[(a + 3) * 6 + b + 3] + s_I[a * 3 + b] + s_dI[a * 3 + b]; };
+        // P^-1: the cofactor of entry (c, r) over det P (the inverse's (r, c) entry)
+        const double cofP = Pm(c1, r1) * Pm(c2, r2) - Pm(c1, r2) * Pm(c2, r1);
+        double detP = 0.0;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            double v;
-            if (j < 6) {
-                v = s_Z[i * 6 + j];
-                if (i == j && i < 3) v += S.M;
-                if (i >= 3 && j >= 3) v += s_I[(i - 3) * 3 + (j - 3)] + s_dI[(i - 3) * 3 + (j - 3)];
-            } else {
-                v = (i == j - 6) ? 1.0 : 0.0;
-            }
-            col[i] = v;
+        for (int k = 0; k < 3; ++k) detP += Pm(0, k) * __shfl_sync(0xffffffffu, cofP, k * 3);
+        bool ok = detP != 0.0;
+        const double Pi = cofP / detP;
+        if (lane < 9) sP[e] = Pi;
+        __syncwarp();
+        // X = P^-1 B, Y = C P^-1
+        double x = 0.0, y = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            x += sP[r * 3 + k] * s_Z[k * 6 + 3 + c];
+            y += s_Z[(3 + r) * 6 + k] * sP[k * 3 + c];
         }
-        bool ok = true;
+        if (lane < 9) { sP[9 + e] = x; sP[18 + e] = y; }
+        __syncwarp();
+        // S = D - C X, then S^-1 by cofactors
+        double sv = Dm(r, c);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            int piv = k;
-            if (lane == k) {
-                unsigned long long best = abs_bits(col[k]);
+        for (int k = 0; k < 3; ++k) sv -= s_Z[(3 + r) * 6 + k] * sP[9 + k * 3 + c];
+        if (lane < 9) sP[27 + e] = sv;
+        __syncwarp();
+        const double* Sm = sP + 27;
+        const double cofS = Sm[c1 * 3 + r1] * Sm[c2 * 3 + r2] - Sm[c1 * 3 + r2] * Sm[c2 * 3 + r1];
+        double detS = 0.0;
 #pragma unroll
-                for (int i = k + 1; i < 6; ++i) {
-                    const unsigned long long bi = abs_bits(col[i]);
-                    if (bi > best) { best = bi; piv = i; }
-                }
-            }
-            piv = __shfl_sync(0xffffffffu, piv, k);
-            double rowk = col[k], rowp = col[k];
+        for (int k = 0; k < 3; ++k) detS += Sm[k] * __shfl_sync(0xffffffffu, cofS, k * 3);
+        ok = ok && detS != 0.0;
+        const double Si = cofS / detS;
+        __syncwarp();
+        if (lane < 9) sP[27 + e] = Si;
+        __syncwarp();
+        // blocks of A^-1: S^-1 Y and X S^-1, then P^-1 + X (S^-1 Y)
+        double sy = 0.0, xs = 0.0;
 #pragma unroll
-            for (int i = k + 1; i < 6; ++i)
-                if (i == piv) rowp = col[i];
-#pragma unroll
-            for (int i = k + 1; i < 6; ++i)
-                if (i == piv) col[i] = rowk;
-            col[k] = rowp;
-            const double pv = __shfl_sync(0xffffffffu, col[k], k);
-            ok = ok && (pv != 0.0);
-            col[k] *= 1.0 / pv;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                if (i == k) continue;
-                const double fi = __shfl_sync(0xffffffffu, col[i], k);
-                col[i] -= fi * col[k];
-            }
+        for (int k = 0; k < 3; ++k) {
+            sy += sP[27 + r * 3 + k] * sP[18 + k * 3 + c];
+            xs += sP[9 + r * 3 + k] * sP[27 + k * 3 + c];
         }
-        if (lane >= 6 && lane < 12) {
+        __syncwarp();
+        if (lane < 9) sP[18 + e] = sy;              // Y no longer needed: S^-1 Y in its place
+        __syncwarp();
+        double tl = Pi;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) G.Ainv[i * 6 + (lane - 6)] = col[i];
+        for (int k = 0; k < 3; ++k) tl += sP[9 + r * 3 + k] * sP[18 + k * 3 + c];
+        if (lane < 9) {
+            G.Ainv[r * 6 + c] = tl;
+            G.Ainv[r * 6 + 3 + c] = -xs;
+            G.Ainv[(3 + r) * 6 + c] = -sy;
+            G.Ainv[(3 + r) * 6 + 3 + c] = Si;
         }
         if (lane == 0 && !ok) atomicOr(P.status, ST_NAN);
     } else if (warp == 1 && lane < 9) {

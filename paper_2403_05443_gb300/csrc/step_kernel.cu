@@ -252,6 +252,7 @@ cudaError_t launch_step(const BulkParams bulk[2], const BndParams bnd[2], const 
     const size_t smem = np > 0 ? maps + (size_t)bnd[0].list_cap * sizeof(unsigned) : 0;
     if (precision == 1) return launch_step_t<StF16>(sp, smem, s);
     if (precision == 2) return launch_step_t<StBF16>(sp, smem, s);
+    if (precision == 3) return launch_step_t<StF32G>(sp, smem, s);   // FP32, the paper's collision
     return launch_step_t<StF32>(sp, smem, s);
 }
 

@@ -43,7 +43,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("didt_mode", C.c_int32), ("device", C.c_int32),
                 ("flags", C.c_uint32), ("max_semi", C.c_int32), ("max_particles", C.c_int32),
                 ("fp16_scale", C.c_double), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
-                ("alloc_user", C.c_void_p)]
+                ("alloc_user", C.c_void_p), ("collision", C.c_int32)]
 
 
 class Particle(C.Structure):
@@ -327,7 +327,7 @@ class Simulation:
     """A context plus the particles of its boxes; marshals to the C entry points."""
 
     def __init__(self, boxes, particles=None, precision=LB_FP32, didt_mode=0, device=0, max_semi=16,
-                 max_particles=None, fp16_scale=0.0, separate_kernels=False, torch_alloc=False):
+                 max_particles=None, fp16_scale=0.0, separate_kernels=False, torch_alloc=False, collision=0):
         self.boxes = [dict(b) for b in boxes]
         parts = particles or [[] for _ in boxes]
         opt = Options()
@@ -336,6 +336,7 @@ class Simulation:
         opt.max_semi = int(max_semi)
         opt.max_particles = int(max_particles or max(1, sum(len(p) for p in parts)))
         opt.fp16_scale = float(fp16_scale)
+        opt.collision = int(collision)
         self._alloc = None
         if torch_alloc:
             self._alloc = _torch_allocator(device)

@@ -229,6 +229,22 @@ def test_cluster_of_three_particles():
     _compare_run([b], [parts], steps=60, every=6)
 
 
+@pytest.mark.parametrize("tau", [0.7, 1.3])
+def test_ghost_mode_collision(tau):
+    """The paper's collision (Sec. II.A: the non-equilibrium part projected on
+    the hydrodynamic modes and relaxed with tau, ghost modes set to
+    equilibrium; lb_options.collision = 1, FP32 storage) with a particle
+    covering and uncovering nodes, a counter force and a moving wall: every
+    field and particle value every 5 steps for 60 steps against the oracle's
+    form of the same scheme."""
+    g = rng(16)
+    b = box(24, 22, 28, tau, counter_force=1, walls=1, wall_u_lo=(-0.005, 0, 0), wall_u_hi=(0.005, 0, 0.001),
+            collision=1)
+    p = particle((4.5, 2.5, 2.0), (11.3, 10.7, 13.9), random_quaternion(g), U=(0.02, -0.01, 0.015),
+                 Om=(0.003, 0.004, -0.002), F_ext=(1e-3, 0, 0), density=3.0)
+    _compare_run([b], [[p]], steps=60, every=5, collision=1)
+
+
 def test_channel_walls_with_particle():
     """Moving walls (Couette) plus a free spheroid; nx = 20 is not a multiple of 128
     (rows shorter than a warp), ny not a power of two."""
