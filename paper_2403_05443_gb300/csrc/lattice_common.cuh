@@ -288,10 +288,15 @@ struct ColliderT {
 
     __device__ __forceinline__ void apply(float (&f)[Q]) const
     {
-        if (GHOST) {
+        if constexpr (GHOST) {
             apply_ghost(f);
-            return;
+        } else {
+            apply_bgk(f);
         }
+    }
+
+    __device__ __forceinline__ void apply_bgk(float (&f)[Q]) const
+    {
         float sm[9], df[9];
 #pragma unroll
         for (int m = 0; m < 9; ++m) {

@@ -519,6 +519,16 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
 
     // ---- occupancy of the new pose: one row per thread, FP32 test per node,
     // near-surface nodes listed for the exact test
+    // Along a row the value v(dx) = a dx^2 + 2 b dx + c is a convex quadratic, so
+    // the row's solid nodes form one interval between its roots.  Nodes at least
+    // one node from both roots have |v - 1| >= a >= 1/29^2, far above both the
+    // FP32 rounding of v and the 1e-4 band of the exact test, and are set from
+    // the interval; the nodes within 1.5 of a root (or within 3 of the vertex
+    // when the interval is shorter than 4 nodes) take the node-by-node test,
+    // which is the whole decision: the map is the one a test of every node gives.
+    const float qa = s_inv[0] * s_e[0][0] * s_e[0][0] + s_inv[1] * s_e[1][0] * s_e[1][0] +
+                     s_inv[2] * s_e[2][0] * s_e[2][0];
+    const uint64_t maskS = Sd >= 64 ? ~0ull : ((1ull << Sd) - 1ull);
     for (int r = tid; r < Sd * Sd; r += CBLOCK) {
         const int my = r % Sd, mz = r / Sd;
         const float dy = s_ro[1] + my, dz = s_ro[2] + mz;
@@ -526,19 +536,41 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
         const float t1 = s_e[1][1] * dy + s_e[1][2] * dz;
         const float t2 = s_e[2][1] * dy + s_e[2][2] * dz;
         uint64_t word = 0;
-        for (int mx = 0; mx < Sd; ++mx) {
+        auto test = [&](int mx) {
             // evaluated from dx directly, not accumulated, so rounding does not grow along the row
             const float dx = s_ro[0] + mx;
             const float u0 = s_e[0][0] * dx + t0;
             const float u1 = s_e[1][0] * dx + t1;
             const float u2 = s_e[2][0] * dx + t2;
             const float v = u0 * u0 * s_inv[0] + u1 * u1 * s_inv[1] + u2 * u2 * s_inv[2];
+            word &= ~(1ull << mx);
             if (fabsf(v - 1.0f) > 1e-4f) {
                 if (v < 1.0f) word |= 1ull << mx;
             } else {
                 const int slot = atomicAdd(&s_namb, 1);
                 if (slot < MAXAMB) s_amb[slot] = (mz << 16) | (my << 8) | mx;
             }
+        };
+        auto band = [&](float lo, float hi) {
+            const int i0 = max(0, (int)ceilf(lo)), i1 = min(Sd - 1, (int)floorf(hi));
+            for (int mx = i0; mx <= i1; ++mx) test(mx);
+        };
+        const float qb = s_inv[0] * s_e[0][0] * t0 + s_inv[1] * s_e[1][0] * t1 + s_inv[2] * s_e[2][0] * t2;
+        const float qc = s_inv[0] * t0 * t0 + s_inv[1] * t1 * t1 + s_inv[2] * t2 * t2;
+        const float disc = qb * qb - qa * (qc - 1.0f);
+        const float xv = -qb / qa - s_ro[0];        // the vertex, in cube nodes
+        if (disc < 4.0f * qa * qa) {
+            band(xv - 3.0f, xv + 3.0f);
+        } else {
+            const float hw = sqrtf(disc) / qa;     // half-width of the interval, >= 2
+            const float x1 = xv - hw, x2 = xv + hw;
+            const int i0 = max(0, (int)ceilf(x1 + 1.0f)), i1 = min(Sd - 1, (int)floorf(x2 - 1.0f));
+            if (i1 >= i0) {
+                const uint64_t hiMask = i1 >= 63 ? ~0ull : ((1ull << (i1 + 1)) - 1ull);
+                word = hiMask & ~((1ull << i0) - 1ull) & maskS;
+            }
+            band(x1 - 1.5f, x1 + 1.5f);
+            band(x2 - 1.5f, x2 + 1.5f);
         }
         s_rows[r] = word;
     }
@@ -592,19 +624,24 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
             return (dsh[0] == 1 ? (w >> 1) : (dsh[0] == -1 ? (w << 1) : w)) & maskS;
         };
         uint64_t* need = P.need + (size_t)p * (MAXS * MAXS);
+        // solid now or before, row (ay, az) of the new cube
+        auto uni = [&](int ay, int az) -> uint64_t {
+            if (ay < 0 || ay >= Sd || az < 0 || az >= Sd) return 0ull;
+            return s_rows[az * Sd + ay] | row_old(ay, az);
+        };
+        auto s3 = [](uint64_t w) { return w | (w << 1) | (w >> 1); };
         for (int r = tid; r < Sd * Sd; r += CBLOCK) {
             const int my = r % Sd, mz = r / Sd;
             const int Yu = s_o[1] + my;
             uint64_t nd = 0;
             if (py || (Yu > 0 && Yu < ny - 1)) {
-                uint64_t dil = 0;
-#pragma unroll
-                for (int b = 1; b < Q; ++b) {
-                    const int ay = my + cy_of(b), az = mz + cz_of(b);
-                    if (ay < 0 || ay >= Sd || az < 0 || az >= Sd) continue;
-                    const uint64_t nb = s_rows[az * Sd + ay] | row_old(ay, az);
-                    dil |= cx_of(b) == 1 ? (nb >> 1) : (cx_of(b) == -1 ? (nb << 1) : nb);
-                }
+                // the D3Q19 neighbourhood by rows: this row shifted by one node
+                // either way, the four face-adjacent rows shifted by -1, 0, +1,
+                // the four diagonal rows unshifted
+                const uint64_t u0 = uni(my, mz);
+                const uint64_t dil = (u0 << 1) | (u0 >> 1) | s3(uni(my - 1, mz)) | s3(uni(my + 1, mz)) |
+                                     s3(uni(my, mz - 1)) | s3(uni(my, mz + 1)) | uni(my - 1, mz - 1) |
+                                     uni(my + 1, mz - 1) | uni(my - 1, mz + 1) | uni(my + 1, mz + 1);
                 const uint64_t nw = s_rows[r], od = row_old(my, mz);
                 nd = (((dil | od) & ~nw) | (nw & ~od)) & maskS;
             }
