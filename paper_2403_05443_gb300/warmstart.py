@@ -67,10 +67,11 @@ def measure_mobility(samples, max_steps: int, force=1e-4, torque=None, device: i
 
     check_every = 0: `max_steps` iterations.  Otherwise each run goes to steady
     state: every check_every iterations the (U, b Omega) of every box is
-    compared with the last check's, and a batch stops once every box has
-    changed by less than tol (relative) at `checks` consecutive checks, or at
-    max_steps (history, a list, collects (step, largest change, median change)
-    of every check).  warm_fluid: each box starts from the lattice fluid's own steady
+    compared with the last check's; a sample is steady once its six boxes have
+    all changed by less than tol (relative) at `checks` consecutive checks, and
+    its mobility is taken then; a batch runs until all its samples are steady or
+    max_steps (history, a list, collects (step, largest change of a sample not
+    yet steady, median change) of every check).  warm_fluid: each box starts from the lattice fluid's own steady
     flow under its particle's force (lb_stokes_field, lb_init_fluid), the
     particles at rest, which leaves only the particle's and the near field's
     adjustment to relax.  Returns (M, steps used per sample, converged per
@@ -102,32 +103,48 @@ def measure_mobility(samples, max_steps: int, force=1e-4, torque=None, device: i
                 L.lb_stokes_field(sim.ctx, bi, u.data_ptr(), d.data_ptr())
                 L.lb_init_fluid(sim.ctx, bi, u.data_ptr(), u.numel() * 4, d.data_ptr(), True, True)
         bscale = np.repeat(np.array([s["b"] for s in chunk]), 6)[:, None]
+        nch = len(chunk)
+        rec_keep = np.zeros((len(boxes), 25))
         if check_every <= 0:
             sim.step(max_steps)
-            done_steps, ok = max_steps, False
+            rec_keep[:] = L.lb_get_force_torque(sim.ctx, -1, len(boxes))
+            used[s0:s0 + nch] = max_steps
         else:
-            prev, streak, done_steps, ok = None, 0, 0, False
-            while done_steps < max_steps:
+            # each sample is steady once all six of its boxes have changed by less
+            # than tol at `checks` consecutive checks; its records are kept from
+            # then on (a node the particle covers later jolts the velocity by
+            # ~1e-3 for a few hundred steps)
+            prev, streak = None, np.zeros(nch, int)
+            done = np.zeros(nch, bool)
+            steps = 0
+            while steps < max_steps and not done.all():
                 sim.step(check_every)
-                done_steps += check_every
+                steps += check_every
                 rec = L.lb_get_force_torque(sim.ctx, -1, len(boxes))
                 X = np.concatenate([rec[:, 12:15], rec[:, 15:18] * bscale], axis=1)
                 if prev is not None:
                     ch = np.linalg.norm(X - prev, axis=1) / np.maximum(np.linalg.norm(X, axis=1), 1e-300)
+                    chs = ch.reshape(nch, 6).max(axis=1)
                     if history is not None:
-                        history.append((done_steps, float(ch.max()), float(np.median(ch))))
-                    streak = streak + 1 if ch.max() < tol else 0
-                    if streak >= checks:
-                        ok = True
-                        break
+                        history.append((steps, float(chs[~done].max()) if (~done).any() else 0.0,
+                                        float(np.median(chs))))
+                    streak = np.where(chs < tol, streak + 1, 0)
+                    newly = (~done) & (streak >= checks)
+                    for i in np.nonzero(newly)[0]:
+                        rec_keep[6 * i:6 * i + 6] = rec[6 * i:6 * i + 6]
+                        used[s0 + i] = steps
+                        conv[s0 + i] = True
+                    done |= newly
                 prev = X
-        rec = L.lb_get_force_torque(sim.ctx, -1, len(boxes))
+            rest = np.nonzero(~done)[0]
+            for i in rest:
+                rec_keep[6 * i:6 * i + 6] = rec[6 * i:6 * i + 6]
+                used[s0 + i] = steps
         sim.close()
         for i, smp in enumerate(chunk):
-            used[s0 + i], conv[s0 + i] = done_steps, ok
             for k in range(6):
                 mag = fofs(smp) if k < 3 else tofs(smp)
-                r = rec[6 * i + k]
+                r = rec_keep[6 * i + k]
                 out[s0 + i, :3, k] = r[12:15] / mag
                 out[s0 + i, 3:, k] = r[15:18] / mag
     return out, used, conv
