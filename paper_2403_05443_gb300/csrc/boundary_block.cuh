@@ -2,6 +2,8 @@
 // boundary kernel and the persistent step kernel.
 #pragma once
 
+#include <type_traits>
+
 #include "lattice_common.cuh"
 
 namespace lbsph {
@@ -152,47 +154,67 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
     const unsigned long long pol = l2_evict_normal();
     T* D = reinterpret_cast<T*>(P.dst) + K.off;
 
-    // ---- this block's nodes; per-thread link sums
+    // ---- this block's nodes, two warps per node: the even warp of a pair takes
+    // the rest population and the directions 1..10, the odd warp 11..18 (each
+    // warp's path stays uniform and each thread's dependent chain is about half
+    // as long); the node's moments (and, for the ghost-mode collision, its second
+    // moments) are added up through shared memory, in one order on both warps, so
+    // that both take identical decisions and values.  Per-thread link sums.
     long long aF[3] = {0, 0, 0}, aT[3] = {0, 0, 0};
     auto rare_add = [&](int j, long long v) {
         if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&s_rare[j - ACC_COV]), (unsigned long long)v);
     };
+    constexpr int NX = St::GHOST ? 10 : 4;         // exchanged partial moments per node
+    __shared__ float s_xch[NW / 2][2][NX][32];
+    const int wpair = warp >> 1;
+    const int rounds = (count + (BBLOCK / 2) - 1) / (BBLOCK / 2);
 
-    for (int e = tid; e < count; e += BBLOCK) {
-        const unsigned code = s_list[e];
-        const int mx = code & 0xff, my = (code >> 8) & 0xff, mz = (code >> 16) & 0xff;
-        const int X = wrapd(K.ow_new[0] + mx, nx), Y = wrapd(K.ow_new[1] + my, ny), Z = wrapd(K.ow_new[2] + mz, nz);
-        const long long own = ((long long)Z * ny + Y) * nx + X;
-        const bool wallrow = walls && (Y == 0 || Y == ny - 1);
-        const bool sol_new = bit_new(mx, my, mz);
-        const bool sol_old = !FIRST && bit_old(mx, my, mz);
-        // partners: a node in the redo masks of two particles is done once, by
-        // the one of lower index; a partner may hold it now (pn) or before (po)
+    auto node_round = [&](auto Hc, int rnd) {
+        constexpr int H = decltype(Hc)::value;
+        auto mine = [](int i) { return H == 0 ? i <= 10 : i >= 11; };
+        const int e = rnd * (BBLOCK / 2) + wpair * 32 + lane;
+        bool act = e < count;
+        int mx = 0, my = 0, mz = 0, X = 0, Y = 0, Z = 0;
+        long long own = 0;
+        bool wallrow = false, sol_new = false, sol_old = false;
         int pn = -1, po = -1;
-        if (nnb > 0) {
-            bool dup = false;
-            for (int j = 0; j < nnb; ++j) {
-                if (K.nb[j] < p) {
-                    const NeedHdr& h = s_ph[j];
-                    int lx = X - h.ow[0], ly = Y - h.ow[1], lz = Z - h.ow[2];
-                    if (lx < 0) lx += nx;
-                    if (ly < 0) ly += ny;
-                    if (lz < 0) lz += nz;
-                    if (lx < h.S && ly < h.S && lz < h.S &&
-                        ((__ldcg(P.need + (size_t)K.nb[j] * (MAXS * MAXS) + lz * h.S + ly) >> lx) & 1ull))
-                        dup = true;
+        if (act) {
+            const unsigned code = s_list[e];
+            mx = code & 0xff; my = (code >> 8) & 0xff; mz = (code >> 16) & 0xff;
+            X = wrapd(K.ow_new[0] + mx, nx); Y = wrapd(K.ow_new[1] + my, ny); Z = wrapd(K.ow_new[2] + mz, nz);
+            own = ((long long)Z * ny + Y) * nx + X;
+            wallrow = walls && (Y == 0 || Y == ny - 1);
+            sol_new = bit_new(mx, my, mz);
+            sol_old = !FIRST && bit_old(mx, my, mz);
+            // partners: a node in the redo masks of two particles is done once, by
+            // the one of lower index; a partner may hold it now (pn) or before (po)
+            if (nnb > 0) {
+                bool dup = false;
+                for (int j = 0; j < nnb; ++j) {
+                    if (K.nb[j] < p) {
+                        const NeedHdr& h = s_ph[j];
+                        int lx = X - h.ow[0], ly = Y - h.ow[1], lz = Z - h.ow[2];
+                        if (lx < 0) lx += nx;
+                        if (ly < 0) ly += ny;
+                        if (lz < 0) lz += nz;
+                        if (lx < h.S && ly < h.S && lz < h.S &&
+                            ((__ldcg(P.need + (size_t)K.nb[j] * (MAXS * MAXS) + lz * h.S + ly) >> lx) & 1ull))
+                            dup = true;
+                    }
+                    if (pbit(j, true, X, Y, Z)) pn = j;
+                    if (!FIRST && pbit(j, false, X, Y, Z)) po = j;
                 }
-                if (pbit(j, true, X, Y, Z)) pn = j;
-                if (!FIRST && pbit(j, false, X, Y, Z)) po = j;
+                if (dup) act = false;
             }
-            if (dup) continue;
         }
         const bool solN = sol_new || pn >= 0, solO = sol_old || po >= 0;
-        bool write = !wallrow;
+        // 0 nothing, 1 solid before and after (untouched), 2 uncovered, 3 first
+        // collision, 4 fluid before (pull with bounce-back; covered if solid now)
+        const int kind = !act ? 0 : ((wallrow || (solN && (solO || FIRST))) ? 1 : (solO ? 2 : (FIRST ? 3 : 4)));
         float f[Q];
-        if (wallrow || (solN && (solO || FIRST))) {
-            write = false;                          // solid before and after: untouched
-        } else if (solO) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = 0.0f;
+        if (kind == 2) {
             // uncovered: f = f_eq(rho0, U + Omega x r) with r = x - x_c(t+1) of the
             // body that held it, whose sums get its cube coordinates m
             int m0 = mx, m1 = my, m2 = mz;
@@ -205,30 +227,35 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
             const float uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
+                if (!mine(i)) continue;
                 const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
                 f[i] = w_of(i) * rho0 * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
             }
-            const long long uv[10] = {1, m0, m1, m2, m0 * m0, m0 * m1, m0 * m2, m1 * m1, m1 * m2, m2 * m2};
-            for (int e2 = 0; e2 < 10; ++e2) {
-                if (sol_old) rare_add(ACC_UNC + e2, uv[e2]);
-                else padd(po, ACC_UNC + e2, uv[e2]);
+            if (H == 0) {
+                const long long uv[10] = {1, m0, m1, m2, m0 * m0, m0 * m1, m0 * m2, m1 * m1, m1 * m2, m2 * m2};
+                for (int e2 = 0; e2 < 10; ++e2) {
+                    if (sol_old) rare_add(ACC_UNC + e2, uv[e2]);
+                    else padd(po, ACC_UNC + e2, uv[e2]);
+                }
             }
-        } else if (FIRST) {
+        } else if (kind == 3) {
             // first collision: the node's initial distributions, no streaming
 #pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = St::ld1(A + ((long long)i * N + own), inv, pol);
-        } else {
-            // fluid at t-1: decide every source first, then issue the 19 loads together
+            for (int i = 0; i < Q; ++i)
+                if (mine(i)) f[i] = St::ld1(A + ((long long)i * N + own), inv, pol);
+        } else if (kind == 4) {
+            // fluid at t-1: decide every source first, then issue the loads together
             unsigned bb = 0, wl = 0, pb = 0;        // own, wall and partner bounce-back
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
+                if (!mine(i)) continue;
                 const int Ys = Y - cy_of(i);
                 if (walls && (Ys == 0 || Ys == ny - 1)) wl |= 1u << i;
                 else if (bit_old(mx - cx_of(i), my - cy_of(i), mz - cz_of(i))) bb |= 1u << i;
             }
             if (nnb > 0) {
                 for (int i = 1; i < Q; ++i) {
-                    if (((bb | wl) >> i) & 1u) continue;
+                    if (!mine(i) || (((bb | wl) >> i) & 1u)) continue;
                     const int Xs = wrapd(X - cx_of(i), nx), Ys = wrapd(Y - cy_of(i), ny), Zs = wrapd(Z - cz_of(i), nz);
                     for (int j = 0; j < nnb; ++j)
                         if (pbit(j, false, Xs, Ys, Zs)) pb |= 1u << i;
@@ -237,6 +264,7 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
+                if (!mine(i)) continue;
                 const bool back = ((bb | wl) >> i) & 1u;
                 const long long src = back ? (long long)opp_of(i) * N + own
                                            : (long long)i * N + ((long long)wrapd(Z - cz_of(i), nz) * ny + wrapd(Y - cy_of(i), ny)) * nx +
@@ -247,7 +275,7 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
             const float ex[3] = {K.e_old[0], K.e_old[1], K.e_old[2]};
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
-                if (!(((bb | wl) >> i) & 1u)) continue;
+                if (!mine(i) || !(((bb | wl) >> i) & 1u)) continue;
                 float ubc;
                 if ((wl >> i) & 1u) {
                     const float* uw = (Y - cy_of(i) == 0) ? K.uw_lo : K.uw_hi;
@@ -289,37 +317,62 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
                 }
                 f[i] += 6.0f * w_of(i) * rho0 * ubc;
             }
-            if (solN) {
-                // covered: mass and momentum go to the next solve of the body that
-                // holds the node now
-                write = false;
-                float drho = 0.f;
+        }
+        // ---- the node's moments: this warp's part and the partner warp's
+        float tot[NX];
+        {
+            float part[NX];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) drho += f[i];
-                const float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
-                const float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
-                const float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
-                const long long Jx = fixq(jx), Jy = fixq(jy), Jz = fixq(jz);
-                int m0 = mx, m1 = my, m2 = mz;
-                if (!sol_new) ploc(pn, true, X, Y, Z, m0, m1, m2);
-                const long long cv[8] = {1, fixq(drho), Jx, Jy, Jz, m1 * Jz - m2 * Jy, m2 * Jx - m0 * Jz,
-                                         m0 * Jy - m1 * Jx};
-                for (int e2 = 0; e2 < 8; ++e2) {
-                    if (sol_new) rare_add(ACC_COV + e2, cv[e2]);
-                    else padd(pn, ACC_COV + e2, cv[e2]);
+            for (int k = 0; k < NX; ++k) part[k] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (!mine(i)) continue;
+                const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+                part[0] += f[i];
+                if (cx) part[1] += cx * f[i];
+                if (cy) part[2] += cy * f[i];
+                if (cz) part[3] += cz * f[i];
+                if constexpr (NX > 4) {
+                    if (cx) part[4] += f[i];
+                    if (cy) part[5] += f[i];
+                    if (cz) part[6] += f[i];
+                    if (cx * cy) part[7] += (cx * cy) * f[i];
+                    if (cx * cz) part[8] += (cx * cz) * f[i];
+                    if (cy * cz) part[9] += (cy * cz) * f[i];
                 }
+            }
+#pragma unroll
+            for (int k = 0; k < NX; ++k) s_xch[wpair][H][k][lane] = part[k];
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + wpair), "r"(64) : "memory");
+#pragma unroll
+            for (int k = 0; k < NX; ++k) tot[k] = s_xch[wpair][0][k][lane] + s_xch[wpair][1][k][lane];
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + wpair), "r"(64) : "memory");
+        }
+        bool write = kind == 2 || kind == 3 || (kind == 4 && !solN);
+        if (kind == 4 && solN && H == 0) {
+            // covered: mass and momentum go to the next solve of the body that
+            // holds the node now
+            const long long Jx = fixq(tot[1]), Jy = fixq(tot[2]), Jz = fixq(tot[3]);
+            int m0 = mx, m1 = my, m2 = mz;
+            if (!sol_new) ploc(pn, true, X, Y, Z, m0, m1, m2);
+            const long long cv[8] = {1, fixq(tot[0]), Jx, Jy, Jz, m1 * Jz - m2 * Jy, m2 * Jx - m0 * Jz,
+                                     m0 * Jy - m1 * Jx};
+            for (int e2 = 0; e2 < 8; ++e2) {
+                if (sol_new) rare_add(ACC_COV + e2, cv[e2]);
+                else padd(pn, ACC_COV + e2, cv[e2]);
             }
         }
         if (write) {
-            collide19<St::GHOST>(f, K.omega, rho0, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps);
+            collide_half<St::GHOST, H>(f, tot, K.omega, rho0, dyn.g[0], dyn.g[1], dyn.g[2], dyn.eps);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) St::st1(D + (long long)i * N + own, f[i], scale, pol);
+            for (int i = 0; i < Q; ++i)
+                if (mine(i)) St::st1(D + (long long)i * N + own, f[i], scale, pol);
             // momentum-exchange sums of the new links (x, b), with f*(t)
             long long fx = 0, fy = 0, fz = 0;
             bool any = false;
 #pragma unroll
             for (int b = 1; b < Q; ++b) {
-                if (!bit_new(mx + cx_of(b), my + cy_of(b), mz + cz_of(b))) continue;
+                if (!mine(b) || !bit_new(mx + cx_of(b), my + cy_of(b), mz + cz_of(b))) continue;
                 const long long d = fixq(f[b]);
                 any = true;
                 if (cx_of(b) == 1) fx += d; else if (cx_of(b) == -1) fx -= d;
@@ -335,6 +388,7 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
             // links to partners' surfaces: their sums, about their cube origins
             if (nnb > 0) {
                 for (int b = 1; b < Q; ++b) {
+                    if (!mine(b)) continue;
                     const int Xb = wrapd(X + cx_of(b), nx), Yb = wrapd(Y + cy_of(b), ny), Zb = wrapd(Z + cz_of(b), nz);
                     for (int j = 0; j < nnb; ++j) {
                         if (!pbit(j, true, Xb, Yb, Zb)) continue;
@@ -349,11 +403,16 @@ __device__ __forceinline__ void boundary_block(const BndParams& P, int p, int c)
                     }
                 }
             }
-        } else if (solN && !wallrow) {
+        } else if (act && solN && !wallrow) {
             // solid now: zero it (never read as a source)
 #pragma unroll
-            for (int i = 0; i < Q; ++i) St::st1(D + (long long)i * N + own, 0.0f, scale, pol);
+            for (int i = 0; i < Q; ++i)
+                if (mine(i)) St::st1(D + (long long)i * N + own, 0.0f, scale, pol);
         }
+    };
+    for (int rnd = 0; rnd < rounds; ++rnd) {
+        if (warp & 1) node_round(std::integral_constant<int, 1>{}, rnd);
+        else node_round(std::integral_constant<int, 0>{}, rnd);
     }
 
     // ---- per-warp link sums into shared memory, then one atomic per nonzero sum

@@ -416,6 +416,70 @@ __device__ __forceinline__ void collide19(float (&f)[Q], float omega, float rho0
 }
 
 
+// The collision of one node, split between two threads: half H = 0 updates the
+// rest population and the pairs of directions 1..10, H = 1 the pairs 11..18,
+// both from the node's totals t = (sum d, j, and for GHOST the second moments
+// sum c c d), which both halves hold bit for bit.  The formulas are those of
+// ColliderT (unscaled populations), with the same eps convention: w_i eps is
+// added to every population first.
+template <bool GHOST, int H, int NT>
+__device__ __forceinline__ void collide_half(float (&f)[Q], const float (&t)[NT], float omega, float rho0,
+                                             float gx, float gy, float gz, float eps)
+{
+    const float om1 = 1.0f - omega, cf = 1.0f - 0.5f * omega;
+    const float drho = t[0] + eps;
+    const float rho = rho0 + drho;
+    const float ir = __fdividef(1.0f, rho);
+    const float ux = (t[1] + 0.5f * gx) * ir, uy = (t[2] + 0.5f * gy) * ir, uz = (t[3] + 0.5f * gz) * ir;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float ug = ux * gx + uy * gy + uz * gz;
+    if constexpr (!GHOST) {
+        const float orho = omega * rho;
+        const float Pc = omega * drho - 1.5f * orho * uu - 3.0f * cf * ug + om1 * eps;
+        if (H == 0) f[0] = om1 * f[0] + w_of(0) * Pc;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const int i = 2 * m + 1;
+            if (H == 0 ? i > 10 : i < 11) continue;
+            const float w = w_of(i);
+            const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
+            const float l = (3.0f * w) * cf * (cx_of(i) * gx + cy_of(i) * gy + cz_of(i) * gz);
+            const float sym = w * Pc + cu * ((4.5f * w) * orho * cu + 3.0f * l);
+            const float asym = (3.0f * w) * orho * cu + l;
+            f[i] = om1 * f[i] + (sym + asym);
+            f[i + 1] = om1 * f[i + 1] + (sym - asym);
+        }
+    } else {
+        static_assert(NT >= 10, "the ghost-mode collision needs the second moments");
+        const float iso = (eps - drho) * (1.0f / 3.0f);
+        const float nxx = t[4] + iso - rho * ux * ux, nyy = t[5] + iso - rho * uy * uy, nzz = t[6] + iso - rho * uz * uz;
+        const float nxy = t[7] - rho * ux * uy, nxz = t[8] - rho * ux * uz, nyz = t[9] - rho * uy * uz;
+        const float tr3 = (nxx + nyy + nzz) * (1.0f / 3.0f);
+        const float even0 = drho - 1.5f * rho * uu - 3.0f * cf * ug;
+        if (H == 0) f[0] = w_of(0) * (even0 - om1 * 4.5f * tr3);
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+            const int i = 2 * m + 1;
+            if (H == 0 ? i > 10 : i < 11) continue;
+            const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+            const float w = w_of(i);
+            const float cu = cx * ux + cy * uy + cz * uz;
+            const float cg = cx * gx + cy * gy + cz * gz;
+            float qn = -tr3;
+            if (cx) qn += nxx;
+            if (cy) qn += nyy;
+            if (cz) qn += nzz;
+            if (cx * cy) qn += 2.0f * (cx * cy) * nxy;
+            if (cx * cz) qn += 2.0f * (cx * cz) * nxz;
+            if (cy * cz) qn += 2.0f * (cy * cz) * nyz;
+            const float sym = w * (even0 + 4.5f * rho * cu * cu + om1 * 4.5f * qn + 9.0f * cf * cu * cg);
+            const float asym = w * (3.0f * rho * cu + 1.5f * cg);
+            f[i] = sym + asym;
+            f[i + 1] = sym - asym;
+        }
+    }
+}
+
 __device__ __forceinline__ long long fixp(float v) { return __float2ll_rn(v * FIXF); }
 
 __device__ __forceinline__ int wrapd(int m, int L) { return m < 0 ? m + L : (m >= L ? m - L : m); }
