@@ -156,6 +156,32 @@ __device__ __forceinline__ double quat_step_component(const double Wm[3], const 
     return qn;
 }
 
+// The same component of q' = qt(Wm) q written as q + (qt - 1) q, for the
+// small rotations of a step (|Wm| < 0.01): the increment's entries
+// (cos(th/2) - 1, sin(th/2)/th Wm) are formed in FP32 from their Taylor series
+// (each is of the order of the angle turned or its square, so their FP32
+// rounding lies far below the FP64 rounding of q) and applied in FP64: four
+// FP64 multiply-adds instead of the whole step in FP64.  Larger rotations take
+// quat_step_component.  Lane k < 3 of the warp holds Wm[k] in wk; every lane
+// gets the component jq.
+__device__ __forceinline__ double quat_step_component_small(float wk, const double* q, int jq)
+{
+    const float w0 = __shfl_sync(0xffffffffu, wk, 0), w1 = __shfl_sync(0xffffffffu, wk, 1),
+                w2 = __shfl_sync(0xffffffffu, wk, 2);
+    const float x2 = 0.25f * (w0 * w0 + w1 * w1 + w2 * w2);
+    const float cm1 = -x2 * (0.5f - x2 * (1.0f / 24.0f - x2 * (1.0f / 720.0f)));
+    const float sc = 0.5f * (1.0f - x2 * (1.0f / 6.0f - x2 * (1.0f / 120.0f - x2 * (1.0f / 5040.0f))));
+    const float dt[4] = {cm1, sc * w0, sc * w1, sc * w2};
+    constexpr unsigned NEG = (1u << 1) | (1u << 2) | (1u << 3) | (1u << 7) | (1u << 9) | (1u << 14);
+    double qn = q[jq];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float ds = ((NEG >> (jq * 4 + m)) & 1u) ? -dt[m] : dt[m];
+        qn = fma((double)ds, q[m ^ jq], qn);
+    }
+    return qn;
+}
+
 // Solution of the 6x6 system A x = b by Gauss-Jordan elimination with partial
 // pivoting, one warp: lane j < 6 holds column j of A, lane 6 holds b (col[i] =
 // row i); on return lane 6 holds x.  Returns false if a pivot vanishes.
@@ -238,7 +264,9 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
     extern __shared__ uint64_t s_maps[];            // both ring slots of the occupancy map, smax*smax rows each
     __shared__ double s_E[9], s_A[9], s_xc[3], s_dm;
     __shared__ float s_e[3][3], s_inv[3], s_ro[3];
+    __shared__ double s_x6[6], s_ft0[6];             // the solution and F0, T0 (force and torque records)
     __shared__ int s_o[3], s_nsolid, s_namb;
+    __shared__ int s_ext[4];                        // rows solid now or before: y min, max, z min, max (new cube)
     __shared__ int s_amb[MAXAMB];
     __shared__ double s_FL[3], s_fpair[MAXPB][3];   // lubrication: total and per other particle of the box
     __shared__ int s_nnb, s_nbl[MAXNB];
@@ -259,7 +287,11 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
             s_maps[r] = __ldcg(r0 + r);
             s_maps[n + r] = __ldcg(r0 + MAXS * MAXS + r);
         }
-        if (tid == 0) { s_nsolid = 0; s_namb = 0; s_dm = 0.0; }
+        if (tid == 0) {
+            s_nsolid = 0; s_namb = 0; s_dm = 0.0;
+            s_ext[0] = s_ext[2] = 1 << 20;
+            s_ext[1] = s_ext[3] = -(1 << 20);
+        }
     }
     __syncthreads();
     if (io_ft) {
@@ -433,54 +465,52 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
             }
             x6 = xr;
         }
-        // F = F0 - zeta_FU U' - zeta_FOmega Omega' (Eq. Fsplit) + the lubrication
-        // force, T likewise (Eq. Tsplit)
-        double xs[6], ft = isT ? ft0 : ft0 + s_FL[k];
+        // the solution to every lane; x6 and ft0 kept for the force and torque
+        // records, which are formed after the new pose is out
+        double xs[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            xs[j] = __shfl_sync(0xffffffffu, x6, j);
-            ft -= S.zeta[row * 6 + j] * xs[j];
-        }
+        for (int j = 0; j < 6; ++j) xs[j] = __shfl_sync(0xffffffffu, x6, j);
+        if (lane < 6) { s_x6[lane] = x6; s_ft0[lane] = ft0; }
         // Eq. posupdate, Eq. qnplus0-1: rotation by Omega_mid = (Omega + Omega') / 2
-        double Wm[3];
-        for (int a = 0; a < 3; ++a) Wm[a] = 0.5 * (S.W[a] + xs[3 + a]);
-        const double qn = quat_step_component(Wm, S.q, lane & 3);
+        // (lane k < 3 forms component k)
+        const double wmk = 0.5 * (S.W[k] + xs[3 + k]);
+        const float wkf = (float)wmk;
+        double qn;
+        const float th2 = __shfl_sync(0xffffffffu, wkf, 0) * __shfl_sync(0xffffffffu, wkf, 0) +
+                          __shfl_sync(0xffffffffu, wkf, 1) * __shfl_sync(0xffffffffu, wkf, 1) +
+                          __shfl_sync(0xffffffffu, wkf, 2) * __shfl_sync(0xffffffffu, wkf, 2);
+        if (th2 < 1e-4f) {
+            qn = quat_step_component_small(wkf, S.q, lane & 3);
+        } else {
+            double Wm[3];
+            for (int a = 0; a < 3; ++a) Wm[a] = __shfl_sync(0xffffffffu, wmk, a);
+            qn = quat_step_component(Wm, S.q, lane & 3);
+        }
         // body x axis at t (the squirmer's axis for the next bounce-back):
         // R_k0 = base + 2 (qa qb + s qc qd)
         const double* q = S.q;
         const double qa = q[k == 0 ? 2 : 1], qb = q[k == 0 ? 2 : (k == 1 ? 2 : 3)];
         const double qc = q[k == 0 ? 3 : 0], qd = q[k == 0 ? 3 : (k == 1 ? 3 : 2)];
-        const double t2 = fma(k == 2 ? -qc : qc, qd, qa * qb);
-        const double ex = fma(k == 0 ? -2.0 : 2.0, t2, k == 0 ? 1.0 : 0.0);
         const double xk = S.x[k], Uk = S.U[k], phik = S.phi[k];
         const int ok = S.o[k];
-        const double ft0_t = __shfl_sync(0xffffffffu, ft0, 3 + k);
-        const double ft_t = __shfl_sync(0xffffffffu, ft, 3 + k);
+        const double xn = xk + 0.5 * (Uk + xs[k]);
         __syncwarp();
         if (lane < 3) {
             const int L = k == 0 ? nx : (k == 1 ? ny : nz);
-            K.ow_old[k] = wrapi(ok, L);
-            K.ro_old[k] = (float)phik;
-            K.e_old[k] = (float)ex;
-            const double xn = xk + 0.5 * (Uk + xs[k]);
             S.x[k] = xn;
             S.U[k] = xs[k];
             S.W[k] = xs[3 + k];
             S.o_prev[k] = ok;
-            S.rec[k] = ft0; S.rec[3 + k] = ft0_t;
-            S.rec[6 + k] = ft; S.rec[9 + k] = ft_t;
+            K.ow_old[k] = wrapi(ok, L);
+            K.ro_old[k] = (float)phik;
+            const double t2 = fma(k == 2 ? -qc : qc, qd, qa * qb);
+            K.e_old[k] = (float)fma(k == 0 ? -2.0 : 2.0, t2, k == 0 ? 1.0 : 0.0);
             S.rec[12 + k] = xs[k]; S.rec[15 + k] = xs[3 + k]; S.rec[18 + k] = xn;
         }
         if (lane < 4) { S.q[lane] = qn; S.rec[21 + lane] = qn; }
         if (lane == 0) {
             K.rows_old = P.rows + ((long long)p * 2 + S.slot) * (MAXS * MAXS);
             K.dm_return = s_dm;
-        }
-        __syncwarp();
-        if (lane < 25) {
-            // exponent all ones: Inf or NaN
-            const unsigned long long b = (unsigned long long)__double_as_longlong(S.rec[lane]);
-            if (((b >> 52) & 0x7ff) == 0x7ff) atomicOr(P.status, ST_NAN);
         }
     } else if (warp == 0 && lane == 0) {
         // initial pose: no remap before, nothing to return
@@ -498,10 +528,18 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
     if (warp == 0) {
         if (lane < 3) {
             const int o = (int)floor(S.x[lane]) - S.h;
+            const float ro = (float)((double)o - S.x[lane]);
             s_o[lane] = o;
             s_xc[lane] = S.x[lane];
-            s_ro[lane] = (float)((double)o - S.x[lane]);
+            s_ro[lane] = ro;
             s_inv[lane] = (float)S.inv_semi2[lane];
+            // the snapshot's new pose and velocities, one component per lane
+            K.ow_new[lane] = wrapi(o, lane == 0 ? nx : (lane == 1 ? ny : nz));
+            K.ro_new[lane] = ro;
+            K.U[lane] = (float)S.U[lane];
+            K.W[lane] = (float)S.W[lane];
+            K.Fext[lane] = S.Fext[lane];
+            if (lane == 1) K.oy_new = o;
         } else if (lane == 3) {
             const double* q = S.q;
             const float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
@@ -517,70 +555,147 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
     }
     __syncthreads();
 
-    // ---- occupancy of the new pose: one row per thread, FP32 test per node,
-    // near-surface nodes listed for the exact test
-    // Along a row the value v(dx) = a dx^2 + 2 b dx + c is a convex quadratic, so
-    // the row's solid nodes form one interval between its roots.  Nodes at least
-    // one node from both roots have |v - 1| >= a >= 1/29^2, far above both the
-    // FP32 rounding of v and the 1e-4 band of the exact test, and are set from
-    // the interval; the nodes within 1.5 of a root (or within 3 of the vertex
-    // when the interval is shorter than 4 nodes) take the node-by-node test,
-    // which is the whole decision: the map is the one a test of every node gives.
-    const float qa = s_inv[0] * s_e[0][0] * s_e[0][0] + s_inv[1] * s_e[1][0] * s_e[1][0] +
-                     s_inv[2] * s_e[2][0] * s_e[2][0];
+    // ---- warp 0: the shape matrix of the exact test (FP64, needed only if a
+    // node turns out ambiguous, formed while the other warps build the map) and
+    // the force and torque records; warps 1..: occupancy of the new pose, one
+    // row per thread, FP32 test per node, near-surface nodes listed for the
+    // exact test.
     const uint64_t maskS = Sd >= 64 ? ~0ull : ((1ull << Sd) - 1ull);
-    for (int r = tid; r < Sd * Sd; r += CBLOCK) {
-        const int my = r % Sd, mz = r / Sd;
-        const float dy = s_ro[1] + my, dz = s_ro[2] + mz;
-        const float t0 = s_e[0][1] * dy + s_e[0][2] * dz;
-        const float t1 = s_e[1][1] * dy + s_e[1][2] * dz;
-        const float t2 = s_e[2][1] * dy + s_e[2][2] * dz;
-        uint64_t word = 0;
-        auto test = [&](int mx) {
-            // evaluated from dx directly, not accumulated, so rounding does not grow along the row
-            const float dx = s_ro[0] + mx;
-            const float u0 = s_e[0][0] * dx + t0;
-            const float u1 = s_e[1][0] * dx + t1;
-            const float u2 = s_e[2][0] * dx + t2;
-            const float v = u0 * u0 * s_inv[0] + u1 * u1 * s_inv[1] + u2 * u2 * s_inv[2];
-            word &= ~(1ull << mx);
-            if (fabsf(v - 1.0f) > 1e-4f) {
-                if (v < 1.0f) word |= 1ull << mx;
-            } else {
-                const int slot = atomicAdd(&s_namb, 1);
-                if (slot < MAXAMB) s_amb[slot] = (mz << 16) | (my << 8) | mx;
+    if (warp == 0) {
+        canon_shape_warp(S.inv_semi2, S.q, s_E, s_A, lane);
+        if (!P.init) {
+            // F = F0 - zeta_FU U' - zeta_FOmega Omega' (Eq. Fsplit) + the
+            // lubrication force, T likewise (Eq. Tsplit)
+            const int row = lane < 6 ? lane : 5;
+            double ft = s_ft0[row] + (row < 3 ? s_FL[row] : 0.0);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) ft -= S.zeta[row * 6 + j] * s_x6[j];
+            if (lane < 6) {
+                S.rec[lane] = s_ft0[lane];
+                S.rec[6 + lane] = ft;
             }
-        };
-        auto band = [&](float lo, float hi) {
-            const int i0 = max(0, (int)ceilf(lo)), i1 = min(Sd - 1, (int)floorf(hi));
-            for (int mx = i0; mx <= i1; ++mx) test(mx);
-        };
-        const float qb = s_inv[0] * s_e[0][0] * t0 + s_inv[1] * s_e[1][0] * t1 + s_inv[2] * s_e[2][0] * t2;
-        const float qc = s_inv[0] * t0 * t0 + s_inv[1] * t1 * t1 + s_inv[2] * t2 * t2;
-        const float disc = qb * qb - qa * (qc - 1.0f);
-        const float xv = -qb / qa - s_ro[0];        // the vertex, in cube nodes
-        if (disc < 4.0f * qa * qa) {
-            band(xv - 3.0f, xv + 3.0f);
-        } else {
-            const float hw = sqrtf(disc) / qa;     // half-width of the interval, >= 2
-            const float x1 = xv - hw, x2 = xv + hw;
-            const int i0 = max(0, (int)ceilf(x1 + 1.0f)), i1 = min(Sd - 1, (int)floorf(x2 - 1.0f));
-            if (i1 >= i0) {
-                const uint64_t hiMask = i1 >= 63 ? ~0ull : ((1ull << (i1 + 1)) - 1ull);
-                word = hiMask & ~((1ull << i0) - 1ull) & maskS;
+            __syncwarp();
+            if (lane < 25) {
+                // exponent all ones: Inf or NaN
+                const unsigned long long b = (unsigned long long)__double_as_longlong(S.rec[lane]);
+                if (((b >> 52) & 0x7ff) == 0x7ff) atomicOr(P.status, ST_NAN);
             }
-            band(x1 - 1.5f, x1 + 1.5f);
-            band(x2 - 1.5f, x2 + 1.5f);
         }
-        s_rows[r] = word;
+    } else {
+        // Along a row the value v(dx) = a dx^2 + 2 b dx + c is a convex quadratic,
+        // so the row's solid nodes form one interval between its roots.  Nodes at
+        // least one node from both roots have |v - 1| >= a >= 1/29^2, far above
+        // both the FP32 rounding of v and the 1e-4 band of the exact test, and are
+        // set from the interval; the nodes within 1.5 of a root (or within 3 of the
+        // vertex when the interval is shorter than 4 nodes) take the node-by-node
+        // test, which is the whole decision: the map is the one a test of every
+        // node gives.  v = sum_m (e_m . d / s_m)^2 with the body axes scaled by
+        // 1 / s_m: a sum of three nonnegative squares, each at most v, so its FP32
+        // rounding stays a few units of 1e-7 near the surface.
+        float es[3][3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float sm = sqrtf(s_inv[m]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) es[m][c] = s_e[m][c] * sm;
+        }
+        const float ro0 = s_ro[0], ro1 = s_ro[1], ro2 = s_ro[2];
+        const float qa = es[0][0] * es[0][0] + es[1][0] * es[1][0] + es[2][0] * es[2][0];
+        // With every semi-axis at least one node (1 / s_m^2 <= 1) and cube sides
+        // of at most 64 nodes the FP32 rounding of the row minimum
+        // v_min = 1 - disc / a stays below 1e-3, so a row with v_min > 1.01 has no
+        // solid node and needs no test, and the FP32 roots are within 0.1 node of
+        // the exact ones, so nodes half a node from both have |v - 1| >= 1.7 a
+        // and the root bands can be one node wide; otherwise the wide bands.
+        const bool narrow = fmaxf(s_inv[0], fmaxf(s_inv[1], s_inv[2])) <= 1.0f;
+        const float wb = narrow ? 0.5f : 1.5f;
+        const int dsh1 = P.init ? 0 : s_o[1] - S.o[1], dsh2 = P.init ? 0 : s_o[2] - S.o[2];
+        int ey0 = 1 << 20, ey1 = -(1 << 20), ez0 = 1 << 20, ez1 = -(1 << 20);   // rows solid now or before
+        for (int base = (warp - 1) * 32; base < Sd * Sd; base += CBLOCK - 32) {
+            const int r = base + lane;
+            if (r < Sd * Sd) {
+                const int my = r % Sd, mz = r / Sd;
+                const float dy = ro1 + my, dz = ro2 + mz;
+                const float t0 = es[0][1] * dy + es[0][2] * dz;
+                const float t1 = es[1][1] * dy + es[1][2] * dz;
+                const float t2 = es[2][1] * dy + es[2][2] * dz;
+                const float qb = es[0][0] * t0 + es[1][0] * t1 + es[2][0] * t2;
+                const float qc = t0 * t0 + t1 * t1 + t2 * t2;
+                const float disc = qb * qb - qa * (qc - 1.0f);
+                const float xv = __fdividef(-qb, qa) - ro0;     // the vertex, in cube nodes
+                uint64_t word = 0;
+                bool touched = false;
+                // node ranges of the node-by-node test: around the vertex, or around each root
+                float bl0 = 0.0f, bl1 = 0.0f;
+                int nbands = 0;
+                if (narrow && disc < -0.01f * qa) {
+                    nbands = 0;                         // v > 1.01 along the whole row
+                } else if (disc < 4.0f * qa * qa) {
+                    bl0 = xv - 3.0f;
+                    bl1 = xv + 3.0f;
+                    nbands = 1;
+                } else {
+                    const float hw = __fdividef(disc * rsqrtf(disc), qa);   // half-width of the interval, >= 2
+                    const float x1 = xv - hw, x2 = xv + hw;
+                    const int i0 = max(0, (int)ceilf(x1 + wb)), i1 = min(Sd - 1, (int)floorf(x2 - wb));
+                    if (i1 >= i0) {
+                        const uint64_t hiMask = i1 >= 63 ? ~0ull : ((1ull << (i1 + 1)) - 1ull);
+                        word = hiMask & ~((1ull << i0) - 1ull) & maskS;
+                    }
+                    bl0 = x1 - wb;
+                    bl1 = x2 - wb;
+                    nbands = 2;
+                }
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    if (b >= nbands) break;
+                    const float lo = b == 0 ? bl0 : bl1, hi = nbands == 1 ? bl1 : lo + 2.0f * wb;
+                    const int m0 = max(0, (int)ceilf(lo)), m1 = min(Sd - 1, (int)floorf(hi));
+                    for (int mx = m0; mx <= m1; ++mx) {
+                        // evaluated from dx directly, not accumulated, so rounding does not grow along the row
+                        const float dx = ro0 + mx;
+                        const float u0 = es[0][0] * dx + t0;
+                        const float u1 = es[1][0] * dx + t1;
+                        const float u2 = es[2][0] * dx + t2;
+                        const float v = u0 * u0 + u1 * u1 + u2 * u2;
+                        const uint64_t bit = 1ull << mx;
+                        if (fabsf(v - 1.0f) > 1e-4f) {
+                            word = v < 1.0f ? (word | bit) : (word & ~bit);
+                        } else {
+                            word &= ~bit;
+                            touched = true;
+                            const int slot = atomicAdd(&s_namb, 1);
+                            if (slot < MAXAMB) s_amb[slot] = (mz << 16) | (my << 8) | mx;
+                        }
+                    }
+                }
+                s_rows[r] = word;
+                if (word != 0 || touched) {
+                    ey0 = min(ey0, my); ey1 = max(ey1, my);
+                    ez0 = min(ez0, mz); ez1 = max(ez1, mz);
+                }
+                // row r of the old map, in the new cube's rows
+                if (!P.init && s_old[r] != 0) {
+                    const int oy = my - dsh1, oz = mz - dsh2;
+                    ey0 = min(ey0, oy); ey1 = max(ey1, oy);
+                    ez0 = min(ez0, oz); ez1 = max(ez1, oz);
+                }
+            }
+        }
+        ey0 = __reduce_min_sync(0xffffffffu, ey0);
+        ey1 = __reduce_max_sync(0xffffffffu, ey1);
+        ez0 = __reduce_min_sync(0xffffffffu, ez0);
+        ez1 = __reduce_max_sync(0xffffffffu, ez1);
+        if (lane == 0 && ey0 <= ey1) {
+            atomicMin(&s_ext[0], ey0); atomicMax(&s_ext[1], ey1);
+            atomicMin(&s_ext[2], ez0); atomicMax(&s_ext[3], ez1);
+        }
     }
     __syncthreads();
     const int namb = s_namb;
     if (namb > 0) {
         // exact FP64 test in the oracle's operation order, only for listed nodes
-        if (warp == 0) canon_shape_warp(S.inv_semi2, S.q, s_E, s_A, lane);
         if (tid == 0 && namb > MAXAMB) atomicOr(P.status, ST_CAPACITY);
-        __syncthreads();
         for (int a = tid; a < min(namb, MAXAMB); a += CBLOCK) {
             const int code = s_amb[a];
             const int mx = code & 0xff, my = (code >> 8) & 0xff, mz = (code >> 16) & 0xff;
@@ -616,7 +731,6 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
         int dsh[3];                                 // new origin - old origin: old-local = new-local + dsh
         for (int k = 0; k < 3; ++k) dsh[k] = P.init ? 0 : s_o[k] - S.o[k];
         if (tid == 0 && (abs(dsh[0]) > 1 || abs(dsh[1]) > 1 || abs(dsh[2]) > 1)) atomicOr(P.status, ST_CAPACITY);
-        const uint64_t maskS = Sd >= 64 ? ~0ull : ((1ull << Sd) - 1ull);
         auto row_old = [&](int ay, int az) -> uint64_t {
             ay += dsh[1]; az += dsh[2];
             if (ay < 0 || ay >= Sd || az < 0 || az >= Sd) return 0ull;
@@ -630,11 +744,14 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
             return s_rows[az * Sd + ay] | row_old(ay, az);
         };
         auto s3 = [](uint64_t w) { return w | (w << 1) | (w >> 1); };
+        // rows more than one row from every row solid now or before have no
+        // solid neighbour: nothing to redo there
+        const int ry0 = s_ext[0] - 1, ry1 = s_ext[1] + 1, rz0 = s_ext[2] - 1, rz1 = s_ext[3] + 1;
         for (int r = tid; r < Sd * Sd; r += CBLOCK) {
             const int my = r % Sd, mz = r / Sd;
             const int Yu = s_o[1] + my;
             uint64_t nd = 0;
-            if (py || (Yu > 0 && Yu < ny - 1)) {
+            if ((py || (Yu > 0 && Yu < ny - 1)) && my >= ry0 && my <= ry1 && mz >= rz0 && mz <= rz1) {
                 // the D3Q19 neighbourhood by rows: this row shifted by one node
                 // either way, the four face-adjacent rows shifted by -1, 0, +1,
                 // the four diagonal rows unshifted
@@ -649,21 +766,13 @@ __device__ __forceinline__ void crit_block(const PParams& P, int p, const double
         }
         if (tid == 0) {
             NeedHdr h;
-            for (int k = 0; k < 3; ++k) h.ow[k] = wrapi(s_o[k], k == 0 ? nx : (k == 1 ? ny : nz));
+            for (int k = 0; k < 3; ++k) h.ow[k] = K.ow_new[k];
             h.S = Sd;
             P.need_hdr[p] = h;
         }
     }
     if (tid == 0) {
         K.rows_new = rows_new;
-        K.oy_new = s_o[1];
-        for (int k = 0; k < 3; ++k) {
-            K.ow_new[k] = wrapi(s_o[k], k == 0 ? nx : (k == 1 ? ny : nz));
-            K.ro_new[k] = s_ro[k];
-            K.U[k] = (float)S.U[k];
-            K.W[k] = (float)S.W[k];
-            K.Fext[k] = S.Fext[k];
-        }
         K.S = Sd;
         K.nsolid = s_nsolid;
         if (P.init) {
@@ -1053,78 +1162,112 @@ static __device__ __noinline__ void aux_block(const PParams& P, int p)
         G.zeta[tid] = v;
     }
     __syncthreads();
-    // ---- inverse of the solve matrix A = [[M + zeta_FU, zeta_FOmega], [zeta_TU, I + dI/dt + zeta_TOmega]]
-    // by blocks, A = [[P, B], [C, D]] (each 3 x 3): with X = P^-1 B, Y = C P^-1
-    // and the Schur complement S = D - C X,
-    //   A^-1 = [[P^-1 + X S^-1 Y, -X S^-1], [-S^-1 Y, S^-1]];
-    // P (M I + the drag's translation block) and S are symmetric positive
-    // definite up to the small dI/dt, so their 3 x 3 inverses by cofactors need
-    // no pivoting.  Lane e < 9 of warp 0 holds entry (e / 3, e % 3) of each
-    // 3 x 3 block: five short dependent rounds and two divisions instead of the
-    // six pivot steps of an elimination on the 6 x 6 system (the FP64 rate of
-    // this part makes every dependent step count).
+    // ---- inverse of the solve matrix A = [[M + zeta_FU, zeta_FOmega], [zeta_TU, I + dI/dt + zeta_TOmega]]:
+    // an FP32 inverse X0 by 3 x 3 blocks, then two Newton-Schulz steps in FP64,
+    // X <- X + X (I - A X), each of which squares the relative error of X (about
+    // 1e-7 times the condition number after FP32), so that X carries FP64
+    // accuracy.  FP64 instructions issue at a small fraction of the FP32 rate on
+    // this GPU, one warp at a time per scheduler, so the FP64 part is only the
+    // two 6-term products per step, one entry of A^-1 per thread.
+    __shared__ double s_Af[36], s_X[36], s_Ei[36];
+    __shared__ float s_f[36];
+    __shared__ int s_bad;
+    if (tid < 36) {
+        const int i = tid / 6, j = tid % 6;
+        double a = s_Z[tid];
+        if (i < 3 && i == j) a += S.M;
+        if (i >= 3 && j >= 3) a += s_I[(i - 3) * 3 + (j - 3)] + s_dI[(i - 3) * 3 + (j - 3)];
+        s_Af[tid] = a;
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
     if (warp == 0) {
-        double* sP = s_P;                           // free again: P^-1 in [0, 9), X [9, 18), Y [18, 27), S^-1 [27, 36)
+        // FP32, by blocks: A = [[P, B], [C, D]] (each 3 x 3), X = P^-1 B,
+        // Y = C P^-1, the Schur complement S = D - C X,
+        //   A^-1 = [[P^-1 + X S^-1 Y, -X S^-1], [-S^-1 Y, S^-1]];
+        // P (M I + the drag's translation block) and S are symmetric positive
+        // definite up to the small dI/dt, so their inverses by cofactors need no
+        // pivoting.  Lane e < 9 holds entry (e / 3, e % 3) of each block.
+        float* sP = s_f;                            // P^-1 [0, 9), X [9, 18), Y [18, 27), S^-1 [27, 36)
         const int e = lane < 9 ? lane : 8, r = e / 3, c = e % 3;
         const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-        auto Pm = [&](int a, int b) { return s_Z[a * 6 + b] + (a == b ? S.M : 0.0); };
-        auto Dm = [&](int a, int b) { return s_Z[(a + 3) * 6 + b + 3] + s_I[a * 3 + b] + s_dI[a * 3 + b]; };
-        // P^-1: the cofactor of entry (c, r) over det P (the inverse's (r, c) entry)
-        const double cofP = Pm(c1, r1) * Pm(c2, r2) - Pm(c1, r2) * Pm(c2, r1);
-        double detP = 0.0;
+        auto Af = [&](int a, int b) { return (float)s_Af[a * 6 + b]; };
+        const float cofP = Af(c1, r1) * Af(c2, r2) - Af(c1, r2) * Af(c2, r1);
+        float detP = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) detP += Pm(0, k) * __shfl_sync(0xffffffffu, cofP, k * 3);
-        bool ok = detP != 0.0;
-        const double Pi = cofP / detP;
+        for (int k = 0; k < 3; ++k) detP += Af(0, k) * __shfl_sync(0xffffffffu, cofP, k * 3);
+        const float Pi = cofP / detP;
         if (lane < 9) sP[e] = Pi;
         __syncwarp();
-        // X = P^-1 B, Y = C P^-1
-        double x = 0.0, y = 0.0;
+        float x = 0.0f, y = 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            x += sP[r * 3 + k] * s_Z[k * 6 + 3 + c];
-            y += s_Z[(3 + r) * 6 + k] * sP[k * 3 + c];
+            x += sP[r * 3 + k] * Af(k, 3 + c);
+            y += Af(3 + r, k) * sP[k * 3 + c];
         }
         if (lane < 9) { sP[9 + e] = x; sP[18 + e] = y; }
         __syncwarp();
-        // S = D - C X, then S^-1 by cofactors
-        double sv = Dm(r, c);
+        float sv = Af(3 + r, 3 + c);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) sv -= s_Z[(3 + r) * 6 + k] * sP[9 + k * 3 + c];
+        for (int k = 0; k < 3; ++k) sv -= Af(3 + r, k) * sP[9 + k * 3 + c];
         if (lane < 9) sP[27 + e] = sv;
         __syncwarp();
-        const double* Sm = sP + 27;
-        const double cofS = Sm[c1 * 3 + r1] * Sm[c2 * 3 + r2] - Sm[c1 * 3 + r2] * Sm[c2 * 3 + r1];
-        double detS = 0.0;
+        const float* Sm = sP + 27;
+        const float cofS = Sm[c1 * 3 + r1] * Sm[c2 * 3 + r2] - Sm[c1 * 3 + r2] * Sm[c2 * 3 + r1];
+        float detS = 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) detS += Sm[k] * __shfl_sync(0xffffffffu, cofS, k * 3);
-        ok = ok && detS != 0.0;
-        const double Si = cofS / detS;
+        const float Si = cofS / detS;
         __syncwarp();
         if (lane < 9) sP[27 + e] = Si;
         __syncwarp();
-        // blocks of A^-1: S^-1 Y and X S^-1, then P^-1 + X (S^-1 Y)
-        double sy = 0.0, xs = 0.0;
+        float sy = 0.0f, xs = 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             sy += sP[27 + r * 3 + k] * sP[18 + k * 3 + c];
             xs += sP[9 + r * 3 + k] * sP[27 + k * 3 + c];
         }
         __syncwarp();
-        if (lane < 9) sP[18 + e] = sy;              // Y no longer needed: S^-1 Y in its place
+        if (lane < 9) sP[18 + e] = sy;
         __syncwarp();
-        double tl = Pi;
+        float tl = Pi;
 #pragma unroll
         for (int k = 0; k < 3; ++k) tl += sP[9 + r * 3 + k] * sP[18 + k * 3 + c];
         if (lane < 9) {
-            G.Ainv[r * 6 + c] = tl;
-            G.Ainv[r * 6 + 3 + c] = -xs;
-            G.Ainv[(3 + r) * 6 + c] = -sy;
-            G.Ainv[(3 + r) * 6 + 3 + c] = Si;
+            s_X[r * 6 + c] = tl;
+            s_X[r * 6 + 3 + c] = -xs;
+            s_X[(3 + r) * 6 + c] = -sy;
+            s_X[(3 + r) * 6 + 3 + c] = Si;
+            if (!(detP != 0.0f && detS != 0.0f && isfinite(tl) && isfinite(xs) && isfinite(sy) && isfinite(Si)))
+                s_bad = 1;
         }
-        if (lane == 0 && !ok) atomicOr(P.status, ST_NAN);
     } else if (warp == 1 && lane < 9) {
         G.Icur[lane] = s_I[lane];
+    }
+    __syncthreads();
+    const int ri = tid / 6, ci = tid % 6;
+#pragma unroll 1
+    for (int step = 0; step < 2; ++step) {
+        if (tid < 36) {                             // I - A X
+            double v = ri == ci ? 1.0 : 0.0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v = fma(-s_Af[ri * 6 + k], s_X[k * 6 + ci], v);
+            s_Ei[tid] = v;
+        }
+        __syncthreads();
+        double xn = 0.0;
+        if (tid < 36) {                             // X + X (I - A X)
+            xn = s_X[tid];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) xn = fma(s_X[ri * 6 + k], s_Ei[k * 6 + ci], xn);
+        }
+        __syncthreads();
+        if (tid < 36) s_X[tid] = xn;
+        __syncthreads();
+    }
+    if (tid < 36) {
+        G.Ainv[tid] = s_X[tid];
+        if ((tid == 0 && s_bad) || !isfinite(s_X[tid])) atomicOr(P.status, ST_NAN);
     }
 }
 

@@ -47,6 +47,29 @@ def test_solid_map_and_links_bit_exact(seed):
     assert gpu_links_as_set(gpu) == oracle_links_as_set(orc)
 
 
+@pytest.mark.parametrize("seed", range(16))
+def test_solid_map_bit_exact_for_thin_long_and_subnode_shapes(seed):
+    """The occupancy map over a wider range of shapes: semi-axes from 0.6 to
+    14 nodes with aspect ratios up to 12 (rows far from the body are skipped
+    and the root bands are one node wide only when every semi-axis is at least
+    one node; below that the wide bands), random poses anywhere in the box."""
+    g = rng(1300 + seed)
+    if seed % 4 == 3:
+        semi = [float(v) for v in g.uniform(0.6, 1.0, 3)]
+    else:
+        a = float(g.uniform(3.0, 14.0))
+        semi = [a, a / float(g.uniform(1.0, 12.0)), a / float(g.uniform(1.0, 12.0))]
+        semi = [max(s_, 1.0) for s_ in semi]
+    n = [int(v) for v in g.choice([40, 48], size=3)]          # the bounding cube (34 nodes at most) fits
+    c, q = random_pose(g, min(n), margin=-1)
+    b = box(*n, 1.0)
+    p = particle(semi, c, q)
+    gpu = _sim([b], [[p]])
+    orc = O.Sim(b, [p], nthreads=4)
+    assert np.array_equal(gpu.field("solid"), orc.owner())
+    assert gpu_links_as_set(gpu) == oracle_links_as_set(orc)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_links_bit_exact_for_a_quaternion_off_unit_norm(seed):
     """Both sides divide the input quaternion by its norm (Eq. vectrotn assumes
