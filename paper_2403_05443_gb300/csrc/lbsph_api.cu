@@ -288,7 +288,7 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     }
     ctx->d_need_hdr = (NeedHdr*)dev_alloc(ctx, sizeof(NeedHdr) * 2 * (size_t)ctx->maxp);
     ctx->d_need = (uint64_t*)dev_alloc(ctx, sizeof(uint64_t) * 2 * (size_t)MAXS * MAXS * ctx->maxp);
-    ctx->d_sync = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * (4 + (size_t)ctx->maxp + 2 * 4096));
+    ctx->d_sync = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * (SYNC_HDR + (size_t)ctx->maxp + 2 * 4096));
     ctx->d_ring = (double*)dev_alloc(ctx, sizeof(double) * 2 * RINGD * (size_t)ctx->maxp);
     for (void* p : {ctx->fbuf[0], ctx->fbuf[1], (void*)ctx->d_boxes, (void*)ctx->d_pd, (void*)ctx->d_pk,
                     (void*)ctx->d_acc, (void*)ctx->d_rows, (void*)ctx->d_status, (void*)ctx->d_count,
@@ -323,7 +323,7 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     err = err ? err : cudaMemsetAsync(ctx->d_need_hdr, 0, sizeof(NeedHdr) * 2 * (size_t)ctx->maxp, ctx->stream);
     err = err ? err : cudaMemsetAsync(ctx->d_need, 0, sizeof(uint64_t) * 2 * (size_t)MAXS * MAXS * ctx->maxp, ctx->stream);
     // the step kernel's counters start at zero and every launch leaves them so
-    err = err ? err : cudaMemsetAsync(ctx->d_sync, 0, sizeof(unsigned) * (4 + (size_t)ctx->maxp + 2 * 4096), ctx->stream);
+    err = err ? err : cudaMemsetAsync(ctx->d_sync, 0, sizeof(unsigned) * (SYNC_HDR + (size_t)ctx->maxp + 2 * 4096), ctx->stream);
     err = err ? err : cudaStreamSynchronize(ctx->stream);
     if (err != cudaSuccess) {
         free_all(ctx);

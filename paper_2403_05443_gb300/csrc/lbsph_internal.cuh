@@ -54,6 +54,7 @@ constexpr int MAXC = 4;             // particles a lattice tile may touch (field
 constexpr int BBLOCK = 256;         // threads per block of the boundary kernel
 constexpr int CBLOCK = 256;         // threads per block of the critical particle kernel
 constexpr int MAXAMB = 512;         // near-surface nodes settled by the exact FP64 test per step
+constexpr int SYNC_HDR = 8;          // step kernel: barrier and work-counter words before the per-particle item counters
 constexpr int MAXNB = 8;            // partners of a particle: others whose bounding cubes come within reach
 constexpr int MAXPB = 64;           // particles of one box when any of them has partners (cluster masks)
 constexpr int RINGD = 10;           // doubles per particle and step parity in the pose ring: x, U, q

@@ -20,64 +20,81 @@
 // A grid barrier ends the iteration: after it the lattice of step t, the box
 // terms and the redo masks of step t+1 are complete.  The auxiliary block of
 // the last iteration runs first in the next launch: a launch ends at its last
-// barrier, and the barrier, work and item counters are zero again then, so
-// launches follow each other with no reset in between.
+// barrier, with the arrival and item counters at zero, so launches follow each
+// other with no reset in between.  The iterations take their bulk units from
+// two counters in turn (by barrier generation), each cleared by block 0 while
+// the other one is in use.
 //
 // Cross-block data are read through L2 (ld.global.cg, see lattice_common.cuh).
 // Every wait is bounded: a barrier that waits longer than SPIN_LIMIT polls
-// sets ST_TIMEOUT in the status word, and every block leaves the kernel at the
-// next barrier it reaches.
+// sets ST_TIMEOUT in the status word and the abort flag, and every block
+// leaves the kernel at the barrier it waits at or at the next one it reaches.
 #include "boundary_block.cuh"
 #include "bulk_tile.cuh"
 #include "particle_blocks.cuh"
 
 namespace lbsph {
 
-constexpr int SYNC_BAR = 0;          // barrier arrivals
-constexpr int SYNC_GEN = 1;          // barrier generation
-constexpr int SYNC_WORK = 2;         // work counter of the current iteration
-constexpr int SYNC_PART = 4;         // + p: items of particle p done in this iteration
+constexpr int SYNC_BAR = 0;          // barrier arrivals (zero between barriers)
+constexpr int SYNC_GEN = 2;          // barrier generation (counts up, wraps), 8-byte aligned with
+constexpr int SYNC_ABORT = 3;        //   the abort flag: nonzero once a wait ran out
+constexpr int SYNC_WORK = 4;         // + (generation & 1): bulk units taken in the iteration of that generation
+constexpr int SYNC_PART = SYNC_HDR;  // + p: items of particle p done in this iteration
 constexpr int MAX_GRID = 4096;
-constexpr long long SPIN_LIMIT = 1ll << 24;   // polls of about 100 ns: under 2 s
+constexpr long long SPIN_LIMIT = 1ll << 22;   // polls (an L2 read, then a 64 ns sleep): a few seconds
 
 struct StepParams {
     BulkParams bulk[2];              // by buffer parity of the iteration
     BndParams bnd[2];
     PParams part[2];
-    unsigned* sync;                  // SYNC_PART + np words, zero at launch (and again at exit), then the blocks' SM ids
+    unsigned* sync;                  // SYNC_PART + np words (the arrival and item counters zero at launch and
+                                     // again at exit), then the blocks' SM ids
     unsigned* status;
     int np, gx, tiles, iters, cur0;
-    int fetch;                       // bulk units per counter fetch (1, 2, 4, 8)
+    int fetch;                       // bulk units per counter fetch (1, 2, 4, 8), single units at the end
     const double* io_ft;             // per iteration np * 6 doubles of F_ext, T_ext (or null)
     double* io_rec;                  // per iteration np * RECD doubles of records (or null)
 };
 
-__device__ __forceinline__ bool grid_barrier(const StepParams& SP)
+// Grid barrier.  Each block counts the generations itself (s_gen, read once
+// at kernel entry), so a barrier costs one arrival atomic and the polls of the
+// generation word: the last block to arrive clears the arrival counter and
+// publishes the next generation; the others poll the generation together with
+// the abort flag (one 8-byte load), which a block whose wait ran out sets
+// after setting ST_TIMEOUT, so that every other block leaves at the barrier it
+// waits at or at its next one.
+__device__ __forceinline__ bool grid_barrier(const StepParams& SP, unsigned& s_gen)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = SP.sync + SYNC_GEN;
-        const unsigned g = *gen;
+        const unsigned g = s_gen;
+        bool ok = true;
         __threadfence();
         if (atomicAdd(SP.sync + SYNC_BAR, 1u) == gridDim.x - 1) {
-            // last to arrive: reset the counters of the next iteration, then release
+            // last to arrive: clear the arrivals, then release the next generation
             SP.sync[SYNC_BAR] = 0;
-            SP.sync[SYNC_WORK] = 0;
             __threadfence();
-            atomicExch(SP.sync + SYNC_GEN, g + 1);
+            *reinterpret_cast<volatile unsigned*>(SP.sync + SYNC_GEN) = g + 1;
         } else {
+            const volatile unsigned long long* ga = reinterpret_cast<const volatile unsigned long long*>(SP.sync + SYNC_GEN);
             long long n = 0;
-            while (*gen == g) {
+            for (;;) {
+                const unsigned long long v = *ga;
+                if ((unsigned)(v >> 32) != 0u) { ok = false; break; }
+                if ((unsigned)v != g) break;
                 if (++n > SPIN_LIMIT) {
                     atomicOr(SP.status, ST_TIMEOUT);
+                    atomicExch(SP.sync + SYNC_ABORT, 1u);
+                    ok = false;
                     break;
                 }
-                __nanosleep(100);
+                if (n > 64) __nanosleep(64);
             }
+            __threadfence();
         }
-        __threadfence();
-        s_ok = (*reinterpret_cast<volatile unsigned*>(SP.status) & ST_TIMEOUT) == 0;
+        s_gen = g + 1;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -121,6 +138,7 @@ template <class St>
 __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__ StepParams SP)
 {
     __shared__ int s_last, s_rank, s_root;
+    __shared__ unsigned s_gen;
     __shared__ unsigned long long s_members;
     const int tid = threadIdx.x;
     const int gx = SP.gx;
@@ -135,8 +153,14 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
         blk_sm[blockIdx.x] = smid;
         s_rank = 0;
+        // the generation before this launch's first barrier (no block can pass
+        // that barrier before every block has read it)
+        s_gen = *reinterpret_cast<volatile unsigned*>(SP.sync + SYNC_GEN);
+        // the work counter of the first iteration was the last launch's last
+        // one: clear it (the launches on a stream do not overlap)
+        if (blockIdx.x == 0) SP.sync[SYNC_WORK + ((s_gen + 1) & 1)] = 0;
     }
-    if (!grid_barrier(SP)) return;
+    if (!grid_barrier(SP, s_gen)) return;
     {
         const unsigned mine = __ldcg(blk_sm + blockIdx.x);
         int before = 0;
@@ -148,11 +172,16 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
     }
     __syncthreads();
     const int prank = s_rank;
+    const int nwarps = (int)gridDim.x * (KBLOCK / 32);
     for (int it = 0; it < SP.iters; ++it) {
         const int cur = (SP.cur0 + it) & 1;
         const BulkParams& BP = SP.bulk[cur];
         const BndParams& NP = SP.bnd[cur];
         const PParams& PP = SP.part[cur];
+        const unsigned gen = s_gen;
+        unsigned* work = SP.sync + SYNC_WORK + (gen & 1);
+        // the other work counter (the last iteration's) for the next iteration
+        if (blockIdx.x == 0 && tid == 0) SP.sync[SYNC_WORK + ((gen + 1) & 1)] = 0;
         // ---- particle items
         for (int item = prank; item < npart; item += gridDim.x) {
             const int p = item / (gx + 1), c = item % (gx + 1);
@@ -191,26 +220,30 @@ __global__ void __launch_bounds__(KBLOCK, 2) step_kernel(const __grid_constant__
             }
             __syncthreads();
         }
-        // ---- bulk work in warp-sized units (32 quads of a tile), SP.fetch
-        // consecutive units per fetch from the counter: no block barrier, each
-        // warp moves on as soon as its stores are issued; the next fetch is
-        // issued before the current units run
+        // ---- bulk work in warp-sized units (32 quads of a tile): SP.fetch
+        // consecutive units per fetch from the counter while more than two
+        // rounds of such fetches remain, then single units, so that the last
+        // units to finish are short; no block barrier, each warp moves on as
+        // soon as its stores are issued; the next fetch is issued before the
+        // current units run
         {
             const int lane = tid & 31;
             const int units = SP.tiles * (KBLOCK / 32);
             const int fetch = SP.fetch;
-            int u = 0;
-            if (lane == 0) u = (int)atomicAdd(SP.sync + SYNC_WORK, 1u) * fetch;
+            const int coarse_end = units - 2 * nwarps * fetch;
+            int u = 0, nf = fetch;
+            if (lane == 0) u = (int)atomicAdd(work, (unsigned)fetch);
             u = __shfl_sync(0xffffffffu, u, 0);
             while (u < units) {
+                const int end = min(u + nf, units);
+                nf = u + nf < coarse_end ? fetch : 1;
                 int nu = 0;
-                if (lane == 0) nu = (int)atomicAdd(SP.sync + SYNC_WORK, 1u) * fetch;
-                const int end = min(u + fetch, units);
+                if (lane == 0) nu = (int)atomicAdd(work, (unsigned)nf);
                 for (int v = u; v < end; ++v) bulk_tile<St, false>(BP, v >> 3, ((v & 7) << 5) + lane);
                 u = __shfl_sync(0xffffffffu, nu, 0);
             }
         }
-        if (!grid_barrier(SP)) return;
+        if (!grid_barrier(SP, s_gen)) return;
     }
     // the auxiliary blocks of the last iteration run as the first items of the
     // next launch (or before the next separate-kernel iteration or getter)
