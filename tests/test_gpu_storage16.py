@@ -18,8 +18,9 @@ magnitude.
 
 The field is random per node (no smoothness hides a neighbour mix-up); the
 batch holds a periodic box whose rows do not line up with warps (nx = 40: five
-8-node groups per row), with a moving particle and a squirmer, and a channel
-with moving walls (the wall links are handled in the bulk tile)."""
+8-node groups per row), with a moving particle and a squirmer, and two channels
+with moving walls (the wall links are handled in the bulk tile), one of them
+with rows that do line up with warps (nx = 32: the x wrap by shuffle)."""
 import math
 
 import numpy as np
@@ -37,12 +38,14 @@ L = pytest.importorskip("paper_2403_05443_gb300.lbsph")
 def _case():
     g = rng(41)
     boxes = [box(40, 24, 32, 0.9, counter_force=1),
-             box(24, 20, 16, 1.0, walls=1, wall_u_lo=(0.01, 0.0, 0.0), wall_u_hi=(-0.01, 0.0, 0.002))]
+             box(24, 20, 16, 1.0, walls=1, wall_u_lo=(0.01, 0.0, 0.0), wall_u_hi=(-0.01, 0.0, 0.002)),
+             box(32, 20, 24, 1.2, walls=1, wall_u_lo=(0.0, 0.0, 0.004), wall_u_hi=(0.008, 0.0, 0.0))]
     parts = [[particle((4.5, 2.5, 2.0), (10.3, 11.1, 9.7), random_quaternion(g), U=(0.01, -0.004, 0.002),
                        Om=(0.0, 0.001, -0.002), F_ext=(2e-4, -1e-4, 5e-5)),
               particle((3.0, 2.0, 2.0), (29.2, 12.6, 23.9), random_quaternion(g), U=(-0.005, 0.0, 0.006),
                        B1=1e-3, B2=2e-3)],
-             [particle((3.0, 2.0, 2.0), (12.4, 9.8, 8.3), random_quaternion(g), U=(0.0, 0.003, -0.004))]]
+             [particle((3.0, 2.0, 2.0), (12.4, 9.8, 8.3), random_quaternion(g), U=(0.0, 0.003, -0.004))],
+             [particle((3.5, 2.5, 2.0), (20.6, 10.3, 11.2), random_quaternion(g), U=(0.004, 0.002, 0.0))]]
     return boxes, parts
 
 

@@ -61,13 +61,16 @@ def test_stokes_field_matches_reference():
     assert err <= 1e-4 and derr <= 1e-4
 
 
-@pytest.mark.parametrize("shape", [(32, 16, 64), (64, 24, 32)])
-def test_stokes_field_with_power_of_two_edges_matches_reference(shape):
+@pytest.mark.parametrize("shape,tau", [((32, 16, 64), 0.8), ((64, 24, 32), 0.8), ((32, 16, 64), 0.52),
+                                       ((64, 24, 32), 1.45)])
+def test_stokes_field_with_power_of_two_edges_matches_reference(shape, tau):
     """Power-of-two edges take the radix-2 FFT pass (one edge of the second box
-    does not, and keeps the transform by definition)."""
+    does not, and keeps the transform by definition).  At tau = 0.52 the
+    per-mode denominator 1 - (1 - omega) cos(theta) falls to about 0.04 near
+    theta = pi, where its FP32 terms lose most digits: the bar still holds."""
     nx, ny, nz = shape
     g = rng(37)
-    b = box(nx, ny, nz, 0.8, counter_force=1)
+    b = box(nx, ny, nz, tau, counter_force=1)
     parts = [particle((4.5, 2.5, 2.0), (nx * 0.3, ny * 0.45, nz * 0.4), random_quaternion(g), F_ext=(2e-4, -1e-4, 5e-5)),
              particle((3.0, 2.0, 2.0), (nx * 0.75, ny * 0.55, nz * 0.8), random_quaternion(g), F_ext=(-5e-5, 1e-4, 1e-4))]
     sim = _sim(b, parts)
@@ -78,7 +81,7 @@ def test_stokes_field_with_power_of_two_edges_matches_reference(shape):
     ref, dref = W.stokes_field(nx, ny, nz, sim.field("solid"), [p["F_ext"] for p in parts], mu, counter=True,
                                density=True, tau=b["tau"], rho0=b["rho0"])
     err, derr = normwise(u, ref), normwise(d, dref)
-    print("stokes error", shape, err, derr)
+    print("stokes error", shape, tau, err, derr)
     assert err <= 1e-4 and derr <= 1e-4
 
 
