@@ -1,5 +1,5 @@
 /*
- * FP64 CPU oracle: lattice Boltzmann D3Q19 fluid coupled to rigid spheroids
+ * FP64 CPU oracle: lattice Boltzmann D3Q19 (or D3Q27) fluid coupled to rigid spheroids
  * by link bounce-back and an implicit velocity / quaternion update.
  *
  * TEST INFRASTRUCTURE ONLY (tests/, __graft_entry__.smoke(), bench.py's
@@ -11,6 +11,10 @@
  *
  * Readings of points the paper leaves open:
  *   - lattice: D3Q19 textbook set, weights 1/3, 1/18, 1/36, c_s^2 = 1/3 (Sec. II.A);
+ *     compiled with -DORC_D3Q27 (liboracle27.so): the D3Q27 set the paper compares it
+ *     with (Sec. III.A), all c in {-1,0,1}^3, weights 8/27, 2/27, 1/54, 1/216 for
+ *     |c|^2 = 0, 1, 2, 3, the same c_s^2 = 1/3; every step below is written for
+ *     either set;
  *   - collision: BGK with the quadratic equilibrium of Eq. 4 (Sec. II.A);
  *   - body force: Guo forcing, u = (sum f c + g/2)/rho, applied on fluid nodes;
  *     with counter_force the fluid gets g = -sum(F_ext)/N_fluid;
@@ -45,10 +49,17 @@
 #include <omp.h>
 #endif
 
+#ifdef ORC_D3Q27
+#define Q 27
+#define QMAXC2 3
+#else
 #define Q 19
+#define QMAXC2 2
+#endif
 
 /* ------------------------------------------------------------------------- */
-/* Lattice: D3Q19 enumerated as all c in {-1,0,1}^3 with |c|^2 <= 2, z slowest. */
+/* Lattice: D3Q19 enumerated as all c in {-1,0,1}^3 with |c|^2 <= 2, z slowest
+ * (D3Q27: every c in {-1,0,1}^3, same order). */
 static int C[Q][3];
 static double Wt[Q];
 static int OPP[Q];
@@ -62,9 +73,13 @@ static void lattice_init(void)
         for (int cy = -1; cy <= 1; ++cy)
             for (int cx = -1; cx <= 1; ++cx) {
                 int m = cx * cx + cy * cy + cz * cz;
-                if (m > 2) continue;
+                if (m > QMAXC2) continue;
                 C[n][0] = cx; C[n][1] = cy; C[n][2] = cz;
+#ifdef ORC_D3Q27
+                Wt[n] = (m == 0) ? 8.0 / 27.0 : (m == 1) ? 2.0 / 27.0 : (m == 2) ? 1.0 / 54.0 : 1.0 / 216.0;
+#else
                 Wt[n] = (m == 0) ? 1.0 / 3.0 : (m == 1) ? 1.0 / 18.0 : 1.0 / 36.0;
+#endif
                 ++n;
             }
     for (int i = 0; i < Q; ++i)
@@ -73,7 +88,9 @@ static void lattice_init(void)
     lattice_ready = 1;
 }
 
-void orc_lattice(int c[19][3], double w[19])
+int orc_q(void) { return Q; }
+
+void orc_lattice(int c[][3], double w[])
 {
     lattice_init();
     memcpy(c, C, sizeof(C));
@@ -104,7 +121,7 @@ struct orc_sim {
     double uw_lo[3], uw_hi[3];
     double *f, *fpost, *fnext;
     int *owner, *owner_new;
-    int* nb;                     /* nb[n*19 + i] = index of node x + c_i (periodic addressing) */
+    int* nb;                     /* nb[n*Q + i] = index of node x + c_i (periodic addressing) */
     unsigned* linkmask;          /* per node: bit b set if x + c_b is a particle node */
     int np;
     part_t* P;
@@ -336,7 +353,7 @@ static double feq_i(int i, double rho, const double u[3])
     return rho * Wt[i] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
 }
 
-void orc_feq(double rho, const double u[3], double out[19])
+void orc_feq(double rho, const double u[3], double out[])
 {
     lattice_init();
     for (int i = 0; i < Q; ++i) out[i] = feq_i(i, rho, u);

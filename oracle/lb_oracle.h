@@ -52,10 +52,12 @@ void     orc_destroy(orc_sim* s);
 int      orc_step(orc_sim* s, int nsteps);          /* 0 ok, nonzero error code */
 long     orc_time(const orc_sim* s);
 
-/* lattice (oracle order) */
-void orc_lattice(int c[19][3], double w[19]);
+/* lattice (oracle order): Q = 19 velocities, or 27 in the library built with
+ * -DORC_D3Q27 (liboracle27.so); c has Q rows of 3, w Q entries */
+int  orc_q(void);
+void orc_lattice(int c[][3], double w[]);
 
-/* fields.  f is node-major: f[node*19 + i], node = (z*ny + y)*nx + x,
+/* fields.  f is node-major: f[node*Q + i], node = (z*ny + y)*nx + x,
  * oracle direction order.  Values are pre-collision f(x, t) at the start of
  * the current iteration; solid nodes read 0. */
 void orc_get_f(const orc_sim* s, double* out);
@@ -76,7 +78,7 @@ int  orc_get_links(const orc_sim* s, int p, int* node, int* cvec /* 3 per link *
 double orc_mass(const orc_sim* s, int p);
 
 /* single pieces, for the pins */
-void orc_feq(double rho, const double u[3], double out[19]);
+void orc_feq(double rho, const double u[3], double out[] /* Q */);
 void orc_quat_mul(const double a[4], const double b[4], double out[4]);
 void orc_rotate(const double q[4], const double s[3], double out[3]);
 void orc_inertia_lab(const double q[4], const double Ibody[3], double out[9]);

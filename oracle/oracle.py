@@ -18,20 +18,30 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lb_oracle.c")
-_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_HDR = os.path.join(_HERE, "lb_oracle.h")
+_LIBS = {19: os.path.join(_HERE, "_build", "liboracle.so"), 27: os.path.join(_HERE, "_build", "liboracle27.so")}
+_LIB = _LIBS[19]
+
+
+def _build_one(q: int, force: bool) -> str:
+    out = _LIBS[q]
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-ffp-contract=off",
+           "-fPIC", "-shared", *(["-DORC_D3Q27"] if q == 27 else []), "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP, no FMA contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-ffp-contract=off",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    """Compile the oracle with gcc (OpenMP, no FMA contraction): the D3Q19
+    library and, from the same source, the D3Q27 one."""
+    _build_one(27, force)
+    return _build_one(19, force)
 
 
 class OrcBox(C.Structure):
@@ -50,16 +60,20 @@ class OrcParticle(C.Structure):
                 ("B1", C.c_double), ("B2", C.c_double)]
 
 
-_lib = None
+_libs = {}
 _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
+def lib(q: int = 19):
+    """The oracle library of the D3Q19 (q = 19) or D3Q27 (q = 27) lattice."""
+    if q not in _LIBS:
+        raise ValueError(f"no oracle for D3Q{q}")
+    if q not in _libs:
+        build()
+        _libs[q] = C.CDLL(_LIBS[q])
+        L = _libs[q]
+        L.orc_q.restype = C.c_int
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParticle), C.c_int, C.c_int]
         L.orc_destroy.argtypes = [C.c_void_p]
@@ -96,7 +110,8 @@ def lib():
         L.orc_rigid_solve.restype = C.c_int
         L.orc_lubrication_pair.argtypes = [_D, _D, _D, _D, C.c_double, _D, _D, _D, _D, C.c_double, _I, _I,
                                            C.c_double, C.c_double, _D, _D]
-    return _lib
+        assert L.orc_q() == q
+    return _libs[q]
 
 
 def _dp(a):
@@ -115,17 +130,17 @@ def _f64(a, n=None):
 
 
 # ----------------------------------------------------------------------------
-def lattice():
-    """D3Q19 velocities c[19,3] and weights w[19] in the oracle's own order."""
-    c = np.zeros((19, 3), dtype=np.int32)
-    w = np.zeros(19)
-    lib().orc_lattice(_ip(c), _dp(w))
+def lattice(q: int = 19):
+    """D3Q19 (or D3Q27) velocities c[q,3] and weights w[q] in the oracle's own order."""
+    c = np.zeros((q, 3), dtype=np.int32)
+    w = np.zeros(q)
+    lib(q).orc_lattice(_ip(c), _dp(w))
     return c, w
 
 
-def feq(rho, u):
-    out = np.zeros(19)
-    lib().orc_feq(float(rho), _dp(_f64(u, 3)), _dp(out))
+def feq(rho, u, q: int = 19):
+    out = np.zeros(q)
+    lib(q).orc_feq(float(rho), _dp(_f64(u, 3)), _dp(out))
     return out
 
 
@@ -216,12 +231,14 @@ class Sim:
     """One box of fluid with its particles, stepped by the oracle.
 
     box: dict with nx, ny, nz, tau, rho0, body_force, counter_force, walls,
-    wall_u_lo, wall_u_hi, didt_mode.  particles: list of dicts with semi, x, q,
-    U, Om, density, F_ext, T_ext, B1, B2.
+    wall_u_lo, wall_u_hi, didt_mode, and lattice (19, the default, or 27).
+    particles: list of dicts with semi, x, q, U, Om, density, F_ext, T_ext, B1,
+    B2.
     """
 
     def __init__(self, box: dict, particles=(), nthreads: int | None = None):
-        L = lib()
+        self.Q = int(box.get("lattice", 19) or 19)
+        L = self._L = lib(self.Q)
         b = OrcBox()
         b.nx, b.ny, b.nz = int(box["nx"]), int(box["ny"]), int(box["nz"])
         b.tau = float(box["tau"])
@@ -258,7 +275,7 @@ class Sim:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -268,45 +285,45 @@ class Sim:
             pass
 
     def step(self, n: int = 1):
-        rc = lib().orc_step(self._h, int(n))
+        rc = self._L.orc_step(self._h, int(n))
         if rc:
             raise RuntimeError(f"oracle step failed with code {rc}")
 
     @property
     def time(self) -> int:
-        return lib().orc_time(self._h)
+        return self._L.orc_time(self._h)
 
     def f(self):
-        """Pre-collision f, shape (nz, ny, nx, 19), oracle direction order."""
-        out = np.zeros(self.N * 19)
-        lib().orc_get_f(self._h, _dp(out))
-        return out.reshape(self.nz, self.ny, self.nx, 19)
+        """Pre-collision f, shape (nz, ny, nx, Q), oracle direction order."""
+        out = np.zeros(self.N * self.Q)
+        self._L.orc_get_f(self._h, _dp(out))
+        return out.reshape(self.nz, self.ny, self.nx, self.Q)
 
     def set_f(self, f):
-        lib().orc_set_f(self._h, _dp(_f64(f, self.N * 19)))
+        self._L.orc_set_f(self._h, _dp(_f64(f, self.N * self.Q)))
 
     def moments(self):
         rho = np.zeros(self.N)
         u = np.zeros(self.N * 3)
-        lib().orc_get_moments(self._h, _dp(rho), _dp(u))
+        self._L.orc_get_moments(self._h, _dp(rho), _dp(u))
         return rho.reshape(self.nz, self.ny, self.nx), u.reshape(self.nz, self.ny, self.nx, 3)
 
     def owner(self):
         o = np.zeros(self.N, dtype=np.int32)
-        lib().orc_get_owner(self._h, _ip(o))
+        self._L.orc_get_owner(self._h, _ip(o))
         return o.reshape(self.nz, self.ny, self.nx)
 
     def fluid_mass(self) -> float:
-        return lib().orc_total_fluid_mass(self._h)
+        return self._L.orc_total_fluid_mass(self._h)
 
     def fluid_momentum(self):
         out = np.zeros(3)
-        lib().orc_total_fluid_momentum(self._h, _dp(out))
+        self._L.orc_total_fluid_momentum(self._h, _dp(out))
         return out
 
     def particle(self, p: int = 0) -> dict:
         out = np.zeros(25)
-        lib().orc_get_particle(self._h, p, _dp(out))
+        self._L.orc_get_particle(self._h, p, _dp(out))
         return {"F0": out[0:3], "T0": out[3:6], "F": out[6:9], "T": out[9:12],
                 "U": out[12:15], "Om": out[15:18], "x": out[18:21], "q": out[21:25],
                 "raw": out}
@@ -314,23 +331,23 @@ class Sim:
     def pending(self, p: int = 0):
         """(dP, dL, dm, dm_return) of the remap terms still to be applied."""
         out = np.zeros(8)
-        lib().orc_get_pending(self._h, p, _dp(out))
+        self._L.orc_get_pending(self._h, p, _dp(out))
         return out[0:3], out[3:6], out[6], out[7]
 
     def zeta(self, p: int = 0):
         out = np.zeros(36)
-        lib().orc_get_zeta(self._h, p, _dp(out))
+        self._L.orc_get_zeta(self._h, p, _dp(out))
         return out.reshape(6, 6)
 
     def mass(self, p: int = 0) -> float:
-        return lib().orc_mass(self._h, p)
+        return self._L.orc_mass(self._h, p)
 
     def links(self, p: int = 0):
         """Boundary links (node index, c_b) of particle p."""
-        n = lib().orc_get_links(self._h, p, None, None, 0)
+        n = self._L.orc_get_links(self._h, p, None, None, 0)
         node = np.zeros(max(n, 1), dtype=np.int32)
         cv = np.zeros(max(n, 1) * 3, dtype=np.int32)
-        lib().orc_get_links(self._h, p, _ip(node), _ip(cv), n)
+        self._L.orc_get_links(self._h, p, _ip(node), _ip(cv), n)
         return node[:n], cv[: 3 * n].reshape(n, 3)
 
 
