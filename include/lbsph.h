@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define LBSPH_ABI_VERSION 4
+#define LBSPH_ABI_VERSION 5
 
 typedef struct lb_ctx lb_ctx;
 
@@ -62,7 +62,7 @@ enum { LB_FP32 = 0, LB_FP16 = 1, LB_BF16 = 2 };
 
 /* field selectors for lb_get_fields */
 enum {
-    LB_FIELD_F = 1u,      /* f_i, float32, [19][nz][ny][nx]; 0 on solid nodes     */
+    LB_FIELD_F = 1u,      /* f_i, float32, [Q][nz][ny][nx] (Q = 19 or 27); 0 on solid nodes */
     LB_FIELD_DF = 2u,     /* f_i - w_i rho0, float32, same layout                  */
     LB_FIELD_RHO = 4u,    /* rho - rho0, float32, [nz][ny][nx]; 0 on solid nodes  */
     LB_FIELD_U = 8u,      /* u = (sum f c + g/2)/rho, float32, [3][nz][ny][nx]     */
@@ -124,6 +124,15 @@ typedef struct {
      * c_s^2 I) : Pi_neq / (2 c_s^4)] + the Guo source; the same as BGK at
      * tau = 1.  1 needs LB_FP32 storage. */
     int32_t collision;
+    /* Lattice: 0 or 19 D3Q19; 27 D3Q27, the lattice the paper compares D3Q19
+     * with (Sec. III.A: all 27 velocities of {-1,0,1}^3, weights 8/27, 2/27,
+     * 1/54, 1/216, c_s^2 = 1/3).  27 takes LB_FP32 storage, collision 0,
+     * periodic boxes (walls 0) and at most one passive particle per box (B1 =
+     * B2 = 0); its distributions and fields have 27 planes in the order of
+     * lb_lattice_q(27, ...).  With 27, lb_step_io, lb_get_force_torque_async,
+     * lb_profile_step, lb_autotune, lb_init_fluid and lb_stokes_field return
+     * LB_ESTATE. */
+    int32_t lattice;
 } lb_options;
 
 typedef struct {
@@ -229,7 +238,7 @@ lb_status lb_step_io(lb_ctx* ctx, int32_t nsteps, const double* ft, double* rec,
 /* Boundary links (x fluid, x + c_b solid) of particle `particle` of box `box`
  * at the current time, compacted on the device: pairs[2k] = node index
  * (z*ny + y)*nx + x of the fluid node, pairs[2k+1] = direction index b in the
- * library's D3Q19 order (lb_lattice).  *count = number of links (all of them
+ * library's order of the context's lattice (lb_lattice_q).  *count = number of links (all of them
  * are written only if count <= cap).  Waits for completion. */
 lb_status lb_get_links(lb_ctx* ctx, int32_t box, int32_t particle, int32_t* pairs, int32_t cap,
                        int32_t* count);
@@ -342,6 +351,14 @@ lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, float* drho_de
 
 /* The library's D3Q19 table: c[19][3] and w[19] (1/3, 1/18, 1/36). */
 void lb_lattice(int32_t* c57, double* w19);
+
+/* The library's table of lattice q (19 or 27): c[q][3] and w[q], either may
+ * be NULL.  The D3Q27 order is the D3Q19 one followed by the eight corners in
+ * +/- pairs (+++, ---, ++-, --+, +-+, -+-, -++, +--); for every direction b > 0
+ * the opposite one is b + 1 (b odd) or b - 1 (b even).  Weights for |c|^2 = 0,
+ * 1, 2, 3: 8/27, 2/27, 1/54, 1/216 (Sec. III.A names the lattice; these are
+ * its standard weights, c_s^2 = 1/3).  Errors: LB_EINVAL for another q. */
+lb_status lb_lattice_q(int32_t q, int32_t* c, double* w);
 
 const char* lb_status_string(lb_status s);
 const char* lb_last_error(const lb_ctx* ctx);

@@ -9,5 +9,5 @@ from .lbsph import (LB_BF16, LB_FIELD_DF, LB_FIELD_F, LB_FIELD_RHO, LB_FIELD_SOL
                     LB_FP16, LB_FP32, LBError, Simulation, lb_abi_version, lb_create, lb_destroy,
                     lb_get_drag, lb_get_fields, lb_get_force_torque, lb_get_force_torque_async, lb_get_links,
                     lb_last_error,
-                    lb_lattice, lb_profile_step, lb_set_external, lb_set_particles, lb_status_string, lb_step, lb_step_io,
+                    lb_lattice, lb_lattice_q, lb_profile_step, lb_set_external, lb_set_particles, lb_status_string, lb_step, lb_step_io,
                     lb_synchronize, library)

@@ -13,6 +13,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbsph.so")
 UNITS = ["bulk_kernel.cu", "boundary_kernel.cu", "lattice_kernel.cu", "particle_kernel.cu", "step_kernel.cu", "lbsph_api.cu",
+         "q27.cu",
          "mlp_kernel.cu", "warm_kernel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without contraction of a*b+c (aarch64 gcc contracts by default): the

@@ -20,6 +20,7 @@
 
 #include "../../include/lbsph.h"
 #include "lbsph_internal.cuh"
+#include "q27.cuh"
 
 namespace lbsph {
 cudaError_t launch_fields(const KParams& p, int precision, int blocks, cudaStream_t s);
@@ -94,6 +95,16 @@ struct lb_ctx {
                                        // last iteration have not run yet (the next launch runs them)
     std::string err;
     std::vector<void*> allocs;
+    // D3Q27 (lb_options.lattice = 27): q27.cuh
+    int lattice = 19;
+    std::vector<q27::Box27> h27;
+    std::vector<q27::Part27> hpart27;  // host copies of the particles as set
+    std::vector<int> box27_part;       // particle slot of every box, or -1
+    q27::Box27* d_box27 = nullptr;
+    q27::Dyn27* d_dyn27 = nullptr;
+    q27::Part27* d_part27 = nullptr;
+    int* d_blk27 = nullptr;
+    int blocks27 = 0;
 };
 
 static lb_status fail(lb_ctx* c, lb_status s, const std::string& msg)
@@ -183,6 +194,204 @@ extern "C" void lb_lattice(int32_t* c57, double* w19)
     }
 }
 
+extern "C" lb_status lb_lattice_q(int32_t q, int32_t* c, double* w)
+{
+    if (q != 19 && q != 27) return LB_EINVAL;
+    for (int i = 0; i < q; ++i) {
+        if (c) { c[3 * i] = q27::cx27(i); c[3 * i + 1] = q27::cy27(i); c[3 * i + 2] = q27::cz27(i); }
+        if (w) w[i] = q == 19 ? wd_of(i) : q27::wd27(i);
+    }
+    return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// D3Q27 path (q27.cuh): the context's boxes, at most one passive particle per
+// box, two kernels per iteration.
+static lb_status q27_create(lb_ctx* ctx, const lb_box_desc* boxes, int nbox)
+{
+    const lb_options& o = ctx->opt;
+    if (o.precision != LB_FP32 || o.collision != 0) return fail(ctx, LB_EINVAL, "D3Q27: FP32 storage and BGK only");
+    for (int b = 0; b < nbox; ++b)
+        if (boxes[b].walls) return fail(ctx, LB_EINVAL, "D3Q27: periodic boxes only");
+    ctx->lattice = 27;
+    ctx->elem = 4;
+    ctx->maxp = nbox;
+    ctx->desc.assign(boxes, boxes + nbox);
+    ctx->parts.assign(nbox, {});
+    ctx->box27_part.assign(nbox, -1);
+    long long off = 0;
+    int blk = 0;
+    std::vector<int> blk_box;
+    size_t tmp = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const lb_box_desc& d = boxes[b];
+        q27::Box27 h{};
+        h.nx = d.nx; h.ny = d.ny; h.nz = d.nz; h.counter = d.counter_force;
+        h.N = (long long)d.nx * d.ny * d.nz;
+        h.off = off;
+        off += 27 * h.N;
+        h.block_begin = blk;
+        h.nblocks = (int)((h.N + 255) / 256);
+        for (int k = 0; k < h.nblocks; ++k) blk_box.push_back(b);
+        blk += h.nblocks;
+        h.omega = (float)(1.0 / d.tau);
+        h.rho0 = d.rho0;
+        h.rho0f = (float)d.rho0;
+        for (int k = 0; k < 3; ++k) h.body[k] = d.body_force[k];
+        h.p = -1;
+        ctx->h27.push_back(h);
+        tmp = std::max(tmp, (size_t)(27 * h.N) * sizeof(float));
+    }
+    ctx->blocks27 = blk;
+    ctx->total_elems = off;
+    ctx->tmp_bytes = tmp;
+    ctx->fbuf[0] = dev_alloc(ctx, (size_t)off * 4);
+    ctx->fbuf[1] = dev_alloc(ctx, (size_t)off * 4);
+    ctx->d_box27 = (q27::Box27*)dev_alloc(ctx, sizeof(q27::Box27) * nbox);
+    ctx->d_dyn27 = (q27::Dyn27*)dev_alloc(ctx, sizeof(q27::Dyn27) * nbox);
+    ctx->d_part27 = (q27::Part27*)dev_alloc(ctx, sizeof(q27::Part27) * nbox);
+    ctx->d_blk27 = (int*)dev_alloc(ctx, sizeof(int) * (size_t)blk);
+    ctx->d_rows = (uint64_t*)dev_alloc(ctx, sizeof(uint64_t) * 2ull * MAXS * MAXS * nbox);
+    ctx->d_acc = (long long*)dev_alloc(ctx, sizeof(long long) * NACC * nbox);
+    ctx->d_status = (unsigned*)dev_alloc(ctx, sizeof(unsigned) * 4);
+    ctx->d_count = (int*)dev_alloc(ctx, sizeof(int) * 4);
+    for (void* q : {ctx->fbuf[0], ctx->fbuf[1], (void*)ctx->d_box27, (void*)ctx->d_dyn27, (void*)ctx->d_part27,
+                    (void*)ctx->d_blk27, (void*)ctx->d_rows, (void*)ctx->d_acc, (void*)ctx->d_status,
+                    (void*)ctx->d_count})
+        if (!q) return fail(ctx, LB_ENOMEM, "D3Q27 state");
+    // fluid at rest: every deviation 0
+    CK(cudaMemsetAsync(ctx->fbuf[0], 0, (size_t)off * 4, ctx->stream));
+    CK(cudaMemsetAsync(ctx->fbuf[1], 0, (size_t)off * 4, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(long long) * NACC * nbox, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned) * 4, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_blk27, blk_box.data(), sizeof(int) * blk_box.size(), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<q27::Dyn27> dyn(nbox);
+    for (int b = 0; b < nbox; ++b) {
+        dyn[b] = q27::Dyn27{};
+        for (int k = 0; k < 3; ++k) dyn[b].g[k] = (float)boxes[b].body_force[k];
+    }
+    CK(cudaMemcpyAsync(ctx->d_dyn27, dyn.data(), sizeof(q27::Dyn27) * nbox, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_box27, ctx->h27.data(), sizeof(q27::Box27) * nbox, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LB_OK;
+}
+
+static lb_status q27_set_particles(lb_ctx* ctx, int box, const lb_particle* p, int n)
+{
+    if (n > 1) return fail(ctx, LB_EINVAL, "D3Q27: at most one particle per box");
+    const lb_box_desc& d = ctx->desc[box];
+    if (n == 1) {
+        const lb_particle& P = p[0];
+        const double m = std::max(P.semi[0], std::max(P.semi[1], P.semi[2]));
+        const double qn2 = P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3];
+        if (!(P.semi[0] > 0 && P.semi[1] > 0 && P.semi[2] > 0) || !(m <= ctx->opt.max_semi) || !(P.density > 0) ||
+            !(qn2 > 0) || !std::isfinite(qn2))
+            return fail(ctx, LB_EINVAL, "bad particle");
+        if (P.B1 != 0.0 || P.B2 != 0.0) return fail(ctx, LB_EINVAL, "D3Q27: passive particles only (B1 = B2 = 0)");
+        const int h = (int)std::ceil(m) + CUBE_MARGIN, S = 2 * h + 2;
+        if (d.nx < S + 2 || d.ny < S + 2 || d.nz < S + 2)
+            return fail(ctx, LB_EINVAL, "box smaller than the particle's bounding cube");
+    }
+    ctx->parts[box].assign(p, p + n);
+    // particle slots in box order
+    ctx->hpart27.clear();
+    int np = 0;
+    for (int b = 0; b < (int)ctx->desc.size(); ++b) {
+        ctx->box27_part[b] = ctx->parts[b].empty() ? -1 : np++;
+        ctx->h27[b].p = ctx->box27_part[b];
+        if (ctx->parts[b].empty()) continue;
+        const lb_particle& P = ctx->parts[b][0];
+        q27::Part27 D{};
+        const double a = P.semi[0], bb = P.semi[1], c = P.semi[2];
+        for (int k = 0; k < 3; ++k) {
+            D.semi[k] = P.semi[k];
+            D.Fext[k] = P.F_ext[k];
+            D.Text[k] = P.T_ext[k];
+            D.x[k] = P.x[k];
+            D.U[k] = P.U[k];
+            D.W[k] = P.Omega[k];
+        }
+        // Eq. vectrotn needs |q| = 1: divided by sqrt of the squares summed in order
+        const double qn = std::sqrt(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
+        for (int k = 0; k < 4; ++k) D.q[k] = P.q[k] / qn;
+        D.M = P.density * 4.0 / 3.0 * M_PI * a * bb * c;       // continuum volume
+        D.Ib[0] = D.M * (bb * bb + c * c) / 5.0;               // Sec. II.D
+        D.Ib[1] = D.M * (a * a + c * c) / 5.0;
+        D.Ib[2] = D.M * (a * a + bb * bb) / 5.0;
+        D.h = (int)std::ceil(std::max(a, std::max(bb, c))) + CUBE_MARGIN;
+        D.S = 2 * D.h + 2;
+        D.box = b;
+        ctx->hpart27.push_back(D);
+    }
+    ctx->np = np;
+    cudaStream_t s = ctx->stream;
+    const int nbox = (int)ctx->desc.size();
+    std::vector<q27::Dyn27> dyn(nbox);
+    for (int b = 0; b < nbox; ++b) {
+        dyn[b] = q27::Dyn27{};
+        for (int k = 0; k < 3; ++k) dyn[b].g[k] = (float)ctx->desc[b].body_force[k];
+    }
+    CK(cudaMemcpyAsync(ctx->d_dyn27, dyn.data(), sizeof(q27::Dyn27) * nbox, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_box27, ctx->h27.data(), sizeof(q27::Box27) * nbox, cudaMemcpyHostToDevice, s));
+    if (np > 0)
+        CK(cudaMemcpyAsync(ctx->d_part27, ctx->hpart27.data(), sizeof(q27::Part27) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(long long) * NACC * ctx->maxp, s));
+    q27::PartParams27 pp{ctx->d_part27, ctx->d_dyn27, ctx->d_box27, ctx->d_rows, ctx->d_acc, ctx->d_status, 1,
+                         ctx->opt.didt_mode};
+    CK(q27::launch_particles27(pp, np, s));
+    CK(cudaStreamSynchronize(s));
+    return read_status(ctx);
+}
+
+static cudaError_t q27_enqueue(lb_ctx* ctx, int nsteps, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        q27::LatParams27 lp{ctx->d_box27, ctx->d_dyn27, ctx->d_blk27, ctx->d_rows, ctx->d_acc,
+                            (const float*)ctx->fbuf[ctx->cur], (float*)ctx->fbuf[ctx->cur ^ 1], ctx->collided ? 0 : 1};
+        if ((e = q27::launch_lattice27(lp, ctx->blocks27, s)) != cudaSuccess) break;
+        q27::PartParams27 pp{ctx->d_part27, ctx->d_dyn27, ctx->d_box27, ctx->d_rows, ctx->d_acc, ctx->d_status, 0,
+                             ctx->opt.didt_mode};
+        e = q27::launch_particles27(pp, ctx->np, s);
+        ctx->cur ^= 1;
+        ctx->collided = true;
+    }
+    return e;
+}
+
+static lb_status q27_get_fields(lb_ctx* ctx, int box, uint32_t what, void* dst, size_t dst_bytes, int dst_is_device,
+                                cudaStream_t s)
+{
+    const q27::Box27& B = ctx->h27[box];
+    size_t need = 0;
+    switch (what) {
+    case LB_FIELD_F: case LB_FIELD_DF: need = 27ull * B.N * 4; break;
+    case LB_FIELD_RHO: case LB_FIELD_SOLID: need = (size_t)B.N * 4; break;
+    case LB_FIELD_U: need = 3ull * B.N * 4; break;
+    default: return fail(ctx, LB_EINVAL, "exactly one LB_FIELD_* bit");
+    }
+    if (dst_bytes != need) return fail(ctx, LB_EINVAL, "dst_bytes does not match the field size");
+    if (!ctx->d_tmp) {
+        ctx->d_tmp = (float*)dev_alloc(ctx, ctx->tmp_bytes);
+        if (!ctx->d_tmp) return fail(ctx, LB_ENOMEM, "field staging buffer");
+    }
+    q27::FieldParams27 fp{};
+    fp.boxes = ctx->d_box27; fp.dyn = ctx->d_dyn27; fp.rows = ctx->d_rows;
+    fp.src = (const float*)ctx->fbuf[ctx->cur];
+    fp.box = box;
+    fp.nopull = ctx->collided ? 0 : 1;
+    fp.out_dev = what == LB_FIELD_DF ? 1 : 0;
+    if (what == LB_FIELD_F || what == LB_FIELD_DF) fp.out_f = ctx->d_tmp;
+    if (what == LB_FIELD_RHO) fp.out_rho = ctx->d_tmp;
+    if (what == LB_FIELD_U) fp.out_u = ctx->d_tmp;
+    if (what == LB_FIELD_SOLID) fp.out_solid = (int*)ctx->d_tmp;
+    CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
+    CK(q27::launch_fields27(fp, B.nblocks, s));
+    CK(cudaMemcpyAsync(dst, ctx->d_tmp, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return read_status(ctx);
+}
+
 extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_options* opt, lb_ctx** out)
 {
     if (!out) return LB_EINVAL;
@@ -201,13 +410,16 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     auto bad = [&](const std::string& m) { delete ctx; (void)m; return LB_EINVAL; };
     if (o.precision < 0 || o.precision > 2 || o.didt_mode < 0 || o.didt_mode > 2 || o.max_semi > 29 ||
         o.collision < 0 || o.collision > 1 || (o.collision == 1 && o.precision != LB_FP32) ||
+        (o.lattice != 0 && o.lattice != 19 && o.lattice != 27) ||
+        (o.lattice == 27 && (o.precision != LB_FP32 || o.collision != 0)) ||
         (o.alloc && !o.release) || (!o.alloc && o.release))
         return bad("options");
     for (int b = 0; b < nbox; ++b) {
         const lb_box_desc& d = boxes[b];
         // rows are moved in 16-byte units: nx a multiple of 4 (8 for 16-bit storage)
         if (d.nx < 4 || d.ny < 4 || d.nz < 4 || d.nx % (o.precision == LB_FP32 ? 4 : 8) != 0) return bad("box size");
-        if (!(d.tau > 0.5) || !(d.rho0 > 0.0) || (d.walls && d.ny < 5) || !(d.lub_cut >= 0.0) || d.lub_cut > 4.0)
+        if (!(d.tau > 0.5) || !(d.rho0 > 0.0) || (d.walls && d.ny < 5) || !(d.lub_cut >= 0.0) || d.lub_cut > 4.0 ||
+            (o.lattice == 27 && d.walls))
             return bad("box parameters");
         if ((long long)d.nx * d.ny * d.nz > (1ll << 31) / 19) return bad("box too large");
     }
@@ -218,6 +430,19 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
         cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming) != cudaSuccess) {
         delete ctx;
         return LB_ECUDA;
+    }
+    if (o.lattice == 27) {
+        const lb_status r = q27_create(ctx, boxes, nbox);
+        if (r != LB_OK) {
+            cudaStreamSynchronize(ctx->stream);
+            free_all(ctx);
+            cudaStreamDestroy(ctx->stream);
+            cudaEventDestroy(ctx->ev_done);
+            delete ctx;
+            return r;
+        }
+        *out = ctx;
+        return LB_OK;
     }
     ctx->elem = o.precision == LB_FP32 ? 4 : 2;
     ctx->kprec = o.collision == 1 ? 3 : o.precision;
@@ -397,6 +622,10 @@ extern "C" lb_status lb_set_particles(lb_ctx* ctx, int32_t box, const lb_particl
     if (!ctx) return LB_EINVAL;
     if (ctx->stepped) return fail(ctx, LB_ESTATE, "particles can only be set before the first step");
     if (box < 0 || box >= (int)ctx->desc.size() || n < 0 || (n > 0 && !p)) return fail(ctx, LB_EINVAL, "bad box or particle array");
+    if (ctx->lattice == 27) {
+        CK(cudaSetDevice(ctx->device));
+        return q27_set_particles(ctx, box, p, n);
+    }
     const lb_box_desc& d = ctx->desc[box];
     int total = 0;
     for (int b = 0; b < (int)ctx->parts.size(); ++b) total += (b == box) ? n : (int)ctx->parts[b].size();
@@ -549,6 +778,14 @@ extern "C" lb_status lb_set_external(lb_ctx* ctx, int32_t box, const double* ft,
     if (n == 0) return LB_OK;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = pick(ctx, stream);
+    if (ctx->lattice == 27) {
+        // F_ext, T_ext are adjacent in the particle state; then the counter force
+        const int slot = all ? 0 : ctx->box27_part[box];
+        CK(cudaMemcpy2DAsync(&ctx->d_part27[slot].Fext[0], sizeof(q27::Part27), ft, 6 * sizeof(double),
+                             6 * sizeof(double), n, cudaMemcpyHostToDevice, s));
+        CK(q27::launch_refresh27(ctx->d_part27, ctx->d_box27, ctx->d_dyn27, ctx->np, s));
+        return LB_OK;
+    }
     const int pbeg = all ? 0 : ctx->hbox[box].pbeg;
     // one strided copy straight into the particle states (F_ext, T_ext are adjacent)
     CK(cudaMemcpy2DAsync(&ctx->d_pd[pbeg].Fext[0], sizeof(PartDev), ft, 6 * sizeof(double), 6 * sizeof(double), n,
@@ -662,6 +899,11 @@ extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
     if (!cap && ctx->last_user_stream && ctx->last_user_stream != s) CK(cudaStreamWaitEvent(s, ctx->ev_done, 0));
     ctx->last_user_stream = s;
     ctx->stepped = true;
+    if (ctx->lattice == 27) {
+        CK(q27_enqueue(ctx, nsteps, s));
+        if (!cap) CK(cudaEventRecord(ctx->ev_done, s));
+        return LB_OK;
+    }
     int left = nsteps;
     if (!ctx->collided) {
         CK(enqueue_iteration(ctx, 1, ctx->cur, s));
@@ -689,6 +931,7 @@ extern "C" lb_status lb_step(lb_ctx* ctx, int32_t nsteps, void* stream)
 extern "C" lb_status lb_profile_step(lb_ctx* ctx, int32_t nsteps, void* stream, double* ms_out)
 {
     if (!ctx) return LB_EINVAL;
+    if (ctx->lattice == 27) return fail(ctx, LB_ESTATE, "not available with the D3Q27 lattice");
     if (nsteps <= 0 || !ms_out) return fail(ctx, LB_EINVAL, "bad step count or output");
     CK(cudaSetDevice(ctx->device));
     clear_stale_error();
@@ -745,6 +988,10 @@ extern "C" lb_status lb_get_fields(lb_ctx* ctx, int32_t box, uint32_t what, void
 {
     if (!ctx) return LB_EINVAL;
     if (box < 0 || box >= (int)ctx->desc.size() || !dst) return fail(ctx, LB_EINVAL, "bad box or destination");
+    if (ctx->lattice == 27) {
+        CK(cudaSetDevice(ctx->device));
+        return q27_get_fields(ctx, box, what, dst, dst_bytes, dst_is_device, pick(ctx, stream));
+    }
     const BoxDev& B = ctx->hbox[box];
     size_t need = 0;
     switch (what) {
@@ -788,6 +1035,13 @@ extern "C" lb_status lb_get_force_torque(lb_ctx* ctx, int32_t box, double* out, 
     if (n == 0) return LB_OK;
     CK(cudaSetDevice(ctx->device));
     if (ctx->last_user_stream) CK(cudaStreamSynchronize(ctx->last_user_stream));
+    if (ctx->lattice == 27) {
+        const int slot = all ? 0 : ctx->box27_part[box];
+        CK(cudaMemcpy2DAsync(out, sizeof(double) * LB_RECORD_DOUBLES, &ctx->d_part27[slot].rec[0], sizeof(q27::Part27),
+                             sizeof(double) * LB_RECORD_DOUBLES, n, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return read_status(ctx);
+    }
     const int pbeg = all ? 0 : ctx->hbox[box].pbeg;
     // gather the records into one staging block, then a single copy
     if (!ctx->d_rec) {
@@ -804,6 +1058,7 @@ extern "C" lb_status lb_get_force_torque(lb_ctx* ctx, int32_t box, double* out, 
 extern "C" lb_status lb_get_force_torque_async(lb_ctx* ctx, int32_t box, double* out, int32_t n, void* stream)
 {
     if (!ctx) return LB_EINVAL;
+    if (ctx->lattice == 27) return fail(ctx, LB_ESTATE, "not available with the D3Q27 lattice");
     const bool all = box == -1;
     if ((!all && (box < 0 || box >= (int)ctx->desc.size())) || !out ||
         n != (all ? ctx->np : (int)ctx->parts[box].size()))
@@ -844,6 +1099,7 @@ static void* device_view(lb_ctx* ctx, const void* p, size_t bytes)
 extern "C" lb_status lb_step_io(lb_ctx* ctx, int32_t nsteps, const double* ft, double* rec, void* stream)
 {
     if (!ctx) return LB_EINVAL;
+    if (ctx->lattice == 27) return fail(ctx, LB_ESTATE, "not available with the D3Q27 lattice");
     if (nsteps < 0) return fail(ctx, LB_EINVAL, "negative step count");
     if (nsteps == 0) return LB_OK;
     const size_t np = (size_t)ctx->np;
@@ -888,6 +1144,10 @@ extern "C" lb_status lb_get_drag(lb_ctx* ctx, int32_t box, int32_t particle, dou
         return fail(ctx, LB_EINVAL, "bad box or particle");
     CK(cudaSetDevice(ctx->device));
     CK(cudaDeviceSynchronize());
+    if (ctx->lattice == 27) {
+        CK(cudaMemcpy(out36, &ctx->d_part27[ctx->box27_part[box]].zeta[0], 36 * sizeof(double), cudaMemcpyDeviceToHost));
+        return read_status(ctx);
+    }
     CK(flush_aux(ctx, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(out36, &ctx->d_pd[ctx->hbox[box].pbeg + particle].zeta[0], 36 * sizeof(double), cudaMemcpyDeviceToHost));
@@ -903,14 +1163,20 @@ extern "C" lb_status lb_get_links(lb_ctx* ctx, int32_t box, int32_t particle, in
         return fail(ctx, LB_EINVAL, "bad box, particle or buffer");
     CK(cudaSetDevice(ctx->device));
     if (!ctx->d_links) {
-        ctx->links_cap = MAXS * MAXS * 18;
+        ctx->links_cap = MAXS * MAXS * (ctx->lattice == 27 ? 26 : 18);
         ctx->d_links = (int*)dev_alloc(ctx, sizeof(int) * 2ull * ctx->links_cap);
         if (!ctx->d_links) return fail(ctx, LB_ENOMEM, "link buffer");
     }
     CK(cudaDeviceSynchronize());
-    const int p = ctx->hbox[box].pbeg + particle;
-    CK(launch_links(ctx->d_pd, ctx->d_pk, ctx->d_rows, ctx->d_boxes, p, ctx->d_links, ctx->links_cap, ctx->d_count,
-                    ctx->stream));
+    if (ctx->lattice == 27) {
+        CK(cudaMemsetAsync(ctx->d_count, 0, sizeof(int), ctx->stream));
+        CK(q27::launch_links27(ctx->d_part27, ctx->d_box27, ctx->d_rows, ctx->box27_part[box], ctx->d_links,
+                               ctx->links_cap, ctx->d_count, ctx->stream));
+    } else {
+        const int p = ctx->hbox[box].pbeg + particle;
+        CK(launch_links(ctx->d_pd, ctx->d_pk, ctx->d_rows, ctx->d_boxes, p, ctx->d_links, ctx->links_cap, ctx->d_count,
+                        ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     int n = 0;
     CK(cudaMemcpy(&n, ctx->d_count, sizeof(int), cudaMemcpyDeviceToHost));
@@ -938,6 +1204,7 @@ extern "C" lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, siz
                                    int32_t is_device, int32_t with_stress, void* stream)
 {
     if (!ctx) return LB_EINVAL;
+    if (ctx->lattice == 27) return fail(ctx, LB_ESTATE, "not available with the D3Q27 lattice");
     if (box < 0 || box >= (int)ctx->desc.size() || !u) return fail(ctx, LB_EINVAL, "bad box or field");
     if (ctx->stepped) return fail(ctx, LB_ESTATE, "lb_init_fluid after the first step");
     const BoxDev& B = ctx->hbox[box];
@@ -964,6 +1231,7 @@ extern "C" lb_status lb_init_fluid(lb_ctx* ctx, int32_t box, const float* u, siz
 extern "C" lb_status lb_stokes_field(lb_ctx* ctx, int32_t box, float* u_dev, float* drho_dev, void* stream)
 {
     if (!ctx) return LB_EINVAL;
+    if (ctx->lattice == 27) return fail(ctx, LB_ESTATE, "not available with the D3Q27 lattice");
     if (box < 0 || box >= (int)ctx->desc.size() || !u_dev) return fail(ctx, LB_EINVAL, "bad box or output");
     const lb_box_desc& d = ctx->desc[box];
     if (d.walls) return fail(ctx, LB_EINVAL, "lb_stokes_field needs a fully periodic box");
@@ -1016,6 +1284,7 @@ extern "C" lb_status lb_autotune(lb_ctx* ctx, int32_t steps_per_candidate, void*
                                  double* ms_per_step)
 {
     if (!ctx) return LB_EINVAL;
+    if (ctx->lattice == 27) return fail(ctx, LB_ESTATE, "not available with the D3Q27 lattice");
     if (steps_per_candidate < 1) return fail(ctx, LB_EINVAL, "steps_per_candidate must be positive");
     if (ctx->opt.flags & LB_FLAG_SEPARATE_KERNELS) return fail(ctx, LB_ESTATE, "no step kernel to tune");
     CK(cudaSetDevice(ctx->device));

@@ -1,0 +1,692 @@
+// D3Q27 lattice and particle kernels (see q27.cuh for the method and the
+// order of an iteration).
+#include "particle_blocks.cuh"   // the exact FP64 inside test (canon_shape, canon_value)
+#include "q27.cuh"
+
+namespace lbsph {
+namespace q27 {
+
+constexpr int LBLOCK = 256;          // threads per lattice block (one node each)
+constexpr int PBLK = 256;            // threads per particle block
+constexpr int RW = MAXS * MAXS;      // words per bitmap slot
+
+__device__ __forceinline__ int wrapc(int a, int L) { return a < 0 ? a + L : (a >= L ? a - L : a); }
+
+// local coordinate of box coordinate X in a cube of side S at wrapped origin o
+// along an axis of length L; returns false outside the cube
+__device__ __forceinline__ bool cube_local(int X, int o, int L, int S, int& m)
+{
+    m = X - o;
+    if (m < 0) m += L;
+    return m < S;
+}
+
+__device__ __forceinline__ bool bit_at(const uint64_t* map, int S, int mx, int my, int mz)
+{
+    if (mx < 0 || my < 0 || mz < 0 || mx >= S || my >= S || mz >= S) return false;
+    return (__ldg(map + mz * S + my) >> mx) & 1ull;
+}
+
+enum { K_FLUID = 0, K_SOLID = 1, K_COVERED = 2, K_UNCOVERED = 3 };
+
+// Pre-collision deviations d = f - w rho0 of node (X, Y, Z) at the start of
+// iteration t, from the post-collision field A of t - 1: pull streaming, with
+// mid-link bounce-back where the source is inside the old surface (Eq. fb,
+// Eq. ub: f_i(x) = f*_{opp i}(x) + 6 w_i rho0 (u_b . c_i), u_b = U + W x r_b,
+// r_b = x - c_i/2 - x_c(t-1)), then the remap to the new map (Appendix step 8):
+// a covered node keeps its pulled values for the particle's sums (its stored
+// values become 0), an uncovered node gets f_eq(rho0, U + W x r) with
+// r = x - x_c(t).  mn: the node's local coordinates in the new cube (when
+// inside it).  nopull: the stored field is taken as it is (before the first
+// collision).
+__device__ __forceinline__ int pre_collision(const Box27& B, const Dyn27& K, const uint64_t* rows, const float* A,
+                                             int X, int Y, int Z, int node, bool nopull, float (&d)[Q27],
+                                             int (&mn)[3], bool& in_new)
+{
+    const int nx = B.nx, ny = B.ny, nz = B.nz, N = (int)B.N;
+    int mo[3] = {0, 0, 0};
+    bool in_old = false;
+    in_new = false;
+    bool sol_old = false, sol_new = false;
+    const uint64_t* map_old = nullptr;
+    const uint64_t* map_new = nullptr;
+    if (K.active) {
+        const int S = K.S;
+        map_old = rows + (size_t)K.slot_old * RW;
+        map_new = rows + (size_t)K.slot_new * RW;
+        in_old = cube_local(X, K.o_old[0], nx, S, mo[0]) && cube_local(Y, K.o_old[1], ny, S, mo[1]) &&
+                 cube_local(Z, K.o_old[2], nz, S, mo[2]);
+        in_new = cube_local(X, K.o_new[0], nx, S, mn[0]) && cube_local(Y, K.o_new[1], ny, S, mn[1]) &&
+                 cube_local(Z, K.o_new[2], nz, S, mn[2]);
+        sol_old = in_old && bit_at(map_old, S, mo[0], mo[1], mo[2]);
+        sol_new = in_new && bit_at(map_new, S, mn[0], mn[1], mn[2]);
+    }
+    if (nopull) {
+#pragma unroll
+        for (int i = 0; i < Q27; ++i) d[i] = sol_new ? 0.0f : __ldg(A + (size_t)i * N + node);
+        return sol_new ? K_SOLID : K_FLUID;
+    }
+    if (sol_old && sol_new) {
+#pragma unroll
+        for (int i = 0; i < Q27; ++i) d[i] = 0.0f;
+        return K_SOLID;
+    }
+    if (sol_old) {
+        // uncovered: f_eq(rho0, u) with u the body's velocity at the node
+        const float rx = K.phi_new[0] + mn[0], ry = K.phi_new[1] + mn[1], rz = K.phi_new[2] + mn[2];
+        const float ux = K.U[0] + (K.W[1] * rz - K.W[2] * ry);
+        const float uy = K.U[1] + (K.W[2] * rx - K.W[0] * rz);
+        const float uz = K.U[2] + (K.W[0] * ry - K.W[1] * rx);
+        const float uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int i = 0; i < Q27; ++i) {
+            const float cu = cx27(i) * ux + cy27(i) * uy + cz27(i) * uz;
+            d[i] = w27(i) * B.rho0f * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+        }
+        return K_UNCOVERED;
+    }
+    // fluid at t - 1: pull, bouncing back from the old surface
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) {
+        const int cx = cx27(i), cy = cy27(i), cz = cz27(i);
+        const bool back = in_old && i > 0 && bit_at(map_old, K.S, mo[0] - cx, mo[1] - cy, mo[2] - cz);
+        if (back) {
+            const float px = K.phi_old[0] + mo[0] - 0.5f * cx;
+            const float py = K.phi_old[1] + mo[1] - 0.5f * cy;
+            const float pz = K.phi_old[2] + mo[2] - 0.5f * cz;
+            const float ux = K.U[0] + (K.W[1] * pz - K.W[2] * py);
+            const float uy = K.U[1] + (K.W[2] * px - K.W[0] * pz);
+            const float uz = K.U[2] + (K.W[0] * py - K.W[1] * px);
+            const float ubc = cx * ux + cy * uy + cz * uz;
+            d[i] = __ldg(A + (size_t)opp27(i) * N + node) + 6.0f * w27(i) * B.rho0f * ubc;
+        } else {
+            const int src = (wrapc(Z - cz, nz) * ny + wrapc(Y - cy, ny)) * nx + wrapc(X - cx, nx);
+            d[i] = __ldg(A + (size_t)i * N + src);
+        }
+    }
+    return sol_new ? K_COVERED : K_FLUID;
+}
+
+// BGK (Eq. 3-4) with Guo forcing on deviations, mass return eps added first
+// as w_i eps to every population
+__device__ __forceinline__ void collide27(float (&d)[Q27], float omega, float rho0, const float g[3], float eps)
+{
+    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) {
+        d[i] += w27(i) * eps;
+        drho += d[i];
+        jx += cx27(i) * d[i];
+        jy += cy27(i) * d[i];
+        jz += cz27(i) * d[i];
+    }
+    const float rho = rho0 + drho;
+    const float ir = 1.0f / rho;
+    const float ux = (jx + 0.5f * g[0]) * ir, uy = (jy + 0.5f * g[1]) * ir, uz = (jz + 0.5f * g[2]) * ir;
+    const float uu = ux * ux + uy * uy + uz * uz, ug = ux * g[0] + uy * g[1] + uz * g[2];
+    const float cf = 1.0f - 0.5f * omega;
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) {
+        const float cu = cx27(i) * ux + cy27(i) * uy + cz27(i) * uz;
+        const float cg = cx27(i) * g[0] + cy27(i) * g[1] + cz27(i) * g[2];
+        const float deq = w27(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+        const float S = cf * w27(i) * (3.0f * (cg - ug) + 9.0f * cu * cg);
+        d[i] = d[i] - omega * (d[i] - deq) + S;
+    }
+}
+
+__device__ __forceinline__ long long wsum(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += (long long)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+    return v;
+}
+
+__device__ __forceinline__ void acc_add(long long* a, long long v)
+{
+    if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(v));
+}
+
+// ---------------------------------------------------------------------------
+// One lattice pass over every node of every box (one node per thread).
+__global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant__ LatParams27 P)
+{
+    const int bi = __ldg(P.blk_box + blockIdx.x);
+    const Box27 B = P.boxes[bi];
+    const Dyn27 K = P.dyn[bi];
+    const int node = (blockIdx.x - B.block_begin) * LBLOCK + threadIdx.x;
+    const bool valid = node < (int)B.N;
+    const int nd = valid ? node : (int)B.N - 1;
+    const int X = nd % B.nx, Y = (nd / B.nx) % B.ny, Z = nd / (B.nx * B.ny);
+    const float* A = P.src + B.off;
+    float* D = P.dst + B.off;
+    const uint64_t* rows = K.active ? P.rows + (size_t)B.p * 2 * RW : nullptr;
+    float d[Q27];
+    int mn[3] = {0, 0, 0};
+    bool in_new = false;
+    const int kind = pre_collision(B, K, rows, A, X, Y, Z, nd, P.first != 0, d, mn, in_new);
+    // integer sums for the particle: links of the new map, covered and uncovered nodes
+    long long aF[3] = {0, 0, 0}, aT[3] = {0, 0, 0};
+    if (valid && kind == K_COVERED) {
+        long long* acc = P.acc + (size_t)B.p * NACC;
+        float sr = 0.0f, j[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < Q27; ++i) {
+            sr += d[i];
+            j[0] += cx27(i) * d[i];
+            j[1] += cy27(i) * d[i];
+            j[2] += cz27(i) * d[i];
+        }
+        const long long J[3] = {fixp(j[0]), fixp(j[1]), fixp(j[2])};
+        acc_add(acc + ACC_COV, 1);
+        acc_add(acc + ACC_COV + 1, fixp(sr));
+        for (int k = 0; k < 3; ++k) acc_add(acc + ACC_COV + 2 + k, J[k]);
+        acc_add(acc + ACC_COV + 5, mn[1] * J[2] - mn[2] * J[1]);
+        acc_add(acc + ACC_COV + 6, mn[2] * J[0] - mn[0] * J[2]);
+        acc_add(acc + ACC_COV + 7, mn[0] * J[1] - mn[1] * J[0]);
+    } else if (valid && kind == K_UNCOVERED) {
+        long long* acc = P.acc + (size_t)B.p * NACC;
+        const long long m0 = mn[0], m1 = mn[1], m2 = mn[2];
+        const long long uv[10] = {1, m0, m1, m2, m0 * m0, m0 * m1, m0 * m2, m1 * m1, m1 * m2, m2 * m2};
+        for (int e = 0; e < 10; ++e) acc_add(acc + ACC_UNC + e, uv[e]);
+    }
+    if (kind == K_FLUID || kind == K_UNCOVERED) {
+        const float g[3] = {K.g[0], K.g[1], K.g[2]};
+        collide27(d, B.omega, B.rho0f, g, K.eps);
+        if (in_new && valid) {
+            const uint64_t* map_new = rows + (size_t)K.slot_new * RW;
+#pragma unroll
+            for (int b = 1; b < Q27; ++b) {
+                const int cx = cx27(b), cy = cy27(b), cz = cz27(b);
+                if (!bit_at(map_new, K.S, mn[0] + cx, mn[1] + cy, mn[2] + cz)) continue;
+                const long long a = fixp(2.0f * d[b]);
+                const long long gx = cx * a, gy = cy * a, gz = cz * a;
+                aF[0] += gx; aF[1] += gy; aF[2] += gz;
+                aT[0] += mn[1] * gz - mn[2] * gy;
+                aT[1] += mn[2] * gx - mn[0] * gz;
+                aT[2] += mn[0] * gy - mn[1] * gx;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q27; ++i) d[i] = 0.0f;
+    }
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < Q27; ++i) D[(size_t)i * B.N + node] = d[i];
+    }
+    // link sums: warp totals, one atomic per nonzero total
+    const bool any = __any_sync(0xffffffffu, (aF[0] | aF[1] | aF[2] | aT[0] | aT[1] | aT[2]) != 0);
+    if (any) {
+        long long* acc = P.acc + (size_t)(B.p >= 0 ? B.p : 0) * NACC;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const long long f = wsum(aF[k]), t = wsum(aT[k]);
+            if ((threadIdx.x & 31) == 0 && B.p >= 0) {
+                acc_add(acc + ACC_F + k, f);
+                acc_add(acc + ACC_T + k, t);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Rigid-body algebra in FP64 (one thread)
+__device__ __forceinline__ void qmul27(const double a[4], const double b[4], double o[4])
+{
+    o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+// q' = qt q, qt the rotation by the angle |W| about W (Eq. qnplus0-1; no
+// rotation for W = 0)
+__device__ __forceinline__ void qstep27(const double q[4], const double W[3], double o[4])
+{
+    const double n = sqrt(W[0] * W[0] + W[1] * W[1] + W[2] * W[2]);
+    double t[4] = {1.0, 0.0, 0.0, 0.0};
+    if (n >= 1e-300) {
+        const double s = sin(0.5 * n) / n;
+        t[0] = cos(0.5 * n);
+        t[1] = s * W[0]; t[2] = s * W[1]; t[3] = s * W[2];
+    }
+    qmul27(t, q, o);
+}
+
+// lab-frame inertia R diag(Ib) R^T (Eq. Irot), R the rotation of unit q
+__device__ __forceinline__ void inertia27(const double q[4], const double Ib[3], double I[9])
+{
+    const double R[9] = {1.0 - 2.0 * (q[2] * q[2] + q[3] * q[3]), 2.0 * (q[1] * q[2] - q[0] * q[3]),
+                         2.0 * (q[1] * q[3] + q[0] * q[2]),       2.0 * (q[1] * q[2] + q[0] * q[3]),
+                         1.0 - 2.0 * (q[1] * q[1] + q[3] * q[3]), 2.0 * (q[2] * q[3] - q[0] * q[1]),
+                         2.0 * (q[1] * q[3] - q[0] * q[2]),       2.0 * (q[2] * q[3] + q[0] * q[1]),
+                         1.0 - 2.0 * (q[1] * q[1] + q[2] * q[2])};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            I[i * 3 + j] = R[i * 3] * Ib[0] * R[j * 3] + R[i * 3 + 1] * Ib[1] * R[j * 3 + 1] +
+                           R[i * 3 + 2] * Ib[2] * R[j * 3 + 2];
+}
+
+// dI/dt = [W]x I - I [W]x (Eq. Irotdiff)
+__device__ __forceinline__ void inertia_rate27(const double I[9], const double W[3], double dI[9])
+{
+    const double X[9] = {0.0, -W[2], W[1], W[2], 0.0, -W[0], -W[1], W[0], 0.0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += X[i * 3 + k] * I[k * 3 + j] - I[i * 3 + k] * X[k * 3 + j];
+            dI[i * 3 + j] = s;
+        }
+}
+
+// Gaussian elimination with partial pivoting, 6 x 6; false if a pivot vanishes
+__device__ __forceinline__ bool solve6_27(const double A[36], const double b[6], double x[6])
+{
+    double M[6][7];
+    for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j < 6; ++j) M[i][j] = A[i * 6 + j];
+        M[i][6] = b[i];
+    }
+    for (int k = 0; k < 6; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < 6; ++i)
+            if (fabs(M[i][k]) > fabs(M[piv][k])) piv = i;
+        if (M[piv][k] == 0.0) return false;
+        if (piv != k)
+            for (int j = 0; j < 7; ++j) { const double t = M[k][j]; M[k][j] = M[piv][j]; M[piv][j] = t; }
+        for (int i = k + 1; i < 6; ++i) {
+            const double l = M[i][k] / M[k][k];
+            for (int j = k; j < 7; ++j) M[i][j] -= l * M[k][j];
+        }
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = M[i][6];
+        for (int j = i + 1; j < 6; ++j) s -= M[i][j] * x[j];
+        x[i] = s / M[i][i];
+    }
+    return true;
+}
+
+__device__ __forceinline__ void cross27(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// the solve of Eq. Fdiscrete / Eq. Tdiscrete for particle D, its F and T,
+// and the pose update; thread 0 of the particle's block
+__device__ void solve_and_move27(const PartParams27& P, Part27* D, const Box27& B, int p)
+{
+    long long* acc = P.acc + (size_t)p * NACC;
+    double a[NACC];
+    for (int e = 0; e < NACC; ++e) {
+        a[e] = (double)acc[e];
+        acc[e] = 0;
+    }
+    const double rho0 = B.rho0;
+    double F0[3], T0[3], Fd[3], Tm[3], J[3], MJ[3], Sm[3], phi[3];
+    for (int k = 0; k < 3; ++k) {
+        Fd[k] = a[ACC_F + k] / FIXD;
+        Tm[k] = a[ACC_T + k] / FIXD;
+        J[k] = a[ACC_COV + 2 + k] / FIXD;
+        MJ[k] = a[ACC_COV + 5 + k] / FIXD;
+        Sm[k] = a[ACC_UNC + 1 + k];
+        phi[k] = D->phi[k];
+    }
+    // Eq. F0 / Eq. T0 over the links of the current map: r_b x c_b = (phi + m) x c_b
+    double pF[3];
+    cross27(phi, Fd, pF);
+    for (int k = 0; k < 3; ++k) {
+        F0[k] = Fd[k] + D->F0g[k];
+        T0[k] = pF[k] + Tm[k] + D->T0g[k];
+    }
+    // remap terms (Appendix step 8): covered nodes give their momentum and its
+    // moment about x_c; uncovered ones take rho0 (U + W x r), r = phi + m
+    const double nc = a[ACC_COV], nu = a[ACC_UNC];
+    const double Smm[9] = {a[ACC_UNC + 4], a[ACC_UNC + 5], a[ACC_UNC + 6], a[ACC_UNC + 5], a[ACC_UNC + 7],
+                           a[ACC_UNC + 8], a[ACC_UNC + 6], a[ACC_UNC + 8], a[ACC_UNC + 9]};
+    double Sr[3], Srr[9];
+    for (int i = 0; i < 3; ++i) Sr[i] = nu * phi[i] + Sm[i];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Srr[i * 3 + j] = nu * phi[i] * phi[j] + phi[i] * Sm[j] + Sm[i] * phi[j] + Smm[i * 3 + j];
+    const double tr = Srr[0] + Srr[4] + Srr[8];
+    double WxSr[3], pJ[3], SrxU[3];
+    cross27(D->W, Sr, WxSr);
+    cross27(phi, J, pJ);
+    cross27(Sr, D->U, SrxU);
+    double dP[3], dL[3];
+    for (int k = 0; k < 3; ++k) {
+        dP[k] = J[k] - rho0 * (nu * D->U[k] + WxSr[k]);
+        const double SrrW = Srr[k * 3] * D->W[0] + Srr[k * 3 + 1] * D->W[1] + Srr[k * 3 + 2] * D->W[2];
+        dL[k] = pJ[k] + MJ[k] - rho0 * (SrxU[k] + D->W[k] * tr - SrrW);
+        D->dP[k] = dP[k];
+        D->dL[k] = dL[k];
+    }
+    D->dm = nc * rho0 + a[ACC_COV + 1] / FIXD - nu * rho0;
+    // implicit solve with I(t+1) per didt_mode
+    double In[9], dI[9], A6[36], rhs[6], x6[6];
+    inertia27(D->q, D->Ib, In);
+    if (P.didt_mode == 1) {
+        for (int k = 0; k < 9; ++k) dI[k] = In[k] - D->Iprev[k];
+    } else {
+        inertia_rate27(In, D->W, dI);
+    }
+    for (int k = 0; k < 36; ++k) A6[k] = D->zeta[k];
+    for (int k = 0; k < 3; ++k) A6[k * 6 + k] += D->M;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) A6[(i + 3) * 6 + j + 3] += In[i * 3 + j] + dI[i * 3 + j];
+    for (int k = 0; k < 3; ++k) {
+        rhs[k] = D->M * D->U[k] + F0[k] + D->Fext[k] + dP[k];
+        rhs[k + 3] = In[k * 3] * D->W[0] + In[k * 3 + 1] * D->W[1] + In[k * 3 + 2] * D->W[2] + T0[k] + D->Text[k] + dL[k];
+    }
+    bool ok = solve6_27(A6, rhs, x6);
+    if (ok && P.didt_mode == 2) {
+        // corrector: I(t+1) of the orientation the first solution predicts
+        double Wm[3], qp[4], Ip[9];
+        for (int k = 0; k < 3; ++k) Wm[k] = 0.5 * (D->W[k] + x6[k + 3]);
+        qstep27(D->q, Wm, qp);
+        inertia27(qp, D->Ib, Ip);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) A6[(i + 3) * 6 + j + 3] = D->zeta[(i + 3) * 6 + j + 3] + Ip[i * 3 + j];
+        ok = solve6_27(A6, rhs, x6);
+    }
+    if (!ok) {
+        atomicOr(P.status, ST_NAN);
+        return;
+    }
+    double F[3], T[3];
+    for (int k = 0; k < 3; ++k) {
+        double zu = 0.0, zw = 0.0, tu = 0.0, tw = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            zu += D->zeta[k * 6 + j] * x6[j];
+            zw += D->zeta[k * 6 + j + 3] * x6[j + 3];
+            tu += D->zeta[(k + 3) * 6 + j] * x6[j];
+            tw += D->zeta[(k + 3) * 6 + j + 3] * x6[j + 3];
+        }
+        F[k] = F0[k] - zu - zw;
+        T[k] = T0[k] - tu - tw;
+    }
+    for (int k = 0; k < 9; ++k) D->Iprev[k] = In[k];
+    // Eq. posupdate and Eq. qnplus0-1 with the mean velocities of the step
+    double Wm[3], qn[4];
+    for (int k = 0; k < 3; ++k) {
+        D->x[k] += 0.5 * (D->U[k] + x6[k]);
+        Wm[k] = 0.5 * (D->W[k] + x6[k + 3]);
+        D->U[k] = x6[k];
+        D->W[k] = x6[k + 3];
+    }
+    qstep27(D->q, Wm, qn);
+    for (int k = 0; k < 4; ++k) D->q[k] = qn[k];
+    double* r = D->rec;
+    for (int k = 0; k < 3; ++k) {
+        r[k] = F0[k]; r[3 + k] = T0[k]; r[6 + k] = F[k]; r[9 + k] = T[k];
+        r[12 + k] = D->U[k]; r[15 + k] = D->W[k]; r[18 + k] = D->x[k];
+    }
+    for (int k = 0; k < 4; ++k) r[21 + k] = D->q[k];
+    bool fin = true;
+    for (int k = 0; k < 25; ++k) fin = fin && isfinite(r[k]);
+    if (!fin) atomicOr(P.status, ST_NAN);
+}
+
+// ---------------------------------------------------------------------------
+// Particle kernel: one block per particle.  Step mode: the solve and pose
+// update of the last lattice pass's iteration (thread 0), then for the new
+// pose the occupancy map (exact FP64 inside test, one thread per cube row),
+// the drag matrix and geometric force terms of its links (Eq. drag1-4, every
+// thread over its rows, summed in a fixed order), and the next collision's
+// uniform terms.  Init mode: the map and its terms for the current pose.
+__global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_constant__ PartParams27 P)
+{
+    constexpr int NS = 27;                       // 21 drag-matrix entries, F0g, T0g
+    constexpr int NW = PBLK / 32;
+    const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Part27* D = P.pd + p;
+    const Box27 B = P.boxes[D->box];
+    __shared__ double s_A[9], s_x[3], s_phi[3];
+    __shared__ int s_o[3], s_ow[3], s_S, s_slot, s_ok;
+    __shared__ double s_red[NW][NS];
+    __shared__ int s_cnt[NW];
+    if (tid == 0) {
+        s_ok = 1;
+        if (!P.init) {
+            solve_and_move27(P, D, B, p);
+            if (__ldcg(P.status) & ST_NAN) s_ok = 0;
+        } else {
+            inertia27(D->q, D->Ib, D->Iprev);      // I(t - 1) = I(t) before the first step
+        }
+        // the cube of the new pose: origin floor(x) - h, side S = 2h + 2
+        const int L[3] = {B.nx, B.ny, B.nz};
+        for (int k = 0; k < 3; ++k) {
+            const int o = (int)floor(D->x[k]) - D->h;
+            s_o[k] = o;
+            s_ow[k] = ((o % L[k]) + L[k]) % L[k];
+            s_phi[k] = (double)o - D->x[k];
+            s_x[k] = D->x[k];
+        }
+        s_S = D->S;
+        s_slot = P.init ? 0 : 1 - D->slot;
+        double e[3][3];
+        canon_shape(D->semi, D->q, s_A, e);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const int S = s_S;
+    uint64_t* map = P.rows + ((size_t)p * 2 + s_slot) * RW;
+    // ---- occupancy of the new pose (Eq. ellipsoidsurface)
+    int nsol = 0;
+    for (int r = tid; r < S * S; r += PBLK) {
+        const int my = r % S, mz = r / S;
+        const int Y = wrapc(s_ow[1] + my, B.ny), Z = wrapc(s_ow[2] + mz, B.nz);
+        uint64_t w = 0;
+        for (int mx = 0; mx < S; ++mx) {
+            const int X = wrapc(s_ow[0] + mx, B.nx);
+            if (canon_value(s_A, s_x, X, Y, Z, B.nx, B.ny, B.nz, true) <= 1.0) w |= 1ull << mx;
+        }
+        map[r] = w;
+        nsol += __popcll(w);
+    }
+    __syncthreads();
+    // ---- links (x fluid, x + c_b solid) of the new map: drag matrix and the
+    // geometric parts of F0 / T0, r_b = phi + m + c_b/2
+    double acc[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) acc[k] = 0.0;
+    const double rho0 = B.rho0;
+    for (int r = tid; r < S * S; r += PBLK) {
+        const int my = r % S, mz = r / S;
+        const uint64_t own = __ldcg(map + r);
+        for (int mx = 0; mx < S; ++mx) {
+            if ((own >> mx) & 1ull) continue;
+            for (int b = 1; b < Q27; ++b) {
+                const int nx_ = mx + cx27(b), ny_ = my + cy27(b), nz_ = mz + cz27(b);
+                if (nx_ < 0 || ny_ < 0 || nz_ < 0 || nx_ >= S || ny_ >= S || nz_ >= S) continue;
+                if (!((__ldcg(map + nz_ * S + ny_) >> nx_) & 1ull)) continue;
+                const double c[3] = {(double)cx27(b), (double)cy27(b), (double)cz27(b)};
+                const double rb[3] = {s_phi[0] + mx + 0.5 * c[0], s_phi[1] + my + 0.5 * c[1], s_phi[2] + mz + 0.5 * c[2]};
+                double rxc[3];
+                cross27(rb, c, rxc);
+                const double v[6] = {c[0], c[1], c[2], rxc[0], rxc[1], rxc[2]};
+                const double wz = 6.0 * rho0 * wd27(b);        // 2 rho0 w_b / c_s^2
+                int k = 0;
+                for (int i = 0; i < 6; ++i)
+                    for (int j = i; j < 6; ++j) acc[k++] += wz * v[i] * v[j];
+                for (int i = 0; i < 3; ++i) {
+                    acc[21 + i] += 2.0 * rho0 * wd27(b) * c[i];
+                    acc[24 + i] += 2.0 * rho0 * wd27(b) * rxc[i];
+                }
+            }
+        }
+    }
+    // fixed-order sums: warp shuffles, then the warps in order
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[warp][k] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) nsol += __shfl_xor_sync(0xffffffffu, nsol, o);
+    if (lane == 0) s_cnt[warp] = nsol;
+    __syncthreads();
+    if (tid == 0) {
+        double t[NS];
+        for (int k = 0; k < NS; ++k) {
+            t[k] = 0.0;
+            for (int w = 0; w < NW; ++w) t[k] += s_red[w][k];
+        }
+        int ns = 0;
+        for (int w = 0; w < NW; ++w) ns += s_cnt[w];
+        int k = 0;
+        for (int i = 0; i < 6; ++i)
+            for (int j = i; j < 6; ++j) {
+                D->zeta[i * 6 + j] = t[k];
+                D->zeta[j * 6 + i] = t[k];
+                ++k;
+            }
+        Dyn27& Y = P.dyn[D->box];
+        for (int i = 0; i < 3; ++i) {
+            D->F0g[i] = t[21 + i];
+            D->T0g[i] = t[24 + i];
+            // the map the next pass bounces back from is the current one
+            Y.phi_old[i] = P.init ? (float)s_phi[i] : (float)D->phi[i];
+            const int L = i == 0 ? B.nx : (i == 1 ? B.ny : B.nz);
+            Y.o_old[i] = P.init ? s_ow[i] : ((D->o[i] % L) + L) % L;
+            Y.phi_new[i] = (float)s_phi[i];
+            Y.o_new[i] = s_ow[i];
+            Y.U[i] = (float)D->U[i];
+            Y.W[i] = (float)D->W[i];
+        }
+        Y.slot_old = P.init ? s_slot : D->slot;
+        Y.slot_new = s_slot;
+        Y.S = S;
+        Y.active = 1;
+        for (int i = 0; i < 3; ++i) {
+            D->phi[i] = s_phi[i];
+            D->o[i] = s_o[i];
+        }
+        D->slot = s_slot;
+        D->nsolid = ns;
+        // uniform terms of the next collision: body force (with the counter
+        // force on the fluid nodes of the new map) and the mass of this remap,
+        // returned over every fluid node
+        const double nf = (double)(B.N - ns);
+        for (int i = 0; i < 3; ++i) Y.g[i] = (float)(B.body[i] - (B.counter ? D->Fext[i] / nf : 0.0));
+        Y.eps = P.init ? 0.0f : (float)(D->dm / nf);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Read-back of one box: the pre-collision populations of the current time
+// (the first half of a lattice pass: pull, bounce-back, remap), their
+// density and velocity (u = (sum f c + g/2) / rho, g of the next collision),
+// and the occupancy.  Solid nodes read 0.
+__global__ void __launch_bounds__(LBLOCK) fields27_kernel(const __grid_constant__ FieldParams27 P)
+{
+    const Box27 B = P.boxes[P.box];
+    const Dyn27 K = P.dyn[P.box];
+    const int node = blockIdx.x * LBLOCK + threadIdx.x;
+    if (node >= (int)B.N) return;
+    const int X = node % B.nx, Y = (node / B.nx) % B.ny, Z = node / (B.nx * B.ny);
+    const uint64_t* rows = K.active ? P.rows + (size_t)B.p * 2 * RW : nullptr;
+    float d[Q27];
+    int mn[3] = {0, 0, 0};
+    bool in_new = false;
+    const int kind = pre_collision(B, K, rows, P.src + B.off, X, Y, Z, node, P.nopull != 0, d, mn, in_new);
+    const bool solid = kind == K_SOLID || kind == K_COVERED;
+    float drho = 0.0f, j[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) {
+        const float v = solid ? 0.0f : d[i];
+        if (P.out_f) P.out_f[(size_t)i * B.N + node] = solid ? 0.0f : (P.out_dev ? v : v + w27(i) * B.rho0f);
+        drho += v;
+        j[0] += cx27(i) * v;
+        j[1] += cy27(i) * v;
+        j[2] += cz27(i) * v;
+    }
+    if (P.out_rho) P.out_rho[node] = solid ? 0.0f : drho;
+    if (P.out_u)
+        for (int k = 0; k < 3; ++k) P.out_u[(size_t)k * B.N + node] = solid ? 0.0f : (j[k] + 0.5f * K.g[k]) / (B.rho0f + drho);
+    if (P.out_solid) P.out_solid[node] = solid ? 1 : 0;
+}
+
+// Boundary links of particle p's current map: pairs (node index in its box,
+// direction b) for every fluid node x with x + c_b solid
+__global__ void links27_kernel(const Part27* pd, const Box27* boxes, const uint64_t* rows, int p, int* out, int cap,
+                               int* count)
+{
+    const Part27& D = pd[p];
+    const Box27 B = boxes[D.box];
+    const int S = D.S;
+    const uint64_t* map = rows + ((size_t)p * 2 + D.slot) * RW;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= S * S) return;
+    const int my = r % S, mz = r / S;
+    const int L[3] = {B.nx, B.ny, B.nz};
+    int ow[3];
+    for (int k = 0; k < 3; ++k) ow[k] = ((D.o[k] % L[k]) + L[k]) % L[k];
+    const uint64_t own = map[r];
+    for (int mx = 0; mx < S; ++mx) {
+        if ((own >> mx) & 1ull) continue;
+        for (int b = 1; b < Q27; ++b) {
+            const int ax = mx + cx27(b), ay = my + cy27(b), az = mz + cz27(b);
+            if (ax < 0 || ay < 0 || az < 0 || ax >= S || ay >= S || az >= S) continue;
+            if (!((map[az * S + ay] >> ax) & 1ull)) continue;
+            const int X = wrapc(ow[0] + mx, B.nx), Y = wrapc(ow[1] + my, B.ny), Z = wrapc(ow[2] + mz, B.nz);
+            const int k = atomicAdd(count, 1);
+            if (k < cap) {
+                out[2 * k] = (Z * B.ny + Y) * B.nx + X;
+                out[2 * k + 1] = b;
+            }
+        }
+    }
+}
+
+// after new external forces: the counter force of the next collision,
+// -F_ext / N_fluid on the fluid nodes of the current map (one thread per particle)
+__global__ void refresh27_kernel(const Part27* pd, const Box27* boxes, Dyn27* dyn, int np)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const Part27& D = pd[p];
+    const Box27& B = boxes[D.box];
+    const double nf = (double)(B.N - D.nsolid);
+    for (int i = 0; i < 3; ++i) dyn[D.box].g[i] = (float)(B.body[i] - (B.counter ? D.Fext[i] / nf : 0.0));
+}
+
+cudaError_t launch_refresh27(const Part27* pd, const Box27* boxes, Dyn27* dyn, int np, cudaStream_t s)
+{
+    if (np <= 0) return cudaSuccess;
+    refresh27_kernel<<<(np + 127) / 128, 128, 0, s>>>(pd, boxes, dyn, np);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lattice27(const LatParams27& p, int blocks, cudaStream_t s)
+{
+    lattice27_kernel<<<blocks, LBLOCK, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_particles27(const PartParams27& p, int np, cudaStream_t s)
+{
+    if (np <= 0) return cudaSuccess;
+    particle27_kernel<<<np, PBLK, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields27(const FieldParams27& p, int blocks, cudaStream_t s)
+{
+    fields27_kernel<<<blocks, LBLOCK, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links27(const Part27* pd, const Box27* boxes, const uint64_t* rows, int p, int* out, int cap,
+                           int* count, cudaStream_t s)
+{
+    // one thread per cube row (at most 64 x 64)
+    links27_kernel<<<(MAXS * MAXS + 255) / 256, 256, 0, s>>>(pd, boxes, rows, p, out, cap, count);
+    return cudaGetLastError();
+}
+
+}  // namespace q27
+}  // namespace lbsph

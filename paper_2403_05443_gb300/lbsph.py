@@ -43,7 +43,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("didt_mode", C.c_int32), ("device", C.c_int32),
                 ("flags", C.c_uint32), ("max_semi", C.c_int32), ("max_particles", C.c_int32),
                 ("fp16_scale", C.c_double), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
-                ("alloc_user", C.c_void_p), ("collision", C.c_int32)]
+                ("alloc_user", C.c_void_p), ("collision", C.c_int32), ("lattice", C.c_int32)]
 
 
 class Particle(C.Structure):
@@ -88,6 +88,8 @@ def library(path: str | None = None):
     L.lb_stokes_field.argtypes = [vp, i32, vp, vp, vp]
     L.lb_lattice.argtypes = [ip, dp]
     L.lb_lattice.restype = None
+    L.lb_lattice_q.argtypes = [i32, ip, dp]
+    L.lb_lattice_q.restype = i32
     L.lb_status_string.argtypes = [i32]
     L.lb_status_string.restype = C.c_char_p
     L.lb_last_error.argtypes = [vp]
@@ -151,6 +153,14 @@ def lb_lattice():
     c = np.zeros((19, 3), np.int32)
     w = np.zeros(19)
     library().lb_lattice(c.ctypes.data_as(C.POINTER(C.c_int32)), w.ctypes.data_as(C.POINTER(C.c_double)))
+    return c, w
+
+
+def lb_lattice_q(q: int):
+    """(c[q,3] int32, w[q]) of the library's order of lattice q (19 or 27)."""
+    c = np.zeros((q, 3), np.int32)
+    w = np.zeros(q)
+    _check(library().lb_lattice_q(int(q), c.ctypes.data_as(C.POINTER(C.c_int32)), w.ctypes.data_as(C.POINTER(C.c_double))))
     return c, w
 
 
@@ -327,8 +337,10 @@ class Simulation:
     """A context plus the particles of its boxes; marshals to the C entry points."""
 
     def __init__(self, boxes, particles=None, precision=LB_FP32, didt_mode=0, device=0, max_semi=16,
-                 max_particles=None, fp16_scale=0.0, separate_kernels=False, torch_alloc=False, collision=0):
+                 max_particles=None, fp16_scale=0.0, separate_kernels=False, torch_alloc=False, collision=0,
+                 lattice=19):
         self.boxes = [dict(b) for b in boxes]
+        self.Q = int(lattice)
         parts = particles or [[] for _ in boxes]
         opt = Options()
         opt.precision, opt.didt_mode, opt.device = precision, didt_mode, device
@@ -337,6 +349,7 @@ class Simulation:
         opt.max_particles = int(max_particles or max(1, sum(len(p) for p in parts)))
         opt.fp16_scale = float(fp16_scale)
         opt.collision = int(collision)
+        opt.lattice = self.Q
         self._alloc = None
         if torch_alloc:
             self._alloc = _torch_allocator(device)
@@ -378,7 +391,7 @@ class Simulation:
         b = self.boxes[box]
         N = b["nx"] * b["ny"] * b["nz"]
         what = _FIELD_NAMES[name]
-        shape = {"f": (19,), "df": (19,), "rho": (), "u": (3,), "solid": ()}[name] + (b["nz"], b["ny"], b["nx"])
+        shape = {"f": (self.Q,), "df": (self.Q,), "rho": (), "u": (3,), "solid": ()}[name] + (b["nz"], b["ny"], b["nx"])
         out = np.zeros(shape, np.int32 if name == "solid" else np.float32)
         lb_get_fields(self.ctx, box, what, out.ctypes.data, out.nbytes, False)
         assert out.size * 4 == out.nbytes and out.size == int(np.prod(shape)) and N > 0

@@ -40,7 +40,7 @@ def test_python_binding_has_the_same_names():
 
 
 def test_abi_version_and_status_strings():
-    assert L.lb_abi_version() == 4
+    assert L.lb_abi_version() == 5
     assert L.lb_status_string(0) == "ok"
     assert L.lb_status_string(1) == "invalid argument"
     assert L.lb_status_string(99) == "unknown status"
@@ -58,6 +58,37 @@ def test_lattice_table_is_d3q19():
     # opposite directions are adjacent pairs (1,2), (3,4), ...
     for i in range(1, 19, 2):
         assert (c[i] == -c[i + 1]).all()
+
+
+def test_lattice_tables_of_both_lattices():
+    """lb_lattice_q(27) against the oracle's D3Q27 (as vectors), its first 19
+    directions are the D3Q19 table in the same order, opposite directions are
+    adjacent pairs; other lattices are refused."""
+    from oracle import oracle as O
+    c19, w19 = L.lb_lattice()
+    c, w = L.lb_lattice_q(19)
+    assert (c == c19).all() and (w == w19).all()
+    c, w = L.lb_lattice_q(27)
+    co, wo = O.lattice(27)
+    assert {tuple(v): wi for v, wi in zip(c.tolist(), w)} == {tuple(v): wi for v, wi in zip(co.tolist(), wo)}
+    assert (c[:19] == c19).all()
+    for i in range(1, 27, 2):
+        assert (c[i] == -c[i + 1]).all()
+    with pytest.raises(L.LBError):
+        L.lb_lattice_q(15)
+
+
+def test_create_rejects_bad_d3q27_options_without_touching_the_gpu():
+    """D3Q27 takes FP32 storage, BGK and periodic boxes; an unknown lattice is refused."""
+    b = {"nx": 32, "ny": 32, "nz": 32, "tau": 1.0}
+    for kw in ({"lattice": 27, "precision": L.LB_BF16}, {"lattice": 27, "collision": 1}, {"lattice": 21}):
+        opt = L.Options()
+        opt.max_semi, opt.max_particles = 8, 4
+        for k, v in kw.items():
+            setattr(opt, k, v)
+        with pytest.raises(L.LBError) as e:
+            L.lb_create([b], opt)
+        assert e.value.status == 1
 
 
 def test_create_rejects_bad_boxes_without_touching_the_gpu():

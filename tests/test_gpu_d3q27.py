@@ -1,0 +1,189 @@
+"""Parity of the D3Q27 path (lb_options.lattice = 27, called through the C ABI)
+with the FP64 D3Q27 oracle (the same oracle source compiled for the 27-velocity
+lattice, pinned in tests/test_oracle_d3q27.py).
+
+Bars, as for D3Q19: occupancy maps and boundary links bit-exact for the same
+FP64 pose (the same exact inside test, links over all 26 neighbours); the drag
+matrix to 1e-12 of its largest entry; the deviations f_i - w_i rho0 and u
+within 1e-5 normwise, F and T within 1e-5 (of their own size, or of their link
+sums where the net value is a small residual of them), the centre and the
+quaternion within 1e-5 of the distance moved / angle turned.  Measured: fields
+5e-7 - 1.2e-6, F and T up to 7e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from lb_inputs import box, particle, random_pose, random_quaternion, rng, single_32
+from parity_util import normwise
+
+pytestmark = pytest.mark.gpu
+
+L = pytest.importorskip("paper_2403_05443_gb300.lbsph")
+
+Q = 27
+
+
+def _sim(boxes, parts, **kw):
+    ms = max([max(p["semi"]) for pl in parts for p in pl] + [1.0])
+    return L.Simulation(boxes, parts, max_semi=int(math.ceil(ms)), lattice=Q, **kw)
+
+
+def _orc(b, pl, didt_mode=0):
+    bb = dict(b)
+    bb["lattice"] = Q
+    bb["didt_mode"] = didt_mode
+    return O.Sim(bb, pl, nthreads=8)
+
+
+def _perm():
+    """perm[i_gpu] = i_oracle for the same velocity vector."""
+    cg, _ = L.lb_lattice_q(Q)
+    co, _ = O.lattice(Q)
+    idx = {tuple(v): k for k, v in enumerate(co.tolist())}
+    return np.array([idx[tuple(v)] for v in cg.tolist()])
+
+
+def _oracle_df(o, rho0=1.0):
+    f = o.f()
+    _, w = O.lattice(Q)
+    df = f - w[None, None, None, :] * rho0
+    df[o.owner() != 0] = 0.0
+    return np.ascontiguousarray(np.moveaxis(df[..., _perm()], -1, 0))
+
+
+def _links(gpu, b=0):
+    node, d = gpu.links(b, 0)
+    c, _ = L.lb_lattice_q(Q)
+    return {(int(n), tuple(int(v) for v in c[k])) for n, k in zip(node, d)}
+
+
+def _orc_links(o):
+    node, cv = o.links(0)
+    return {(int(n), tuple(int(v) for v in c)) for n, c in zip(node, cv)}
+
+
+def _compare(boxes, parts, steps, every, didt_mode=0, tol=1e-5, ft_scale="self"):
+    """Side by side every `every` steps.  F and T against their own size, or
+    (ft_scale "links", for a body whose net force or torque is a small
+    residual of F = F0 - zeta (U', Omega')) against the size of their parts:
+    F0 for the force, the larger of T0 and F0 times the long semi-axis for the
+    torque."""
+    gpu = _sim(boxes, parts, didt_mode=didt_mode)
+    orcs = [_orc(b, pl, didt_mode) for b, pl in zip(boxes, parts)]
+    worst = {"df": 0.0, "u": 0.0, "F": 0.0, "T": 0.0, "x": 0.0, "q": 0.0}
+    hist = {}
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        gpu.step(k)
+        for o in orcs:
+            o.step(k)
+        done += k
+        for bi, (b, o) in enumerate(zip(boxes, orcs)):
+            worst["df"] = max(worst["df"], normwise(gpu.field("df", bi), _oracle_df(o, b.get("rho0", 1.0))))
+            _, ur = o.moments()
+            worst["u"] = max(worst["u"], normwise(gpu.field("u", bi), np.moveaxis(ur, -1, 0)))
+            if parts[bi]:
+                r, s = gpu.particle(bi, 0), o.particle(0)
+                h = hist.setdefault(bi, {"F": [], "Fr": [], "T": [], "Tr": [], "F0r": [], "T0r": []})
+                h["F"].append(r["F"]); h["Fr"].append(s["F"]); h["T"].append(r["T"]); h["Tr"].append(s["T"])
+                h["F0r"].append(s["F0"]); h["T0r"].append(s["T0"])
+                p0 = parts[bi][0]
+                moved = float(np.abs(s["x"] - np.array(p0["x"])).max())
+                turned = 2.0 * math.acos(min(1.0, abs(float(s["q"] @ np.array(p0.get("q", (1, 0, 0, 0)), float)))))
+                worst["x"] = max(worst["x"], float(np.abs(r["x"] - s["x"]).max()) / (1e-5 * moved + 1e-9))
+                worst["q"] = max(worst["q"], float(np.abs(r["q"] - s["q"]).max()) / (1e-5 * turned + 1e-9))
+    for bi, h in hist.items():
+        for q in ("F", "T"):
+            got, ref = np.array(h[q]), np.array(h[q + "r"])
+            if ft_scale == "links":
+                den = float(np.abs(np.array(h[q + "0r"])).max())
+                if q == "T":
+                    den = max(den, max(parts[bi][0]["semi"]) * float(np.abs(np.array(h["F0r"])).max()))
+                worst[q] = max(worst[q], float(np.abs(got - ref).max()) / max(den, 1e-30))
+            else:
+                worst[q] = max(worst[q], normwise(got, ref))
+    print("d3q27 parity", worst)
+    assert worst["df"] <= tol and worst["u"] <= tol
+    assert worst["F"] <= tol and worst["T"] <= tol
+    assert worst["x"] <= 1.0 and worst["q"] <= 1.0
+    return gpu, orcs
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_d3q27_solid_map_links_and_drag_matrix(seed):
+    g = rng(2700 + seed)
+    n = [int(v) for v in g.choice([24, 28, 32], size=3)]
+    semi = [float(v) for v in g.uniform(1.5, 5.0, 3)]
+    c, q = random_pose(g, min(n), margin=-1)       # anywhere: periodic wrap of the cube
+    b = box(*n, 1.0)
+    p = particle(semi, c, q)
+    gpu = _sim([b], [[p]])
+    o = _orc(b, [p])
+    assert np.array_equal(gpu.field("solid"), (o.owner() != 0).astype(np.int32))
+    got, want = _links(gpu), _orc_links(o)
+    assert got == want
+    assert any(sum(abs(t) for t in l[1]) == 3 for l in got)      # corner links present
+    Z, Zr = gpu.drag(0, 0), o.zeta(0)
+    assert np.abs(Z - Zr).max() <= 1e-12 * np.abs(Zr).max()
+
+
+def test_d3q27_rest_state_and_fluid_with_body_force():
+    """No particle: a box with a uniform body force and a box at rest, 40
+    steps, every field against the oracle."""
+    boxes = [box(24, 20, 28, 0.8, body_force=(2e-6, -1e-6, 5e-7)), box(16, 16, 16, 1.0)]
+    _compare(boxes, [[], []], steps=40, every=10)
+
+
+def test_d3q27_single_spheroid_32_every_step():
+    """Config 1 on the D3Q27 lattice: 32^3, tau = 1, spheroid (4,2,2), random
+    pose, F_ext = 1e-4 with counter force, every step for 200 steps."""
+    boxes, parts = single_32(seed=0)
+    _compare(boxes, parts, steps=200, every=1)
+
+
+def test_d3q27_spheroid_at_tau_08_uneven_boxes():
+    """Three boxes of different sizes in one context, tau 0.8 and 1.3, one of
+    them without a particle; the sphere under a torque alone feels a net force
+    that is a residual of its link sums, compared against their size."""
+    g = rng(27)
+    boxes = [box(28, 24, 32, 0.8, counter_force=1), box(20, 20, 20, 1.3), box(24, 24, 24, 1.3, counter_force=1)]
+    parts = [[particle((5.0, 2.5, 2.5), (13.3, 11.7, 15.2), random_quaternion(g), F_ext=(2e-4, -1e-4, 5e-5))], [],
+             [particle((3.0, 3.0, 3.0), (11.6, 12.1, 12.4), random_quaternion(g), T_ext=(1e-3, 0.0, 5e-4))]]
+    _compare(boxes, parts, steps=100, every=10, ft_scale="links")
+
+
+def test_d3q27_fast_particle_covers_and_uncovers_nodes():
+    g = rng(9)
+    b = box(24, 20, 28, 0.9)
+    p = particle((4.5, 2.5, 2.0), (10.3, 9.1, 11.7), random_quaternion(g), U=(0.03, -0.02, 0.025),
+                 Om=(0.004, 0.006, -0.005), density=5.0)
+    _compare([b], [[p]], steps=60, every=3)
+
+
+@pytest.mark.parametrize("didt_mode", [1, 2])
+def test_d3q27_inertia_rate_modes(didt_mode):
+    g = rng(13)
+    b = box(24, 24, 28, 0.9)
+    p = particle((5.5, 3.5, 2.5), (11.7, 12.2, 13.9), random_quaternion(g), Om=(0.004, -0.006, 0.008),
+                 T_ext=(2e-3, 1e-3, -1.5e-3), density=3.0)
+    _compare([b], [[p]], steps=60, every=6, didt_mode=didt_mode)
+
+
+def test_d3q27_unsupported_requests_are_refused():
+    b = box(24, 24, 24, 1.0)
+    g = rng(5)
+    with pytest.raises(L.LBError) as e:           # two particles in a box
+        _sim([b], [[particle((3.0, 2.0, 2.0), (6.0, 6.0, 6.0), random_quaternion(g)),
+                    particle((3.0, 2.0, 2.0), (17.0, 17.0, 17.0), random_quaternion(g))]])
+    assert e.value.status == 1
+    with pytest.raises(L.LBError) as e:           # a squirmer
+        _sim([b], [[particle((3.0, 2.0, 2.0), (12.0, 12.0, 12.0), random_quaternion(g), B1=1e-3)]])
+    assert e.value.status == 1
+    gpu = _sim([b], [[particle((3.0, 2.0, 2.0), (12.0, 12.0, 12.0), random_quaternion(g))]])
+    with pytest.raises(L.LBError) as e:
+        L.lb_autotune(gpu.ctx, 2)
+    assert e.value.status == 8
