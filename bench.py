@@ -15,7 +15,9 @@ The line's value is the FP32 leg (or --precision's).  After it, the same
 workload runs with FP16 and BF16 deviation storage for the same K steps
 ("mixed": MLUPS, roofline fraction and ratio to FP32), and one box of the sweep
 is run in all three formats against the FP64 oracle for --drag-steps
-iterations ("mixed.drag_error_vs_oracle").  "steps_to_steady" is the learned
+iterations ("mixed.drag_error_vs_oracle"), and the D3Q27 lattice runs the
+same workload in FP32 ("d3q27": MLUPS and the fraction of the HBM roofline at
+216 bytes per lattice update).  "steps_to_steady" is the learned
 warm start on the surrogate workload's evaluation box (128^3, 16 spheroids):
 steps until every particle's velocity stays within 1e-2 / 3e-3 / 1e-3 of its
 steady value, cold, with the lattice fluid's steady flow only, and warm.
@@ -324,17 +326,22 @@ def steps_to_steady_block(args):
     return ev
 
 
-def run_leg(args, pkg, precision, boxes, parts, local, dist, stream, sp, primary):
-    """Warm-up, autotune and the timed K steps of one storage format on the
-    workload; returns its measurements (and the simulation, still open)."""
+def run_leg(args, pkg, precision, boxes, parts, local, dist, stream, sp, primary, lattice=19):
+    """Warm-up, autotune and the timed K steps of one storage format (or of the
+    D3Q27 lattice, which has no tuner) on the workload; returns its
+    measurements (and the simulation, still open)."""
     import torch
 
     nodes = sum(b["nx"] * b["ny"] * b["nz"] for b in boxes)
-    sim = pkg.Simulation(boxes, parts, precision=PREC[precision], max_semi=8, device=local, torch_alloc=True)
+    sim = pkg.Simulation(boxes, parts, precision=PREC[precision], max_semi=8, device=local, torch_alloc=True,
+                         lattice=lattice)
     sim.step(args.warmup, stream=sp)
-    # launch shape of the step kernel for this workload (untimed; the
-    # candidates compute identical values, so this is more warm-up)
-    (fetch, gx, _), tune_ms = pkg.lbsph.lb_autotune(sim.ctx, 64, sp)
+    if lattice == 19:
+        # launch shape of the step kernel for this workload (untimed; the
+        # candidates compute identical values, so this is more warm-up)
+        (fetch, gx, _), tune_ms = pkg.lbsph.lb_autotune(sim.ctx, 64, sp)
+    else:
+        fetch, gx, tune_ms = None, None, [0.0] * 10
     sim.step(args.warmup, stream=sp)           # the kept shape, right before the timed steps
     torch.cuda.synchronize()
     if dist is not None:
@@ -354,7 +361,7 @@ def run_leg(args, pkg, precision, boxes, parts, local, dist, stream, sp, primary
     ms = max_over_ranks(e0.elapsed_time(e1), dist)
     per = ms / args.steps / 1e3
     peak, peak_src = measured_peak()
-    achieved = BYTES_PER_LUP[precision] * nodes / per / 1e9
+    achieved = (BYTES_PER_LUP[precision] if lattice == 19 else 2 * 27 * 4) * nodes / per / 1e9
     return sim, {"value": whole_job_mlups(nodes, args.steps, env_int("WORLD_SIZE", 1), ms / 1e3),
                  "ms_per_step": ms / args.steps, "achieved_gbs": achieved, "frac": achieved / peak,
                  "peak": peak, "peak_source": peak_src,
@@ -443,6 +450,17 @@ def run_ours(args):
                                         "frac": leg["frac"], "bytes_per_lup": BYTES_PER_LUP[prec]},
                            "tuning": leg["tuning"]}
             mixed[prec]["ratio_vs_fp32"] = leg["value"] / lead["value"]
+    # the D3Q27 lattice on the same workload (FP32; two kernels per step)
+    d3q27 = None
+    if args.precision == "fp32" and not args.no_d3q27:
+        s27, leg = run_leg(args, pkg, "fp32", boxes, parts, local, dist, stream, sp, False, lattice=27)
+        s27.close()
+        d3q27 = {"value": leg["value"], "unit": "MLUPS", "ms_per_step": leg["ms_per_step"],
+                 "roofline": {"achieved": leg["achieved_gbs"], "peak": leg["peak"], "unit": "GB/s",
+                              "frac": leg["frac"], "bytes_per_lup": 2 * 27 * 4},
+                 "ratio_vs_d3q19_fp32": leg["value"] / lead["value"],
+                 "kernels": "lattice27_kernel (pull, bounce-back, remap, collision, link sums) + "
+                            "particle27_kernel (solve, pose, map, drag matrix) per step"}
     clk = clocks.stop()
 
     extra = {}
@@ -475,6 +493,7 @@ def run_ours(args):
                              "method": f"lb_profile_step: the four parts as separate kernels, {nprof} "
                                        "iterations after the timed region, CUDA events between them"}},
             "mixed": mixed,
+            "d3q27": d3q27,
             "e2e": {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": int(ft_in.numel() * 8),
                     "d2h_bytes_per_step": int(rec_out.numel() * 8), "steps": ke,
                     "path": "lb_step_io over all steps: per step F_ext/T_ext in from that step's pinned slot, "
@@ -505,6 +524,7 @@ def main():
     ap.add_argument("--workload", default="sweep_8x64", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP16 / BF16 legs")
+    ap.add_argument("--no-d3q27", action="store_true", help="skip the D3Q27 leg")
     ap.add_argument("--drag-steps", type=int, default=3000,
                     help="iterations of the drag-error check against the oracle (0: skip)")
     ap.add_argument("--steady-steps", type=int, default=40000,

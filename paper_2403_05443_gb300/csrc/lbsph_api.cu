@@ -239,6 +239,9 @@ static lb_status q27_create(lb_ctx* ctx, const lb_box_desc* boxes, int nbox)
         h.rho0f = (float)d.rho0;
         for (int k = 0; k < 3; ++k) h.body[k] = d.body_force[k];
         h.p = -1;
+        magic_div((unsigned)d.nx, h.dx_m, h.dx_s);
+        magic_div((unsigned)d.ny, h.dy_m, h.dy_s);
+        if (27ll * h.N >= (1ll << 31)) return fail(ctx, LB_EINVAL, "D3Q27: box too large (27 N >= 2^31)");
         ctx->h27.push_back(h);
         tmp = std::max(tmp, (size_t)(27 * h.N) * sizeof(float));
     }

@@ -63,7 +63,7 @@ __device__ __forceinline__ int pre_collision(const Box27& B, const Dyn27& K, con
     }
     if (nopull) {
 #pragma unroll
-        for (int i = 0; i < Q27; ++i) d[i] = sol_new ? 0.0f : __ldg(A + (size_t)i * N + node);
+        for (int i = 0; i < Q27; ++i) d[i] = sol_new ? 0.0f : __ldg(A + (i * N + node));
         return sol_new ? K_SOLID : K_FLUID;
     }
     if (sol_old && sol_new) {
@@ -85,11 +85,23 @@ __device__ __forceinline__ int pre_collision(const Box27& B, const Dyn27& K, con
         }
         return K_UNCOVERED;
     }
-    // fluid at t - 1: pull, bouncing back from the old surface
+    // fluid at t - 1: pull, bouncing back from the old surface.  The source
+    // x - c_i is node + ox[c_x] + oy[c_y] + oz[c_z], each offset wrapped at the
+    // box faces (index 0: c = -1, 2: c = +1).
+    const int nxy = nx * ny;
+    const int ox[3] = {X == nx - 1 ? 1 - nx : 1, 0, X == 0 ? nx - 1 : -1};
+    const int oy[3] = {Y == ny - 1 ? nx - nxy : nx, 0, Y == 0 ? nxy - nx : -nx};
+    const int oz[3] = {Z == nz - 1 ? nxy - N : nxy, 0, Z == 0 ? N - nxy : -nxy};
+    if (!in_old) {
+#pragma unroll
+        for (int i = 0; i < Q27; ++i)
+            d[i] = __ldg(A + (i * N + node + ox[cx27(i) + 1] + oy[cy27(i) + 1] + oz[cz27(i) + 1]));
+        return sol_new ? K_COVERED : K_FLUID;
+    }
 #pragma unroll
     for (int i = 0; i < Q27; ++i) {
         const int cx = cx27(i), cy = cy27(i), cz = cz27(i);
-        const bool back = in_old && i > 0 && bit_at(map_old, K.S, mo[0] - cx, mo[1] - cy, mo[2] - cz);
+        const bool back = i > 0 && bit_at(map_old, K.S, mo[0] - cx, mo[1] - cy, mo[2] - cz);
         if (back) {
             const float px = K.phi_old[0] + mo[0] - 0.5f * cx;
             const float py = K.phi_old[1] + mo[1] - 0.5f * cy;
@@ -98,10 +110,9 @@ __device__ __forceinline__ int pre_collision(const Box27& B, const Dyn27& K, con
             const float uy = K.U[1] + (K.W[2] * px - K.W[0] * pz);
             const float uz = K.U[2] + (K.W[0] * py - K.W[1] * px);
             const float ubc = cx * ux + cy * uy + cz * uz;
-            d[i] = __ldg(A + (size_t)opp27(i) * N + node) + 6.0f * w27(i) * B.rho0f * ubc;
+            d[i] = __ldg(A + (opp27(i) * N + node)) + 6.0f * w27(i) * B.rho0f * ubc;
         } else {
-            const int src = (wrapc(Z - cz, nz) * ny + wrapc(Y - cy, ny)) * nx + wrapc(X - cx, nx);
-            d[i] = __ldg(A + (size_t)i * N + src);
+            d[i] = __ldg(A + (i * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]));
         }
     }
     return sol_new ? K_COVERED : K_FLUID;
@@ -151,13 +162,24 @@ __device__ __forceinline__ void acc_add(long long* a, long long v)
 // One lattice pass over every node of every box (one node per thread).
 __global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant__ LatParams27 P)
 {
+    __shared__ Box27 sB;
+    __shared__ Dyn27 sK;
     const int bi = __ldg(P.blk_box + blockIdx.x);
-    const Box27 B = P.boxes[bi];
-    const Dyn27 K = P.dyn[bi];
+    if (threadIdx.x < sizeof(Box27) / 4)
+        reinterpret_cast<int*>(&sB)[threadIdx.x] = __ldg(reinterpret_cast<const int*>(P.boxes + bi) + threadIdx.x);
+    else if (threadIdx.x >= 64 && threadIdx.x < 64 + sizeof(Dyn27) / 4)
+        reinterpret_cast<int*>(&sK)[threadIdx.x - 64] =
+            __ldg(reinterpret_cast<const int*>(P.dyn + bi) + (threadIdx.x - 64));
+    __syncthreads();
+    const Box27& B = sB;
+    const Dyn27& K = sK;
     const int node = (blockIdx.x - B.block_begin) * LBLOCK + threadIdx.x;
     const bool valid = node < (int)B.N;
     const int nd = valid ? node : (int)B.N - 1;
-    const int X = nd % B.nx, Y = (nd / B.nx) % B.ny, Z = nd / (B.nx * B.ny);
+    const int row = div_magic(nd, B.dx_m, B.dx_s);
+    const int X = nd - row * B.nx;
+    const int Z = div_magic(row, B.dy_m, B.dy_s);
+    const int Y = row - Z * B.ny;
     const float* A = P.src + B.off;
     float* D = P.dst + B.off;
     const uint64_t* rows = K.active ? P.rows + (size_t)B.p * 2 * RW : nullptr;
@@ -433,21 +455,29 @@ __device__ void solve_and_move27(const PartParams27& P, Part27* D, const Box27& 
 // ---------------------------------------------------------------------------
 // Particle kernel: one block per particle.  Step mode: the solve and pose
 // update of the last lattice pass's iteration (thread 0), then for the new
-// pose the occupancy map (exact FP64 inside test, one thread per cube row),
-// the drag matrix and geometric force terms of its links (Eq. drag1-4, every
-// thread over its rows, summed in a fixed order), and the next collision's
-// uniform terms.  Init mode: the map and its terms for the current pose.
+// pose the occupancy map (Eq. ellipsoidsurface), built in shared memory one
+// cube row per thread: along a row the inside value is the quadratic
+// a x^2 + b x + c, evaluated in FP32 and decided there when it is farther than
+// 1e-3 from 1 (its FP32 error stays below 1e-4 inside the cube), and by the
+// exact FP64 test in the oracle's operation order otherwise, so the map is
+// bit-identical to the oracle's.  The links (x fluid, x + c_b solid) of each
+// row and direction are a bit mask; their drag matrix and the geometric parts
+// of F0 / T0 (Eq. drag1-4, Eq. F0, Eq. T0) come from exact integer sums per
+// direction (link count, sum of m, sum of m m^T over the cube coordinates m of
+// the fluid ends), combined once in FP64 with p = phi + m, r_b x c_b = p x c_b.
+// Init mode: the map and its terms for the current pose.
 __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_constant__ PartParams27 P)
 {
-    constexpr int NS = 27;                       // 21 drag-matrix entries, F0g, T0g
-    constexpr int NW = PBLK / 32;
-    const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NSUM = 10;                     // per direction: n, sum m (3), sum m m^T (6)
+    const int p = blockIdx.x, tid = threadIdx.x;
     Part27* D = P.pd + p;
     const Box27 B = P.boxes[D->box];
+    __shared__ uint64_t s_map[MAXS * MAXS];
+    __shared__ int s_sum[Q27][NSUM];
+    __shared__ double s_con[Q27][42];            // per direction: drag matrix (36), F0g (3), T0g (3)
     __shared__ double s_A[9], s_x[3], s_phi[3];
-    __shared__ int s_o[3], s_ow[3], s_S, s_slot, s_ok;
-    __shared__ double s_red[NW][NS];
-    __shared__ int s_cnt[NW];
+    __shared__ float s_A32[9], s_d0[3];
+    __shared__ int s_o[3], s_ow[3], s_S, s_slot, s_ok, s_nsol;
     if (tid == 0) {
         s_ok = 1;
         if (!P.init) {
@@ -463,95 +493,146 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
             s_o[k] = o;
             s_ow[k] = ((o % L[k]) + L[k]) % L[k];
             s_phi[k] = (double)o - D->x[k];
+            s_d0[k] = (float)s_phi[k];             // d = X - x_c at cube coordinate 0
             s_x[k] = D->x[k];
         }
         s_S = D->S;
         s_slot = P.init ? 0 : 1 - D->slot;
+        s_nsol = 0;
         double e[3][3];
         canon_shape(D->semi, D->q, s_A, e);
+        for (int k = 0; k < 9; ++k) s_A32[k] = (float)s_A[k];
     }
+    for (int k = tid; k < Q27 * NSUM; k += PBLK) (&s_sum[0][0])[k] = 0;
     __syncthreads();
     if (!s_ok) return;
     const int S = s_S;
-    uint64_t* map = P.rows + ((size_t)p * 2 + s_slot) * RW;
-    // ---- occupancy of the new pose (Eq. ellipsoidsurface)
+    const uint64_t full = S == 64 ? ~0ull : ((1ull << S) - 1ull);
+    // ---- occupancy of the new pose
     int nsol = 0;
     for (int r = tid; r < S * S; r += PBLK) {
         const int my = r % S, mz = r / S;
         const int Y = wrapc(s_ow[1] + my, B.ny), Z = wrapc(s_ow[2] + mz, B.nz);
+        const float dy = s_d0[1] + (float)my, dz = s_d0[2] + (float)mz;
+        const float qa = s_A32[0], qb = 2.0f * (s_A32[1] * dy + s_A32[2] * dz);
+        const float qc = s_A32[4] * dy * dy + 2.0f * s_A32[5] * dy * dz + s_A32[8] * dz * dz;
         uint64_t w = 0;
         for (int mx = 0; mx < S; ++mx) {
-            const int X = wrapc(s_ow[0] + mx, B.nx);
-            if (canon_value(s_A, s_x, X, Y, Z, B.nx, B.ny, B.nz, true) <= 1.0) w |= 1ull << mx;
+            const float dx = s_d0[0] + (float)mx;
+            const float v = (qa * dx + qb) * dx + qc;
+            bool in;
+            if (fabsf(v - 1.0f) > 1e-3f) {
+                in = v < 1.0f;
+            } else {
+                const int X = wrapc(s_ow[0] + mx, B.nx);
+                in = canon_value(s_A, s_x, X, Y, Z, B.nx, B.ny, B.nz, true) <= 1.0;
+            }
+            if (in) w |= 1ull << mx;
         }
-        map[r] = w;
+        s_map[r] = w;
         nsol += __popcll(w);
     }
+    if (nsol) atomicAdd(&s_nsol, nsol);
     __syncthreads();
-    // ---- links (x fluid, x + c_b solid) of the new map: drag matrix and the
-    // geometric parts of F0 / T0, r_b = phi + m + c_b/2
-    double acc[NS];
-#pragma unroll
-    for (int k = 0; k < NS; ++k) acc[k] = 0.0;
-    const double rho0 = B.rho0;
+    // ---- links of the new map, summed per direction in integers
     for (int r = tid; r < S * S; r += PBLK) {
         const int my = r % S, mz = r / S;
-        const uint64_t own = __ldcg(map + r);
-        for (int mx = 0; mx < S; ++mx) {
-            if ((own >> mx) & 1ull) continue;
-            for (int b = 1; b < Q27; ++b) {
-                const int nx_ = mx + cx27(b), ny_ = my + cy27(b), nz_ = mz + cz27(b);
-                if (nx_ < 0 || ny_ < 0 || nz_ < 0 || nx_ >= S || ny_ >= S || nz_ >= S) continue;
-                if (!((__ldcg(map + nz_ * S + ny_) >> nx_) & 1ull)) continue;
-                const double c[3] = {(double)cx27(b), (double)cy27(b), (double)cz27(b)};
-                const double rb[3] = {s_phi[0] + mx + 0.5 * c[0], s_phi[1] + my + 0.5 * c[1], s_phi[2] + mz + 0.5 * c[2]};
-                double rxc[3];
-                cross27(rb, c, rxc);
-                const double v[6] = {c[0], c[1], c[2], rxc[0], rxc[1], rxc[2]};
-                const double wz = 6.0 * rho0 * wd27(b);        // 2 rho0 w_b / c_s^2
-                int k = 0;
-                for (int i = 0; i < 6; ++i)
-                    for (int j = i; j < 6; ++j) acc[k++] += wz * v[i] * v[j];
-                for (int i = 0; i < 3; ++i) {
-                    acc[21 + i] += 2.0 * rho0 * wd27(b) * c[i];
-                    acc[24 + i] += 2.0 * rho0 * wd27(b) * rxc[i];
-                }
+        const uint64_t fluid = ~s_map[r] & full;
+#pragma unroll
+        for (int b = 1; b < Q27; ++b) {
+            const int ny_ = my + cy27(b), nz_ = mz + cz27(b);
+            if (ny_ < 0 || nz_ < 0 || ny_ >= S || nz_ >= S) continue;
+            const uint64_t nb = s_map[nz_ * S + ny_];
+            const uint64_t sol = cx27(b) == 1 ? (nb >> 1) : (cx27(b) == -1 ? (nb << 1) : nb);
+            uint64_t links = fluid & sol & full;
+            if (!links) continue;
+            int n = 0, sx = 0, sxx = 0;
+            while (links) {
+                const int mx = __ffsll((long long)links) - 1;
+                links &= links - 1;
+                ++n; sx += mx; sxx += mx * mx;
             }
+            int* t = s_sum[b];
+            atomicAdd(t + 0, n);
+            atomicAdd(t + 1, sx);
+            atomicAdd(t + 2, n * my);
+            atomicAdd(t + 3, n * mz);
+            atomicAdd(t + 4, sxx);
+            atomicAdd(t + 5, sx * my);
+            atomicAdd(t + 6, sx * mz);
+            atomicAdd(t + 7, n * my * my);
+            atomicAdd(t + 8, n * my * mz);
+            atomicAdd(t + 9, n * mz * mz);
         }
     }
-    // fixed-order sums: warp shuffles, then the warps in order
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        double v = acc[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_red[warp][k] = v;
+    // the map into its global slot (the lattice kernel and the read-back use it)
+    uint64_t* map = P.rows + ((size_t)p * 2 + s_slot) * RW;
+    for (int r = tid; r < S * S; r += PBLK) map[r] = s_map[r];
+    __syncthreads();
+    // each direction's share of the drag matrix and of F0g / T0g (thread b),
+    // then every entry summed over the directions in order (threads 0..56)
+    if (tid >= 1 && tid < Q27) {
+        const int b = tid;
+        const double rho0 = B.rho0;
+        const double* phi = s_phi;
+        double* out = s_con[b];
+        const int* t = s_sum[b];
+        const double n = t[0];
+        const double c[3] = {(double)cx27(b), (double)cy27(b), (double)cz27(b)};
+        const double Sm[3] = {(double)t[1], (double)t[2], (double)t[3]};
+        const double Qm[9] = {(double)t[4], (double)t[5], (double)t[6], (double)t[5], (double)t[7],
+                              (double)t[8], (double)t[6], (double)t[8], (double)t[9]};
+        // sums over the direction's links of p = phi + m and p p^T
+        double Pb[3], PP[9];
+        for (int i = 0; i < 3; ++i) Pb[i] = n * phi[i] + Sm[i];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                PP[i * 3 + j] = n * phi[i] * phi[j] + phi[i] * Sm[j] + Sm[i] * phi[j] + Qm[i * 3 + j];
+        // p x c = K p, K = -[c]x
+        const double K[9] = {0.0, c[2], -c[1], -c[2], 0.0, c[0], c[1], -c[0], 0.0};
+        double KP[3], KPP[9];
+        for (int i = 0; i < 3; ++i) KP[i] = K[i * 3] * Pb[0] + K[i * 3 + 1] * Pb[1] + K[i * 3 + 2] * Pb[2];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                KPP[i * 3 + j] = K[i * 3] * PP[j] + K[i * 3 + 1] * PP[3 + j] + K[i * 3 + 2] * PP[6 + j];
+        const double wz = 6.0 * rho0 * wd27(b);        // 2 rho0 w_b / c_s^2
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                out[i * 6 + j] = wz * n * c[i] * c[j];
+                out[i * 6 + j + 3] = wz * c[i] * KP[j];
+                out[(i + 3) * 6 + j] = wz * KP[i] * c[j];
+                out[(i + 3) * 6 + j + 3] =
+                    wz * (KPP[i * 3] * K[j * 3] + KPP[i * 3 + 1] * K[j * 3 + 1] + KPP[i * 3 + 2] * K[j * 3 + 2]);
+            }
+        for (int i = 0; i < 3; ++i) {
+            out[36 + i] = 2.0 * rho0 * wd27(b) * n * c[i];
+            out[39 + i] = 2.0 * rho0 * wd27(b) * KP[i];
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) nsol += __shfl_xor_sync(0xffffffffu, nsol, o);
-    if (lane == 0) s_cnt[warp] = nsol;
+    __syncthreads();
+    if (tid < 42) {
+        double v = 0.0;
+        for (int b = 1; b < Q27; ++b) v += s_con[b][tid];
+        s_con[0][tid] = v;
+    }
     __syncthreads();
     if (tid == 0) {
-        double t[NS];
-        for (int k = 0; k < NS; ++k) {
-            t[k] = 0.0;
-            for (int w = 0; w < NW; ++w) t[k] += s_red[w][k];
+        double Z6[36], F0g[3], T0g[3];
+        for (int k = 0; k < 36; ++k) Z6[k] = s_con[0][k];
+        for (int i = 0; i < 3; ++i) {
+            F0g[i] = s_con[0][36 + i];
+            T0g[i] = s_con[0][39 + i];
         }
-        int ns = 0;
-        for (int w = 0; w < NW; ++w) ns += s_cnt[w];
-        int k = 0;
-        for (int i = 0; i < 6; ++i)
-            for (int j = i; j < 6; ++j) {
-                D->zeta[i * 6 + j] = t[k];
-                D->zeta[j * 6 + i] = t[k];
-                ++k;
-            }
+        for (int k = 0; k < 36; ++k) D->zeta[k] = Z6[k];
+        const int ns = s_nsol;
         Dyn27& Y = P.dyn[D->box];
         for (int i = 0; i < 3; ++i) {
-            D->F0g[i] = t[21 + i];
-            D->T0g[i] = t[24 + i];
+            D->F0g[i] = F0g[i];
+            D->T0g[i] = T0g[i];
             // the map the next pass bounces back from is the current one
+            const int Lk = i == 0 ? B.nx : (i == 1 ? B.ny : B.nz);
             Y.phi_old[i] = P.init ? (float)s_phi[i] : (float)D->phi[i];
-            const int L = i == 0 ? B.nx : (i == 1 ? B.ny : B.nz);
-            Y.o_old[i] = P.init ? s_ow[i] : ((D->o[i] % L) + L) % L;
+            Y.o_old[i] = P.init ? s_ow[i] : ((D->o[i] % Lk) + Lk) % Lk;
             Y.phi_new[i] = (float)s_phi[i];
             Y.o_new[i] = s_ow[i];
             Y.U[i] = (float)D->U[i];

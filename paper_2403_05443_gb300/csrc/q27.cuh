@@ -22,6 +22,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "lbsph_internal.cuh"
+
 namespace lbsph {
 namespace q27 {
 
@@ -64,6 +66,8 @@ struct Box27 {
     float omega, rho0f;
     double rho0, body[3];
     int p;                          // the box's particle, or -1
+    unsigned dx_m, dy_m;            // n / nx and n / ny as __umulhi(n, m) >> s (div_magic)
+    int dx_s, dy_s;
     int pad;
 };
 
