@@ -105,6 +105,10 @@ struct lb_ctx {
     q27::Part27* d_part27 = nullptr;
     int* d_blk27 = nullptr;
     int blocks27 = 0;
+    int dpar27 = 0;                    // slot of d_dyn27 ([2][nbox]) the next lattice pass reads
+    int nbpp27 = 1;                    // near-pass blocks per particle
+    cudaStream_t s27 = nullptr;        // near pass and particle kernel, beside the bulk pass
+    cudaEvent_t ev27a = nullptr, ev27b = nullptr;
 };
 
 static lb_status fail(lb_ctx* c, lb_status s, const std::string& msg)
@@ -251,7 +255,7 @@ static lb_status q27_create(lb_ctx* ctx, const lb_box_desc* boxes, int nbox)
     ctx->fbuf[0] = dev_alloc(ctx, (size_t)off * 4);
     ctx->fbuf[1] = dev_alloc(ctx, (size_t)off * 4);
     ctx->d_box27 = (q27::Box27*)dev_alloc(ctx, sizeof(q27::Box27) * nbox);
-    ctx->d_dyn27 = (q27::Dyn27*)dev_alloc(ctx, sizeof(q27::Dyn27) * nbox);
+    ctx->d_dyn27 = (q27::Dyn27*)dev_alloc(ctx, sizeof(q27::Dyn27) * 2 * nbox);
     ctx->d_part27 = (q27::Part27*)dev_alloc(ctx, sizeof(q27::Part27) * nbox);
     ctx->d_blk27 = (int*)dev_alloc(ctx, sizeof(int) * (size_t)blk);
     ctx->d_rows = (uint64_t*)dev_alloc(ctx, sizeof(uint64_t) * 2ull * MAXS * MAXS * nbox);
@@ -273,8 +277,17 @@ static lb_status q27_create(lb_ctx* ctx, const lb_box_desc* boxes, int nbox)
         dyn[b] = q27::Dyn27{};
         for (int k = 0; k < 3; ++k) dyn[b].g[k] = (float)boxes[b].body_force[k];
     }
-    CK(cudaMemcpyAsync(ctx->d_dyn27, dyn.data(), sizeof(q27::Dyn27) * nbox, cudaMemcpyHostToDevice, ctx->stream));
+    for (int slot = 0; slot < 2; ++slot)
+        CK(cudaMemcpyAsync(ctx->d_dyn27 + slot * nbox, dyn.data(), sizeof(q27::Dyn27) * nbox, cudaMemcpyHostToDevice,
+                           ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_box27, ctx->h27.data(), sizeof(q27::Box27) * nbox, cudaMemcpyHostToDevice, ctx->stream));
+    // the near pass and the particle kernel are the step's critical chain: the
+    // highest stream priority places their blocks before waiting bulk blocks
+    int prio_lo = 0, prio_hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    CK(cudaStreamCreateWithPriority(&ctx->s27, cudaStreamNonBlocking, prio_hi));
+    CK(cudaEventCreateWithFlags(&ctx->ev27a, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev27b, cudaEventDisableTiming));
     CK(cudaStreamSynchronize(ctx->stream));
     return LB_OK;
 }
@@ -334,29 +347,61 @@ static lb_status q27_set_particles(lb_ctx* ctx, int box, const lb_particle* p, i
         dyn[b] = q27::Dyn27{};
         for (int k = 0; k < 3; ++k) dyn[b].g[k] = (float)ctx->desc[b].body_force[k];
     }
-    CK(cudaMemcpyAsync(ctx->d_dyn27, dyn.data(), sizeof(q27::Dyn27) * nbox, cudaMemcpyHostToDevice, s));
+    for (int slot = 0; slot < 2; ++slot)
+        CK(cudaMemcpyAsync(ctx->d_dyn27 + slot * nbox, dyn.data(), sizeof(q27::Dyn27) * nbox, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_box27, ctx->h27.data(), sizeof(q27::Box27) * nbox, cudaMemcpyHostToDevice, s));
+    // the near pass covers the union of a particle's old and new cubes, at most
+    // (S + 1)^3 nodes while it moves less than one node per step
+    long long umax = 1;
+    for (const auto& D : ctx->hpart27) umax = std::max(umax, (long long)(D.S + 1) * (D.S + 1) * (D.S + 1));
+    ctx->nbpp27 = (int)((umax + 255) / 256);
     if (np > 0)
         CK(cudaMemcpyAsync(ctx->d_part27, ctx->hpart27.data(), sizeof(q27::Part27) * np, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(long long) * NACC * ctx->maxp, s));
-    q27::PartParams27 pp{ctx->d_part27, ctx->d_dyn27, ctx->d_box27, ctx->d_rows, ctx->d_acc, ctx->d_status, 1,
-                         ctx->opt.didt_mode};
+    q27::PartParams27 pp{ctx->d_part27, ctx->d_dyn27 + (size_t)ctx->dpar27 * nbox, ctx->d_box27, ctx->d_rows,
+                         ctx->d_acc, ctx->d_status, 1, ctx->opt.didt_mode};
     CK(q27::launch_particles27(pp, np, s));
     CK(cudaStreamSynchronize(s));
     return read_status(ctx);
 }
 
+// One step: the first collision, or a context without particles, is one
+// lattice pass over every node and then the particle kernel; afterwards the
+// nodes of the particles' cube unions (near pass) and the particle kernel run
+// on a stream of their own beside the bulk pass over every other node, and the
+// next step waits for both.  The particle kernel writes the box terms of the
+// next pass into the other slot of d_dyn27, so the bulk pass never reads a slot
+// that is being written.
 static cudaError_t q27_enqueue(lb_ctx* ctx, int nsteps, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
+    const size_t nbox = ctx->desc.size();
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        q27::LatParams27 lp{ctx->d_box27, ctx->d_dyn27, ctx->d_blk27, ctx->d_rows, ctx->d_acc,
-                            (const float*)ctx->fbuf[ctx->cur], (float*)ctx->fbuf[ctx->cur ^ 1], ctx->collided ? 0 : 1};
-        if ((e = q27::launch_lattice27(lp, ctx->blocks27, s)) != cudaSuccess) break;
-        q27::PartParams27 pp{ctx->d_part27, ctx->d_dyn27, ctx->d_box27, ctx->d_rows, ctx->d_acc, ctx->d_status, 0,
+        const q27::Dyn27* dcur = ctx->d_dyn27 + (size_t)ctx->dpar27 * nbox;
+        q27::Dyn27* dnext = ctx->d_dyn27 + (size_t)(ctx->dpar27 ^ 1) * nbox;
+        q27::LatParams27 lp{ctx->d_box27, dcur, ctx->d_part27, ctx->d_blk27, ctx->d_rows, ctx->d_acc,
+                            (const float*)ctx->fbuf[ctx->cur], (float*)ctx->fbuf[ctx->cur ^ 1], ctx->collided ? 0 : 1,
+                            q27::LAT_ALL, ctx->nbpp27};
+        q27::PartParams27 pp{ctx->d_part27, dnext, ctx->d_box27, ctx->d_rows, ctx->d_acc, ctx->d_status, 0,
                              ctx->opt.didt_mode};
-        e = q27::launch_particles27(pp, ctx->np, s);
+        if (!ctx->collided || ctx->np == 0) {
+            if ((e = q27::launch_lattice27(lp, ctx->blocks27, s)) != cudaSuccess) break;
+            if ((e = q27::launch_particles27(pp, ctx->np, s)) != cudaSuccess) break;
+        } else {
+            if ((e = cudaEventRecord(ctx->ev27a, s)) != cudaSuccess) break;
+            if ((e = cudaStreamWaitEvent(ctx->s27, ctx->ev27a, 0)) != cudaSuccess) break;
+            q27::LatParams27 near = lp;
+            near.mode = q27::LAT_NEAR;
+            if ((e = q27::launch_lattice27(near, ctx->np * ctx->nbpp27, ctx->s27)) != cudaSuccess) break;
+            if ((e = q27::launch_particles27(pp, ctx->np, ctx->s27)) != cudaSuccess) break;
+            q27::LatParams27 bulk = lp;
+            bulk.mode = q27::LAT_BULK;
+            if ((e = q27::launch_lattice27(bulk, ctx->blocks27, s)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(ctx->ev27b, ctx->s27)) != cudaSuccess) break;
+            if ((e = cudaStreamWaitEvent(s, ctx->ev27b, 0)) != cudaSuccess) break;
+        }
         ctx->cur ^= 1;
+        ctx->dpar27 ^= 1;
         ctx->collided = true;
     }
     return e;
@@ -379,7 +424,7 @@ static lb_status q27_get_fields(lb_ctx* ctx, int box, uint32_t what, void* dst, 
         if (!ctx->d_tmp) return fail(ctx, LB_ENOMEM, "field staging buffer");
     }
     q27::FieldParams27 fp{};
-    fp.boxes = ctx->d_box27; fp.dyn = ctx->d_dyn27; fp.rows = ctx->d_rows;
+    fp.boxes = ctx->d_box27; fp.dyn = ctx->d_dyn27 + (size_t)ctx->dpar27 * ctx->desc.size(); fp.rows = ctx->d_rows;
     fp.src = (const float*)ctx->fbuf[ctx->cur];
     fp.box = box;
     fp.nopull = ctx->collided ? 0 : 1;
@@ -439,6 +484,9 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
         if (r != LB_OK) {
             cudaStreamSynchronize(ctx->stream);
             free_all(ctx);
+            if (ctx->s27) cudaStreamDestroy(ctx->s27);
+            if (ctx->ev27a) cudaEventDestroy(ctx->ev27a);
+            if (ctx->ev27b) cudaEventDestroy(ctx->ev27b);
             cudaStreamDestroy(ctx->stream);
             cudaEventDestroy(ctx->ev_done);
             delete ctx;
@@ -571,6 +619,9 @@ extern "C" lb_status lb_destroy(lb_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     cudaDeviceSynchronize();
     free_all(ctx);
+    if (ctx->s27) cudaStreamDestroy(ctx->s27);
+    if (ctx->ev27a) cudaEventDestroy(ctx->ev27a);
+    if (ctx->ev27b) cudaEventDestroy(ctx->ev27b);
     cudaStreamDestroy(ctx->stream);
     cudaEventDestroy(ctx->ev_done);
     delete ctx;
@@ -786,7 +837,8 @@ extern "C" lb_status lb_set_external(lb_ctx* ctx, int32_t box, const double* ft,
         const int slot = all ? 0 : ctx->box27_part[box];
         CK(cudaMemcpy2DAsync(&ctx->d_part27[slot].Fext[0], sizeof(q27::Part27), ft, 6 * sizeof(double),
                              6 * sizeof(double), n, cudaMemcpyHostToDevice, s));
-        CK(q27::launch_refresh27(ctx->d_part27, ctx->d_box27, ctx->d_dyn27, ctx->np, s));
+        CK(q27::launch_refresh27(ctx->d_part27, ctx->d_box27, ctx->d_dyn27 + (size_t)ctx->dpar27 * ctx->desc.size(),
+                                 ctx->np, s));
         return LB_OK;
     }
     const int pbeg = all ? 0 : ctx->hbox[box].pbeg;

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant
 {
     __shared__ Box27 sB;
     __shared__ Dyn27 sK;
-    const int bi = __ldg(P.blk_box + blockIdx.x);
+    const int bi = P.mode == LAT_NEAR ? __ldg(&P.pd[blockIdx.x / P.nbpp].box) : __ldg(P.blk_box + blockIdx.x);
     if (threadIdx.x < sizeof(Box27) / 4)
         reinterpret_cast<int*>(&sB)[threadIdx.x] = __ldg(reinterpret_cast<const int*>(P.boxes + bi) + threadIdx.x);
     else if (threadIdx.x >= 64 && threadIdx.x < 64 + sizeof(Dyn27) / 4)
@@ -173,20 +173,52 @@ __global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant
     __syncthreads();
     const Box27& B = sB;
     const Dyn27& K = sK;
-    const int node = (blockIdx.x - B.block_begin) * LBLOCK + threadIdx.x;
-    const bool valid = node < (int)B.N;
-    const int nd = valid ? node : (int)B.N - 1;
-    const int row = div_magic(nd, B.dx_m, B.dx_s);
-    const int X = nd - row * B.nx;
-    const int Z = div_magic(row, B.dy_m, B.dy_s);
-    const int Y = row - Z * B.ny;
+    bool valid, skip = false;
+    int nd, X, Y, Z;
+    if (P.mode == LAT_NEAR) {
+        // the nodes of the box that holds the particle's old and new cubes
+        const int l = (blockIdx.x % P.nbpp) * LBLOCK + threadIdx.x;
+        const int e0 = K.E[0], e1 = K.E[1];
+        valid = l < e0 * e1 * K.E[2];
+        const int ll = valid ? l : 0;
+        const int mz = ll / (e0 * e1), my = (ll / e0) % e1, mx = ll % e0;
+        X = wrapc(K.uo[0] + mx, B.nx);
+        Y = wrapc(K.uo[1] + my, B.ny);
+        Z = wrapc(K.uo[2] + mz, B.nz);
+        nd = (Z * B.ny + Y) * B.nx + X;
+    } else {
+        const int node = (blockIdx.x - B.block_begin) * LBLOCK + threadIdx.x;
+        valid = node < (int)B.N;
+        nd = valid ? node : (int)B.N - 1;
+        const int row = div_magic(nd, B.dx_m, B.dx_s);
+        X = nd - row * B.nx;
+        Z = div_magic(row, B.dy_m, B.dy_s);
+        Y = row - Z * B.ny;
+        if (P.mode == LAT_BULK && K.active) {
+            // nodes of the cube union are left to the near pass
+            int m;
+            if (cube_local(X, K.uo[0], B.nx, K.E[0], m) && cube_local(Y, K.uo[1], B.ny, K.E[1], m) &&
+                cube_local(Z, K.uo[2], B.nz, K.E[2], m))
+                skip = true;
+        }
+    }
+    const int node = nd;
     const float* A = P.src + B.off;
     float* D = P.dst + B.off;
     const uint64_t* rows = K.active ? P.rows + (size_t)B.p * 2 * RW : nullptr;
     float d[Q27];
     int mn[3] = {0, 0, 0};
     bool in_new = false;
-    const int kind = pre_collision(B, K, rows, A, X, Y, Z, nd, P.first != 0, d, mn, in_new);
+    // a skipped node reads nothing: its cube's maps may be rewritten meanwhile
+    // by the particle kernel beside this pass
+    if (skip) valid = false;
+    int kind = K_SOLID;
+    if (skip) {
+#pragma unroll
+        for (int i = 0; i < Q27; ++i) d[i] = 0.0f;
+    } else {
+        kind = pre_collision(B, K, rows, A, X, Y, Z, nd, P.first != 0, d, mn, in_new);
+    }
     // integer sums for the particle: links of the new map, covered and uncovered nodes
     long long aF[3] = {0, 0, 0}, aT[3] = {0, 0, 0};
     if (valid && kind == K_COVERED) {
@@ -302,34 +334,6 @@ __device__ __forceinline__ void inertia_rate27(const double I[9], const double W
         }
 }
 
-// Gaussian elimination with partial pivoting, 6 x 6; false if a pivot vanishes
-__device__ __forceinline__ bool solve6_27(const double A[36], const double b[6], double x[6])
-{
-    double M[6][7];
-    for (int i = 0; i < 6; ++i) {
-        for (int j = 0; j < 6; ++j) M[i][j] = A[i * 6 + j];
-        M[i][6] = b[i];
-    }
-    for (int k = 0; k < 6; ++k) {
-        int piv = k;
-        for (int i = k + 1; i < 6; ++i)
-            if (fabs(M[i][k]) > fabs(M[piv][k])) piv = i;
-        if (M[piv][k] == 0.0) return false;
-        if (piv != k)
-            for (int j = 0; j < 7; ++j) { const double t = M[k][j]; M[k][j] = M[piv][j]; M[piv][j] = t; }
-        for (int i = k + 1; i < 6; ++i) {
-            const double l = M[i][k] / M[k][k];
-            for (int j = k; j < 7; ++j) M[i][j] -= l * M[k][j];
-        }
-    }
-    for (int i = 5; i >= 0; --i) {
-        double s = M[i][6];
-        for (int j = i + 1; j < 6; ++j) s -= M[i][j] * x[j];
-        x[i] = s / M[i][i];
-    }
-    return true;
-}
-
 __device__ __forceinline__ void cross27(const double a[3], const double b[3], double o[3])
 {
     o[0] = a[1] * b[2] - a[2] * b[1];
@@ -337,9 +341,13 @@ __device__ __forceinline__ void cross27(const double a[3], const double b[3], do
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// the solve of Eq. Fdiscrete / Eq. Tdiscrete for particle D, its F and T,
-// and the pose update; thread 0 of the particle's block
-__device__ void solve_and_move27(const PartParams27& P, Part27* D, const Box27& B, int p)
+// The parts of the solve of Eq. Fdiscrete / Eq. Tdiscrete for particle D,
+// spread over the block: q27_sums (one thread) turns the integer sums of the
+// last lattice pass into F0, T0 and the remap terms; the inertia and its rate
+// come from another warp at the same time; a warp solves the 6 x 6 system
+// (Gauss-Jordan, partial pivoting, one column per lane); q27_finish (one
+// thread) forms F and T and moves the particle.
+__device__ void q27_sums(const PartParams27& P, Part27* D, const Box27& B, int p, double F0[3], double T0[3])
 {
     long long* acc = P.acc + (size_t)p * NACC;
     double a[NACC];
@@ -348,7 +356,7 @@ __device__ void solve_and_move27(const PartParams27& P, Part27* D, const Box27& 
         acc[e] = 0;
     }
     const double rho0 = B.rho0;
-    double F0[3], T0[3], Fd[3], Tm[3], J[3], MJ[3], Sm[3], phi[3];
+    double Fd[3], Tm[3], J[3], MJ[3], Sm[3], phi[3];
     for (int k = 0; k < 3; ++k) {
         Fd[k] = a[ACC_F + k] / FIXD;
         Tm[k] = a[ACC_T + k] / FIXD;
@@ -378,46 +386,44 @@ __device__ void solve_and_move27(const PartParams27& P, Part27* D, const Box27& 
     cross27(D->W, Sr, WxSr);
     cross27(phi, J, pJ);
     cross27(Sr, D->U, SrxU);
-    double dP[3], dL[3];
     for (int k = 0; k < 3; ++k) {
-        dP[k] = J[k] - rho0 * (nu * D->U[k] + WxSr[k]);
+        D->dP[k] = J[k] - rho0 * (nu * D->U[k] + WxSr[k]);
         const double SrrW = Srr[k * 3] * D->W[0] + Srr[k * 3 + 1] * D->W[1] + Srr[k * 3 + 2] * D->W[2];
-        dL[k] = pJ[k] + MJ[k] - rho0 * (SrxU[k] + D->W[k] * tr - SrrW);
-        D->dP[k] = dP[k];
-        D->dL[k] = dL[k];
+        D->dL[k] = pJ[k] + MJ[k] - rho0 * (SrxU[k] + D->W[k] * tr - SrrW);
     }
     D->dm = nc * rho0 + a[ACC_COV + 1] / FIXD - nu * rho0;
-    // implicit solve with I(t+1) per didt_mode
-    double In[9], dI[9], A6[36], rhs[6], x6[6];
-    inertia27(D->q, D->Ib, In);
-    if (P.didt_mode == 1) {
-        for (int k = 0; k < 9; ++k) dI[k] = In[k] - D->Iprev[k];
-    } else {
-        inertia_rate27(In, D->W, dI);
-    }
+}
+
+// the system of Eq. Fdiscrete / Eq. Tdiscrete: A = zeta + diag(M) + (I + dI)
+// in the rotational block, rhs = (M U + F0 + F_ext + dP, I W + T0 + T_ext + dL)
+__device__ void q27_system(const Part27* D, const double In[9], const double dI[9], const double F0[3],
+                           const double T0[3], double A6[36], double rhs[6])
+{
     for (int k = 0; k < 36; ++k) A6[k] = D->zeta[k];
     for (int k = 0; k < 3; ++k) A6[k * 6 + k] += D->M;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) A6[(i + 3) * 6 + j + 3] += In[i * 3 + j] + dI[i * 3 + j];
     for (int k = 0; k < 3; ++k) {
-        rhs[k] = D->M * D->U[k] + F0[k] + D->Fext[k] + dP[k];
-        rhs[k + 3] = In[k * 3] * D->W[0] + In[k * 3 + 1] * D->W[1] + In[k * 3 + 2] * D->W[2] + T0[k] + D->Text[k] + dL[k];
+        rhs[k] = D->M * D->U[k] + F0[k] + D->Fext[k] + D->dP[k];
+        rhs[k + 3] = In[k * 3] * D->W[0] + In[k * 3 + 1] * D->W[1] + In[k * 3 + 2] * D->W[2] + T0[k] + D->Text[k] +
+                     D->dL[k];
     }
-    bool ok = solve6_27(A6, rhs, x6);
-    if (ok && P.didt_mode == 2) {
-        // corrector: I(t+1) of the orientation the first solution predicts
-        double Wm[3], qp[4], Ip[9];
-        for (int k = 0; k < 3; ++k) Wm[k] = 0.5 * (D->W[k] + x6[k + 3]);
-        qstep27(D->q, Wm, qp);
-        inertia27(qp, D->Ib, Ip);
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) A6[(i + 3) * 6 + j + 3] = D->zeta[(i + 3) * 6 + j + 3] + Ip[i * 3 + j];
-        ok = solve6_27(A6, rhs, x6);
-    }
-    if (!ok) {
-        atomicOr(P.status, ST_NAN);
-        return;
-    }
+}
+
+// one warp: x = A^-1 rhs (lane 6 holds the result); false if a pivot vanishes
+__device__ __forceinline__ bool q27_warp_solve(const double A6[36], const double rhs[6], double x6[6], int lane)
+{
+    double col[6];
+    for (int i = 0; i < 6; ++i) col[i] = lane < 6 ? A6[i * 6 + lane] : (lane == 6 ? rhs[i] : 0.0);
+    const bool ok = gj_solve6_warp(col, lane);
+    if (lane == 6)
+        for (int i = 0; i < 6; ++i) x6[i] = col[i];
+    return ok;
+}
+
+__device__ void q27_finish(const PartParams27& P, Part27* D, const double In[9], const double x6[6],
+                           const double F0[3], const double T0[3])
+{
     double F[3], T[3];
     for (int k = 0; k < 3; ++k) {
         double zu = 0.0, zw = 0.0, tu = 0.0, tw = 0.0;
@@ -478,10 +484,52 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
     __shared__ double s_A[9], s_x[3], s_phi[3];
     __shared__ float s_A32[9], s_d0[3];
     __shared__ int s_o[3], s_ow[3], s_S, s_slot, s_ok, s_nsol;
+    if (!P.init) {
+        __shared__ double s_F0[3], s_T0[3], s_In[9], s_dI[9], s_A6[36], s_rhs[6], s_x6[6];
+        __shared__ int s_solved;
+        if (tid == 0) {
+            q27_sums(P, D, B, p, s_F0, s_T0);
+        } else if (tid == 32) {
+            inertia27(D->q, D->Ib, s_In);
+            if (P.didt_mode == 1) {
+                for (int k = 0; k < 9; ++k) s_dI[k] = s_In[k] - D->Iprev[k];
+            } else {
+                inertia_rate27(s_In, D->W, s_dI);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) q27_system(D, s_In, s_dI, s_F0, s_T0, s_A6, s_rhs);
+        __syncthreads();
+        if (tid < 32) {
+            const bool ok = q27_warp_solve(s_A6, s_rhs, s_x6, tid);
+            if (tid == 0) s_solved = ok;
+        }
+        __syncthreads();
+        if (P.didt_mode == 2 && s_solved) {
+            // corrector: I(t+1) of the orientation the first solution predicts
+            if (tid == 0) {
+                double Wm[3], qp[4], Ip[9];
+                for (int k = 0; k < 3; ++k) Wm[k] = 0.5 * (D->W[k] + s_x6[k + 3]);
+                qstep27(D->q, Wm, qp);
+                inertia27(qp, D->Ib, Ip);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) s_A6[(i + 3) * 6 + j + 3] = D->zeta[(i + 3) * 6 + j + 3] + Ip[i * 3 + j];
+            }
+            __syncthreads();
+            if (tid < 32) {
+                const bool ok = q27_warp_solve(s_A6, s_rhs, s_x6, tid);
+                if (tid == 0) s_solved = ok;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            if (!s_solved) atomicOr(P.status, ST_NAN);
+            else q27_finish(P, D, s_In, s_x6, s_F0, s_T0);
+        }
+    }
     if (tid == 0) {
         s_ok = 1;
         if (!P.init) {
-            solve_and_move27(P, D, B, p);
             if (__ldcg(P.status) & ST_NAN) s_ok = 0;
         } else {
             inertia27(D->q, D->Ib, D->Iprev);      // I(t - 1) = I(t) before the first step
@@ -534,35 +582,39 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
     }
     if (nsol) atomicAdd(&s_nsol, nsol);
     __syncthreads();
-    // ---- links of the new map, summed per direction in integers
-    for (int r = tid; r < S * S; r += PBLK) {
-        const int my = r % S, mz = r / S;
-        const uint64_t fluid = ~s_map[r] & full;
+    // ---- links of the new map, summed per direction in integers: the warp's
+    // lanes walk their rows in step, each (row, direction) a bit mask of the
+    // fluid ends, summed over the warp and added once per warp and value
+    for (int r0 = 0; r0 < S * S; r0 += PBLK) {
+        const int r = r0 + tid;
+        const bool has = r < S * S;
+        const int my = has ? r % S : 0, mz = has ? r / S : 0;
+        const uint64_t fluid = has ? (~s_map[r] & full) : 0ull;
 #pragma unroll
         for (int b = 1; b < Q27; ++b) {
-            const int ny_ = my + cy27(b), nz_ = mz + cz27(b);
-            if (ny_ < 0 || nz_ < 0 || ny_ >= S || nz_ >= S) continue;
-            const uint64_t nb = s_map[nz_ * S + ny_];
-            const uint64_t sol = cx27(b) == 1 ? (nb >> 1) : (cx27(b) == -1 ? (nb << 1) : nb);
-            uint64_t links = fluid & sol & full;
-            if (!links) continue;
             int n = 0, sx = 0, sxx = 0;
-            while (links) {
-                const int mx = __ffsll((long long)links) - 1;
-                links &= links - 1;
-                ++n; sx += mx; sxx += mx * mx;
+            const int ny_ = my + cy27(b), nz_ = mz + cz27(b);
+            if (fluid && ny_ >= 0 && nz_ >= 0 && ny_ < S && nz_ < S) {
+                const uint64_t nb = s_map[nz_ * S + ny_];
+                const uint64_t sol = cx27(b) == 1 ? (nb >> 1) : (cx27(b) == -1 ? (nb << 1) : nb);
+                uint64_t links = fluid & sol & full;
+                n = __popcll(links);
+                while (links) {
+                    const int mx = __ffsll((long long)links) - 1;
+                    links &= links - 1;
+                    sx += mx; sxx += mx * mx;
+                }
             }
-            int* t = s_sum[b];
-            atomicAdd(t + 0, n);
-            atomicAdd(t + 1, sx);
-            atomicAdd(t + 2, n * my);
-            atomicAdd(t + 3, n * mz);
-            atomicAdd(t + 4, sxx);
-            atomicAdd(t + 5, sx * my);
-            atomicAdd(t + 6, sx * mz);
-            atomicAdd(t + 7, n * my * my);
-            atomicAdd(t + 8, n * my * mz);
-            atomicAdd(t + 9, n * mz * mz);
+            if (__any_sync(0xffffffffu, n != 0)) {
+                const unsigned v[NSUM] = {(unsigned)n, (unsigned)sx, (unsigned)(n * my), (unsigned)(n * mz),
+                                          (unsigned)sxx, (unsigned)(sx * my), (unsigned)(sx * mz),
+                                          (unsigned)(n * my * my), (unsigned)(n * my * mz), (unsigned)(n * mz * mz)};
+#pragma unroll
+                for (int k = 0; k < NSUM; ++k) {
+                    const unsigned t = __reduce_add_sync(0xffffffffu, v[k]);
+                    if ((tid & 31) == 0 && t) atomicAdd(&s_sum[b][k], (int)t);
+                }
+            }
         }
     }
     // the map into its global slot (the lattice kernel and the read-back use it)
@@ -614,16 +666,15 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
         double v = 0.0;
         for (int b = 1; b < Q27; ++b) v += s_con[b][tid];
         s_con[0][tid] = v;
+        if (tid < 36) D->zeta[tid] = v;
     }
     __syncthreads();
     if (tid == 0) {
-        double Z6[36], F0g[3], T0g[3];
-        for (int k = 0; k < 36; ++k) Z6[k] = s_con[0][k];
+        double F0g[3], T0g[3];
         for (int i = 0; i < 3; ++i) {
             F0g[i] = s_con[0][36 + i];
             T0g[i] = s_con[0][39 + i];
         }
-        for (int k = 0; k < 36; ++k) D->zeta[k] = Z6[k];
         const int ns = s_nsol;
         Dyn27& Y = P.dyn[D->box];
         for (int i = 0; i < 3; ++i) {
@@ -633,6 +684,12 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
             const int Lk = i == 0 ? B.nx : (i == 1 ? B.ny : B.nz);
             Y.phi_old[i] = P.init ? (float)s_phi[i] : (float)D->phi[i];
             Y.o_old[i] = P.init ? s_ow[i] : ((D->o[i] % Lk) + Lk) % Lk;
+            // the box that holds both cubes (the near pass covers its nodes)
+            const int lo = P.init ? s_o[i] : min(D->o[i], s_o[i]);
+            const int hi = (P.init ? s_o[i] : max(D->o[i], s_o[i])) + S;
+            Y.E[i] = min(hi - lo, Lk);
+            Y.uo[i] = ((lo % Lk) + Lk) % Lk;
+            if (!P.init && abs(s_o[i] - D->o[i]) > 1) atomicOr(P.status, ST_CAPACITY);
             Y.phi_new[i] = (float)s_phi[i];
             Y.o_new[i] = s_ow[i];
             Y.U[i] = (float)D->U[i];

@@ -81,6 +81,7 @@ struct Dyn27 {
     int o_old[3], o_new[3];         // cube origins wrapped into the box
     float U[3], W[3];               // velocities of the last solve (bounce-back and uncovered nodes)
     float phi_old[3], phi_new[3];   // cube origin - particle centre, old and new pose
+    int uo[3], E[3];                // the box that holds both cubes: wrapped origin and extents
 };
 
 // per particle, FP64, read and written by the particle kernel only
@@ -98,15 +99,23 @@ struct Part27 {
     int pad;
 };
 
+// lattice pass modes: every node; every node outside the particles' cube
+// unions (bulk); the nodes of the cube unions only (near: block b takes
+// particle b / nbpp)
+enum { LAT_ALL = 0, LAT_BULK = 1, LAT_NEAR = 2 };
+
 struct LatParams27 {
     const Box27* boxes;
     const Dyn27* dyn;
+    const Part27* pd;               // LAT_NEAR: the box of each particle
     const int* blk_box;             // box of every lattice block
     const uint64_t* rows;           // [np][2][64*64] occupancy bitmaps
     long long* acc;                 // [np][24] integer link and remap sums
     const float* src;               // post-collision deviations of t-1 (first: the initial field)
     float* dst;
     int first;                      // 1: collide the stored field, no streaming
+    int mode;                       // LAT_ALL, LAT_BULK or LAT_NEAR
+    int nbpp;                       // LAT_NEAR: blocks per particle (covering (S + 1)^3 nodes)
 };
 
 struct PartParams27 {
