@@ -296,11 +296,21 @@ __device__ __forceinline__ void qmul27(const double a[4], const double b[4], dou
 
 // q' = qt q, qt the rotation by the angle |W| about W (Eq. qnplus0-1; no
 // rotation for W = 0)
+// For |W| < 0.01 (a step's rotation, always in practice) cos(n/2) and
+// sin(n/2)/n come from their Taylor series in n^2, 1 - n^2/8 + n^4/384 and
+// 1/2 - n^2/48 + n^4/3840: the next terms (n^6/46080, n^6/645120) lie below
+// the FP64 rounding of the results, and no square root or trigonometric
+// function is evaluated.
 __device__ __forceinline__ void qstep27(const double q[4], const double W[3], double o[4])
 {
-    const double n = sqrt(W[0] * W[0] + W[1] * W[1] + W[2] * W[2]);
+    const double n2 = W[0] * W[0] + W[1] * W[1] + W[2] * W[2];
     double t[4] = {1.0, 0.0, 0.0, 0.0};
-    if (n >= 1e-300) {
+    if (n2 < 1e-4) {
+        const double s = 0.5 - n2 * (1.0 / 48.0 - n2 * (1.0 / 3840.0));
+        t[0] = 1.0 - n2 * (0.125 - n2 * (1.0 / 384.0));
+        t[1] = s * W[0]; t[2] = s * W[1]; t[3] = s * W[2];
+    } else {
+        const double n = sqrt(n2);
         const double s = sin(0.5 * n) / n;
         t[0] = cos(0.5 * n);
         t[1] = s * W[0]; t[2] = s * W[1]; t[3] = s * W[2];
@@ -480,10 +490,16 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
     const Box27 B = P.boxes[D->box];
     __shared__ uint64_t s_map[MAXS * MAXS];
     __shared__ int s_sum[Q27][NSUM];
-    __shared__ double s_con[Q27][42];            // per direction: drag matrix (36), F0g (3), T0g (3)
+    constexpr int NG = PBLK / (Q27 - 1);         // row groups of the link sums (one direction per thread)
+    // per direction: drag matrix (36), F0g (3), T0g (3); before that, the link
+    // sums of each row group (the two are not used at the same time)
+    __shared__ double s_scratch[(NG * Q27 * NSUM * 4 > Q27 * 42 * 8 ? NG * Q27 * NSUM * 4 : Q27 * 42 * 8) / 8 + 1];
+    double (*s_con)[42] = reinterpret_cast<double (*)[42]>(s_scratch);
+    int (*s_part)[Q27][NSUM] = reinterpret_cast<int (*)[Q27][NSUM]>(s_scratch);
     __shared__ double s_A[9], s_x[3], s_phi[3];
     __shared__ float s_A32[9], s_d0[3];
     __shared__ int s_o[3], s_ow[3], s_S, s_slot, s_ok, s_nsol;
+    __shared__ float s_band;
     if (!P.init) {
         __shared__ double s_F0[3], s_T0[3], s_In[9], s_dI[9], s_A6[36], s_rhs[6], s_x6[6];
         __shared__ int s_solved;
@@ -547,9 +563,22 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
         s_S = D->S;
         s_slot = P.init ? 0 : 1 - D->slot;
         s_nsol = 0;
-        double e[3][3];
-        canon_shape(D->semi, D->q, s_A, e);
-        for (int k = 0; k < 9; ++k) s_A32[k] = (float)s_A[k];
+        // FP32 decides a node when its inside value is farther than this from
+        // 1: the FP32 rounding of the row quadratic near the surface grows with
+        // the squared aspect ratio (the terms that cancel) and with 1 / the
+        // short semi-axis (the gradient times the coordinate's rounding)
+        const double amax = fmax(D->semi[0], fmax(D->semi[1], D->semi[2]));
+        const double amin = fmin(D->semi[0], fmin(D->semi[1], D->semi[2]));
+        s_band = (float)(1e-4 * (1.0 + 0.25 * (amax / amin) * (amax / amin) + 1.0 / amin));
+    }
+    __syncwarp();
+    if (tid < 32) {
+        // the exact inside-test matrix of the new orientation (lanes 0..8)
+        __shared__ double s_inv[3], s_E[9];
+        if (tid < 3) s_inv[tid] = __ddiv_rn(1.0, __dmul_rn(D->semi[tid], D->semi[tid]));
+        __syncwarp();
+        canon_shape_warp(s_inv, D->q, s_E, s_A, tid);
+        if (tid < 9) s_A32[tid] = (float)s_A[tid];
     }
     for (int k = tid; k < Q27 * NSUM; k += PBLK) (&s_sum[0][0])[k] = 0;
     __syncthreads();
@@ -569,7 +598,7 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
             const float dx = s_d0[0] + (float)mx;
             const float v = (qa * dx + qb) * dx + qc;
             bool in;
-            if (fabsf(v - 1.0f) > 1e-3f) {
+            if (fabsf(v - 1.0f) > s_band) {
                 in = v < 1.0f;
             } else {
                 const int X = wrapc(s_ow[0] + mx, B.nx);
@@ -582,40 +611,56 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
     }
     if (nsol) atomicAdd(&s_nsol, nsol);
     __syncthreads();
-    // ---- links of the new map, summed per direction in integers: the warp's
-    // lanes walk their rows in step, each (row, direction) a bit mask of the
-    // fluid ends, summed over the warp and added once per warp and value
-    for (int r0 = 0; r0 < S * S; r0 += PBLK) {
-        const int r = r0 + tid;
-        const bool has = r < S * S;
-        const int my = has ? r % S : 0, mz = has ? r / S : 0;
-        const uint64_t fluid = has ? (~s_map[r] & full) : 0ull;
+    // ---- links of the new map, summed per direction in integers: thread t
+    // takes direction 1 + t % 26 over the rows g, g + NG, ... (g = t / 26); the
+    // sums of x and x^2 over a row's link bits come from popcounts of the masks
+    // of bit positions whose bit p is set (x = sum_p 2^p [bit p of x])
+    {
+        const int b = 1 + tid % (Q27 - 1), g = tid / (Q27 - 1);
+        int t[NSUM];
 #pragma unroll
-        for (int b = 1; b < Q27; ++b) {
-            int n = 0, sx = 0, sxx = 0;
-            const int ny_ = my + cy27(b), nz_ = mz + cz27(b);
-            if (fluid && ny_ >= 0 && nz_ >= 0 && ny_ < S && nz_ < S) {
-                const uint64_t nb = s_map[nz_ * S + ny_];
-                const uint64_t sol = cx27(b) == 1 ? (nb >> 1) : (cx27(b) == -1 ? (nb << 1) : nb);
-                uint64_t links = fluid & sol & full;
-                n = __popcll(links);
-                while (links) {
-                    const int mx = __ffsll((long long)links) - 1;
-                    links &= links - 1;
-                    sx += mx; sxx += mx * mx;
-                }
-            }
-            if (__any_sync(0xffffffffu, n != 0)) {
-                const unsigned v[NSUM] = {(unsigned)n, (unsigned)sx, (unsigned)(n * my), (unsigned)(n * mz),
-                                          (unsigned)sxx, (unsigned)(sx * my), (unsigned)(sx * mz),
-                                          (unsigned)(n * my * my), (unsigned)(n * my * mz), (unsigned)(n * mz * mz)};
+        for (int k = 0; k < NSUM; ++k) t[k] = 0;
+        if (g < NG) {
+            const int cx = cx27(b), cy = cy27(b), cz = cz27(b);
+            const uint64_t M[6] = {0xAAAAAAAAAAAAAAAAull, 0xCCCCCCCCCCCCCCCCull, 0xF0F0F0F0F0F0F0F0ull,
+                                   0xFF00FF00FF00FF00ull, 0xFFFF0000FFFF0000ull, 0xFFFFFFFF00000000ull};
+            int my = g % S, mz = g / S;
+            for (int r = g; r < S * S; r += NG) {
+                const int ny_ = my + cy, nz_ = mz + cz;
+                if (ny_ >= 0 && nz_ >= 0 && ny_ < S && nz_ < S) {
+                    const uint64_t nb = s_map[nz_ * S + ny_];
+                    const uint64_t sol = cx == 1 ? (nb >> 1) : (cx == -1 ? (nb << 1) : nb);
+                    const uint64_t L = ~s_map[r] & sol & full;
+                    if (L) {
+                        const int n = __popcll(L);
+                        int pc[6], sx = 0, sxx = 0;
 #pragma unroll
-                for (int k = 0; k < NSUM; ++k) {
-                    const unsigned t = __reduce_add_sync(0xffffffffu, v[k]);
-                    if ((tid & 31) == 0 && t) atomicAdd(&s_sum[b][k], (int)t);
+                        for (int q = 0; q < 6; ++q) {
+                            pc[q] = __popcll(L & M[q]);
+                            sx += pc[q] << q;
+                            sxx += pc[q] << (2 * q);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 6; ++q)
+#pragma unroll
+                            for (int q2 = q + 1; q2 < 6; ++q2) sxx += __popcll(L & M[q] & M[q2]) << (q + q2 + 1);
+                        t[0] += n; t[1] += sx; t[2] += n * my; t[3] += n * mz; t[4] += sxx;
+                        t[5] += sx * my; t[6] += sx * mz; t[7] += n * my * my; t[8] += n * my * mz; t[9] += n * mz * mz;
+                    }
                 }
+                my += NG;
+                while (my >= S) { my -= S; ++mz; }
             }
+#pragma unroll
+            for (int k = 0; k < NSUM; ++k) s_part[g][b][k] = t[k];
         }
+    }
+    __syncthreads();
+    for (int e = tid; e < (Q27 - 1) * NSUM; e += PBLK) {
+        const int b = 1 + e / NSUM, k = e % NSUM;
+        int v = 0;
+        for (int g = 0; g < NG; ++g) v += s_part[g][b][k];
+        s_sum[b][k] = v;
     }
     // the map into its global slot (the lattice kernel and the read-back use it)
     uint64_t* map = P.rows + ((size_t)p * 2 + s_slot) * RW;
