@@ -334,6 +334,15 @@ static lb_status q27_set_particles(lb_ctx* ctx, int box, const lb_particle* p, i
         D.Ib[0] = D.M * (bb * bb + c * c) / 5.0;               // Sec. II.D
         D.Ib[1] = D.M * (a * a + c * c) / 5.0;
         D.Ib[2] = D.M * (a * a + bb * bb) / 5.0;
+        for (int k = 0; k < 3; ++k) D.inv2[k] = 1.0 / (P.semi[k] * P.semi[k]);   // IEEE: as the device rounds it
+        // FP32 decides a node of the map when its inside value is farther than
+        // this from 1: the FP32 rounding of the row quadratic near the surface
+        // grows with the squared aspect ratio (the terms that cancel) and with
+        // 1 / the short semi-axis (the gradient times the coordinate's rounding)
+        {
+            const double amax = std::max(a, std::max(bb, c)), amin = std::min(a, std::min(bb, c));
+            D.band = (float)(1e-4 * (1.0 + 0.25 * (amax / amin) * (amax / amin) + 1.0 / amin));
+        }
         D.h = (int)std::ceil(std::max(a, std::max(bb, c))) + CUBE_MARGIN;
         D.S = 2 * D.h + 2;
         D.box = b;

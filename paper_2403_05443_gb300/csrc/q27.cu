@@ -355,8 +355,8 @@ __device__ __forceinline__ void cross27(const double a[3], const double b[3], do
 // spread over the block: q27_sums (one thread) turns the integer sums of the
 // last lattice pass into F0, T0 and the remap terms; the inertia and its rate
 // come from another warp at the same time; a warp solves the 6 x 6 system
-// (Gauss-Jordan, partial pivoting, one column per lane); q27_finish (one
-// thread) forms F and T and moves the particle.
+// (Gauss-Jordan, partial pivoting, one column per lane); six threads form F
+// and T; q27_finish (one thread) moves the particle and writes its record.
 __device__ void q27_sums(const PartParams27& P, Part27* D, const Box27& B, int p, double F0[3], double T0[3])
 {
     long long* acc = P.acc + (size_t)p * NACC;
@@ -385,6 +385,11 @@ __device__ void q27_sums(const PartParams27& P, Part27* D, const Box27& B, int p
     // remap terms (Appendix step 8): covered nodes give their momentum and its
     // moment about x_c; uncovered ones take rho0 (U + W x r), r = phi + m
     const double nc = a[ACC_COV], nu = a[ACC_UNC];
+    if (nc == 0.0 && nu == 0.0) {              // most steps: no node changed sides
+        for (int k = 0; k < 3; ++k) D->dP[k] = D->dL[k] = 0.0;
+        D->dm = 0.0;
+        return;
+    }
     const double Smm[9] = {a[ACC_UNC + 4], a[ACC_UNC + 5], a[ACC_UNC + 6], a[ACC_UNC + 5], a[ACC_UNC + 7],
                            a[ACC_UNC + 8], a[ACC_UNC + 6], a[ACC_UNC + 8], a[ACC_UNC + 9]};
     double Sr[3], Srr[9];
@@ -404,22 +409,6 @@ __device__ void q27_sums(const PartParams27& P, Part27* D, const Box27& B, int p
     D->dm = nc * rho0 + a[ACC_COV + 1] / FIXD - nu * rho0;
 }
 
-// the system of Eq. Fdiscrete / Eq. Tdiscrete: A = zeta + diag(M) + (I + dI)
-// in the rotational block, rhs = (M U + F0 + F_ext + dP, I W + T0 + T_ext + dL)
-__device__ void q27_system(const Part27* D, const double In[9], const double dI[9], const double F0[3],
-                           const double T0[3], double A6[36], double rhs[6])
-{
-    for (int k = 0; k < 36; ++k) A6[k] = D->zeta[k];
-    for (int k = 0; k < 3; ++k) A6[k * 6 + k] += D->M;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) A6[(i + 3) * 6 + j + 3] += In[i * 3 + j] + dI[i * 3 + j];
-    for (int k = 0; k < 3; ++k) {
-        rhs[k] = D->M * D->U[k] + F0[k] + D->Fext[k] + D->dP[k];
-        rhs[k + 3] = In[k * 3] * D->W[0] + In[k * 3 + 1] * D->W[1] + In[k * 3 + 2] * D->W[2] + T0[k] + D->Text[k] +
-                     D->dL[k];
-    }
-}
-
 // one warp: x = A^-1 rhs (lane 6 holds the result); false if a pivot vanishes
 __device__ __forceinline__ bool q27_warp_solve(const double A6[36], const double rhs[6], double x6[6], int lane)
 {
@@ -432,20 +421,10 @@ __device__ __forceinline__ bool q27_warp_solve(const double A6[36], const double
 }
 
 __device__ void q27_finish(const PartParams27& P, Part27* D, const double In[9], const double x6[6],
-                           const double F0[3], const double T0[3])
+                           const double F0[3], const double T0[3], const double FT[6])
 {
-    double F[3], T[3];
-    for (int k = 0; k < 3; ++k) {
-        double zu = 0.0, zw = 0.0, tu = 0.0, tw = 0.0;
-        for (int j = 0; j < 3; ++j) {
-            zu += D->zeta[k * 6 + j] * x6[j];
-            zw += D->zeta[k * 6 + j + 3] * x6[j + 3];
-            tu += D->zeta[(k + 3) * 6 + j] * x6[j];
-            tw += D->zeta[(k + 3) * 6 + j + 3] * x6[j + 3];
-        }
-        F[k] = F0[k] - zu - zw;
-        T[k] = T0[k] - tu - tw;
-    }
+    const double* F = FT;
+    const double* T = FT + 3;
     for (int k = 0; k < 9; ++k) D->Iprev[k] = In[k];
     // Eq. posupdate and Eq. qnplus0-1 with the mean velocities of the step
     double Wm[3], qn[4];
@@ -514,7 +493,24 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
             }
         }
         __syncthreads();
-        if (tid == 0) q27_system(D, s_In, s_dI, s_F0, s_T0, s_A6, s_rhs);
+        if (tid < 36) {
+            // A = zeta + diag(M) + (I + dI) in the rotational block
+            const int i = tid / 6, j = tid % 6;
+            double a = D->zeta[tid];
+            if (i == j && i < 3) a += D->M;
+            if (i >= 3 && j >= 3) a += s_In[(i - 3) * 3 + j - 3] + s_dI[(i - 3) * 3 + j - 3];
+            s_A6[tid] = a;
+        } else if (tid >= 64 && tid < 70) {
+            // rhs = (M U + F0 + F_ext + dP, I W + T0 + T_ext + dL)
+            const int k = tid - 64;
+            if (k < 3) {
+                s_rhs[k] = D->M * D->U[k] + s_F0[k] + D->Fext[k] + D->dP[k];
+            } else {
+                const int m = k - 3;
+                s_rhs[k] = s_In[m * 3] * D->W[0] + s_In[m * 3 + 1] * D->W[1] + s_In[m * 3 + 2] * D->W[2] + s_T0[m] +
+                           D->Text[m] + D->dL[m];
+            }
+        }
         __syncthreads();
         if (tid < 32) {
             const bool ok = q27_warp_solve(s_A6, s_rhs, s_x6, tid);
@@ -538,9 +534,17 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
             }
             __syncthreads();
         }
+        // F = F0 - zeta_F (U', W'), T = T0 - zeta_T (U', W'), one component per thread
+        __shared__ double s_FT[6];
+        if (tid < 6) {
+            double z = 0.0;
+            for (int j = 0; j < 6; ++j) z += D->zeta[tid * 6 + j] * s_x6[j];
+            s_FT[tid] = (tid < 3 ? s_F0[tid] : s_T0[tid - 3]) - z;
+        }
+        __syncthreads();
         if (tid == 0) {
             if (!s_solved) atomicOr(P.status, ST_NAN);
-            else q27_finish(P, D, s_In, s_x6, s_F0, s_T0);
+            else q27_finish(P, D, s_In, s_x6, s_F0, s_T0, s_FT);
         }
     }
     if (tid == 0) {
@@ -563,21 +567,13 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
         s_S = D->S;
         s_slot = P.init ? 0 : 1 - D->slot;
         s_nsol = 0;
-        // FP32 decides a node when its inside value is farther than this from
-        // 1: the FP32 rounding of the row quadratic near the surface grows with
-        // the squared aspect ratio (the terms that cancel) and with 1 / the
-        // short semi-axis (the gradient times the coordinate's rounding)
-        const double amax = fmax(D->semi[0], fmax(D->semi[1], D->semi[2]));
-        const double amin = fmin(D->semi[0], fmin(D->semi[1], D->semi[2]));
-        s_band = (float)(1e-4 * (1.0 + 0.25 * (amax / amin) * (amax / amin) + 1.0 / amin));
+        s_band = D->band;                          // the FP32 decision band of the map (set on the host)
     }
     __syncwarp();
     if (tid < 32) {
         // the exact inside-test matrix of the new orientation (lanes 0..8)
-        __shared__ double s_inv[3], s_E[9];
-        if (tid < 3) s_inv[tid] = __ddiv_rn(1.0, __dmul_rn(D->semi[tid], D->semi[tid]));
-        __syncwarp();
-        canon_shape_warp(s_inv, D->q, s_E, s_A, tid);
+        __shared__ double s_E[9];
+        canon_shape_warp(D->inv2, D->q, s_E, s_A, tid);
         if (tid < 9) s_A32[tid] = (float)s_A[tid];
     }
     for (int k = tid; k < Q27 * NSUM; k += PBLK) (&s_sum[0][0])[k] = 0;
@@ -666,10 +662,12 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
     uint64_t* map = P.rows + ((size_t)p * 2 + s_slot) * RW;
     for (int r = tid; r < S * S; r += PBLK) map[r] = s_map[r];
     __syncthreads();
-    // each direction's share of the drag matrix and of F0g / T0g (thread b),
-    // then every entry summed over the directions in order (threads 0..56)
-    if (tid >= 1 && tid < Q27) {
-        const int b = tid;
+    // each direction's share of the drag matrix and of F0g / T0g: thread b the
+    // translational and mixed blocks, thread 32 + b (another warp) the
+    // rotational block; then every entry summed over the directions in order
+    if ((tid >= 1 && tid < Q27) || (tid >= 33 && tid < 32 + Q27)) {
+        const int b = tid & 31;
+        const bool rot = tid >= 32;
         const double rho0 = B.rho0;
         const double* phi = s_phi;
         double* out = s_con[b];
@@ -677,33 +675,37 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
         const double n = t[0];
         const double c[3] = {(double)cx27(b), (double)cy27(b), (double)cz27(b)};
         const double Sm[3] = {(double)t[1], (double)t[2], (double)t[3]};
-        const double Qm[9] = {(double)t[4], (double)t[5], (double)t[6], (double)t[5], (double)t[7],
-                              (double)t[8], (double)t[6], (double)t[8], (double)t[9]};
-        // sums over the direction's links of p = phi + m and p p^T
-        double Pb[3], PP[9];
-        for (int i = 0; i < 3; ++i) Pb[i] = n * phi[i] + Sm[i];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j)
-                PP[i * 3 + j] = n * phi[i] * phi[j] + phi[i] * Sm[j] + Sm[i] * phi[j] + Qm[i * 3 + j];
-        // p x c = K p, K = -[c]x
+        // p x c = K p, K = -[c]x, p = phi + m over the direction's links
         const double K[9] = {0.0, c[2], -c[1], -c[2], 0.0, c[0], c[1], -c[0], 0.0};
-        double KP[3], KPP[9];
-        for (int i = 0; i < 3; ++i) KP[i] = K[i * 3] * Pb[0] + K[i * 3 + 1] * Pb[1] + K[i * 3 + 2] * Pb[2];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j)
-                KPP[i * 3 + j] = K[i * 3] * PP[j] + K[i * 3 + 1] * PP[3 + j] + K[i * 3 + 2] * PP[6 + j];
         const double wz = 6.0 * rho0 * wd27(b);        // 2 rho0 w_b / c_s^2
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) {
-                out[i * 6 + j] = wz * n * c[i] * c[j];
-                out[i * 6 + j + 3] = wz * c[i] * KP[j];
-                out[(i + 3) * 6 + j] = wz * KP[i] * c[j];
-                out[(i + 3) * 6 + j + 3] =
-                    wz * (KPP[i * 3] * K[j * 3] + KPP[i * 3 + 1] * K[j * 3 + 1] + KPP[i * 3 + 2] * K[j * 3 + 2]);
+        if (!rot) {
+            double Pb[3], KP[3];
+            for (int i = 0; i < 3; ++i) Pb[i] = n * phi[i] + Sm[i];
+            for (int i = 0; i < 3; ++i) KP[i] = K[i * 3] * Pb[0] + K[i * 3 + 1] * Pb[1] + K[i * 3 + 2] * Pb[2];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    out[i * 6 + j] = wz * n * c[i] * c[j];
+                    out[i * 6 + j + 3] = wz * c[i] * KP[j];
+                    out[(i + 3) * 6 + j] = wz * KP[i] * c[j];
+                }
+            for (int i = 0; i < 3; ++i) {
+                out[36 + i] = 2.0 * rho0 * wd27(b) * n * c[i];
+                out[39 + i] = 2.0 * rho0 * wd27(b) * KP[i];
             }
-        for (int i = 0; i < 3; ++i) {
-            out[36 + i] = 2.0 * rho0 * wd27(b) * n * c[i];
-            out[39 + i] = 2.0 * rho0 * wd27(b) * KP[i];
+        } else {
+            const double Qm[9] = {(double)t[4], (double)t[5], (double)t[6], (double)t[5], (double)t[7],
+                                  (double)t[8], (double)t[6], (double)t[8], (double)t[9]};
+            double PP[9], KPP[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    PP[i * 3 + j] = n * phi[i] * phi[j] + phi[i] * Sm[j] + Sm[i] * phi[j] + Qm[i * 3 + j];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    KPP[i * 3 + j] = K[i * 3] * PP[j] + K[i * 3 + 1] * PP[3 + j] + K[i * 3 + 2] * PP[6 + j];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    out[(i + 3) * 6 + j + 3] =
+                        wz * (KPP[i * 3] * K[j * 3] + KPP[i * 3 + 1] * K[j * 3 + 1] + KPP[i * 3 + 2] * K[j * 3 + 2]);
         }
     }
     __syncthreads();
@@ -714,48 +716,43 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
         if (tid < 36) D->zeta[tid] = v;
     }
     __syncthreads();
-    if (tid == 0) {
-        double F0g[3], T0g[3];
-        for (int i = 0; i < 3; ++i) {
-            F0g[i] = s_con[0][36 + i];
-            T0g[i] = s_con[0][39 + i];
-        }
+    // the new state, one thread per axis (thread 0 also the scalars)
+    if (tid < 3) {
+        const int i = tid;
         const int ns = s_nsol;
         Dyn27& Y = P.dyn[D->box];
-        for (int i = 0; i < 3; ++i) {
-            D->F0g[i] = F0g[i];
-            D->T0g[i] = T0g[i];
-            // the map the next pass bounces back from is the current one
-            const int Lk = i == 0 ? B.nx : (i == 1 ? B.ny : B.nz);
-            Y.phi_old[i] = P.init ? (float)s_phi[i] : (float)D->phi[i];
-            Y.o_old[i] = P.init ? s_ow[i] : ((D->o[i] % Lk) + Lk) % Lk;
-            // the box that holds both cubes (the near pass covers its nodes)
-            const int lo = P.init ? s_o[i] : min(D->o[i], s_o[i]);
-            const int hi = (P.init ? s_o[i] : max(D->o[i], s_o[i])) + S;
-            Y.E[i] = min(hi - lo, Lk);
-            Y.uo[i] = ((lo % Lk) + Lk) % Lk;
-            if (!P.init && abs(s_o[i] - D->o[i]) > 1) atomicOr(P.status, ST_CAPACITY);
-            Y.phi_new[i] = (float)s_phi[i];
-            Y.o_new[i] = s_ow[i];
-            Y.U[i] = (float)D->U[i];
-            Y.W[i] = (float)D->W[i];
-        }
-        Y.slot_old = P.init ? s_slot : D->slot;
-        Y.slot_new = s_slot;
-        Y.S = S;
-        Y.active = 1;
-        for (int i = 0; i < 3; ++i) {
-            D->phi[i] = s_phi[i];
-            D->o[i] = s_o[i];
-        }
-        D->slot = s_slot;
-        D->nsolid = ns;
+        D->F0g[i] = s_con[0][36 + i];
+        D->T0g[i] = s_con[0][39 + i];
+        // the map the next pass bounces back from is the current one
+        const int Lk = i == 0 ? B.nx : (i == 1 ? B.ny : B.nz);
+        Y.phi_old[i] = P.init ? (float)s_phi[i] : (float)D->phi[i];
+        Y.o_old[i] = P.init ? s_ow[i] : ((D->o[i] % Lk) + Lk) % Lk;
+        // the box that holds both cubes (the near pass covers its nodes)
+        const int lo = P.init ? s_o[i] : min(D->o[i], s_o[i]);
+        const int hi = (P.init ? s_o[i] : max(D->o[i], s_o[i])) + S;
+        Y.E[i] = min(hi - lo, Lk);
+        Y.uo[i] = ((lo % Lk) + Lk) % Lk;
+        if (!P.init && abs(s_o[i] - D->o[i]) > 1) atomicOr(P.status, ST_CAPACITY);
+        Y.phi_new[i] = (float)s_phi[i];
+        Y.o_new[i] = s_ow[i];
+        Y.U[i] = (float)D->U[i];
+        Y.W[i] = (float)D->W[i];
+        D->phi[i] = s_phi[i];
+        D->o[i] = s_o[i];
         // uniform terms of the next collision: body force (with the counter
         // force on the fluid nodes of the new map) and the mass of this remap,
         // returned over every fluid node
-        const double nf = (double)(B.N - ns);
-        for (int i = 0; i < 3; ++i) Y.g[i] = (float)(B.body[i] - (B.counter ? D->Fext[i] / nf : 0.0));
-        Y.eps = P.init ? 0.0f : (float)(D->dm / nf);
+        const double inf = 1.0 / (double)(B.N - ns);
+        Y.g[i] = (float)(B.body[i] - (B.counter ? D->Fext[i] * inf : 0.0));
+        if (i == 0) {
+            Y.slot_old = P.init ? s_slot : D->slot;
+            Y.slot_new = s_slot;
+            Y.S = S;
+            Y.active = 1;
+            D->slot = s_slot;
+            D->nsolid = ns;
+            Y.eps = P.init ? 0.0f : (float)(D->dm * inf);
+        }
     }
 }
 

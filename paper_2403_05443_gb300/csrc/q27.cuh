@@ -89,6 +89,9 @@ struct Part27 {
     double semi[3], M, Ib[3], Fext[3], Text[3];
     double x[3], q[4], U[3], W[3];  // at time t
     double Iprev[9];                // lab inertia of the last solve (finite-difference rate)
+    double inv2[3];                 // 1 / semi^2, rounded as the exact inside test rounds it
+    float band;                     // FP32 decides a node farther than this from the surface value 1
+    float fpad;
     double zeta[36];                // drag matrix of the links of the current map (Eq. drag1-4)
     double F0g[3], T0g[3];          // 2 rho0 sum w_b c_b and 2 rho0 sum w_b r_b x c_b over those links
     double phi[3];                  // cube origin - x of the current map
