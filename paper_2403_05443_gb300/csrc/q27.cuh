@@ -1,22 +1,24 @@
 // D3Q27 path: the 27-velocity lattice the paper compares D3Q19 with
 // (Sec. III.A), for periodic boxes holding at most one passive spheroid each,
-// FP32 deviation storage and BGK with Guo forcing.  Two kernels per iteration
-// (q27.cu):
-//   lattice   every node: pull streaming of the last post-collision field
-//             with mid-link bounce-back on the old surface (Eq. fb, Eq. ub),
-//             the remap of covered / uncovered nodes to the new map
-//             (Appendix step 8), the collision (Appendix step 1) and the
-//             integer momentum-exchange sums of the new links (Eq. F0, T0);
+// FP32 deviation storage and BGK with Guo forcing (q27.cu):
+//   lattice   pull streaming of the last post-collision field with mid-link
+//             bounce-back on the old surface (Eq. fb, Eq. ub), the remap of
+//             covered / uncovered nodes to the new map (Appendix step 8), the
+//             collision (Appendix step 1) and the integer momentum-exchange
+//             sums of the new links (Eq. F0, T0); one pass over every node, or
+//             (after the first step) a near pass over the nodes of each
+//             particle's old and new cubes and a bulk pass over all others;
 //   particle  one block per particle: F0, T0 and the remap terms, the
 //             implicit solve (Eq. Fdiscrete, Tdiscrete), the pose update
 //             (Eq. posupdate, qnplus0-1), the new occupancy map (Eq.
-//             ellipsoidsurface, exact FP64 test) and the drag matrix of its
-//             links (Eq. drag1-4), and the box's uniform terms of the next
-//             collision.
+//             ellipsoidsurface, exact FP64 test near the surface) and the drag
+//             matrix of its links (Eq. drag1-4), and the box's uniform terms of
+//             the next collision.
 // The iteration is the oracle's Appendix order turned by half a step: a
 // lattice pass does the streaming, bounce-back and remap of iteration t-1 and
-// the collision of iteration t, so the particle solve of t-1 sits between two
-// lattice passes and every population is read and written once per step.
+// the collision of iteration t, so the particle solve sits between two lattice
+// passes and every population is read and written once per step.  The near
+// pass and the particle kernel run on their own stream beside the bulk pass.
 #pragma once
 
 #include <cstdint>
