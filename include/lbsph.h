@@ -126,7 +126,7 @@ typedef struct {
     int32_t collision;
     /* Lattice: 0 or 19 D3Q19; 27 D3Q27, the lattice the paper compares D3Q19
      * with (Sec. III.A: all 27 velocities of {-1,0,1}^3, weights 8/27, 2/27,
-     * 1/54, 1/216, c_s^2 = 1/3).  27 takes LB_FP32 storage, collision 0,
+     * 1/54, 1/216, c_s^2 = 1/3).  27 takes LB_FP32 storage, either collision,
      * periodic boxes (walls 0) and at most one passive particle per box (B1 =
      * B2 = 0); its distributions and fields have 27 planes in the order of
      * lb_lattice_q(27, ...).  With 27, lb_step_io, lb_get_force_torque_async,

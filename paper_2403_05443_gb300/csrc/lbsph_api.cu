@@ -214,7 +214,7 @@ extern "C" lb_status lb_lattice_q(int32_t q, int32_t* c, double* w)
 static lb_status q27_create(lb_ctx* ctx, const lb_box_desc* boxes, int nbox)
 {
     const lb_options& o = ctx->opt;
-    if (o.precision != LB_FP32 || o.collision != 0) return fail(ctx, LB_EINVAL, "D3Q27: FP32 storage and BGK only");
+    if (o.precision != LB_FP32) return fail(ctx, LB_EINVAL, "D3Q27: FP32 storage only");
     for (int b = 0; b < nbox; ++b)
         if (boxes[b].walls) return fail(ctx, LB_EINVAL, "D3Q27: periodic boxes only");
     ctx->lattice = 27;
@@ -390,7 +390,7 @@ static cudaError_t q27_enqueue(lb_ctx* ctx, int nsteps, cudaStream_t s)
         q27::Dyn27* dnext = ctx->d_dyn27 + (size_t)(ctx->dpar27 ^ 1) * nbox;
         q27::LatParams27 lp{ctx->d_box27, dcur, ctx->d_part27, ctx->d_blk27, ctx->d_rows, ctx->d_acc,
                             (const float*)ctx->fbuf[ctx->cur], (float*)ctx->fbuf[ctx->cur ^ 1], ctx->collided ? 0 : 1,
-                            q27::LAT_ALL, ctx->nbpp27};
+                            q27::LAT_ALL, ctx->nbpp27, ctx->opt.collision};
         q27::PartParams27 pp{ctx->d_part27, dnext, ctx->d_box27, ctx->d_rows, ctx->d_acc, ctx->d_status, 0,
                              ctx->opt.didt_mode};
         if (!ctx->collided || ctx->np == 0) {
@@ -468,7 +468,7 @@ extern "C" lb_status lb_create(const lb_box_desc* boxes, int32_t nbox, const lb_
     if (o.precision < 0 || o.precision > 2 || o.didt_mode < 0 || o.didt_mode > 2 || o.max_semi > 29 ||
         o.collision < 0 || o.collision > 1 || (o.collision == 1 && o.precision != LB_FP32) ||
         (o.lattice != 0 && o.lattice != 19 && o.lattice != 27) ||
-        (o.lattice == 27 && (o.precision != LB_FP32 || o.collision != 0)) ||
+        (o.lattice == 27 && o.precision != LB_FP32) ||
         (o.alloc && !o.release) || (!o.alloc && o.release))
         return bad("options");
     for (int b = 0; b < nbox; ++b) {

@@ -119,10 +119,22 @@ __device__ __forceinline__ int pre_collision(const Box27& B, const Dyn27& K, con
 }
 
 // BGK (Eq. 3-4) with Guo forcing on deviations, mass return eps added first
-// as w_i eps to every population
+// as w_i eps to every population.
+//
+// GHOST: the collision of the paper's simulations (Sec. II.A: one relaxation
+// time for the non-conserved hydrodynamic modes, the non-hydrodynamic ones
+// relaxed at once).  Of f - f_eq only the projection on the hydrodynamic
+// Hermite modes survives, relaxed by 1 - omega:
+//   d_i' = deq_i + (1 - omega) w_i [3 c_i.j_neq + 4.5 (c_i c_i - I/3) : Pi_neq] + S_i,
+// j_neq = j - rho u = -g/2 (u carries the half-force shift) and
+// Pi_neq = sum_i c_i c_i d_i - drho/3 I - rho u u (the rest state w rho0
+// contributes rho0/3 I, the equilibrium rho/3 I + rho u u).  The 18 modes of
+// D3Q27 beyond these ten leave at equilibrium.  At omega = 1 it is BGK.
+template <bool GHOST>
 __device__ __forceinline__ void collide27(float (&d)[Q27], float omega, float rho0, const float g[3], float eps)
 {
     float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q27; ++i) {
         d[i] += w27(i) * eps;
@@ -130,19 +142,54 @@ __device__ __forceinline__ void collide27(float (&d)[Q27], float omega, float rh
         jx += cx27(i) * d[i];
         jy += cy27(i) * d[i];
         jz += cz27(i) * d[i];
+        if constexpr (GHOST) {
+            const int cx = cx27(i), cy = cy27(i), cz = cz27(i);
+            if (cx) pxx += d[i];
+            if (cy) pyy += d[i];
+            if (cz) pzz += d[i];
+            if (cx * cy) pxy += (cx * cy) * d[i];
+            if (cx * cz) pxz += (cx * cz) * d[i];
+            if (cy * cz) pyz += (cy * cz) * d[i];
+        }
     }
     const float rho = rho0 + drho;
     const float ir = 1.0f / rho;
     const float ux = (jx + 0.5f * g[0]) * ir, uy = (jy + 0.5f * g[1]) * ir, uz = (jz + 0.5f * g[2]) * ir;
     const float uu = ux * ux + uy * uy + uz * uz, ug = ux * g[0] + uy * g[1] + uz * g[2];
     const float cf = 1.0f - 0.5f * omega;
+    if constexpr (GHOST) {
+        const float iso = -drho * (1.0f / 3.0f);
+        const float nxx = pxx + iso - rho * ux * ux, nyy = pyy + iso - rho * uy * uy, nzz = pzz + iso - rho * uz * uz;
+        const float nxy = pxy - rho * ux * uy, nxz = pxz - rho * ux * uz, nyz = pyz - rho * uy * uz;
+        const float tr3 = (nxx + nyy + nzz) * (1.0f / 3.0f);
+        const float om1 = 1.0f - omega;
+        const float jnx = -0.5f * g[0], jny = -0.5f * g[1], jnz = -0.5f * g[2];
 #pragma unroll
-    for (int i = 0; i < Q27; ++i) {
-        const float cu = cx27(i) * ux + cy27(i) * uy + cz27(i) * uz;
-        const float cg = cx27(i) * g[0] + cy27(i) * g[1] + cz27(i) * g[2];
-        const float deq = w27(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-        const float S = cf * w27(i) * (3.0f * (cg - ug) + 9.0f * cu * cg);
-        d[i] = d[i] - omega * (d[i] - deq) + S;
+        for (int i = 0; i < Q27; ++i) {
+            const int cx = cx27(i), cy = cy27(i), cz = cz27(i);
+            const float cu = cx * ux + cy * uy + cz * uz;
+            const float cg = cx * g[0] + cy * g[1] + cz * g[2];
+            const float deq = w27(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+            const float S = cf * w27(i) * (3.0f * (cg - ug) + 9.0f * cu * cg);
+            float qp = -tr3;
+            if (cx) qp += nxx;
+            if (cy) qp += nyy;
+            if (cz) qp += nzz;
+            if (cx * cy) qp += (2 * cx * cy) * nxy;
+            if (cx * cz) qp += (2 * cx * cz) * nxz;
+            if (cy * cz) qp += (2 * cy * cz) * nyz;
+            const float cj = cx * jnx + cy * jny + cz * jnz;
+            d[i] = deq + om1 * w27(i) * (3.0f * cj + 4.5f * qp) + S;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q27; ++i) {
+            const float cu = cx27(i) * ux + cy27(i) * uy + cz27(i) * uz;
+            const float cg = cx27(i) * g[0] + cy27(i) * g[1] + cz27(i) * g[2];
+            const float deq = w27(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+            const float S = cf * w27(i) * (3.0f * (cg - ug) + 9.0f * cu * cg);
+            d[i] = d[i] - omega * (d[i] - deq) + S;
+        }
     }
 }
 
@@ -160,6 +207,7 @@ __device__ __forceinline__ void acc_add(long long* a, long long v)
 
 // ---------------------------------------------------------------------------
 // One lattice pass over every node of every box (one node per thread).
+template <bool GHOST>
 __global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant__ LatParams27 P)
 {
     __shared__ Box27 sB;
@@ -246,7 +294,7 @@ __global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant
     }
     if (kind == K_FLUID || kind == K_UNCOVERED) {
         const float g[3] = {K.g[0], K.g[1], K.g[2]};
-        collide27(d, B.omega, B.rho0f, g, K.eps);
+        collide27<GHOST>(d, B.omega, B.rho0f, g, K.eps);
         if (in_new && valid) {
             const uint64_t* map_new = rows + (size_t)K.slot_new * RW;
 #pragma unroll
@@ -843,7 +891,10 @@ cudaError_t launch_refresh27(const Part27* pd, const Box27* boxes, Dyn27* dyn, i
 
 cudaError_t launch_lattice27(const LatParams27& p, int blocks, cudaStream_t s)
 {
-    lattice27_kernel<<<blocks, LBLOCK, 0, s>>>(p);
+    if (p.ghost)
+        lattice27_kernel<true><<<blocks, LBLOCK, 0, s>>>(p);
+    else
+        lattice27_kernel<false><<<blocks, LBLOCK, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // D3Q27 path: the 27-velocity lattice the paper compares D3Q19 with
 // (Sec. III.A), for periodic boxes holding at most one passive spheroid each,
-// FP32 deviation storage and BGK with Guo forcing (q27.cu):
+// FP32 deviation storage, BGK or the paper's ghost-mode collision, with Guo
+// forcing (q27.cu):
 //   lattice   pull streaming of the last post-collision field with mid-link
 //             bounce-back on the old surface (Eq. fb, Eq. ub), the remap of
 //             covered / uncovered nodes to the new map (Appendix step 8), the
@@ -121,6 +122,7 @@ struct LatParams27 {
     int first;                      // 1: collide the stored field, no streaming
     int mode;                       // LAT_ALL, LAT_BULK or LAT_NEAR
     int nbpp;                       // LAT_NEAR: blocks per particle (covering (S + 1)^3 nodes)
+    int ghost;                      // 1: the paper's ghost-mode collision, 0: BGK
 };
 
 struct PartParams27 {

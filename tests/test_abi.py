@@ -79,9 +79,11 @@ def test_lattice_tables_of_both_lattices():
 
 
 def test_create_rejects_bad_d3q27_options_without_touching_the_gpu():
-    """D3Q27 takes FP32 storage, BGK and periodic boxes; an unknown lattice is refused."""
+    """D3Q27 takes FP32 storage and periodic boxes; an unknown lattice or
+    collision is refused."""
     b = {"nx": 32, "ny": 32, "nz": 32, "tau": 1.0}
-    for kw in ({"lattice": 27, "precision": L.LB_BF16}, {"lattice": 27, "collision": 1}, {"lattice": 21}):
+    for kw in ({"lattice": 27, "precision": L.LB_BF16}, {"lattice": 27, "precision": L.LB_FP16},
+               {"lattice": 27, "collision": 2}, {"lattice": 21}):
         opt = L.Options()
         opt.max_semi, opt.max_particles = 8, 4
         for k, v in kw.items():

@@ -31,10 +31,11 @@ def _sim(boxes, parts, **kw):
     return L.Simulation(boxes, parts, max_semi=int(math.ceil(ms)), lattice=Q, **kw)
 
 
-def _orc(b, pl, didt_mode=0):
+def _orc(b, pl, didt_mode=0, collision=0):
     bb = dict(b)
     bb["lattice"] = Q
     bb["didt_mode"] = didt_mode
+    bb["collision"] = collision
     return O.Sim(bb, pl, nthreads=8)
 
 
@@ -65,14 +66,14 @@ def _orc_links(o):
     return {(int(n), tuple(int(v) for v in c)) for n, c in zip(node, cv)}
 
 
-def _compare(boxes, parts, steps, every, didt_mode=0, tol=1e-5, ft_scale="self"):
+def _compare(boxes, parts, steps, every, didt_mode=0, tol=1e-5, ft_scale="self", collision=0):
     """Side by side every `every` steps.  F and T against their own size, or
     (ft_scale "links", for a body whose net force or torque is a small
     residual of F = F0 - zeta (U', Omega')) against the size of their parts:
     F0 for the force, the larger of T0 and F0 times the long semi-axis for the
     torque."""
-    gpu = _sim(boxes, parts, didt_mode=didt_mode)
-    orcs = [_orc(b, pl, didt_mode) for b, pl in zip(boxes, parts)]
+    gpu = _sim(boxes, parts, didt_mode=didt_mode, collision=collision)
+    orcs = [_orc(b, pl, didt_mode, collision) for b, pl in zip(boxes, parts)]
     worst = {"df": 0.0, "u": 0.0, "F": 0.0, "T": 0.0, "x": 0.0, "q": 0.0}
     hist = {}
     done = 0
@@ -162,6 +163,23 @@ def test_d3q27_fast_particle_covers_and_uncovers_nodes():
     p = particle((4.5, 2.5, 2.0), (10.3, 9.1, 11.7), random_quaternion(g), U=(0.03, -0.02, 0.025),
                  Om=(0.004, 0.006, -0.005), density=5.0)
     _compare([b], [[p]], steps=60, every=3)
+
+
+@pytest.mark.parametrize("tau", [0.62, 0.8, 1.3])
+def test_d3q27_ghost_mode_collision(tau):
+    """The paper's collision (Sec. II.A: the non-equilibrium part projected on
+    the hydrodynamic modes and relaxed with tau, the other 18 modes of D3Q27
+    set to equilibrium; lb_options.collision = 1) with a spheroid under a force
+    and a torque, a box without a particle beside it, and a fast particle that
+    covers and uncovers nodes."""
+    g = rng(270)
+    boxes = [box(28, 24, 32, tau, counter_force=1), box(20, 20, 20, tau, body_force=(1e-6, -2e-6, 5e-7)),
+             box(24, 20, 28, tau)]
+    parts = [[particle((5.0, 2.5, 2.5), (13.3, 11.7, 15.2), random_quaternion(g), F_ext=(2e-4, -1e-4, 5e-5),
+                       T_ext=(3e-4, 0.0, -2e-4))], [],
+             [particle((4.5, 2.5, 2.0), (10.3, 9.1, 11.7), random_quaternion(g), U=(0.03, -0.02, 0.025),
+                       Om=(0.004, 0.006, -0.005), density=5.0)]]
+    _compare(boxes, parts, steps=60, every=6, ft_scale="links", collision=1)
 
 
 @pytest.mark.parametrize("didt_mode", [1, 2])
