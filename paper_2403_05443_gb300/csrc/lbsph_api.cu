@@ -405,7 +405,7 @@ static cudaError_t q27_enqueue(lb_ctx* ctx, int nsteps, cudaStream_t s)
             if ((e = q27::launch_particles27(pp, ctx->np, ctx->s27)) != cudaSuccess) break;
             q27::LatParams27 bulk = lp;
             bulk.mode = q27::LAT_BULK;
-            if ((e = q27::launch_lattice27(bulk, ctx->blocks27, s)) != cudaSuccess) break;
+            if ((e = q27::launch_bulk27(bulk, ctx->blocks27, s)) != cudaSuccess) break;
             if ((e = cudaEventRecord(ctx->ev27b, ctx->s27)) != cudaSuccess) break;
             if ((e = cudaStreamWaitEvent(s, ctx->ev27b, 0)) != cudaSuccess) break;
         }

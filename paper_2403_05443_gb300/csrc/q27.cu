@@ -7,7 +7,7 @@ namespace lbsph {
 namespace q27 {
 
 constexpr int LBLOCK = 256;          // threads per lattice block (one node each)
-constexpr int PBLK = 256;            // threads per particle block
+constexpr int PBLK = 512;            // threads per particle block
 constexpr int RW = MAXS * MAXS;      // words per bitmap slot
 
 __device__ __forceinline__ int wrapc(int a, int L) { return a < 0 ? a + L : (a >= L ? a - L : a); }
@@ -133,44 +133,53 @@ __device__ __forceinline__ int pre_collision(const Box27& B, const Dyn27& K, con
 template <bool GHOST>
 __device__ __forceinline__ void collide27(float (&d)[Q27], float omega, float rho0, const float g[3], float eps)
 {
-    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    // moments, per pair of opposite directions (2m+1, 2m+2), c_{2m+2} = -c_{2m+1}:
+    // the sum sm enters drho and the second moments, the difference df the momentum
+    float sm[13], df[13];
+    d[0] += w27(0) * eps;
+    float drho = d[0], jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
 #pragma unroll
-    for (int i = 0; i < Q27; ++i) {
-        d[i] += w27(i) * eps;
-        drho += d[i];
-        jx += cx27(i) * d[i];
-        jy += cy27(i) * d[i];
-        jz += cz27(i) * d[i];
+    for (int m = 0; m < 13; ++m) {
+        const int i = 2 * m + 1;
+        const float we = w27(i) * eps;
+        sm[m] = (d[i] + we) + (d[i + 1] + we);
+        df[m] = (d[i] + we) - (d[i + 1] + we);
+        const int cx = cx27(i), cy = cy27(i), cz = cz27(i);
+        drho += sm[m];
+        if (cx) jx += cx * df[m];
+        if (cy) jy += cy * df[m];
+        if (cz) jz += cz * df[m];
         if constexpr (GHOST) {
-            const int cx = cx27(i), cy = cy27(i), cz = cz27(i);
-            if (cx) pxx += d[i];
-            if (cy) pyy += d[i];
-            if (cz) pzz += d[i];
-            if (cx * cy) pxy += (cx * cy) * d[i];
-            if (cx * cz) pxz += (cx * cz) * d[i];
-            if (cy * cz) pyz += (cy * cz) * d[i];
+            if (cx) pxx += sm[m];
+            if (cy) pyy += sm[m];
+            if (cz) pzz += sm[m];
+            if (cx * cy) pxy += (cx * cy) * sm[m];
+            if (cx * cz) pxz += (cx * cz) * sm[m];
+            if (cy * cz) pyz += (cy * cz) * sm[m];
         }
     }
     const float rho = rho0 + drho;
     const float ir = 1.0f / rho;
     const float ux = (jx + 0.5f * g[0]) * ir, uy = (jy + 0.5f * g[1]) * ir, uz = (jz + 0.5f * g[2]) * ir;
     const float uu = ux * ux + uy * uy + uz * uz, ug = ux * g[0] + uy * g[1] + uz * g[2];
-    const float cf = 1.0f - 0.5f * omega;
+    const float cf = 1.0f - 0.5f * omega, om1 = 1.0f - omega;
+    // even part of the equilibrium about rho0 w (without the w factor)
+    const float e0 = drho - 1.5f * rho * uu;
     if constexpr (GHOST) {
+        // d_i' = deq_i + (1 - omega) w_i [3 c_i.j_neq + 4.5 (c_i c_i - I/3) : Pi_neq] + S_i;
+        // per pair the odd part is 3 w rho cu + 1.5 w cg whatever omega (j_neq = -g/2)
         const float iso = -drho * (1.0f / 3.0f);
         const float nxx = pxx + iso - rho * ux * ux, nyy = pyy + iso - rho * uy * uy, nzz = pzz + iso - rho * uz * uz;
         const float nxy = pxy - rho * ux * uy, nxz = pxz - rho * ux * uz, nyz = pyz - rho * uy * uz;
         const float tr3 = (nxx + nyy + nzz) * (1.0f / 3.0f);
-        const float om1 = 1.0f - omega;
-        const float jnx = -0.5f * g[0], jny = -0.5f * g[1], jnz = -0.5f * g[2];
+        d[0] = w27(0) * (e0 - om1 * 4.5f * tr3 - cf * 3.0f * ug);
 #pragma unroll
-        for (int i = 0; i < Q27; ++i) {
+        for (int m = 0; m < 13; ++m) {
+            const int i = 2 * m + 1;
             const int cx = cx27(i), cy = cy27(i), cz = cz27(i);
             const float cu = cx * ux + cy * uy + cz * uz;
             const float cg = cx * g[0] + cy * g[1] + cz * g[2];
-            const float deq = w27(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-            const float S = cf * w27(i) * (3.0f * (cg - ug) + 9.0f * cu * cg);
             float qp = -tr3;
             if (cx) qp += nxx;
             if (cy) qp += nyy;
@@ -178,17 +187,25 @@ __device__ __forceinline__ void collide27(float (&d)[Q27], float omega, float rh
             if (cx * cy) qp += (2 * cx * cy) * nxy;
             if (cx * cz) qp += (2 * cx * cz) * nxz;
             if (cy * cz) qp += (2 * cy * cz) * nyz;
-            const float cj = cx * jnx + cy * jny + cz * jnz;
-            d[i] = deq + om1 * w27(i) * (3.0f * cj + 4.5f * qp) + S;
+            const float E = w27(i) * (e0 + 4.5f * rho * cu * cu + om1 * 4.5f * qp + cf * (9.0f * cu * cg - 3.0f * ug));
+            const float O = w27(i) * (3.0f * rho * cu + 1.5f * cg);
+            d[i] = E + O;
+            d[i + 1] = E - O;
         }
     } else {
+        // d_i' = (1 - omega) d_i + omega deq_i + S_i, even and odd parts per pair
+        d[0] = om1 * d[0] + w27(0) * (omega * e0 - cf * 3.0f * ug);
 #pragma unroll
-        for (int i = 0; i < Q27; ++i) {
-            const float cu = cx27(i) * ux + cy27(i) * uy + cz27(i) * uz;
-            const float cg = cx27(i) * g[0] + cy27(i) * g[1] + cz27(i) * g[2];
-            const float deq = w27(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-            const float S = cf * w27(i) * (3.0f * (cg - ug) + 9.0f * cu * cg);
-            d[i] = d[i] - omega * (d[i] - deq) + S;
+        for (int m = 0; m < 13; ++m) {
+            const int i = 2 * m + 1;
+            const int cx = cx27(i), cy = cy27(i), cz = cz27(i);
+            const float cu = cx * ux + cy * uy + cz * uz;
+            const float cg = cx * g[0] + cy * g[1] + cz * g[2];
+            const float E = w27(i) * (omega * (e0 + 4.5f * rho * cu * cu) + cf * (9.0f * cu * cg - 3.0f * ug));
+            const float O = w27(i) * (omega * 3.0f * rho * cu + cf * 3.0f * cg);
+            const float a = om1 * (0.5f * sm[m]), b = om1 * (0.5f * df[m]);
+            d[i] = (a + b) + E + O;
+            d[i + 1] = (a - b) + E - O;
         }
     }
 }
@@ -333,6 +350,57 @@ __global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant
 }
 
 // ---------------------------------------------------------------------------
+// Bulk pass (LAT_BULK): every node outside the particles' cube unions takes the
+// plain pull of the last post-collision field and the collision, exactly as in
+// lattice27_kernel (outside both cubes no source is solid and no node changes
+// sides), without the bounce-back, remap and link-sum code: fewer registers and
+// instructions per node, so more warps and more loads in flight per SM.
+#ifndef BULK27_MINB
+#define BULK27_MINB 3
+#endif
+template <bool GHOST>
+__global__ void __launch_bounds__(LBLOCK, BULK27_MINB) bulk27_kernel(const __grid_constant__ LatParams27 P)
+{
+    __shared__ Box27 sB;
+    __shared__ Dyn27 sK;
+    const int bi = __ldg(P.blk_box + blockIdx.x);
+    if (threadIdx.x < sizeof(Box27) / 4)
+        reinterpret_cast<int*>(&sB)[threadIdx.x] = __ldg(reinterpret_cast<const int*>(P.boxes + bi) + threadIdx.x);
+    else if (threadIdx.x >= 64 && threadIdx.x < 64 + sizeof(Dyn27) / 4)
+        reinterpret_cast<int*>(&sK)[threadIdx.x - 64] =
+            __ldg(reinterpret_cast<const int*>(P.dyn + bi) + (threadIdx.x - 64));
+    __syncthreads();
+    const Box27& B = sB;
+    const Dyn27& K = sK;
+    const int node = (blockIdx.x - B.block_begin) * LBLOCK + threadIdx.x;
+    if (node >= (int)B.N) return;
+    const int row = div_magic(node, B.dx_m, B.dx_s);
+    const int X = node - row * B.nx;
+    const int Z = div_magic(row, B.dy_m, B.dy_s);
+    const int Y = row - Z * B.ny;
+    if (K.active) {
+        int m;
+        if (cube_local(X, K.uo[0], B.nx, K.E[0], m) && cube_local(Y, K.uo[1], B.ny, K.E[1], m) &&
+            cube_local(Z, K.uo[2], B.nz, K.E[2], m))
+            return;                                // a node of the near pass
+    }
+    const int nx = B.nx, ny = B.ny, nz = B.nz, N = (int)B.N;
+    const int nxy = nx * ny;
+    const int ox[3] = {X == nx - 1 ? 1 - nx : 1, 0, X == 0 ? nx - 1 : -1};
+    const int oy[3] = {Y == ny - 1 ? nx - nxy : nx, 0, Y == 0 ? nxy - nx : -nx};
+    const int oz[3] = {Z == nz - 1 ? nxy - N : nxy, 0, Z == 0 ? N - nxy : -nxy};
+    const float* A = P.src + B.off;
+    float* D = P.dst + B.off;
+    float d[Q27];
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) d[i] = __ldg(A + (i * N + node + ox[cx27(i) + 1] + oy[cy27(i) + 1] + oz[cz27(i) + 1]));
+    const float g[3] = {K.g[0], K.g[1], K.g[2]};
+    collide27<GHOST>(d, B.omega, B.rho0f, g, K.eps);
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) D[(size_t)i * B.N + node] = d[i];
+}
+
+// ---------------------------------------------------------------------------
 // Rigid-body algebra in FP64 (one thread)
 __device__ __forceinline__ void qmul27(const double a[4], const double b[4], double o[4])
 {
@@ -403,8 +471,8 @@ __device__ __forceinline__ void cross27(const double a[3], const double b[3], do
 // spread over the block: q27_sums (one thread) turns the integer sums of the
 // last lattice pass into F0, T0 and the remap terms; the inertia and its rate
 // come from another warp at the same time; a warp solves the 6 x 6 system
-// (Gauss-Jordan, partial pivoting, one column per lane); six threads form F
-// and T; q27_finish (one thread) moves the particle and writes its record.
+// (q27_solve6); six threads form F and T; three threads move the centre and
+// another the orientation, and a warp writes the record.
 __device__ void q27_sums(const PartParams27& P, Part27* D, const Box27& B, int p, double F0[3], double T0[3])
 {
     long long* acc = P.acc + (size_t)p * NACC;
@@ -457,78 +525,142 @@ __device__ void q27_sums(const PartParams27& P, Part27* D, const Box27& B, int p
     D->dm = nc * rho0 + a[ACC_COV + 1] / FIXD - nu * rho0;
 }
 
-// one warp: x = A^-1 rhs (lane 6 holds the result); false if a pivot vanishes
-__device__ __forceinline__ bool q27_warp_solve(const double A6[36], const double rhs[6], double x6[6], int lane)
+// Gauss-Jordan with partial pivoting on one warp in FP32: lane j < 12 holds
+// column j of [A | I] (rows 0..5); on return lanes 6..11 hold the columns of
+// A^-1.  The pivot is chosen by lane k and broadcast, so every lane takes the
+// same row exchanges; false (on every lane) if a pivot vanishes.
+__device__ __forceinline__ bool gj_inv6_warp_f32(float (&col)[6], int lane)
 {
-    double col[6];
-    for (int i = 0; i < 6; ++i) col[i] = lane < 6 ? A6[i * 6 + lane] : (lane == 6 ? rhs[i] : 0.0);
-    const bool ok = gj_solve6_warp(col, lane);
-    if (lane == 6)
-        for (int i = 0; i < 6; ++i) x6[i] = col[i];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        int piv = k;
+        if (lane == k) {
+            float best = fabsf(col[k]);
+#pragma unroll
+            for (int i = k + 1; i < 6; ++i)
+                if (fabsf(col[i]) > best) { best = fabsf(col[i]); piv = i; }
+        }
+        piv = __shfl_sync(0xffffffffu, piv, k);
+        float rowk = col[k], rowp = col[k];
+#pragma unroll
+        for (int i = k + 1; i < 6; ++i)
+            if (i == piv) rowp = col[i];
+#pragma unroll
+        for (int i = k + 1; i < 6; ++i)
+            if (i == piv) col[i] = rowk;
+        col[k] = rowp;
+        const float pv = __shfl_sync(0xffffffffu, col[k], k);
+        ok = ok && (pv != 0.0f);
+        col[k] *= 1.0f / pv;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            if (i == k) continue;
+            const float fi = __shfl_sync(0xffffffffu, col[i], k);
+            col[i] -= fi * col[k];
+        }
+    }
     return ok;
 }
 
-__device__ void q27_finish(const PartParams27& P, Part27* D, const double In[9], const double x6[6],
-                           const double F0[3], const double T0[3], const double FT[6])
+// x = A^-1 rhs for the 6 x 6 system of Eq. Fdiscrete / Eq. Tdiscrete on one
+// warp: the inverse in FP32, then iterative refinement, x += A^-1 (rhs - A x)
+// with the residual in FP64.  Each step multiplies the error by about cond(A)
+// times the FP32 rounding; three steps bring it to FP64 rounding for these
+// systems (mass, inertia and drag matrices: cond(A) of order 10-10^3).  The
+// FP32 inverse keeps the chain of dependent FP64 operations short (a dependent
+// FP64 operation costs about 0.1 us on this part; the Gauss-Jordan elimination in
+// FP64 took 15 us).  s_Ai: 36 floats of scratch.  Writes x6 (lanes 0..5);
+// false if a pivot vanishes.
+__device__ bool q27_solve6(const double* A6, const double* rhs, double* x6, float* s_Ai, int lane)
 {
-    const double* F = FT;
-    const double* T = FT + 3;
-    for (int k = 0; k < 9; ++k) D->Iprev[k] = In[k];
-    // Eq. posupdate and Eq. qnplus0-1 with the mean velocities of the step
-    double Wm[3], qn[4];
-    for (int k = 0; k < 3; ++k) {
-        D->x[k] += 0.5 * (D->U[k] + x6[k]);
-        Wm[k] = 0.5 * (D->W[k] + x6[k + 3]);
-        D->U[k] = x6[k];
-        D->W[k] = x6[k + 3];
+    float col[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        col[i] = lane < 6 ? (float)A6[i * 6 + lane] : (lane - 6 == i ? 1.0f : 0.0f);
+    const bool ok = gj_inv6_warp_f32(col, lane);
+    if (lane >= 6 && lane < 12)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s_Ai[i * 6 + lane - 6] = col[i];
+    __syncwarp();
+    const int i = lane < 6 ? lane : 0;
+    double a[6];
+    float ai[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        a[j] = A6[i * 6 + j];
+        ai[j] = s_Ai[i * 6 + j];
     }
-    qstep27(D->q, Wm, qn);
-    for (int k = 0; k < 4; ++k) D->q[k] = qn[k];
-    double* r = D->rec;
-    for (int k = 0; k < 3; ++k) {
-        r[k] = F0[k]; r[3 + k] = T0[k]; r[6 + k] = F[k]; r[9 + k] = T[k];
-        r[12 + k] = D->U[k]; r[15 + k] = D->W[k]; r[18 + k] = D->x[k];
+    const double b = rhs[i];
+    float xf = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) xf += ai[j] * (float)rhs[j];
+    double x = xf;
+    for (int it = 0; it < 3; ++it) {
+        double r0 = b, r1 = 0.0;
+#pragma unroll
+        for (int j = 0; j < 6; j += 2) {
+            r0 -= a[j] * __shfl_sync(0xffffffffu, x, j);
+            r1 -= a[j + 1] * __shfl_sync(0xffffffffu, x, j + 1);
+        }
+        const float r = (float)(r0 + r1);
+        float d = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) d += ai[j] * __shfl_sync(0xffffffffu, r, j);
+        x += (double)d;
     }
-    for (int k = 0; k < 4; ++k) r[21 + k] = D->q[k];
-    bool fin = true;
-    for (int k = 0; k < 25; ++k) fin = fin && isfinite(r[k]);
-    if (!fin) atomicOr(P.status, ST_NAN);
+    if (lane < 6) x6[lane] = x;
+    __syncwarp();
+    return ok;
 }
 
 // ---------------------------------------------------------------------------
-// Particle kernel: one block per particle.  Step mode: the solve and pose
-// update of the last lattice pass's iteration (thread 0), then for the new
-// pose the occupancy map (Eq. ellipsoidsurface), built in shared memory one
-// cube row per thread: along a row the inside value is the quadratic
-// a x^2 + b x + c, evaluated in FP32 and decided there when it is farther than
-// 1e-3 from 1 (its FP32 error stays below 1e-4 inside the cube), and by the
-// exact FP64 test in the oracle's operation order otherwise, so the map is
-// bit-identical to the oracle's.  The links (x fluid, x + c_b solid) of each
-// row and direction are a bit mask; their drag matrix and the geometric parts
-// of F0 / T0 (Eq. drag1-4, Eq. F0, Eq. T0) come from exact integer sums per
-// direction (link count, sum of m, sum of m m^T over the cube coordinates m of
-// the fluid ends), combined once in FP64 with p = phi + m, r_b x c_b = p x c_b.
-// Init mode: the map and its terms for the current pose.
+// Particle kernel: one block of 512 threads per particle, the particle's state
+// staged in shared memory and written back at the end.  Step mode: the solve
+// and pose update of the last lattice pass's iteration, then for the new pose
+// the occupancy map (Eq. ellipsoidsurface), built in shared memory one cube row
+// per thread: along a row the inside value is the quadratic a x^2 + b x + c,
+// evaluated in FP32 and decided there outside a band around 1 (its FP32 error
+// stays far below the band inside the cube); the nodes inside the band are
+// collected and then tested by the exact FP64 test in the oracle's operation
+// order, one node per thread, so the map is bit-identical to the oracle's.
+// The links (x fluid, x + c_b solid) of each row and direction are a bit mask;
+// their drag matrix and the geometric parts of F0 / T0 (Eq. drag1-4, Eq. F0,
+// Eq. T0) come from exact integer sums per direction (link count, sum of m,
+// sum of m m^T over the cube coordinates m of the fluid ends), combined once
+// in FP64 with p = phi + m, r_b x c_b = p x c_b.  Init mode: the map and its
+// terms for the current pose.
+constexpr int NCAND = 512;                       // nodes of the FP32 band tested exactly after the row pass
 __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_constant__ PartParams27 P)
 {
     constexpr int NSUM = 10;                     // per direction: n, sum m (3), sum m m^T (6)
-    const int p = blockIdx.x, tid = threadIdx.x;
-    Part27* D = P.pd + p;
-    const Box27 B = P.boxes[D->box];
+    constexpr int NG = PBLK / (Q27 - 1);         // row groups of the link sums (one direction per thread)
+    const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Part27* G = P.pd + p;
+    __shared__ Part27 sD;
+    __shared__ Box27 sB;
     __shared__ uint64_t s_map[MAXS * MAXS];
     __shared__ int s_sum[Q27][NSUM];
-    constexpr int NG = PBLK / (Q27 - 1);         // row groups of the link sums (one direction per thread)
-    // per direction: drag matrix (36), F0g (3), T0g (3); before that, the link
-    // sums of each row group (the two are not used at the same time)
-    __shared__ double s_scratch[(NG * Q27 * NSUM * 4 > Q27 * 42 * 8 ? NG * Q27 * NSUM * 4 : Q27 * 42 * 8) / 8 + 1];
-    double (*s_con)[42] = reinterpret_cast<double (*)[42]>(s_scratch);
-    int (*s_part)[Q27][NSUM] = reinterpret_cast<int (*)[Q27][NSUM]>(s_scratch);
-    __shared__ double s_A[9], s_x[3], s_phi[3];
+    __shared__ double s_con[Q27][42];            // per direction: drag matrix (36), F0g (3), T0g (3)
+    __shared__ double s_A[9], s_E[9], s_x[3], s_phi[3];
     __shared__ float s_A32[9], s_d0[3];
-    __shared__ int s_o[3], s_ow[3], s_S, s_slot, s_ok, s_nsol;
+    __shared__ int s_o[3], s_ow[3], s_S, s_slot, s_ok, s_nsol, s_ncand;
     __shared__ float s_band;
+    __shared__ int s_cand[NCAND];
+    static_assert(sizeof(Part27) % 8 == 0 && sizeof(Box27) % 4 == 0, "staged as words");
+    {
+        const int bi = __ldg(&G->box);
+        for (int k = tid; k < (int)(sizeof(Part27) / 8); k += PBLK)
+            reinterpret_cast<unsigned long long*>(&sD)[k] = reinterpret_cast<const unsigned long long*>(G)[k];
+        if (tid >= 256 && tid < 256 + (int)(sizeof(Box27) / 4))
+            reinterpret_cast<int*>(&sB)[tid - 256] = __ldg(reinterpret_cast<const int*>(P.boxes + bi) + (tid - 256));
+    }
+    __syncthreads();
+    Part27* D = &sD;
+    const Box27& B = sB;
     if (!P.init) {
-        __shared__ double s_F0[3], s_T0[3], s_In[9], s_dI[9], s_A6[36], s_rhs[6], s_x6[6];
+        __shared__ double s_F0[3], s_T0[3], s_In[9], s_dI[9], s_A6[36], s_rhs[6], s_x6[6], s_FT[6], s_xn[3], s_qn[4];
+        __shared__ float s_Ai[36];
         __shared__ int s_solved;
         if (tid == 0) {
             q27_sums(P, D, B, p, s_F0, s_T0);
@@ -561,7 +693,7 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
         }
         __syncthreads();
         if (tid < 32) {
-            const bool ok = q27_warp_solve(s_A6, s_rhs, s_x6, tid);
+            const bool ok = q27_solve6(s_A6, s_rhs, s_x6, s_Ai, tid);
             if (tid == 0) s_solved = ok;
         }
         __syncthreads();
@@ -577,94 +709,151 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
             }
             __syncthreads();
             if (tid < 32) {
-                const bool ok = q27_warp_solve(s_A6, s_rhs, s_x6, tid);
+                const bool ok = q27_solve6(s_A6, s_rhs, s_x6, s_Ai, tid);
                 if (tid == 0) s_solved = ok;
             }
             __syncthreads();
         }
-        // F = F0 - zeta_F (U', W'), T = T0 - zeta_T (U', W'), one component per thread
-        __shared__ double s_FT[6];
+        // F = F0 - zeta_F (U', W'), T = T0 - zeta_T (U', W'), one component per
+        // thread; the new centre (Eq. posupdate) on three threads and the new
+        // orientation (Eq. qnplus0-1, mean angular velocity of the step) on another
         if (tid < 6) {
             double z = 0.0;
             for (int j = 0; j < 6; ++j) z += D->zeta[tid * 6 + j] * s_x6[j];
             s_FT[tid] = (tid < 3 ? s_F0[tid] : s_T0[tid - 3]) - z;
+        } else if (tid >= 32 && tid < 35) {
+            const int k = tid - 32;
+            s_xn[k] = D->x[k] + 0.5 * (D->U[k] + s_x6[k]);
+        } else if (tid == 64) {
+            double Wm[3];
+            for (int k = 0; k < 3; ++k) Wm[k] = 0.5 * (D->W[k] + s_x6[k + 3]);
+            qstep27(D->q, Wm, s_qn);
         }
         __syncthreads();
-        if (tid == 0) {
-            if (!s_solved) atomicOr(P.status, ST_NAN);
-            else q27_finish(P, D, s_In, s_x6, s_F0, s_T0, s_FT);
+        if (s_solved) {
+            // the new state, and the record F0, T0, F, T, U, W, x, q (finite or ST_NAN)
+            if (tid < 9) {
+                D->Iprev[tid] = s_In[tid];
+                if (tid < 3) {
+                    D->x[tid] = s_xn[tid];
+                    D->U[tid] = s_x6[tid];
+                    D->W[tid] = s_x6[tid + 3];
+                }
+                if (tid < 4) D->q[tid] = s_qn[tid];
+            } else if (warp == 1) {
+                double v = 0.0;
+                if (lane < 3) v = s_F0[lane];
+                else if (lane < 6) v = s_T0[lane - 3];
+                else if (lane < 12) v = s_FT[lane - 6];
+                else if (lane < 18) v = s_x6[lane - 12];
+                else if (lane < 21) v = s_xn[lane - 18];
+                else if (lane < 25) v = s_qn[lane - 21];
+                if (lane < 25) D->rec[lane] = v;
+                if (!__all_sync(0xffffffffu, lane >= 25 || isfinite(v)) && lane == 0) atomicOr(P.status, ST_NAN);
+            }
+        } else if (tid == 0) {
+            atomicOr(P.status, ST_NAN);
         }
+        __syncthreads();
     }
-    if (tid == 0) {
-        s_ok = 1;
-        if (!P.init) {
-            if (__ldcg(P.status) & ST_NAN) s_ok = 0;
-        } else {
-            inertia27(D->q, D->Ib, D->Iprev);      // I(t - 1) = I(t) before the first step
+    // the cube of the new pose (origin floor(x) - h, side S = 2h + 2), one axis
+    // per thread; the exact inside-test matrix of the new orientation on another
+    // warp (lanes 0..8)
+    if (tid < 3) {
+        const int k = tid;
+        const int L = k == 0 ? B.nx : (k == 1 ? B.ny : B.nz);
+        const int o = (int)floor(D->x[k]) - D->h;
+        s_o[k] = o;
+        s_ow[k] = ((o % L) + L) % L;
+        s_phi[k] = (double)o - D->x[k];
+        s_d0[k] = (float)s_phi[k];                 // d = X - x_c at cube coordinate 0
+        s_x[k] = D->x[k];
+        if (k == 0) {
+            s_ok = 1;
+            if (!P.init) {
+                if (__ldcg(P.status) & ST_NAN) s_ok = 0;
+            }
+            s_S = D->S;
+            s_slot = P.init ? 0 : 1 - D->slot;
+            s_nsol = 0;
+            s_ncand = 0;
+            s_band = D->band;                      // the FP32 decision band of the map (set on the host)
         }
-        // the cube of the new pose: origin floor(x) - h, side S = 2h + 2
-        const int L[3] = {B.nx, B.ny, B.nz};
-        for (int k = 0; k < 3; ++k) {
-            const int o = (int)floor(D->x[k]) - D->h;
-            s_o[k] = o;
-            s_ow[k] = ((o % L[k]) + L[k]) % L[k];
-            s_phi[k] = (double)o - D->x[k];
-            s_d0[k] = (float)s_phi[k];             // d = X - x_c at cube coordinate 0
-            s_x[k] = D->x[k];
-        }
-        s_S = D->S;
-        s_slot = P.init ? 0 : 1 - D->slot;
-        s_nsol = 0;
-        s_band = D->band;                          // the FP32 decision band of the map (set on the host)
-    }
-    __syncwarp();
-    if (tid < 32) {
-        // the exact inside-test matrix of the new orientation (lanes 0..8)
-        __shared__ double s_E[9];
-        canon_shape_warp(D->inv2, D->q, s_E, s_A, tid);
-        if (tid < 9) s_A32[tid] = (float)s_A[tid];
+    } else if (warp == 1) {
+        canon_shape_warp(D->inv2, D->q, s_E, s_A, lane);
+        if (lane < 9) s_A32[lane] = (float)s_A[lane];
+    } else if (P.init && tid == 64) {
+        inertia27(D->q, D->Ib, D->Iprev);          // I(t - 1) = I(t) before the first step
     }
     for (int k = tid; k < Q27 * NSUM; k += PBLK) (&s_sum[0][0])[k] = 0;
     __syncthreads();
-    if (!s_ok) return;
+    if (!s_ok) {
+        for (int k = tid; k < (int)(sizeof(Part27) / 8); k += PBLK)
+            reinterpret_cast<unsigned long long*>(G)[k] = reinterpret_cast<const unsigned long long*>(&sD)[k];
+        return;
+    }
     const int S = s_S;
     const uint64_t full = S == 64 ? ~0ull : ((1ull << S) - 1ull);
-    // ---- occupancy of the new pose
-    int nsol = 0;
+    // ---- occupancy of the new pose: FP32 outside the band, band nodes listed
     for (int r = tid; r < S * S; r += PBLK) {
         const int my = r % S, mz = r / S;
-        const int Y = wrapc(s_ow[1] + my, B.ny), Z = wrapc(s_ow[2] + mz, B.nz);
         const float dy = s_d0[1] + (float)my, dz = s_d0[2] + (float)mz;
         const float qa = s_A32[0], qb = 2.0f * (s_A32[1] * dy + s_A32[2] * dz);
         const float qc = s_A32[4] * dy * dy + 2.0f * s_A32[5] * dy * dz + s_A32[8] * dz * dz;
+        const float band = s_band;
         uint64_t w = 0;
         for (int mx = 0; mx < S; ++mx) {
             const float dx = s_d0[0] + (float)mx;
             const float v = (qa * dx + qb) * dx + qc;
-            bool in;
-            if (fabsf(v - 1.0f) > s_band) {
-                in = v < 1.0f;
+            if (fabsf(v - 1.0f) > band) {
+                if (v < 1.0f) w |= 1ull << mx;
             } else {
-                const int X = wrapc(s_ow[0] + mx, B.nx);
-                in = canon_value(s_A, s_x, X, Y, Z, B.nx, B.ny, B.nz, true) <= 1.0;
+                const int c = atomicAdd(&s_ncand, 1);
+                if (c < NCAND) {
+                    s_cand[c] = (mz << 16) | (my << 8) | mx;
+                } else {
+                    const int X = wrapc(s_ow[0] + mx, B.nx), Y = wrapc(s_ow[1] + my, B.ny),
+                              Z = wrapc(s_ow[2] + mz, B.nz);
+                    if (canon_value(s_A, s_x, X, Y, Z, B.nx, B.ny, B.nz, true) <= 1.0) w |= 1ull << mx;
+                }
             }
-            if (in) w |= 1ull << mx;
         }
         s_map[r] = w;
-        nsol += __popcll(w);
     }
-    if (nsol) atomicAdd(&s_nsol, nsol);
     __syncthreads();
-    // ---- links of the new map, summed per direction in integers: thread t
-    // takes direction 1 + t % 26 over the rows g, g + NG, ... (g = t / 26); the
-    // sums of x and x^2 over a row's link bits come from popcounts of the masks
-    // of bit positions whose bit p is set (x = sum_p 2^p [bit p of x])
+    {
+        const int nc = min(s_ncand, NCAND);
+        for (int c = tid; c < nc; c += PBLK) {
+            const int code = s_cand[c];
+            const int mx = code & 0xff, my = (code >> 8) & 0xff, mz = code >> 16;
+            const int X = wrapc(s_ow[0] + mx, B.nx), Y = wrapc(s_ow[1] + my, B.ny), Z = wrapc(s_ow[2] + mz, B.nz);
+            if (canon_value(s_A, s_x, X, Y, Z, B.nx, B.ny, B.nz, true) <= 1.0)
+                atomicOr(reinterpret_cast<unsigned long long*>(&s_map[mz * S + my]), 1ull << mx);
+        }
+    }
+    __syncthreads();
+    // ---- solid nodes; the map into its global slot (the lattice kernel and the
+    // read-back use it); links of the new map summed per direction in integers:
+    // thread t takes direction 1 + t % 26 over the rows g, g + NG, ... (g = t / 26);
+    // the sums of x and x^2 over a row's link bits come from popcounts of the
+    // masks of bit positions whose bit p is set (x = sum_p 2^p [bit p of x])
+    {
+        uint64_t* map = P.rows + ((size_t)p * 2 + s_slot) * RW;
+        int ns = 0;
+        for (int r = tid; r < S * S; r += PBLK) {
+            const uint64_t w = s_map[r];
+            map[r] = w;
+            ns += __popcll(w);
+        }
+        ns = __reduce_add_sync(0xffffffffu, ns);
+        if (lane == 0 && ns) atomicAdd(&s_nsol, ns);
+    }
     {
         const int b = 1 + tid % (Q27 - 1), g = tid / (Q27 - 1);
-        int t[NSUM];
-#pragma unroll
-        for (int k = 0; k < NSUM; ++k) t[k] = 0;
         if (g < NG) {
+            int t[NSUM];
+#pragma unroll
+            for (int k = 0; k < NSUM; ++k) t[k] = 0;
             const int cx = cx27(b), cy = cy27(b), cz = cz27(b);
             const uint64_t M[6] = {0xAAAAAAAAAAAAAAAAull, 0xCCCCCCCCCCCCCCCCull, 0xF0F0F0F0F0F0F0F0ull,
                                    0xFF00FF00FF00FF00ull, 0xFFFF0000FFFF0000ull, 0xFFFFFFFF00000000ull};
@@ -674,20 +863,31 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
                 if (ny_ >= 0 && nz_ >= 0 && ny_ < S && nz_ < S) {
                     const uint64_t nb = s_map[nz_ * S + ny_];
                     const uint64_t sol = cx == 1 ? (nb >> 1) : (cx == -1 ? (nb << 1) : nb);
-                    const uint64_t L = ~s_map[r] & sol & full;
+                    uint64_t L = ~s_map[r] & sol & full;
                     if (L) {
                         const int n = __popcll(L);
-                        int pc[6], sx = 0, sxx = 0;
+                        int sx = 0, sxx = 0;
+                        if (n <= 4) {
+                            // a few links: their positions one by one
+                            while (L) {
+                                const int x = __ffsll((long long)L) - 1;
+                                L &= L - 1;
+                                sx += x;
+                                sxx += x * x;
+                            }
+                        } else {
+                            int pc[6];
 #pragma unroll
-                        for (int q = 0; q < 6; ++q) {
-                            pc[q] = __popcll(L & M[q]);
-                            sx += pc[q] << q;
-                            sxx += pc[q] << (2 * q);
+                            for (int q = 0; q < 6; ++q) {
+                                pc[q] = __popcll(L & M[q]);
+                                sx += pc[q] << q;
+                                sxx += pc[q] << (2 * q);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 6; ++q)
+#pragma unroll
+                                for (int q2 = q + 1; q2 < 6; ++q2) sxx += __popcll(L & M[q] & M[q2]) << (q + q2 + 1);
                         }
-#pragma unroll
-                        for (int q = 0; q < 6; ++q)
-#pragma unroll
-                            for (int q2 = q + 1; q2 < 6; ++q2) sxx += __popcll(L & M[q] & M[q2]) << (q + q2 + 1);
                         t[0] += n; t[1] += sx; t[2] += n * my; t[3] += n * mz; t[4] += sxx;
                         t[5] += sx * my; t[6] += sx * mz; t[7] += n * my * my; t[8] += n * my * mz; t[9] += n * mz * mz;
                     }
@@ -696,23 +896,14 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
                 while (my >= S) { my -= S; ++mz; }
             }
 #pragma unroll
-            for (int k = 0; k < NSUM; ++k) s_part[g][b][k] = t[k];
+            for (int k = 0; k < NSUM; ++k)
+                if (t[k]) atomicAdd(&s_sum[b][k], t[k]);
         }
     }
     __syncthreads();
-    for (int e = tid; e < (Q27 - 1) * NSUM; e += PBLK) {
-        const int b = 1 + e / NSUM, k = e % NSUM;
-        int v = 0;
-        for (int g = 0; g < NG; ++g) v += s_part[g][b][k];
-        s_sum[b][k] = v;
-    }
-    // the map into its global slot (the lattice kernel and the read-back use it)
-    uint64_t* map = P.rows + ((size_t)p * 2 + s_slot) * RW;
-    for (int r = tid; r < S * S; r += PBLK) map[r] = s_map[r];
-    __syncthreads();
     // each direction's share of the drag matrix and of F0g / T0g: thread b the
     // translational and mixed blocks, thread 32 + b (another warp) the
-    // rotational block; then every entry summed over the directions in order
+    // rotational block
     if ((tid >= 1 && tid < Q27) || (tid >= 33 && tid < 32 + Q27)) {
         const int b = tid & 31;
         const bool rot = tid >= 32;
@@ -757,11 +948,17 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
         }
     }
     __syncthreads();
-    if (tid < 42) {
-        double v = 0.0;
-        for (int b = 1; b < Q27; ++b) v += s_con[b][tid];
-        s_con[0][tid] = v;
-        if (tid < 36) D->zeta[tid] = v;
+    // every entry summed over the 26 directions: a warp per entry, lane l the
+    // direction l + 1, a shuffle tree (five dependent additions)
+    for (int e = warp; e < 42; e += PBLK / 32) {
+        double v = lane < Q27 - 1 ? s_con[lane + 1][e] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            if (e < 36) D->zeta[e] = v;
+            else if (e < 39) D->F0g[e - 36] = v;
+            else D->T0g[e - 39] = v;
+        }
     }
     __syncthreads();
     // the new state, one thread per axis (thread 0 also the scalars)
@@ -769,8 +966,6 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
         const int i = tid;
         const int ns = s_nsol;
         Dyn27& Y = P.dyn[D->box];
-        D->F0g[i] = s_con[0][36 + i];
-        D->T0g[i] = s_con[0][39 + i];
         // the map the next pass bounces back from is the current one
         const int Lk = i == 0 ? B.nx : (i == 1 ? B.ny : B.nz);
         Y.phi_old[i] = P.init ? (float)s_phi[i] : (float)D->phi[i];
@@ -785,8 +980,6 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
         Y.o_new[i] = s_ow[i];
         Y.U[i] = (float)D->U[i];
         Y.W[i] = (float)D->W[i];
-        D->phi[i] = s_phi[i];
-        D->o[i] = s_o[i];
         // uniform terms of the next collision: body force (with the counter
         // force on the fluid nodes of the new map) and the mass of this remap,
         // returned over every fluid node
@@ -797,11 +990,21 @@ __global__ void __launch_bounds__(PBLK, 1) particle27_kernel(const __grid_consta
             Y.slot_new = s_slot;
             Y.S = S;
             Y.active = 1;
-            D->slot = s_slot;
-            D->nsolid = ns;
             Y.eps = P.init ? 0.0f : (float)(D->dm * inf);
         }
     }
+    __syncthreads();
+    if (tid < 3) {
+        D->phi[tid] = s_phi[tid];
+        D->o[tid] = s_o[tid];
+        if (tid == 0) {
+            D->slot = s_slot;
+            D->nsolid = s_nsol;
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < (int)(sizeof(Part27) / 8); k += PBLK)
+        reinterpret_cast<unsigned long long*>(G)[k] = reinterpret_cast<const unsigned long long*>(&sD)[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -895,6 +1098,15 @@ cudaError_t launch_lattice27(const LatParams27& p, int blocks, cudaStream_t s)
         lattice27_kernel<true><<<blocks, LBLOCK, 0, s>>>(p);
     else
         lattice27_kernel<false><<<blocks, LBLOCK, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bulk27(const LatParams27& p, int blocks, cudaStream_t s)
+{
+    if (p.ghost)
+        bulk27_kernel<true><<<blocks, LBLOCK, 0, s>>>(p);
+    else
+        bulk27_kernel<false><<<blocks, LBLOCK, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -149,6 +149,7 @@ struct FieldParams27 {
 };
 
 cudaError_t launch_lattice27(const LatParams27& p, int blocks, cudaStream_t s);
+cudaError_t launch_bulk27(const LatParams27& p, int blocks, cudaStream_t s);   // LAT_BULK only
 cudaError_t launch_particles27(const PartParams27& p, int np, cudaStream_t s);
 cudaError_t launch_fields27(const FieldParams27& p, int blocks, cudaStream_t s);
 cudaError_t launch_refresh27(const Part27* pd, const Box27* boxes, Dyn27* dyn, int np, cudaStream_t s);
