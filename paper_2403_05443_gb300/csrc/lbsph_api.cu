@@ -393,7 +393,12 @@ static cudaError_t q27_enqueue(lb_ctx* ctx, int nsteps, cudaStream_t s)
                             q27::LAT_ALL, ctx->nbpp27, ctx->opt.collision};
         q27::PartParams27 pp{ctx->d_part27, dnext, ctx->d_box27, ctx->d_rows, ctx->d_acc, ctx->d_status, 0,
                              ctx->opt.didt_mode};
-        if (!ctx->collided || ctx->np == 0) {
+        if (ctx->collided && ctx->np == 0) {
+            // no particle in any box: every node takes the plain pull and the collision
+            q27::LatParams27 bulk = lp;
+            bulk.mode = q27::LAT_BULK;
+            if ((e = q27::launch_bulk27(bulk, ctx->blocks27, s)) != cudaSuccess) break;
+        } else if (!ctx->collided) {
             if ((e = q27::launch_lattice27(lp, ctx->blocks27, s)) != cudaSuccess) break;
             if ((e = q27::launch_particles27(pp, ctx->np, s)) != cudaSuccess) break;
         } else {

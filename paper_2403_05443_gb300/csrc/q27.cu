@@ -27,6 +27,33 @@ __device__ __forceinline__ bool bit_at(const uint64_t* map, int S, int mx, int m
     return (__ldg(map + mz * S + my) >> mx) & 1ull;
 }
 
+// The 3 x 3 x 3 neighbourhood of cube cell (mx, my, mz), 0 <= m < S, of a map of
+// side S as one mask: bit (dx + 1) + 3 (dy + 1) + 9 (dz + 1) is the cell
+// (mx + dx, my + dy, mz + dz), 0 outside the cube (rows hold no bits at S and
+// beyond).  Nine row loads instead of a bounds-checked load per direction.
+__device__ __forceinline__ unsigned nbhd27(const uint64_t* map, int S, int mx, int my, int mz)
+{
+    unsigned nb = 0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int y = my + dy, z = mz + dz;
+            if (y < 0 || z < 0 || y >= S || z >= S) continue;
+            const uint64_t w = __ldg(map + z * S + y);
+            // bits mx - 1, mx, mx + 1 of the row
+            const unsigned t = mx > 0 ? (unsigned)((w >> (mx - 1)) & 7ull) : (unsigned)((w << 1) & 6ull);
+            nb |= t << (3 * (dy + 1) + 9 * (dz + 1));
+        }
+    return nb;
+}
+
+// bit of the neighbour at offset c in a mask of nbhd27
+__device__ __forceinline__ bool nb_bit(unsigned nb, int cx, int cy, int cz)
+{
+    return (nb >> (13 + cx + 3 * cy + 9 * cz)) & 1u;
+}
+
 enum { K_FLUID = 0, K_SOLID = 1, K_COVERED = 2, K_UNCOVERED = 3 };
 
 // Pre-collision deviations d = f - w rho0 of node (X, Y, Z) at the start of
@@ -41,25 +68,27 @@ enum { K_FLUID = 0, K_SOLID = 1, K_COVERED = 2, K_UNCOVERED = 3 };
 // collision).
 __device__ __forceinline__ int pre_collision(const Box27& B, const Dyn27& K, const uint64_t* rows, const float* A,
                                              int X, int Y, int Z, int node, bool nopull, float (&d)[Q27],
-                                             int (&mn)[3], bool& in_new)
+                                             int (&mn)[3], bool& in_new, unsigned& nb_new)
 {
     const int nx = B.nx, ny = B.ny, nz = B.nz, N = (int)B.N;
     int mo[3] = {0, 0, 0};
     bool in_old = false;
     in_new = false;
     bool sol_old = false, sol_new = false;
-    const uint64_t* map_old = nullptr;
-    const uint64_t* map_new = nullptr;
+    unsigned nb_old = 0u;
+    nb_new = 0u;
     if (K.active) {
         const int S = K.S;
-        map_old = rows + (size_t)K.slot_old * RW;
-        map_new = rows + (size_t)K.slot_new * RW;
+        const uint64_t* map_old = rows + (size_t)K.slot_old * RW;
+        const uint64_t* map_new = rows + (size_t)K.slot_new * RW;
         in_old = cube_local(X, K.o_old[0], nx, S, mo[0]) && cube_local(Y, K.o_old[1], ny, S, mo[1]) &&
                  cube_local(Z, K.o_old[2], nz, S, mo[2]);
         in_new = cube_local(X, K.o_new[0], nx, S, mn[0]) && cube_local(Y, K.o_new[1], ny, S, mn[1]) &&
                  cube_local(Z, K.o_new[2], nz, S, mn[2]);
-        sol_old = in_old && bit_at(map_old, S, mo[0], mo[1], mo[2]);
-        sol_new = in_new && bit_at(map_new, S, mn[0], mn[1], mn[2]);
+        nb_old = in_old ? nbhd27(map_old, S, mo[0], mo[1], mo[2]) : 0u;
+        nb_new = in_new ? nbhd27(map_new, S, mn[0], mn[1], mn[2]) : 0u;
+        sol_old = nb_bit(nb_old, 0, 0, 0);
+        sol_new = nb_bit(nb_new, 0, 0, 0);
     }
     if (nopull) {
 #pragma unroll
@@ -101,7 +130,7 @@ __device__ __forceinline__ int pre_collision(const Box27& B, const Dyn27& K, con
 #pragma unroll
     for (int i = 0; i < Q27; ++i) {
         const int cx = cx27(i), cy = cy27(i), cz = cz27(i);
-        const bool back = i > 0 && bit_at(map_old, K.S, mo[0] - cx, mo[1] - cy, mo[2] - cz);
+        const bool back = i > 0 && nb_bit(nb_old, -cx, -cy, -cz);
         if (back) {
             const float px = K.phi_old[0] + mo[0] - 0.5f * cx;
             const float py = K.phi_old[1] + mo[1] - 0.5f * cy;
@@ -225,7 +254,7 @@ __device__ __forceinline__ void acc_add(long long* a, long long v)
 // ---------------------------------------------------------------------------
 // One lattice pass over every node of every box (one node per thread).
 template <bool GHOST>
-__global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant__ LatParams27 P)
+__global__ void __launch_bounds__(LBLOCK, 3) lattice27_kernel(const __grid_constant__ LatParams27 P)
 {
     __shared__ Box27 sB;
     __shared__ Dyn27 sK;
@@ -274,6 +303,7 @@ __global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant
     float d[Q27];
     int mn[3] = {0, 0, 0};
     bool in_new = false;
+    unsigned nb_new = 0u;
     // a skipped node reads nothing: its cube's maps may be rewritten meanwhile
     // by the particle kernel beside this pass
     if (skip) valid = false;
@@ -282,7 +312,7 @@ __global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant
 #pragma unroll
         for (int i = 0; i < Q27; ++i) d[i] = 0.0f;
     } else {
-        kind = pre_collision(B, K, rows, A, X, Y, Z, nd, P.first != 0, d, mn, in_new);
+        kind = pre_collision(B, K, rows, A, X, Y, Z, nd, P.first != 0, d, mn, in_new, nb_new);
     }
     // integer sums for the particle: links of the new map, covered and uncovered nodes
     long long aF[3] = {0, 0, 0}, aT[3] = {0, 0, 0};
@@ -313,11 +343,10 @@ __global__ void __launch_bounds__(LBLOCK) lattice27_kernel(const __grid_constant
         const float g[3] = {K.g[0], K.g[1], K.g[2]};
         collide27<GHOST>(d, B.omega, B.rho0f, g, K.eps);
         if (in_new && valid) {
-            const uint64_t* map_new = rows + (size_t)K.slot_new * RW;
 #pragma unroll
             for (int b = 1; b < Q27; ++b) {
                 const int cx = cx27(b), cy = cy27(b), cz = cz27(b);
-                if (!bit_at(map_new, K.S, mn[0] + cx, mn[1] + cy, mn[2] + cz)) continue;
+                if (!nb_bit(nb_new, cx, cy, cz)) continue;
                 const long long a = fixp(2.0f * d[b]);
                 const long long gx = cx * a, gy = cy * a, gz = cz * a;
                 aF[0] += gx; aF[1] += gy; aF[2] += gz;
@@ -1023,7 +1052,8 @@ __global__ void __launch_bounds__(LBLOCK) fields27_kernel(const __grid_constant_
     float d[Q27];
     int mn[3] = {0, 0, 0};
     bool in_new = false;
-    const int kind = pre_collision(B, K, rows, P.src + B.off, X, Y, Z, node, P.nopull != 0, d, mn, in_new);
+    unsigned nb_new = 0;
+    const int kind = pre_collision(B, K, rows, P.src + B.off, X, Y, Z, node, P.nopull != 0, d, mn, in_new, nb_new);
     const bool solid = kind == K_SOLID || kind == K_COVERED;
     float drho = 0.0f, j[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
