@@ -10,7 +10,13 @@
 // core matrices are 128 bytes apart along K and 1024 bytes apart along the
 // rows); one elected thread issues four tcgen05.mma (M = 128, K = 16 each)
 // accumulating in tensor memory and commits them to an mbarrier that every
-// thread waits on (bounded) before the next chunk overwrites the stage.  The
+// thread waits on (bounded).  Two stages: while the products of chunk c run,
+// the threads stage chunk c + 1 into the other stage (whose products, those of
+// chunk c - 1, were waited for).  The staging loads are coalesced for either
+// operand layout: 16-byte loads of 8 consecutive K (K-major operands) or of 8
+// consecutive rows (transposed operands) where strides and alignment allow,
+// else one element per thread with consecutive threads on the contiguous
+// index.  The
 // epilogue: warp w reads TMEM lanes 32w..32w+31 (one output row per lane) with
 // tcgen05.ld, adds the bias, applies ReLU and writes FP32 and/or BF16.
 // The network is small (8 -> 256 -> 256 -> 21), so the staging is done by
@@ -32,7 +38,8 @@ constexpr int GK = 64;                  // K chunk per staging round
 constexpr int GTHREADS = 128;           // one warpgroup
 constexpr int SMEM_A = GM * GK * 2;     // 16 KiB
 constexpr int SMEM_B = GN * GK * 2;     // 32 KiB
-constexpr int GEMM_SMEM = SMEM_A + SMEM_B;
+constexpr int GEMM_STAGE = SMEM_A + SMEM_B;
+constexpr int GEMM_SMEM = 2 * GEMM_STAGE; // two stages, 96 KiB
 constexpr long long SPIN_LIMIT = 1ll << 24;
 
 struct GemmArgs {
@@ -84,13 +91,78 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
 // byte offset of element (r, k) of a staged 64-wide K chunk
 __device__ __forceinline__ int core_off(int r, int k) { return (((r >> 3) * 8 + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1); }
 
+// Rows [r0, r0 + rows) x K columns [k0, k0 + 64) of X (element (r, k) at
+// X[r s_r + k s_k]) into a stage in the core-matrix layout; rows at or beyond
+// nrow and columns at or beyond K are zero.  rows is a multiple of 8, r0 and k0
+// of 64.
+__device__ __forceinline__ void stage_operand(const __nv_bfloat16* X, long long s_r, long long s_k, int r0, int rows,
+                                              int nrow, int k0, int K, unsigned char* dst, int tid)
+{
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    const bool al = (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+    if (s_k == 1 && al && (s_r & 7) == 0) {
+        // K-major: 8 consecutive K per thread, one 16-byte load and store
+        for (int idx = tid; idx < rows * (GK / 8); idx += GTHREADS) {
+            const int r = idx / (GK / 8), kc = (idx % (GK / 8)) * 8;
+            const int m = r0 + r, kk = k0 + kc;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m < nrow) {
+                if (kk + 8 <= K) {
+                    v = __ldg(reinterpret_cast<const uint4*>(X + m * s_r + kk));
+                } else {
+                    unsigned w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (kk + j < K)
+                            w[j >> 1] |= (unsigned)__bfloat16_as_ushort(X[m * s_r + kk + j]) << (16 * (j & 1));
+                    v = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            *reinterpret_cast<uint4*>(dst + core_off(r, kc)) = v;
+        }
+    } else if (s_r == 1 && al && (s_k & 7) == 0) {
+        // transposed: 8 consecutive rows per thread, one 16-byte load, eight
+        // 2-byte stores (the rows of a core matrix are 16 bytes apart)
+        for (int idx = tid; idx < (rows / 8) * GK; idx += GTHREADS) {
+            const int rc = (idx % (rows / 8)) * 8, k = idx / (rows / 8);
+            const int m = r0 + rc, kk = k0 + k;
+            unsigned w[4] = {0u, 0u, 0u, 0u};
+            if (kk < K && m + 8 <= nrow) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4*>(X + m + kk * s_k));
+                w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (kk < K && m + j < nrow)
+                        w[j >> 1] |= (unsigned)__bfloat16_as_ushort(X[m + j + kk * s_k]) << (16 * (j & 1));
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<unsigned short*>(dst + core_off(rc + j, k)) = (unsigned short)(w[j >> 1] >> (16 * (j & 1)));
+        }
+    } else if (s_r == 1) {
+        // transposed, unaligned: consecutive threads on consecutive rows
+        for (int idx = tid; idx < rows * GK; idx += GTHREADS) {
+            const int r = idx % rows, k = idx / rows;
+            const int m = r0 + r, kk = k0 + k;
+            *reinterpret_cast<__nv_bfloat16*>(dst + core_off(r, k)) = (m < nrow && kk < K) ? X[m + kk * s_k] : zero;
+        }
+    } else {
+        for (int idx = tid; idx < rows * GK; idx += GTHREADS) {
+            const int r = idx / GK, k = idx % GK;
+            const int m = r0 + r, kk = k0 + k;
+            *reinterpret_cast<__nv_bfloat16*>(dst + core_off(r, k)) =
+                (m < nrow && kk < K) ? X[m * s_r + kk * s_k] : zero;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(GTHREADS) gemm_kernel(const GemmArgs g)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ unsigned long long bar;
     __shared__ unsigned s_tmem;
-    unsigned char* sa = sm;
-    unsigned char* sb = sm + SMEM_A;
+    // stage b: A at sm + b GEMM_STAGE, B SMEM_A after it
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
     const int nrem = g.N - n0;
@@ -112,30 +184,22 @@ __global__ void __launch_bounds__(GTHREADS) gemm_kernel(const GemmArgs g)
     const unsigned idesc = idesc_bf16(GM, nt);
     unsigned phase = 0;
     bool ok = true;
-    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = 0; k0 < g.K; k0 += GK) {
-        for (int idx = tid; idx < GM * GK; idx += GTHREADS) {
-            const int r = idx / GK, k = idx % GK;
-            const int m = m0 + r, kk = k0 + k;
-            const __nv_bfloat16 v = (m < g.M && kk < g.K) ? g.A[m * g.a_sm + kk * g.a_sk] : zero;
-            *reinterpret_cast<__nv_bfloat16*>(sa + core_off(r, k)) = v;
-        }
-        for (int idx = tid; idx < nt * GK; idx += GTHREADS) {
-            const int r = idx / GK, k = idx % GK;
-            const int n = n0 + r, kk = k0 + k;
-            const __nv_bfloat16 v = (n < g.N && kk < g.K) ? g.B[n * g.b_sn + kk * g.b_sk] : zero;
-            *reinterpret_cast<__nv_bfloat16*>(sb + core_off(r, k)) = v;
-        }
-        // generic-proxy writes of the stage before the tensor core reads them
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+    const int nchunk = (g.K + GK - 1) / GK;
+    stage_operand(g.A, g.a_sm, g.a_sk, m0, GM, g.M, 0, g.K, sm, tid);
+    stage_operand(g.B, g.b_sn, g.b_sk, n0, nt, g.N, 0, g.K, sm + SMEM_A, tid);
+    // generic-proxy writes of the stage before the tensor core reads them
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    for (int c = 0; c < nchunk; ++c) {
+        unsigned char* sa = sm + (c & 1) * GEMM_STAGE;
+        unsigned char* sb = sa + SMEM_A;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int kk = 0; kk < GK / 16; ++kk) {
                 const unsigned long long ad = sdesc(smem_u32(sa) + kk * 256u, 128u, 1024u);
                 const unsigned long long bd = sdesc(smem_u32(sb) + kk * 256u, 128u, 1024u);
-                const unsigned acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+                const unsigned acc = (c > 0 || kk > 0) ? 1u : 0u;
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
                              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
@@ -144,6 +208,13 @@ __global__ void __launch_bounds__(GTHREADS) gemm_kernel(const GemmArgs g)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&bar))
                          : "memory");
+        }
+        if (c + 1 < nchunk) {
+            // the next chunk into the other stage while these products run
+            unsigned char* na = sm + ((c + 1) & 1) * GEMM_STAGE;
+            stage_operand(g.A, g.a_sm, g.a_sk, m0, GM, g.M, (c + 1) * GK, g.K, na, tid);
+            stage_operand(g.B, g.b_sn, g.b_sk, n0, nt, g.N, (c + 1) * GK, g.K, na + SMEM_A, tid);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         const bool got = mbar_wait(&bar, phase);
         phase ^= 1u;

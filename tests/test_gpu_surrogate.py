@@ -42,6 +42,9 @@ def _normwise(a, b):
     (1, 1, 1, False, False, True, False),
     (300, 300, 1000, True, True, True, False),
     (37, 16, 64, True, False, False, True),
+    # transposed operands whose strides allow 16-byte staging loads, with
+    # partial tiles in M (8 rows of a third tile), N (200 of 208) and K
+    (264, 200, 136, True, True, True, True),
 ])
 def test_gemm_matches_fp64_product_of_the_same_bf16_operands(M, N, K, transA, transB, bias, relu):
     g = np.random.default_rng(M * 7 + N * 3 + K)
