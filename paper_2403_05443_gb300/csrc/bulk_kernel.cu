@@ -33,14 +33,15 @@ __global__ void __launch_bounds__(KBLOCK, 2) bulk_kernel(const BulkParams P, int
         bulk_tile<St, FIRST>(P, u / WPB, (u % WPB) * 32 + lane);
 }
 
+// two blocks per SM of the current device (queried on every launch: a process
+// may drive devices of different sizes; the grid-stride loop covers every unit
+// whatever the grid)
 static int bulk_grid(int tiles)
 {
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            nsm = 1;
-    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        nsm < 1)
+        nsm = 1;
     const int g = 2 * nsm;
     return tiles < g ? tiles : g;
 }

@@ -266,12 +266,10 @@ __global__ void __launch_bounds__(GTHREADS) gemm_kernel(const GemmArgs g)
 
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s)
 {
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // the opt-in to 96 KiB of dynamic shared memory is per device: set it on
+    // every launch (a cheap call) rather than once per process
+    const cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+    if (e != cudaSuccess) return e;
     const dim3 grid((g.M + GM - 1) / GM, (g.N + GN - 1) / GN);
     gemm_kernel<<<grid, GTHREADS, GEMM_SMEM, s>>>(g);
     return cudaGetLastError();
