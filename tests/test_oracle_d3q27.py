@@ -163,14 +163,18 @@ def test_d3q27_links_match_brute_force(seed):
     assert len(got) > len(got19)
 
 
-def test_d3q27_momentum_and_mass_through_cover_uncover():
+@pytest.mark.parametrize("collision", [0, 1])
+def test_d3q27_momentum_and_mass_through_cover_uncover(collision):
     """A fast particle crossing nodes: fluid + particle momentum + the pending
     remap impulse constant to round-off; fluid mass + the two pending mass
-    amounts constant (the remap's mass return, Appendix step 8).  The fluid
-    starts perturbed: summing some 150,000 equal rest populations would round
-    the same way everywhere and hide the balance under 1e-8 of drift."""
+    amounts constant (the remap's mass return, Appendix step 8); with BGK and
+    with the paper's ghost-mode collision (mass and momentum are hydrodynamic
+    modes: the collision keeps both).  The fluid starts perturbed: summing some
+    150,000 equal rest populations would round the same way everywhere and hide
+    the balance under 1e-8 of drift."""
     g = rng(7)
-    s = O.Sim(_box(20, 18, 22, 0.9), [particle((4.5, 2.5, 2.0), (10.3, 9.1, 11.7), random_quaternion(g),
+    s = O.Sim(_box(20, 18, 22, 0.9, collision=collision),
+              [particle((4.5, 2.5, 2.0), (10.3, 9.1, 11.7), random_quaternion(g),
                                                 U=(0.03, -0.02, 0.025), Om=(0.004, 0.006, -0.005), density=5.0)],
               nthreads=2)
     _, w = O.lattice(Q)
