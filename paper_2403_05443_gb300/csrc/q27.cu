@@ -596,11 +596,12 @@ __device__ __forceinline__ bool gj_inv6_warp_f32(float (&col)[6], int lane)
 // warp: the inverse in FP32, then iterative refinement, x += A^-1 (rhs - A x)
 // with the residual in FP64.  Each step multiplies the error by about cond(A)
 // times the FP32 rounding; three steps bring it to FP64 rounding for these
-// systems (mass, inertia and drag matrices: cond(A) of order 10-10^3).  The
-// FP32 inverse keeps the chain of dependent FP64 operations short (a dependent
-// FP64 operation costs about 0.1 us on this part; the Gauss-Jordan elimination in
-// FP64 took 15 us).  s_Ai: 36 floats of scratch.  Writes x6 (lanes 0..5);
-// false if a pivot vanishes.
+// systems (mass, inertia and drag matrices: cond(A) of order 10-10^3).  Only
+// the residuals are FP64, so the chain of dependent FP64 operations is short;
+// measured beside the bulk pass the solve still takes about as long as a
+// Gauss-Jordan elimination in FP64 (about 15 us), which points at latency and
+// instruction fetch rather than arithmetic.  s_Ai: 36 floats of scratch.
+// Writes x6 (lanes 0..5); false if a pivot vanishes.
 __device__ bool q27_solve6(const double* A6, const double* rhs, double* x6, float* s_Ai, int lane)
 {
     float col[6];
