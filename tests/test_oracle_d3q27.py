@@ -198,8 +198,8 @@ def test_d3q27_momentum_and_mass_through_cover_uncover(collision):
     assert changed > 20
 
 
-def _settle_sphere(a, L, F, q, tol=2e-5, max_steps=20000):
-    b = box(L, L, L, 1.0, counter_force=1)
+def _settle_sphere(a, L, F, q, tol=2e-5, max_steps=20000, tau=1.0, collision=0):
+    b = box(L, L, L, tau, counter_force=1, collision=collision)
     b["lattice"] = q
     s = O.Sim(b, [particle((a, a, a), (L / 2 + 0.25, L / 2 - 0.125, L / 2 + 0.375), F_ext=(F, 0.0, 0.0))])
     prev = None
@@ -227,6 +227,20 @@ def test_d3q27_sphere_settling_absolute_scale_and_lattice_comparison():
     assert abs((U2 - U1) / want - 1.0) < 0.05
     U1_19 = _settle_sphere(a, L1, F, 19)
     assert abs(U1 / U1_19 - 1.0) < 0.03
+
+
+def test_d3q19_and_d3q27_settle_alike_under_the_ghost_mode_collision():
+    """The lattice comparison of Sec. III.A with the paper's own collision at
+    tau = 0.8, where it differs from BGK: the same sphere settles within a few
+    per cent on both lattices, and the ghost-mode and BGK velocities agree to
+    the same order (the two collisions share mass, momentum and viscosity)."""
+    a, F, L = 3.0, 1e-4, 20
+    U27 = _settle_sphere(a, L, F, Q, tau=0.8, collision=1)
+    U19 = _settle_sphere(a, L, F, 19, tau=0.8, collision=1)
+    U27b = _settle_sphere(a, L, F, Q, tau=0.8, collision=0)
+    assert U27 > 0 and U19 > 0
+    assert abs(U27 / U19 - 1.0) < 0.03
+    assert abs(U27 / U27b - 1.0) < 0.03
 
 
 # ---------------------------------------------------------------------------
