@@ -157,7 +157,7 @@ __device__ __forceinline__ int pre_collision(const Box27& B, const Dyn27& K, con
 //   d_i' = deq_i + (1 - omega) w_i [3 c_i.j_neq + 4.5 (c_i c_i - I/3) : Pi_neq] + S_i,
 // j_neq = j - rho u = -g/2 (u carries the half-force shift) and
 // Pi_neq = sum_i c_i c_i d_i - drho/3 I - rho u u (the rest state w rho0
-// contributes rho0/3 I, the equilibrium rho/3 I + rho u u).  The 18 modes of
+// contributes rho0/3 I, the equilibrium rho/3 I + rho u u).  The 17 modes of
 // D3Q27 beyond these ten leave at equilibrium.  At omega = 1 it is BGK.
 template <bool GHOST>
 __device__ __forceinline__ void collide27(float (&d)[Q27], float omega, float rho0, const float g[3], float eps)

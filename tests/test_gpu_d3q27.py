@@ -168,7 +168,7 @@ def test_d3q27_fast_particle_covers_and_uncovers_nodes():
 @pytest.mark.parametrize("tau", [0.62, 0.8, 1.3])
 def test_d3q27_ghost_mode_collision(tau):
     """The paper's collision (Sec. II.A: the non-equilibrium part projected on
-    the hydrodynamic modes and relaxed with tau, the other 18 modes of D3Q27
+    the hydrodynamic modes and relaxed with tau, the other 17 modes of D3Q27
     set to equilibrium; lb_options.collision = 1) with a spheroid under a force
     and a torque, a box without a particle beside it, and a fast particle that
     covers and uncovers nodes."""

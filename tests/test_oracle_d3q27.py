@@ -247,7 +247,7 @@ def test_d3q19_and_d3q27_settle_alike_under_the_ghost_mode_collision():
 # The paper's collision on D3Q27 (Sec. II.A: one relaxation time for the
 # non-conserved hydrodynamic modes, the others relaxed at once; box option
 # collision = 1).  The 27-velocity set has more non-hydrodynamic modes than
-# D3Q19 (18 of them), all of which must leave the collision at equilibrium.
+# D3Q19 (17 of them, against 9), all of which must leave the collision at equilibrium.
 
 def _uniform_collision27(tau, collision, g=(2e-5, -1e-5, 3e-5), seed=5):
     """One step of a uniform random non-equilibrium state in a periodic box:
