@@ -599,8 +599,9 @@ __device__ __forceinline__ bool gj_inv6_warp_f32(float (&col)[6], int lane)
 // systems (mass, inertia and drag matrices: cond(A) of order 10-10^3).  Only
 // the residuals are FP64, so the chain of dependent FP64 operations is short;
 // measured beside the bulk pass the solve still takes about as long as a
-// Gauss-Jordan elimination in FP64 (about 15 us), which points at latency and
-// instruction fetch rather than arithmetic.  s_Ai: 36 floats of scratch.
+// Gauss-Jordan elimination in FP64 (about 15 us; with the pivot loop rolled up,
+// a fifth of the code, 17.5 us), so its time is the latency of its dependent
+// chain, not arithmetic or instruction fetch.  s_Ai: 36 floats of scratch.
 // Writes x6 (lanes 0..5); false if a pivot vanishes.
 __device__ bool q27_solve6(const double* A6, const double* rhs, double* x6, float* s_Ai, int lane)
 {
